@@ -1,0 +1,760 @@
+/*
+ * pn_oracle.c -- TEST INFRASTRUCTURE, not part of the product.
+ *
+ * A plain, slow, FP64 CPU evaluation of the limited first-order
+ * post-Newtonian (1PN) N-body equations of T. Tatekawa, "Accelerating
+ * N-body simulation of self-gravitating systems with limited first-order
+ * post-Newtonian approximation" (arXiv:1801.07986):
+ *
+ *   Section 2, Eq. 1-3  acceleration of the massive body ("#1", index 0 here)
+ *   Section 2, Eq. 4-6  acceleration of a low-mass star i
+ *   Section 2, Eq. 7-8  1PN energy and momentum
+ *   Section 4, Eq. 10   Plummer softening between stars
+ *
+ * plus, for cross-checks only, the general EIH equations and EIH energy
+ * (Einstein, Infeld & Hoffmann 1938; Lorentz & Droste 1917), of which the
+ * paper's equations are the one-heavy-body limit (Section 2).
+ *
+ * Every sum is written the way the paper prints it: one loop per printed
+ * sum, the heavy body's double sums over (j, k) as explicit double loops,
+ * no algebraic regrouping.  Accumulation is compensated (Knuth TwoSum), and
+ * each target's sum runs in a fixed order, so results do not depend on the
+ * number of OpenMP threads.  Build with -ffp-contract=off.
+ *
+ * Only the tests, the package's smoke check and the CPU-baseline leg of the
+ * benchmark may load this library.  It shares no code with the CUDA path.
+ *
+ * Readings of the printed equations (the paper is garbled in places):
+ *  R1  x_ab = x_a - x_b and v_ab = v_a - v_b for every pair, although the
+ *      text below Eq. 1 and below Eq. 6 prints the opposite order; only this
+ *      order makes the Newtonian terms attractive and reproduces EIH.
+ *  R2  Eq. 4's star-star Newtonian term divides by r_ij^3 (the cube is
+ *      missing in print).
+ *  R3  Eq. 2's (3/2)(v_j . n_1j) term is squared, as in Eq. 6 and EIH.
+ *  R4  Eq. 5's v_a is v_i.
+ *  R5  Sums over j, k run over stars; a star sum for target i skips j = i.
+ *      In Eq. 3 the first two double sums skip k = j; the last one (the
+ *      terms that replace the heavy body's velocity) keeps k = j, like the
+ *      explicit self term printed in Eq. 6.
+ *  R6  The heavy body's velocity never enters Eqs. 1-6 (they assume the
+ *      zero-momentum frame); it is evolved as state and used in Eqs. 7-8.
+ *  R7  Softening (Eq. 10) applies to star-star separations only, to every
+ *      occurrence of r_ij (1/r, 1/r^3, r^2, and n_ij = x_ij / r_ij); body-star
+ *      separations are never softened.
+ *  R8  In Eq. 7 the last double sum keeps i = j; the other double sums of
+ *      Eqs. 7-8 run over ordered pairs i != j.
+ *  R9  Integrator (the paper's Section 4 uses RK4): kick-drift-kick leapfrog
+ *      whose force after the drift is evaluated at the predicted velocity
+ *      v_half + (dt/2) a_old (vel_mode 0) or at v_half (vel_mode 1).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ---------------------------------------------------------------- sums -- */
+
+typedef struct { double s, c; } ksum;              /* value = s + c */
+typedef struct { ksum k[3]; } ksum3;
+
+static void kadd(ksum *a, double x)
+{
+    /* Knuth's TwoSum: s + x = t + e exactly */
+    double t = a->s + x;
+    double bp = t - a->s;
+    double e = (a->s - (t - bp)) + (x - bp);
+    a->s = t;
+    a->c += e;
+}
+
+static double kval(const ksum *a) { return a->s + a->c; }
+
+/* acc += f * w (vector) */
+static void kadd3(ksum3 *a, double f, const double w[3])
+{
+    kadd(&a->k[0], f * w[0]);
+    kadd(&a->k[1], f * w[1]);
+    kadd(&a->k[2], f * w[2]);
+}
+
+static void kval3(const ksum3 *a, double out[3])
+{
+    out[0] = kval(&a->k[0]);
+    out[1] = kval(&a->k[1]);
+    out[2] = kval(&a->k[2]);
+}
+
+/* ------------------------------------------------------------- vectors -- */
+
+static double dot(const double a[3], const double b[3])
+{
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+static void sub(const double a[3], const double b[3], double out[3])
+{
+    out[0] = a[0] - b[0];
+    out[1] = a[1] - b[1];
+    out[2] = a[2] - b[2];
+}
+
+static const double *row(const double *p, int64_t i) { return p + 3 * i; }
+
+static int g_threads = 0;
+
+void orc_set_threads(int n) { g_threads = n; }
+
+int orc_get_threads(void)
+{
+#ifdef _OPENMP
+    return g_threads > 0 ? g_threads : omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ============================================== limited 1PN, Section 2 == */
+
+/*
+ * Acceleration of star i (1 <= i < n), Eq. 4 with Eq. 5 and Eq. 6.
+ * out = Newtonian part + inv_c2 * ([a_i]_BH + [a_i]_Cross).
+ */
+static void star_accel(int64_t n, const double *x, const double *v,
+                       const double *m, double G, double inv_c2, double eps,
+                       int64_t i, double out[3])
+{
+    const double M = m[0];
+    const double *x1 = row(x, 0);
+    const double *xi = row(x, i), *vi = row(v, i);
+    const double mi = m[i];
+    double xi1[3];
+    sub(xi, x1, xi1);                                 /* x_i1 = x_i - x_1 */
+    const double ri1 = sqrt(dot(xi1, xi1));
+    const double ri1_2 = ri1 * ri1, ri1_3 = ri1_2 * ri1, ri1_4 = ri1_3 * ri1;
+    const double vi2 = dot(vi, vi);
+    const double vi_xi1 = dot(vi, xi1);
+    const double e2 = eps * eps;
+    ksum3 newt, pn;
+    memset(&newt, 0, sizeof newt);
+    memset(&pn, 0, sizeof pn);
+
+    /* Eq. 4, first term: -G M x_i1 / r_i1^3 */
+    kadd3(&newt, -G * M / ri1_3, xi1);
+
+    /* Eq. 5: [a_i]_BH = G M x_i1/r_i1^3 (4GM/r_i1 - v_i^2)
+     *                  + 4 G M/r_i1^3 (v_i . x_i1) v_i                       */
+    kadd3(&pn, G * M / ri1_3 * (4.0 * G * M / ri1 - vi2), xi1);
+    kadd3(&pn, 4.0 * G * M / ri1_3 * vi_xi1, vi);
+
+    /* Eq. 6, first line: 5 G^2 m_i M x_i1/r_i1^4
+     *                    - G m_i/r_i1^3 [4 v_i^2 x_i1 - 7 (v_i . x_i1) v_i]  */
+    kadd3(&pn, 5.0 * G * G * mi * M / ri1_4, xi1);
+    kadd3(&pn, -G * mi / ri1_3 * 4.0 * vi2, xi1);
+    kadd3(&pn, G * mi / ri1_3 * 7.0 * vi_xi1, vi);
+
+    for (int64_t j = 1; j < n; ++j) {
+        if (j == i)
+            continue;
+        const double *xj = row(x, j), *vj = row(v, j);
+        const double mj = m[j];
+        double xij[3], xj1[3], vij[3], w[3];
+        sub(xi, xj, xij);                             /* x_ij = x_i - x_j */
+        sub(xj, x1, xj1);                             /* x_j1 = x_j - x_1 */
+        sub(vi, vj, vij);                             /* v_ij = v_i - v_j */
+        /* Eq. 10: softened star-star separation */
+        const double rij_2 = dot(xij, xij) + e2;
+        const double rij = sqrt(rij_2);
+        const double rij_3 = rij_2 * rij;
+        const double rj1 = sqrt(dot(xj1, xj1));
+        const double rj1_3 = rj1 * rj1 * rj1;
+
+        /* Eq. 4, second term: -sum_j G m_j x_ij / r_ij^3 */
+        kadd3(&newt, -G * mj / rij_3, xij);
+
+        /* Eq. 6, second line:
+         * sum_j G^2 m_j M x_i1/r_i1^3
+         *      (4/r_ij + 5/(4 r_j1) + r_i1^2/(4 r_j1^3) - r_ij^2/(4 r_j1^3)) */
+        kadd3(&pn, G * G * mj * M / ri1_3 *
+                   (4.0 / rij + 5.0 / (4.0 * rj1) + ri1_2 / (4.0 * rj1_3)
+                    - rij_2 / (4.0 * rj1_3)), xi1);
+
+        /* Eq. 6, third line:
+         * sum_j G^2 m_j M x_ij/r_ij^3
+         *      (4/r_i1 + 5/(4 r_j1) - r_i1^2/(4 r_j1^3) + r_ij^2/(4 r_j1^3)) */
+        kadd3(&pn, G * G * mj * M / rij_3 *
+                   (4.0 / ri1 + 5.0 / (4.0 * rj1) - ri1_2 / (4.0 * rj1_3)
+                    + rij_2 / (4.0 * rj1_3)), xij);
+
+        /* Eq. 6, fourth line:
+         * -7/2 sum_j G^2 m_j M x_j1/r_j1^3 (1/r_ij - 1/r_i1)                 */
+        kadd3(&pn, -3.5 * G * G * mj * M / rj1_3 * (1.0 / rij - 1.0 / ri1), xj1);
+
+        /* Eq. 6, fifth line:
+         * -sum_j G m_j/r_i1^3 [4 (v_i . v_j) x_i1 - 3 (v_j . x_i1) v_i
+         *                      - 4 (v_i . x_i1) v_j]                         */
+        const double g5 = G * mj / ri1_3;
+        kadd3(&pn, -g5 * 4.0 * dot(vi, vj), xi1);
+        kadd3(&pn, g5 * 3.0 * dot(vj, xi1), vi);
+        kadd3(&pn, g5 * 4.0 * vi_xi1, vj);
+
+        /* Eq. 6, sixth line:
+         * sum_j G m_j x_ij/r_ij^3 [v_i^2 - 2 |v_ij|^2 + 3/2 (v_j . n_ij)^2]  */
+        const double vj_nij = dot(vj, xij) / rij;
+        kadd3(&pn, G * mj / rij_3 *
+                   (vi2 - 2.0 * dot(vij, vij) + 1.5 * vj_nij * vj_nij), xij);
+
+        /* Eq. 6, seventh line:
+         * sum_j G m_j/r_ij^3 [x_ij . (4 v_i - 3 v_j)] v_ij                    */
+        w[0] = 4.0 * vi[0] - 3.0 * vj[0];
+        w[1] = 4.0 * vi[1] - 3.0 * vj[1];
+        w[2] = 4.0 * vi[2] - 3.0 * vj[2];
+        kadd3(&pn, G * mj / rij_3 * dot(xij, w), vij);
+    }
+
+    double an[3], ap[3];
+    kval3(&newt, an);
+    kval3(&pn, ap);
+    out[0] = an[0] + inv_c2 * ap[0];
+    out[1] = an[1] + inv_c2 * ap[1];
+    out[2] = an[2] + inv_c2 * ap[2];
+}
+
+/*
+ * Inner k-sums of the three double sums of Eq. 3 for one outer index j:
+ *   sum_{k != j} G^2 m_j m_k x_1j/r_1j^3
+ *        (4/r_1k + 5/(4 r_jk) - r_1k^2/(4 r_jk^3) + r_1j^2/(4 r_jk^3))
+ * - 7/2 sum_{k != j} G^2 m_j m_k x_jk/(r_jk^3 r_1j)
+ * - sum_k G m_j m_k/(M r_1j^3)
+ *        [4 (v_j . v_k) x_1j - 3 (v_j . x_1j) v_k - 4 (v_k . x_1j) v_j]
+ */
+static void bh_double_sum_row(int64_t n, const double *x, const double *v,
+                              const double *m, double G, double eps,
+                              int64_t j, double out[3])
+{
+    const double M = m[0];
+    const double *x1 = row(x, 0);
+    const double *xj = row(x, j), *vj = row(v, j);
+    const double mj = m[j];
+    const double e2 = eps * eps;
+    double x1j[3];
+    sub(x1, xj, x1j);                                 /* x_1j = x_1 - x_j */
+    const double r1j = sqrt(dot(x1j, x1j));
+    const double r1j_2 = r1j * r1j, r1j_3 = r1j_2 * r1j;
+    const double vj_x1j = dot(vj, x1j);
+    ksum3 acc;
+    memset(&acc, 0, sizeof acc);
+    for (int64_t k = 1; k < n; ++k) {
+        const double *xk = row(x, k), *vk = row(v, k);
+        const double mk = m[k];
+        double x1k[3];
+        sub(x1, xk, x1k);
+        /* terms that replace the heavy body's velocity: k = j included */
+        const double g = G * mj * mk / (M * r1j_3);
+        kadd3(&acc, -g * 4.0 * dot(vj, vk), x1j);
+        kadd3(&acc, g * 3.0 * vj_x1j, vk);
+        kadd3(&acc, g * 4.0 * dot(vk, x1j), vj);
+        if (k == j)
+            continue;
+        const double r1k_2 = dot(x1k, x1k);
+        const double r1k = sqrt(r1k_2);
+        double xjk[3];
+        sub(xj, xk, xjk);
+        const double rjk_2 = dot(xjk, xjk) + e2;      /* Eq. 10 */
+        const double rjk = sqrt(rjk_2);
+        const double rjk_3 = rjk_2 * rjk;
+        kadd3(&acc, G * G * mj * mk / r1j_3 *
+                    (4.0 / r1k + 5.0 / (4.0 * rjk) - r1k_2 / (4.0 * rjk_3)
+                     + r1j_2 / (4.0 * rjk_3)), x1j);
+        kadd3(&acc, -3.5 * G * G * mj * mk / (rjk_3 * r1j), xjk);
+    }
+    kval3(&acc, out);
+}
+
+/*
+ * Acceleration of the heavy body, Eq. 1 with Eq. 2 and Eq. 3.
+ * `rows` (length n, scratch) receives the per-j inner double sums.
+ */
+static void bh_accel(int64_t n, const double *x, const double *v,
+                     const double *m, double G, double inv_c2, double eps,
+                     double *rows, double out[3])
+{
+    const double M = m[0];
+    const double *x1 = row(x, 0);
+    ksum3 newt, pn;
+    memset(&newt, 0, sizeof newt);
+    memset(&pn, 0, sizeof pn);
+
+    for (int64_t j = 1; j < n; ++j) {
+        const double *xj = row(x, j), *vj = row(v, j);
+        const double mj = m[j];
+        double x1j[3];
+        sub(x1, xj, x1j);
+        const double r1j = sqrt(dot(x1j, x1j));
+        const double r1j_3 = r1j * r1j * r1j, r1j_4 = r1j_3 * r1j;
+        const double vj_n = dot(vj, x1j) / r1j;
+        /* Eq. 1: -sum_j G m_j x_1j / r_1j^3 */
+        kadd3(&newt, -G * mj / r1j_3, x1j);
+        /* Eq. 2: sum_j G m_j x_1j/r_1j^3 (5GM/r_1j - 2 v_j^2 + 3/2 (v_j.n_1j)^2)
+         *        + 3 sum_j G m_j/r_1j^3 (v_j . x_1j) v_j                     */
+        kadd3(&pn, G * mj / r1j_3 *
+                   (5.0 * G * M / r1j - 2.0 * dot(vj, vj) + 1.5 * vj_n * vj_n), x1j);
+        kadd3(&pn, 3.0 * G * mj / r1j_3 * dot(vj, x1j), vj);
+        /* Eq. 3, first line: 4 sum_j G^2 m_j^2 x_1j / r_1j^4 */
+        kadd3(&pn, 4.0 * G * G * mj * mj / r1j_4, x1j);
+    }
+
+    /* Eq. 3, double sums: one row per outer index j, then added in j order */
+    int nt = orc_get_threads();
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
+    for (int64_t j = 1; j < n; ++j)
+        bh_double_sum_row(n, x, v, m, G, eps, j, rows + 3 * j);
+    for (int64_t j = 1; j < n; ++j) {
+        static const double one = 1.0;
+        kadd3(&pn, one, rows + 3 * j);
+    }
+
+    double an[3], ap[3];
+    kval3(&newt, an);
+    kval3(&pn, ap);
+    out[0] = an[0] + inv_c2 * ap[0];
+    out[1] = an[1] + inv_c2 * ap[1];
+    out[2] = an[2] + inv_c2 * ap[2];
+}
+
+static int check_args(int64_t n, const void *x, const void *v, const void *m)
+{
+    if (n < 2 || !x || !v || !m)
+        return 1;
+    return 0;
+}
+
+/* Accelerations of all n bodies (body 0 = heavy body).  Returns 0 on success. */
+int orc_accel(int64_t n, const double *x, const double *v, const double *m,
+              double G, double inv_c2, double eps, double *a)
+{
+    if (check_args(n, x, v, m) || !a)
+        return 1;
+    double *rows = (double *)calloc((size_t)(3 * n), sizeof(double));
+    if (!rows)
+        return 2;
+    bh_accel(n, x, v, m, G, inv_c2, eps, rows, a);
+    int nt = orc_get_threads();
+#pragma omp parallel for schedule(dynamic, 8) num_threads(nt)
+    for (int64_t i = 1; i < n; ++i)
+        star_accel(n, x, v, m, G, inv_c2, eps, i, a + 3 * i);
+    free(rows);
+    return 0;
+}
+
+/* Accelerations of the listed targets only (index 0 = heavy body). */
+int orc_accel_rows(int64_t n, const double *x, const double *v, const double *m,
+                   double G, double inv_c2, double eps, int64_t nrows,
+                   const int64_t *targets, double *a_rows)
+{
+    if (check_args(n, x, v, m) || !targets || !a_rows || nrows < 0)
+        return 1;
+    for (int64_t r = 0; r < nrows; ++r)
+        if (targets[r] < 0 || targets[r] >= n)
+            return 1;
+    int nt = orc_get_threads();
+    for (int64_t r = 0; r < nrows; ++r) {
+        if (targets[r] != 0)
+            continue;
+        double *rows = (double *)calloc((size_t)(3 * n), sizeof(double));
+        if (!rows)
+            return 2;
+        bh_accel(n, x, v, m, G, inv_c2, eps, rows, a_rows + 3 * r);
+        free(rows);
+    }
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+    for (int64_t r = 0; r < nrows; ++r)
+        if (targets[r] != 0)
+            star_accel(n, x, v, m, G, inv_c2, eps, targets[r], a_rows + 3 * r);
+    return 0;
+}
+
+/* The heavy body's inner double-sum rows of Eq. 3 for the listed outer
+ * indices j (each 1 <= j < n); used to time a bounded sample of that work. */
+int orc_bh_rows(int64_t n, const double *x, const double *v, const double *m,
+                double G, double eps, int64_t nrows, const int64_t *js,
+                double *out)
+{
+    if (check_args(n, x, v, m) || !js || !out)
+        return 1;
+    for (int64_t r = 0; r < nrows; ++r)
+        if (js[r] < 1 || js[r] >= n)
+            return 1;
+    int nt = orc_get_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+    for (int64_t r = 0; r < nrows; ++r)
+        bh_double_sum_row(n, x, v, m, G, eps, js[r], out + 3 * r);
+    return 0;
+}
+
+/* Newtonian accelerations alone, written out directly: the body-star terms
+ * unsoftened, the star-star terms softened (Eq. 1 and Eq. 4 with c -> inf). */
+int orc_newton_accel(int64_t n, const double *x, const double *m, double G,
+                     double eps, double *a)
+{
+    if (n < 2 || !x || !m || !a)
+        return 1;
+    int nt = orc_get_threads();
+#pragma omp parallel for schedule(dynamic, 8) num_threads(nt)
+    for (int64_t i = 0; i < n; ++i) {
+        ksum3 acc;
+        memset(&acc, 0, sizeof acc);
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i)
+                continue;
+            double d[3];
+            sub(row(x, j), row(x, i), d);             /* points from i to j */
+            double r2 = dot(d, d);
+            if (i != 0 && j != 0)
+                r2 += eps * eps;
+            const double r = sqrt(r2);
+            kadd3(&acc, G * m[j] / (r2 * r), d);
+        }
+        kval3(&acc, a + 3 * i);
+    }
+    return 0;
+}
+
+/*
+ * 1PN energy (Eq. 7) and momentum (Eq. 8).
+ * out[0] = Newtonian energy, out[1] = inv_c2 * (the 1/c^2 bracket of Eq. 7),
+ * out[2..4] = Newtonian momentum, out[5..7] = 1/c^2 part of Eq. 8.
+ */
+int orc_energy(int64_t n, const double *x, const double *v, const double *m,
+               double G, double inv_c2, double eps, double *out)
+{
+    if (check_args(n, x, v, m) || !out)
+        return 1;
+    const double M = m[0];
+    const double *x1 = row(x, 0), *v1 = row(v, 0);
+    const double e2 = eps * eps;
+    const double v1_2 = dot(v1, v1);
+    /* per-star pair sums, each in fixed j order, added in i order below */
+    double *pe = (double *)calloc((size_t)(9 * n), sizeof(double));
+    if (!pe)
+        return 2;
+    int nt = orc_get_threads();
+#pragma omp parallel for schedule(dynamic, 8) num_threads(nt)
+    for (int64_t i = 1; i < n; ++i) {
+        const double *xi = row(x, i), *vi = row(v, i);
+        const double mi = m[i];
+        double xi1[3];
+        sub(xi, x1, xi1);
+        const double r1i = sqrt(dot(xi1, xi1));
+        const double vi2 = dot(vi, vi);
+        ksum s_pot, s_pn, s_3b, s_bb;
+        ksum3 s_p;
+        memset(&s_pot, 0, sizeof s_pot);
+        memset(&s_pn, 0, sizeof s_pn);
+        memset(&s_3b, 0, sizeof s_3b);
+        memset(&s_bb, 0, sizeof s_bb);
+        memset(&s_p, 0, sizeof s_p);
+        for (int64_t j = 1; j < n; ++j) {
+            const double *xj = row(x, j), *vj = row(v, j);
+            const double mj = m[j];
+            double xj1[3];
+            sub(xj, x1, xj1);
+            const double r1j = sqrt(dot(xj1, xj1));
+            /* (1/2) sum_{i,j} G^2 M m_i m_j/(r_1i r_1j), i = j included (R8) */
+            kadd(&s_bb, G * G * M * mi * mj / (r1i * r1j));
+            if (j == i)
+                continue;
+            double xij[3];
+            sub(xi, xj, xij);
+            const double rij = sqrt(dot(xij, xij) + e2);
+            const double nvi = dot(xij, vi) / rij, nvj = dot(xij, vj) / rij;
+            const double gmm = G * mi * mj / rij;
+            /* -(1/2) sum_{i,j} G m_i m_j / r_ij */
+            kadd(&s_pot, -0.5 * gmm);
+            /* (1/4) sum_{i,j} G m_i m_j/r_ij [6 v_i^2 - 7 v_i.v_j - (n.v_i)(n.v_j)] */
+            kadd(&s_pn, 0.25 * gmm * (6.0 * vi2 - 7.0 * dot(vi, vj) - nvi * nvj));
+            /* sum_{i,j} G^2 M m_i m_j / (r_ij r_1i) */
+            kadd(&s_3b, G * gmm * M / r1i);
+            /* Eq. 8: -1/2 sum_{i,j} G m_i m_j/r_ij [v_i + (v_i . n_ij) n_ij] */
+            double w[3];
+            w[0] = vi[0] + nvi * xij[0] / rij;
+            w[1] = vi[1] + nvi * xij[1] / rij;
+            w[2] = vi[2] + nvi * xij[2] / rij;
+            kadd3(&s_p, -0.5 * gmm, w);
+        }
+        double *o = pe + 9 * i;
+        o[0] = kval(&s_pot);
+        o[1] = kval(&s_pn);
+        o[2] = kval(&s_3b);
+        o[3] = kval(&s_bb);
+        kval3(&s_p, o + 4);
+    }
+
+    ksum eN, ePN;
+    ksum3 pN, pPN;
+    memset(&eN, 0, sizeof eN);
+    memset(&ePN, 0, sizeof ePN);
+    memset(&pN, 0, sizeof pN);
+    memset(&pPN, 0, sizeof pPN);
+    /* (1/2) M v_1^2 and M v_1 */
+    kadd(&eN, 0.5 * M * v1_2);
+    kadd3(&pN, M, v1);
+    for (int64_t i = 1; i < n; ++i) {
+        const double *xi = row(x, i), *vi = row(v, i);
+        const double mi = m[i];
+        double xi1[3];
+        sub(xi, x1, xi1);
+        const double r1i = sqrt(dot(xi1, xi1));
+        const double vi2 = dot(vi, vi);
+        const double n1i_vi = dot(xi1, vi) / r1i, n1i_v1 = dot(xi1, v1) / r1i;
+        const double gmm = G * M * mi / r1i;
+        const double *o = pe + 9 * i;
+        /* Eq. 7, Newtonian part */
+        kadd(&eN, 0.5 * mi * vi2);
+        kadd(&eN, o[0]);
+        kadd(&eN, -gmm);
+        /* Eq. 7, 1/c^2 bracket */
+        kadd(&ePN, 0.375 * mi * vi2 * vi2);
+        kadd(&ePN, 1.5 * gmm * vi2);
+        kadd(&ePN, 0.5 * G * G * M * M * mi / (r1i * r1i));
+        kadd(&ePN, o[1]);
+        kadd(&ePN, 0.5 * gmm * (3.0 * v1_2 - 7.0 * dot(v1, vi) - n1i_v1 * n1i_vi));
+        kadd(&ePN, o[2]);
+        kadd(&ePN, 0.5 * o[3]);
+        /* Eq. 8 */
+        kadd3(&pN, mi, vi);
+        kadd3(&pPN, 0.5 * mi * vi2, vi);
+        double w[3];
+        w[0] = vi[0] + n1i_vi * xi1[0] / r1i;
+        w[1] = vi[1] + n1i_vi * xi1[1] / r1i;
+        w[2] = vi[2] + n1i_vi * xi1[2] / r1i;
+        kadd3(&pPN, -0.5 * gmm, w);
+        w[0] = v1[0] + n1i_v1 * xi1[0] / r1i;
+        w[1] = v1[1] + n1i_v1 * xi1[1] / r1i;
+        w[2] = v1[2] + n1i_v1 * xi1[2] / r1i;
+        kadd3(&pPN, -0.5 * gmm, w);
+        static const double one = 1.0;
+        kadd3(&pPN, one, o + 4);
+    }
+    free(pe);
+    double p0[3], p1[3];
+    kval3(&pN, p0);
+    kval3(&pPN, p1);
+    out[0] = kval(&eN);
+    out[1] = inv_c2 * kval(&ePN);
+    for (int d = 0; d < 3; ++d) {
+        out[2 + d] = p0[d];
+        out[5 + d] = inv_c2 * p1[d];
+    }
+    return 0;
+}
+
+/* ============================================== general EIH (checks) == */
+
+/*
+ * EIH accelerations of n bodies of equal status (no softening):
+ *   a_a = sum_{b!=a} G m_b n_ba/r_ab^2 [1 + (1/c^2)(v_a^2 + 2 v_b^2
+ *           - 4 v_a.v_b - 3/2 (n_ab.v_b)^2 - 4 sum_{c!=a} G m_c/r_ac
+ *           - sum_{c!=b} G m_c/r_bc + 1/2 (x_b - x_a).a_b)]
+ *       + (1/c^2) sum_{b!=a} G m_b/r_ab^2 [n_ab.(4 v_a - 3 v_b)] (v_a - v_b)
+ *       + (7/(2 c^2)) sum_{b!=a} G m_b a_b / r_ab
+ * with n_ab = (x_a - x_b)/r_ab and a_b the Newtonian acceleration of b.
+ */
+int orc_eih_accel(int64_t n, const double *x, const double *v, const double *m,
+                  double G, double inv_c2, double *a)
+{
+    if (check_args(n, x, v, m) || !a)
+        return 1;
+    double *aN = (double *)calloc((size_t)(3 * n), sizeof(double));
+    double *phi = (double *)calloc((size_t)n, sizeof(double));
+    if (!aN || !phi) {
+        free(aN);
+        free(phi);
+        return 2;
+    }
+    for (int64_t b = 0; b < n; ++b) {
+        ksum3 acc;
+        ksum p;
+        memset(&acc, 0, sizeof acc);
+        memset(&p, 0, sizeof p);
+        for (int64_t c = 0; c < n; ++c) {
+            if (c == b)
+                continue;
+            double d[3];
+            sub(row(x, c), row(x, b), d);
+            const double r = sqrt(dot(d, d));
+            kadd3(&acc, G * m[c] / (r * r * r), d);
+            kadd(&p, G * m[c] / r);
+        }
+        kval3(&acc, aN + 3 * b);
+        phi[b] = kval(&p);
+    }
+    for (int64_t ia = 0; ia < n; ++ia) {
+        const double *xa = row(x, ia), *va = row(v, ia);
+        ksum3 newt, pn;
+        memset(&newt, 0, sizeof newt);
+        memset(&pn, 0, sizeof pn);
+        for (int64_t ib = 0; ib < n; ++ib) {
+            if (ib == ia)
+                continue;
+            const double *xb = row(x, ib), *vb = row(v, ib);
+            double dba[3], nab[3], w[3], vab[3];
+            sub(xb, xa, dba);                         /* x_b - x_a */
+            const double r = sqrt(dot(dba, dba));
+            nab[0] = -dba[0] / r;
+            nab[1] = -dba[1] / r;
+            nab[2] = -dba[2] / r;
+            const double nab_vb = dot(nab, vb);
+            const double br = dot(va, va) + 2.0 * dot(vb, vb) - 4.0 * dot(va, vb)
+                              - 1.5 * nab_vb * nab_vb - 4.0 * phi[ia] - phi[ib]
+                              + 0.5 * dot(dba, aN + 3 * ib);
+            const double f = G * m[ib] / (r * r * r);
+            kadd3(&newt, f, dba);
+            kadd3(&pn, f * br, dba);
+            w[0] = 4.0 * va[0] - 3.0 * vb[0];
+            w[1] = 4.0 * va[1] - 3.0 * vb[1];
+            w[2] = 4.0 * va[2] - 3.0 * vb[2];
+            sub(va, vb, vab);
+            kadd3(&pn, G * m[ib] / (r * r) * dot(nab, w), vab);
+            kadd3(&pn, 3.5 * G * m[ib] / r, aN + 3 * ib);
+        }
+        double an[3], ap[3];
+        kval3(&newt, an);
+        kval3(&pn, ap);
+        for (int d = 0; d < 3; ++d)
+            a[3 * ia + d] = an[d] + inv_c2 * ap[d];
+    }
+    free(aN);
+    free(phi);
+    return 0;
+}
+
+/* EIH (Lagrangian) energy and momentum.
+ * out[0] Newtonian energy, out[1] inv_c2 * 1PN energy bracket:
+ *   3/8 sum m v^4 + 1/4 sum_{a!=b} G m_a m_b/r_ab (6 v_a^2 - 7 v_a.v_b
+ *   - (n_ab.v_a)(n_ab.v_b)) + 1/2 sum_a sum_{b!=a} sum_{c!=a}
+ *   G^2 m_a m_b m_c / (r_ab r_ac);
+ * out[2..4] sum m_a v_a, out[5..7] inv_c2 * 1PN momentum bracket:
+ *   sum 1/2 m_a v_a^2 v_a - 1/2 sum_{a!=b} G m_a m_b/r_ab
+ *   [v_a + (v_a.n_ab) n_ab].                                              */
+int orc_eih_energy(int64_t n, const double *x, const double *v, const double *m,
+                   double G, double inv_c2, double *out)
+{
+    if (check_args(n, x, v, m) || !out)
+        return 1;
+    ksum e0, e1;
+    ksum3 p0, p1;
+    memset(&e0, 0, sizeof e0);
+    memset(&e1, 0, sizeof e1);
+    memset(&p0, 0, sizeof p0);
+    memset(&p1, 0, sizeof p1);
+    for (int64_t a = 0; a < n; ++a) {
+        const double *xa = row(x, a), *va = row(v, a);
+        const double va2 = dot(va, va);
+        kadd(&e0, 0.5 * m[a] * va2);
+        kadd(&e1, 0.375 * m[a] * va2 * va2);
+        kadd3(&p0, m[a], va);
+        kadd3(&p1, 0.5 * m[a] * va2, va);
+        for (int64_t b = 0; b < n; ++b) {
+            if (b == a)
+                continue;
+            const double *xb = row(x, b), *vb = row(v, b);
+            double d[3];
+            sub(xa, xb, d);
+            const double r = sqrt(dot(d, d));
+            const double na = dot(d, va) / r, nb = dot(d, vb) / r;
+            const double gmm = G * m[a] * m[b] / r;
+            kadd(&e0, -0.5 * gmm);
+            kadd(&e1, 0.25 * gmm * (6.0 * va2 - 7.0 * dot(va, vb) - na * nb));
+            double w[3];
+            w[0] = va[0] + na * d[0] / r;
+            w[1] = va[1] + na * d[1] / r;
+            w[2] = va[2] + na * d[2] / r;
+            kadd3(&p1, -0.5 * gmm, w);
+            for (int64_t c = 0; c < n; ++c) {
+                if (c == a)
+                    continue;
+                double dc[3];
+                sub(xa, row(x, c), dc);
+                const double rc = sqrt(dot(dc, dc));
+                kadd(&e1, 0.5 * G * G * m[a] * m[b] * m[c] / (r * rc));
+            }
+        }
+    }
+    double q0[3], q1[3];
+    kval3(&p0, q0);
+    kval3(&p1, q1);
+    out[0] = kval(&e0);
+    out[1] = inv_c2 * kval(&e1);
+    for (int d = 0; d < 3; ++d) {
+        out[2 + d] = q0[d];
+        out[5 + d] = inv_c2 * q1[d];
+    }
+    return 0;
+}
+
+/* ========================================================= integrator == */
+
+typedef int (*accel_fn)(int64_t, const double *, const double *, const double *,
+                        double, double, double, double *);
+
+static int eih_as_accel(int64_t n, const double *x, const double *v,
+                        const double *m, double G, double inv_c2, double eps,
+                        double *a)
+{
+    (void)eps;
+    return orc_eih_accel(n, x, v, m, G, inv_c2, a);
+}
+
+/*
+ * nsteps of kick-drift-kick leapfrog (reading R9).  `a` holds the
+ * acceleration at the entry state and is updated; x and v are updated.
+ *   v_h = v + dt/2 a;  x = x + dt v_h;
+ *   v_p = v_h + dt/2 a (vel_mode 0)  or  v_h (vel_mode 1);
+ *   a = A(x, v_p);  v = v_h + dt/2 a.
+ */
+static int kdk_steps(accel_fn f, int64_t n, double *x, double *v,
+                     const double *m, double *a, double G, double inv_c2,
+                     double eps, double dt, int64_t nsteps, int vel_mode)
+{
+    if (check_args(n, x, v, m) || !a || nsteps < 0 || !(dt > 0.0) ||
+        (vel_mode != 0 && vel_mode != 1))
+        return 1;
+    double *vh = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    double *vp = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    if (!vh || !vp) {
+        free(vh);
+        free(vp);
+        return 2;
+    }
+    const double h = 0.5 * dt;
+    int rc = 0;
+    for (int64_t s = 0; s < nsteps && rc == 0; ++s) {
+        for (int64_t q = 0; q < 3 * n; ++q) {
+            vh[q] = v[q] + h * a[q];
+            x[q] = x[q] + dt * vh[q];
+            vp[q] = vel_mode == 0 ? vh[q] + h * a[q] : vh[q];
+        }
+        rc = f(n, x, vp, m, G, inv_c2, eps, a);
+        for (int64_t q = 0; q < 3 * n; ++q)
+            v[q] = vh[q] + h * a[q];
+    }
+    free(vh);
+    free(vp);
+    return rc;
+}
+
+int orc_step(int64_t n, double *x, double *v, const double *m, double *a,
+             double G, double inv_c2, double eps, double dt, int64_t nsteps,
+             int vel_mode)
+{
+    return kdk_steps(orc_accel, n, x, v, m, a, G, inv_c2, eps, dt, nsteps, vel_mode);
+}
+
+int orc_eih_step(int64_t n, double *x, double *v, const double *m, double *a,
+                 double G, double inv_c2, double dt, int64_t nsteps, int vel_mode)
+{
+    return kdk_steps(eih_as_accel, n, x, v, m, a, G, inv_c2, 0.0, dt, nsteps, vel_mode);
+}

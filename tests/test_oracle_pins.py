@@ -1,0 +1,404 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper and by the
+mathematics, independent of the oracle's own code.
+
+Each test below would fail on a plausible transcription mistake in the oracle
+(a dropped term, a wrong sign, index or coefficient):
+
+* Newtonian brute force at N = 3 and exact pair antisymmetry;
+* the c -> infinity limit and exact linearity of the result in 1/c^2;
+* the 1PN circular-orbit frequency and periastron advance of a test star
+  (closed forms of the harmonic-gauge test-body equation, Eq. 5);
+* the limited equations (Eq. 1-6) differ from the general EIH equations only
+  by terms of fixed degree in the star mass (Section 2: the star-star 1PN
+  interaction is dropped), checked by exact polynomial-degree ratios;
+* the EIH evaluator itself reproduces the textbook two-body 1PN relative
+  acceleration (Kidder 1995) and two-body 1PN energy (Blanchet 2014), and
+  conserves its energy and momentum through 1PN order;
+* Eq. 7 and Eq. 8 are conserved by Eq. 1-6 through 1PN order (along the
+  flow dE/dt and dP/dt start at O(1/c^4));
+* the integrator's convergence order in each velocity mode;
+* rotation and translation invariance, thread-count independence.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1801_07986_b300.inputs import make_cluster
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b, axis=-1) / np.linalg.norm(b, axis=-1)
+
+
+def _random_state(n, seed, m_bh=1.0, m_star=1e-3, vscale=0.3, spread=1.0):
+    rng = np.random.default_rng(seed)
+    x = rng.normal(size=(n, 3)) * spread
+    x[0] = 0.0
+    v = rng.normal(size=(n, 3)) * vscale
+    m = np.full(n, m_star)
+    m[0] = m_bh
+    return x, v, m
+
+
+# ------------------------------------------------------------ Newtonian --
+
+def test_newton_three_bodies_by_hand(orc):
+    """Hole + 2 stars: Newton's law written out pair by pair (c = inf)."""
+    G, eps = 1.3, 0.05
+    x = np.array([[0.1, -0.2, 0.3], [1.0, 0.5, -0.25], [-0.7, 0.9, 0.4]])
+    v = np.array([[0.0, 0.0, 0.0], [0.1, 0.2, 0.3], [-0.3, 0.1, 0.2]])
+    m = np.array([2.0, 0.3, 0.7])
+
+    def pull(i, j, soft):
+        d = x[j] - x[i]
+        r2 = d @ d + (eps * eps if soft else 0.0)
+        return G * m[j] * d / r2 ** 1.5
+
+    want = np.array([pull(0, 1, False) + pull(0, 2, False),
+                     pull(1, 0, False) + pull(1, 2, True),
+                     pull(2, 0, False) + pull(2, 1, True)])
+    got = orc.accel(x, v, m, G=G, c=np.inf, eps=eps)
+    assert np.all(_rel(got, want) < 1e-15)
+
+
+def test_newton_momentum_conserved_exactly(orc):
+    """sum_a m_a a_a = 0 for the Newtonian part (pair antisymmetry)."""
+    x, v, m = make_cluster(200, 0.1, 11)
+    a = orc.accel(x, v, m, c=np.inf, eps=1e-3)
+    f = (m[:, None] * a).sum(0)
+    scale = (m[:, None] * np.abs(a)).sum(0)
+    assert np.all(np.abs(f) < 1e-14 * scale)
+
+
+def test_c_infinity_is_newtonian_and_pn_is_linear_in_inv_c2(orc):
+    x, v, m = make_cluster(96, 0.2, 12)
+    eps = 1e-3
+    a_inf = orc.accel(x, v, m, c=np.inf, eps=eps)
+    a_newt = orc.newton_accel(x, m, eps=eps)
+    assert np.all(_rel(a_inf, a_newt) < 1e-14)
+    d1 = (orc.accel(x, v, m, c=20.0, eps=eps) - a_inf) * 20.0 ** 2
+    d2 = (orc.accel(x, v, m, c=7.0, eps=eps) - a_inf) * 7.0 ** 2
+    assert np.all(_rel(d1, d2) < 1e-9)
+    assert np.all(np.linalg.norm(d1, axis=1) > 0)
+
+
+# ------------------------------------------------------ test-body closed forms --
+
+def test_circular_orbit_frequency(orc):
+    """Eq. 5 on a circular orbit: omega^2 = GM/r^3 (1 - 3 GM/(c^2 r)) + O(c^-4)."""
+    G, M, c = 1.0, 1.0, 40.0
+    for r in (0.5, 1.0, 3.0):
+        om2 = G * M / r ** 3 * (1.0 - 3.0 * G * M / (c * c * r))
+        vt = math.sqrt(om2) * r
+        x = np.array([[0.0, 0.0, 0.0], [r, 0.0, 0.0]])
+        v = np.array([[0.0, 0.0, 0.0], [0.0, vt, 0.0]])
+        m = np.array([M, 0.0])
+        a = orc.accel(x, v, m, G=G, c=c)[1]
+        want = -om2 * r
+        beta = G * M / (c * c * r)
+        assert abs(a[0] - want) <= 5 * beta ** 2 * abs(want)
+        assert abs(a[1]) < 1e-15 and abs(a[2]) < 1e-15
+        # a wrong 1PN coefficient would show up at O(beta), not O(beta^2)
+        assert abs(a[0] - (-G * M / r ** 2)) > 2.5 * beta * G * M / r ** 2
+
+
+def _periapsis_angles(orc, c, a_orb, e, steps_per_orbit, n_orbits):
+    G, M = 1.0, 1.0
+    rp = a_orb * (1 - e)
+    vp = math.sqrt(G * M * (1 + e) / rp)
+    x = np.array([[0.0, 0.0, 0.0], [rp, 0.0, 0.0]])
+    v = np.array([[0.0, 0.0, 0.0], [0.0, vp, 0.0]])
+    m = np.array([M, 0.0])
+    period = 2 * math.pi * math.sqrt(a_orb ** 3 / (G * M))
+    dt = period / steps_per_orbit
+    a = orc.accel(x, v, m, c=c)
+    angles = []
+    prev = None
+    for _ in range(int(steps_per_orbit * (n_orbits + 0.5))):
+        xn, vn, an = orc.step(x, v, m, a, dt, 1, c=c)
+        s_old = x[1] @ v[1]
+        s_new = xn[1] @ vn[1]
+        if s_old < 0.0 <= s_new:
+            # x.v crosses zero upward at periapsis: interpolate the angle
+            f = -s_old / (s_new - s_old)
+            th0 = math.atan2(x[1, 1], x[1, 0])
+            th1 = math.atan2(xn[1, 1], xn[1, 0])
+            dth = (th1 - th0 + math.pi) % (2 * math.pi) - math.pi
+            th = th0 + f * dth
+            if prev is not None:
+                while th < prev - math.pi:
+                    th += 2 * math.pi
+            angles.append(th)
+            prev = th
+        x, v, a = xn, vn, an
+    return np.array(angles)
+
+
+def test_periastron_advance(orc):
+    """Test star (m = 0) about the hole: the periapsis advances by
+    6 pi G M / (c^2 a (1 - e^2)) per orbit (Eq. 5); the same run at c = inf
+    removes the integrator's own precession."""
+    a_orb, e, c = 1.0, 0.5, 100.0
+    th_pn = _periapsis_angles(orc, c, a_orb, e, 2000, 8)
+    th_n = _periapsis_angles(orc, np.inf, a_orb, e, 2000, 8)
+    k = min(len(th_pn), len(th_n))
+    assert k >= 7
+    rate_pn = np.polyfit(np.arange(k), th_pn[:k], 1)[0]
+    rate_n = np.polyfit(np.arange(k), th_n[:k], 1)[0]
+    want = 6 * math.pi / (c * c * a_orb * (1 - e * e))
+    got = rate_pn - rate_n
+    assert abs(got - want) < 2e-3 * want, (got, want)
+
+
+# ------------------------------------------------------------ EIH cross-check --
+
+def _zero_momentum(v, m):
+    v = v.copy()
+    v[0] = -(m[1:, None] * v[1:]).sum(0) / m[0]
+    return v
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_limited_equals_eih_up_to_dropped_orders(orc, seed):
+    """Section 2: the limited equations keep every EIH term of the hole-star
+    interaction.  With the hole's velocity set by zero momentum, the
+    difference limited - EIH is a homogeneous polynomial of degree 2 in the
+    star masses for a star and of degree 3 for the hole, so halving every
+    star mass divides it by exactly 4 and 8.  A wrong or missing retained term
+    would leave a degree-0 or degree-1 part and break the ratios."""
+    x, v, m = _random_state(7, seed, m_bh=1.0, m_star=0.05, vscale=0.4)
+    c = 6.0
+
+    def diff(scale):
+        mm = m.copy()
+        mm[1:] *= scale
+        vv = _zero_momentum(v, mm)
+        return orc.accel(x, vv, mm, c=c) - orc.eih_accel(x, vv, mm, c=c)
+
+    d1, d2, d3 = diff(1.0), diff(0.5), diff(0.25)
+    np.testing.assert_allclose(d1[1:] / d2[1:], 4.0, rtol=1e-6)
+    np.testing.assert_allclose(d2[1:] / d3[1:], 4.0, rtol=1e-6)
+    np.testing.assert_allclose(d1[0] / d2[0], 8.0, rtol=1e-6)
+    np.testing.assert_allclose(d2[0] / d3[0], 8.0, rtol=1e-6)
+
+
+def test_eih_two_body_matches_kidder(orc):
+    """Two-body EIH relative acceleration in the centre-of-mass frame equals
+    the harmonic-gauge 1PN relative acceleration a = -(Gm/r^2)[(1+A) n + B v],
+    A = [(1+3nu) v^2 - 3/2 nu rdot^2 - 2(2+nu) Gm/r]/c^2,
+    B = -2(2-nu) rdot/c^2 (Kidder, PRD 52, 821 (1995), Eq. 2.2)."""
+    G, c = 1.0, 5.0
+    m1, m2 = 0.7, 0.45
+    mt = m1 + m2
+    nu = m1 * m2 / mt ** 2
+    xr = np.array([1.1, -0.4, 0.3])
+    vr = np.array([0.2, 0.6, -0.1])
+    x = np.array([m2 / mt * xr, -m1 / mt * xr])
+    v = np.array([m2 / mt * vr, -m1 / mt * vr])
+    m = np.array([m1, m2])
+    a = orc.eih_accel(x, v, m, G=G, c=c)
+    r = np.linalg.norm(xr)
+    nvec = xr / r
+    rdot = nvec @ vr
+    v2 = vr @ vr
+    A = ((1 + 3 * nu) * v2 - 1.5 * nu * rdot ** 2 - 2 * (2 + nu) * G * mt / r) / c ** 2
+    B = -2 * (2 - nu) * rdot / c ** 2
+    want = -(G * mt / r ** 2) * ((1 + A) * nvec + B * vr)
+    np.testing.assert_allclose(a[0] - a[1], want, rtol=1e-13, atol=1e-15)
+
+
+def test_eih_two_body_energy_matches_textbook(orc):
+    """E_1PN of a two-body system in the centre-of-mass frame:
+    3/8 (1-3nu) mu v^4 + 1/2 (G m mu/r)[(3+nu) v^2 + nu rdot^2 + G m/r]
+    (Blanchet, Living Rev. Rel. 17, 2 (2014), two-body 1PN energy)."""
+    G, c = 1.0, 3.0
+    m1, m2 = 0.8, 0.3
+    mt = m1 + m2
+    mu = m1 * m2 / mt
+    nu = mu / mt
+    xr = np.array([0.9, 0.2, -0.5])
+    vr = np.array([-0.3, 0.7, 0.25])
+    x = np.array([m2 / mt * xr, -m1 / mt * xr])
+    v = np.array([m2 / mt * vr, -m1 / mt * vr])
+    e = orc.eih_energy(x, v, np.array([m1, m2]), G=G, c=c)
+    r = np.linalg.norm(xr)
+    rdot = xr @ vr / r
+    v2 = vr @ vr
+    e1 = (0.375 * (1 - 3 * nu) * mu * v2 ** 2
+          + 0.5 * G * mt * mu / r * ((3 + nu) * v2 + nu * rdot ** 2 + G * mt / r)) / c ** 2
+    e0 = 0.5 * mu * v2 - G * mt * mu / r
+    assert abs(e["E_N"] - e0) < 1e-14
+    assert abs(e["E_PN"] - e1) < 1e-14 * abs(e1) + 1e-16
+
+
+def _balance(E, A, x, v, m, c, key, h=1e-4):
+    """d(key)/dt along the flow (xdot = v, vdot = A), by a 4th-order central
+    difference of the conserved quantity along (v, a)."""
+    a = A(x, v, m, c)
+    f = lambda s: E(x + s * v, v + s * a, m, c)[key]
+    return (8 * (f(h) - f(-h)) - (f(2 * h) - f(-2 * h))) / (12 * h)
+
+
+def _triple():
+    m = np.array([1.0, 0.3, 0.2])
+    x = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.05], [0.0, -2.0, 0.3]])
+    v = np.array([[0.0, 0.0, 0.0], [0.1, 1.08, 0.0], [0.87, 0.2, 0.02]])
+    v -= (m[:, None] * v).sum(0) / m.sum()
+    return x, v, m
+
+
+def test_eih_energy_and_momentum_balance(orc):
+    """The EIH equations conserve the EIH energy and momentum through 1PN
+    order: along the flow dE/dt and dP/dt vanish at O(1/c^2) and start at
+    O(1/c^4), so doubling c divides them by 16 (an error in any 1PN term of
+    the equations or of E, P would leave an O(1/c^2) part, ratio 4).  Three
+    bodies of comparable mass exercise the three-body terms."""
+    x, v, m = _triple()
+    E = lambda xx, vv, mm, c: orc.eih_energy(xx, vv, mm, c=c)
+    A = lambda xx, vv, mm, c: orc.eih_accel(xx, vv, mm, c=c)
+    for key in ("E", "P"):
+        r = [_balance(E, A, x, v, m, c, key) for c in (10.0, 20.0, 40.0)]
+        np.testing.assert_allclose(np.asarray(r[0]) / r[1], 16.0, rtol=5e-3)
+        np.testing.assert_allclose(np.asarray(r[1]) / r[2], 16.0, rtol=5e-3)
+
+
+@pytest.mark.parametrize("m_star,rtol", [(1e-9, 1e-5), (1e-3, 2e-2)])
+def test_limited_energy_and_momentum_balance(orc, m_star, rtol):
+    """Eq. 7 and Eq. 8 are conserved by Eq. 1-6 through 1PN order, up to the
+    dropped terms of degree >= 3 in the star masses: dE/dt and dP/dt scale
+    as 1/c^4 (ratio 16 when c doubles) once the star masses are small."""
+    rng = np.random.default_rng(0)
+    n = 6
+    x = rng.normal(size=(n, 3))
+    x[0] = 0.0
+    v = rng.normal(size=(n, 3)) * 0.4
+    m = np.full(n, m_star)
+    m[0] = 1.0
+    v = _zero_momentum(v, m)
+    E = lambda xx, vv, mm, c: orc.energy(xx, vv, mm, c=c)
+    A = lambda xx, vv, mm, c: orc.accel(xx, vv, mm, c=c)
+    for key in ("E", "P"):
+        r = [_balance(E, A, x, v, m, c, key) for c in (10.0, 20.0)]
+        np.testing.assert_allclose(np.asarray(r[0]) / r[1], 16.0, rtol=rtol)
+
+
+def test_limited_energy_and_momentum_equal_eih_up_to_dropped_orders(orc):
+    """Eq. 7 and Eq. 8 keep every EIH energy and momentum term that is of
+    degree <= 2 in the star masses; the dropped part is of degree >= 3, so
+    the differences shrink by 8 (or 16) when the star masses halve."""
+    x, v, m = _random_state(6, 5, m_bh=1.0, m_star=0.02, vscale=0.4)
+    c = 5.0
+
+    def diff(scale):
+        mm = m.copy()
+        mm[1:] *= scale
+        vv = _zero_momentum(v, mm)
+        lim = orc.energy(x, vv, mm, c=c)
+        eih = orc.eih_energy(x, vv, mm, c=c)
+        return lim["E"] - eih["E"], lim["P"] - eih["P"]
+
+    (e1, p1), (e2, p2), (e3, p3) = diff(1.0), diff(0.5), diff(0.25)
+    for r in (e1 / e2, e2 / e3):
+        assert 7.9 < r < 16.1
+    for r in (p1 / p2, p2 / p3):
+        assert np.all((7.9 < r) & (r < 16.1)), r
+
+
+# ------------------------------------------------------- conservation laws --
+
+def _orbiting_stars(n_stars, m_star, M=1.0, seed=0):
+    """Stars on near-circular orbits at well-separated radii."""
+    rng = np.random.default_rng(seed)
+    x = np.zeros((n_stars + 1, 3))
+    v = np.zeros((n_stars + 1, 3))
+    for k in range(n_stars):
+        r = 1.0 + 0.7 * k
+        h = rng.normal(size=3)
+        h /= np.linalg.norm(h)
+        p = np.cross(h, rng.normal(size=3))
+        p /= np.linalg.norm(p)
+        q = np.cross(h, p)
+        x[k + 1] = r * p
+        v[k + 1] = math.sqrt(M / r) * 1.1 * q
+    m = np.full(n_stars + 1, m_star)
+    m[0] = M
+    v[0] = -(m[1:, None] * v[1:]).sum(0) / M
+    return x, v, m
+
+
+def _self_convergence(orc, vel_mode, c):
+    x, v, m = _orbiting_stars(2, 1e-3, seed=4)
+    a = orc.accel(x, v, m, c=c)
+    T = 2.0
+    xs = []
+    for nst in (200, 400, 800):
+        xx, vv, aa = orc.step(x, v, m, a, T / nst, nst, c=c, vel_mode=vel_mode)
+        xs.append(xx)
+    return np.linalg.norm(xs[0] - xs[1]) / np.linalg.norm(xs[1] - xs[2])
+
+
+def test_integrator_order(orc):
+    """KDK with the force taken at the predicted end-of-step velocity is
+    second order (self-convergence ratio 4); taking it at the half-step
+    velocity is only first order in the velocity-dependent 1PN part."""
+    r_end = _self_convergence(orc, 0, 4.0)
+    r_half = _self_convergence(orc, 1, 4.0)
+    assert 3.6 < r_end < 4.4, r_end
+    assert r_half < 3.0, r_half
+    assert 3.6 < _self_convergence(orc, 1, np.inf) < 4.4
+
+
+def test_softening_acts_only_between_stars(orc):
+    """Eq. 10 softens star-star separations only.  Hole, a star at 0.01 and a
+    star at 10 on one line: the only softened separation is ~10 long, so a
+    softening of 1e-3 may move the far star's acceleration by ~eps^2/(2 r r')
+    of its 1PN cross terms and the others by roundoff only.  Softening a
+    hole-star separation instead would change them by ~eps^2/0.01^2.  Two
+    stars 0.01 apart do feel the softening."""
+    x = np.array([[0.0, 0.0, 0.0], [0.01, 0.0, 0.0], [10.0, 0.0, 0.0]])
+    rng = np.random.default_rng(1)
+    v = rng.normal(size=(3, 3)) * 0.3
+    m = np.array([1.0, 1e-2, 1e-2])
+    v = _zero_momentum(v, m)
+    c, eps = 3.0, 1e-3
+    a0 = orc.accel(x, v, m, c=c, eps=0.0)
+    a1 = orc.accel(x, v, m, c=c, eps=eps)
+    r = _rel(a1, a0)
+    assert r[0] < 1e-12 and r[1] < 1e-12 and r[2] < 2e-5, r
+    e0 = orc.energy(x, v, m, c=c, eps=0.0)
+    e1 = orc.energy(x, v, m, c=c, eps=eps)
+    assert abs(e1["E"] - e0["E"]) < 1e-10 * abs(e0["E"])
+    assert np.linalg.norm(e1["P"] - e0["P"]) < 1e-10 * np.linalg.norm(m[:, None] * v)
+    x2 = np.array([[0.0, 0.0, 0.0], [3.0, 0.0, 0.0], [3.0, 0.01, 0.0]])
+    b0 = orc.accel(x2, v, m, c=c, eps=0.0)
+    b1 = orc.accel(x2, v, m, c=c, eps=0.01)
+    assert np.min(_rel(b1[1:], b0[1:])) > 0.1
+
+
+# ------------------------------------------------------------ invariances --
+
+def test_rotation_and_translation_invariance(orc):
+    x, v, m = make_cluster(128, 0.1, 21)
+    c, eps = 15.0, 1e-3
+    a = orc.accel(x, v, m, c=c, eps=eps)
+    th = 0.7
+    R = np.array([[math.cos(th), -math.sin(th), 0.0], [math.sin(th), math.cos(th), 0.0],
+                  [0.0, 0.0, 1.0]])
+    R = R @ np.array([[1.0, 0.0, 0.0], [0.0, math.cos(0.3), -math.sin(0.3)],
+                      [0.0, math.sin(0.3), math.cos(0.3)]])
+    ar = orc.accel(x @ R.T, v @ R.T, m, c=c, eps=eps)
+    assert np.max(_rel(ar, a @ R.T)) < 1e-12
+    at = orc.accel(x + np.array([3.0, -2.0, 5.0]), v, m, c=c, eps=eps)
+    assert np.max(_rel(at, a)) < 1e-11
+
+
+def test_thread_count_does_not_change_results(orc):
+    x, v, m = make_cluster(150, 0.1, 22)
+    orc.set_threads(1)
+    a1 = orc.accel(x, v, m, c=10.0, eps=1e-3)
+    e1 = orc.energy(x, v, m, c=10.0, eps=1e-3)["E"]
+    orc.set_threads(0)
+    a2 = orc.accel(x, v, m, c=10.0, eps=1e-3)
+    e2 = orc.energy(x, v, m, c=10.0, eps=1e-3)["E"]
+    assert np.array_equal(a1, a2) and e1 == e2
