@@ -1,0 +1,178 @@
+/*
+ * pn.h -- C ABI of libpn: the limited first-order post-Newtonian (1PN)
+ * N-body acceleration and integrator of T. Tatekawa, arXiv:1801.07986,
+ * on NVIDIA B300 (sm_103a).
+ *
+ * The system is one heavy body (a black hole, the paper's body "#1") plus
+ * n-1 low-mass stars.  The library evaluates
+ *   - the hole's acceleration, Section 2, Eq. 1 with Eq. 2 and Eq. 3,
+ *   - each star's acceleration, Section 2, Eq. 4 with Eq. 5 and Eq. 6,
+ *   - the 1PN energy and momentum, Section 2, Eq. 7 and Eq. 8,
+ * with Plummer softening between stars only (Section 4, Eq. 10), and
+ * advances the state with a kick-drift-kick leapfrog whose force after the
+ * drift is taken at a predicted velocity.
+ *
+ * Conventions shared by every entry point
+ *   - Body 0 is the hole (mass M = m[0]); bodies 1..n-1 are stars.
+ *   - x, v, a are n x 3 row-major arrays of double (x, y, z per body);
+ *     m is an array of n doubles.
+ *   - Pointers passed to pn_accel, pn_step and pn_energy are DEVICE pointers
+ *     on the context's device (e.g. torch tensor data_ptr()); pn_step_host
+ *     takes HOST pointers.  The caller owns every array it passes; the
+ *     library owns its scratch memory, allocated by pn_init and freed by
+ *     pn_destroy.
+ *   - Work is enqueued on the context's CUDA stream and the calls return
+ *     before it finishes, except pn_energy, pn_step_host and pn_sync, which
+ *     wait for the stream.
+ *   - Every call returns a pn_status and never aborts the process.  On an
+ *     error, pn_last_error() gives a message for the calling thread.
+ *     Argument errors are caught on the host before anything is launched.
+ *     Non-finite accelerations detected on the device are reported by the
+ *     next waiting call (pn_sync, pn_energy, pn_step_host) as PN_ENONFINITE,
+ *     with the first step index that produced one in the message.
+ *   - A context is not thread-safe: one thread at a time per context.
+ */
+#ifndef PN_H
+#define PN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pn_ctx pn_ctx;                  /* opaque, library-owned */
+
+typedef enum {
+    PN_OK = 0,
+    PN_EINVAL = 1,        /* bad argument (caught on the host)              */
+    PN_ENOMEM = 2,        /* device or host allocation failed               */
+    PN_ECUDA = 3,         /* a CUDA runtime call failed                     */
+    PN_ENONFINITE = 4,    /* a non-finite acceleration was produced         */
+    PN_ETIMEOUT = 5,      /* a bounded device-side wait gave up             */
+    PN_EUNSUPPORTED = 6   /* the device is not an sm_103 part               */
+} pn_status;
+
+enum { PN_FP64 = 0, PN_MIXED = 1 };            /* pn_params.precision */
+enum { PN_VPRED_END = 0, PN_VHALF = 1 };       /* pn_params.vel_mode  */
+
+/*
+ * Physical constants and evaluation mode.
+ *   G          gravitational constant (> 0)
+ *   c          speed of light (> 0); INFINITY gives the Newtonian equations
+ *              (every 1PN term multiplied by exactly 0)
+ *   eps        Plummer softening (>= 0) of star-star separations only
+ *              (Section 4, Eq. 10); hole-star separations are never softened
+ *   precision  PN_FP64: every operation in double precision.
+ *              PN_MIXED: pair arithmetic in single precision with the pair
+ *              separation formed from a hi/lo split of the hole-relative
+ *              positions, per-tile single-precision partial sums carried in
+ *              double-single accumulators, and everything O(n) (hole terms,
+ *              global sums, assembly, integrator, energy) in double.
+ *   vel_mode   velocity at which the force after a drift is evaluated:
+ *              PN_VPRED_END  v_half + (dt/2) a_old (second order),
+ *              PN_VHALF      v_half.
+ */
+typedef struct {
+    double G;
+    double c;
+    double eps;
+    int precision;
+    int vel_mode;
+} pn_params;
+
+/*
+ * Create a context for n bodies (n >= 2) on CUDA device `device`, enqueuing
+ * on `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
+ * Allocates all scratch memory for n.  Errors: PN_EINVAL (ctx NULL, n < 2,
+ * bad params), PN_EUNSUPPORTED (device is not compute capability 10.3),
+ * PN_ENOMEM, PN_ECUDA.
+ */
+pn_status pn_init(pn_ctx **ctx, int64_t n, const pn_params *params, int device,
+                  void *cuda_stream);
+
+/* Replace the parameters (G, c, eps, precision, vel_mode) without
+ * reallocating.  Errors: PN_EINVAL. */
+pn_status pn_set_params(pn_ctx *ctx, const pn_params *params);
+
+/* Enqueue subsequent work on another stream of the same device. */
+pn_status pn_set_stream(pn_ctx *ctx, void *cuda_stream);
+
+/*
+ * a = A(x, v): accelerations of all n bodies (Section 2, Eq. 1-6) at
+ * positions x and velocities v, both used as given.  x, v, m, a: device
+ * pointers (n x 3, n x 3, n, n x 3 doubles); a must not alias x, v or m.
+ * Errors: PN_EINVAL (NULL pointer).
+ */
+pn_status pn_accel(pn_ctx *ctx, const double *x, const double *v, const double *m,
+                   double *a);
+
+/*
+ * Advance the state in place by nsteps kick-drift-kick steps of size dt:
+ *   v_h = v + dt/2 a;  x = x + dt v_h;
+ *   v_p = v_h + dt/2 a (PN_VPRED_END) or v_h (PN_VHALF);
+ *   a = A(x, v_p);  v = v_h + dt/2 a.
+ * `a` is carried state: on entry it must hold the acceleration of the entry
+ * state (call pn_accel once before the first pn_step).  Device pointers.
+ * Errors: PN_EINVAL (NULL pointer, dt not finite or <= 0, nsteps < 0).
+ */
+pn_status pn_step(pn_ctx *ctx, double *x, double *v, const double *m, double *a,
+                  double dt, int64_t nsteps);
+
+/*
+ * pn_step on HOST arrays: copies x, v, m, a to device buffers owned by the
+ * context, runs nsteps steps, copies x, v, a back, and waits.  The arrays
+ * may be pageable or pinned host memory.  Errors: as pn_step, plus
+ * PN_ENONFINITE.
+ */
+pn_status pn_step_host(pn_ctx *ctx, double *x, double *v, const double *m, double *a,
+                       double dt, int64_t nsteps);
+
+/*
+ * 1PN energy (Eq. 7) and momentum (Eq. 8) of the state (x, v), evaluated in
+ * double precision whatever pn_params.precision says.  Device pointers in,
+ * host array out[8]:
+ *   out[0]  Newtonian energy         out[1]    1/c^2 part of Eq. 7
+ *   out[2..4] Newtonian momentum     out[5..7] 1/c^2 part of Eq. 8
+ * (E = out[0] + out[1], P = out[2..4] + out[5..7]).  Waits for the stream.
+ * Errors: PN_EINVAL, PN_ENONFINITE (pending from earlier steps).
+ */
+pn_status pn_energy(pn_ctx *ctx, const double *x, const double *v, const double *m,
+                    double out[8]);
+
+/* Wait for the context's stream; PN_ENONFINITE if a non-finite acceleration
+ * was produced since the last report (the flag is then cleared). */
+pn_status pn_sync(pn_ctx *ctx);
+
+/*
+ * Kernel timing for measurement.  While enabled, pn_accel/pn_step record a
+ * CUDA event pair on the context's stream around each pair-interaction
+ * kernel launch.  pn_get_timing waits for the stream and returns, for
+ * kernel k (0 = pass 1, 1 = pass 2), the summed milliseconds and launch
+ * count since timing was last enabled.
+ */
+pn_status pn_set_timing(pn_ctx *ctx, int enable);
+pn_status pn_get_timing(pn_ctx *ctx, double ms[2], int64_t launches[2]);
+
+/*
+ * Launch shape of the pair kernels for this context: out[0] threads per
+ * block, out[1] targets per thread, out[2] sources per shared-memory tile,
+ * out[3] blocks along targets, out[4] source splits, out[5] resident blocks
+ * per SM, out[6] SM count.
+ */
+pn_status pn_get_launch(pn_ctx *ctx, int64_t out[7]);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *pn_last_error(void);
+
+/* Free the context and its device memory (NULL is a no-op). */
+void pn_destroy(pn_ctx *ctx);
+
+/* Library version, 100 * major + minor. */
+int pn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PN_H */

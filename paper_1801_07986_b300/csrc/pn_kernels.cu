@@ -1,0 +1,979 @@
+// pn_kernels.cu -- CUDA kernels of libpn for sm_103a.
+//
+// One evaluation of the accelerations A(x, v) of the limited-1PN system of
+// Tatekawa (arXiv:1801.07986, Section 2, Eq. 1-6) runs as
+//
+//   prologue   O(n)   hole-relative star records + global sums (Q, W, ...)
+//   pass 1     O(n^2) per star i: N_i = sum_j m_j x_ij / r_ij^3,
+//                     U_i = sum_j m_j / r_ij, Y_i = sum_j m_j (r_i1^2 - r_j1^2)/r_ij^3
+//   pass 2     O(n^2) per star i: the velocity-dependent 1PN pair sums
+//   epilogue   O(n)   assembles each star's acceleration from passes 1 and 2
+//                     and the hole's three-body terms from pass 1
+//   hole       O(n)   deterministic reduction of the hole's terms
+//
+// The pair sums are regrouped algebraically (exactly, in real arithmetic)
+// so that each pair costs one reciprocal square root and a handful of
+// FMAs; the groupings are stated next to each kernel.  x_ij = x_i - x_j,
+// v_ij = v_i - v_j, d_j = x_j - x_hole, R_j = |d_j|, r_ij is the softened
+// star-star distance sqrt(|x_ij|^2 + eps^2) (Eq. 10).
+#include <math.h>
+#include <stdint.h>
+
+#include "pn_internal.h"
+
+namespace pn {
+
+// ------------------------------------------------------------- helpers --
+
+// Double-single running sum: hi + lo carries ~48 significant bits.  Each
+// tile's single-precision partial is added with Knuth's TwoSum.
+__device__ __forceinline__ void ds_add(float &hi, float &lo, float p)
+{
+    const float s = hi + p;
+    const float bp = s - hi;
+    const float e = (hi - (s - bp)) + (p - bp);
+    hi = s;
+    lo += e;
+}
+
+// 1/sqrt(s2) in double: single-precision seed refined by two Newton steps
+// y <- y (3/2 - s2/2 y^2) (quadratic convergence: ~2^-22 -> 2^-44 -> round-off).
+__device__ __forceinline__ double rsqrt_f64(double s2)
+{
+    double y = (double)rsqrtf((float)s2);
+    const double h = 0.5 * s2;
+    y = y * fma(-h, y * y, 1.5);
+    y = y * fma(-h, y * y, 1.5);
+    return y;
+}
+
+// Deterministic block sum of K doubles per thread (fixed tree, blockDim =
+// kGlueThreads); thread 0 ends with the totals in sh[k][0].
+template <int K>
+__device__ __forceinline__ void block_sum(double (&val)[K], double (*sh)[kGlueThreads])
+{
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        sh[k][t] = val[k];
+    __syncthreads();
+    for (int s = kGlueThreads / 2; s > 0; s >>= 1) {
+        if (t < s) {
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                sh[k][t] += sh[k][t + s];
+        }
+        __syncthreads();
+    }
+}
+
+// Sum per-block partials blk[b*K + k] over b in a fixed order (one block).
+template <int K>
+__device__ __forceinline__ void sum_blocks(const double *__restrict__ blk, int64_t nblk,
+                                           double (*sh)[kGlueThreads])
+{
+    double v[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        v[k] = 0.0;
+    for (int64_t b = threadIdx.x; b < nblk; b += kGlueThreads) {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            v[k] += blk[b * K + k];
+    }
+    block_sum<K>(v, sh);
+}
+
+__device__ __forceinline__ void flag_nonfinite(const double a[3], int *flag,
+                                               unsigned long long *flag_step,
+                                               unsigned long long step)
+{
+    if (!(isfinite(a[0]) && isfinite(a[1]) && isfinite(a[2]))) {
+        atomicOr(flag, 1);
+        atomicMin(flag_step, step);
+    }
+}
+
+// --------------------------------------------------------- integrator --
+
+// Kick and drift of every body (hole included):
+//   v_h = v + h a;  x += dt v_h;  v_p = v_h + h a (mode 0) or v_h (mode 1).
+// v is overwritten with v_h; the final kick is applied by the epilogue.
+__global__ void k_kick_drift(int64_t n3, double *__restrict__ x, double *__restrict__ v,
+                             const double *__restrict__ a, double *__restrict__ vp, double h,
+                             double dt, int mode)
+{
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n3;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const double aq = a[q];
+        const double vh = fma(h, aq, v[q]);
+        v[q] = vh;
+        x[q] = fma(dt, vh, x[q]);
+        vp[q] = mode == 0 ? fma(h, aq, vh) : vh;
+    }
+}
+
+// ------------------------------------------------------------ prologue --
+
+// Per star slot t (star j = t + 1; slots >= ns are padding with zero mass):
+//   d_j = x_j - x_hole, R_j = |d_j|,
+//   c_j = G M (3/(2 R_j) + eps^2/(4 R_j^3)),   e_j = G M d_j/(2 R_j^3),
+//   w_j = m_j d_j / R_j^3,
+// and the global sums Q = sum m_j v_j, W = sum w_j, SA = sum 5 m_j/(4 R_j),
+// SB = sum m_j (R_j^2 + eps^2)/(4 R_j^3), Phi = sum m_j / R_j.
+// Records: mixed  A = (hi(d), m) B = (lo(d), c) C = (v, 0) D = (e, 0) E = (w, 0)
+//          double A = (d, m)     B = (v, c)     C = (e, 0) D = (w, 0)
+// Energy records (double): A = (d, m), B = (v, 0).
+template <int MODE>   // 0 mixed, 1 double, 2 energy
+__global__ void __launch_bounds__(kGlueThreads)
+k_prologue(int64_t ns, int64_t ns_pad, const double *__restrict__ x,
+           const double *__restrict__ vel, const double *__restrict__ m, double G,
+           double eps2, float4 *__restrict__ mrec, double4_32a *__restrict__ drec,
+           double *__restrict__ blk)
+{
+    __shared__ double sh[kGlobVals][kGlueThreads];
+    const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
+    double g[kGlobVals];
+#pragma unroll
+    for (int k = 0; k < kGlobVals; ++k)
+        g[k] = 0.0;
+    if (t < ns_pad) {
+        if (t < ns) {
+            const int64_t j = t + 1;
+            const double d0 = x[3 * j] - x[0], d1 = x[3 * j + 1] - x[1], d2 = x[3 * j + 2] - x[2];
+            const double R2 = d0 * d0 + d1 * d1 + d2 * d2;
+            const double R = sqrt(R2);
+            const double iR = 1.0 / R;
+            const double iR3 = iR * iR * iR;
+            const double mj = m[j];
+            const double M = m[0];
+            const double v0 = vel[3 * j], v1 = vel[3 * j + 1], v2 = vel[3 * j + 2];
+            const double cj = G * M * (1.5 * iR + 0.25 * eps2 * iR3);
+            const double ef = 0.5 * G * M * iR3;
+            const double wf = mj * iR3;
+            if (MODE == 0) {
+                const float h0 = (float)d0, h1 = (float)d1, h2 = (float)d2;
+                mrec[t] = make_float4(h0, h1, h2, (float)mj);
+                mrec[ns_pad + t] = make_float4((float)(d0 - (double)h0), (float)(d1 - (double)h1),
+                                               (float)(d2 - (double)h2), (float)cj);
+                mrec[2 * ns_pad + t] = make_float4((float)v0, (float)v1, (float)v2, 0.0f);
+                mrec[3 * ns_pad + t] =
+                    make_float4((float)(ef * d0), (float)(ef * d1), (float)(ef * d2), 0.0f);
+                mrec[4 * ns_pad + t] =
+                    make_float4((float)(wf * d0), (float)(wf * d1), (float)(wf * d2), 0.0f);
+            } else if (MODE == 1) {
+                drec[t] = make_double4_32a(d0, d1, d2, mj);
+                drec[ns_pad + t] = make_double4_32a(v0, v1, v2, cj);
+                drec[2 * ns_pad + t] = make_double4_32a(ef * d0, ef * d1, ef * d2, 0.0);
+                drec[3 * ns_pad + t] = make_double4_32a(wf * d0, wf * d1, wf * d2, 0.0);
+            } else {
+                drec[t] = make_double4_32a(d0, d1, d2, mj);
+                drec[ns_pad + t] = make_double4_32a(v0, v1, v2, 0.0);
+            }
+            g[0] = mj * v0;
+            g[1] = mj * v1;
+            g[2] = mj * v2;
+            g[3] = wf * d0;
+            g[4] = wf * d1;
+            g[5] = wf * d2;
+            g[6] = 1.25 * mj * iR;
+            g[7] = 0.25 * mj * (R2 + eps2) * iR3;
+            g[8] = mj * iR;
+        } else {
+            // padding: zero mass far away, distinct positions
+            const double px = 1.0e4 + (double)(t - ns);
+            if (MODE == 0) {
+                mrec[t] = make_float4((float)px, 0.0f, 0.0f, 0.0f);
+                for (int k = 1; k < 5; ++k)
+                    mrec[k * ns_pad + t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            } else {
+                drec[t] = make_double4_32a(px, 0.0, 0.0, 0.0);
+                const int nk = MODE == 1 ? 4 : 2;
+                for (int k = 1; k < nk; ++k)
+                    drec[k * ns_pad + t] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+            }
+        }
+    }
+    if (MODE == 2)
+        return;   // block-uniform
+    block_sum<kGlobVals>(g, sh);
+    if (threadIdx.x < kGlobVals)
+        blk[(int64_t)blockIdx.x * kGlobVals + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(kGlueThreads)
+k_global_sums(const double *__restrict__ blk, int64_t nblk, double *__restrict__ glob)
+{
+    __shared__ double sh[kGlobVals][kGlueThreads];
+    sum_blocks<kGlobVals>(blk, nblk, sh);
+    if (threadIdx.x < kGlobVals)
+        glob[threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// ------------------------------------------------- pair kernels: mixed --
+
+struct MixTarget {
+    float hx, hy, hz, lx, ly, lz;   // hi/lo split of d_i
+    float vx, vy, vz;               // velocity of target i (pass 2)
+};
+
+// Pass 1, one shared-memory tile of sources.  Per pair:
+//   N += m_j x_ij / r^3,  U += m_j / r,
+//   Y += m_j (R_i^2 - R_j^2) / r^3  with  R_i^2 - R_j^2 = x_ij . (d_i + d_j).
+// x_ij = (hi_i - hi_j) + (lo_i - lo_j) keeps ~48 bits of the difference.
+template <bool MASK>
+__device__ __forceinline__ void pass1_tile(const float4 *__restrict__ sA,
+                                           const float4 *__restrict__ sB, int64_t j0,
+                                           const MixTarget (&tg)[kMixTargets],
+                                           const int64_t (&ti)[kMixTargets], float eps2,
+                                           float (&acc)[kMixTargets][kP1Vals])
+{
+#pragma unroll 2
+    for (int q = 0; q < kMixTile; ++q) {
+        const float4 A = sA[q];
+        const float4 B = sB[q];
+#pragma unroll
+        for (int p = 0; p < kMixTargets; ++p) {
+            const float dx = (tg[p].hx - A.x) + (tg[p].lx - B.x);
+            const float dy = (tg[p].hy - A.y) + (tg[p].ly - B.y);
+            const float dz = (tg[p].hz - A.z) + (tg[p].lz - B.z);
+            float s2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+            float mj = A.w;
+            if (MASK) {
+                const bool self = (j0 + q == ti[p]);
+                s2 = self ? 1.0f : s2;
+                mj = self ? 0.0f : mj;
+            }
+            const float is = rsqrtf(s2);
+            const float mis = mj * is;
+            const float mis3 = mis * (is * is);
+            acc[p][0] = fmaf(mis3, dx, acc[p][0]);
+            acc[p][1] = fmaf(mis3, dy, acc[p][1]);
+            acc[p][2] = fmaf(mis3, dz, acc[p][2]);
+            acc[p][3] += mis;
+            const float sx = tg[p].hx + A.x, sy = tg[p].hy + A.y, sz = tg[p].hz + A.z;
+            const float r2d = fmaf(dx, sx, fmaf(dy, sy, dz * sz));
+            acc[p][4] = fmaf(mis3, r2d, acc[p][4]);
+        }
+    }
+}
+
+// Pass 2, one tile.  Per pair (velocities are those at which A is taken):
+//   V += m_j x_ij / r^3 [c_j - e_j . d_i - 2 |v_ij|^2 + 3/2 (v_j . x_ij)^2 / r^2]
+//   H += m_j / r^3 [x_ij . (4 v_i - 3 v_j)] v_ij
+//   E += w_j / r
+// V carries Eq. 6 line 3 (without its 4/R_i part) and line 6 (without its
+// v_i^2 part): with r_ij^2 - R_i^2 = R_j^2 + eps^2 - 2 d_i . d_j, line 3's
+// bracket is 4/R_i + c_j/(G M) - e_j . d_i/(G M).  H is Eq. 6 line 7, E the
+// 1/r_ij part of line 4.
+template <bool MASK>
+__device__ __forceinline__ void pass2_tile(const float4 *__restrict__ sA,
+                                           const float4 *__restrict__ sB,
+                                           const float4 *__restrict__ sC,
+                                           const float4 *__restrict__ sD,
+                                           const float4 *__restrict__ sE, int64_t j0,
+                                           const MixTarget (&tg)[kMixTargets],
+                                           const int64_t (&ti)[kMixTargets], float eps2,
+                                           float (&acc)[kMixTargets][kP2Vals])
+{
+#pragma unroll 1
+    for (int q = 0; q < kMixTile; ++q) {
+        const float4 A = sA[q];
+        const float4 B = sB[q];
+        const float4 C = sC[q];
+        const float4 D = sD[q];
+        const float4 E = sE[q];
+#pragma unroll
+        for (int p = 0; p < kMixTargets; ++p) {
+            const float dx = (tg[p].hx - A.x) + (tg[p].lx - B.x);
+            const float dy = (tg[p].hy - A.y) + (tg[p].ly - B.y);
+            const float dz = (tg[p].hz - A.z) + (tg[p].lz - B.z);
+            float s2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+            float mj = A.w;
+            float wx = E.x, wy = E.y, wz = E.z;
+            if (MASK) {
+                const bool self = (j0 + q == ti[p]);
+                s2 = self ? 1.0f : s2;
+                mj = self ? 0.0f : mj;
+                wx = self ? 0.0f : wx;
+                wy = self ? 0.0f : wy;
+                wz = self ? 0.0f : wz;
+            }
+            const float is = rsqrtf(s2);
+            const float is2 = is * is;
+            const float mis3 = (mj * is) * is2;
+            const float ux = tg[p].vx - C.x, uy = tg[p].vy - C.y, uz = tg[p].vz - C.z;
+            const float u2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+            const float xvj = fmaf(dx, C.x, fmaf(dy, C.y, dz * C.z));
+            const float xvi = fmaf(dx, tg[p].vx, fmaf(dy, tg[p].vy, dz * tg[p].vz));
+            const float ed = fmaf(D.x, tg[p].hx, fmaf(D.y, tg[p].hy, D.z * tg[p].hz));
+            const float tq = (xvj * xvj) * is2;
+            const float kap = fmaf(1.5f, tq, fmaf(-2.0f, u2, B.w - ed));
+            const float f = mis3 * kap;
+            acc[p][0] = fmaf(f, dx, acc[p][0]);
+            acc[p][1] = fmaf(f, dy, acc[p][1]);
+            acc[p][2] = fmaf(f, dz, acc[p][2]);
+            const float sg = fmaf(4.0f, xvi, -3.0f * xvj);
+            const float gg = mis3 * sg;
+            acc[p][3] = fmaf(gg, ux, acc[p][3]);
+            acc[p][4] = fmaf(gg, uy, acc[p][4]);
+            acc[p][5] = fmaf(gg, uz, acc[p][5]);
+            acc[p][6] = fmaf(wx, is, acc[p][6]);
+            acc[p][7] = fmaf(wy, is, acc[p][7]);
+            acc[p][8] = fmaf(wz, is, acc[p][8]);
+        }
+    }
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(kMixThreads)
+k_pass_mixed(const float4 *__restrict__ rec, int64_t ns_pad, int ntiles, int tps, float eps2,
+             double *__restrict__ part)
+{
+    constexpr int NV = PASS == 1 ? kP1Vals : kP2Vals;
+    constexpr int NA = PASS == 1 ? 2 : 5;
+    constexpr int TI = kMixThreads * kMixTargets;
+    __shared__ float4 sh[NA][kMixTile];
+    const int64_t t0 = (int64_t)blockIdx.x * TI;
+
+    MixTarget tg[kMixTargets];
+    int64_t ti[kMixTargets];
+#pragma unroll
+    for (int p = 0; p < kMixTargets; ++p) {
+        ti[p] = t0 + p * kMixThreads + threadIdx.x;
+        const float4 A = rec[ti[p]];
+        const float4 B = rec[ns_pad + ti[p]];
+        tg[p].hx = A.x; tg[p].hy = A.y; tg[p].hz = A.z;
+        tg[p].lx = B.x; tg[p].ly = B.y; tg[p].lz = B.z;
+        if constexpr (PASS == 2) {
+            const float4 C = rec[2 * ns_pad + ti[p]];
+            tg[p].vx = C.x; tg[p].vy = C.y; tg[p].vz = C.z;
+        } else {
+            tg[p].vx = tg[p].vy = tg[p].vz = 0.0f;
+        }
+    }
+    float hi[kMixTargets][NV], lo[kMixTargets][NV];
+#pragma unroll
+    for (int p = 0; p < kMixTargets; ++p)
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+            hi[p][k] = lo[p][k] = 0.0f;
+
+    const int tb = blockIdx.y * tps;
+    const int te = min(ntiles, tb + tps);
+    for (int tile = tb; tile < te; ++tile) {
+        const int64_t j0 = (int64_t)tile * kMixTile;
+        __syncthreads();
+        for (int q = threadIdx.x; q < kMixTile; q += kMixThreads) {
+#pragma unroll
+            for (int k = 0; k < NA; ++k)
+                sh[k][q] = rec[k * ns_pad + j0 + q];
+        }
+        __syncthreads();
+        float acc[kMixTargets][NV];
+#pragma unroll
+        for (int p = 0; p < kMixTargets; ++p)
+#pragma unroll
+            for (int k = 0; k < NV; ++k)
+                acc[p][k] = 0.0f;
+        const bool diag = (j0 < t0 + TI) && (t0 < j0 + kMixTile);
+        if constexpr (PASS == 1) {
+            if (diag)
+                pass1_tile<true>(sh[0], sh[1], j0, tg, ti, eps2, acc);
+            else
+                pass1_tile<false>(sh[0], sh[1], j0, tg, ti, eps2, acc);
+        } else {
+            if (diag)
+                pass2_tile<true>(sh[0], sh[1], sh[2], sh[3], sh[4], j0, tg, ti, eps2, acc);
+            else
+                pass2_tile<false>(sh[0], sh[1], sh[2], sh[3], sh[4], j0, tg, ti, eps2, acc);
+        }
+#pragma unroll
+        for (int p = 0; p < kMixTargets; ++p)
+#pragma unroll
+            for (int k = 0; k < NV; ++k)
+                ds_add(hi[p][k], lo[p][k], acc[p][k]);
+    }
+#pragma unroll
+    for (int p = 0; p < kMixTargets; ++p)
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+            part[((int64_t)blockIdx.y * NV + k) * ns_pad + ti[p]] =
+                (double)hi[p][k] + (double)lo[p][k];
+}
+
+// ------------------------------------------------ pair kernels: double --
+
+// The same pair sums as pass 1 / pass 2 above, in double precision
+// (records A = (d, m), B = (v, c), C = (e, 0), D = (w, 0)).
+template <int PASS, bool MASK>
+__device__ __forceinline__ void f64_tile(const double4_32a (*__restrict__ sh)[kF64Tile], int64_t j0,
+                                         const double (&di)[3], const double (&vi)[3],
+                                         int64_t ti, double eps2, double (&acc)[kP2Vals])
+{
+#pragma unroll 1
+    for (int q = 0; q < kF64Tile; ++q) {
+        const double4_32a A = sh[0][q];
+        const double dx = di[0] - A.x, dy = di[1] - A.y, dz = di[2] - A.z;
+        double s2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
+        double mj = A.w;
+        const bool self = MASK && (j0 + q == ti);
+        if (MASK) {
+            s2 = self ? 1.0 : s2;
+            mj = self ? 0.0 : mj;
+        }
+        const double is = rsqrt_f64(s2);
+        const double is2 = is * is;
+        const double mis = mj * is;
+        const double mis3 = mis * is2;
+        if constexpr (PASS == 1) {
+            acc[0] = fma(mis3, dx, acc[0]);
+            acc[1] = fma(mis3, dy, acc[1]);
+            acc[2] = fma(mis3, dz, acc[2]);
+            acc[3] += mis;
+            const double r2d = fma(dx, di[0] + A.x, fma(dy, di[1] + A.y, dz * (di[2] + A.z)));
+            acc[4] = fma(mis3, r2d, acc[4]);
+        } else {
+            const double4_32a B = sh[1][q];
+            const double4_32a C = sh[2][q];
+            const double4_32a D = sh[3][q];
+            const double wx = self ? 0.0 : D.x, wy = self ? 0.0 : D.y, wz = self ? 0.0 : D.z;
+            const double ux = vi[0] - B.x, uy = vi[1] - B.y, uz = vi[2] - B.z;
+            const double u2 = fma(ux, ux, fma(uy, uy, uz * uz));
+            const double xvj = fma(dx, B.x, fma(dy, B.y, dz * B.z));
+            const double xvi = fma(dx, vi[0], fma(dy, vi[1], dz * vi[2]));
+            const double ed = fma(C.x, di[0], fma(C.y, di[1], C.z * di[2]));
+            const double tq = (xvj * xvj) * is2;
+            const double kap = fma(1.5, tq, fma(-2.0, u2, B.w - ed));
+            const double f = mis3 * kap;
+            acc[0] = fma(f, dx, acc[0]);
+            acc[1] = fma(f, dy, acc[1]);
+            acc[2] = fma(f, dz, acc[2]);
+            const double gg = mis3 * fma(4.0, xvi, -3.0 * xvj);
+            acc[3] = fma(gg, ux, acc[3]);
+            acc[4] = fma(gg, uy, acc[4]);
+            acc[5] = fma(gg, uz, acc[5]);
+            acc[6] = fma(wx, is, acc[6]);
+            acc[7] = fma(wy, is, acc[7]);
+            acc[8] = fma(wz, is, acc[8]);
+        }
+    }
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(kF64Threads)
+k_pass_f64(const double4_32a *__restrict__ rec, int64_t ns_pad, int ntiles, int tps, double eps2,
+           double *__restrict__ part)
+{
+    constexpr int NV = PASS == 1 ? kP1Vals : kP2Vals;
+    constexpr int NA = PASS == 1 ? 1 : 4;
+    __shared__ double4_32a sh[4][kF64Tile];
+    const int64_t t0 = (int64_t)blockIdx.x * kF64Threads;
+    const int64_t ti = t0 + threadIdx.x;
+    const double4_32a A = rec[ti];
+    const double di[3] = {A.x, A.y, A.z};
+    double vi[3] = {0.0, 0.0, 0.0};
+    if (PASS == 2) {
+        const double4_32a B = rec[ns_pad + ti];
+        vi[0] = B.x; vi[1] = B.y; vi[2] = B.z;
+    }
+    double acc[kP2Vals];
+#pragma unroll
+    for (int k = 0; k < kP2Vals; ++k)
+        acc[k] = 0.0;
+    const int tb = blockIdx.y * tps;
+    const int te = min(ntiles, tb + tps);
+    for (int tile = tb; tile < te; ++tile) {
+        const int64_t j0 = (int64_t)tile * kF64Tile;
+        __syncthreads();
+        for (int q = threadIdx.x; q < kF64Tile; q += kF64Threads) {
+#pragma unroll
+            for (int k = 0; k < NA; ++k)
+                sh[k][q] = rec[k * ns_pad + j0 + q];
+        }
+        __syncthreads();
+        const bool diag = (j0 < t0 + kF64Threads) && (t0 < j0 + kF64Tile);
+        if (diag)
+            f64_tile<PASS, true>(sh, j0, di, vi, ti, eps2, acc);
+        else
+            f64_tile<PASS, false>(sh, j0, di, vi, ti, eps2, acc);
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+        part[((int64_t)blockIdx.y * NV + k) * ns_pad + ti] = acc[k];
+}
+
+// Energy pair sums, double precision, records A = (d, m), B = (v, 0):
+//   pot += m_j/r, Smv += m_j/r v_j, Snn += m_j/r (n.v_i)(n.v_j),
+//   Spx += m_j/r (n.v_i)/r x_ij,   n = x_ij / r.
+template <bool MASK>
+__device__ __forceinline__ void energy_tile(const double4_32a (*__restrict__ sh)[kF64Tile],
+                                            int64_t j0, const double (&di)[3],
+                                            const double (&vi)[3], int64_t ti, double eps2,
+                                            double (&acc)[kEVals])
+{
+#pragma unroll 1
+    for (int q = 0; q < kF64Tile; ++q) {
+        const double4_32a A = sh[0][q];
+        const double4_32a B = sh[1][q];
+        const double dx = di[0] - A.x, dy = di[1] - A.y, dz = di[2] - A.z;
+        double s2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
+        double mj = A.w;
+        if (MASK) {
+            const bool self = (j0 + q == ti);
+            s2 = self ? 1.0 : s2;
+            mj = self ? 0.0 : mj;
+        }
+        const double is = rsqrt_f64(s2);
+        const double ms = mj * is;
+        const double nvi = fma(dx, vi[0], fma(dy, vi[1], dz * vi[2])) * is;
+        const double nvj = fma(dx, B.x, fma(dy, B.y, dz * B.z)) * is;
+        acc[0] += ms;
+        acc[1] = fma(ms, B.x, acc[1]);
+        acc[2] = fma(ms, B.y, acc[2]);
+        acc[3] = fma(ms, B.z, acc[3]);
+        acc[4] = fma(ms * nvi, nvj, acc[4]);
+        const double px = ms * nvi * is;
+        acc[5] = fma(px, dx, acc[5]);
+        acc[6] = fma(px, dy, acc[6]);
+        acc[7] = fma(px, dz, acc[7]);
+    }
+}
+
+__global__ void __launch_bounds__(kF64Threads)
+k_energy_pairs(const double4_32a *__restrict__ rec, int64_t ns_pad, int ntiles, int tps, double eps2,
+               double *__restrict__ part)
+{
+    __shared__ double4_32a sh[2][kF64Tile];
+    const int64_t t0 = (int64_t)blockIdx.x * kF64Threads;
+    const int64_t ti = t0 + threadIdx.x;
+    const double4_32a A = rec[ti];
+    const double4_32a B = rec[ns_pad + ti];
+    const double di[3] = {A.x, A.y, A.z};
+    const double vi[3] = {B.x, B.y, B.z};
+    double acc[kEVals];
+#pragma unroll
+    for (int k = 0; k < kEVals; ++k)
+        acc[k] = 0.0;
+    const int tb = blockIdx.y * tps;
+    const int te = min(ntiles, tb + tps);
+    for (int tile = tb; tile < te; ++tile) {
+        const int64_t j0 = (int64_t)tile * kF64Tile;
+        __syncthreads();
+        for (int q = threadIdx.x; q < kF64Tile; q += kF64Threads) {
+            sh[0][q] = rec[j0 + q];
+            sh[1][q] = rec[ns_pad + j0 + q];
+        }
+        __syncthreads();
+        const bool diag = (j0 < t0 + kF64Threads) && (t0 < j0 + kF64Tile);
+        if (diag)
+            energy_tile<true>(sh, j0, di, vi, ti, eps2, acc);
+        else
+            energy_tile<false>(sh, j0, di, vi, ti, eps2, acc);
+    }
+#pragma unroll
+    for (int k = 0; k < kEVals; ++k)
+        part[((int64_t)blockIdx.y * kEVals + k) * ns_pad + ti] = acc[k];
+}
+
+// ------------------------------------------------------------ epilogue --
+
+// Star i = t + 1 (double precision throughout), velocities v = those at
+// which A is taken:
+//   a_i = -G M d_i/R_i^3 - G N_i + (1/c^2) {
+//       G M d_i/R_i^3 (4 G M/R_i - v_i^2) + 4 G M (v_i.d_i) v_i/R_i^3   [Eq. 5]
+//     + 5 G^2 m_i M d_i/R_i^4                                          [Eq. 6 l.1]
+//     + G^2 M d_i/R_i^3 S_i                                            [Eq. 6 l.2]
+//     + G [V_i + (4 G M/R_i + v_i^2) N_i]                              [l.3 + l.6]
+//     - 7/2 G^2 M [E_i - (W - w_i)/R_i]                                [l.4]
+//     - G/R_i^3 [4 (v_i.Q) d_i - 3 (Q.d_i) v_i - 4 (v_i.d_i) Q]        [l.1 + l.5]
+//     + G H_i }                                                        [l.7]
+// with S_i = sum_{j!=i} m_j (4/r_ij + 5/(4R_j) + (R_i^2 - r_ij^2)/(4R_j^3))
+//          = 4 U_i + (SA - 5 m_i/(4R_i)) + d_i.(W - w_i)/2
+//            - (SB - m_i (R_i^2 + eps^2)/(4 R_i^3))
+// (R_i^2 - r_ij^2 = 2 d_i.d_j - R_j^2 - eps^2).  Line 1's self term and
+// line 5 together are the k-sum over all stars, hence Q.
+//
+// The same thread also forms star i's term of the hole's 1PN acceleration
+// (Eq. 2 and Eq. 3, with j = i):
+//   -G w_j (5 G M/R_j - 2 v_j^2 + 3/2 (v_j.d_j)^2/R_j^2) - 3 G m_j/R_j^3 (v_j.d_j) v_j
+//   - 4 G^2 m_j w_j / R_j
+//   - G^2 w_j [4 (Phi - m_j/R_j) + 5/4 U_j + 1/4 Y_j]
+//   - 7/2 G^2 (m_j/R_j) N_j
+//   + G/M m_j/R_j^3 [4 (v_j.Q) d_j - 3 (v_j.d_j) Q - 4 (Q.d_j) v_j]
+// and the block's sum of these goes to blk (deterministic tree).
+__global__ void __launch_bounds__(kGlueThreads)
+k_epilogue(int64_t ns, int64_t ns_pad, const double *__restrict__ x,
+           const double *__restrict__ vel, const double *__restrict__ m,
+           const double *__restrict__ p1, int js1, const double *__restrict__ p2, int js2,
+           const double *__restrict__ glob, double G, double inv_c2, double eps2,
+           double *__restrict__ a, double *__restrict__ v, double h, int *flag,
+           unsigned long long *flag_step, unsigned long long step, double *__restrict__ blk)
+{
+    __shared__ double sh[3][kGlueThreads];
+    const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
+    double bh[3] = {0.0, 0.0, 0.0};
+    if (t < ns) {
+        const int64_t i = t + 1;
+        const double M = m[0], mi = m[i];
+        const double GM = G * M;
+        const double d[3] = {x[3 * i] - x[0], x[3 * i + 1] - x[1], x[3 * i + 2] - x[2]};
+        const double R2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        const double R = sqrt(R2);
+        const double iR = 1.0 / R;
+        const double iR3 = iR * iR * iR;
+        const double vv[3] = {vel[3 * i], vel[3 * i + 1], vel[3 * i + 2]};
+        const double v2 = vv[0] * vv[0] + vv[1] * vv[1] + vv[2] * vv[2];
+        const double vd = vv[0] * d[0] + vv[1] * d[1] + vv[2] * d[2];
+        double s1[kP1Vals], s2[kP2Vals];
+        for (int k = 0; k < kP1Vals; ++k) {
+            double acc = 0.0;
+            for (int s = 0; s < js1; ++s)
+                acc += p1[((int64_t)s * kP1Vals + k) * ns_pad + t];
+            s1[k] = acc;
+        }
+        for (int k = 0; k < kP2Vals; ++k) {
+            double acc = 0.0;
+            for (int s = 0; s < js2; ++s)
+                acc += p2[((int64_t)s * kP2Vals + k) * ns_pad + t];
+            s2[k] = acc;
+        }
+        const double N[3] = {s1[0], s1[1], s1[2]};
+        const double U = s1[3], Y = s1[4];
+        const double Q[3] = {glob[0], glob[1], glob[2]};
+        const double W[3] = {glob[3], glob[4], glob[5]};
+        const double SA = glob[6], SB = glob[7], Phi = glob[8];
+        const double wi[3] = {mi * iR3 * d[0], mi * iR3 * d[1], mi * iR3 * d[2]};
+        const double Wx[3] = {W[0] - wi[0], W[1] - wi[1], W[2] - wi[2]};
+        const double vQ = vv[0] * Q[0] + vv[1] * Q[1] + vv[2] * Q[2];
+        const double Qd = Q[0] * d[0] + Q[1] * d[1] + Q[2] * d[2];
+        const double S = 4.0 * U + (SA - 1.25 * mi * iR) +
+                         0.5 * (d[0] * Wx[0] + d[1] * Wx[1] + d[2] * Wx[2]) -
+                         (SB - 0.25 * mi * (R2 + eps2) * iR3);
+        const double cd = GM * iR3 * (4.0 * GM * iR - v2) + 5.0 * G * GM * mi * iR3 * iR +
+                          G * GM * iR3 * S - 4.0 * G * iR3 * vQ;
+        const double cv = 4.0 * GM * iR3 * vd + 3.0 * G * iR3 * Qd;
+        const double cN = G * (4.0 * GM * iR + v2);
+        const double cQ = 4.0 * G * iR3 * vd;
+        const double c7 = 3.5 * G * GM;
+        double ai[3];
+        for (int k = 0; k < 3; ++k) {
+            const double pn = cd * d[k] + cv * vv[k] + G * s2[k] + cN * N[k] -
+                              c7 * (s2[6 + k] - Wx[k] * iR) + cQ * Q[k] + G * s2[3 + k];
+            ai[k] = (-GM * iR3 * d[k] - G * N[k]) + inv_c2 * pn;
+        }
+        // hole's term from this star
+        const double b1 = -G * (5.0 * GM * iR - 2.0 * v2 + 1.5 * vd * vd * iR * iR) -
+                          4.0 * G * G * mi * iR - G * G * (4.0 * (Phi - mi * iR) + 1.25 * U + 0.25 * Y);
+        const double gmr3 = G * mi * iR3;
+        for (int k = 0; k < 3; ++k)
+            bh[k] = b1 * wi[k] - 3.0 * gmr3 * vd * vv[k] - 3.5 * G * G * mi * iR * N[k] +
+                    (gmr3 / M) * (4.0 * vQ * d[k] - 3.0 * vd * Q[k] - 4.0 * Qd * vv[k]);
+        flag_nonfinite(ai, flag, flag_step, step);
+        for (int k = 0; k < 3; ++k) {
+            a[3 * i + k] = ai[k];
+            if (v)
+                v[3 * i + k] = fma(h, ai[k], v[3 * i + k]);
+        }
+    }
+    block_sum<3>(bh, sh);
+    if (threadIdx.x < 3)
+        blk[(int64_t)blockIdx.x * 3 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// The hole: a_0 = G W + (1/c^2) sum_j (star j's term above).
+__global__ void __launch_bounds__(kGlueThreads)
+k_hole(const double *__restrict__ blk, int64_t nblk, const double *__restrict__ glob, double G,
+       double inv_c2, double *__restrict__ a, double *__restrict__ v, double h, int *flag,
+       unsigned long long *flag_step, unsigned long long step)
+{
+    __shared__ double sh[3][kGlueThreads];
+    sum_blocks<3>(blk, nblk, sh);
+    if (threadIdx.x == 0) {
+        double a0[3];
+        for (int k = 0; k < 3; ++k)
+            a0[k] = G * glob[3 + k] + inv_c2 * sh[k][0];
+        flag_nonfinite(a0, flag, flag_step, step);
+        for (int k = 0; k < 3; ++k) {
+            a[k] = a0[k];
+            if (v)
+                v[k] = fma(h, a0[k], v[k]);
+        }
+    }
+}
+
+// ------------------------------------------------------------- energy --
+
+// Per star i (Eq. 7 and Eq. 8, double):
+//   eN  = 1/2 m_i v_i^2 - 1/2 G m_i pot_i - G M m_i / R_i
+//   ePN = 3/8 m_i v_i^4 + 3/2 G M m_i v_i^2 / R_i + 1/2 G^2 M^2 m_i / R_i^2
+//       + 1/4 G m_i pn_i + 1/2 G M m_i/R_i [3 v_1^2 - 7 v_1.v_i - (n.v_1)(n.v_i)]
+//       + G^2 M m_i pot_i / R_i
+//   pN  = m_i v_i
+//   pPN = 1/2 m_i v_i^2 v_i - 1/2 G M m_i/R_i [v_i + (v_i.n)n + v_1 + (v_1.n)n]
+//       - 1/2 G m_i p_i
+// with pn_i = 6 v_i^2 pot_i - 7 v_i.Smv_i - Snn_i, p_i = v_i pot_i + Spx_i,
+// n = d_i/R_i (its sign cancels), plus sum m_i/R_i for the i = j double sum.
+__global__ void __launch_bounds__(kGlueThreads)
+k_energy_epilogue(int64_t ns, int64_t ns_pad, const double *__restrict__ x,
+                  const double *__restrict__ vel, const double *__restrict__ m,
+                  const double *__restrict__ pe, int js, double G, double *__restrict__ blk)
+{
+    __shared__ double sh[kEBlockVals][kGlueThreads];
+    const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
+    double o[kEBlockVals];
+    for (int k = 0; k < kEBlockVals; ++k)
+        o[k] = 0.0;
+    if (t < ns) {
+        const int64_t i = t + 1;
+        const double M = m[0], mi = m[i];
+        const double d[3] = {x[3 * i] - x[0], x[3 * i + 1] - x[1], x[3 * i + 2] - x[2]};
+        const double R = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        const double iR = 1.0 / R;
+        const double vi[3] = {vel[3 * i], vel[3 * i + 1], vel[3 * i + 2]};
+        const double v1[3] = {vel[0], vel[1], vel[2]};
+        double s[kEVals];
+        for (int k = 0; k < kEVals; ++k) {
+            double acc = 0.0;
+            for (int q = 0; q < js; ++q)
+                acc += pe[((int64_t)q * kEVals + k) * ns_pad + t];
+            s[k] = acc;
+        }
+        const double vi2 = vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2];
+        const double v12 = v1[0] * v1[0] + v1[1] * v1[1] + v1[2] * v1[2];
+        const double v1vi = v1[0] * vi[0] + v1[1] * vi[1] + v1[2] * vi[2];
+        const double nvi = (d[0] * vi[0] + d[1] * vi[1] + d[2] * vi[2]) * iR;
+        const double nv1 = (d[0] * v1[0] + d[1] * v1[1] + d[2] * v1[2]) * iR;
+        const double pot = s[0];
+        const double vSmv = vi[0] * s[1] + vi[1] * s[2] + vi[2] * s[3];
+        const double pni = 6.0 * vi2 * pot - 7.0 * vSmv - s[4];
+        const double gmm = G * M * mi * iR;
+        o[0] = 0.5 * mi * vi2 - 0.5 * G * mi * pot - gmm;
+        o[1] = 0.375 * mi * vi2 * vi2 + 1.5 * gmm * vi2 + 0.5 * G * gmm * M * iR +
+               0.25 * G * mi * pni + 0.5 * gmm * (3.0 * v12 - 7.0 * v1vi - nv1 * nvi) +
+               G * gmm * pot;
+        for (int k = 0; k < 3; ++k) {
+            o[2 + k] = mi * vi[k];
+            const double pk = vi[k] * pot + s[5 + k];
+            o[5 + k] = 0.5 * mi * vi2 * vi[k] -
+                       0.5 * gmm * (vi[k] + nvi * d[k] * iR + v1[k] + nv1 * d[k] * iR) -
+                       0.5 * G * mi * pk;
+        }
+        o[8] = mi * iR;
+    }
+    block_sum<kEBlockVals>(o, sh);
+    if (threadIdx.x < kEBlockVals)
+        blk[(int64_t)blockIdx.x * kEBlockVals + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// Totals plus the hole's own terms: 1/2 M v_1^2, M v_1 and the i = j
+// double sum 1/2 G^2 M (sum_i m_i/R_i)^2 of Eq. 7.
+__global__ void __launch_bounds__(kGlueThreads)
+k_energy_final(const double *__restrict__ blk, int64_t nblk, const double *__restrict__ vel,
+               const double *__restrict__ m, double G, double inv_c2, double *__restrict__ out)
+{
+    __shared__ double sh[kEBlockVals][kGlueThreads];
+    sum_blocks<kEBlockVals>(blk, nblk, sh);
+    if (threadIdx.x == 0) {
+        const double M = m[0];
+        const double v1[3] = {vel[0], vel[1], vel[2]};
+        const double smr = sh[8][0];
+        out[0] = sh[0][0] + 0.5 * M * (v1[0] * v1[0] + v1[1] * v1[1] + v1[2] * v1[2]);
+        out[1] = inv_c2 * (sh[1][0] + 0.5 * G * G * M * smr * smr);
+        for (int k = 0; k < 3; ++k) {
+            out[2 + k] = sh[2 + k][0] + M * v1[k];
+            out[5 + k] = inv_c2 * sh[5 + k][0];
+        }
+    }
+}
+
+// ------------------------------------------------------------ launchers --
+
+static int64_t glue_blocks(int64_t n) { return (n + kGlueThreads - 1) / kGlueThreads; }
+
+cudaError_t launch_kick_drift(pn_ctx *c, double *x, double *v, const double *a, double dt)
+{
+    const int64_t n3 = 3 * c->n;
+    const int64_t nb = glue_blocks(n3) < 4 * (int64_t)c->sm_count ? glue_blocks(n3)
+                                                                    : 4 * (int64_t)c->sm_count;
+    k_kick_drift<<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(n3, x, v, a, c->vp, 0.5 * dt, dt,
+                                                               c->p.vel_mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prologue(pn_ctx *c, const double *x, const double *vel, const double *m,
+                            bool energy_records)
+{
+    const int64_t nb = glue_blocks(c->ns_pad);
+    const double eps2 = c->p.eps * c->p.eps;
+    if (energy_records) {
+        k_prologue<2><<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
+            c->ns, c->ns_pad, x, vel, m, c->p.G, eps2, c->mrec, c->drec, c->blk);
+        return cudaGetLastError();
+    }
+    if (c->p.precision == PN_MIXED)
+        k_prologue<0><<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
+            c->ns, c->ns_pad, x, vel, m, c->p.G, eps2, c->mrec, c->drec, c->blk);
+    else
+        k_prologue<1><<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
+            c->ns, c->ns_pad, x, vel, m, c->p.G, eps2, c->mrec, c->drec, c->blk);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    k_global_sums<<<1, kGlueThreads, 0, c->stream>>>(c->blk, nb, c->glob);
+    return cudaGetLastError();
+}
+
+static void timing_begin(pn_ctx *c, int k, cudaEvent_t *end_out);
+
+cudaError_t launch_pass1(pn_ctx *c)
+{
+    const double eps2 = c->p.eps * c->p.eps;
+    cudaEvent_t end = nullptr;
+    timing_begin(c, 0, &end);
+    if (c->p.precision == PN_MIXED) {
+        const Shape &s = c->mix;
+        dim3 grid((unsigned)s.nblk_i, (unsigned)s.jsplit);
+        k_pass_mixed<1><<<grid, kMixThreads, 0, c->stream>>>(c->mrec, c->ns_pad, s.ntiles,
+                                                             s.tiles_per_split, (float)eps2, c->part);
+    } else {
+        const Shape &s = c->f64;
+        dim3 grid((unsigned)s.nblk_i, (unsigned)s.jsplit);
+        k_pass_f64<1><<<grid, kF64Threads, 0, c->stream>>>(c->drec, c->ns_pad, s.ntiles,
+                                                           s.tiles_per_split, eps2, c->part);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (end)
+        cudaEventRecord(end, c->stream);
+    return e;
+}
+
+static int64_t p2_offset(pn_ctx *c)
+{
+    const Shape &s = c->p.precision == PN_MIXED ? c->mix : c->f64;
+    return (int64_t)s.jsplit * kP1Vals * c->ns_pad;
+}
+
+cudaError_t launch_pass2(pn_ctx *c)
+{
+    const double eps2 = c->p.eps * c->p.eps;
+    double *p2 = c->part + p2_offset(c);
+    cudaEvent_t end = nullptr;
+    timing_begin(c, 1, &end);
+    if (c->p.precision == PN_MIXED) {
+        const Shape &s = c->mix;
+        dim3 grid((unsigned)s.nblk_i, (unsigned)s.jsplit);
+        k_pass_mixed<2><<<grid, kMixThreads, 0, c->stream>>>(c->mrec, c->ns_pad, s.ntiles,
+                                                             s.tiles_per_split, (float)eps2, p2);
+    } else {
+        const Shape &s = c->f64;
+        dim3 grid((unsigned)s.nblk_i, (unsigned)s.jsplit);
+        k_pass_f64<2><<<grid, kF64Threads, 0, c->stream>>>(c->drec, c->ns_pad, s.ntiles,
+                                                           s.tiles_per_split, eps2, p2);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (end)
+        cudaEventRecord(end, c->stream);
+    return e;
+}
+
+cudaError_t launch_epilogue(pn_ctx *c, const double *x, const double *vel, const double *m,
+                            double *a, double *v, double h, unsigned long long step)
+{
+    const Shape &s = c->p.precision == PN_MIXED ? c->mix : c->f64;
+    const int64_t nb = glue_blocks(c->ns_pad);
+    const double eps2 = c->p.eps * c->p.eps;
+    k_epilogue<<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
+        c->ns, c->ns_pad, x, vel, m, c->part, s.jsplit, c->part + p2_offset(c), s.jsplit,
+        c->glob, c->p.G, c->inv_c2, eps2, a, v, h, c->flag, c->flag_step, step, c->blk);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    k_hole<<<1, kGlueThreads, 0, c->stream>>>(c->blk, nb, c->glob, c->p.G, c->inv_c2, a, v, h,
+                                              c->flag, c->flag_step, step);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy(pn_ctx *c, const double *x, const double *v, const double *m)
+{
+    cudaError_t e = launch_prologue(c, x, v, m, true);
+    if (e != cudaSuccess)
+        return e;
+    const Shape &s = c->f64;
+    const double eps2 = c->p.eps * c->p.eps;
+    dim3 grid((unsigned)s.nblk_i, (unsigned)s.jsplit);
+    k_energy_pairs<<<grid, kF64Threads, 0, c->stream>>>(c->drec, c->ns_pad, s.ntiles,
+                                                        s.tiles_per_split, eps2, c->part);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    const int64_t nb = glue_blocks(c->ns_pad);
+    k_energy_epilogue<<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(c->ns, c->ns_pad, x, v, m,
+                                                                    c->part, s.jsplit, c->p.G,
+                                                                    c->blk);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    k_energy_final<<<1, kGlueThreads, 0, c->stream>>>(c->blk, nb, v, m, c->p.G, c->inv_c2,
+                                                      c->eout);
+    return cudaGetLastError();
+}
+
+// Timing ring: an event pair per pair-kernel launch; the oldest pair is
+// folded into the total when the ring is full (this waits for that event,
+// which lies far behind the queued work).
+static void timing_begin(pn_ctx *c, int k, cudaEvent_t *end_out)
+{
+    *end_out = nullptr;
+    if (!c->timing_on)
+        return;
+    Timing &t = c->tm;
+    if (t.count[k] == Timing::kRing) {
+        const int old = t.head[k];
+        float ms = 0.0f;
+        if (cudaEventSynchronize(t.ev1[k][old]) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, t.ev0[k][old], t.ev1[k][old]) == cudaSuccess)
+            t.ms[k] += ms;
+        t.launches[k] += 1;
+        t.head[k] = (old + 1) % Timing::kRing;
+        t.count[k] -= 1;
+    }
+    const int slot = (t.head[k] + t.count[k]) % Timing::kRing;
+    cudaEventRecord(t.ev0[k][slot], c->stream);
+    *end_out = t.ev1[k][slot];
+    t.count[k] += 1;
+}
+
+void shapes(int64_t ns_pad, int sm_count, int occ_mix, int occ_f64, Shape *mix, Shape *f64)
+{
+    struct Cfg { int threads, targets, tile, occ; Shape *out; } cfg[2] = {
+        {kMixThreads, kMixTargets, kMixTile, occ_mix, mix},
+        {kF64Threads, kF64Targets, kF64Tile, occ_f64, f64}};
+    for (auto &c : cfg) {
+        Shape &s = *c.out;
+        s.threads = c.threads;
+        s.targets = c.targets;
+        s.tile = c.tile;
+        s.occupancy = c.occ > 0 ? c.occ : 1;
+        s.nblk_i = ns_pad / (c.threads * c.targets);
+        s.ntiles = (int)(ns_pad / c.tile);
+        const int64_t resident = (int64_t)s.occupancy * sm_count;
+        int64_t want = (8 * resident + s.nblk_i - 1) / s.nblk_i;   // splits for ~8 waves
+        if (want < 1)
+            want = 1;
+        int64_t tps = (s.ntiles + want - 1) / want;
+        if (tps < 1)
+            tps = 1;
+        s.tiles_per_split = (int)tps;
+        s.jsplit = (int)((s.ntiles + tps - 1) / tps);
+    }
+}
+
+cudaError_t occupancy(int *occ_mix, int *occ_f64)
+{
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_mix, k_pass_mixed<2>,
+                                                                  kMixThreads, 0);
+    if (e != cudaSuccess)
+        return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_f64, k_pass_f64<2>, kF64Threads, 0);
+}
+
+}  // namespace pn

@@ -1,0 +1,254 @@
+"""Thin ctypes binding of libpn's C ABI (include/pn.h), same names.
+
+Argument marshalling only: every step of the computation runs in libpn's
+CUDA kernels.  Device arrays are torch tensors (float64, contiguous, on the
+context's device); ``pn_step_host`` takes numpy arrays.  If ``libpn.so`` is
+missing the first call raises -- there is no CPU fallback.
+
+    ctx = pn_init(n, G=1.0, c=50.0, eps=1e-4, precision="mixed")
+    pn_accel(ctx, x, v, m, a)             # a = A(x, v)
+    pn_step(ctx, x, v, m, a, dt, nsteps)  # KDK steps, in place
+    e = pn_energy(ctx, x, v, m)           # Eq. 7 / Eq. 8
+    pn_destroy(ctx)
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+PN_OK, PN_EINVAL, PN_ENOMEM, PN_ECUDA, PN_ENONFINITE, PN_ETIMEOUT, PN_EUNSUPPORTED = range(7)
+STATUS_NAMES = {0: "PN_OK", 1: "PN_EINVAL", 2: "PN_ENOMEM", 3: "PN_ECUDA", 4: "PN_ENONFINITE",
+                5: "PN_ETIMEOUT", 6: "PN_EUNSUPPORTED"}
+PN_FP64, PN_MIXED = 0, 1
+PN_VPRED_END, PN_VHALF = 0, 1
+_PRECISION = {"fp64": PN_FP64, "mixed": PN_MIXED, PN_FP64: PN_FP64, PN_MIXED: PN_MIXED}
+_VEL_MODE = {"vpred_end": PN_VPRED_END, "vhalf": PN_VHALF, PN_VPRED_END: PN_VPRED_END,
+             PN_VHALF: PN_VHALF}
+
+
+class PNError(RuntimeError):
+    """A libpn call returned a status other than PN_OK."""
+
+    def __init__(self, status: int, message: str):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("G", ctypes.c_double), ("c", ctypes.c_double), ("eps", ctypes.c_double),
+                ("precision", ctypes.c_int), ("vel_mode", ctypes.c_int)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return os.environ.get("PN_LIBRARY") or os.path.join(HERE, "libpn.so")
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = library_path()
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is not built: run `python -m paper_1801_07986_b300.build`"
+                                   " (or __graft_entry__.build()); there is no CPU fallback")
+            lib = ctypes.CDLL(path)
+            P, I64, I, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+            sig = {
+                "pn_init": [ctypes.POINTER(P), I64, ctypes.POINTER(_Params), I, P],
+                "pn_set_params": [P, ctypes.POINTER(_Params)],
+                "pn_set_stream": [P, P],
+                "pn_accel": [P, P, P, P, P],
+                "pn_step": [P, P, P, P, P, D, I64],
+                "pn_step_host": [P, P, P, P, P, D, I64],
+                "pn_energy": [P, P, P, P, P],
+                "pn_sync": [P],
+                "pn_set_timing": [P, I],
+                "pn_get_timing": [P, P, P],
+                "pn_get_launch": [P, P],
+            }
+            for name, args in sig.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_int
+            lib.pn_last_error.argtypes = []
+            lib.pn_last_error.restype = ctypes.c_char_p
+            lib.pn_destroy.argtypes = [P]
+            lib.pn_destroy.restype = None
+            lib.pn_version.argtypes = []
+            lib.pn_version.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _check(status: int) -> None:
+    if status != PN_OK:
+        raise PNError(status, pn_last_error())
+
+
+def pn_last_error() -> str:
+    return _load().pn_last_error().decode()
+
+
+def pn_version() -> int:
+    return int(_load().pn_version())
+
+
+def _params(G, c, eps, precision, vel_mode) -> _Params:
+    if precision not in _PRECISION:
+        raise ValueError(f"precision must be 'fp64' or 'mixed', got {precision!r}")
+    if vel_mode not in _VEL_MODE:
+        raise ValueError(f"vel_mode must be 'vpred_end' or 'vhalf', got {vel_mode!r}")
+    return _Params(float(G), float(c), float(eps), _PRECISION[precision], _VEL_MODE[vel_mode])
+
+
+class Context:
+    """Owns one pn_ctx handle (pn_destroy on close / garbage collection)."""
+
+    def __init__(self, handle: int, n: int, device: int, params: _Params):
+        self.handle = ctypes.c_void_p(handle)
+        self.n = n
+        self.device = device
+        self.params = params
+
+    def close(self) -> None:
+        if self.handle:
+            _load().pn_destroy(self.handle)
+            self.handle = ctypes.c_void_p(None)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _torch_stream(device, stream):
+    if stream is not None:
+        return getattr(stream, "cuda_stream", stream)
+    import torch
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def pn_init(n: int, G: float = 1.0, c: float = math.inf, eps: float = 0.0,
+            precision="mixed", vel_mode="vpred_end", device: int | None = None,
+            stream=None) -> Context:
+    """Create a context for n bodies (body 0 = the hole)."""
+    lib = _load()
+    if device is None:
+        import torch
+        device = torch.cuda.current_device()
+    p = _params(G, c, eps, precision, vel_mode)
+    h = ctypes.c_void_p()
+    _check(lib.pn_init(ctypes.byref(h), int(n), ctypes.byref(p), int(device),
+                       ctypes.c_void_p(_torch_stream(device, stream))))
+    return Context(h.value, int(n), int(device), p)
+
+
+def pn_set_params(ctx: Context, G=None, c=None, eps=None, precision=None, vel_mode=None) -> None:
+    q = ctx.params
+    inv = {v: k for k, v in _PRECISION.items() if isinstance(k, str)}
+    invv = {v: k for k, v in _VEL_MODE.items() if isinstance(k, str)}
+    p = _params(q.G if G is None else G, q.c if c is None else c, q.eps if eps is None else eps,
+                inv[q.precision] if precision is None else precision,
+                invv[q.vel_mode] if vel_mode is None else vel_mode)
+    _check(_load().pn_set_params(ctx.handle, ctypes.byref(p)))
+    ctx.params = p
+
+
+def pn_set_stream(ctx: Context, stream) -> None:
+    _check(_load().pn_set_stream(ctx.handle, ctypes.c_void_p(getattr(stream, "cuda_stream", stream))))
+
+
+def _dev(ctx: Context, t, shape, name):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor on cuda:{ctx.device}")
+    if t.dtype != torch.float64 or not t.is_cuda or t.device.index != ctx.device:
+        raise TypeError(f"{name} must be float64 on cuda:{ctx.device} (got {t.dtype}, {t.device})")
+    if tuple(t.shape) != shape or not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous with shape {shape} (got {tuple(t.shape)})")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def pn_accel(ctx: Context, x, v, m, a) -> None:
+    """a = A(x, v) for all bodies (device tensors (n,3), (n,3), (n,), (n,3))."""
+    n = ctx.n
+    _check(_load().pn_accel(ctx.handle, _dev(ctx, x, (n, 3), "x"), _dev(ctx, v, (n, 3), "v"),
+                            _dev(ctx, m, (n,), "m"), _dev(ctx, a, (n, 3), "a")))
+
+
+def pn_step(ctx: Context, x, v, m, a, dt: float, nsteps: int = 1) -> None:
+    """nsteps KDK steps in place; a must hold A at the entry state."""
+    n = ctx.n
+    _check(_load().pn_step(ctx.handle, _dev(ctx, x, (n, 3), "x"), _dev(ctx, v, (n, 3), "v"),
+                           _dev(ctx, m, (n,), "m"), _dev(ctx, a, (n, 3), "a"), float(dt),
+                           int(nsteps)))
+
+
+def _host(arr, shape, name):
+    if not isinstance(arr, np.ndarray) or arr.dtype != np.float64 or arr.shape != shape \
+            or not arr.flags.c_contiguous or not arr.flags.writeable:
+        raise TypeError(f"{name} must be a writeable C-contiguous float64 numpy array {shape}")
+    return arr.ctypes.data_as(ctypes.c_void_p)
+
+
+def pn_step_host(ctx: Context, x, v, m, a, dt: float, nsteps: int = 1) -> None:
+    """pn_step on host (numpy) arrays, copies included; waits for the result."""
+    n = ctx.n
+    _check(_load().pn_step_host(ctx.handle, _host(x, (n, 3), "x"), _host(v, (n, 3), "v"),
+                                _host(m, (n,), "m"), _host(a, (n, 3), "a"), float(dt),
+                                int(nsteps)))
+
+
+def pn_energy(ctx: Context, x, v, m) -> dict:
+    """Eq. 7 energy and Eq. 8 momentum (FP64), as a dict like the oracle's."""
+    n = ctx.n
+    out = np.zeros(8)
+    _check(_load().pn_energy(ctx.handle, _dev(ctx, x, (n, 3), "x"), _dev(ctx, v, (n, 3), "v"),
+                             _dev(ctx, m, (n,), "m"), out.ctypes.data_as(ctypes.c_void_p)))
+    return {"E_N": out[0], "E_PN": out[1], "E": out[0] + out[1],
+            "P_N": out[2:5].copy(), "P_PN": out[5:8].copy(), "P": out[2:5] + out[5:8]}
+
+
+def pn_sync(ctx: Context) -> None:
+    _check(_load().pn_sync(ctx.handle))
+
+
+def pn_set_timing(ctx: Context, enable: bool) -> None:
+    _check(_load().pn_set_timing(ctx.handle, 1 if enable else 0))
+
+
+def pn_get_timing(ctx: Context):
+    """(milliseconds, launches) of pass 1 and pass 2 since timing was enabled."""
+    ms = np.zeros(2)
+    nl = np.zeros(2, dtype=np.int64)
+    _check(_load().pn_get_timing(ctx.handle, ms.ctypes.data_as(ctypes.c_void_p),
+                                 nl.ctypes.data_as(ctypes.c_void_p)))
+    return ms, nl
+
+
+def pn_get_launch(ctx: Context) -> dict:
+    out = np.zeros(7, dtype=np.int64)
+    _check(_load().pn_get_launch(ctx.handle, out.ctypes.data_as(ctypes.c_void_p)))
+    keys = ("threads", "targets_per_thread", "tile", "blocks_i", "jsplit", "occupancy", "sms")
+    return {k: int(v) for k, v in zip(keys, out)}
+
+
+def pn_destroy(ctx: Context) -> None:
+    ctx.close()

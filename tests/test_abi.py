@@ -1,0 +1,124 @@
+"""The C ABI on the host: libpn builds, loads, exports every symbol the
+header declares, and rejects bad arguments before touching the GPU."""
+import ctypes
+import math
+import os
+import re
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pn.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1801_07986_b300 import build, pn
+    build.build_library()
+    return pn._load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pn_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for want in ("pn_init", "pn_accel", "pn_step", "pn_energy", "pn_set_params", "pn_destroy",
+                 "pn_last_error", "pn_step_host", "pn_sync"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", lib._name], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r" T (pn_[a-z_]+)", out))
+    assert set(declared_functions()) <= exported
+
+
+def test_header_compiles_as_c():
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-fsyntax-only", "-x", "c", HEADER],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
+def _params(G=1.0, c=50.0, eps=1e-4, precision=1, vel_mode=0):
+    from paper_1801_07986_b300.pn import _Params
+    return _Params(G, c, eps, precision, vel_mode)
+
+
+@pytest.mark.parametrize("n,kw,msg", [
+    (1, {}, "n must be"),
+    (0, {}, "n must be"),
+    (100, {"G": 0.0}, "G must be"),
+    (100, {"G": float("nan")}, "G must be"),
+    (100, {"c": -1.0}, "c must be"),
+    (100, {"c": float("nan")}, "c must be"),
+    (100, {"eps": -1e-3}, "eps must be"),
+    (100, {"eps": float("inf")}, "eps must be"),
+    (100, {"precision": 7}, "precision"),
+    (100, {"vel_mode": 3}, "vel_mode"),
+])
+def test_init_rejects_bad_arguments_on_host(lib, n, kw, msg):
+    h = ctypes.c_void_p()
+    p = _params(**kw)
+    st = lib.pn_init(ctypes.byref(h), n, ctypes.byref(p), 0, None)
+    assert st == 1  # PN_EINVAL
+    assert msg in lib.pn_last_error().decode()
+    assert not h.value
+
+
+def test_null_arguments(lib):
+    p = _params()
+    assert lib.pn_init(None, 10, ctypes.byref(p), 0, None) == 1
+    assert lib.pn_init(ctypes.byref(ctypes.c_void_p()), 10, None, 0, None) == 1
+    for name, nargs in (("pn_accel", 5), ("pn_step", 7), ("pn_energy", 5), ("pn_sync", 1),
+                        ("pn_step_host", 7), ("pn_set_timing", 2), ("pn_get_launch", 2)):
+        fn = getattr(lib, name)
+        args = [None] * nargs
+        if name in ("pn_step", "pn_step_host"):
+            args[5] = 0.01
+            args[6] = 1
+        if name == "pn_set_timing":
+            args[1] = 1
+        assert fn(*args) == 1, name
+        assert "NULL" in lib.pn_last_error().decode()
+    lib.pn_destroy(None)   # no-op
+
+
+def test_injected_allocation_failure():
+    code = ("import ctypes; from paper_1801_07986_b300 import pn; lib = pn._load();"
+            "p = pn._Params(1.0, 50.0, 1e-4, 1, 0); h = ctypes.c_void_p();"
+            "print(lib.pn_init(ctypes.byref(h), 100, ctypes.byref(p), 0, None),"
+            " lib.pn_last_error().decode())")
+    env = dict(os.environ, PN_FAIL_ALLOC="1", PYTHONPATH=ROOT)
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                         check=True).stdout
+    assert out.startswith("2 ") and "PN_FAIL_ALLOC" in out
+
+
+def test_python_binding_fails_loudly_without_library(tmp_path):
+    code = ("from paper_1801_07986_b300 import pn\n"
+            "try:\n    pn.pn_version()\nexcept RuntimeError as e:\n    print('raised', e)\n")
+    env = dict(os.environ, PN_LIBRARY=str(tmp_path / "missing.so"), PYTHONPATH=ROOT)
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                         check=True).stdout
+    assert out.startswith("raised") and "no CPU fallback" in out
+
+
+def test_version(lib):
+    assert lib.pn_version() >= 100
+
+
+def test_python_binding_validates_before_calling(lib):
+    from paper_1801_07986_b300 import pn
+    with pytest.raises(ValueError):
+        pn._params(1.0, math.inf, 0.0, "fp32", "vpred_end")
+    with pytest.raises(ValueError):
+        pn._params(1.0, math.inf, 0.0, "mixed", "rk4")

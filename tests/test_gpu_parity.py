@@ -1,0 +1,253 @@
+"""GPU (libpn, through the C ABI) vs the FP64 CPU oracle, element by element.
+
+Tolerances (relative force error |a_gpu - a_oracle| / |a_oracle| per body):
+  FP64 mode   <= 1e-12 for every body;
+  mixed mode  <= 2e-7 median and <= 1e-5 max over all bodies.
+Sizes span several 256-star blocks and ragged tails; the 16k and 128k
+Plummer workloads are checked on sampled targets in the launch shape the
+benchmark uses.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1801_07986_b300 import pn  # noqa: E402
+from paper_1801_07986_b300.inputs import WORKLOADS, make_cluster  # noqa: E402
+
+DEV = torch.device("cuda:0")
+FP64_TOL = 1e-12
+MIX_MED, MIX_MAX = 2e-7, 1e-5
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b, axis=-1) / np.linalg.norm(b, axis=-1)
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+def gpu_accel(x, v, m, precision, G=1.0, c=math.inf, eps=0.0, vel_mode="vpred_end"):
+    n = m.shape[0]
+    ctx = pn.pn_init(n, G=G, c=c, eps=eps, precision=precision, vel_mode=vel_mode, device=0)
+    X, V, M = dev(x), dev(v), dev(m)
+    A = torch.empty_like(X)
+    pn.pn_accel(ctx, X, V, M, A)
+    pn.pn_sync(ctx)
+    out = A.cpu().numpy()
+    ctx.close()
+    return out
+
+
+@pytest.mark.parametrize("n", [2, 3, 33, 257, 300, 1024])
+def test_fp64_matches_oracle(orc, n):
+    x, v, m = make_cluster(n, 0.1, 100 + n)
+    for c in (100.0, 5.0):
+        want = orc.accel(x, v, m, c=c, eps=1e-4)
+        got = gpu_accel(x, v, m, "fp64", c=c, eps=1e-4)
+        err = rel(got, want)
+        assert err.max() <= FP64_TOL, (c, err.max(), int(err.argmax()))
+
+
+@pytest.mark.parametrize("n", [2, 3, 300, 1024, 4097])
+def test_mixed_matches_oracle(orc, n):
+    x, v, m = make_cluster(n, 0.1, 200 + n)
+    want = orc.accel(x, v, m, c=20.0, eps=1e-4)
+    got = gpu_accel(x, v, m, "mixed", c=20.0, eps=1e-4)
+    err = rel(got, want)
+    assert np.median(err) <= MIX_MED and err.max() <= MIX_MAX, (np.median(err), err.max())
+
+
+def test_plummer1k_workload_fp64_every_body(orc):
+    w = WORKLOADS["plummer1k_fp64"]
+    x, v, m = w.state()
+    want = orc.accel(x, v, m, G=w.G, c=w.c, eps=w.eps)
+    got = gpu_accel(x, v, m, "fp64", G=w.G, c=w.c, eps=w.eps)
+    assert rel(got, want).max() <= FP64_TOL
+
+
+def test_newtonian_limit_and_linearity_in_inv_c2(orc):
+    x, v, m = make_cluster(700, 0.2, 31)
+    eps = 1e-3
+    a_inf = gpu_accel(x, v, m, "fp64", c=math.inf, eps=eps)
+    assert rel(a_inf, orc.newton_accel(x, m, eps=eps)).max() <= FP64_TOL
+    d1 = (gpu_accel(x, v, m, "fp64", c=20.0, eps=eps) - a_inf) * 400.0
+    d2 = (gpu_accel(x, v, m, "fp64", c=7.0, eps=eps) - a_inf) * 49.0
+    assert rel(d1, d2).max() < 1e-8
+    # the 1PN part alone agrees with the oracle's 1PN part
+    o1 = (orc.accel(x, v, m, c=20.0, eps=eps) - orc.accel(x, v, m, c=math.inf, eps=eps)) * 400.0
+    assert rel(d1, o1).max() < 1e-8
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-12)])
+def test_energy_matches_oracle(orc, precision, tol):
+    x, v, m = make_cluster(513, 0.1, 41)
+    v = v.copy()
+    v[0] = [0.01, -0.02, 0.005]          # a moving hole exercises the v_1 terms
+    c, eps = 10.0, 1e-3
+    want = orc.energy(x, v, m, c=c, eps=eps)
+    ctx = pn.pn_init(513, c=c, eps=eps, precision=precision, device=0)
+    got = pn.pn_energy(ctx, dev(x), dev(v), dev(m))
+    ctx.close()
+    for k in ("E_N", "E_PN"):
+        assert abs(got[k] - want[k]) <= tol * abs(want[k]), k
+    pscale = float(np.sum(m[:, None] * np.abs(v)))
+    for k in ("P_N", "P_PN"):
+        assert np.abs(got[k] - want[k]).max() <= tol * pscale, k
+
+
+@pytest.mark.parametrize("vel_mode,mode_id", [("vpred_end", 0), ("vhalf", 1)])
+def test_steps_fp64_match_oracle(orc, vel_mode, mode_id):
+    """20 KDK steps of the 1k workload: same trajectory to round-off, and at
+    the final state the force equals the oracle's on the GPU's own state."""
+    w = WORKLOADS["plummer1k_fp64"]
+    x, v, m = w.state()
+    ctx = pn.pn_init(w.n, G=w.G, c=w.c, eps=w.eps, precision="fp64", vel_mode=vel_mode, device=0)
+    X, V, M = dev(x), dev(v), dev(m)
+    A = torch.empty_like(X)
+    pn.pn_accel(ctx, X, V, M, A)
+    a0 = orc.accel(x, v, m, G=w.G, c=w.c, eps=w.eps)
+    pn.pn_step(ctx, X, V, M, A, w.dt, 20)
+    pn.pn_sync(ctx)
+    xo, vo, ao = orc.step(x, v, m, a0, w.dt, 20, G=w.G, c=w.c, eps=w.eps, vel_mode=mode_id)
+    xg, vg, ag = X.cpu().numpy(), V.cpu().numpy(), A.cpu().numpy()
+    assert np.abs(xg - xo).max() < 1e-12
+    assert np.abs(vg - vo).max() < 1e-11 * np.abs(vo).max()
+    assert rel(ag, ao).max() < 1e-9
+    ctx.close()
+
+
+def test_step_force_is_accel_at_predicted_velocity():
+    """After one step, a equals pn_accel at (x_new, v_half + dt/2 a_old)."""
+    x, v, m = make_cluster(1000, 0.1, 51)
+    dt = 1.0 / 512
+    ctx = pn.pn_init(1000, c=15.0, eps=1e-4, precision="fp64", device=0)
+    X, V, M = dev(x), dev(v), dev(m)
+    A = torch.empty_like(X)
+    pn.pn_accel(ctx, X, V, M, A)
+    a_old = A.clone()
+    v_half = V + 0.5 * dt * a_old
+    x_new = X + dt * v_half
+    pn.pn_step(ctx, X, V, M, A, dt, 1)
+    B = torch.empty_like(X)
+    pn.pn_accel(ctx, x_new, v_half + 0.5 * dt * a_old, M, B)
+    pn.pn_sync(ctx)
+    assert rel(A.cpu().numpy(), B.cpu().numpy()).max() < 1e-13
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_plummer16k_sampled_targets_and_hole(orc, precision):
+    w = WORKLOADS["plummer16k"]
+    x, v, m = w.state()
+    got = gpu_accel(x, v, m, precision, G=w.G, c=w.c, eps=w.eps)
+    rng = np.random.default_rng(5)
+    targets = np.concatenate([[0, 1, w.n - 1], rng.choice(np.arange(2, w.n - 1), 300, replace=False)])
+    want = orc.accel_rows(x, v, m, targets, G=w.G, c=w.c, eps=w.eps)
+    err = rel(got[targets], want)
+    if precision == "fp64":
+        assert err.max() <= FP64_TOL, err.max()
+    else:
+        assert np.median(err) <= MIX_MED and err.max() <= MIX_MAX, (np.median(err), err.max())
+
+
+def test_plummer128k_eccentric_sampled_targets(orc):
+    """The 128k workload with 1% of stars on e = 0.9 orbits about the hole:
+    sampled targets (all kinds) against the oracle, mixed precision."""
+    w = WORKLOADS["plummer128k_ecc"]
+    x, v, m = w.state()
+    got = gpu_accel(x, v, m, "mixed", G=w.G, c=w.c, eps=w.eps)
+    assert np.all(np.isfinite(got))
+    rng = np.random.default_rng(6)
+    n_ecc = int(round(w.ecc_frac * (w.n - 1)))
+    targets = np.concatenate([[1, n_ecc, n_ecc + 1, w.n - 1],
+                              rng.choice(np.arange(2, n_ecc), 60, replace=False),
+                              rng.choice(np.arange(n_ecc + 2, w.n - 1), 140, replace=False)])
+    want = orc.accel_rows(x, v, m, targets, G=w.G, c=w.c, eps=w.eps)
+    err = rel(got[targets], want)
+    assert np.median(err) <= MIX_MED and err.max() <= MIX_MAX, (np.median(err), err.max())
+
+
+def test_plummer128k_newtonian_momentum_balance():
+    """At c = inf the Newtonian pair forces cancel: sum_a m_a a_a = 0 up to
+    single-precision pair round-off (a property that holds at any size)."""
+    w = WORKLOADS["plummer128k_ecc"]
+    x, v, m = w.state()
+    a = gpu_accel(x, v, m, "mixed", G=w.G, c=math.inf, eps=w.eps)
+    f = (m[:, None] * a).sum(0)
+    scale = (m[:, None] * np.abs(a)).sum(0)
+    assert np.all(np.abs(f) <= 1e-6 * scale)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_deterministic(precision):
+    x, v, m = make_cluster(3000, 0.1, 61)
+    a1 = gpu_accel(x, v, m, precision, c=30.0, eps=1e-4)
+    a2 = gpu_accel(x, v, m, precision, c=30.0, eps=1e-4)
+    assert np.array_equal(a1, a2)
+
+
+def test_translation_invariance_mixed(orc):
+    x, v, m = make_cluster(2000, 0.1, 71)
+    shift = np.array([1.0e3, -2.0e3, 5.0e2])
+    got = gpu_accel(x + shift, v, m, "mixed", c=20.0, eps=1e-4)
+    want = orc.accel(x, v, m, c=20.0, eps=1e-4)
+    err = rel(got, want)
+    assert np.median(err) <= MIX_MED and err.max() <= MIX_MAX
+
+
+def test_nonfinite_is_reported_and_cleared():
+    x, v, m = make_cluster(300, 0.1, 81)
+    x = x.copy()
+    x[5] = x[0]                      # a star on top of the hole: r = 0
+    ctx = pn.pn_init(300, c=20.0, eps=1e-4, precision="mixed", device=0)
+    X, V, M = dev(x), dev(v), dev(m)
+    A = torch.empty_like(X)
+    pn.pn_accel(ctx, X, V, M, A)
+    with pytest.raises(pn.PNError) as ei:
+        pn.pn_sync(ctx)
+    assert ei.value.status == pn.PN_ENONFINITE
+    x2, _, _ = make_cluster(300, 0.1, 81)
+    pn.pn_accel(ctx, dev(x2), V, M, A)
+    pn.pn_sync(ctx)                  # flag was cleared
+    ctx.close()
+
+
+def test_step_host_equals_device_path():
+    x, v, m = make_cluster(1500, 0.1, 91)
+    dt = 1.0 / 1024
+    ctx = pn.pn_init(1500, c=30.0, eps=1e-4, precision="mixed", device=0)
+    X, V, M = dev(x), dev(v), dev(m)
+    A = torch.empty_like(X)
+    pn.pn_accel(ctx, X, V, M, A)
+    a_host = A.cpu().numpy().copy()
+    xh, vh = x.copy(), v.copy()
+    pn.pn_step(ctx, X, V, M, A, dt, 3)
+    pn.pn_step_host(ctx, xh, vh, m.copy(), a_host, dt, 3)
+    assert np.array_equal(X.cpu().numpy(), xh)
+    assert np.array_equal(V.cpu().numpy(), vh)
+    assert np.array_equal(A.cpu().numpy(), a_host)
+    ctx.close()
+
+
+def test_timing_counts_launches():
+    x, v, m = make_cluster(2048, 0.1, 95)
+    ctx = pn.pn_init(2048, c=30.0, eps=1e-4, precision="mixed", device=0)
+    X, V, M = dev(x), dev(v), dev(m)
+    A = torch.empty_like(X)
+    pn.pn_accel(ctx, X, V, M, A)
+    pn.pn_set_timing(ctx, True)
+    pn.pn_step(ctx, X, V, M, A, 1e-3, 70)    # more than the 64-entry event ring
+    ms, nl = pn.pn_get_timing(ctx)
+    assert list(nl) == [70, 70] and np.all(ms > 0)
+    shape = pn.pn_get_launch(ctx)
+    assert shape["sms"] > 0 and shape["jsplit"] >= 1
+    pn.pn_set_timing(ctx, False)
+    ctx.close()
