@@ -1,0 +1,383 @@
+"""Throughput of the limited-1PN N-body step on B300: 1PN pair interactions/s.
+
+One step = one kick-drift-kick leapfrog step through the C ABI (pn_step):
+kick/drift, prologue, pass 1, pass 2, epilogue, hole reduction -- the whole
+hot path -- over the full synthetic workload.  An interaction is one ordered
+pair of bodies (i, j), i != j, in one acceleration evaluation, so a step of
+N bodies counts N (N - 1).
+
+Usage:
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                    [--precision mixed|fp64] [--impl reference]
+
+Default workload: 131072 bodies (hole of mass 0.76 + Plummer stars, 1% on
+e = 0.9 orbits about the hole), c = 30, eps = 5e-5, dt = 1/8192, mixed
+precision, 200 steps.  Prints ONE JSON line on rank 0.
+
+--impl reference times the FP64 CPU oracle (the checker of this library, as
+it stands) on the host cores, each step a bounded sample of the same
+evaluation (a fixed number of star rows and hole rows of the O(N^2) work),
+scaled to interactions/s.
+
+With --gpus N > 1 (launched by torch.distributed.run) every rank runs an
+independent replica of the workload on its own GPU (the path has no
+cross-GPU exchange in this build): value = all ranks' interactions / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "1PN pair interactions/s at N=16k/128k, mixed vs FP64 on B300 at <=1e-5 rel err"
+FLOPS_PASS1 = 36   # hand count of the mixed pass-1 pair body (FMA = 2, rsqrt = 1)
+FLOPS_PASS2 = 72   # hand count of the mixed pass-2 pair body
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="plummer128k_ecc")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+# ------------------------------------------------------------- clocks --
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return None
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        load = [s for s in sm if s > 0.5 * max(sm)]
+        return {"sm_mhz": float(np.median(load)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------- CPU oracle --
+
+def oracle_rate(x, v, m, w, star_rows: int, hole_rows: int, seed: int = 0):
+    """Time the oracle on `star_rows` star targets (each a full sum over all
+    bodies) plus `hole_rows` rows of the hole's O(N^2) double sum, and scale
+    to interactions/s of a full evaluation (N - 1 of each kind of row)."""
+    import oracle
+    n = w.n
+    rng = np.random.default_rng(seed)
+    stars = rng.choice(np.arange(1, n), size=min(star_rows, n - 1), replace=False)
+    js = rng.choice(np.arange(1, n), size=min(hole_rows, n - 1), replace=False)
+    t0 = time.perf_counter()
+    oracle.accel_rows(x, v, m, stars, G=w.G, c=w.c, eps=w.eps)
+    t1 = time.perf_counter()
+    oracle.bh_rows(x, v, m, js, G=w.G, eps=w.eps)
+    t2 = time.perf_counter()
+    per_eval = (n - 1) * ((t1 - t0) / len(stars) + (t2 - t1) / len(js))
+    return n * (n - 1) / per_eval, t2 - t0, oracle.threads()
+
+
+def run_reference(args, w):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    x, v, m = w.state()
+    steps = args.steps if args.steps is not None else 20
+    rows = 16
+    for _ in range(args.warmup):
+        oracle_rate(x, v, m, w, rows, rows, seed=1)
+    rates, secs = [], 0.0
+    for k in range(steps):
+        r, t, cores = oracle_rate(x, v, m, w, rows, rows, seed=100 + k)
+        rates.append(r)
+        secs += t
+    value = len(rates) / sum(1.0 / r for r in rates)
+    sample = (f"each step: {rows} star rows + {rows} hole double-sum rows of the N={w.n} "
+              f"evaluation, scaled by (N-1)/rows")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "interactions/s",
+        "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * w.n * (w.n - 1) / value, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(w, "fp64", args),
+        "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": cores,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def config_of(w, precision, args):
+    return {"workload": w.name, "n_bodies": w.n, "m_bh": w.m_bh, "c": w.c, "eps": w.eps,
+            "dt": w.dt, "precision": precision, "ecc_frac": w.ecc_frac,
+            "parallelism": "replicas" if args.gpus > 1 else "single",
+            "l2": "256 MiB buffer written between timed steps"}
+
+
+# ---------------------------------------------------------------- GPU --
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("pn_kernels.cu", "pn_internal.h"):
+        with open(os.path.join(ROOT, "paper_1801_07986_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_tag: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    d = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(d):
+        return None
+    src = kernel_source_hash()
+    for f in sorted(os.listdir(d)):
+        if not f.endswith(".md"):
+            continue
+        txt = open(os.path.join(d, f)).read()
+        m1 = re.search(rf"traffic_bytes_per_launch\[{kernel_tag}\]:\s*([0-9.eE+]+)", txt)
+        m2 = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+        if m1 and m2 and m2.group(1) == src:
+            return float(m1.group(1))
+    return None
+
+
+def run_native(args, w):
+    import torch
+    from paper_1801_07986_b300 import pn
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    steps = args.steps if args.steps is not None else w.steps
+    x, v, m = w.state()
+    X = torch.tensor(x, device=dev)
+    V = torch.tensor(v, device=dev)
+    M = torch.tensor(m, device=dev)
+    A = torch.empty_like(X)
+    stream = torch.cuda.current_stream(dev)
+    ctx = pn.pn_init(w.n, G=w.G, c=w.c, eps=w.eps, precision=args.precision, device=local,
+                     stream=stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    pn.pn_accel(ctx, X, V, M, A)
+    for _ in range(args.warmup):
+        pn.pn_step(ctx, X, V, M, A, w.dt, 1)
+    pn.pn_sync(ctx)
+
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    pn.pn_set_timing(ctx, True)
+    with ClockSampler(local) as clk:
+        for k in range(steps):
+            flush.zero_()
+            ev0[k].record(stream)
+            pn.pn_step(ctx, X, V, M, A, w.dt, 1)
+            ev1[k].record(stream)
+        torch.cuda.synchronize(dev)
+    pn.pn_sync(ctx)
+    kms, klaunch = pn.pn_get_timing(ctx)
+    pn.pn_set_timing(ctx, False)
+    ms = float(sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)))
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    inter = float(w.n) * (w.n - 1) * steps * world
+    value = inter / (ms * 1e-3)
+    launch = pn.pn_get_launch(ctx)
+
+    # roofline of the dominant pair kernel (plain FP32 ALU bound)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    sms = launch["sms"]
+    peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    k_dom = int(np.argmax(kms[:2]))
+    per_launch_ms = kms[k_dom] / max(1, klaunch[k_dom])
+    pairs = float(w.n - 1) * (w.n - 2)
+    flops = (FLOPS_PASS2 if k_dom == 1 else FLOPS_PASS1) * pairs
+    achieved = flops / (per_launch_ms * 1e-3) / 1e12
+    clocks = clk.summary()
+    tag = f"pass{k_dom + 1}_{args.precision}"
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": profiled_traffic(tag), "kernel": tag,
+            "flops_per_pair": FLOPS_PASS2 if k_dom == 1 else FLOPS_PASS1,
+            "launch_ms": per_launch_ms,
+            "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz "
+                          "(sm_max_mhz of MEASURED_PEAKS.json)",
+            "kernel_ms_share": {"pass1": kms[0] / ms, "pass2": kms[1] / ms,
+                                "near": kms[2] / ms}}
+    if clocks and clocks.get("sm_mhz"):
+        roof["frac_at_sampled_clock"] = achieved / (peak * clocks["sm_mhz"] / sm_max)
+    if args.precision == "mixed":
+        roof["flops_per_interaction_both_passes"] = FLOPS_PASS1 + FLOPS_PASS2
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": ms / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "mixed" else "f64",
+        "data": "synthetic", "config": config_of(w, args.precision, args),
+        "roofline": roof, "gpu_launches": 9 * steps, "clocks": clocks,
+        "launch_shape": launch,
+    }
+
+    # end to end through the host-array entry point, copies inside the timing
+    if not args.no_e2e:
+        xh = torch.tensor(x).pin_memory().numpy()
+        vh = torch.tensor(v).pin_memory().numpy()
+        mh = torch.tensor(m).pin_memory().numpy()
+        ah = torch.empty((w.n, 3), dtype=torch.float64).pin_memory().numpy()
+        ah[:] = A.cpu().numpy()
+        e2e_steps = max(3, min(steps, 50))
+        pn.pn_step_host(ctx, xh, vh, mh, ah, w.dt, 1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for _ in range(e2e_steps):
+            flush.zero_()
+            e0.record(stream)
+            pn.pn_step_host(ctx, xh, vh, mh, ah, w.dt, 1)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        line["e2e"] = {"value": float(w.n) * (w.n - 1) * e2e_steps / (tot * 1e-3),
+                       "unit": "interactions/s", "h2d_bytes_per_step": 80 * w.n,
+                       "d2h_bytes_per_step": 72 * w.n, "steps": e2e_steps}
+
+    # the same workload on the FP64 path (a few steps) for the mixed/FP64 ratio
+    if args.precision == "mixed" and not args.no_fp64_compare:
+        c64 = pn.pn_init(w.n, G=w.G, c=w.c, eps=w.eps, precision="fp64", device=local,
+                         stream=stream)
+        X2, V2, A2 = X.clone(), V.clone(), A.clone()
+        pn.pn_step(c64, X2, V2, M, A2, w.dt, 1)
+        pn.pn_sync(c64)
+        nst = 3 if w.n > 50000 else 20
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pn.pn_step(c64, X2, V2, M, A2, w.dt, nst)
+        e1.record(stream)
+        e1.synchronize()
+        r64 = float(w.n) * (w.n - 1) * nst / (e0.elapsed_time(e1) * 1e-3)
+        line["fp64_path"] = {"value": r64, "unit": "interactions/s", "steps": nst,
+                             "mixed_over_fp64": value / world / r64}
+        c64.close()
+
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            r, secs, cores = oracle_rate(x, v, m, w, 64, 64)
+            line["cpu_baseline"] = {
+                "value": r, "unit": "interactions/s", "cores": cores, "kind": "oracle",
+                "sample": f"64 star rows + 64 hole double-sum rows of the N={w.n} evaluation "
+                          f"({secs:.1f} s), scaled by (N-1)/64"}
+        except Exception as e:  # the baseline is reported, not required
+            line["cpu_baseline"] = {"value": None, "error": str(e)[:200]}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    from paper_1801_07986_b300.inputs import WORKLOADS
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_native(args, w)
+
+
+if __name__ == "__main__":
+    main()

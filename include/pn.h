@@ -72,6 +72,12 @@ enum { PN_VPRED_END = 0, PN_VHALF = 1 };       /* pn_params.vel_mode  */
  *   vel_mode   velocity at which the force after a drift is evaluated:
  *              PN_VPRED_END  v_half + (dt/2) a_old (second order),
  *              PN_VHALF      v_half.
+ *   r_near     (>= 0) stars closer than r_near to the hole are "near"
+ *              sources: their hole-relative cross terms (Eq. 6, lines 2-4),
+ *              which are large and cancel one another, are summed in a
+ *              separate cancellation-free pair form instead of through
+ *              global sums.  The result is the same in exact arithmetic;
+ *              only rounding changes.  0 disables the split.
  */
 typedef struct {
     double G;
@@ -79,6 +85,7 @@ typedef struct {
     double eps;
     int precision;
     int vel_mode;
+    double r_near;
 } pn_params;
 
 /*
@@ -148,11 +155,11 @@ pn_status pn_sync(pn_ctx *ctx);
  * Kernel timing for measurement.  While enabled, pn_accel/pn_step record a
  * CUDA event pair on the context's stream around each pair-interaction
  * kernel launch.  pn_get_timing waits for the stream and returns, for
- * kernel k (0 = pass 1, 1 = pass 2), the summed milliseconds and launch
- * count since timing was last enabled.
+ * kernel k (0 = pass 1, 1 = pass 2, 2 = near-source pass), the summed
+ * milliseconds and launch count since timing was last enabled.
  */
 pn_status pn_set_timing(pn_ctx *ctx, int enable);
-pn_status pn_get_timing(pn_ctx *ctx, double ms[2], int64_t launches[2]);
+pn_status pn_get_timing(pn_ctx *ctx, double ms[3], int64_t launches[3]);
 
 /*
  * Launch shape of the pair kernels for this context: out[0] threads per

@@ -71,6 +71,8 @@ bool params_ok(const pn_params *p)
     if (p->vel_mode != PN_VPRED_END && p->vel_mode != PN_VHALF)
         return (void)fail(PN_EINVAL, "vel_mode must be PN_VPRED_END or PN_VHALF (got %d)",
                           p->vel_mode), false;
+    if (!(std::isfinite(p->r_near) && p->r_near >= 0.0))
+        return (void)fail(PN_EINVAL, "r_near must be finite and >= 0 (got %g)", p->r_near), false;
     return true;
 }
 
@@ -83,12 +85,13 @@ void set_params(pn_ctx *c, const pn_params *p)
 void free_all(pn_ctx *c)
 {
     void *bufs[] = {c->vp, c->mrec, c->drec, c->part, c->blk, c->glob, c->eout, c->flag,
-                    c->flag_step, c->hx, c->hv, c->hm, c->ha};
+                    c->flag_step, c->hx, c->hv, c->hm, c->ha, c->nrec, c->ndrec, c->ncount,
+                    c->nflag};
     for (void *b : bufs)
         if (b)
             cudaFree(b);
     if (c->timing_on || c->tm.ev0[0][0]) {
-        for (int k = 0; k < 2; ++k)
+        for (int k = 0; k < pn::Timing::kKernels; ++k)
             for (int r = 0; r < pn::Timing::kRing; ++r) {
                 if (c->tm.ev0[k][r])
                     cudaEventDestroy(c->tm.ev0[k][r]);
@@ -133,6 +136,7 @@ pn_status evaluate(pn_ctx *c, const double *x, const double *vel, const double *
     PN_CUDA(pn::launch_prologue(c, x, vel, m, false), "prologue launch");
     PN_CUDA(pn::launch_pass1(c), "pass-1 launch");
     PN_CUDA(pn::launch_pass2(c), "pass-2 launch");
+    PN_CUDA(pn::launch_near(c), "near-pass launch");
     PN_CUDA(pn::launch_epilogue(c, x, vel, m, a, v, h, (unsigned long long)c->step_counter),
             "epilogue launch");
     return PN_OK;
@@ -215,9 +219,11 @@ pn_status pn_init(pn_ctx **out, int64_t n, const pn_params *params, int device,
         part = part_f64;
     if (part_e > part)
         part = part_e;
+    part += (int64_t)pn::kNearVals * np;   // near-pass partials after both passes
     c->part_len = part;
     const int64_t nglue = (np + pn::kGlueThreads - 1) / pn::kGlueThreads;
     c->blk_len = nglue * pn::kGlobVals;
+    c->nnear_cap = np + pn::kNearTile;
 
     struct Req { void **p; size_t bytes; } req[] = {
         {(void **)&c->vp, sizeof(double) * 3 * (size_t)n},
@@ -226,6 +232,10 @@ pn_status pn_init(pn_ctx **out, int64_t n, const pn_params *params, int device,
         {(void **)&c->part, sizeof(double) * (size_t)part},
         {(void **)&c->blk, sizeof(double) * (size_t)c->blk_len},
         {(void **)&c->glob, sizeof(double) * 16},
+        {(void **)&c->nrec, sizeof(float4) * 4 * (size_t)c->nnear_cap},
+        {(void **)&c->ndrec, sizeof(double4_32a) * 3 * (size_t)c->nnear_cap},
+        {(void **)&c->ncount, sizeof(int) * (size_t)(1 + nglue)},
+        {(void **)&c->nflag, (size_t)np},
         {(void **)&c->eout, sizeof(double) * 8},
         {(void **)&c->flag, sizeof(int)},
         {(void **)&c->flag_step, sizeof(unsigned long long)},
@@ -379,13 +389,13 @@ pn_status pn_set_timing(pn_ctx *c, int enable)
     DeviceGuard g(c->device);
     PN_CUDA(g.err, "cudaSetDevice");
     if (enable && !c->tm.ev0[0][0]) {
-        for (int k = 0; k < 2; ++k)
+        for (int k = 0; k < pn::Timing::kKernels; ++k)
             for (int r = 0; r < pn::Timing::kRing; ++r) {
                 PN_CUDA(cudaEventCreate(&c->tm.ev0[k][r]), "cudaEventCreate");
                 PN_CUDA(cudaEventCreate(&c->tm.ev1[k][r]), "cudaEventCreate");
             }
     }
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < pn::Timing::kKernels; ++k) {
         c->tm.head[k] = c->tm.count[k] = 0;
         c->tm.ms[k] = 0.0;
         c->tm.launches[k] = 0;
@@ -394,7 +404,7 @@ pn_status pn_set_timing(pn_ctx *c, int enable)
     return ok();
 }
 
-pn_status pn_get_timing(pn_ctx *c, double ms[2], int64_t launches[2])
+pn_status pn_get_timing(pn_ctx *c, double ms[3], int64_t launches[3])
 {
     if (check_ctx(c) != PN_OK)
         return PN_EINVAL;
@@ -403,7 +413,7 @@ pn_status pn_get_timing(pn_ctx *c, double ms[2], int64_t launches[2])
     DeviceGuard g(c->device);
     PN_CUDA(g.err, "cudaSetDevice");
     PN_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < pn::Timing::kKernels; ++k) {
         pn::Timing &t = c->tm;
         while (t.count[k] > 0) {
             const int old = t.head[k];

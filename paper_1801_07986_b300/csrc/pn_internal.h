@@ -26,8 +26,13 @@ constexpr int kGlueThreads = 256;
 constexpr int kP1Vals = 5;         // N (3), U, Y
 constexpr int kP2Vals = 9;         // V (3), H (3), E (3)
 constexpr int kEVals = 8;          // pot, Smv (3), Snn, Spx (3)
-// Global O(n) sums computed by the prologue.
-constexpr int kGlobVals = 10;      // Q (3), W (3), SA, SB, Phi, spare
+// Near-source pass: sources per tile and values per target.
+constexpr int kNearTile = 128;
+constexpr int kNearVals = 6;       // P (3), Ee (3)
+// Global O(n) sums computed by the prologue (block partials, then totals):
+//   Q (3), W over all stars (3), W over far stars (3), SA_far, SB_far, Phi,
+//   near-star count (as a double in the block partials).
+constexpr int kGlobVals = 13;
 // Per-block values of the energy epilogue.
 constexpr int kEBlockVals = 9;     // eN, ePN, pN (3), pPN (3), sum m/R
 
@@ -42,10 +47,11 @@ struct Shape {
 
 struct Timing {
     static constexpr int kRing = 64;
-    cudaEvent_t ev0[2][kRing], ev1[2][kRing];
-    int head[2], count[2];
-    double ms[2];
-    int64_t launches[2];
+    static constexpr int kKernels = 3;   // pass 1, pass 2, near pass
+    cudaEvent_t ev0[kKernels][kRing], ev1[kKernels][kRing];
+    int head[kKernels], count[kKernels];
+    double ms[kKernels];
+    int64_t launches[kKernels];
 };
 
 }  // namespace pn
@@ -67,7 +73,12 @@ struct pn_ctx {
     int64_t part_len;    // doubles in `part`
     double *blk;         // per-block partial sums of the O(n) kernels
     int64_t blk_len;
-    double *glob;        // global sums
+    double *glob;        // global sums (kGlobVals doubles)
+    float4 *nrec;        // mixed near-source records: 4 arrays of ns_pad + kNearTile
+    double4_32a *ndrec;  // double near-source records: 4 arrays of ns_pad + kNearTile
+    int *ncount;         // [0] near-star count; [1 + b] prefix offset of prologue block b
+    unsigned char *nflag;   // per star slot: 1 if a near source
+    int64_t nnear_cap;   // entries per near-record array
     double *eout;        // 8 doubles: energy / momentum result
     int *flag;           // [0] non-finite flag
     unsigned long long *flag_step;   // first step index with a non-finite value
@@ -89,6 +100,7 @@ cudaError_t launch_prologue(pn_ctx *c, const double *x, const double *vel, const
                             bool energy_records);
 cudaError_t launch_pass1(pn_ctx *c);
 cudaError_t launch_pass2(pn_ctx *c);
+cudaError_t launch_near(pn_ctx *c);
 cudaError_t launch_epilogue(pn_ctx *c, const double *x, const double *vel, const double *m,
                             double *a, double *v, double half_dt, unsigned long long step);
 cudaError_t launch_energy(pn_ctx *c, const double *x, const double *v, const double *m);

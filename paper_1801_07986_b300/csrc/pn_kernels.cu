@@ -118,9 +118,13 @@ __global__ void k_kick_drift(int64_t n3, double *__restrict__ x, double *__restr
 // Per star slot t (star j = t + 1; slots >= ns are padding with zero mass):
 //   d_j = x_j - x_hole, R_j = |d_j|,
 //   c_j = G M (3/(2 R_j) + eps^2/(4 R_j^3)),   e_j = G M d_j/(2 R_j^3),
-//   w_j = m_j d_j / R_j^3,
-// and the global sums Q = sum m_j v_j, W = sum w_j, SA = sum 5 m_j/(4 R_j),
-// SB = sum m_j (R_j^2 + eps^2)/(4 R_j^3), Phi = sum m_j / R_j.
+//   w_j = m_j d_j / R_j^3.
+// A star with R_j < r_near is a near source: its c_j, e_j and w_j are left
+// out of the main records and of the far sums below (the near pass sums its
+// hole-relative cross terms pair by pair instead).  Global sums:
+//   Q = sum m_j v_j, W = sum w_j (all), W_far = sum_far w_j,
+//   SA_far = sum_far 5 m_j/(4 R_j), SB_far = sum_far m_j (R_j^2 + eps^2)/(4 R_j^3),
+//   Phi = sum m_j / R_j, and the number of near stars.
 // Records: mixed  A = (hi(d), m) B = (lo(d), c) C = (v, 0) D = (e, 0) E = (w, 0)
 //          double A = (d, m)     B = (v, c)     C = (e, 0) D = (w, 0)
 // Energy records (double): A = (d, m), B = (v, 0).
@@ -128,7 +132,8 @@ template <int MODE>   // 0 mixed, 1 double, 2 energy
 __global__ void __launch_bounds__(kGlueThreads)
 k_prologue(int64_t ns, int64_t ns_pad, const double *__restrict__ x,
            const double *__restrict__ vel, const double *__restrict__ m, double G,
-           double eps2, float4 *__restrict__ mrec, double4_32a *__restrict__ drec,
+           double eps2, double r_near, float4 *__restrict__ mrec,
+           double4_32a *__restrict__ drec, unsigned char *__restrict__ nflag,
            double *__restrict__ blk)
 {
     __shared__ double sh[kGlobVals][kGlueThreads];
@@ -148,8 +153,10 @@ k_prologue(int64_t ns, int64_t ns_pad, const double *__restrict__ x,
             const double mj = m[j];
             const double M = m[0];
             const double v0 = vel[3 * j], v1 = vel[3 * j + 1], v2 = vel[3 * j + 2];
-            const double cj = G * M * (1.5 * iR + 0.25 * eps2 * iR3);
-            const double ef = 0.5 * G * M * iR3;
+            const bool near = MODE != 2 && R < r_near;
+            const double far = near ? 0.0 : 1.0;
+            const double cj = far * G * M * (1.5 * iR + 0.25 * eps2 * iR3);
+            const double ef = far * 0.5 * G * M * iR3;
             const double wf = mj * iR3;
             if (MODE == 0) {
                 const float h0 = (float)d0, h1 = (float)d1, h2 = (float)d2;
@@ -159,26 +166,33 @@ k_prologue(int64_t ns, int64_t ns_pad, const double *__restrict__ x,
                 mrec[2 * ns_pad + t] = make_float4((float)v0, (float)v1, (float)v2, 0.0f);
                 mrec[3 * ns_pad + t] =
                     make_float4((float)(ef * d0), (float)(ef * d1), (float)(ef * d2), 0.0f);
-                mrec[4 * ns_pad + t] =
-                    make_float4((float)(wf * d0), (float)(wf * d1), (float)(wf * d2), 0.0f);
+                mrec[4 * ns_pad + t] = make_float4((float)(far * wf * d0), (float)(far * wf * d1),
+                                                   (float)(far * wf * d2), 0.0f);
             } else if (MODE == 1) {
                 drec[t] = make_double4_32a(d0, d1, d2, mj);
                 drec[ns_pad + t] = make_double4_32a(v0, v1, v2, cj);
                 drec[2 * ns_pad + t] = make_double4_32a(ef * d0, ef * d1, ef * d2, 0.0);
-                drec[3 * ns_pad + t] = make_double4_32a(wf * d0, wf * d1, wf * d2, 0.0);
+                drec[3 * ns_pad + t] =
+                    make_double4_32a(far * wf * d0, far * wf * d1, far * wf * d2, 0.0);
             } else {
                 drec[t] = make_double4_32a(d0, d1, d2, mj);
                 drec[ns_pad + t] = make_double4_32a(v0, v1, v2, 0.0);
             }
+            if (MODE != 2)
+                nflag[t] = near ? 1 : 0;
             g[0] = mj * v0;
             g[1] = mj * v1;
             g[2] = mj * v2;
             g[3] = wf * d0;
             g[4] = wf * d1;
             g[5] = wf * d2;
-            g[6] = 1.25 * mj * iR;
-            g[7] = 0.25 * mj * (R2 + eps2) * iR3;
-            g[8] = mj * iR;
+            g[6] = far * wf * d0;
+            g[7] = far * wf * d1;
+            g[8] = far * wf * d2;
+            g[9] = far * 1.25 * mj * iR;
+            g[10] = far * 0.25 * mj * (R2 + eps2) * iR3;
+            g[11] = mj * iR;
+            g[12] = near ? 1.0 : 0.0;
         } else {
             // padding: zero mass far away, distinct positions
             const double px = 1.0e4 + (double)(t - ns);
@@ -192,6 +206,8 @@ k_prologue(int64_t ns, int64_t ns_pad, const double *__restrict__ x,
                 for (int k = 1; k < nk; ++k)
                     drec[k * ns_pad + t] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
             }
+            if (MODE != 2)
+                nflag[t] = 0;
         }
     }
     if (MODE == 2)
@@ -201,13 +217,108 @@ k_prologue(int64_t ns, int64_t ns_pad, const double *__restrict__ x,
         blk[(int64_t)blockIdx.x * kGlobVals + threadIdx.x] = sh[threadIdx.x][0];
 }
 
+// Totals of the prologue's block sums (fixed order), the exclusive prefix
+// of the per-block near-star counts (ncount[1 + b]), their total
+// (ncount[0]), and zero-mass padding of the near-record arrays up to the
+// next multiple of kNearTile.
+template <int MODE>   // 0 mixed, 1 double
 __global__ void __launch_bounds__(kGlueThreads)
-k_global_sums(const double *__restrict__ blk, int64_t nblk, double *__restrict__ glob)
+k_global_sums(const double *__restrict__ blk, int64_t nblk, double *__restrict__ glob,
+              int *__restrict__ ncount, float4 *__restrict__ nrec,
+              double4_32a *__restrict__ ndrec, int64_t ncap)
 {
     __shared__ double sh[kGlobVals][kGlueThreads];
+    __shared__ int scan[kGlueThreads];
     sum_blocks<kGlobVals>(blk, nblk, sh);
     if (threadIdx.x < kGlobVals)
         glob[threadIdx.x] = sh[threadIdx.x][0];
+    // exclusive prefix of block counts: each thread owns a contiguous chunk
+    const int64_t chunk = (nblk + kGlueThreads - 1) / kGlueThreads;
+    const int64_t b0 = threadIdx.x * chunk;
+    const int64_t b1 = b0 + chunk < nblk ? b0 + chunk : nblk;
+    int local = 0;
+    for (int64_t b = b0; b < b1; ++b)
+        local += (int)blk[b * kGlobVals + 12];
+    scan[threadIdx.x] = local;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int k = 0; k < kGlueThreads; ++k) {
+            const int c = scan[k];
+            scan[k] = run;
+            run += c;
+        }
+        ncount[0] = run;
+    }
+    __syncthreads();
+    int run = scan[threadIdx.x];
+    for (int64_t b = b0; b < b1; ++b) {
+        ncount[1 + b] = run;
+        run += (int)blk[b * kGlobVals + 12];
+    }
+    __syncthreads();
+    const int nn = ncount[0];
+    const int npad = (int)((nn + kNearTile - 1) / kNearTile * kNearTile);
+    for (int q = nn + threadIdx.x; q < npad && q < ncap; q += kGlueThreads) {
+        const double px = 1.0e4 + (double)(q - nn);
+        if (MODE == 0) {
+            nrec[q] = make_float4((float)px, 0.0f, 0.0f, 0.0f);
+            nrec[ncap + q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            nrec[2 * ncap + q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            nrec[3 * ncap + q] = make_float4(1.0f, __int_as_float(-1), 0.0f, 0.0f);
+        } else {
+            ndrec[q] = make_double4_32a(px, 0.0, 0.0, 0.0);
+            ndrec[ncap + q] = make_double4_32a(0.0, 0.0, 1.0, -1.0);
+            ndrec[2 * ncap + q] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+        }
+    }
+}
+
+// Near-source records in slot order (deterministic block scan of the flags):
+//   mixed  NA = (hi(d), m)  NB = (lo(d), 5/(4R))  NC = (w, 1/(4R^3))
+//          ND = (R^2 + eps^2, slot bits, 0, 0)
+//   double NA = (d, m)  NB = (5/(4R), 1/(4R^3), R^2 + eps^2, slot)  NC = (w, 0)
+template <int MODE>
+__global__ void __launch_bounds__(kGlueThreads)
+k_near_scatter(int64_t ns, const double *__restrict__ x, const double *__restrict__ m,
+               double eps2, const unsigned char *__restrict__ nflag,
+               const int *__restrict__ ncount, float4 *__restrict__ nrec,
+               double4_32a *__restrict__ ndrec, int64_t ncap)
+{
+    __shared__ int wsum[kGlueThreads / 32];
+    const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
+    const bool near = t < ns && nflag[t];
+    const unsigned mask = __ballot_sync(0xffffffffu, near);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+        wsum[warp] = __popc(mask);
+    __syncthreads();
+    int before = 0;
+    for (int k = 0; k < warp; ++k)
+        before += wsum[k];
+    if (!near)
+        return;
+    const int64_t pos = ncount[1 + blockIdx.x] + before + __popc(mask & ((1u << lane) - 1u));
+    const int64_t j = t + 1;
+    const double d0 = x[3 * j] - x[0], d1 = x[3 * j + 1] - x[1], d2 = x[3 * j + 2] - x[2];
+    const double R2 = d0 * d0 + d1 * d1 + d2 * d2;
+    const double R = sqrt(R2);
+    const double iR = 1.0 / R;
+    const double iR3 = iR * iR * iR;
+    const double mj = m[j];
+    const double A = 1.25 * iR, B = 0.25 * iR3, w = mj * iR3;
+    if (MODE == 0) {
+        const float h0 = (float)d0, h1 = (float)d1, h2 = (float)d2;
+        nrec[pos] = make_float4(h0, h1, h2, (float)mj);
+        nrec[ncap + pos] = make_float4((float)(d0 - (double)h0), (float)(d1 - (double)h1),
+                                       (float)(d2 - (double)h2), (float)A);
+        nrec[2 * ncap + pos] = make_float4((float)(w * d0), (float)(w * d1), (float)(w * d2), (float)B);
+        nrec[3 * ncap + pos] = make_float4((float)(R2 + eps2), __int_as_float((int)t), 0.0f, 0.0f);
+    } else {
+        ndrec[pos] = make_double4_32a(d0, d1, d2, mj);
+        ndrec[ncap + pos] = make_double4_32a(A, B, R2 + eps2, (double)t);
+        ndrec[2 * ncap + pos] = make_double4_32a(w * d0, w * d1, w * d2, 0.0);
+    }
 }
 
 // ------------------------------------------------- pair kernels: mixed --
@@ -576,6 +687,167 @@ k_energy_pairs(const double4_32a *__restrict__ rec, int64_t ns_pad, int ntiles, 
         part[((int64_t)blockIdx.y * kEVals + k) * ns_pad + ti] = acc[k];
 }
 
+// ------------------------------------------------------- near sources --
+
+// Eq. 6 lines 2-4 for a near source j (R_j < r_near), pair by pair in a
+// form free of cancellation.  With q = R_i^2 - r_ij^2 = 2 d_i.d_j - R_j^2 - eps^2,
+// A_j = 5/(4 R_j), B_j = 1/(4 R_j^3), s = r_ij:
+//   line 2 + line 3 without their 4/r_ij and 4/R_i parts (those stay in
+//   pass 1's U_i and N_i) = G^2 M m_j [A_j (d_i/R_i^3 + x_ij/s^3)
+//                                      + B_j q (d_i (1/R_i^3 - 1/s^3) + d_j/s^3)]
+//   line 4 = -7/2 G^2 M w_j (1/s - 1/R_i),
+// with 1/s - 1/R_i = q / (s R_i (R_i + s)) and
+// 1/R_i^3 - 1/s^3 = -(1/s - 1/R_i)(1/R_i^2 + 1/(R_i s) + 1/s^2).
+// Accumulators: P (3) = sum m_j [...], Ee (3) = sum w_j (1/s - 1/R_i).
+template <typename R_t>
+struct NearMath {
+    __device__ __forceinline__ static void pair(R_t dx, R_t dy, R_t dz, R_t s2, R_t is,
+                                                const R_t (&di)[3], const R_t (&dj)[3],
+                                                R_t Ri, R_t iR, R_t iR3, R_t mj, R_t A, R_t B,
+                                                R_t Rj2e, R_t wx, R_t wy, R_t wz,
+                                                R_t (&acc)[kNearVals])
+    {
+        const R_t is2 = is * is;
+        const R_t is3 = is2 * is;
+        const R_t sd = s2 * is;                                  // s
+        const R_t q = (R_t)2 * (dj[0] * di[0] + dj[1] * di[1] + dj[2] * di[2]) - Rj2e;
+        const R_t dis = q * is * iR / (Ri + sd);                 // 1/s - 1/R_i
+        const R_t d3 = -dis * (iR * iR + iR * is + is2);         // 1/R_i^3 - 1/s^3
+        const R_t ca = mj * A;
+        const R_t cb = mj * B * q;
+        acc[0] += ca * (di[0] * iR3 + dx * is3) + cb * (di[0] * d3 + dj[0] * is3);
+        acc[1] += ca * (di[1] * iR3 + dy * is3) + cb * (di[1] * d3 + dj[1] * is3);
+        acc[2] += ca * (di[2] * iR3 + dz * is3) + cb * (di[2] * d3 + dj[2] * is3);
+        acc[3] += wx * dis;
+        acc[4] += wy * dis;
+        acc[5] += wz * dis;
+    }
+};
+
+__global__ void __launch_bounds__(kMixThreads)
+k_near_mixed(const float4 *__restrict__ rec, const float4 *__restrict__ nrec,
+             const int *__restrict__ ncount, int64_t ns_pad, int64_t ncap, float eps2,
+             double *__restrict__ part)
+{
+    constexpr int TI = kMixThreads * kMixTargets;
+    __shared__ float4 sh[4][kNearTile];
+    const int64_t t0 = (int64_t)blockIdx.x * TI;
+    const int nn = ncount[0];
+    const int ntiles = (nn + kNearTile - 1) / kNearTile;
+    float hx[kMixTargets][3], lx[kMixTargets][3], Ri[kMixTargets], iR[kMixTargets],
+        iR3[kMixTargets];
+    int ti[kMixTargets];
+    float hi[kMixTargets][kNearVals], lo[kMixTargets][kNearVals];
+#pragma unroll
+    for (int p = 0; p < kMixTargets; ++p) {
+        ti[p] = (int)(t0 + p * kMixThreads + threadIdx.x);
+        const float4 A = rec[ti[p]];
+        const float4 B = rec[ns_pad + ti[p]];
+        hx[p][0] = A.x; hx[p][1] = A.y; hx[p][2] = A.z;
+        lx[p][0] = B.x; lx[p][1] = B.y; lx[p][2] = B.z;
+        Ri[p] = sqrtf(A.x * A.x + A.y * A.y + A.z * A.z);
+        iR[p] = 1.0f / Ri[p];
+        iR3[p] = iR[p] * iR[p] * iR[p];
+#pragma unroll
+        for (int k = 0; k < kNearVals; ++k)
+            hi[p][k] = lo[p][k] = 0.0f;
+    }
+    for (int tile = 0; tile < ntiles; ++tile) {
+        const int64_t j0 = (int64_t)tile * kNearTile;
+        __syncthreads();
+        for (int q = threadIdx.x; q < kNearTile; q += kMixThreads) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                sh[k][q] = nrec[k * ncap + j0 + q];
+        }
+        __syncthreads();
+        float acc[kMixTargets][kNearVals];
+#pragma unroll
+        for (int p = 0; p < kMixTargets; ++p)
+#pragma unroll
+            for (int k = 0; k < kNearVals; ++k)
+                acc[p][k] = 0.0f;
+#pragma unroll 1
+        for (int q = 0; q < kNearTile; ++q) {
+            const float4 A = sh[0][q], B = sh[1][q], C = sh[2][q], D = sh[3][q];
+            const float dj[3] = {A.x, A.y, A.z};
+#pragma unroll
+            for (int p = 0; p < kMixTargets; ++p) {
+                const float dx = (hx[p][0] - A.x) + (lx[p][0] - B.x);
+                const float dy = (hx[p][1] - A.y) + (lx[p][1] - B.y);
+                const float dz = (hx[p][2] - A.z) + (lx[p][2] - B.z);
+                float s2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+                const bool self = __float_as_int(D.y) == ti[p];
+                s2 = self ? 1.0f : s2;
+                const float mj = self ? 0.0f : A.w;
+                const float wx = self ? 0.0f : C.x, wy = self ? 0.0f : C.y, wz = self ? 0.0f : C.z;
+                const float is = rsqrtf(s2);
+                NearMath<float>::pair(dx, dy, dz, s2, is, hx[p], dj, Ri[p], iR[p], iR3[p], mj,
+                                      B.w, C.w, D.x, wx, wy, wz, acc[p]);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < kMixTargets; ++p)
+#pragma unroll
+            for (int k = 0; k < kNearVals; ++k)
+                ds_add(hi[p][k], lo[p][k], acc[p][k]);
+    }
+#pragma unroll
+    for (int p = 0; p < kMixTargets; ++p)
+#pragma unroll
+        for (int k = 0; k < kNearVals; ++k)
+            part[(int64_t)k * ns_pad + ti[p]] = (double)hi[p][k] + (double)lo[p][k];
+}
+
+__global__ void __launch_bounds__(kF64Threads)
+k_near_f64(const double4_32a *__restrict__ rec, const double4_32a *__restrict__ nrec,
+           const int *__restrict__ ncount, int64_t ns_pad, int64_t ncap, double eps2,
+           double *__restrict__ part)
+{
+    constexpr int TILE = kNearTile / 2;
+    __shared__ double4_32a sh[3][TILE];
+    const int64_t t0 = (int64_t)blockIdx.x * kF64Threads;
+    const int ti = (int)(t0 + threadIdx.x);
+    const int nn = ncount[0];
+    const int ntiles = (nn + TILE - 1) / TILE;
+    const double4_32a Ta = rec[ti];
+    const double di[3] = {Ta.x, Ta.y, Ta.z};
+    const double Ri = sqrt(di[0] * di[0] + di[1] * di[1] + di[2] * di[2]);
+    const double iR = 1.0 / Ri;
+    const double iR3 = iR * iR * iR;
+    double acc[kNearVals];
+#pragma unroll
+    for (int k = 0; k < kNearVals; ++k)
+        acc[k] = 0.0;
+    for (int tile = 0; tile < ntiles; ++tile) {
+        const int64_t j0 = (int64_t)tile * TILE;
+        __syncthreads();
+        for (int q = threadIdx.x; q < TILE; q += kF64Threads) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                sh[k][q] = nrec[k * ncap + j0 + q];
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int q = 0; q < TILE; ++q) {
+            const double4_32a A = sh[0][q], B = sh[1][q], C = sh[2][q];
+            const double dj[3] = {A.x, A.y, A.z};
+            const double dx = di[0] - A.x, dy = di[1] - A.y, dz = di[2] - A.z;
+            double s2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
+            const bool self = (int)B.w == ti;
+            s2 = self ? 1.0 : s2;
+            const double mj = self ? 0.0 : A.w;
+            const double wx = self ? 0.0 : C.x, wy = self ? 0.0 : C.y, wz = self ? 0.0 : C.z;
+            const double is = rsqrt_f64(s2);
+            NearMath<double>::pair(dx, dy, dz, s2, is, di, dj, Ri, iR, iR3, mj, B.x, B.y, B.z,
+                                   wx, wy, wz, acc);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kNearVals; ++k)
+        part[(int64_t)k * ns_pad + ti] = acc[k];
+}
+
 // ------------------------------------------------------------ epilogue --
 
 // Star i = t + 1 (double precision throughout), velocities v = those at
@@ -585,13 +857,16 @@ k_energy_pairs(const double4_32a *__restrict__ rec, int64_t ns_pad, int ntiles, 
 //     + 5 G^2 m_i M d_i/R_i^4                                          [Eq. 6 l.1]
 //     + G^2 M d_i/R_i^3 S_i                                            [Eq. 6 l.2]
 //     + G [V_i + (4 G M/R_i + v_i^2) N_i]                              [l.3 + l.6]
-//     - 7/2 G^2 M [E_i - (W - w_i)/R_i]                                [l.4]
+//     - 7/2 G^2 M [E_i - (W_far - w_i)/R_i]                            [l.4]
 //     - G/R_i^3 [4 (v_i.Q) d_i - 3 (Q.d_i) v_i - 4 (v_i.d_i) Q]        [l.1 + l.5]
-//     + G H_i }                                                        [l.7]
-// with S_i = sum_{j!=i} m_j (4/r_ij + 5/(4R_j) + (R_i^2 - r_ij^2)/(4R_j^3))
-//          = 4 U_i + (SA - 5 m_i/(4R_i)) + d_i.(W - w_i)/2
-//            - (SB - m_i (R_i^2 + eps^2)/(4 R_i^3))
-// (R_i^2 - r_ij^2 = 2 d_i.d_j - R_j^2 - eps^2).  Line 1's self term and
+//     + G H_i                                                          [l.7]
+//     + G^2 M (P_i - 7/2 Ee_i) }                                       [near sources]
+// with, over far sources j != i,
+//   S_i = 4 U_i + sum_far m_j (5/(4R_j) + (R_i^2 - r_ij^2)/(4R_j^3))
+//       = 4 U_i + (SA_far - 5 m_i/(4R_i)) + d_i.(W_far - w_i)/2
+//         - (SB_far - m_i (R_i^2 + eps^2)/(4 R_i^3))
+// (R_i^2 - r_ij^2 = 2 d_i.d_j - R_j^2 - eps^2; the m_i / w_i self terms are
+// removed only when star i is itself a far source).  Line 1's self term and
 // line 5 together are the k-sum over all stars, hence Q.
 //
 // The same thread also forms star i's term of the hole's 1PN acceleration
@@ -606,6 +881,7 @@ __global__ void __launch_bounds__(kGlueThreads)
 k_epilogue(int64_t ns, int64_t ns_pad, const double *__restrict__ x,
            const double *__restrict__ vel, const double *__restrict__ m,
            const double *__restrict__ p1, int js1, const double *__restrict__ p2, int js2,
+           const double *__restrict__ pnear, const unsigned char *__restrict__ nflag,
            const double *__restrict__ glob, double G, double inv_c2, double eps2,
            double *__restrict__ a, double *__restrict__ v, double h, int *flag,
            unsigned long long *flag_step, unsigned long long step, double *__restrict__ blk)
@@ -625,7 +901,7 @@ k_epilogue(int64_t ns, int64_t ns_pad, const double *__restrict__ x,
         const double vv[3] = {vel[3 * i], vel[3 * i + 1], vel[3 * i + 2]};
         const double v2 = vv[0] * vv[0] + vv[1] * vv[1] + vv[2] * vv[2];
         const double vd = vv[0] * d[0] + vv[1] * d[1] + vv[2] * d[2];
-        double s1[kP1Vals], s2[kP2Vals];
+        double s1[kP1Vals], s2[kP2Vals], sn[kNearVals];
         for (int k = 0; k < kP1Vals; ++k) {
             double acc = 0.0;
             for (int s = 0; s < js1; ++s)
@@ -638,18 +914,21 @@ k_epilogue(int64_t ns, int64_t ns_pad, const double *__restrict__ x,
                 acc += p2[((int64_t)s * kP2Vals + k) * ns_pad + t];
             s2[k] = acc;
         }
+        for (int k = 0; k < kNearVals; ++k)
+            sn[k] = pnear ? pnear[(int64_t)k * ns_pad + t] : 0.0;
+        const double fi = nflag[t] ? 0.0 : 1.0;   // 1 if star i is a far source
         const double N[3] = {s1[0], s1[1], s1[2]};
         const double U = s1[3], Y = s1[4];
         const double Q[3] = {glob[0], glob[1], glob[2]};
-        const double W[3] = {glob[3], glob[4], glob[5]};
-        const double SA = glob[6], SB = glob[7], Phi = glob[8];
+        const double Wf[3] = {glob[6], glob[7], glob[8]};
+        const double SA = glob[9], SB = glob[10], Phi = glob[11];
         const double wi[3] = {mi * iR3 * d[0], mi * iR3 * d[1], mi * iR3 * d[2]};
-        const double Wx[3] = {W[0] - wi[0], W[1] - wi[1], W[2] - wi[2]};
+        const double Wx[3] = {Wf[0] - fi * wi[0], Wf[1] - fi * wi[1], Wf[2] - fi * wi[2]};
         const double vQ = vv[0] * Q[0] + vv[1] * Q[1] + vv[2] * Q[2];
         const double Qd = Q[0] * d[0] + Q[1] * d[1] + Q[2] * d[2];
-        const double S = 4.0 * U + (SA - 1.25 * mi * iR) +
+        const double S = 4.0 * U + (SA - fi * 1.25 * mi * iR) +
                          0.5 * (d[0] * Wx[0] + d[1] * Wx[1] + d[2] * Wx[2]) -
-                         (SB - 0.25 * mi * (R2 + eps2) * iR3);
+                         (SB - fi * 0.25 * mi * (R2 + eps2) * iR3);
         const double cd = GM * iR3 * (4.0 * GM * iR - v2) + 5.0 * G * GM * mi * iR3 * iR +
                           G * GM * iR3 * S - 4.0 * G * iR3 * vQ;
         const double cv = 4.0 * GM * iR3 * vd + 3.0 * G * iR3 * Qd;
@@ -659,7 +938,8 @@ k_epilogue(int64_t ns, int64_t ns_pad, const double *__restrict__ x,
         double ai[3];
         for (int k = 0; k < 3; ++k) {
             const double pn = cd * d[k] + cv * vv[k] + G * s2[k] + cN * N[k] -
-                              c7 * (s2[6 + k] - Wx[k] * iR) + cQ * Q[k] + G * s2[3 + k];
+                              c7 * (s2[6 + k] - Wx[k] * iR) + cQ * Q[k] + G * s2[3 + k] +
+                              G * GM * (sn[k] - 3.5 * sn[3 + k]);
             ai[k] = (-GM * iR3 * d[k] - G * N[k]) + inv_c2 * pn;
         }
         // hole's term from this star
@@ -806,21 +1086,36 @@ cudaError_t launch_prologue(pn_ctx *c, const double *x, const double *vel, const
 {
     const int64_t nb = glue_blocks(c->ns_pad);
     const double eps2 = c->p.eps * c->p.eps;
+    const double r_near = c->p.r_near > 0.0 ? c->p.r_near : -1.0;
     if (energy_records) {
         k_prologue<2><<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
-            c->ns, c->ns_pad, x, vel, m, c->p.G, eps2, c->mrec, c->drec, c->blk);
+            c->ns, c->ns_pad, x, vel, m, c->p.G, eps2, r_near, c->mrec, c->drec, c->nflag, c->blk);
         return cudaGetLastError();
     }
-    if (c->p.precision == PN_MIXED)
+    const bool mixed = c->p.precision == PN_MIXED;
+    if (mixed)
         k_prologue<0><<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
-            c->ns, c->ns_pad, x, vel, m, c->p.G, eps2, c->mrec, c->drec, c->blk);
+            c->ns, c->ns_pad, x, vel, m, c->p.G, eps2, r_near, c->mrec, c->drec, c->nflag, c->blk);
     else
         k_prologue<1><<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
-            c->ns, c->ns_pad, x, vel, m, c->p.G, eps2, c->mrec, c->drec, c->blk);
+            c->ns, c->ns_pad, x, vel, m, c->p.G, eps2, r_near, c->mrec, c->drec, c->nflag, c->blk);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
-    k_global_sums<<<1, kGlueThreads, 0, c->stream>>>(c->blk, nb, c->glob);
+    if (mixed)
+        k_global_sums<0><<<1, kGlueThreads, 0, c->stream>>>(c->blk, nb, c->glob, c->ncount,
+                                                            c->nrec, c->ndrec, c->nnear_cap);
+    else
+        k_global_sums<1><<<1, kGlueThreads, 0, c->stream>>>(c->blk, nb, c->glob, c->ncount,
+                                                            c->nrec, c->ndrec, c->nnear_cap);
+    if ((e = cudaGetLastError()) != cudaSuccess || r_near < 0.0)
+        return e;
+    if (mixed)
+        k_near_scatter<0><<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
+            c->ns, x, m, eps2, c->nflag, c->ncount, c->nrec, c->ndrec, c->nnear_cap);
+    else
+        k_near_scatter<1><<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
+            c->ns, x, m, eps2, c->nflag, c->ncount, c->nrec, c->ndrec, c->nnear_cap);
     return cudaGetLastError();
 }
 
@@ -854,6 +1149,32 @@ static int64_t p2_offset(pn_ctx *c)
     return (int64_t)s.jsplit * kP1Vals * c->ns_pad;
 }
 
+static int64_t near_offset(pn_ctx *c)
+{
+    const Shape &s = c->p.precision == PN_MIXED ? c->mix : c->f64;
+    return (int64_t)s.jsplit * (kP1Vals + kP2Vals) * c->ns_pad;
+}
+
+cudaError_t launch_near(pn_ctx *c)
+{
+    if (!(c->p.r_near > 0.0))
+        return cudaSuccess;
+    const double eps2 = c->p.eps * c->p.eps;
+    double *pn = c->part + near_offset(c);
+    cudaEvent_t end = nullptr;
+    timing_begin(c, 2, &end);
+    if (c->p.precision == PN_MIXED)
+        k_near_mixed<<<(unsigned)c->mix.nblk_i, kMixThreads, 0, c->stream>>>(
+            c->mrec, c->nrec, c->ncount, c->ns_pad, c->nnear_cap, (float)eps2, pn);
+    else
+        k_near_f64<<<(unsigned)c->f64.nblk_i, kF64Threads, 0, c->stream>>>(
+            c->drec, c->ndrec, c->ncount, c->ns_pad, c->nnear_cap, eps2, pn);
+    cudaError_t e = cudaGetLastError();
+    if (end)
+        cudaEventRecord(end, c->stream);
+    return e;
+}
+
 cudaError_t launch_pass2(pn_ctx *c)
 {
     const double eps2 = c->p.eps * c->p.eps;
@@ -883,9 +1204,10 @@ cudaError_t launch_epilogue(pn_ctx *c, const double *x, const double *vel, const
     const Shape &s = c->p.precision == PN_MIXED ? c->mix : c->f64;
     const int64_t nb = glue_blocks(c->ns_pad);
     const double eps2 = c->p.eps * c->p.eps;
+    const double *pnear = c->p.r_near > 0.0 ? c->part + near_offset(c) : nullptr;
     k_epilogue<<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
-        c->ns, c->ns_pad, x, vel, m, c->part, s.jsplit, c->part + p2_offset(c), s.jsplit,
-        c->glob, c->p.G, c->inv_c2, eps2, a, v, h, c->flag, c->flag_step, step, c->blk);
+        c->ns, c->ns_pad, x, vel, m, c->part, s.jsplit, c->part + p2_offset(c), s.jsplit, pnear,
+        c->nflag, c->glob, c->p.G, c->inv_c2, eps2, a, v, h, c->flag, c->flag_step, step, c->blk);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;

@@ -42,7 +42,13 @@ class PNError(RuntimeError):
 
 class _Params(ctypes.Structure):
     _fields_ = [("G", ctypes.c_double), ("c", ctypes.c_double), ("eps", ctypes.c_double),
-                ("precision", ctypes.c_int), ("vel_mode", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("vel_mode", ctypes.c_int),
+                ("r_near", ctypes.c_double)]
+
+
+# Default radius (in the state's length unit) inside which stars are summed
+# as near sources of the hole-relative cross terms; see pn_params.r_near.
+R_NEAR_DEFAULT = 0.05
 
 
 _lock = threading.Lock()
@@ -103,12 +109,13 @@ def pn_version() -> int:
     return int(_load().pn_version())
 
 
-def _params(G, c, eps, precision, vel_mode) -> _Params:
+def _params(G, c, eps, precision, vel_mode, r_near=R_NEAR_DEFAULT) -> _Params:
     if precision not in _PRECISION:
         raise ValueError(f"precision must be 'fp64' or 'mixed', got {precision!r}")
     if vel_mode not in _VEL_MODE:
         raise ValueError(f"vel_mode must be 'vpred_end' or 'vhalf', got {vel_mode!r}")
-    return _Params(float(G), float(c), float(eps), _PRECISION[precision], _VEL_MODE[vel_mode])
+    return _Params(float(G), float(c), float(eps), _PRECISION[precision], _VEL_MODE[vel_mode],
+                   float(r_near))
 
 
 class Context:
@@ -147,26 +154,28 @@ def _torch_stream(device, stream):
 
 def pn_init(n: int, G: float = 1.0, c: float = math.inf, eps: float = 0.0,
             precision="mixed", vel_mode="vpred_end", device: int | None = None,
-            stream=None) -> Context:
+            stream=None, r_near: float = R_NEAR_DEFAULT) -> Context:
     """Create a context for n bodies (body 0 = the hole)."""
     lib = _load()
     if device is None:
         import torch
         device = torch.cuda.current_device()
-    p = _params(G, c, eps, precision, vel_mode)
+    p = _params(G, c, eps, precision, vel_mode, r_near)
     h = ctypes.c_void_p()
     _check(lib.pn_init(ctypes.byref(h), int(n), ctypes.byref(p), int(device),
                        ctypes.c_void_p(_torch_stream(device, stream))))
     return Context(h.value, int(n), int(device), p)
 
 
-def pn_set_params(ctx: Context, G=None, c=None, eps=None, precision=None, vel_mode=None) -> None:
+def pn_set_params(ctx: Context, G=None, c=None, eps=None, precision=None, vel_mode=None,
+                  r_near=None) -> None:
     q = ctx.params
     inv = {v: k for k, v in _PRECISION.items() if isinstance(k, str)}
     invv = {v: k for k, v in _VEL_MODE.items() if isinstance(k, str)}
     p = _params(q.G if G is None else G, q.c if c is None else c, q.eps if eps is None else eps,
                 inv[q.precision] if precision is None else precision,
-                invv[q.vel_mode] if vel_mode is None else vel_mode)
+                invv[q.vel_mode] if vel_mode is None else vel_mode,
+                q.r_near if r_near is None else r_near)
     _check(_load().pn_set_params(ctx.handle, ctypes.byref(p)))
     ctx.params = p
 
@@ -235,9 +244,10 @@ def pn_set_timing(ctx: Context, enable: bool) -> None:
 
 
 def pn_get_timing(ctx: Context):
-    """(milliseconds, launches) of pass 1 and pass 2 since timing was enabled."""
-    ms = np.zeros(2)
-    nl = np.zeros(2, dtype=np.int64)
+    """(milliseconds, launches) of pass 1, pass 2 and the near-source pass
+    since timing was enabled."""
+    ms = np.zeros(3)
+    nl = np.zeros(3, dtype=np.int64)
     _check(_load().pn_get_timing(ctx.handle, ms.ctypes.data_as(ctypes.c_void_p),
                                  nl.ctypes.data_as(ctypes.c_void_p)))
     return ms, nl
