@@ -169,6 +169,29 @@ pn_status pn_get_timing(pn_ctx *ctx, double ms[3], int64_t launches[3]);
  */
 pn_status pn_get_launch(pn_ctx *ctx, int64_t out[7]);
 
+/*
+ * Energy and momentum like pn_energy, for callers that cannot allocate
+ * device memory (their GPU memory belongs to another allocator, or they
+ * must not allocate after start-up): no context, no cudaMalloc.  The paper
+ * has no counterpart; this is a deployment convenience.
+ *   n         number of bodies, 2 <= n <= PN_NOALLOC_MAX_BODIES; larger n
+ *             is rejected with PN_EINVAL
+ *   G, c, eps as in pn_params (c may be INFINITY)
+ *   x, v, m   device pointers as for pn_energy
+ *   out       DEVICE pointer to 8 doubles, written as pn_energy's out[]
+ * Work is enqueued on `cuda_stream` of `device` and the call returns
+ * without waiting.  The scratch is a fixed array inside the library (about
+ * 5 MiB on every device that loads libpn, held until exit), shared by all
+ * calls: calls whose work overlaps on the GPU race on it and must be
+ * serialised by the caller.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  Errors: PN_EINVAL, PN_ECUDA.
+ */
+#define PN_NOALLOC_MAX_BODIES 16384
+pn_status pn_energy_noalloc(int device, void *cuda_stream, int64_t n, double G, double c,
+                            double eps, const double *x, const double *v, const double *m,
+                            double *out);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *pn_last_error(void);
 

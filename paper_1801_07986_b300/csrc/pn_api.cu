@@ -157,6 +157,20 @@ pn_status run_steps(pn_ctx *c, double *x, double *v, const double *m, double *a,
 
 }  // namespace
 
+namespace pn {
+
+// Records an error message for pn_last_error from other translation units.
+pn_status set_error(pn_status s, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+}  // namespace pn
+
 extern "C" {
 
 int pn_version(void) { return 100; }

@@ -104,6 +104,12 @@ cudaError_t launch_near(pn_ctx *c);
 cudaError_t launch_epilogue(pn_ctx *c, const double *x, const double *vel, const double *m,
                             double *a, double *v, double half_dt, unsigned long long step);
 cudaError_t launch_energy(pn_ctx *c, const double *x, const double *v, const double *m);
+cudaError_t launch_energy_on(cudaStream_t st, int64_t ns, int64_t ns_pad, const double *x,
+                             const double *v, const double *m, double G, double inv_c2,
+                             double eps, int jsplit_max, double4_32a *drec, double *part,
+                             double *blk, double *out);
+
+pn_status set_error(pn_status s, const char *fmt, ...);
 
 void shapes(int64_t ns_pad, int sm_count, int occ_mix, int occ_f64, Shape *mix, Shape *f64);
 cudaError_t occupancy(int *occ_mix, int *occ_f64);

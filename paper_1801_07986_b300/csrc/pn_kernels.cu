@@ -1299,3 +1299,37 @@ cudaError_t occupancy(int *occ_mix, int *occ_f64)
 }
 
 }  // namespace pn
+
+namespace pn {
+
+// The energy evaluation of launch_energy on scratch the caller provides
+// (records, pair partials, block partials) instead of a context's buffers;
+// the source range is split into at most `jsplit_max` parts.
+cudaError_t launch_energy_on(cudaStream_t st, int64_t ns, int64_t ns_pad, const double *x,
+                             const double *v, const double *m, double G, double inv_c2,
+                             double eps, int jsplit_max, double4_32a *drec, double *part,
+                             double *blk, double *out)
+{
+    const double eps2 = eps * eps;
+    const int64_t nb = glue_blocks(ns_pad);
+    k_prologue<2><<<(unsigned)nb, kGlueThreads, 0, st>>>(ns, ns_pad, x, v, m, G, eps2, -1.0,
+                                                         nullptr, drec, nullptr, nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    const int ntiles = (int)(ns_pad / kF64Tile);
+    const int tps = (ntiles + jsplit_max - 1) / jsplit_max;
+    const int jsplit = (ntiles + tps - 1) / tps;
+    dim3 grid((unsigned)(ns_pad / kF64Threads), (unsigned)jsplit);
+    k_energy_pairs<<<grid, kF64Threads, 0, st>>>(drec, ns_pad, ntiles, tps, eps2, part);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    k_energy_epilogue<<<(unsigned)nb, kGlueThreads, 0, st>>>(ns, ns_pad, x, v, m, part, jsplit, G,
+                                                             blk);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    k_energy_final<<<1, kGlueThreads, 0, st>>>(blk, nb, v, m, G, inv_c2, out);
+    return cudaGetLastError();
+}
+
+}  // namespace pn

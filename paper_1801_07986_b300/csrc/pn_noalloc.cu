@@ -1,0 +1,100 @@
+// pn_noalloc.cu -- pn_energy_noalloc: the energy/momentum evaluation for
+// callers that must not allocate device memory.
+//
+// Some callers cannot call cudaMalloc: a process whose device memory is
+// owned by another allocator (a framework's caching pool that has reserved
+// the GPU), code that must not allocate after start-up (real-time loops,
+// library hooks with a fixed memory budget), or code running where
+// allocation calls are forbidden.  pn_energy needs a context, and pn_init
+// allocates; this entry point instead works in a scratch array compiled into
+// the library, so it allocates nothing.
+//
+// The scratch is a file-scope __device__ array: every GPU that loads
+// libpn holds it (kScratchBytes, about 5 MiB) until the process exits.  Its
+// host-side name is only a stand-in, so its device address is looked up
+// with cudaGetSymbolAddress once per device (on the first call on that
+// device, with that device current) and cached.  Every call shares the
+// array; each call writes every scratch byte it later reads, so nothing
+// needs clearing, but calls whose work overlaps on the GPU (other streams,
+// or another thread) race on the array.
+#include <cmath>
+#include <mutex>
+
+#include "pn_internal.h"
+
+namespace {
+
+constexpr int64_t kMaxBodies = 16384;                       // PN_NOALLOC_MAX_BODIES
+constexpr int64_t kPadMax = (kMaxBodies - 1 + pn::kPad - 1) / pn::kPad * pn::kPad;
+constexpr int kSplitMax = 4;                                // source splits of the pair kernel
+constexpr int64_t kRecBytes = 2 * kPadMax * (int64_t)sizeof(double4_32a);
+constexpr int64_t kPartBytes = (int64_t)kSplitMax * pn::kEVals * kPadMax * 8;
+constexpr int64_t kBlkBytes = (kPadMax / pn::kGlueThreads) * pn::kEBlockVals * 8;
+constexpr int64_t kAlign = 256;
+constexpr int64_t kRecOff = 0;
+constexpr int64_t kPartOff = (kRecOff + kRecBytes + kAlign - 1) / kAlign * kAlign;
+constexpr int64_t kBlkOff = (kPartOff + kPartBytes + kAlign - 1) / kAlign * kAlign;
+constexpr int64_t kScratchBytes = (kBlkOff + kBlkBytes + kAlign - 1) / kAlign * kAlign;
+
+static __device__ __align__(256) unsigned char g_energy_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void *g_addr[kMaxDevices];
+
+pn_status fail(pn_status s, const char *msg, const char *detail = "")
+{
+    return pn::set_error(s, "%s%s", msg, detail);
+}
+
+}  // namespace
+
+extern "C" pn_status pn_energy_noalloc(int device, void *cuda_stream, int64_t n, double G,
+                                       double c, double eps, const double *x, const double *v,
+                                       const double *m, double *out)
+{
+    if (n < 2)
+        return fail(PN_EINVAL, "pn_energy_noalloc: n must be >= 2");
+    if (n > kMaxBodies)
+        return fail(PN_EINVAL, "pn_energy_noalloc: n exceeds PN_NOALLOC_MAX_BODIES (16384)");
+    if (!x || !v || !m || !out)
+        return fail(PN_EINVAL, "pn_energy_noalloc: NULL array");
+    if (!(std::isfinite(G) && G > 0.0) || !(c > 0.0) || !(std::isfinite(eps) && eps >= 0.0))
+        return fail(PN_EINVAL, "pn_energy_noalloc: need G > 0, c > 0 (or INFINITY), eps >= 0");
+    if (device < 0 || device >= kMaxDevices)
+        return fail(PN_EINVAL, "pn_energy_noalloc: device index out of range");
+    int prev = -1;
+    cudaError_t e = cudaGetDevice(&prev);
+    if (e == cudaSuccess && prev != device)
+        e = cudaSetDevice(device);
+    if (e != cudaSuccess)
+        return fail(PN_ECUDA, "pn_energy_noalloc: cudaSetDevice: ", cudaGetErrorString(e));
+    void *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        if (!g_addr[device]) {
+            e = cudaGetSymbolAddress(&g_addr[device], g_energy_scratch);
+            if (e != cudaSuccess)
+                g_addr[device] = nullptr;
+        }
+        base = g_addr[device];
+    }
+    if (!base) {
+        if (prev >= 0 && prev != device)
+            cudaSetDevice(prev);
+        return fail(PN_ECUDA, "pn_energy_noalloc: cudaGetSymbolAddress: ", cudaGetErrorString(e));
+    }
+    unsigned char *b = static_cast<unsigned char *>(base);
+    const int64_t ns = n - 1;
+    const int64_t ns_pad = (ns + pn::kPad - 1) / pn::kPad * pn::kPad;
+    const double inv_c2 = std::isinf(c) ? 0.0 : 1.0 / (c * c);
+    e = pn::launch_energy_on((cudaStream_t)cuda_stream, ns, ns_pad, x, v, m, G, inv_c2, eps,
+                             kSplitMax, reinterpret_cast<double4_32a *>(b + kRecOff),
+                             reinterpret_cast<double *>(b + kPartOff),
+                             reinterpret_cast<double *>(b + kBlkOff), out);
+    if (prev >= 0 && prev != device)
+        cudaSetDevice(prev);
+    if (e != cudaSuccess)
+        return fail(PN_ECUDA, "pn_energy_noalloc: launch: ", cudaGetErrorString(e));
+    return PN_OK;
+}

@@ -27,6 +27,7 @@ STATUS_NAMES = {0: "PN_OK", 1: "PN_EINVAL", 2: "PN_ENOMEM", 3: "PN_ECUDA", 4: "P
                 5: "PN_ETIMEOUT", 6: "PN_EUNSUPPORTED"}
 PN_FP64, PN_MIXED = 0, 1
 PN_VPRED_END, PN_VHALF = 0, 1
+PN_NOALLOC_MAX_BODIES = 16384
 _PRECISION = {"fp64": PN_FP64, "mixed": PN_MIXED, PN_FP64: PN_FP64, PN_MIXED: PN_MIXED}
 _VEL_MODE = {"vpred_end": PN_VPRED_END, "vhalf": PN_VHALF, PN_VPRED_END: PN_VPRED_END,
              PN_VHALF: PN_VHALF}
@@ -81,6 +82,7 @@ def _load():
                 "pn_set_timing": [P, I],
                 "pn_get_timing": [P, P, P],
                 "pn_get_launch": [P, P],
+                "pn_energy_noalloc": [I, P, I64, D, D, D, P, P, P, P],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -185,11 +187,15 @@ def pn_set_stream(ctx: Context, stream) -> None:
 
 
 def _dev(ctx: Context, t, shape, name):
+    return _dev_on(ctx.device, t, shape, name)
+
+
+def _dev_on(device: int, t, shape, name):
     import torch
     if not isinstance(t, torch.Tensor):
-        raise TypeError(f"{name} must be a torch tensor on cuda:{ctx.device}")
-    if t.dtype != torch.float64 or not t.is_cuda or t.device.index != ctx.device:
-        raise TypeError(f"{name} must be float64 on cuda:{ctx.device} (got {t.dtype}, {t.device})")
+        raise TypeError(f"{name} must be a torch tensor on cuda:{device}")
+    if t.dtype != torch.float64 or not t.is_cuda or t.device.index != device:
+        raise TypeError(f"{name} must be float64 on cuda:{device} (got {t.dtype}, {t.device})")
     if tuple(t.shape) != shape or not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous with shape {shape} (got {tuple(t.shape)})")
     return ctypes.c_void_p(t.data_ptr())
@@ -233,6 +239,26 @@ def pn_energy(ctx: Context, x, v, m) -> dict:
                              _dev(ctx, m, (n,), "m"), out.ctypes.data_as(ctypes.c_void_p)))
     return {"E_N": out[0], "E_PN": out[1], "E": out[0] + out[1],
             "P_N": out[2:5].copy(), "P_PN": out[5:8].copy(), "P": out[2:5] + out[5:8]}
+
+
+def pn_energy_noalloc(x, v, m, out, G: float = 1.0, c: float = math.inf, eps: float = 0.0,
+                      device: int | None = None, stream=None) -> None:
+    """pn_energy without a context and without any device allocation (for
+    callers whose device memory is owned by another allocator): writes the 8
+    results of pn_energy into the device tensor `out` (float64, shape (8,)),
+    asynchronously on `stream`.  At most PN_NOALLOC_MAX_BODIES (16384)
+    bodies; concurrent calls on overlapping streams race on the library's
+    shared scratch."""
+    import torch
+    if device is None:
+        device = x.device.index
+    n = int(m.shape[0])
+    args = (_dev_on(device, x, (n, 3), "x"), _dev_on(device, v, (n, 3), "v"),
+            _dev_on(device, m, (n,), "m"), _dev_on(device, out, (8,), "out"))
+    st = torch.cuda.current_stream(device).cuda_stream if stream is None \
+        else getattr(stream, "cuda_stream", stream)
+    _check(_load().pn_energy_noalloc(int(device), ctypes.c_void_p(st), n, float(G), float(c),
+                                     float(eps), *args))
 
 
 def pn_sync(ctx: Context) -> None:
