@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="plummer128k_ecc")
+    ap.add_argument("--bodies", type=int, default=None,
+                    help="override the workload's body count (smaller profiling cases)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -373,6 +375,9 @@ def main():
     args = parse()
     from paper_1801_07986_b300.inputs import WORKLOADS
     w = WORKLOADS[args.workload]
+    if args.bodies:
+        import dataclasses
+        w = dataclasses.replace(w, n=args.bodies, name=f"{w.name}@n={args.bodies}")
     if args.impl == "reference":
         run_reference(args, w)
     else:
