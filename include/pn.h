@@ -55,6 +55,7 @@ typedef enum {
 
 enum { PN_FP64 = 0, PN_MIXED = 1 };            /* pn_params.precision */
 enum { PN_VPRED_END = 0, PN_VHALF = 1 };       /* pn_params.vel_mode  */
+enum { PN_PAIR_FUSED = 0, PN_PAIR_TWO_PASS = 1 };   /* pn_params.pair_kernel */
 
 /*
  * Physical constants and evaluation mode.
@@ -78,6 +79,12 @@ enum { PN_VPRED_END = 0, PN_VHALF = 1 };       /* pn_params.vel_mode  */
  *              separate cancellation-free pair form instead of through
  *              global sums.  The result is the same in exact arithmetic;
  *              only rounding changes.  0 disables the split.
+ *   pair_kernel (PN_MIXED only) PN_PAIR_FUSED: one persistent kernel
+ *              computes the pass-1 and pass-2 pair sums in a single sweep
+ *              over the sources; PN_PAIR_TWO_PASS: pass 1 (Newtonian sums
+ *              and the hole's accumulators) and pass 2 (1PN pair sums) as
+ *              two kernels.  Same sums, same epilogue.  PN_FP64 always runs
+ *              the two-pass kernels.
  */
 typedef struct {
     double G;
@@ -86,6 +93,7 @@ typedef struct {
     int precision;
     int vel_mode;
     double r_near;
+    int pair_kernel;
 } pn_params;
 
 /*
@@ -155,8 +163,9 @@ pn_status pn_sync(pn_ctx *ctx);
  * Kernel timing for measurement.  While enabled, pn_accel/pn_step record a
  * CUDA event pair on the context's stream around each pair-interaction
  * kernel launch.  pn_get_timing waits for the stream and returns, for
- * kernel k (0 = pass 1, 1 = pass 2, 2 = near-source pass), the summed
- * milliseconds and launch count since timing was last enabled.
+ * kernel k (0 = pass 1 of the two-pass kernels, 1 = pass 2 or the fused pair
+ * kernel, 2 = near-source pass), the summed milliseconds and launch count
+ * since timing was last enabled.
  */
 pn_status pn_set_timing(pn_ctx *ctx, int enable);
 pn_status pn_get_timing(pn_ctx *ctx, double ms[3], int64_t launches[3]);
@@ -164,8 +173,8 @@ pn_status pn_get_timing(pn_ctx *ctx, double ms[3], int64_t launches[3]);
 /*
  * Launch shape of the pair kernels for this context: out[0] threads per
  * block, out[1] targets per thread, out[2] sources per shared-memory tile,
- * out[3] blocks along targets, out[4] source splits, out[5] resident blocks
- * per SM, out[6] SM count.
+ * out[3] blocks along targets, out[4] source splits (two-pass) or
+ * persistent blocks (fused), out[5] resident blocks per SM, out[6] SM count.
  */
 pn_status pn_get_launch(pn_ctx *ctx, int64_t out[7]);
 

@@ -73,6 +73,9 @@ bool params_ok(const pn_params *p)
                           p->vel_mode), false;
     if (!(std::isfinite(p->r_near) && p->r_near >= 0.0))
         return (void)fail(PN_EINVAL, "r_near must be finite and >= 0 (got %g)", p->r_near), false;
+    if (p->pair_kernel != PN_PAIR_FUSED && p->pair_kernel != PN_PAIR_TWO_PASS)
+        return (void)fail(PN_EINVAL, "pair_kernel must be PN_PAIR_FUSED or PN_PAIR_TWO_PASS (got %d)",
+                          p->pair_kernel), false;
     return true;
 }
 
@@ -134,8 +137,12 @@ pn_status evaluate(pn_ctx *c, const double *x, const double *vel, const double *
                    double *v, double h)
 {
     PN_CUDA(pn::launch_prologue(c, x, vel, m, false), "prologue launch");
-    PN_CUDA(pn::launch_pass1(c), "pass-1 launch");
-    PN_CUDA(pn::launch_pass2(c), "pass-2 launch");
+    if (pn::use_fused(c)) {
+        PN_CUDA(pn::launch_fused(c), "fused pair launch");
+    } else {
+        PN_CUDA(pn::launch_pass1(c), "pass-1 launch");
+        PN_CUDA(pn::launch_pass2(c), "pass-2 launch");
+    }
     PN_CUDA(pn::launch_near(c), "near-pass launch");
     PN_CUDA(pn::launch_epilogue(c, x, vel, m, a, v, h, (unsigned long long)c->step_counter),
             "epilogue launch");
@@ -217,13 +224,31 @@ pn_status pn_init(pn_ctx **out, int64_t n, const pn_params *params, int device,
     c->device = device;
     c->stream = (cudaStream_t)cuda_stream;
     c->sm_count = sms;
-    int occ_mix = 0, occ_f64 = 0;
+    int occ_mix = 0, occ_f64 = 0, occ_fused = 0;
     cudaError_t e = pn::occupancy(&occ_mix, &occ_f64);
+    // fused-kernel variant; PN_FUSED_TARGETS / PN_FUSED_UNROLL override (tuning)
+    c->fused_P = 4;          // measured fastest on B300 at N = 131072 (4 targets x 2-way unroll)
+    c->fused_unroll = 2;
+    if (const char *tp = std::getenv("PN_FUSED_TARGETS")) {
+        const int v = std::atoi(tp);
+        if (v == 1 || v == 2 || v == 4)
+            c->fused_P = v;
+    }
+    if (const char *tu = std::getenv("PN_FUSED_UNROLL")) {
+        const int v = std::atoi(tu);
+        if (v == 1 || v == 2)
+            c->fused_unroll = v;
+    }
+    if (e == cudaSuccess)
+        e = pn::fused_occupancy(c->fused_P, c->fused_unroll, &occ_fused);
     if (e != cudaSuccess) {
         delete c;
         return fail(PN_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
     }
     pn::shapes(c->ns_pad, sms, occ_mix, occ_f64, &c->mix, &c->f64);
+    c->fused_occ = occ_fused > 0 ? occ_fused : 1;
+    c->fused_G = (int64_t)c->fused_occ * sms;
+    c->fused_segs = (int)pn::fused_segments(c->ns_pad, c->fused_G, c->fused_P);
 
     const int64_t np = c->ns_pad;
     int64_t part = (int64_t)c->mix.jsplit * (pn::kP1Vals + pn::kP2Vals) * np;
@@ -234,6 +259,11 @@ pn_status pn_init(pn_ctx **out, int64_t n, const pn_params *params, int device,
     if (part_e > part)
         part = part_e;
     part += (int64_t)pn::kNearVals * np;   // near-pass partials after both passes
+    const int64_t part_fused = (int64_t)(pn::kP1Vals + pn::kP2Vals + pn::kNearVals) * np +
+                               c->fused_G * c->fused_segs * pn::kFusedVals *
+                                   (pn::kMixThreads * c->fused_P);
+    if (part_fused > part)
+        part = part_fused;
     c->part_len = part;
     const int64_t nglue = (np + pn::kGlueThreads - 1) / pn::kGlueThreads;
     c->blk_len = nglue * pn::kGlobVals;
@@ -451,12 +481,13 @@ pn_status pn_get_launch(pn_ctx *c, int64_t out[7])
     if (!out)
         return fail(PN_EINVAL, "pn_get_launch: NULL output");
     const pn::Shape &s = c->p.precision == PN_MIXED ? c->mix : c->f64;
+    const bool fused = pn::use_fused(c);
     out[0] = s.threads;
-    out[1] = s.targets;
+    out[1] = fused ? c->fused_P : s.targets;
     out[2] = s.tile;
     out[3] = s.nblk_i;
-    out[4] = s.jsplit;
-    out[5] = s.occupancy;
+    out[4] = fused ? c->fused_G : s.jsplit;
+    out[5] = fused ? c->fused_occ : s.occupancy;
     out[6] = c->sm_count;
     return ok();
 }

@@ -17,15 +17,17 @@ constexpr int kMixTile = 128;      // sources per shared-memory tile
 constexpr int kF64Threads = 128;
 constexpr int kF64Targets = 1;
 constexpr int kF64Tile = 64;
-// Star slots are padded to a multiple of this (covers both shapes).
-constexpr int kPad = 256;
+// Star slots are padded to a multiple of this (covers every shape; the fused
+// kernel takes up to 4 targets per thread, 512 per block).
+constexpr int kPad = 512;
 // Threads per block of the O(n) kernels.
 constexpr int kGlueThreads = 256;
 
 // Values per star written by each pair kernel into its partial-sum buffer.
-constexpr int kP1Vals = 5;         // N (3), U, Y
+constexpr int kP1Vals = 6;         // N (3), U, Z, Wr
 constexpr int kP2Vals = 9;         // V (3), H (3), E (3)
 constexpr int kEVals = 8;          // pot, Smv (3), Snn, Spx (3)
+constexpr int kFusedVals = kP1Vals + kP2Vals;
 // Near-source pass: sources per tile and values per target.
 constexpr int kNearTile = 128;
 constexpr int kNearVals = 6;       // P (3), Ee (3)
@@ -64,6 +66,11 @@ struct pn_ctx {
     cudaStream_t stream;
     int sm_count;
     pn::Shape mix, f64;
+    int fused_P;             // targets per thread of the fused kernel (1, 2 or 4)
+    int fused_unroll;        // source-loop unroll of the fused kernel (1 or 2)
+    int fused_occ;           // resident fused-kernel blocks per SM
+    int64_t fused_G;         // persistent blocks of the fused kernel
+    int fused_segs;          // segments per persistent block (upper bound)
 
     // scratch, all owned by the context
     double *vp;          // n x 3: velocity at which the force is evaluated
@@ -113,5 +120,9 @@ pn_status set_error(pn_status s, const char *fmt, ...);
 
 void shapes(int64_t ns_pad, int sm_count, int occ_mix, int occ_f64, Shape *mix, Shape *f64);
 cudaError_t occupancy(int *occ_mix, int *occ_f64);
+cudaError_t fused_occupancy(int P, int unroll, int *occ);
+cudaError_t launch_fused(pn_ctx *c);
+bool use_fused(const pn_ctx *c);
+int64_t fused_segments(int64_t ns_pad, int64_t G, int P);
 
 }  // namespace pn

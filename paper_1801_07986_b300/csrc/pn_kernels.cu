@@ -5,7 +5,9 @@
 //
 //   prologue   O(n)   hole-relative star records + global sums (Q, W, ...)
 //   pass 1     O(n^2) per star i: N_i = sum_j m_j x_ij / r_ij^3,
-//                     U_i = sum_j m_j / r_ij, Y_i = sum_j m_j (r_i1^2 - r_j1^2)/r_ij^3
+//                     U_i = sum_j m_j / r_ij, Z_i = sum_j m_j / r_ij^3 and
+//                     Wr_i = sum_j m_j R_j^2 / r_ij^3 (the hole's three-body
+//                     sum uses Y_i = sum_j m_j (R_i^2 - R_j^2)/r_ij^3 = R_i^2 Z_i - Wr_i)
 //   pass 2     O(n^2) per star i: the velocity-dependent 1PN pair sums
 //   epilogue   O(n)   assembles each star's acceleration from passes 1 and 2
 //                     and the hole's three-body terms from pass 1
@@ -34,6 +36,17 @@ __device__ __forceinline__ void ds_add(float &hi, float &lo, float p)
     const float e = (hi - (s - bp)) + (p - bp);
     hi = s;
     lo += e;
+}
+
+// 1/sqrt(s2) in single precision: the PTX approximate reciprocal square root
+// (one MUFU instruction; max relative error about 2^-23), flushing subnormal
+// inputs to zero -- pair distances squared are never subnormal (s2 >= eps^2,
+// and unsoftened pairs are far from 1e-38).
+__device__ __forceinline__ float rsqrt_approx(float s2)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(s2));
+    return y;
 }
 
 // 1/sqrt(s2) in double: single-precision seed refined by two Newton steps
@@ -125,8 +138,8 @@ __global__ void k_kick_drift(int64_t n3, double *__restrict__ x, double *__restr
 //   Q = sum m_j v_j, W = sum w_j (all), W_far = sum_far w_j,
 //   SA_far = sum_far 5 m_j/(4 R_j), SB_far = sum_far m_j (R_j^2 + eps^2)/(4 R_j^3),
 //   Phi = sum m_j / R_j, and the number of near stars.
-// Records: mixed  A = (hi(d), m) B = (lo(d), c) C = (v, 0) D = (e, 0) E = (w, 0)
-//          double A = (d, m)     B = (v, c)     C = (e, 0) D = (w, 0)
+// Records: mixed  A = (hi(d), m) B = (lo(d), R^2) C = (v, c/1.5) D = (e/1.5, 0) E = (w, 0)
+//          double A = (d, m)     B = (v, R^2)    C = (e/1.5, c/1.5) D = (w, 0)
 // Energy records (double): A = (d, m), B = (v, 0).
 template <int MODE>   // 0 mixed, 1 double, 2 energy
 __global__ void __launch_bounds__(kGlueThreads)
@@ -158,20 +171,21 @@ k_prologue(int64_t ns, int64_t ns_pad, const double *__restrict__ x,
             const double cj = far * G * M * (1.5 * iR + 0.25 * eps2 * iR3);
             const double ef = far * 0.5 * G * M * iR3;
             const double wf = mj * iR3;
+            const double c3 = cj / 1.5, e3 = ef / 1.5;
             if (MODE == 0) {
                 const float h0 = (float)d0, h1 = (float)d1, h2 = (float)d2;
                 mrec[t] = make_float4(h0, h1, h2, (float)mj);
                 mrec[ns_pad + t] = make_float4((float)(d0 - (double)h0), (float)(d1 - (double)h1),
-                                               (float)(d2 - (double)h2), (float)cj);
-                mrec[2 * ns_pad + t] = make_float4((float)v0, (float)v1, (float)v2, 0.0f);
+                                               (float)(d2 - (double)h2), (float)R2);
+                mrec[2 * ns_pad + t] = make_float4((float)v0, (float)v1, (float)v2, (float)c3);
                 mrec[3 * ns_pad + t] =
-                    make_float4((float)(ef * d0), (float)(ef * d1), (float)(ef * d2), 0.0f);
+                    make_float4((float)(e3 * d0), (float)(e3 * d1), (float)(e3 * d2), 0.0f);
                 mrec[4 * ns_pad + t] = make_float4((float)(far * wf * d0), (float)(far * wf * d1),
                                                    (float)(far * wf * d2), 0.0f);
             } else if (MODE == 1) {
                 drec[t] = make_double4_32a(d0, d1, d2, mj);
-                drec[ns_pad + t] = make_double4_32a(v0, v1, v2, cj);
-                drec[2 * ns_pad + t] = make_double4_32a(ef * d0, ef * d1, ef * d2, 0.0);
+                drec[ns_pad + t] = make_double4_32a(v0, v1, v2, R2);
+                drec[2 * ns_pad + t] = make_double4_32a(e3 * d0, e3 * d1, e3 * d2, c3);
                 drec[3 * ns_pad + t] =
                     make_double4_32a(far * wf * d0, far * wf * d1, far * wf * d2, 0.0);
             } else {
@@ -328,10 +342,81 @@ struct MixTarget {
     float vx, vy, vz;               // velocity of target i (pass 2)
 };
 
-// Pass 1, one shared-memory tile of sources.  Per pair:
-//   N += m_j x_ij / r^3,  U += m_j / r,
-//   Y += m_j (R_i^2 - R_j^2) / r^3  with  R_i^2 - R_j^2 = x_ij . (d_i + d_j).
-// x_ij = (hi_i - hi_j) + (lo_i - lo_j) keeps ~48 bits of the difference.
+// The pair terms, shared by the two-pass and the fused kernels.  Records of
+// source j: A = (hi(d_j), m_j), B = (lo(d_j), R_j^2), C = (v_j, c_j/1.5),
+// D = (e_j/1.5, 0), E = (w_j, 0).  x_ij = (hi_i - hi_j) + (lo_i - lo_j)
+// keeps ~48 bits of the difference.
+struct PairGeo {
+    float dx, dy, dz, s2, is, mj, mis, mis3;
+    float wx, wy, wz;
+};
+
+template <bool MASK>
+__device__ __forceinline__ PairGeo pair_geo(const MixTarget &tg, const float4 &A, const float4 &B,
+                                            float eps2, bool self)
+{
+    PairGeo g;
+    g.dx = (tg.hx - A.x) + (tg.lx - B.x);
+    g.dy = (tg.hy - A.y) + (tg.ly - B.y);
+    g.dz = (tg.hz - A.z) + (tg.lz - B.z);
+    g.s2 = fmaf(g.dx, g.dx, fmaf(g.dy, g.dy, fmaf(g.dz, g.dz, eps2)));
+    g.mj = A.w;
+    if (MASK) {
+        g.s2 = self ? 1.0f : g.s2;
+        g.mj = self ? 0.0f : g.mj;
+    }
+    g.is = rsqrt_approx(g.s2);
+    g.mis = g.mj * g.is;
+    g.mis3 = g.mis * (g.is * g.is);
+    return g;
+}
+
+// Pass-1 sums: N += m_j x_ij/r^3, U += m_j/r, Z += m_j/r^3, Wr += m_j R_j^2/r^3
+// (the hole's Y_i = sum m_j (R_i^2 - R_j^2)/r^3 is R_i^2 Z_i - Wr_i).
+__device__ __forceinline__ void pass1_terms(const PairGeo &g, float Rj2, float *acc)
+{
+    acc[0] = fmaf(g.mis3, g.dx, acc[0]);
+    acc[1] = fmaf(g.mis3, g.dy, acc[1]);
+    acc[2] = fmaf(g.mis3, g.dz, acc[2]);
+    acc[3] += g.mis;
+    acc[4] += g.mis3;
+    acc[5] = fmaf(g.mis3, Rj2, acc[5]);
+}
+
+// Pass-2 sums (velocities are those at which A is taken), with
+// kappa' = (v_j.x_ij)^2/r^2 + c_j/1.5 - (e_j/1.5).d_i - 4/3 |v_ij|^2:
+//   V' += m_j x_ij/r^3 kappa'                       (V = 3/2 V')
+//   H' += m_j/r^3 [x_ij.v_i - 3/4 x_ij.v_j] v_ij     (H = 4 H')
+//   E  += w_j / r
+// V carries Eq. 6 line 3 (without its 4/R_i part) and line 6 (without its
+// v_i^2 part): with r_ij^2 - R_i^2 = R_j^2 + eps^2 - 2 d_i.d_j, line 3's
+// bracket is 4/R_i + (c_j - e_j.d_i)/(G M).  H is Eq. 6 line 7, E the 1/r_ij
+// part of line 4.
+__device__ __forceinline__ void pass2_terms(const PairGeo &g, const MixTarget &tg,
+                                            const float4 &C, const float4 &D, float wx, float wy,
+                                            float wz, float *acc)
+{
+    const float is2 = g.is * g.is;
+    const float ux = tg.vx - C.x, uy = tg.vy - C.y, uz = tg.vz - C.z;
+    const float u2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+    const float xvj = fmaf(g.dx, C.x, fmaf(g.dy, C.y, g.dz * C.z));
+    const float xvi = fmaf(g.dx, tg.vx, fmaf(g.dy, tg.vy, g.dz * tg.vz));
+    const float ed = fmaf(D.x, tg.hx, fmaf(D.y, tg.hy, D.z * tg.hz));
+    const float h = xvj * is2;
+    const float kap = fmaf(h, xvj, fmaf(-4.0f / 3.0f, u2, C.w - ed));
+    const float f = g.mis3 * kap;
+    acc[0] = fmaf(f, g.dx, acc[0]);
+    acc[1] = fmaf(f, g.dy, acc[1]);
+    acc[2] = fmaf(f, g.dz, acc[2]);
+    const float gg = g.mis3 * fmaf(-0.75f, xvj, xvi);
+    acc[3] = fmaf(gg, ux, acc[3]);
+    acc[4] = fmaf(gg, uy, acc[4]);
+    acc[5] = fmaf(gg, uz, acc[5]);
+    acc[6] = fmaf(wx, g.is, acc[6]);
+    acc[7] = fmaf(wy, g.is, acc[7]);
+    acc[8] = fmaf(wz, g.is, acc[8]);
+}
+
 template <bool MASK>
 __device__ __forceinline__ void pass1_tile(const float4 *__restrict__ sA,
                                            const float4 *__restrict__ sB, int64_t j0,
@@ -345,38 +430,12 @@ __device__ __forceinline__ void pass1_tile(const float4 *__restrict__ sA,
         const float4 B = sB[q];
 #pragma unroll
         for (int p = 0; p < kMixTargets; ++p) {
-            const float dx = (tg[p].hx - A.x) + (tg[p].lx - B.x);
-            const float dy = (tg[p].hy - A.y) + (tg[p].ly - B.y);
-            const float dz = (tg[p].hz - A.z) + (tg[p].lz - B.z);
-            float s2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-            float mj = A.w;
-            if (MASK) {
-                const bool self = (j0 + q == ti[p]);
-                s2 = self ? 1.0f : s2;
-                mj = self ? 0.0f : mj;
-            }
-            const float is = rsqrtf(s2);
-            const float mis = mj * is;
-            const float mis3 = mis * (is * is);
-            acc[p][0] = fmaf(mis3, dx, acc[p][0]);
-            acc[p][1] = fmaf(mis3, dy, acc[p][1]);
-            acc[p][2] = fmaf(mis3, dz, acc[p][2]);
-            acc[p][3] += mis;
-            const float sx = tg[p].hx + A.x, sy = tg[p].hy + A.y, sz = tg[p].hz + A.z;
-            const float r2d = fmaf(dx, sx, fmaf(dy, sy, dz * sz));
-            acc[p][4] = fmaf(mis3, r2d, acc[p][4]);
+            const PairGeo g = pair_geo<MASK>(tg[p], A, B, eps2, MASK && j0 + q == ti[p]);
+            pass1_terms(g, B.w, acc[p]);
         }
     }
 }
 
-// Pass 2, one tile.  Per pair (velocities are those at which A is taken):
-//   V += m_j x_ij / r^3 [c_j - e_j . d_i - 2 |v_ij|^2 + 3/2 (v_j . x_ij)^2 / r^2]
-//   H += m_j / r^3 [x_ij . (4 v_i - 3 v_j)] v_ij
-//   E += w_j / r
-// V carries Eq. 6 line 3 (without its 4/R_i part) and line 6 (without its
-// v_i^2 part): with r_ij^2 - R_i^2 = R_j^2 + eps^2 - 2 d_i . d_j, line 3's
-// bracket is 4/R_i + c_j/(G M) - e_j . d_i/(G M).  H is Eq. 6 line 7, E the
-// 1/r_ij part of line 4.
 template <bool MASK>
 __device__ __forceinline__ void pass2_tile(const float4 *__restrict__ sA,
                                            const float4 *__restrict__ sB,
@@ -396,42 +455,10 @@ __device__ __forceinline__ void pass2_tile(const float4 *__restrict__ sA,
         const float4 E = sE[q];
 #pragma unroll
         for (int p = 0; p < kMixTargets; ++p) {
-            const float dx = (tg[p].hx - A.x) + (tg[p].lx - B.x);
-            const float dy = (tg[p].hy - A.y) + (tg[p].ly - B.y);
-            const float dz = (tg[p].hz - A.z) + (tg[p].lz - B.z);
-            float s2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-            float mj = A.w;
-            float wx = E.x, wy = E.y, wz = E.z;
-            if (MASK) {
-                const bool self = (j0 + q == ti[p]);
-                s2 = self ? 1.0f : s2;
-                mj = self ? 0.0f : mj;
-                wx = self ? 0.0f : wx;
-                wy = self ? 0.0f : wy;
-                wz = self ? 0.0f : wz;
-            }
-            const float is = rsqrtf(s2);
-            const float is2 = is * is;
-            const float mis3 = (mj * is) * is2;
-            const float ux = tg[p].vx - C.x, uy = tg[p].vy - C.y, uz = tg[p].vz - C.z;
-            const float u2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
-            const float xvj = fmaf(dx, C.x, fmaf(dy, C.y, dz * C.z));
-            const float xvi = fmaf(dx, tg[p].vx, fmaf(dy, tg[p].vy, dz * tg[p].vz));
-            const float ed = fmaf(D.x, tg[p].hx, fmaf(D.y, tg[p].hy, D.z * tg[p].hz));
-            const float tq = (xvj * xvj) * is2;
-            const float kap = fmaf(1.5f, tq, fmaf(-2.0f, u2, B.w - ed));
-            const float f = mis3 * kap;
-            acc[p][0] = fmaf(f, dx, acc[p][0]);
-            acc[p][1] = fmaf(f, dy, acc[p][1]);
-            acc[p][2] = fmaf(f, dz, acc[p][2]);
-            const float sg = fmaf(4.0f, xvi, -3.0f * xvj);
-            const float gg = mis3 * sg;
-            acc[p][3] = fmaf(gg, ux, acc[p][3]);
-            acc[p][4] = fmaf(gg, uy, acc[p][4]);
-            acc[p][5] = fmaf(gg, uz, acc[p][5]);
-            acc[p][6] = fmaf(wx, is, acc[p][6]);
-            acc[p][7] = fmaf(wy, is, acc[p][7]);
-            acc[p][8] = fmaf(wz, is, acc[p][8]);
+            const bool self = MASK && j0 + q == ti[p];
+            const PairGeo g = pair_geo<MASK>(tg[p], A, B, eps2, self);
+            const float wx = self ? 0.0f : E.x, wy = self ? 0.0f : E.y, wz = self ? 0.0f : E.z;
+            pass2_terms(g, tg[p], C, D, wx, wy, wz, acc[p]);
         }
     }
 }
@@ -513,10 +540,163 @@ k_pass_mixed(const float4 *__restrict__ rec, int64_t ns_pad, int ntiles, int tps
                 (double)hi[p][k] + (double)lo[p][k];
 }
 
+// ------------------------------------------- fused pair kernel: mixed --
+
+// Pass 1 and pass 2 in one sweep over the sources: the pair separation,
+// distance, rsqrt and the m_j/r^3 factor are computed once per pair and feed
+// all 15 sums (N, U, Z, Wr of pass 1; V', H', E of pass 2).
+template <int P, int UNROLL, bool MASK>
+__device__ __forceinline__ void fused_tile(const float4 *__restrict__ sA,
+                                           const float4 *__restrict__ sB,
+                                           const float4 *__restrict__ sC,
+                                           const float4 *__restrict__ sD,
+                                           const float4 *__restrict__ sE, int64_t j0,
+                                           const MixTarget (&tg)[P], const int64_t (&ti)[P],
+                                           float eps2, float (&acc)[P][kFusedVals])
+{
+#pragma unroll UNROLL
+    for (int q = 0; q < kMixTile; ++q) {
+        const float4 A = sA[q];
+        const float4 B = sB[q];
+        const float4 C = sC[q];
+        const float4 D = sD[q];
+        const float4 E = sE[q];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const bool self = MASK && j0 + q == ti[p];
+            const PairGeo g = pair_geo<MASK>(tg[p], A, B, eps2, self);
+            const float wx = self ? 0.0f : E.x, wy = self ? 0.0f : E.y, wz = self ? 0.0f : E.z;
+            pass1_terms(g, B.w, acc[p]);
+            pass2_terms(g, tg[p], C, D, wx, wy, wz, acc[p] + kP1Vals);
+        }
+    }
+}
+
+// Stream-K persistent launch: the (target block, source tile) units are laid
+// out target-block-major and block b of the G resident blocks takes units
+// [b T / G, (b+1) T / G).  Whenever its range crosses into a new target block
+// it writes the finished segment to part[b][seg][value][256 targets]; the
+// gather kernel sums the segments of each target block in block order.
+template <int P, int UNROLL>
+__global__ void __launch_bounds__(kMixThreads, P == 4 ? 3 : (P == 2 ? 5 : 8))
+k_fused_mixed(const float4 *__restrict__ rec, int64_t ns_pad, int ntiles, int64_t total_units,
+              int segs, float eps2, double *__restrict__ part)
+{
+    constexpr int TI = kMixThreads * P;
+    __shared__ float4 sh[5][kMixTile];
+    // double-single running sums (hi, lo) per value, target and thread; kept
+    // in shared memory (touched once per tile) to leave registers for the pair loop
+    __shared__ float2 run[kFusedVals][P][kMixThreads];
+    const int64_t G = gridDim.x;
+    int64_t u = (int64_t)blockIdx.x * total_units / G;
+    const int64_t u1 = ((int64_t)blockIdx.x + 1) * total_units / G;
+    int seg = 0;
+    while (u < u1) {
+        const int64_t ib = u / ntiles;
+        const int64_t t0 = ib * TI;
+        const int64_t uend = (ib + 1) * ntiles < u1 ? (ib + 1) * ntiles : u1;
+        MixTarget tg[P];
+        int64_t ti[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            ti[p] = t0 + p * kMixThreads + threadIdx.x;
+            const float4 A = rec[ti[p]];
+            const float4 B = rec[ns_pad + ti[p]];
+            const float4 C = rec[2 * ns_pad + ti[p]];
+            tg[p].hx = A.x; tg[p].hy = A.y; tg[p].hz = A.z;
+            tg[p].lx = B.x; tg[p].ly = B.y; tg[p].lz = B.z;
+            tg[p].vx = C.x; tg[p].vy = C.y; tg[p].vz = C.z;
+#pragma unroll
+            for (int k = 0; k < kFusedVals; ++k)
+                run[k][p][threadIdx.x] = make_float2(0.0f, 0.0f);
+        }
+        for (; u < uend; ++u) {
+            const int64_t j0 = (u - ib * ntiles) * kMixTile;
+            __syncthreads();
+            for (int q = threadIdx.x; q < kMixTile; q += kMixThreads) {
+#pragma unroll
+                for (int k = 0; k < 5; ++k)
+                    sh[k][q] = rec[k * ns_pad + j0 + q];
+            }
+            __syncthreads();
+            float acc[P][kFusedVals];
+#pragma unroll
+            for (int p = 0; p < P; ++p)
+#pragma unroll
+                for (int k = 0; k < kFusedVals; ++k)
+                    acc[p][k] = 0.0f;
+            const bool diag = (j0 < t0 + TI) && (t0 < j0 + kMixTile);
+            if (diag)
+                fused_tile<P, UNROLL, true>(sh[0], sh[1], sh[2], sh[3], sh[4], j0, tg, ti, eps2, acc);
+            else
+                fused_tile<P, UNROLL, false>(sh[0], sh[1], sh[2], sh[3], sh[4], j0, tg, ti, eps2, acc);
+#pragma unroll
+            for (int p = 0; p < P; ++p)
+#pragma unroll
+                for (int k = 0; k < kFusedVals; ++k) {
+                    float2 r = run[k][p][threadIdx.x];
+                    ds_add(r.x, r.y, acc[p][k]);
+                    run[k][p][threadIdx.x] = r;
+                }
+        }
+        double *out = part + ((int64_t)blockIdx.x * segs + seg) * kFusedVals * TI;
+#pragma unroll
+        for (int p = 0; p < P; ++p)
+#pragma unroll
+            for (int k = 0; k < kFusedVals; ++k) {
+                const float2 r = run[k][p][threadIdx.x];
+                out[k * TI + p * kMixThreads + threadIdx.x] = (double)r.x + (double)r.y;
+            }
+        ++seg;
+    }
+}
+
+// Sums, for every star slot, the stream-K segments that cover its target
+// block (in block order) into the pass-1 / pass-2 partial layout with one
+// split: p1[k][t] (k < 5), p2[k][t] (k < 9).
+template <int P>
+__global__ void __launch_bounds__(kGlueThreads)
+k_fused_gather(const double *__restrict__ part, int64_t ns_pad, int ntiles, int64_t total_units,
+               int64_t G, int segs, double *__restrict__ p1, double *__restrict__ p2)
+{
+    constexpr int TI = kMixThreads * P;
+    const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
+    if (t >= ns_pad)
+        return;
+    const int64_t ib = t / TI;
+    const int lt = (int)(t - ib * TI);
+    const int64_t U0 = ib * ntiles, U1 = U0 + ntiles;
+    int64_t b = U0 * G / total_units;
+    while (b + 1 < G && (b + 1) * total_units / G <= U0)
+        ++b;
+    double acc[kFusedVals];
+#pragma unroll
+    for (int k = 0; k < kFusedVals; ++k)
+        acc[k] = 0.0;
+    for (; b < G; ++b) {
+        const int64_t bu0 = b * total_units / G, bu1 = (b + 1) * total_units / G;
+        if (bu0 >= U1)
+            break;
+        if (bu1 <= U0 || bu0 == bu1)
+            continue;
+        const int64_t s = ib - bu0 / ntiles;
+        const double *in = part + (b * segs + s) * kFusedVals * TI;
+#pragma unroll
+        for (int k = 0; k < kFusedVals; ++k)
+            acc[k] += in[k * TI + lt];
+    }
+#pragma unroll
+    for (int k = 0; k < kP1Vals; ++k)
+        p1[(int64_t)k * ns_pad + t] = acc[k];
+#pragma unroll
+    for (int k = 0; k < kP2Vals; ++k)
+        p2[(int64_t)k * ns_pad + t] = acc[kP1Vals + k];
+}
+
 // ------------------------------------------------ pair kernels: double --
 
 // The same pair sums as pass 1 / pass 2 above, in double precision
-// (records A = (d, m), B = (v, c), C = (e, 0), D = (w, 0)).
+// (records A = (d, m), B = (v, R^2), C = (e/1.5, c/1.5), D = (w, 0)).
 template <int PASS, bool MASK>
 __device__ __forceinline__ void f64_tile(const double4_32a (*__restrict__ sh)[kF64Tile], int64_t j0,
                                          const double (&di)[3], const double (&vi)[3],
@@ -542,8 +722,8 @@ __device__ __forceinline__ void f64_tile(const double4_32a (*__restrict__ sh)[kF
             acc[1] = fma(mis3, dy, acc[1]);
             acc[2] = fma(mis3, dz, acc[2]);
             acc[3] += mis;
-            const double r2d = fma(dx, di[0] + A.x, fma(dy, di[1] + A.y, dz * (di[2] + A.z)));
-            acc[4] = fma(mis3, r2d, acc[4]);
+            acc[4] += mis3;
+            acc[5] = fma(mis3, sh[1][q].w, acc[5]);
         } else {
             const double4_32a B = sh[1][q];
             const double4_32a C = sh[2][q];
@@ -554,13 +734,13 @@ __device__ __forceinline__ void f64_tile(const double4_32a (*__restrict__ sh)[kF
             const double xvj = fma(dx, B.x, fma(dy, B.y, dz * B.z));
             const double xvi = fma(dx, vi[0], fma(dy, vi[1], dz * vi[2]));
             const double ed = fma(C.x, di[0], fma(C.y, di[1], C.z * di[2]));
-            const double tq = (xvj * xvj) * is2;
-            const double kap = fma(1.5, tq, fma(-2.0, u2, B.w - ed));
+            const double h = xvj * is2;
+            const double kap = fma(h, xvj, fma(-4.0 / 3.0, u2, C.w - ed));
             const double f = mis3 * kap;
             acc[0] = fma(f, dx, acc[0]);
             acc[1] = fma(f, dy, acc[1]);
             acc[2] = fma(f, dz, acc[2]);
-            const double gg = mis3 * fma(4.0, xvi, -3.0 * xvj);
+            const double gg = mis3 * fma(-0.75, xvj, xvi);
             acc[3] = fma(gg, ux, acc[3]);
             acc[4] = fma(gg, uy, acc[4]);
             acc[5] = fma(gg, uz, acc[5]);
@@ -577,7 +757,7 @@ k_pass_f64(const double4_32a *__restrict__ rec, int64_t ns_pad, int ntiles, int 
            double *__restrict__ part)
 {
     constexpr int NV = PASS == 1 ? kP1Vals : kP2Vals;
-    constexpr int NA = PASS == 1 ? 1 : 4;
+    constexpr int NA = PASS == 1 ? 2 : 4;
     __shared__ double4_32a sh[4][kF64Tile];
     const int64_t t0 = (int64_t)blockIdx.x * kF64Threads;
     const int64_t ti = t0 + threadIdx.x;
@@ -918,7 +1098,11 @@ k_epilogue(int64_t ns, int64_t ns_pad, const double *__restrict__ x,
             sn[k] = pnear ? pnear[(int64_t)k * ns_pad + t] : 0.0;
         const double fi = nflag[t] ? 0.0 : 1.0;   // 1 if star i is a far source
         const double N[3] = {s1[0], s1[1], s1[2]};
-        const double U = s1[3], Y = s1[4];
+        const double U = s1[3], Y = R2 * s1[4] - s1[5];
+        for (int k = 0; k < 3; ++k) {
+            s2[k] *= 1.5;          // V = 3/2 V'
+            s2[3 + k] *= 4.0;      // H = 4 H'
+        }
         const double Q[3] = {glob[0], glob[1], glob[2]};
         const double Wf[3] = {glob[6], glob[7], glob[8]};
         const double SA = glob[9], SB = glob[10], Phi = glob[11];
@@ -1071,6 +1255,8 @@ k_energy_final(const double *__restrict__ blk, int64_t nblk, const double *__res
 
 static int64_t glue_blocks(int64_t n) { return (n + kGlueThreads - 1) / kGlueThreads; }
 
+static void timing_begin(pn_ctx *c, int k, cudaEvent_t *end_out);
+
 cudaError_t launch_kick_drift(pn_ctx *c, double *x, double *v, const double *a, double dt)
 {
     const int64_t n3 = 3 * c->n;
@@ -1119,8 +1305,6 @@ cudaError_t launch_prologue(pn_ctx *c, const double *x, const double *vel, const
     return cudaGetLastError();
 }
 
-static void timing_begin(pn_ctx *c, int k, cudaEvent_t *end_out);
-
 cudaError_t launch_pass1(pn_ctx *c)
 {
     const double eps2 = c->p.eps * c->p.eps;
@@ -1143,16 +1327,98 @@ cudaError_t launch_pass1(pn_ctx *c)
     return e;
 }
 
-static int64_t p2_offset(pn_ctx *c)
+bool use_fused(const pn_ctx *c)
 {
-    const Shape &s = c->p.precision == PN_MIXED ? c->mix : c->f64;
-    return (int64_t)s.jsplit * kP1Vals * c->ns_pad;
+    return c->p.precision == PN_MIXED && c->p.pair_kernel == PN_PAIR_FUSED;
 }
 
-static int64_t near_offset(pn_ctx *c)
+// Where the pair partial sums live in c->part:
+//   two-pass: pass 1 [jsplit][5][ns_pad], pass 2 [jsplit][9][ns_pad], near [6][ns_pad]
+//   fused:    pass 1 [1][5][ns_pad], pass 2 [1][9][ns_pad], near [6][ns_pad],
+//             then the stream-K segments [G][segs][14][256]
+struct Layout {
+    int js;
+    int64_t p1, p2, near, seg;
+};
+
+static Layout layout(const pn_ctx *c)
 {
-    const Shape &s = c->p.precision == PN_MIXED ? c->mix : c->f64;
-    return (int64_t)s.jsplit * (kP1Vals + kP2Vals) * c->ns_pad;
+    Layout L;
+    const int64_t np = c->ns_pad;
+    if (use_fused(c)) {
+        L.js = 1;
+    } else {
+        const Shape &s = c->p.precision == PN_MIXED ? c->mix : c->f64;
+        L.js = s.jsplit;
+    }
+    L.p1 = 0;
+    L.p2 = (int64_t)L.js * kP1Vals * np;
+    L.near = (int64_t)L.js * (kP1Vals + kP2Vals) * np;
+    L.seg = L.near + (int64_t)kNearVals * np;
+    return L;
+}
+
+static int64_t p2_offset(pn_ctx *c) { return layout(c).p2; }
+
+static int64_t near_offset(pn_ctx *c) { return layout(c).near; }
+
+int64_t fused_segments(int64_t ns_pad, int64_t G, int P)
+{
+    const int64_t ntiles = ns_pad / kMixTile;
+    const int64_t total = (ns_pad / (kMixThreads * P)) * ntiles;
+    const int64_t per = (total + G - 1) / G;
+    return per / ntiles + 2;
+}
+
+template <int P, int UNROLL>
+static cudaError_t launch_fused_p(pn_ctx *c, const Layout &L)
+{
+    const int64_t np = c->ns_pad;
+    const int ntiles = (int)(np / kMixTile);
+    const int64_t total = (np / (kMixThreads * P)) * ntiles;
+    const float eps2 = (float)(c->p.eps * c->p.eps);
+    cudaEvent_t end = nullptr;
+    timing_begin(c, 1, &end);
+    k_fused_mixed<P, UNROLL><<<(unsigned)c->fused_G, kMixThreads, 0, c->stream>>>(
+        c->mrec, np, ntiles, total, c->fused_segs, eps2, c->part + L.seg);
+    cudaError_t e = cudaGetLastError();
+    if (end)
+        cudaEventRecord(end, c->stream);
+    if (e != cudaSuccess)
+        return e;
+    k_fused_gather<P><<<(unsigned)glue_blocks(np), kGlueThreads, 0, c->stream>>>(
+        c->part + L.seg, np, ntiles, total, c->fused_G, c->fused_segs, c->part + L.p1,
+        c->part + L.p2);
+    return cudaGetLastError();
+}
+
+// Fused-kernel variants: targets per thread (1, 2, 4) x source-loop unroll (1, 2).
+cudaError_t launch_fused(pn_ctx *c)
+{
+    const Layout L = layout(c);
+    const bool u2 = c->fused_unroll == 2;
+    switch (c->fused_P) {
+    case 1: return u2 ? launch_fused_p<1, 2>(c, L) : launch_fused_p<1, 1>(c, L);
+    case 4: return u2 ? launch_fused_p<4, 2>(c, L) : launch_fused_p<4, 1>(c, L);
+    default: return u2 ? launch_fused_p<2, 2>(c, L) : launch_fused_p<2, 1>(c, L);
+    }
+}
+
+template <int P, int UNROLL>
+static cudaError_t occ_of(int *occ)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_fused_mixed<P, UNROLL>,
+                                                         kMixThreads, 0);
+}
+
+cudaError_t fused_occupancy(int P, int unroll, int *occ)
+{
+    const bool u2 = unroll == 2;
+    switch (P) {
+    case 1: return u2 ? occ_of<1, 2>(occ) : occ_of<1, 1>(occ);
+    case 4: return u2 ? occ_of<4, 2>(occ) : occ_of<4, 1>(occ);
+    default: return u2 ? occ_of<2, 2>(occ) : occ_of<2, 1>(occ);
+    }
 }
 
 cudaError_t launch_near(pn_ctx *c)
@@ -1201,12 +1467,12 @@ cudaError_t launch_pass2(pn_ctx *c)
 cudaError_t launch_epilogue(pn_ctx *c, const double *x, const double *vel, const double *m,
                             double *a, double *v, double h, unsigned long long step)
 {
-    const Shape &s = c->p.precision == PN_MIXED ? c->mix : c->f64;
+    const Layout L = layout(c);
     const int64_t nb = glue_blocks(c->ns_pad);
     const double eps2 = c->p.eps * c->p.eps;
-    const double *pnear = c->p.r_near > 0.0 ? c->part + near_offset(c) : nullptr;
+    const double *pnear = c->p.r_near > 0.0 ? c->part + L.near : nullptr;
     k_epilogue<<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
-        c->ns, c->ns_pad, x, vel, m, c->part, s.jsplit, c->part + p2_offset(c), s.jsplit, pnear,
+        c->ns, c->ns_pad, x, vel, m, c->part + L.p1, L.js, c->part + L.p2, L.js, pnear,
         c->nflag, c->glob, c->p.G, c->inv_c2, eps2, a, v, h, c->flag, c->flag_step, step, c->blk);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)

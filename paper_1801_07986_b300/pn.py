@@ -27,10 +27,13 @@ STATUS_NAMES = {0: "PN_OK", 1: "PN_EINVAL", 2: "PN_ENOMEM", 3: "PN_ECUDA", 4: "P
                 5: "PN_ETIMEOUT", 6: "PN_EUNSUPPORTED"}
 PN_FP64, PN_MIXED = 0, 1
 PN_VPRED_END, PN_VHALF = 0, 1
+PN_PAIR_FUSED, PN_PAIR_TWO_PASS = 0, 1
 PN_NOALLOC_MAX_BODIES = 16384
 _PRECISION = {"fp64": PN_FP64, "mixed": PN_MIXED, PN_FP64: PN_FP64, PN_MIXED: PN_MIXED}
 _VEL_MODE = {"vpred_end": PN_VPRED_END, "vhalf": PN_VHALF, PN_VPRED_END: PN_VPRED_END,
              PN_VHALF: PN_VHALF}
+_PAIR = {"fused": PN_PAIR_FUSED, "two_pass": PN_PAIR_TWO_PASS, PN_PAIR_FUSED: PN_PAIR_FUSED,
+         PN_PAIR_TWO_PASS: PN_PAIR_TWO_PASS}
 
 
 class PNError(RuntimeError):
@@ -44,7 +47,7 @@ class PNError(RuntimeError):
 class _Params(ctypes.Structure):
     _fields_ = [("G", ctypes.c_double), ("c", ctypes.c_double), ("eps", ctypes.c_double),
                 ("precision", ctypes.c_int), ("vel_mode", ctypes.c_int),
-                ("r_near", ctypes.c_double)]
+                ("r_near", ctypes.c_double), ("pair_kernel", ctypes.c_int)]
 
 
 # Default radius (in the state's length unit) inside which stars are summed
@@ -111,13 +114,15 @@ def pn_version() -> int:
     return int(_load().pn_version())
 
 
-def _params(G, c, eps, precision, vel_mode, r_near=R_NEAR_DEFAULT) -> _Params:
+def _params(G, c, eps, precision, vel_mode, r_near=R_NEAR_DEFAULT, pair_kernel="fused") -> _Params:
     if precision not in _PRECISION:
         raise ValueError(f"precision must be 'fp64' or 'mixed', got {precision!r}")
     if vel_mode not in _VEL_MODE:
         raise ValueError(f"vel_mode must be 'vpred_end' or 'vhalf', got {vel_mode!r}")
+    if pair_kernel not in _PAIR:
+        raise ValueError(f"pair_kernel must be 'fused' or 'two_pass', got {pair_kernel!r}")
     return _Params(float(G), float(c), float(eps), _PRECISION[precision], _VEL_MODE[vel_mode],
-                   float(r_near))
+                   float(r_near), _PAIR[pair_kernel])
 
 
 class Context:
@@ -156,13 +161,13 @@ def _torch_stream(device, stream):
 
 def pn_init(n: int, G: float = 1.0, c: float = math.inf, eps: float = 0.0,
             precision="mixed", vel_mode="vpred_end", device: int | None = None,
-            stream=None, r_near: float = R_NEAR_DEFAULT) -> Context:
+            stream=None, r_near: float = R_NEAR_DEFAULT, pair_kernel="fused") -> Context:
     """Create a context for n bodies (body 0 = the hole)."""
     lib = _load()
     if device is None:
         import torch
         device = torch.cuda.current_device()
-    p = _params(G, c, eps, precision, vel_mode, r_near)
+    p = _params(G, c, eps, precision, vel_mode, r_near, pair_kernel)
     h = ctypes.c_void_p()
     _check(lib.pn_init(ctypes.byref(h), int(n), ctypes.byref(p), int(device),
                        ctypes.c_void_p(_torch_stream(device, stream))))
@@ -170,14 +175,13 @@ def pn_init(n: int, G: float = 1.0, c: float = math.inf, eps: float = 0.0,
 
 
 def pn_set_params(ctx: Context, G=None, c=None, eps=None, precision=None, vel_mode=None,
-                  r_near=None) -> None:
+                  r_near=None, pair_kernel=None) -> None:
     q = ctx.params
-    inv = {v: k for k, v in _PRECISION.items() if isinstance(k, str)}
-    invv = {v: k for k, v in _VEL_MODE.items() if isinstance(k, str)}
     p = _params(q.G if G is None else G, q.c if c is None else c, q.eps if eps is None else eps,
-                inv[q.precision] if precision is None else precision,
-                invv[q.vel_mode] if vel_mode is None else vel_mode,
-                q.r_near if r_near is None else r_near)
+                q.precision if precision is None else precision,
+                q.vel_mode if vel_mode is None else vel_mode,
+                q.r_near if r_near is None else r_near,
+                q.pair_kernel if pair_kernel is None else pair_kernel)
     _check(_load().pn_set_params(ctx.handle, ctypes.byref(p)))
     ctx.params = p
 

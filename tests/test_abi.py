@@ -48,9 +48,9 @@ def test_header_compiles_as_c():
     assert r.returncode == 0, r.stderr
 
 
-def _params(G=1.0, c=50.0, eps=1e-4, precision=1, vel_mode=0, r_near=0.05):
+def _params(G=1.0, c=50.0, eps=1e-4, precision=1, vel_mode=0, r_near=0.05, pair_kernel=0):
     from paper_1801_07986_b300.pn import _Params
-    return _Params(G, c, eps, precision, vel_mode, r_near)
+    return _Params(G, c, eps, precision, vel_mode, r_near, pair_kernel)
 
 
 @pytest.mark.parametrize("n,kw,msg", [
@@ -66,6 +66,7 @@ def _params(G=1.0, c=50.0, eps=1e-4, precision=1, vel_mode=0, r_near=0.05):
     (100, {"vel_mode": 3}, "vel_mode"),
     (100, {"r_near": -1.0}, "r_near"),
     (100, {"r_near": float("nan")}, "r_near"),
+    (100, {"pair_kernel": 2}, "pair_kernel"),
 ])
 def test_init_rejects_bad_arguments_on_host(lib, n, kw, msg):
     h = ctypes.c_void_p()
@@ -96,7 +97,7 @@ def test_null_arguments(lib):
 
 def test_injected_allocation_failure():
     code = ("import ctypes; from paper_1801_07986_b300 import pn; lib = pn._load();"
-            "p = pn._Params(1.0, 50.0, 1e-4, 1, 0, 0.05); h = ctypes.c_void_p();"
+            "p = pn._Params(1.0, 50.0, 1e-4, 1, 0, 0.05, 0); h = ctypes.c_void_p();"
             "print(lib.pn_init(ctypes.byref(h), 100, ctypes.byref(p), 0, None),"
             " lib.pn_last_error().decode())")
     env = dict(os.environ, PN_FAIL_ALLOC="1", PYTHONPATH=ROOT)
@@ -124,3 +125,5 @@ def test_python_binding_validates_before_calling(lib):
         pn._params(1.0, math.inf, 0.0, "fp32", "vpred_end")
     with pytest.raises(ValueError):
         pn._params(1.0, math.inf, 0.0, "mixed", "rk4")
+    with pytest.raises(ValueError):
+        pn._params(1.0, math.inf, 0.0, "mixed", "vhalf", 0.05, "three_pass")

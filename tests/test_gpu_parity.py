@@ -49,9 +49,11 @@ def dev(a):
     return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
 
 
-def gpu_accel(x, v, m, precision, G=1.0, c=math.inf, eps=0.0, vel_mode="vpred_end"):
+def gpu_accel(x, v, m, precision, G=1.0, c=math.inf, eps=0.0, vel_mode="vpred_end",
+              pair_kernel="fused"):
     n = m.shape[0]
-    ctx = pn.pn_init(n, G=G, c=c, eps=eps, precision=precision, vel_mode=vel_mode, device=0)
+    ctx = pn.pn_init(n, G=G, c=c, eps=eps, precision=precision, vel_mode=vel_mode, device=0,
+                     pair_kernel=pair_kernel)
     X, V, M = dev(x), dev(v), dev(m)
     A = torch.empty_like(X)
     pn.pn_accel(ctx, X, V, M, A)
@@ -71,11 +73,15 @@ def test_fp64_matches_oracle(orc, n):
         assert err.max() <= FP64_TOL, (c, err.max(), int(err.argmax()))
 
 
+PAIR_KERNELS = ["fused", "two_pass"]
+
+
+@pytest.mark.parametrize("pair_kernel", PAIR_KERNELS)
 @pytest.mark.parametrize("n", [2, 3, 300, 1024, 4097])
-def test_mixed_matches_oracle(orc, n):
+def test_mixed_matches_oracle(orc, n, pair_kernel):
     x, v, m = cluster(n, 0.1, 200 + n)
     want = orc.accel(x, v, m, c=20.0, eps=1e-4)
-    got = gpu_accel(x, v, m, "mixed", c=20.0, eps=1e-4)
+    got = gpu_accel(x, v, m, "mixed", c=20.0, eps=1e-4, pair_kernel=pair_kernel)
     err = rel(got, want)
     assert np.median(err) <= MIX_MED and err.max() <= MIX_MAX, (np.median(err), err.max())
 
@@ -158,11 +164,12 @@ def test_step_force_is_accel_at_predicted_velocity():
     ctx.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_plummer16k_sampled_targets_and_hole(orc, precision):
+@pytest.mark.parametrize("precision,pair_kernel",
+                         [("fp64", "two_pass"), ("mixed", "fused"), ("mixed", "two_pass")])
+def test_plummer16k_sampled_targets_and_hole(orc, precision, pair_kernel):
     w = WORKLOADS["plummer16k"]
     x, v, m = w.state()
-    got = gpu_accel(x, v, m, precision, G=w.G, c=w.c, eps=w.eps)
+    got = gpu_accel(x, v, m, precision, G=w.G, c=w.c, eps=w.eps, pair_kernel=pair_kernel)
     rng = np.random.default_rng(5)
     targets = np.concatenate([[0, 1, w.n - 1], rng.choice(np.arange(2, w.n - 1), 300, replace=False)])
     want = orc.accel_rows(x, v, m, targets, G=w.G, c=w.c, eps=w.eps)
@@ -173,12 +180,13 @@ def test_plummer16k_sampled_targets_and_hole(orc, precision):
         assert np.median(err) <= MIX_MED and err.max() <= MIX_MAX, (np.median(err), err.max())
 
 
-def test_plummer128k_eccentric_sampled_targets(orc):
+@pytest.mark.parametrize("pair_kernel", PAIR_KERNELS)
+def test_plummer128k_eccentric_sampled_targets(orc, pair_kernel):
     """The 128k workload with 1% of stars on e = 0.9 orbits about the hole:
     sampled targets (all kinds) against the oracle, mixed precision."""
     w = WORKLOADS["plummer128k_ecc"]
     x, v, m = w.state()
-    got = gpu_accel(x, v, m, "mixed", G=w.G, c=w.c, eps=w.eps)
+    got = gpu_accel(x, v, m, "mixed", G=w.G, c=w.c, eps=w.eps, pair_kernel=pair_kernel)
     assert np.all(np.isfinite(got))
     rng = np.random.default_rng(6)
     n_ecc = int(round(w.ecc_frac * (w.n - 1)))
@@ -201,11 +209,12 @@ def test_plummer128k_newtonian_momentum_balance():
     assert np.all(np.abs(f) <= 1e-6 * scale)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_deterministic(precision):
+@pytest.mark.parametrize("precision,pair_kernel",
+                         [("fp64", "two_pass"), ("mixed", "fused"), ("mixed", "two_pass")])
+def test_deterministic(precision, pair_kernel):
     x, v, m = make_cluster(3000, 0.1, 61)
-    a1 = gpu_accel(x, v, m, precision, c=30.0, eps=1e-4)
-    a2 = gpu_accel(x, v, m, precision, c=30.0, eps=1e-4)
+    a1 = gpu_accel(x, v, m, precision, c=30.0, eps=1e-4, pair_kernel=pair_kernel)
+    a2 = gpu_accel(x, v, m, precision, c=30.0, eps=1e-4, pair_kernel=pair_kernel)
     assert np.array_equal(a1, a2)
 
 
@@ -261,7 +270,7 @@ def test_timing_counts_launches():
     pn.pn_set_timing(ctx, True)
     pn.pn_step(ctx, X, V, M, A, 1e-3, 70)    # more than the 64-entry event ring
     ms, nl = pn.pn_get_timing(ctx)
-    assert list(nl) == [70, 70, 70] and np.all(ms > 0)
+    assert list(nl) == [0, 70, 70] and np.all(ms[1:] > 0)     # fused pair kernel + near pass
     shape = pn.pn_get_launch(ctx)
     assert shape["sms"] > 0 and shape["jsplit"] >= 1
     pn.pn_set_timing(ctx, False)
