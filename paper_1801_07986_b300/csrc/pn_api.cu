@@ -236,7 +236,7 @@ pn_status pn_init(pn_ctx **out, int64_t n, const pn_params *params, int device,
     }
     if (const char *tu = std::getenv("PN_FUSED_UNROLL")) {
         const int v = std::atoi(tu);
-        if (v == 1 || v == 2)
+        if (v >= 1 && v <= 4)
             c->fused_unroll = v;
     }
     if (e == cudaSuccess)

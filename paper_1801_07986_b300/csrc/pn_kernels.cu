@@ -578,7 +578,7 @@ __device__ __forceinline__ void fused_tile(const float4 *__restrict__ sA,
 // it writes the finished segment to part[b][seg][value][256 targets]; the
 // gather kernel sums the segments of each target block in block order.
 template <int P, int UNROLL>
-__global__ void __launch_bounds__(kMixThreads, P == 4 ? 3 : (P == 2 ? 5 : 8))
+__global__ void __launch_bounds__(kMixThreads, P == 4 ? (UNROLL == 3 ? 2 : 3) : (P == 2 ? 5 : 8))
 k_fused_mixed(const float4 *__restrict__ rec, int64_t ns_pad, int ntiles, int64_t total_units,
               int segs, float eps2, double *__restrict__ part)
 {
@@ -1396,11 +1396,16 @@ static cudaError_t launch_fused_p(pn_ctx *c, const Layout &L)
 cudaError_t launch_fused(pn_ctx *c)
 {
     const Layout L = layout(c);
-    const bool u2 = c->fused_unroll == 2;
+    const int u = c->fused_unroll;
     switch (c->fused_P) {
-    case 1: return u2 ? launch_fused_p<1, 2>(c, L) : launch_fused_p<1, 1>(c, L);
-    case 4: return u2 ? launch_fused_p<4, 2>(c, L) : launch_fused_p<4, 1>(c, L);
-    default: return u2 ? launch_fused_p<2, 2>(c, L) : launch_fused_p<2, 1>(c, L);
+    case 1: return u == 2 ? launch_fused_p<1, 2>(c, L) : launch_fused_p<1, 1>(c, L);
+    case 4:
+        return u == 4 ? launch_fused_p<4, 4>(c, L)
+             : u == 3 ? launch_fused_p<4, 3>(c, L)
+             : u == 2 ? launch_fused_p<4, 2>(c, L) : launch_fused_p<4, 1>(c, L);
+    default:
+        return u == 4 ? launch_fused_p<2, 4>(c, L)
+             : u == 2 ? launch_fused_p<2, 2>(c, L) : launch_fused_p<2, 1>(c, L);
     }
 }
 
@@ -1413,11 +1418,15 @@ static cudaError_t occ_of(int *occ)
 
 cudaError_t fused_occupancy(int P, int unroll, int *occ)
 {
-    const bool u2 = unroll == 2;
     switch (P) {
-    case 1: return u2 ? occ_of<1, 2>(occ) : occ_of<1, 1>(occ);
-    case 4: return u2 ? occ_of<4, 2>(occ) : occ_of<4, 1>(occ);
-    default: return u2 ? occ_of<2, 2>(occ) : occ_of<2, 1>(occ);
+    case 1: return unroll == 2 ? occ_of<1, 2>(occ) : occ_of<1, 1>(occ);
+    case 4:
+        return unroll == 4 ? occ_of<4, 4>(occ)
+             : unroll == 3 ? occ_of<4, 3>(occ)
+             : unroll == 2 ? occ_of<4, 2>(occ) : occ_of<4, 1>(occ);
+    default:
+        return unroll == 4 ? occ_of<2, 4>(occ)
+             : unroll == 2 ? occ_of<2, 2>(occ) : occ_of<2, 1>(occ);
     }
 }
 
