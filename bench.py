@@ -202,10 +202,30 @@ def config_of(w, precision, args):
 
 # ---------------------------------------------------------------- GPU --
 
-def kernel_source_hash():
+# Source region of each measured kernel (from its first line to the next
+# section marker), so that a committed ncu traffic figure stays valid only
+# while that kernel's own source is unchanged.
+_KERNEL_REGIONS = {
+    "fused_mixed": ("// The pair terms, shared by the two-pass and the fused kernels.",
+                    "// ------------------------------------------------ pair kernels: double --"),
+}
+
+
+def kernel_source_hash(tag: str | None = None):
     h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1801_07986_b300", "csrc")
+    if tag in _KERNEL_REGIONS:
+        text = open(os.path.join(csrc, "pn_kernels.cu")).read()
+        a, b = _KERNEL_REGIONS[tag]
+        i0 = text.find(a)
+        i1 = text.find(b, i0)
+        if i0 >= 0 and i1 > i0:
+            h.update(text[i0:i1].encode())
+            hdr = open(os.path.join(csrc, "pn_internal.h")).read().splitlines()
+            h.update("\n".join(l for l in hdr if l.startswith("constexpr")).encode())
+            return h.hexdigest()[:16]
     for f in ("pn_kernels.cu", "pn_internal.h"):
-        with open(os.path.join(ROOT, "paper_1801_07986_b300", "csrc", f), "rb") as fh:
+        with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -216,7 +236,7 @@ def profiled_traffic(kernel_tag: str):
     d = os.path.join(ROOT, "profiles")
     if not os.path.isdir(d):
         return None
-    src = kernel_source_hash()
+    src = kernel_source_hash(kernel_tag)
     for f in sorted(os.listdir(d)):
         if not f.endswith(".md"):
             continue
@@ -304,6 +324,13 @@ def run_native(args, w):
                                 "near": kms[2] / ms}}
     if clocks and clocks.get("sm_mhz"):
         roof["frac_at_sampled_clock"] = achieved / (peak * clocks["sm_mhz"] / sm_max)
+    try:
+        meas = pn.pn_measure_peaks(local, stream)
+        roof["fp32_fma_microbench_tflops"] = meas["fp32_fma_tflops"]
+        roof["frac_of_fma_microbench"] = achieved / meas["fp32_fma_tflops"]
+        roof["fp64_fma_microbench_tflops"] = meas["fp64_fma_tflops"]
+    except Exception as e:  # reported, not required
+        roof["fp32_fma_microbench_error"] = str(e)[:200]
     roof["flops_per_interaction"] = FLOPS_FUSED if fused else FLOPS_PASS1 + FLOPS_PASS2
 
     line = {

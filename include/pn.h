@@ -56,6 +56,7 @@ typedef enum {
 enum { PN_FP64 = 0, PN_MIXED = 1 };            /* pn_params.precision */
 enum { PN_VPRED_END = 0, PN_VHALF = 1 };       /* pn_params.vel_mode  */
 enum { PN_PAIR_FUSED = 0, PN_PAIR_TWO_PASS = 1 };   /* pn_params.pair_kernel */
+enum { PN_KDK = 0, PN_RK4 = 1 };                   /* pn_params.integrator  */
 
 /*
  * Physical constants and evaluation mode.
@@ -85,6 +86,10 @@ enum { PN_PAIR_FUSED = 0, PN_PAIR_TWO_PASS = 1 };   /* pn_params.pair_kernel */
  *              and the hole's accumulators) and pass 2 (1PN pair sums) as
  *              two kernels.  Same sums, same epilogue.  PN_FP64 always runs
  *              the two-pass kernels.
+ *   integrator PN_KDK: kick-drift-kick leapfrog (vel_mode applies), one
+ *              force evaluation per step.  PN_RK4: classical fourth-order
+ *              Runge-Kutta, the paper's own integrator (Section 4), four
+ *              evaluations per step.
  */
 typedef struct {
     double G;
@@ -94,6 +99,7 @@ typedef struct {
     int vel_mode;
     double r_near;
     int pair_kernel;
+    int integrator;
 } pn_params;
 
 /*
@@ -123,12 +129,16 @@ pn_status pn_accel(pn_ctx *ctx, const double *x, const double *v, const double *
                    double *a);
 
 /*
- * Advance the state in place by nsteps kick-drift-kick steps of size dt:
+ * Advance the state in place by nsteps steps of size dt.
+ * PN_KDK (kick-drift-kick):
  *   v_h = v + dt/2 a;  x = x + dt v_h;
  *   v_p = v_h + dt/2 a (PN_VPRED_END) or v_h (PN_VHALF);
  *   a = A(x, v_p);  v = v_h + dt/2 a.
+ * PN_RK4: k1 = (v, a), k2 = f(y + dt/2 k1), k3 = f(y + dt/2 k2),
+ *   k4 = f(y + dt k3), y += dt/6 (k1 + 2 k2 + 2 k3 + k4), a = A(y).
  * `a` is carried state: on entry it must hold the acceleration of the entry
- * state (call pn_accel once before the first pn_step).  Device pointers.
+ * state (call pn_accel once before the first pn_step); on return it holds
+ * the acceleration of the final state.  Device pointers.
  * Errors: PN_EINVAL (NULL pointer, dt not finite or <= 0, nsteps < 0).
  */
 pn_status pn_step(pn_ctx *ctx, double *x, double *v, const double *m, double *a,
@@ -200,6 +210,15 @@ pn_status pn_get_launch(pn_ctx *ctx, int64_t out[7]);
 pn_status pn_energy_noalloc(int device, void *cuda_stream, int64_t n, double G, double c,
                             double eps, const double *x, const double *v, const double *m,
                             double *out);
+
+/*
+ * Roofline denominators measured on `device` now: out[0] FP32 FMA TFLOP/s,
+ * out[1] FP64 FMA TFLOP/s, out[2] single-precision rsqrt Gop/s, out[3] SM
+ * count (independent FMA chains on every SM, CUDA-event timed; allocates
+ * and frees a small buffer; waits for the stream).  Errors: PN_EINVAL,
+ * PN_ENOMEM, PN_ECUDA.
+ */
+pn_status pn_measure_peaks(int device, void *cuda_stream, double out[4]);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *pn_last_error(void);

@@ -16,6 +16,7 @@ Functions follow the paper (Tatekawa, arXiv:1801.07986):
 * :func:`accel_rows` the same for selected targets
 * :func:`energy`     Section 2, Eq. 7 and Eq. 8
 * :func:`step`       kick-drift-kick leapfrog, force at the predicted velocity
+* :func:`rk4_step`   the paper's classical fourth-order Runge-Kutta (Section 4)
 * :func:`newton_accel`  Newtonian accelerations alone (the c -> infinity limit)
 * :func:`eih_accel`, :func:`eih_energy`, :func:`eih_step`  general EIH
   equations (Einstein, Infeld & Hoffmann 1938) used only as a cross-check.
@@ -77,11 +78,12 @@ def _load():
             lib.orc_eih_energy.argtypes = [i64, p, p, p, d, d, p]
             lib.orc_step.argtypes = [i64, p, p, p, p, d, d, d, d, i64, ctypes.c_int]
             lib.orc_eih_step.argtypes = [i64, p, p, p, p, d, d, d, i64, ctypes.c_int]
+            lib.orc_rk4_step.argtypes = [i64, p, p, p, p, d, d, d, d, i64]
             lib.orc_set_threads.argtypes = [ctypes.c_int]
             lib.orc_get_threads.restype = ctypes.c_int
             for f in ("orc_accel", "orc_accel_rows", "orc_bh_rows", "orc_newton_accel",
                       "orc_energy", "orc_eih_accel", "orc_eih_energy", "orc_step",
-                      "orc_eih_step"):
+                      "orc_eih_step", "orc_rk4_step"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -181,6 +183,19 @@ def step(x, v, m, a, dt, nsteps, G=1.0, c=np.inf, eps=0.0, vel_mode=0):
                           dt, int(nsteps), int(vel_mode))
     if rc:
         raise ValueError(f"orc_step failed ({rc})")
+    return x, v, a
+
+
+def rk4_step(x, v, m, a, dt, nsteps, G=1.0, c=np.inf, eps=0.0):
+    """Advance copies of (x, v, a) by nsteps classical RK4 steps (Section 4);
+    `a` must hold A at the entry state; returns (x, v, a at the final state)."""
+    x, v, m, n = _state(x, v, m)
+    x, v = x.copy(), v.copy()
+    a = _f64(a, (n, 3)).copy()
+    rc = _load().orc_rk4_step(n, _ptr(x), _ptr(v), _ptr(m), _ptr(a), G, _inv_c2(c), eps,
+                              dt, int(nsteps))
+    if rc:
+        raise ValueError(f"orc_rk4_step failed ({rc})")
     return x, v, a
 
 

@@ -43,9 +43,10 @@
  *      separations are never softened.
  *  R8  In Eq. 7 the last double sum keeps i = j; the other double sums of
  *      Eqs. 7-8 run over ordered pairs i != j.
- *  R9  Integrator (the paper's Section 4 uses RK4): kick-drift-kick leapfrog
- *      whose force after the drift is evaluated at the predicted velocity
- *      v_half + (dt/2) a_old (vel_mode 0) or at v_half (vel_mode 1).
+ *  R9  Integrator: kick-drift-kick leapfrog whose force after the drift is
+ *      evaluated at the predicted velocity v_half + (dt/2) a_old (vel_mode 0)
+ *      or at v_half (vel_mode 1); and the paper's own classical RK4
+ *      (Section 4), orc_rk4_step.
  */
 #include <math.h>
 #include <stdint.h>
@@ -751,6 +752,64 @@ int orc_step(int64_t n, double *x, double *v, const double *m, double *a,
              int vel_mode)
 {
     return kdk_steps(orc_accel, n, x, v, m, a, G, inv_c2, eps, dt, nsteps, vel_mode);
+}
+
+/*
+ * nsteps of the classical fourth-order Runge-Kutta method (the paper's own
+ * integrator, Section 4) for x' = v, v' = A(x, v):
+ *   k1 = (v, A(x, v)),  k2 = f(y + dt/2 k1),  k3 = f(y + dt/2 k2),
+ *   k4 = f(y + dt k3),  y += dt/6 (k1 + 2 k2 + 2 k3 + k4).
+ * `a` holds A at the entry state (k1's acceleration) and on return holds A
+ * at the final state, so each step costs four evaluations.
+ */
+int orc_rk4_step(int64_t n, double *x, double *v, const double *m, double *a,
+                 double G, double inv_c2, double eps, double dt, int64_t nsteps)
+{
+    if (check_args(n, x, v, m) || !a || nsteps < 0 || !(dt > 0.0))
+        return 1;
+    const size_t b = sizeof(double) * 3 * (size_t)n;
+    double *xs = (double *)malloc(b), *vs = (double *)malloc(b);
+    double *k2v = (double *)malloc(b), *k3v = (double *)malloc(b), *k4v = (double *)malloc(b);
+    double *k2x = (double *)malloc(b), *k3x = (double *)malloc(b), *k4x = (double *)malloc(b);
+    double *bufs[] = {xs, vs, k2v, k3v, k4v, k2x, k3x, k4x};
+    int rc = 0;
+    for (int q = 0; q < 8; ++q)
+        if (!bufs[q])
+            rc = 2;
+    for (int64_t s = 0; s < nsteps && rc == 0; ++s) {
+        /* k2 at y + dt/2 k1 */
+        for (int64_t q = 0; q < 3 * n; ++q) {
+            xs[q] = x[q] + 0.5 * dt * v[q];
+            vs[q] = v[q] + 0.5 * dt * a[q];
+            k2x[q] = vs[q];
+        }
+        rc = orc_accel(n, xs, vs, m, G, inv_c2, eps, k2v);
+        /* k3 at y + dt/2 k2 */
+        for (int64_t q = 0; q < 3 * n && rc == 0; ++q) {
+            xs[q] = x[q] + 0.5 * dt * k2x[q];
+            vs[q] = v[q] + 0.5 * dt * k2v[q];
+            k3x[q] = vs[q];
+        }
+        if (rc == 0)
+            rc = orc_accel(n, xs, vs, m, G, inv_c2, eps, k3v);
+        /* k4 at y + dt k3 */
+        for (int64_t q = 0; q < 3 * n && rc == 0; ++q) {
+            xs[q] = x[q] + dt * k3x[q];
+            vs[q] = v[q] + dt * k3v[q];
+            k4x[q] = vs[q];
+        }
+        if (rc == 0)
+            rc = orc_accel(n, xs, vs, m, G, inv_c2, eps, k4v);
+        for (int64_t q = 0; q < 3 * n && rc == 0; ++q) {
+            x[q] = x[q] + dt / 6.0 * (v[q] + 2.0 * k2x[q] + 2.0 * k3x[q] + k4x[q]);
+            v[q] = v[q] + dt / 6.0 * (a[q] + 2.0 * k2v[q] + 2.0 * k3v[q] + k4v[q]);
+        }
+        if (rc == 0)
+            rc = orc_accel(n, x, v, m, G, inv_c2, eps, a);
+    }
+    for (int q = 0; q < 8; ++q)
+        free(bufs[q]);
+    return rc;
 }
 
 int orc_eih_step(int64_t n, double *x, double *v, const double *m, double *a,

@@ -76,6 +76,9 @@ bool params_ok(const pn_params *p)
     if (p->pair_kernel != PN_PAIR_FUSED && p->pair_kernel != PN_PAIR_TWO_PASS)
         return (void)fail(PN_EINVAL, "pair_kernel must be PN_PAIR_FUSED or PN_PAIR_TWO_PASS (got %d)",
                           p->pair_kernel), false;
+    if (p->integrator != PN_KDK && p->integrator != PN_RK4)
+        return (void)fail(PN_EINVAL, "integrator must be PN_KDK or PN_RK4 (got %d)", p->integrator),
+               false;
     return true;
 }
 
@@ -89,7 +92,7 @@ void free_all(pn_ctx *c)
 {
     void *bufs[] = {c->vp, c->mrec, c->drec, c->part, c->blk, c->glob, c->eout, c->flag,
                     c->flag_step, c->hx, c->hv, c->hm, c->ha, c->nrec, c->ndrec, c->ncount,
-                    c->nflag};
+                    c->nflag, c->rk_x, c->rk_v, c->rk_a, c->rk_sx, c->rk_sv};
     for (void *b : bufs)
         if (b)
             cudaFree(b);
@@ -149,9 +152,30 @@ pn_status evaluate(pn_ctx *c, const double *x, const double *vel, const double *
     return PN_OK;
 }
 
+pn_status run_rk4(pn_ctx *c, double *x, double *v, const double *m, double *a, double dt,
+                  int64_t nsteps)
+{
+    for (int64_t s = 0; s < nsteps; ++s) {
+        c->step_counter += 1;
+        for (int stage = 0; stage < 3; ++stage) {
+            PN_CUDA(pn::launch_rk4_stage(c, stage, x, v, a, dt), "rk4 stage launch");
+            pn_status st = evaluate(c, c->rk_x, c->rk_v, m, c->rk_a, nullptr, 0.0);
+            if (st != PN_OK)
+                return st;
+        }
+        PN_CUDA(pn::launch_rk4_stage(c, 3, x, v, a, dt), "rk4 stage launch");
+        pn_status st = evaluate(c, x, v, m, a, nullptr, 0.0);
+        if (st != PN_OK)
+            return st;
+    }
+    return PN_OK;
+}
+
 pn_status run_steps(pn_ctx *c, double *x, double *v, const double *m, double *a, double dt,
                     int64_t nsteps)
 {
+    if (c->p.integrator == PN_RK4)
+        return run_rk4(c, x, v, m, a, dt, nsteps);
     for (int64_t s = 0; s < nsteps; ++s) {
         c->step_counter += 1;
         PN_CUDA(pn::launch_kick_drift(c, x, v, a, dt), "kick-drift launch");
@@ -271,6 +295,11 @@ pn_status pn_init(pn_ctx **out, int64_t n, const pn_params *params, int device,
 
     struct Req { void **p; size_t bytes; } req[] = {
         {(void **)&c->vp, sizeof(double) * 3 * (size_t)n},
+        {(void **)&c->rk_x, sizeof(double) * 3 * (size_t)n},
+        {(void **)&c->rk_v, sizeof(double) * 3 * (size_t)n},
+        {(void **)&c->rk_a, sizeof(double) * 3 * (size_t)n},
+        {(void **)&c->rk_sx, sizeof(double) * 3 * (size_t)n},
+        {(void **)&c->rk_sv, sizeof(double) * 3 * (size_t)n},
         {(void **)&c->mrec, sizeof(float4) * 5 * (size_t)np},
         {(void **)&c->drec, sizeof(double4_32a) * 4 * (size_t)np},
         {(void **)&c->part, sizeof(double) * (size_t)part},

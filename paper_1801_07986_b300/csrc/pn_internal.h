@@ -91,6 +91,10 @@ struct pn_ctx {
     unsigned long long *flag_step;   // first step index with a non-finite value
     int64_t step_counter;
 
+    // RK4 stage buffers (n x 3 each): stage position / velocity, stage
+    // acceleration, and the running k-sums of x and v
+    double *rk_x, *rk_v, *rk_a, *rk_sx, *rk_sv;
+
     // device copies used by pn_step_host
     double *hx, *hv, *hm, *ha;
 
@@ -103,6 +107,8 @@ namespace pn {
 // O(n) kernels and pair kernels (pn_kernels.cu).  Each returns the first
 // launch error (cudaSuccess if none).
 cudaError_t launch_kick_drift(pn_ctx *c, double *x, double *v, const double *a, double dt);
+cudaError_t launch_rk4_stage(pn_ctx *c, int stage, double *x, double *v, const double *a,
+                             double dt);
 cudaError_t launch_prologue(pn_ctx *c, const double *x, const double *vel, const double *m,
                             bool energy_records);
 cudaError_t launch_pass1(pn_ctx *c);

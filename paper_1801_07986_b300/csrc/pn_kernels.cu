@@ -126,6 +126,39 @@ __global__ void k_kick_drift(int64_t n3, double *__restrict__ x, double *__restr
     }
 }
 
+// Classical RK4 (the paper's Section 4 integrator) for x' = v, v' = A, in
+// stages around the force evaluations.  Buffers: (xs, vs) the stage state,
+// ka the stage acceleration just evaluated, (sx, sv) the running k-sums.
+//   stage 0: sx = v, sv = a;              xs = x + h/2 v,  vs = v + h/2 a
+//   stage 1: sx += 2 vs, sv += 2 ka;      xs = x + h/2 vs, vs = v + h/2 ka
+//   stage 2: sx += 2 vs, sv += 2 ka;      xs = x + h vs,   vs = v + h ka
+//   stage 3: x += h/6 (sx + vs),  v += h/6 (sv + ka)
+__global__ void k_rk4_stage(int stage, int64_t n3, double *__restrict__ x, double *__restrict__ v,
+                            const double *__restrict__ a, const double *__restrict__ ka,
+                            double *__restrict__ xs, double *__restrict__ vs,
+                            double *__restrict__ sx, double *__restrict__ sv, double h)
+{
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n3;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        if (stage == 0) {
+            sx[q] = v[q];
+            sv[q] = a[q];
+            xs[q] = x[q] + 0.5 * h * v[q];
+            vs[q] = v[q] + 0.5 * h * a[q];
+        } else if (stage < 3) {
+            const double kx = vs[q], kv = ka[q];
+            sx[q] += 2.0 * kx;
+            sv[q] += 2.0 * kv;
+            const double f = stage == 1 ? 0.5 * h : h;
+            xs[q] = x[q] + f * kx;
+            vs[q] = v[q] + f * kv;
+        } else {
+            x[q] = x[q] + h / 6.0 * (sx[q] + vs[q]);
+            v[q] = v[q] + h / 6.0 * (sv[q] + ka[q]);
+        }
+    }
+}
+
 // ------------------------------------------------------------ prologue --
 
 // Per star slot t (star j = t + 1; slots >= ns are padding with zero mass):
@@ -1264,6 +1297,18 @@ cudaError_t launch_kick_drift(pn_ctx *c, double *x, double *v, const double *a, 
                                                                     : 4 * (int64_t)c->sm_count;
     k_kick_drift<<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(n3, x, v, a, c->vp, 0.5 * dt, dt,
                                                                c->p.vel_mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rk4_stage(pn_ctx *c, int stage, double *x, double *v, const double *a,
+                             double dt)
+{
+    const int64_t n3 = 3 * c->n;
+    const int64_t nb = glue_blocks(n3) < 4 * (int64_t)c->sm_count ? glue_blocks(n3)
+                                                                    : 4 * (int64_t)c->sm_count;
+    k_rk4_stage<<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(stage, n3, x, v, a, c->rk_a,
+                                                              c->rk_x, c->rk_v, c->rk_sx,
+                                                              c->rk_sv, dt);
     return cudaGetLastError();
 }
 

@@ -28,12 +28,14 @@ STATUS_NAMES = {0: "PN_OK", 1: "PN_EINVAL", 2: "PN_ENOMEM", 3: "PN_ECUDA", 4: "P
 PN_FP64, PN_MIXED = 0, 1
 PN_VPRED_END, PN_VHALF = 0, 1
 PN_PAIR_FUSED, PN_PAIR_TWO_PASS = 0, 1
+PN_KDK, PN_RK4 = 0, 1
 PN_NOALLOC_MAX_BODIES = 16384
 _PRECISION = {"fp64": PN_FP64, "mixed": PN_MIXED, PN_FP64: PN_FP64, PN_MIXED: PN_MIXED}
 _VEL_MODE = {"vpred_end": PN_VPRED_END, "vhalf": PN_VHALF, PN_VPRED_END: PN_VPRED_END,
              PN_VHALF: PN_VHALF}
 _PAIR = {"fused": PN_PAIR_FUSED, "two_pass": PN_PAIR_TWO_PASS, PN_PAIR_FUSED: PN_PAIR_FUSED,
          PN_PAIR_TWO_PASS: PN_PAIR_TWO_PASS}
+_INTEGRATOR = {"kdk": PN_KDK, "rk4": PN_RK4, PN_KDK: PN_KDK, PN_RK4: PN_RK4}
 
 
 class PNError(RuntimeError):
@@ -47,7 +49,8 @@ class PNError(RuntimeError):
 class _Params(ctypes.Structure):
     _fields_ = [("G", ctypes.c_double), ("c", ctypes.c_double), ("eps", ctypes.c_double),
                 ("precision", ctypes.c_int), ("vel_mode", ctypes.c_int),
-                ("r_near", ctypes.c_double), ("pair_kernel", ctypes.c_int)]
+                ("r_near", ctypes.c_double), ("pair_kernel", ctypes.c_int),
+                ("integrator", ctypes.c_int)]
 
 
 # Default radius (in the state's length unit) inside which stars are summed
@@ -86,6 +89,7 @@ def _load():
                 "pn_get_timing": [P, P, P],
                 "pn_get_launch": [P, P],
                 "pn_energy_noalloc": [I, P, I64, D, D, D, P, P, P, P],
+                "pn_measure_peaks": [I, P, P],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -114,15 +118,18 @@ def pn_version() -> int:
     return int(_load().pn_version())
 
 
-def _params(G, c, eps, precision, vel_mode, r_near=R_NEAR_DEFAULT, pair_kernel="fused") -> _Params:
+def _params(G, c, eps, precision, vel_mode, r_near=R_NEAR_DEFAULT, pair_kernel="fused",
+            integrator="kdk") -> _Params:
     if precision not in _PRECISION:
         raise ValueError(f"precision must be 'fp64' or 'mixed', got {precision!r}")
     if vel_mode not in _VEL_MODE:
         raise ValueError(f"vel_mode must be 'vpred_end' or 'vhalf', got {vel_mode!r}")
     if pair_kernel not in _PAIR:
         raise ValueError(f"pair_kernel must be 'fused' or 'two_pass', got {pair_kernel!r}")
+    if integrator not in _INTEGRATOR:
+        raise ValueError(f"integrator must be 'kdk' or 'rk4', got {integrator!r}")
     return _Params(float(G), float(c), float(eps), _PRECISION[precision], _VEL_MODE[vel_mode],
-                   float(r_near), _PAIR[pair_kernel])
+                   float(r_near), _PAIR[pair_kernel], _INTEGRATOR[integrator])
 
 
 class Context:
@@ -161,13 +168,14 @@ def _torch_stream(device, stream):
 
 def pn_init(n: int, G: float = 1.0, c: float = math.inf, eps: float = 0.0,
             precision="mixed", vel_mode="vpred_end", device: int | None = None,
-            stream=None, r_near: float = R_NEAR_DEFAULT, pair_kernel="fused") -> Context:
+            stream=None, r_near: float = R_NEAR_DEFAULT, pair_kernel="fused",
+            integrator="kdk") -> Context:
     """Create a context for n bodies (body 0 = the hole)."""
     lib = _load()
     if device is None:
         import torch
         device = torch.cuda.current_device()
-    p = _params(G, c, eps, precision, vel_mode, r_near, pair_kernel)
+    p = _params(G, c, eps, precision, vel_mode, r_near, pair_kernel, integrator)
     h = ctypes.c_void_p()
     _check(lib.pn_init(ctypes.byref(h), int(n), ctypes.byref(p), int(device),
                        ctypes.c_void_p(_torch_stream(device, stream))))
@@ -175,13 +183,14 @@ def pn_init(n: int, G: float = 1.0, c: float = math.inf, eps: float = 0.0,
 
 
 def pn_set_params(ctx: Context, G=None, c=None, eps=None, precision=None, vel_mode=None,
-                  r_near=None, pair_kernel=None) -> None:
+                  r_near=None, pair_kernel=None, integrator=None) -> None:
     q = ctx.params
     p = _params(q.G if G is None else G, q.c if c is None else c, q.eps if eps is None else eps,
                 q.precision if precision is None else precision,
                 q.vel_mode if vel_mode is None else vel_mode,
                 q.r_near if r_near is None else r_near,
-                q.pair_kernel if pair_kernel is None else pair_kernel)
+                q.pair_kernel if pair_kernel is None else pair_kernel,
+                q.integrator if integrator is None else integrator)
     _check(_load().pn_set_params(ctx.handle, ctypes.byref(p)))
     ctx.params = p
 
@@ -263,6 +272,18 @@ def pn_energy_noalloc(x, v, m, out, G: float = 1.0, c: float = math.inf, eps: fl
         else getattr(stream, "cuda_stream", stream)
     _check(_load().pn_energy_noalloc(int(device), ctypes.c_void_p(st), n, float(G), float(c),
                                      float(eps), *args))
+
+
+def pn_measure_peaks(device: int = 0, stream=None) -> dict:
+    """FP32 / FP64 FMA TFLOP/s and rsqrt Gop/s measured now on `device`."""
+    import torch
+    out = np.zeros(4)
+    st = torch.cuda.current_stream(device).cuda_stream if stream is None \
+        else getattr(stream, "cuda_stream", stream)
+    _check(_load().pn_measure_peaks(int(device), ctypes.c_void_p(st),
+                                    out.ctypes.data_as(ctypes.c_void_p)))
+    return {"fp32_fma_tflops": out[0], "fp64_fma_tflops": out[1], "rsqrt_gops": out[2],
+            "sms": int(out[3])}
 
 
 def pn_sync(ctx: Context) -> None:

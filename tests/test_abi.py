@@ -48,9 +48,10 @@ def test_header_compiles_as_c():
     assert r.returncode == 0, r.stderr
 
 
-def _params(G=1.0, c=50.0, eps=1e-4, precision=1, vel_mode=0, r_near=0.05, pair_kernel=0):
+def _params(G=1.0, c=50.0, eps=1e-4, precision=1, vel_mode=0, r_near=0.05, pair_kernel=0,
+            integrator=0):
     from paper_1801_07986_b300.pn import _Params
-    return _Params(G, c, eps, precision, vel_mode, r_near, pair_kernel)
+    return _Params(G, c, eps, precision, vel_mode, r_near, pair_kernel, integrator)
 
 
 @pytest.mark.parametrize("n,kw,msg", [
@@ -67,6 +68,7 @@ def _params(G=1.0, c=50.0, eps=1e-4, precision=1, vel_mode=0, r_near=0.05, pair_
     (100, {"r_near": -1.0}, "r_near"),
     (100, {"r_near": float("nan")}, "r_near"),
     (100, {"pair_kernel": 2}, "pair_kernel"),
+    (100, {"integrator": 5}, "integrator"),
 ])
 def test_init_rejects_bad_arguments_on_host(lib, n, kw, msg):
     h = ctypes.c_void_p()
@@ -97,7 +99,7 @@ def test_null_arguments(lib):
 
 def test_injected_allocation_failure():
     code = ("import ctypes; from paper_1801_07986_b300 import pn; lib = pn._load();"
-            "p = pn._Params(1.0, 50.0, 1e-4, 1, 0, 0.05, 0); h = ctypes.c_void_p();"
+            "p = pn._Params(1.0, 50.0, 1e-4, 1, 0, 0.05, 0, 0); h = ctypes.c_void_p();"
             "print(lib.pn_init(ctypes.byref(h), 100, ctypes.byref(p), 0, None),"
             " lib.pn_last_error().decode())")
     env = dict(os.environ, PN_FAIL_ALLOC="1", PYTHONPATH=ROOT)

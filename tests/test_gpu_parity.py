@@ -145,6 +145,33 @@ def test_steps_fp64_match_oracle(orc, vel_mode, mode_id):
     ctx.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_rk4_steps_match_oracle(orc, precision):
+    """The paper's own integrator (RK4, Section 4): 10 steps of the 1k
+    workload against the oracle's RK4."""
+    w = WORKLOADS["plummer1k_fp64"]
+    x, v, m = w.state()
+    ctx = pn.pn_init(w.n, G=w.G, c=w.c, eps=w.eps, precision=precision, integrator="rk4",
+                     device=0)
+    X, V, M = dev(x), dev(v), dev(m)
+    A = torch.empty_like(X)
+    pn.pn_accel(ctx, X, V, M, A)
+    a0 = orc.accel(x, v, m, G=w.G, c=w.c, eps=w.eps)
+    pn.pn_step(ctx, X, V, M, A, w.dt, 10)
+    pn.pn_sync(ctx)
+    xo, vo, ao = orc.rk4_step(x, v, m, a0, w.dt, 10, G=w.G, c=w.c, eps=w.eps)
+    xg, vg, ag = X.cpu().numpy(), V.cpu().numpy(), A.cpu().numpy()
+    if precision == "fp64":
+        assert np.abs(xg - xo).max() < 1e-12
+        assert rel(ag, ao).max() < 1e-9
+    else:
+        # single-precision pair sums: the state drifts by ~dt^2 * 1e-7 |a| per step
+        assert np.abs(xg - xo).max() < 1e-10
+        err = rel(ag, ao)
+        assert np.median(err) < 1e-6 and err.max() < 1e-4
+    ctx.close()
+
+
 def test_step_force_is_accel_at_predicted_velocity():
     """After one step, a equals pn_accel at (x_new, v_half + dt/2 a_old)."""
     x, v, m = make_cluster(1000, 0.1, 51)

@@ -376,6 +376,22 @@ def test_softening_acts_only_between_stars(orc):
     assert np.min(_rel(b1[1:], b0[1:])) > 0.1
 
 
+def test_rk4_is_fourth_order(orc):
+    """The paper's integrator (Section 4): self-convergence ratio 2^4 = 16."""
+    x, v, m = _orbiting_stars(2, 1e-3, seed=4)
+    c = 4.0
+    a = orc.accel(x, v, m, c=c)
+    T = 2.0
+    xs = []
+    for nst in (50, 100, 200):
+        xx, vv, aa = orc.rk4_step(x, v, m, a, T / nst, nst, c=c)
+        xs.append(xx)
+    r = np.linalg.norm(xs[0] - xs[1]) / np.linalg.norm(xs[1] - xs[2])
+    assert 14.0 < r < 18.0, r
+    # and its final acceleration is the force at the final state
+    np.testing.assert_allclose(aa, orc.accel(xx, vv, m, c=c), rtol=0, atol=0)
+
+
 # ------------------------------------------------------------ invariances --
 
 def test_rotation_and_translation_invariance(orc):
