@@ -112,8 +112,31 @@ typedef struct {
 pn_status pn_init(pn_ctx **ctx, int64_t n, const pn_params *params, int device,
                   void *cuda_stream);
 
-/* Replace the parameters (G, c, eps, precision, vel_mode) without
- * reallocating.  Errors: PN_EINVAL. */
+/* Per-cluster constants of a batched context (see pn_init_batched). */
+typedef struct {
+    double G;
+    double c;      /* INFINITY allowed */
+    double eps;
+} pn_cluster;
+
+/*
+ * A context for many independent clusters evaluated together (one launch of
+ * each kernel covers all of them; the pair kernel balances their uneven
+ * work over the GPU).  Cluster k holds bodies [offsets[k], offsets[k+1]) of
+ * the state arrays, its hole first; offsets[0] = 0 and each cluster has at
+ * least 2 bodies.  `clusters[k]` gives its G, c and eps (NULL: every cluster
+ * takes params->G, c, eps); the mode fields (precision, vel_mode, r_near,
+ * pair_kernel, integrator) come from `params`.  Every entry point then works
+ * on the concatenated arrays; pn_energy writes 8 values per cluster.
+ * Errors: as pn_init.
+ */
+pn_status pn_init_batched(pn_ctx **ctx, int n_clusters, const int64_t *offsets,
+                          const pn_cluster *clusters, const pn_params *params, int device,
+                          void *cuda_stream);
+
+/* Replace the parameters without reallocating; on a batched context every
+ * cluster takes the new G, c, eps and r_near.  Waits for the stream.
+ * Errors: PN_EINVAL. */
 pn_status pn_set_params(pn_ctx *ctx, const pn_params *params);
 
 /* Enqueue subsequent work on another stream of the same device. */
@@ -145,6 +168,28 @@ pn_status pn_step(pn_ctx *ctx, double *x, double *v, const double *m, double *a,
                   double dt, int64_t nsteps);
 
 /*
+ * pn_step captured into one CUDA graph and launched as a whole: the first
+ * call for a given (x, v, m, a, dt, nsteps) records the nsteps steps (every
+ * kernel launch of every step) into a graph; later calls with the same
+ * arguments replay it with a single launch.  The step index in non-finite
+ * reports is the index within the captured sequence.  Kernel timing
+ * (pn_set_timing) does not see launches inside the graph.
+ * Errors: as pn_step, plus PN_ECUDA if capture or instantiation fails.
+ */
+pn_status pn_step_graph(pn_ctx *ctx, double *x, double *v, const double *m, double *a,
+                        double dt, int64_t nsteps);
+
+/*
+ * Autotuner of the fused pair kernel's launch shape (targets per thread x
+ * source-loop unroll): times each candidate on the given state (a is
+ * overwritten with A(x, v)) and keeps the fastest; results are cached per
+ * workload size bucket for the process.  out (may be NULL): [0] targets per
+ * thread, [1] unroll, [2] 1 if the result came from the cache.  Waits.
+ */
+pn_status pn_tune(pn_ctx *ctx, const double *x, const double *v, const double *m, double *a,
+                  int64_t out[3]);
+
+/*
  * pn_step on HOST arrays: copies x, v, m, a to device buffers owned by the
  * context, runs nsteps steps, copies x, v, a back, and waits.  The arrays
  * may be pageable or pinned host memory.  Errors: as pn_step, plus
@@ -156,14 +201,14 @@ pn_status pn_step_host(pn_ctx *ctx, double *x, double *v, const double *m, doubl
 /*
  * 1PN energy (Eq. 7) and momentum (Eq. 8) of the state (x, v), evaluated in
  * double precision whatever pn_params.precision says.  Device pointers in,
- * host array out[8]:
+ * host array out[8] (out[8 n_clusters] on a batched context, 8 per cluster):
  *   out[0]  Newtonian energy         out[1]    1/c^2 part of Eq. 7
  *   out[2..4] Newtonian momentum     out[5..7] 1/c^2 part of Eq. 8
  * (E = out[0] + out[1], P = out[2..4] + out[5..7]).  Waits for the stream.
  * Errors: PN_EINVAL, PN_ENONFINITE (pending from earlier steps).
  */
 pn_status pn_energy(pn_ctx *ctx, const double *x, const double *v, const double *m,
-                    double out[8]);
+                    double *out);
 
 /* Wait for the context's stream; PN_ENONFINITE if a non-finite acceleration
  * was produced since the last report (the flag is then cleared). */

@@ -7,6 +7,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 
 #include "pn_internal.h"
@@ -82,20 +84,50 @@ bool params_ok(const pn_params *p)
     return true;
 }
 
-void set_params(pn_ctx *c, const pn_params *p)
+double inv_c2_of(double c) { return std::isinf(c) ? 0.0 : 1.0 / (c * c); }
+
+// Copies the host cluster table to the device (stream-ordered, then waits:
+// table updates are rare and must not race with queued kernels).
+pn_status upload_clusters(pn_ctx *c)
+{
+    PN_CUDA(cudaMemcpyAsync(c->d_clu, c->hclu, sizeof(pn::Clu) * (size_t)c->nclu,
+                            cudaMemcpyHostToDevice, c->stream), "upload cluster table");
+    PN_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
+    return PN_OK;
+}
+
+// Mode fields for every cluster; G, c, eps and r_near for every cluster too
+// when `all_physics` (single-cluster contexts and pn_set_params).
+void set_params(pn_ctx *c, const pn_params *p, bool all_physics)
 {
     c->p = *p;
-    c->inv_c2 = std::isinf(p->c) ? 0.0 : 1.0 / (p->c * p->c);
+    c->any_near = false;
+    for (int k = 0; k < c->nclu; ++k) {
+        if (all_physics) {
+            c->hclu[k].G = p->G;
+            c->hclu[k].inv_c2 = inv_c2_of(p->c);
+            c->hclu[k].eps2 = p->eps * p->eps;
+            c->hclu[k].r_near = p->r_near > 0.0 ? p->r_near : -1.0;
+        }
+        if (c->hclu[k].r_near > 0.0)
+            c->any_near = true;
+    }
 }
 
 void free_all(pn_ctx *c)
 {
     void *bufs[] = {c->vp, c->mrec, c->drec, c->part, c->blk, c->glob, c->eout, c->flag,
                     c->flag_step, c->hx, c->hv, c->hm, c->ha, c->nrec, c->ndrec, c->ncount,
-                    c->nflag, c->rk_x, c->rk_v, c->rk_a, c->rk_sx, c->rk_sv};
+                    c->nflag, c->rk_x, c->rk_v, c->rk_a, c->rk_sx, c->rk_sv, c->d_clu,
+                    c->blk_clu};
     for (void *b : bufs)
         if (b)
             cudaFree(b);
+    if (c->graph_exec)
+        cudaGraphExecDestroy(c->graph_exec);
+    if (c->cap_stream)
+        cudaStreamDestroy(c->cap_stream);
+    delete[] c->hclu;
     if (c->timing_on || c->tm.ev0[0][0]) {
         for (int k = 0; k < pn::Timing::kKernels; ++k)
             for (int r = 0; r < pn::Timing::kRing; ++r) {
@@ -208,19 +240,28 @@ int pn_version(void) { return 100; }
 
 const char *pn_last_error(void) { return g_err; }
 
-pn_status pn_init(pn_ctx **out, int64_t n, const pn_params *params, int device,
-                  void *cuda_stream)
+// Context for one or more clusters: cluster k holds bodies
+// [off[k], off[k+1]) of the state arrays, its hole first.  Per-cluster G, c,
+// eps come from `cp` (NULL: all from `params`).
+static pn_status init_common(pn_ctx **out, int nclu, const int64_t *off, const pn_cluster *cp,
+                             const pn_params *params, int device, void *cuda_stream)
 {
-    if (!out)
-        return fail(PN_EINVAL, "ctx output pointer is NULL");
-    *out = nullptr;
-    if (n < 2)
-        return fail(PN_EINVAL, "n must be >= 2 (the hole and at least one star), got %lld",
-                    (long long)n);
-    if (n > ((int64_t)1 << 31))
-        return fail(PN_EINVAL, "n = %lld exceeds the supported 2^31 bodies", (long long)n);
     if (!params_ok(params))
         return PN_EINVAL;
+    const int64_t n = off[nclu];
+    if (n > ((int64_t)1 << 31) - (int64_t)nclu * pn::kPad)
+        return fail(PN_EINVAL, "n = %lld exceeds the supported 2^31 bodies", (long long)n);
+    for (int k = 0; k < nclu; ++k) {
+        if (off[k + 1] - off[k] < 2)
+            return fail(PN_EINVAL, "cluster %d has %lld bodies (need the hole and a star)", k,
+                        (long long)(off[k + 1] - off[k]));
+        if (cp) {
+            const pn_cluster &q = cp[k];
+            if (!(std::isfinite(q.G) && q.G > 0.0) || !(q.c > 0.0) ||
+                !(std::isfinite(q.eps) && q.eps >= 0.0))
+                return fail(PN_EINVAL, "cluster %d: need G > 0, c > 0 (or INFINITY), eps >= 0", k);
+        }
+    }
     const char *inj = std::getenv("PN_FAIL_ALLOC");
     if (inj && inj[0] == '1')
         return fail(PN_ENOMEM, "allocation failure injected by PN_FAIL_ALLOC");
@@ -241,13 +282,40 @@ pn_status pn_init(pn_ctx **out, int64_t n, const pn_params *params, int device,
     pn_ctx *c = new (std::nothrow) pn_ctx();
     if (!c)
         return fail(PN_ENOMEM, "host allocation of the context failed");
+    c->hclu = new (std::nothrow) pn::Clu[nclu]();
+    if (!c->hclu) {
+        delete c;
+        return fail(PN_ENOMEM, "host allocation of the cluster table failed");
+    }
     c->n = n;
-    c->ns = n - 1;
-    c->ns_pad = (c->ns + pn::kPad - 1) / pn::kPad * pn::kPad;
-    set_params(c, params);
+    c->nclu = nclu;
     c->device = device;
     c->stream = (cudaStream_t)cuda_stream;
     c->sm_count = sms;
+    int64_t slot = 0, nearc = 0, maxp = 0;
+    for (int k = 0; k < nclu; ++k) {
+        pn::Clu &C = c->hclu[k];
+        C.body0 = off[k];
+        C.ns = off[k + 1] - off[k] - 1;
+        C.ns_pad = (C.ns + pn::kPad - 1) / pn::kPad * pn::kPad;
+        C.slot0 = slot;
+        C.near0 = nearc;
+        slot += C.ns_pad;
+        nearc += C.ns_pad + pn::kNearTile;
+        if (C.ns_pad > maxp)
+            maxp = C.ns_pad;
+        const double G = cp ? cp[k].G : params->G, cc = cp ? cp[k].c : params->c,
+                     eps = cp ? cp[k].eps : params->eps;
+        C.G = G;
+        C.inv_c2 = inv_c2_of(cc);
+        C.eps2 = eps * eps;
+        C.r_near = params->r_near > 0.0 ? params->r_near : -1.0;
+    }
+    c->S = slot;
+    c->NC = nearc;
+    c->max_ns_pad = maxp;
+    set_params(c, params, false);
+
     int occ_mix = 0, occ_f64 = 0, occ_fused = 0;
     cudaError_t e = pn::occupancy(&occ_mix, &occ_f64);
     // fused-kernel variant; PN_FUSED_TARGETS / PN_FUSED_UNROLL override (tuning)
@@ -266,32 +334,32 @@ pn_status pn_init(pn_ctx **out, int64_t n, const pn_params *params, int device,
     if (e == cudaSuccess)
         e = pn::fused_occupancy(c->fused_P, c->fused_unroll, &occ_fused);
     if (e != cudaSuccess) {
+        delete[] c->hclu;
         delete c;
         return fail(PN_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
     }
-    pn::shapes(c->ns_pad, sms, occ_mix, occ_f64, &c->mix, &c->f64);
+    pn::shapes(c->S, c->max_ns_pad, sms, occ_mix, occ_f64, &c->mix, &c->f64);
     c->fused_occ = occ_fused > 0 ? occ_fused : 1;
     c->fused_G = (int64_t)c->fused_occ * sms;
-    c->fused_segs = (int)pn::fused_segments(c->ns_pad, c->fused_G, c->fused_P);
+    c->fused_units = pn::fused_units(c->hclu, nclu, c->fused_P, c->hclu);
 
-    const int64_t np = c->ns_pad;
-    int64_t part = (int64_t)c->mix.jsplit * (pn::kP1Vals + pn::kP2Vals) * np;
-    const int64_t part_f64 = (int64_t)c->f64.jsplit * (pn::kP1Vals + pn::kP2Vals) * np;
-    const int64_t part_e = (int64_t)c->f64.jsplit * pn::kEVals * np;
+    const int64_t S = c->S;
+    int64_t part = (int64_t)c->mix.jsplit * (pn::kP1Vals + pn::kP2Vals) * S;
+    const int64_t part_f64 = (int64_t)c->f64.jsplit * (pn::kP1Vals + pn::kP2Vals) * S;
     if (part_f64 > part)
         part = part_f64;
-    if (part_e > part)
-        part = part_e;
-    part += (int64_t)pn::kNearVals * np;   // near-pass partials after both passes
-    const int64_t part_fused = (int64_t)(pn::kP1Vals + pn::kP2Vals + pn::kNearVals) * np +
-                               c->fused_G * c->fused_segs * pn::kFusedVals *
-                                   (pn::kMixThreads * c->fused_P);
+    if ((int64_t)pn::kEVals * S > part)
+        part = (int64_t)pn::kEVals * S;
+    part += (int64_t)pn::kNearVals * S;   // near-pass partials after both passes
+    // fused layout, for the largest target block (4 targets per thread)
+    const int64_t ti_max = pn::kMixThreads * 4;
+    const int64_t part_fused = (int64_t)(pn::kP1Vals + pn::kP2Vals + pn::kNearVals) * S +
+                               (S / pn::kMixThreads + c->fused_G) * pn::kFusedVals * ti_max;
     if (part_fused > part)
         part = part_fused;
     c->part_len = part;
-    const int64_t nglue = (np + pn::kGlueThreads - 1) / pn::kGlueThreads;
+    const int64_t nglue = S / pn::kGlueThreads;
     c->blk_len = nglue * pn::kGlobVals;
-    c->nnear_cap = np + pn::kNearTile;
 
     struct Req { void **p; size_t bytes; } req[] = {
         {(void **)&c->vp, sizeof(double) * 3 * (size_t)n},
@@ -300,18 +368,20 @@ pn_status pn_init(pn_ctx **out, int64_t n, const pn_params *params, int device,
         {(void **)&c->rk_a, sizeof(double) * 3 * (size_t)n},
         {(void **)&c->rk_sx, sizeof(double) * 3 * (size_t)n},
         {(void **)&c->rk_sv, sizeof(double) * 3 * (size_t)n},
-        {(void **)&c->mrec, sizeof(float4) * 5 * (size_t)np},
-        {(void **)&c->drec, sizeof(double4_32a) * 4 * (size_t)np},
+        {(void **)&c->mrec, sizeof(float4) * 5 * (size_t)S},
+        {(void **)&c->drec, sizeof(double4_32a) * 4 * (size_t)S},
         {(void **)&c->part, sizeof(double) * (size_t)part},
         {(void **)&c->blk, sizeof(double) * (size_t)c->blk_len},
-        {(void **)&c->glob, sizeof(double) * 16},
-        {(void **)&c->nrec, sizeof(float4) * 4 * (size_t)c->nnear_cap},
-        {(void **)&c->ndrec, sizeof(double4_32a) * 3 * (size_t)c->nnear_cap},
-        {(void **)&c->ncount, sizeof(int) * (size_t)(1 + nglue)},
-        {(void **)&c->nflag, (size_t)np},
-        {(void **)&c->eout, sizeof(double) * 8},
+        {(void **)&c->glob, sizeof(double) * pn::kGlobVals * (size_t)nclu},
+        {(void **)&c->nrec, sizeof(float4) * 4 * (size_t)c->NC},
+        {(void **)&c->ndrec, sizeof(double4_32a) * 3 * (size_t)c->NC},
+        {(void **)&c->ncount, sizeof(int) * (size_t)(nclu + nglue)},
+        {(void **)&c->nflag, (size_t)S},
+        {(void **)&c->eout, sizeof(double) * 8 * (size_t)nclu},
         {(void **)&c->flag, sizeof(int)},
         {(void **)&c->flag_step, sizeof(unsigned long long)},
+        {(void **)&c->d_clu, sizeof(pn::Clu) * (size_t)nclu},
+        {(void **)&c->blk_clu, sizeof(int) * (size_t)nglue},
     };
     for (auto &r : req) {
         e = cudaMalloc(r.p, r.bytes);
@@ -323,17 +393,63 @@ pn_status pn_init(pn_ctx **out, int64_t n, const pn_params *params, int device,
                         cudaGetErrorString(e));
         }
     }
+    int *hb = new (std::nothrow) int[(size_t)nglue];
+    if (!hb) {
+        free_all(c);
+        delete c;
+        return fail(PN_ENOMEM, "host allocation failed");
+    }
+    for (int k = 0; k < nclu; ++k)
+        for (int64_t b = c->hclu[k].slot0 / pn::kGlueThreads;
+             b < (c->hclu[k].slot0 + c->hclu[k].ns_pad) / pn::kGlueThreads; ++b)
+            hb[b] = k;
     const unsigned long long none = ULLONG_MAX;
-    e = cudaMemset(c->flag, 0, sizeof(int));
+    e = cudaMemcpy(c->blk_clu, hb, sizeof(int) * (size_t)nglue, cudaMemcpyHostToDevice);
+    delete[] hb;
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_clu, c->hclu, sizeof(pn::Clu) * (size_t)nclu, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemset(c->flag, 0, sizeof(int));
     if (e == cudaSuccess)
         e = cudaMemcpy(c->flag_step, &none, sizeof none, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemset(c->ncount, 0, sizeof(int) * (size_t)(nclu + nglue));
     if (e != cudaSuccess) {
         free_all(c);
         delete c;
-        return fail(PN_ECUDA, "initialising the error flag: %s", cudaGetErrorString(e));
+        return fail(PN_ECUDA, "initialising the context: %s", cudaGetErrorString(e));
     }
     *out = c;
     return ok();
+}
+
+pn_status pn_init(pn_ctx **out, int64_t n, const pn_params *params, int device,
+                  void *cuda_stream)
+{
+    if (!out)
+        return fail(PN_EINVAL, "ctx output pointer is NULL");
+    *out = nullptr;
+    if (n < 2)
+        return fail(PN_EINVAL, "n must be >= 2 (the hole and at least one star), got %lld",
+                    (long long)n);
+    if (!params_ok(params))
+        return PN_EINVAL;
+    const int64_t off[2] = {0, n};
+    return init_common(out, 1, off, nullptr, params, device, cuda_stream);
+}
+
+pn_status pn_init_batched(pn_ctx **out, int n_clusters, const int64_t *offsets,
+                          const pn_cluster *clusters, const pn_params *params, int device,
+                          void *cuda_stream)
+{
+    if (!out)
+        return fail(PN_EINVAL, "ctx output pointer is NULL");
+    *out = nullptr;
+    if (n_clusters < 1 || !offsets)
+        return fail(PN_EINVAL, "need n_clusters >= 1 and an offsets array");
+    if (offsets[0] != 0)
+        return fail(PN_EINVAL, "offsets[0] must be 0");
+    return init_common(out, n_clusters, offsets, clusters, params, device, cuda_stream);
 }
 
 pn_status pn_set_params(pn_ctx *c, const pn_params *params)
@@ -342,8 +458,11 @@ pn_status pn_set_params(pn_ctx *c, const pn_params *params)
         return PN_EINVAL;
     if (!params_ok(params))
         return PN_EINVAL;
-    set_params(c, params);
-    return ok();
+    DeviceGuard g(c->device);
+    PN_CUDA(g.err, "cudaSetDevice");
+    set_params(c, params, true);
+    pn_status st = upload_clusters(c);
+    return st == PN_OK ? ok() : st;
 }
 
 pn_status pn_set_stream(pn_ctx *c, void *cuda_stream)
@@ -385,6 +504,61 @@ pn_status pn_step(pn_ctx *c, double *x, double *v, const double *m, double *a, d
     PN_CUDA(g.err, "cudaSetDevice");
     pn_status st = run_steps(c, x, v, m, a, dt, nsteps);
     return st == PN_OK ? ok() : st;
+}
+
+pn_status pn_step_graph(pn_ctx *c, double *x, double *v, const double *m, double *a, double dt,
+                        int64_t nsteps)
+{
+    if (check_ctx(c) != PN_OK)
+        return PN_EINVAL;
+    if (!x || !v || !m || !a)
+        return fail(PN_EINVAL, "pn_step_graph: NULL array");
+    if (!(std::isfinite(dt) && dt > 0.0))
+        return fail(PN_EINVAL, "pn_step_graph: dt must be finite and > 0 (got %g)", dt);
+    if (nsteps < 1)
+        return fail(PN_EINVAL, "pn_step_graph: nsteps must be >= 1");
+    DeviceGuard g(c->device);
+    PN_CUDA(g.err, "cudaSetDevice");
+    const void *key[4] = {x, v, m, a};
+    const bool same = c->graph_exec && c->graph_dt == dt && c->graph_steps == nsteps &&
+                      std::memcmp(key, c->graph_key, sizeof key) == 0;
+    if (!same) {
+        if (c->graph_exec) {
+            cudaGraphExecDestroy(c->graph_exec);
+            c->graph_exec = nullptr;
+        }
+        if (!c->cap_stream)
+            PN_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking),
+                    "capture stream");
+        cudaStream_t user = c->stream;
+        c->stream = c->cap_stream;
+        c->capturing = true;
+        cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+        pn_status st = e == cudaSuccess ? run_steps(c, x, v, m, a, dt, nsteps) : PN_ECUDA;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
+        c->stream = user;
+        c->capturing = false;
+        if (e != cudaSuccess || e2 != cudaSuccess || st != PN_OK) {
+            if (graph)
+                cudaGraphDestroy(graph);
+            if (st != PN_OK)
+                return st;
+            return fail(PN_ECUDA, "graph capture: %s",
+                        cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        e = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            c->graph_exec = nullptr;
+            return fail(PN_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        }
+        std::memcpy(c->graph_key, key, sizeof key);
+        c->graph_dt = dt;
+        c->graph_steps = nsteps;
+    }
+    PN_CUDA(cudaGraphLaunch(c->graph_exec, c->stream), "graph launch");
+    return ok();
 }
 
 pn_status pn_step_host(pn_ctx *c, double *x, double *v, const double *m, double *a, double dt,
@@ -429,7 +603,7 @@ pn_status pn_step_host(pn_ctx *c, double *x, double *v, const double *m, double 
     return st == PN_OK ? ok() : st;
 }
 
-pn_status pn_energy(pn_ctx *c, const double *x, const double *v, const double *m, double out[8])
+pn_status pn_energy(pn_ctx *c, const double *x, const double *v, const double *m, double *out)
 {
     if (check_ctx(c) != PN_OK)
         return PN_EINVAL;
@@ -438,8 +612,8 @@ pn_status pn_energy(pn_ctx *c, const double *x, const double *v, const double *m
     DeviceGuard g(c->device);
     PN_CUDA(g.err, "cudaSetDevice");
     PN_CUDA(pn::launch_energy(c, x, v, m), "energy launch");
-    PN_CUDA(cudaMemcpyAsync(out, c->eout, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->stream),
-            "copy energy out");
+    PN_CUDA(cudaMemcpyAsync(out, c->eout, sizeof(double) * 8 * (size_t)c->nclu,
+                            cudaMemcpyDeviceToHost, c->stream), "copy energy out");
     pn_status st = report_flag(c);
     return st == PN_OK ? ok() : st;
 }
@@ -518,6 +692,112 @@ pn_status pn_get_launch(pn_ctx *c, int64_t out[7])
     out[4] = fused ? c->fused_G : s.jsplit;
     out[5] = fused ? c->fused_occ : s.occupancy;
     out[6] = c->sm_count;
+    return ok();
+}
+
+namespace {
+// Autotuner results per (workload bucket): the fused-kernel variant found
+// fastest, keyed by the number of work units (log2) and cluster count class.
+struct TuneKey {
+    int bucket, many;
+    bool operator<(const TuneKey &o) const
+    {
+        return bucket < o.bucket || (bucket == o.bucket && many < o.many);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune;
+
+pn_status apply_variant(pn_ctx *c, int P, int unroll)
+{
+    int occ = 0;
+    PN_CUDA(pn::fused_occupancy(P, unroll, &occ), "occupancy");
+    c->fused_P = P;
+    c->fused_unroll = unroll;
+    c->fused_occ = occ > 0 ? occ : 1;
+    c->fused_G = (int64_t)c->fused_occ * c->sm_count;
+    c->fused_units = pn::fused_units(c->hclu, c->nclu, P, c->hclu);
+    if (c->graph_exec) {              // the captured graph holds the old launch shape
+        cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = nullptr;
+    }
+    return upload_clusters(c);
+}
+}  // namespace
+
+pn_status pn_tune(pn_ctx *c, const double *x, const double *v, const double *m, double *a,
+                  int64_t out[3])
+{
+    if (check_ctx(c) != PN_OK)
+        return PN_EINVAL;
+    if (!x || !v || !m || !a)
+        return fail(PN_EINVAL, "pn_tune: NULL array");
+    DeviceGuard g(c->device);
+    PN_CUDA(g.err, "cudaSetDevice");
+    static const int cand[][2] = {{2, 1}, {2, 2}, {4, 1}, {4, 2}};
+    int64_t work = 0;                         // pair work of all clusters, in tiles^2
+    for (int k = 0; k < c->nclu; ++k)
+        work += (c->hclu[k].ns_pad / pn::kMixTile) * (c->hclu[k].ns_pad / pn::kMixTile);
+    int bucket = 0;
+    for (int64_t u = work; u > 1; u >>= 1)
+        ++bucket;
+    const TuneKey key{bucket, c->nclu > 1 ? 1 : 0};
+    int bestP = c->fused_P, bestU = c->fused_unroll;
+    double best_ms = -1.0;
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            bestP = it->second.first;
+            bestU = it->second.second;
+            cached = true;
+        }
+    }
+    if (!cached && c->p.precision == PN_MIXED && c->p.pair_kernel == PN_PAIR_FUSED) {
+        cudaEvent_t e0, e1;
+        PN_CUDA(cudaEventCreate(&e0), "event");
+        PN_CUDA(cudaEventCreate(&e1), "event");
+        const int was_timing = c->timing_on;
+        c->timing_on = 0;
+        for (auto &cv : cand) {
+            pn_status st = apply_variant(c, cv[0], cv[1]);
+            if (st != PN_OK)
+                return st;
+            PN_CUDA(cudaMemcpyAsync(c->vp, v, sizeof(double) * 3 * (size_t)c->n,
+                                    cudaMemcpyDeviceToDevice, c->stream), "copy velocities");
+            st = evaluate(c, x, c->vp, m, a, nullptr, 0.0);   // warm-up
+            if (st != PN_OK)
+                return st;
+            PN_CUDA(cudaEventRecord(e0, c->stream), "event");
+            for (int r = 0; r < 2 && st == PN_OK; ++r)
+                st = evaluate(c, x, c->vp, m, a, nullptr, 0.0);
+            PN_CUDA(cudaEventRecord(e1, c->stream), "event");
+            PN_CUDA(cudaEventSynchronize(e1), "event sync");
+            if (st != PN_OK)
+                return st;
+            float ms = 0.0f;
+            PN_CUDA(cudaEventElapsedTime(&ms, e0, e1), "event time");
+            if (best_ms < 0.0 || ms < best_ms) {
+                best_ms = ms;
+                bestP = cv[0];
+                bestU = cv[1];
+            }
+        }
+        c->timing_on = was_timing;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune[key] = {bestP, bestU};
+    }
+    pn_status st = apply_variant(c, bestP, bestU);
+    if (st != PN_OK)
+        return st;
+    if (out) {
+        out[0] = bestP;
+        out[1] = bestU;
+        out[2] = cached ? 1 : 0;
+    }
     return ok();
 }
 

@@ -38,6 +38,18 @@ constexpr int kGlobVals = 13;
 // Per-block values of the energy epilogue.
 constexpr int kEBlockVals = 9;     // eN, ePN, pN (3), pPN (3), sum m/R
 
+// One cluster of the state: a hole (body body0) and ns stars after it.
+struct Clu {
+    int64_t body0;     // index of the cluster's hole in x, v, m, a
+    int64_t ns;        // number of stars
+    int64_t slot0;     // first star slot in the record arrays (multiple of kPad)
+    int64_t ns_pad;    // star slots, padded to a multiple of kPad
+    int64_t unit0;     // first work unit of the fused kernel
+    int64_t near0;     // first entry of the cluster's near-record slice
+    double G, inv_c2, eps2;
+    double r_near;     // near-source radius; <= 0 disables the split
+};
+
 struct Shape {
     int threads, targets, tile;     // as above
     int64_t nblk_i;                 // blocks along targets
@@ -59,9 +71,16 @@ struct Timing {
 }  // namespace pn
 
 struct pn_ctx {
-    int64_t n, ns, ns_pad;
+    int64_t n;               // bodies in the state arrays (all clusters)
+    int nclu;                // clusters
+    int64_t S;               // star slots of all clusters (multiple of kPad)
+    int64_t max_ns_pad;      // largest cluster's padded star count
+    int64_t NC;              // entries per near-record array (all clusters)
+    pn::Clu *hclu;           // host copy of the cluster table
+    pn::Clu *d_clu;          // device cluster table
+    int *blk_clu;            // device: cluster of each 256-slot block
+    bool any_near;           // some cluster has r_near > 0
     pn_params p;
-    double inv_c2;
     int device;
     cudaStream_t stream;
     int sm_count;
@@ -70,23 +89,22 @@ struct pn_ctx {
     int fused_unroll;        // source-loop unroll of the fused kernel (1 or 2)
     int fused_occ;           // resident fused-kernel blocks per SM
     int64_t fused_G;         // persistent blocks of the fused kernel
-    int fused_segs;          // segments per persistent block (upper bound)
+    int64_t fused_units;     // work units of the fused kernel (all clusters)
 
     // scratch, all owned by the context
     double *vp;          // n x 3: velocity at which the force is evaluated
-    float4 *mrec;        // mixed records: 5 arrays of ns_pad float4
-    double4_32a *drec;       // double records: 4 arrays of ns_pad double4_32a
-    double *part;        // pair partial sums [jsplit][vals][ns_pad]
+    float4 *mrec;        // mixed records: 5 arrays of S float4
+    double4_32a *drec;   // double records: 4 arrays of S double4_32a
+    double *part;        // pair partial sums [jsplit][vals][S] (+ fused segments)
     int64_t part_len;    // doubles in `part`
     double *blk;         // per-block partial sums of the O(n) kernels
     int64_t blk_len;
-    double *glob;        // global sums (kGlobVals doubles)
-    float4 *nrec;        // mixed near-source records: 4 arrays of ns_pad + kNearTile
-    double4_32a *ndrec;  // double near-source records: 4 arrays of ns_pad + kNearTile
-    int *ncount;         // [0] near-star count; [1 + b] prefix offset of prologue block b
+    double *glob;        // global sums [nclu][kGlobVals]
+    float4 *nrec;        // mixed near-source records: 4 arrays of NC
+    double4_32a *ndrec;  // double near-source records: 3 arrays of NC
+    int *ncount;         // [k] near-star count of cluster k; [nclu + b] prefix offset of block b
     unsigned char *nflag;   // per star slot: 1 if a near source
-    int64_t nnear_cap;   // entries per near-record array
-    double *eout;        // 8 doubles: energy / momentum result
+    double *eout;        // [nclu][8]: energy / momentum results
     int *flag;           // [0] non-finite flag
     unsigned long long *flag_step;   // first step index with a non-finite value
     int64_t step_counter;
@@ -99,7 +117,15 @@ struct pn_ctx {
     double *hx, *hv, *hm, *ha;
 
     int timing_on;
+    bool capturing;          // a CUDA graph is being captured
     pn::Timing tm;
+
+    // CUDA graph of pn_step_graph: captured once per (arrays, dt, nsteps)
+    cudaStream_t cap_stream;
+    cudaGraphExec_t graph_exec;
+    const void *graph_key[4];
+    double graph_dt;
+    int64_t graph_steps;
 };
 
 namespace pn {
@@ -117,18 +143,18 @@ cudaError_t launch_near(pn_ctx *c);
 cudaError_t launch_epilogue(pn_ctx *c, const double *x, const double *vel, const double *m,
                             double *a, double *v, double half_dt, unsigned long long step);
 cudaError_t launch_energy(pn_ctx *c, const double *x, const double *v, const double *m);
-cudaError_t launch_energy_on(cudaStream_t st, int64_t ns, int64_t ns_pad, const double *x,
-                             const double *v, const double *m, double G, double inv_c2,
-                             double eps, int jsplit_max, double4_32a *drec, double *part,
+cudaError_t launch_energy_on(cudaStream_t st, int64_t S, const Clu *clu, const double *x,
+                             const double *v, const double *m, double4_32a *drec, double *part,
                              double *blk, double *out);
 
 pn_status set_error(pn_status s, const char *fmt, ...);
 
-void shapes(int64_t ns_pad, int sm_count, int occ_mix, int occ_f64, Shape *mix, Shape *f64);
+void shapes(int64_t S, int64_t max_ns_pad, int sm_count, int occ_mix, int occ_f64, Shape *mix,
+            Shape *f64);
 cudaError_t occupancy(int *occ_mix, int *occ_f64);
 cudaError_t fused_occupancy(int P, int unroll, int *occ);
 cudaError_t launch_fused(pn_ctx *c);
 bool use_fused(const pn_ctx *c);
-int64_t fused_segments(int64_t ns_pad, int64_t G, int P);
+int64_t fused_units(const Clu *h, int nclu, int P, Clu *out);
 
 }  // namespace pn

@@ -13,6 +13,10 @@
 //                     and the hole's three-body terms from pass 1
 //   hole       O(n)   deterministic reduction of the hole's terms
 //
+// The state may hold several independent clusters (a hole and its stars
+// each); every kernel finds its cluster in a small table (struct Clu), so a
+// single cluster is the one-entry case.
+//
 // The pair sums are regrouped algebraically (exactly, in real arithmetic)
 // so that each pair costs one reciprocal square root and a handful of
 // FMAs; the groupings are stated next to each kernel.  x_ij = x_i - x_j,
@@ -161,13 +165,25 @@ __global__ void k_rk4_stage(int stage, int64_t n3, double *__restrict__ x, doubl
 
 // ------------------------------------------------------------ prologue --
 
-// Per star slot t (star j = t + 1; slots >= ns are padding with zero mass):
+// Clusters: the state arrays hold one or more independent clusters, each a
+// hole (body clu.body0) followed by clu.ns stars.  Star slots of all
+// clusters are laid end to end, each cluster padded to a multiple of kPad
+// (zero-mass far-away dummies), so every 256-slot block and every target
+// block lies inside one cluster; blk_clu[slot / 256] names it (nullptr:
+// a single cluster, index 0).
+__device__ __forceinline__ int cluster_of_block(const int *__restrict__ blk_clu, int64_t b)
+{
+    return blk_clu ? blk_clu[b] : 0;
+}
+
+// Per star slot t of cluster k (star j = body0 + 1 + (t - slot0); slots past
+// the cluster's stars are padding):
 //   d_j = x_j - x_hole, R_j = |d_j|,
 //   c_j = G M (3/(2 R_j) + eps^2/(4 R_j^3)),   e_j = G M d_j/(2 R_j^3),
 //   w_j = m_j d_j / R_j^3.
 // A star with R_j < r_near is a near source: its c_j, e_j and w_j are left
 // out of the main records and of the far sums below (the near pass sums its
-// hole-relative cross terms pair by pair instead).  Global sums:
+// hole-relative cross terms pair by pair instead).  Per-block sums:
 //   Q = sum m_j v_j, W = sum w_j (all), W_far = sum_far w_j,
 //   SA_far = sum_far 5 m_j/(4 R_j), SB_far = sum_far m_j (R_j^2 + eps^2)/(4 R_j^3),
 //   Phi = sum m_j / R_j, and the number of near stars.
@@ -176,86 +192,86 @@ __global__ void k_rk4_stage(int stage, int64_t n3, double *__restrict__ x, doubl
 // Energy records (double): A = (d, m), B = (v, 0).
 template <int MODE>   // 0 mixed, 1 double, 2 energy
 __global__ void __launch_bounds__(kGlueThreads)
-k_prologue(int64_t ns, int64_t ns_pad, const double *__restrict__ x,
-           const double *__restrict__ vel, const double *__restrict__ m, double G,
-           double eps2, double r_near, float4 *__restrict__ mrec,
+k_prologue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_clu,
+           const double *__restrict__ x, const double *__restrict__ vel,
+           const double *__restrict__ m, float4 *__restrict__ mrec,
            double4_32a *__restrict__ drec, unsigned char *__restrict__ nflag,
            double *__restrict__ blk)
 {
     __shared__ double sh[kGlobVals][kGlueThreads];
     const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
+    const Clu C = clu[cluster_of_block(blk_clu, blockIdx.x)];
+    const int64_t lt = t - C.slot0;
+    const double G = C.G, eps2 = C.eps2;
     double g[kGlobVals];
 #pragma unroll
     for (int k = 0; k < kGlobVals; ++k)
         g[k] = 0.0;
-    if (t < ns_pad) {
-        if (t < ns) {
-            const int64_t j = t + 1;
-            const double d0 = x[3 * j] - x[0], d1 = x[3 * j + 1] - x[1], d2 = x[3 * j + 2] - x[2];
-            const double R2 = d0 * d0 + d1 * d1 + d2 * d2;
-            const double R = sqrt(R2);
-            const double iR = 1.0 / R;
-            const double iR3 = iR * iR * iR;
-            const double mj = m[j];
-            const double M = m[0];
-            const double v0 = vel[3 * j], v1 = vel[3 * j + 1], v2 = vel[3 * j + 2];
-            const bool near = MODE != 2 && R < r_near;
-            const double far = near ? 0.0 : 1.0;
-            const double cj = far * G * M * (1.5 * iR + 0.25 * eps2 * iR3);
-            const double ef = far * 0.5 * G * M * iR3;
-            const double wf = mj * iR3;
-            const double c3 = cj / 1.5, e3 = ef / 1.5;
-            if (MODE == 0) {
-                const float h0 = (float)d0, h1 = (float)d1, h2 = (float)d2;
-                mrec[t] = make_float4(h0, h1, h2, (float)mj);
-                mrec[ns_pad + t] = make_float4((float)(d0 - (double)h0), (float)(d1 - (double)h1),
-                                               (float)(d2 - (double)h2), (float)R2);
-                mrec[2 * ns_pad + t] = make_float4((float)v0, (float)v1, (float)v2, (float)c3);
-                mrec[3 * ns_pad + t] =
-                    make_float4((float)(e3 * d0), (float)(e3 * d1), (float)(e3 * d2), 0.0f);
-                mrec[4 * ns_pad + t] = make_float4((float)(far * wf * d0), (float)(far * wf * d1),
-                                                   (float)(far * wf * d2), 0.0f);
-            } else if (MODE == 1) {
-                drec[t] = make_double4_32a(d0, d1, d2, mj);
-                drec[ns_pad + t] = make_double4_32a(v0, v1, v2, R2);
-                drec[2 * ns_pad + t] = make_double4_32a(e3 * d0, e3 * d1, e3 * d2, c3);
-                drec[3 * ns_pad + t] =
-                    make_double4_32a(far * wf * d0, far * wf * d1, far * wf * d2, 0.0);
-            } else {
-                drec[t] = make_double4_32a(d0, d1, d2, mj);
-                drec[ns_pad + t] = make_double4_32a(v0, v1, v2, 0.0);
-            }
-            if (MODE != 2)
-                nflag[t] = near ? 1 : 0;
-            g[0] = mj * v0;
-            g[1] = mj * v1;
-            g[2] = mj * v2;
-            g[3] = wf * d0;
-            g[4] = wf * d1;
-            g[5] = wf * d2;
-            g[6] = far * wf * d0;
-            g[7] = far * wf * d1;
-            g[8] = far * wf * d2;
-            g[9] = far * 1.25 * mj * iR;
-            g[10] = far * 0.25 * mj * (R2 + eps2) * iR3;
-            g[11] = mj * iR;
-            g[12] = near ? 1.0 : 0.0;
+    if (lt < C.ns) {
+        const int64_t j = C.body0 + 1 + lt, h = C.body0;
+        const double d0 = x[3 * j] - x[3 * h], d1 = x[3 * j + 1] - x[3 * h + 1],
+                     d2 = x[3 * j + 2] - x[3 * h + 2];
+        const double R2 = d0 * d0 + d1 * d1 + d2 * d2;
+        const double R = sqrt(R2);
+        const double iR = 1.0 / R;
+        const double iR3 = iR * iR * iR;
+        const double mj = m[j];
+        const double M = m[h];
+        const double v0 = vel[3 * j], v1 = vel[3 * j + 1], v2 = vel[3 * j + 2];
+        const bool near = MODE != 2 && R < C.r_near;
+        const double far = near ? 0.0 : 1.0;
+        const double cj = far * G * M * (1.5 * iR + 0.25 * eps2 * iR3);
+        const double ef = far * 0.5 * G * M * iR3;
+        const double wf = mj * iR3;
+        const double c3 = cj / 1.5, e3 = ef / 1.5;
+        if (MODE == 0) {
+            const float h0 = (float)d0, h1 = (float)d1, h2 = (float)d2;
+            mrec[t] = make_float4(h0, h1, h2, (float)mj);
+            mrec[S + t] = make_float4((float)(d0 - (double)h0), (float)(d1 - (double)h1),
+                                      (float)(d2 - (double)h2), (float)R2);
+            mrec[2 * S + t] = make_float4((float)v0, (float)v1, (float)v2, (float)c3);
+            mrec[3 * S + t] = make_float4((float)(e3 * d0), (float)(e3 * d1), (float)(e3 * d2), 0.0f);
+            mrec[4 * S + t] = make_float4((float)(far * wf * d0), (float)(far * wf * d1),
+                                          (float)(far * wf * d2), 0.0f);
+        } else if (MODE == 1) {
+            drec[t] = make_double4_32a(d0, d1, d2, mj);
+            drec[S + t] = make_double4_32a(v0, v1, v2, R2);
+            drec[2 * S + t] = make_double4_32a(e3 * d0, e3 * d1, e3 * d2, c3);
+            drec[3 * S + t] = make_double4_32a(far * wf * d0, far * wf * d1, far * wf * d2, 0.0);
         } else {
-            // padding: zero mass far away, distinct positions
-            const double px = 1.0e4 + (double)(t - ns);
-            if (MODE == 0) {
-                mrec[t] = make_float4((float)px, 0.0f, 0.0f, 0.0f);
-                for (int k = 1; k < 5; ++k)
-                    mrec[k * ns_pad + t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            } else {
-                drec[t] = make_double4_32a(px, 0.0, 0.0, 0.0);
-                const int nk = MODE == 1 ? 4 : 2;
-                for (int k = 1; k < nk; ++k)
-                    drec[k * ns_pad + t] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
-            }
-            if (MODE != 2)
-                nflag[t] = 0;
+            drec[t] = make_double4_32a(d0, d1, d2, mj);
+            drec[S + t] = make_double4_32a(v0, v1, v2, 0.0);
         }
+        if (MODE != 2)
+            nflag[t] = near ? 1 : 0;
+        g[0] = mj * v0;
+        g[1] = mj * v1;
+        g[2] = mj * v2;
+        g[3] = wf * d0;
+        g[4] = wf * d1;
+        g[5] = wf * d2;
+        g[6] = far * wf * d0;
+        g[7] = far * wf * d1;
+        g[8] = far * wf * d2;
+        g[9] = far * 1.25 * mj * iR;
+        g[10] = far * 0.25 * mj * (R2 + eps2) * iR3;
+        g[11] = mj * iR;
+        g[12] = near ? 1.0 : 0.0;
+    } else {
+        // padding: zero mass far away, distinct positions
+        const double px = 1.0e4 + (double)(lt - C.ns);
+        if (MODE == 0) {
+            mrec[t] = make_float4((float)px, 0.0f, 0.0f, 0.0f);
+            for (int k = 1; k < 5; ++k)
+                mrec[k * S + t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        } else {
+            drec[t] = make_double4_32a(px, 0.0, 0.0, 0.0);
+            const int nk = MODE == 1 ? 4 : 2;
+            for (int k = 1; k < nk; ++k)
+                drec[k * S + t] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+        }
+        if (MODE != 2)
+            nflag[t] = 0;
     }
     if (MODE == 2)
         return;   // block-uniform
@@ -264,90 +280,101 @@ k_prologue(int64_t ns, int64_t ns_pad, const double *__restrict__ x,
         blk[(int64_t)blockIdx.x * kGlobVals + threadIdx.x] = sh[threadIdx.x][0];
 }
 
-// Totals of the prologue's block sums (fixed order), the exclusive prefix
-// of the per-block near-star counts (ncount[1 + b]), their total
-// (ncount[0]), and zero-mass padding of the near-record arrays up to the
-// next multiple of kNearTile.
+// One block per cluster: totals of its prologue blocks (fixed order) into
+// glob[k][.], the exclusive prefix of its per-block near-star counts into
+// ncount[nclu + b], the count into ncount[k], and zero-mass padding of its
+// near-record slice up to the next multiple of kNearTile.
 template <int MODE>   // 0 mixed, 1 double
 __global__ void __launch_bounds__(kGlueThreads)
-k_global_sums(const double *__restrict__ blk, int64_t nblk, double *__restrict__ glob,
-              int *__restrict__ ncount, float4 *__restrict__ nrec,
-              double4_32a *__restrict__ ndrec, int64_t ncap)
+k_global_sums(const Clu *__restrict__ clu, int nclu, const double *__restrict__ blk,
+              double *__restrict__ glob, int *__restrict__ ncount, float4 *__restrict__ nrec,
+              double4_32a *__restrict__ ndrec, int64_t NC)
 {
     __shared__ double sh[kGlobVals][kGlueThreads];
     __shared__ int scan[kGlueThreads];
-    sum_blocks<kGlobVals>(blk, nblk, sh);
+    const int k = blockIdx.x;
+    const Clu C = clu[k];
+    const int64_t b0 = C.slot0 / kGlueThreads;
+    const int64_t nblk = C.ns_pad / kGlueThreads;
+    const double *cb = blk + b0 * kGlobVals;
+    sum_blocks<kGlobVals>(cb, nblk, sh);
     if (threadIdx.x < kGlobVals)
-        glob[threadIdx.x] = sh[threadIdx.x][0];
+        glob[(int64_t)k * kGlobVals + threadIdx.x] = sh[threadIdx.x][0];
     // exclusive prefix of block counts: each thread owns a contiguous chunk
     const int64_t chunk = (nblk + kGlueThreads - 1) / kGlueThreads;
-    const int64_t b0 = threadIdx.x * chunk;
-    const int64_t b1 = b0 + chunk < nblk ? b0 + chunk : nblk;
+    const int64_t c0 = threadIdx.x * chunk;
+    const int64_t c1 = c0 + chunk < nblk ? c0 + chunk : nblk;
     int local = 0;
-    for (int64_t b = b0; b < b1; ++b)
-        local += (int)blk[b * kGlobVals + 12];
+    for (int64_t b = c0; b < c1; ++b)
+        local += (int)cb[b * kGlobVals + 12];
     scan[threadIdx.x] = local;
     __syncthreads();
     if (threadIdx.x == 0) {
         int run = 0;
-        for (int k = 0; k < kGlueThreads; ++k) {
-            const int c = scan[k];
-            scan[k] = run;
-            run += c;
+        for (int q = 0; q < kGlueThreads; ++q) {
+            const int cnt = scan[q];
+            scan[q] = run;
+            run += cnt;
         }
-        ncount[0] = run;
+        ncount[k] = run;
     }
     __syncthreads();
     int run = scan[threadIdx.x];
-    for (int64_t b = b0; b < b1; ++b) {
-        ncount[1 + b] = run;
-        run += (int)blk[b * kGlobVals + 12];
+    for (int64_t b = c0; b < c1; ++b) {
+        ncount[nclu + b0 + b] = run;
+        run += (int)cb[b * kGlobVals + 12];
     }
     __syncthreads();
-    const int nn = ncount[0];
+    const int nn = ncount[k];
     const int npad = (int)((nn + kNearTile - 1) / kNearTile * kNearTile);
-    for (int q = nn + threadIdx.x; q < npad && q < ncap; q += kGlueThreads) {
+    for (int q = nn + threadIdx.x; q < npad; q += kGlueThreads) {
+        const int64_t e = C.near0 + q;
         const double px = 1.0e4 + (double)(q - nn);
         if (MODE == 0) {
-            nrec[q] = make_float4((float)px, 0.0f, 0.0f, 0.0f);
-            nrec[ncap + q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            nrec[2 * ncap + q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            nrec[3 * ncap + q] = make_float4(1.0f, __int_as_float(-1), 0.0f, 0.0f);
+            nrec[e] = make_float4((float)px, 0.0f, 0.0f, 0.0f);
+            nrec[NC + e] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            nrec[2 * NC + e] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            nrec[3 * NC + e] = make_float4(1.0f, __int_as_float(-1), 0.0f, 0.0f);
         } else {
-            ndrec[q] = make_double4_32a(px, 0.0, 0.0, 0.0);
-            ndrec[ncap + q] = make_double4_32a(0.0, 0.0, 1.0, -1.0);
-            ndrec[2 * ncap + q] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+            ndrec[e] = make_double4_32a(px, 0.0, 0.0, 0.0);
+            ndrec[NC + e] = make_double4_32a(0.0, 0.0, 1.0, -1.0);
+            ndrec[2 * NC + e] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
         }
     }
 }
 
-// Near-source records in slot order (deterministic block scan of the flags):
+// Near-source records in slot order within each cluster (deterministic
+// block scan of the flags), slice of cluster k starting at clu.near0:
 //   mixed  NA = (hi(d), m)  NB = (lo(d), 5/(4R))  NC = (w, 1/(4R^3))
-//          ND = (R^2 + eps^2, slot bits, 0, 0)
-//   double NA = (d, m)  NB = (5/(4R), 1/(4R^3), R^2 + eps^2, slot)  NC = (w, 0)
+//          ND = (R^2 + eps^2, global slot bits, 0, 0)
+//   double NA = (d, m)  NB = (5/(4R), 1/(4R^3), R^2 + eps^2, global slot)  NC = (w, 0)
 template <int MODE>
 __global__ void __launch_bounds__(kGlueThreads)
-k_near_scatter(int64_t ns, const double *__restrict__ x, const double *__restrict__ m,
-               double eps2, const unsigned char *__restrict__ nflag,
-               const int *__restrict__ ncount, float4 *__restrict__ nrec,
-               double4_32a *__restrict__ ndrec, int64_t ncap)
+k_near_scatter(const Clu *__restrict__ clu, int nclu, const int *__restrict__ blk_clu,
+               const double *__restrict__ x, const double *__restrict__ m,
+               const unsigned char *__restrict__ nflag, const int *__restrict__ ncount,
+               float4 *__restrict__ nrec, double4_32a *__restrict__ ndrec, int64_t NC)
 {
     __shared__ int wsum[kGlueThreads / 32];
     const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
-    const bool near = t < ns && nflag[t];
+    const Clu C = clu[cluster_of_block(blk_clu, blockIdx.x)];
+    const int64_t lt = t - C.slot0;
+    const bool near = lt < C.ns && nflag[t];
     const unsigned mask = __ballot_sync(0xffffffffu, near);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0)
         wsum[warp] = __popc(mask);
     __syncthreads();
     int before = 0;
-    for (int k = 0; k < warp; ++k)
-        before += wsum[k];
+    for (int q = 0; q < warp; ++q)
+        before += wsum[q];
     if (!near)
         return;
-    const int64_t pos = ncount[1 + blockIdx.x] + before + __popc(mask & ((1u << lane) - 1u));
-    const int64_t j = t + 1;
-    const double d0 = x[3 * j] - x[0], d1 = x[3 * j + 1] - x[1], d2 = x[3 * j + 2] - x[2];
+    const int64_t pos = C.near0 + ncount[nclu + blockIdx.x] + before +
+                        __popc(mask & ((1u << lane) - 1u));
+    const int64_t j = C.body0 + 1 + lt, h = C.body0;
+    const double d0 = x[3 * j] - x[3 * h], d1 = x[3 * j + 1] - x[3 * h + 1],
+                 d2 = x[3 * j + 2] - x[3 * h + 2];
     const double R2 = d0 * d0 + d1 * d1 + d2 * d2;
     const double R = sqrt(R2);
     const double iR = 1.0 / R;
@@ -357,14 +384,14 @@ k_near_scatter(int64_t ns, const double *__restrict__ x, const double *__restric
     if (MODE == 0) {
         const float h0 = (float)d0, h1 = (float)d1, h2 = (float)d2;
         nrec[pos] = make_float4(h0, h1, h2, (float)mj);
-        nrec[ncap + pos] = make_float4((float)(d0 - (double)h0), (float)(d1 - (double)h1),
-                                       (float)(d2 - (double)h2), (float)A);
-        nrec[2 * ncap + pos] = make_float4((float)(w * d0), (float)(w * d1), (float)(w * d2), (float)B);
-        nrec[3 * ncap + pos] = make_float4((float)(R2 + eps2), __int_as_float((int)t), 0.0f, 0.0f);
+        nrec[NC + pos] = make_float4((float)(d0 - (double)h0), (float)(d1 - (double)h1),
+                                     (float)(d2 - (double)h2), (float)A);
+        nrec[2 * NC + pos] = make_float4((float)(w * d0), (float)(w * d1), (float)(w * d2), (float)B);
+        nrec[3 * NC + pos] = make_float4((float)(R2 + C.eps2), __int_as_float((int)t), 0.0f, 0.0f);
     } else {
         ndrec[pos] = make_double4_32a(d0, d1, d2, mj);
-        ndrec[ncap + pos] = make_double4_32a(A, B, R2 + eps2, (double)t);
-        ndrec[2 * ncap + pos] = make_double4_32a(w * d0, w * d1, w * d2, 0.0);
+        ndrec[NC + pos] = make_double4_32a(A, B, R2 + C.eps2, (double)t);
+        ndrec[2 * NC + pos] = make_double4_32a(w * d0, w * d1, w * d2, 0.0);
     }
 }
 
@@ -496,16 +523,24 @@ __device__ __forceinline__ void pass2_tile(const float4 *__restrict__ sA,
     }
 }
 
+// Two-pass grid: (target blocks of all clusters, source splits).  Split s of a
+// target block in cluster k sweeps tiles [s tps_k, (s+1) tps_k) of its own
+// cluster, tps_k = ceil(ntiles_k / jsplit); splits past the cluster's tiles
+// write zeros.
 template <int PASS>
 __global__ void __launch_bounds__(kMixThreads)
-k_pass_mixed(const float4 *__restrict__ rec, int64_t ns_pad, int ntiles, int tps, float eps2,
-             double *__restrict__ part)
+k_pass_mixed(const float4 *__restrict__ rec, int64_t S, const Clu *__restrict__ clu,
+             const int *__restrict__ blk_clu, double *__restrict__ part)
 {
     constexpr int NV = PASS == 1 ? kP1Vals : kP2Vals;
     constexpr int NA = PASS == 1 ? 2 : 5;
     constexpr int TI = kMixThreads * kMixTargets;
     __shared__ float4 sh[NA][kMixTile];
     const int64_t t0 = (int64_t)blockIdx.x * TI;
+    const Clu C = clu[cluster_of_block(blk_clu, t0 / kGlueThreads)];
+    const float eps2 = (float)C.eps2;
+    const int ntiles = (int)(C.ns_pad / kMixTile);
+    const int tps = (ntiles + (int)gridDim.y - 1) / (int)gridDim.y;
 
     MixTarget tg[kMixTargets];
     int64_t ti[kMixTargets];
@@ -513,12 +548,12 @@ k_pass_mixed(const float4 *__restrict__ rec, int64_t ns_pad, int ntiles, int tps
     for (int p = 0; p < kMixTargets; ++p) {
         ti[p] = t0 + p * kMixThreads + threadIdx.x;
         const float4 A = rec[ti[p]];
-        const float4 B = rec[ns_pad + ti[p]];
+        const float4 B = rec[S + ti[p]];
         tg[p].hx = A.x; tg[p].hy = A.y; tg[p].hz = A.z;
         tg[p].lx = B.x; tg[p].ly = B.y; tg[p].lz = B.z;
         if constexpr (PASS == 2) {
-            const float4 C = rec[2 * ns_pad + ti[p]];
-            tg[p].vx = C.x; tg[p].vy = C.y; tg[p].vz = C.z;
+            const float4 Cc = rec[2 * S + ti[p]];
+            tg[p].vx = Cc.x; tg[p].vy = Cc.y; tg[p].vz = Cc.z;
         } else {
             tg[p].vx = tg[p].vy = tg[p].vz = 0.0f;
         }
@@ -533,12 +568,12 @@ k_pass_mixed(const float4 *__restrict__ rec, int64_t ns_pad, int ntiles, int tps
     const int tb = blockIdx.y * tps;
     const int te = min(ntiles, tb + tps);
     for (int tile = tb; tile < te; ++tile) {
-        const int64_t j0 = (int64_t)tile * kMixTile;
+        const int64_t j0 = C.slot0 + (int64_t)tile * kMixTile;
         __syncthreads();
         for (int q = threadIdx.x; q < kMixTile; q += kMixThreads) {
 #pragma unroll
             for (int k = 0; k < NA; ++k)
-                sh[k][q] = rec[k * ns_pad + j0 + q];
+                sh[k][q] = rec[k * S + j0 + q];
         }
         __syncthreads();
         float acc[kMixTargets][NV];
@@ -569,8 +604,7 @@ k_pass_mixed(const float4 *__restrict__ rec, int64_t ns_pad, int ntiles, int tps
     for (int p = 0; p < kMixTargets; ++p)
 #pragma unroll
         for (int k = 0; k < NV; ++k)
-            part[((int64_t)blockIdx.y * NV + k) * ns_pad + ti[p]] =
-                (double)hi[p][k] + (double)lo[p][k];
+            part[((int64_t)blockIdx.y * NV + k) * S + ti[p]] = (double)hi[p][k] + (double)lo[p][k];
 }
 
 // ------------------------------------------- fused pair kernel: mixed --
@@ -605,15 +639,30 @@ __device__ __forceinline__ void fused_tile(const float4 *__restrict__ sA,
     }
 }
 
-// Stream-K persistent launch: the (target block, source tile) units are laid
-// out target-block-major and block b of the G resident blocks takes units
-// [b T / G, (b+1) T / G).  Whenever its range crosses into a new target block
-// it writes the finished segment to part[b][seg][value][256 targets]; the
-// gather kernel sums the segments of each target block in block order.
+// Stream-K persistent launch: the (cluster, target block, source tile) units
+// of all clusters are laid out cluster-major, then target-block-major, and
+// block b of the G resident blocks takes units [b T / G, (b+1) T / G).  At
+// each target-block boundary it writes the finished segment to slot
+// (global target block + b) of the segment buffer, which holds
+// (target blocks + G) entries of [value][TI targets]; the gather kernel sums
+// the segments of each target block in block order.
+__device__ __forceinline__ int cluster_of_unit(const Clu *__restrict__ clu, int nclu, int64_t u)
+{
+    int lo = 0, hi = nclu - 1;
+    while (lo < hi) {                        // last cluster with unit0 <= u
+        const int mid = (lo + hi + 1) >> 1;
+        if (clu[mid].unit0 <= u)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
 template <int P, int UNROLL>
 __global__ void __launch_bounds__(kMixThreads, P == 4 ? (UNROLL == 3 ? 2 : 3) : (P == 2 ? 5 : 8))
-k_fused_mixed(const float4 *__restrict__ rec, int64_t ns_pad, int ntiles, int64_t total_units,
-              int segs, float eps2, double *__restrict__ part)
+k_fused_mixed(const float4 *__restrict__ rec, int64_t S, const Clu *__restrict__ clu, int nclu,
+              int64_t total_units, double *__restrict__ part)
 {
     constexpr int TI = kMixThreads * P;
     __shared__ float4 sh[5][kMixTile];
@@ -623,33 +672,36 @@ k_fused_mixed(const float4 *__restrict__ rec, int64_t ns_pad, int ntiles, int64_
     const int64_t G = gridDim.x;
     int64_t u = (int64_t)blockIdx.x * total_units / G;
     const int64_t u1 = ((int64_t)blockIdx.x + 1) * total_units / G;
-    int seg = 0;
     while (u < u1) {
-        const int64_t ib = u / ntiles;
-        const int64_t t0 = ib * TI;
-        const int64_t uend = (ib + 1) * ntiles < u1 ? (ib + 1) * ntiles : u1;
+        const Clu C = clu[cluster_of_unit(clu, nclu, u)];
+        const int64_t ntiles = C.ns_pad / kMixTile;
+        const int64_t ib = (u - C.unit0) / ntiles;
+        const int64_t t0 = C.slot0 + ib * TI;
+        const int64_t ub = C.unit0 + ib * ntiles;          // first unit of this target block
+        const int64_t uend = ub + ntiles < u1 ? ub + ntiles : u1;
+        const float eps2 = (float)C.eps2;
         MixTarget tg[P];
         int64_t ti[P];
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             ti[p] = t0 + p * kMixThreads + threadIdx.x;
             const float4 A = rec[ti[p]];
-            const float4 B = rec[ns_pad + ti[p]];
-            const float4 C = rec[2 * ns_pad + ti[p]];
+            const float4 B = rec[S + ti[p]];
+            const float4 Cc = rec[2 * S + ti[p]];
             tg[p].hx = A.x; tg[p].hy = A.y; tg[p].hz = A.z;
             tg[p].lx = B.x; tg[p].ly = B.y; tg[p].lz = B.z;
-            tg[p].vx = C.x; tg[p].vy = C.y; tg[p].vz = C.z;
+            tg[p].vx = Cc.x; tg[p].vy = Cc.y; tg[p].vz = Cc.z;
 #pragma unroll
             for (int k = 0; k < kFusedVals; ++k)
                 run[k][p][threadIdx.x] = make_float2(0.0f, 0.0f);
         }
         for (; u < uend; ++u) {
-            const int64_t j0 = (u - ib * ntiles) * kMixTile;
+            const int64_t j0 = C.slot0 + (u - ub) * kMixTile;
             __syncthreads();
             for (int q = threadIdx.x; q < kMixTile; q += kMixThreads) {
 #pragma unroll
                 for (int k = 0; k < 5; ++k)
-                    sh[k][q] = rec[k * ns_pad + j0 + q];
+                    sh[k][q] = rec[k * S + j0 + q];
             }
             __syncthreads();
             float acc[P][kFusedVals];
@@ -672,7 +724,7 @@ k_fused_mixed(const float4 *__restrict__ rec, int64_t ns_pad, int ntiles, int64_
                     run[k][p][threadIdx.x] = r;
                 }
         }
-        double *out = part + ((int64_t)blockIdx.x * segs + seg) * kFusedVals * TI;
+        double *out = part + (t0 / TI + blockIdx.x) * (int64_t)(kFusedVals * TI);
 #pragma unroll
         for (int p = 0; p < P; ++p)
 #pragma unroll
@@ -680,25 +732,28 @@ k_fused_mixed(const float4 *__restrict__ rec, int64_t ns_pad, int ntiles, int64_
                 const float2 r = run[k][p][threadIdx.x];
                 out[k * TI + p * kMixThreads + threadIdx.x] = (double)r.x + (double)r.y;
             }
-        ++seg;
     }
 }
 
 // Sums, for every star slot, the stream-K segments that cover its target
 // block (in block order) into the pass-1 / pass-2 partial layout with one
-// split: p1[k][t] (k < 5), p2[k][t] (k < 9).
+// split: p1[k][t] (k < kP1Vals), p2[k][t] (k < kP2Vals).
 template <int P>
 __global__ void __launch_bounds__(kGlueThreads)
-k_fused_gather(const double *__restrict__ part, int64_t ns_pad, int ntiles, int64_t total_units,
-               int64_t G, int segs, double *__restrict__ p1, double *__restrict__ p2)
+k_fused_gather(const double *__restrict__ part, int64_t S, const Clu *__restrict__ clu,
+               const int *__restrict__ blk_clu, int64_t total_units, int64_t G,
+               double *__restrict__ p1, double *__restrict__ p2)
 {
     constexpr int TI = kMixThreads * P;
     const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
-    if (t >= ns_pad)
+    if (t >= S)
         return;
-    const int64_t ib = t / TI;
-    const int lt = (int)(t - ib * TI);
-    const int64_t U0 = ib * ntiles, U1 = U0 + ntiles;
+    const Clu C = clu[cluster_of_block(blk_clu, blockIdx.x)];
+    const int64_t ntiles = C.ns_pad / kMixTile;
+    const int64_t ib = (t - C.slot0) / TI;
+    const int64_t gtb = t / TI;                                 // global target block
+    const int lt = (int)(t - gtb * TI);
+    const int64_t U0 = C.unit0 + ib * ntiles, U1 = U0 + ntiles;
     int64_t b = U0 * G / total_units;
     while (b + 1 < G && (b + 1) * total_units / G <= U0)
         ++b;
@@ -712,18 +767,17 @@ k_fused_gather(const double *__restrict__ part, int64_t ns_pad, int ntiles, int6
             break;
         if (bu1 <= U0 || bu0 == bu1)
             continue;
-        const int64_t s = ib - bu0 / ntiles;
-        const double *in = part + (b * segs + s) * kFusedVals * TI;
+        const double *in = part + (gtb + b) * (int64_t)(kFusedVals * TI);
 #pragma unroll
         for (int k = 0; k < kFusedVals; ++k)
             acc[k] += in[k * TI + lt];
     }
 #pragma unroll
     for (int k = 0; k < kP1Vals; ++k)
-        p1[(int64_t)k * ns_pad + t] = acc[k];
+        p1[(int64_t)k * S + t] = acc[k];
 #pragma unroll
     for (int k = 0; k < kP2Vals; ++k)
-        p2[(int64_t)k * ns_pad + t] = acc[kP1Vals + k];
+        p2[(int64_t)k * S + t] = acc[kP1Vals + k];
 }
 
 // ------------------------------------------------ pair kernels: double --
@@ -786,19 +840,23 @@ __device__ __forceinline__ void f64_tile(const double4_32a (*__restrict__ sh)[kF
 
 template <int PASS>
 __global__ void __launch_bounds__(kF64Threads)
-k_pass_f64(const double4_32a *__restrict__ rec, int64_t ns_pad, int ntiles, int tps, double eps2,
-           double *__restrict__ part)
+k_pass_f64(const double4_32a *__restrict__ rec, int64_t S, const Clu *__restrict__ clu,
+           const int *__restrict__ blk_clu, double *__restrict__ part)
 {
     constexpr int NV = PASS == 1 ? kP1Vals : kP2Vals;
     constexpr int NA = PASS == 1 ? 2 : 4;
     __shared__ double4_32a sh[4][kF64Tile];
     const int64_t t0 = (int64_t)blockIdx.x * kF64Threads;
+    const Clu C = clu[cluster_of_block(blk_clu, t0 / kGlueThreads)];
+    const double eps2 = C.eps2;
+    const int ntiles = (int)(C.ns_pad / kF64Tile);
+    const int tps = (ntiles + (int)gridDim.y - 1) / (int)gridDim.y;
     const int64_t ti = t0 + threadIdx.x;
     const double4_32a A = rec[ti];
     const double di[3] = {A.x, A.y, A.z};
     double vi[3] = {0.0, 0.0, 0.0};
     if (PASS == 2) {
-        const double4_32a B = rec[ns_pad + ti];
+        const double4_32a B = rec[S + ti];
         vi[0] = B.x; vi[1] = B.y; vi[2] = B.z;
     }
     double acc[kP2Vals];
@@ -808,12 +866,12 @@ k_pass_f64(const double4_32a *__restrict__ rec, int64_t ns_pad, int ntiles, int 
     const int tb = blockIdx.y * tps;
     const int te = min(ntiles, tb + tps);
     for (int tile = tb; tile < te; ++tile) {
-        const int64_t j0 = (int64_t)tile * kF64Tile;
+        const int64_t j0 = C.slot0 + (int64_t)tile * kF64Tile;
         __syncthreads();
         for (int q = threadIdx.x; q < kF64Tile; q += kF64Threads) {
 #pragma unroll
             for (int k = 0; k < NA; ++k)
-                sh[k][q] = rec[k * ns_pad + j0 + q];
+                sh[k][q] = rec[k * S + j0 + q];
         }
         __syncthreads();
         const bool diag = (j0 < t0 + kF64Threads) && (t0 < j0 + kF64Tile);
@@ -824,7 +882,7 @@ k_pass_f64(const double4_32a *__restrict__ rec, int64_t ns_pad, int ntiles, int 
     }
 #pragma unroll
     for (int k = 0; k < NV; ++k)
-        part[((int64_t)blockIdx.y * NV + k) * ns_pad + ti] = acc[k];
+        part[((int64_t)blockIdx.y * NV + k) * S + ti] = acc[k];
 }
 
 // Energy pair sums, double precision, records A = (d, m), B = (v, 0):
@@ -864,29 +922,31 @@ __device__ __forceinline__ void energy_tile(const double4_32a (*__restrict__ sh)
     }
 }
 
+// One block per 128 target slots, sweeping every tile of its own cluster.
 __global__ void __launch_bounds__(kF64Threads)
-k_energy_pairs(const double4_32a *__restrict__ rec, int64_t ns_pad, int ntiles, int tps, double eps2,
-               double *__restrict__ part)
+k_energy_pairs(const double4_32a *__restrict__ rec, int64_t S, const Clu *__restrict__ clu,
+               const int *__restrict__ blk_clu, double *__restrict__ part)
 {
     __shared__ double4_32a sh[2][kF64Tile];
     const int64_t t0 = (int64_t)blockIdx.x * kF64Threads;
+    const Clu C = clu[cluster_of_block(blk_clu, t0 / kGlueThreads)];
+    const double eps2 = C.eps2;
+    const int ntiles = (int)(C.ns_pad / kF64Tile);
     const int64_t ti = t0 + threadIdx.x;
     const double4_32a A = rec[ti];
-    const double4_32a B = rec[ns_pad + ti];
+    const double4_32a B = rec[S + ti];
     const double di[3] = {A.x, A.y, A.z};
     const double vi[3] = {B.x, B.y, B.z};
     double acc[kEVals];
 #pragma unroll
     for (int k = 0; k < kEVals; ++k)
         acc[k] = 0.0;
-    const int tb = blockIdx.y * tps;
-    const int te = min(ntiles, tb + tps);
-    for (int tile = tb; tile < te; ++tile) {
-        const int64_t j0 = (int64_t)tile * kF64Tile;
+    for (int tile = 0; tile < ntiles; ++tile) {
+        const int64_t j0 = C.slot0 + (int64_t)tile * kF64Tile;
         __syncthreads();
         for (int q = threadIdx.x; q < kF64Tile; q += kF64Threads) {
             sh[0][q] = rec[j0 + q];
-            sh[1][q] = rec[ns_pad + j0 + q];
+            sh[1][q] = rec[S + j0 + q];
         }
         __syncthreads();
         const bool diag = (j0 < t0 + kF64Threads) && (t0 < j0 + kF64Tile);
@@ -897,7 +957,7 @@ k_energy_pairs(const double4_32a *__restrict__ rec, int64_t ns_pad, int ntiles, 
     }
 #pragma unroll
     for (int k = 0; k < kEVals; ++k)
-        part[((int64_t)blockIdx.y * kEVals + k) * ns_pad + ti] = acc[k];
+        part[(int64_t)k * S + ti] = acc[k];
 }
 
 // ------------------------------------------------------- near sources --
@@ -939,13 +999,16 @@ struct NearMath {
 
 __global__ void __launch_bounds__(kMixThreads)
 k_near_mixed(const float4 *__restrict__ rec, const float4 *__restrict__ nrec,
-             const int *__restrict__ ncount, int64_t ns_pad, int64_t ncap, float eps2,
-             double *__restrict__ part)
+             const int *__restrict__ ncount, int64_t S, int64_t NC, const Clu *__restrict__ clu,
+             const int *__restrict__ blk_clu, double *__restrict__ part)
 {
     constexpr int TI = kMixThreads * kMixTargets;
     __shared__ float4 sh[4][kNearTile];
     const int64_t t0 = (int64_t)blockIdx.x * TI;
-    const int nn = ncount[0];
+    const int k_clu = cluster_of_block(blk_clu, t0 / kGlueThreads);
+    const Clu C = clu[k_clu];
+    const float eps2 = (float)C.eps2;
+    const int nn = ncount[k_clu];
     const int ntiles = (nn + kNearTile - 1) / kNearTile;
     float hx[kMixTargets][3], lx[kMixTargets][3], Ri[kMixTargets], iR[kMixTargets],
         iR3[kMixTargets];
@@ -955,7 +1018,7 @@ k_near_mixed(const float4 *__restrict__ rec, const float4 *__restrict__ nrec,
     for (int p = 0; p < kMixTargets; ++p) {
         ti[p] = (int)(t0 + p * kMixThreads + threadIdx.x);
         const float4 A = rec[ti[p]];
-        const float4 B = rec[ns_pad + ti[p]];
+        const float4 B = rec[S + ti[p]];
         hx[p][0] = A.x; hx[p][1] = A.y; hx[p][2] = A.z;
         lx[p][0] = B.x; lx[p][1] = B.y; lx[p][2] = B.z;
         Ri[p] = sqrtf(A.x * A.x + A.y * A.y + A.z * A.z);
@@ -966,12 +1029,12 @@ k_near_mixed(const float4 *__restrict__ rec, const float4 *__restrict__ nrec,
             hi[p][k] = lo[p][k] = 0.0f;
     }
     for (int tile = 0; tile < ntiles; ++tile) {
-        const int64_t j0 = (int64_t)tile * kNearTile;
+        const int64_t j0 = C.near0 + (int64_t)tile * kNearTile;
         __syncthreads();
         for (int q = threadIdx.x; q < kNearTile; q += kMixThreads) {
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                sh[k][q] = nrec[k * ncap + j0 + q];
+                sh[k][q] = nrec[k * NC + j0 + q];
         }
         __syncthreads();
         float acc[kMixTargets][kNearVals];
@@ -982,7 +1045,7 @@ k_near_mixed(const float4 *__restrict__ rec, const float4 *__restrict__ nrec,
                 acc[p][k] = 0.0f;
 #pragma unroll 1
         for (int q = 0; q < kNearTile; ++q) {
-            const float4 A = sh[0][q], B = sh[1][q], C = sh[2][q], D = sh[3][q];
+            const float4 A = sh[0][q], B = sh[1][q], Cn = sh[2][q], D = sh[3][q];
             const float dj[3] = {A.x, A.y, A.z};
 #pragma unroll
             for (int p = 0; p < kMixTargets; ++p) {
@@ -993,10 +1056,10 @@ k_near_mixed(const float4 *__restrict__ rec, const float4 *__restrict__ nrec,
                 const bool self = __float_as_int(D.y) == ti[p];
                 s2 = self ? 1.0f : s2;
                 const float mj = self ? 0.0f : A.w;
-                const float wx = self ? 0.0f : C.x, wy = self ? 0.0f : C.y, wz = self ? 0.0f : C.z;
+                const float wx = self ? 0.0f : Cn.x, wy = self ? 0.0f : Cn.y, wz = self ? 0.0f : Cn.z;
                 const float is = rsqrtf(s2);
                 NearMath<float>::pair(dx, dy, dz, s2, is, hx[p], dj, Ri[p], iR[p], iR3[p], mj,
-                                      B.w, C.w, D.x, wx, wy, wz, acc[p]);
+                                      B.w, Cn.w, D.x, wx, wy, wz, acc[p]);
             }
         }
 #pragma unroll
@@ -1009,19 +1072,22 @@ k_near_mixed(const float4 *__restrict__ rec, const float4 *__restrict__ nrec,
     for (int p = 0; p < kMixTargets; ++p)
 #pragma unroll
         for (int k = 0; k < kNearVals; ++k)
-            part[(int64_t)k * ns_pad + ti[p]] = (double)hi[p][k] + (double)lo[p][k];
+            part[(int64_t)k * S + ti[p]] = (double)hi[p][k] + (double)lo[p][k];
 }
 
 __global__ void __launch_bounds__(kF64Threads)
 k_near_f64(const double4_32a *__restrict__ rec, const double4_32a *__restrict__ nrec,
-           const int *__restrict__ ncount, int64_t ns_pad, int64_t ncap, double eps2,
-           double *__restrict__ part)
+           const int *__restrict__ ncount, int64_t S, int64_t NC, const Clu *__restrict__ clu,
+           const int *__restrict__ blk_clu, double *__restrict__ part)
 {
     constexpr int TILE = kNearTile / 2;
     __shared__ double4_32a sh[3][TILE];
     const int64_t t0 = (int64_t)blockIdx.x * kF64Threads;
+    const int k_clu = cluster_of_block(blk_clu, t0 / kGlueThreads);
+    const Clu C = clu[k_clu];
+    const double eps2 = C.eps2;
     const int ti = (int)(t0 + threadIdx.x);
-    const int nn = ncount[0];
+    const int nn = ncount[k_clu];
     const int ntiles = (nn + TILE - 1) / TILE;
     const double4_32a Ta = rec[ti];
     const double di[3] = {Ta.x, Ta.y, Ta.z};
@@ -1033,24 +1099,24 @@ k_near_f64(const double4_32a *__restrict__ rec, const double4_32a *__restrict__ 
     for (int k = 0; k < kNearVals; ++k)
         acc[k] = 0.0;
     for (int tile = 0; tile < ntiles; ++tile) {
-        const int64_t j0 = (int64_t)tile * TILE;
+        const int64_t j0 = C.near0 + (int64_t)tile * TILE;
         __syncthreads();
         for (int q = threadIdx.x; q < TILE; q += kF64Threads) {
 #pragma unroll
             for (int k = 0; k < 3; ++k)
-                sh[k][q] = nrec[k * ncap + j0 + q];
+                sh[k][q] = nrec[k * NC + j0 + q];
         }
         __syncthreads();
 #pragma unroll 1
         for (int q = 0; q < TILE; ++q) {
-            const double4_32a A = sh[0][q], B = sh[1][q], C = sh[2][q];
+            const double4_32a A = sh[0][q], B = sh[1][q], Cn = sh[2][q];
             const double dj[3] = {A.x, A.y, A.z};
             const double dx = di[0] - A.x, dy = di[1] - A.y, dz = di[2] - A.z;
             double s2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
             const bool self = (int)B.w == ti;
             s2 = self ? 1.0 : s2;
             const double mj = self ? 0.0 : A.w;
-            const double wx = self ? 0.0 : C.x, wy = self ? 0.0 : C.y, wz = self ? 0.0 : C.z;
+            const double wx = self ? 0.0 : Cn.x, wy = self ? 0.0 : Cn.y, wz = self ? 0.0 : Cn.z;
             const double is = rsqrt_f64(s2);
             NearMath<double>::pair(dx, dy, dz, s2, is, di, dj, Ri, iR, iR3, mj, B.x, B.y, B.z,
                                    wx, wy, wz, acc);
@@ -1058,7 +1124,7 @@ k_near_f64(const double4_32a *__restrict__ rec, const double4_32a *__restrict__ 
     }
 #pragma unroll
     for (int k = 0; k < kNearVals; ++k)
-        part[(int64_t)k * ns_pad + ti] = acc[k];
+        part[(int64_t)k * S + ti] = acc[k];
 }
 
 // ------------------------------------------------------------ epilogue --
@@ -1091,22 +1157,28 @@ k_near_f64(const double4_32a *__restrict__ rec, const double4_32a *__restrict__ 
 //   + G/M m_j/R_j^3 [4 (v_j.Q) d_j - 3 (v_j.d_j) Q - 4 (Q.d_j) v_j]
 // and the block's sum of these goes to blk (deterministic tree).
 __global__ void __launch_bounds__(kGlueThreads)
-k_epilogue(int64_t ns, int64_t ns_pad, const double *__restrict__ x,
-           const double *__restrict__ vel, const double *__restrict__ m,
-           const double *__restrict__ p1, int js1, const double *__restrict__ p2, int js2,
-           const double *__restrict__ pnear, const unsigned char *__restrict__ nflag,
-           const double *__restrict__ glob, double G, double inv_c2, double eps2,
+k_epilogue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_clu,
+           const double *__restrict__ x, const double *__restrict__ vel,
+           const double *__restrict__ m, const double *__restrict__ p1, int js1,
+           const double *__restrict__ p2, int js2, const double *__restrict__ pnear,
+           const unsigned char *__restrict__ nflag, const double *__restrict__ globs,
            double *__restrict__ a, double *__restrict__ v, double h, int *flag,
            unsigned long long *flag_step, unsigned long long step, double *__restrict__ blk)
 {
     __shared__ double sh[3][kGlueThreads];
     const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
+    const int k_clu = cluster_of_block(blk_clu, blockIdx.x);
+    const Clu Cl = clu[k_clu];
+    const double G = Cl.G, inv_c2 = Cl.inv_c2, eps2 = Cl.eps2;
+    const double *glob = globs + (int64_t)k_clu * kGlobVals;
+    const int64_t lt = t - Cl.slot0;
     double bh[3] = {0.0, 0.0, 0.0};
-    if (t < ns) {
-        const int64_t i = t + 1;
-        const double M = m[0], mi = m[i];
+    if (lt < Cl.ns) {
+        const int64_t i = Cl.body0 + 1 + lt, hb = Cl.body0;
+        const double M = m[hb], mi = m[i];
         const double GM = G * M;
-        const double d[3] = {x[3 * i] - x[0], x[3 * i + 1] - x[1], x[3 * i + 2] - x[2]};
+        const double d[3] = {x[3 * i] - x[3 * hb], x[3 * i + 1] - x[3 * hb + 1],
+                             x[3 * i + 2] - x[3 * hb + 2]};
         const double R2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
         const double R = sqrt(R2);
         const double iR = 1.0 / R;
@@ -1118,17 +1190,17 @@ k_epilogue(int64_t ns, int64_t ns_pad, const double *__restrict__ x,
         for (int k = 0; k < kP1Vals; ++k) {
             double acc = 0.0;
             for (int s = 0; s < js1; ++s)
-                acc += p1[((int64_t)s * kP1Vals + k) * ns_pad + t];
+                acc += p1[((int64_t)s * kP1Vals + k) * S + t];
             s1[k] = acc;
         }
         for (int k = 0; k < kP2Vals; ++k) {
             double acc = 0.0;
             for (int s = 0; s < js2; ++s)
-                acc += p2[((int64_t)s * kP2Vals + k) * ns_pad + t];
+                acc += p2[((int64_t)s * kP2Vals + k) * S + t];
             s2[k] = acc;
         }
         for (int k = 0; k < kNearVals; ++k)
-            sn[k] = pnear ? pnear[(int64_t)k * ns_pad + t] : 0.0;
+            sn[k] = pnear ? pnear[(int64_t)k * S + t] : 0.0;
         const double fi = nflag[t] ? 0.0 : 1.0;   // 1 if star i is a far source
         const double N[3] = {s1[0], s1[1], s1[2]};
         const double U = s1[3], Y = R2 * s1[4] - s1[5];
@@ -1178,23 +1250,27 @@ k_epilogue(int64_t ns, int64_t ns_pad, const double *__restrict__ x,
         blk[(int64_t)blockIdx.x * 3 + threadIdx.x] = sh[threadIdx.x][0];
 }
 
-// The hole: a_0 = G W + (1/c^2) sum_j (star j's term above).
+// The hole of each cluster (one block per cluster):
+// a_hole = G W + (1/c^2) sum_j (star j's term above).
 __global__ void __launch_bounds__(kGlueThreads)
-k_hole(const double *__restrict__ blk, int64_t nblk, const double *__restrict__ glob, double G,
-       double inv_c2, double *__restrict__ a, double *__restrict__ v, double h, int *flag,
-       unsigned long long *flag_step, unsigned long long step)
+k_hole(const Clu *__restrict__ clu, const double *__restrict__ blk,
+       const double *__restrict__ globs, double *__restrict__ a, double *__restrict__ v,
+       double h, int *flag, unsigned long long *flag_step, unsigned long long step)
 {
     __shared__ double sh[3][kGlueThreads];
-    sum_blocks<3>(blk, nblk, sh);
+    const Clu C = clu[blockIdx.x];
+    sum_blocks<3>(blk + (C.slot0 / kGlueThreads) * 3, C.ns_pad / kGlueThreads, sh);
     if (threadIdx.x == 0) {
+        const double *glob = globs + (int64_t)blockIdx.x * kGlobVals;
+        const int64_t hb = C.body0;
         double a0[3];
         for (int k = 0; k < 3; ++k)
-            a0[k] = G * glob[3 + k] + inv_c2 * sh[k][0];
+            a0[k] = C.G * glob[3 + k] + C.inv_c2 * sh[k][0];
         flag_nonfinite(a0, flag, flag_step, step);
         for (int k = 0; k < 3; ++k) {
-            a[k] = a0[k];
+            a[3 * hb + k] = a0[k];
             if (v)
-                v[k] = fma(h, a0[k], v[k]);
+                v[3 * hb + k] = fma(h, a0[k], v[3 * hb + k]);
         }
     }
 }
@@ -1212,30 +1288,31 @@ k_hole(const double *__restrict__ blk, int64_t nblk, const double *__restrict__ 
 // with pn_i = 6 v_i^2 pot_i - 7 v_i.Smv_i - Snn_i, p_i = v_i pot_i + Spx_i,
 // n = d_i/R_i (its sign cancels), plus sum m_i/R_i for the i = j double sum.
 __global__ void __launch_bounds__(kGlueThreads)
-k_energy_epilogue(int64_t ns, int64_t ns_pad, const double *__restrict__ x,
-                  const double *__restrict__ vel, const double *__restrict__ m,
-                  const double *__restrict__ pe, int js, double G, double *__restrict__ blk)
+k_energy_epilogue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_clu,
+                  const double *__restrict__ x, const double *__restrict__ vel,
+                  const double *__restrict__ m, const double *__restrict__ pe,
+                  double *__restrict__ blk)
 {
     __shared__ double sh[kEBlockVals][kGlueThreads];
     const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
+    const Clu Cl = clu[cluster_of_block(blk_clu, blockIdx.x)];
+    const double G = Cl.G;
+    const int64_t lt = t - Cl.slot0;
     double o[kEBlockVals];
     for (int k = 0; k < kEBlockVals; ++k)
         o[k] = 0.0;
-    if (t < ns) {
-        const int64_t i = t + 1;
-        const double M = m[0], mi = m[i];
-        const double d[3] = {x[3 * i] - x[0], x[3 * i + 1] - x[1], x[3 * i + 2] - x[2]};
+    if (lt < Cl.ns) {
+        const int64_t i = Cl.body0 + 1 + lt, hb = Cl.body0;
+        const double M = m[hb], mi = m[i];
+        const double d[3] = {x[3 * i] - x[3 * hb], x[3 * i + 1] - x[3 * hb + 1],
+                             x[3 * i + 2] - x[3 * hb + 2]};
         const double R = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         const double iR = 1.0 / R;
         const double vi[3] = {vel[3 * i], vel[3 * i + 1], vel[3 * i + 2]};
-        const double v1[3] = {vel[0], vel[1], vel[2]};
+        const double v1[3] = {vel[3 * hb], vel[3 * hb + 1], vel[3 * hb + 2]};
         double s[kEVals];
-        for (int k = 0; k < kEVals; ++k) {
-            double acc = 0.0;
-            for (int q = 0; q < js; ++q)
-                acc += pe[((int64_t)q * kEVals + k) * ns_pad + t];
-            s[k] = acc;
-        }
+        for (int k = 0; k < kEVals; ++k)
+            s[k] = pe[(int64_t)k * S + t];
         const double vi2 = vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2];
         const double v12 = v1[0] * v1[0] + v1[1] * v1[1] + v1[2] * v1[2];
         const double v1vi = v1[0] * vi[0] + v1[1] * vi[1] + v1[2] * vi[2];
@@ -1263,23 +1340,29 @@ k_energy_epilogue(int64_t ns, int64_t ns_pad, const double *__restrict__ x,
         blk[(int64_t)blockIdx.x * kEBlockVals + threadIdx.x] = sh[threadIdx.x][0];
 }
 
-// Totals plus the hole's own terms: 1/2 M v_1^2, M v_1 and the i = j
-// double sum 1/2 G^2 M (sum_i m_i/R_i)^2 of Eq. 7.
+// Totals per cluster (one block per cluster) plus the hole's own terms:
+// 1/2 M v_1^2, M v_1 and the i = j double sum 1/2 G^2 M (sum_i m_i/R_i)^2 of
+// Eq. 7; out[8 k .. 8 k + 7] for cluster k.
 __global__ void __launch_bounds__(kGlueThreads)
-k_energy_final(const double *__restrict__ blk, int64_t nblk, const double *__restrict__ vel,
-               const double *__restrict__ m, double G, double inv_c2, double *__restrict__ out)
+k_energy_final(const Clu *__restrict__ clu, const double *__restrict__ blk,
+               const double *__restrict__ vel, const double *__restrict__ m,
+               double *__restrict__ out)
 {
     __shared__ double sh[kEBlockVals][kGlueThreads];
-    sum_blocks<kEBlockVals>(blk, nblk, sh);
+    const Clu C = clu[blockIdx.x];
+    sum_blocks<kEBlockVals>(blk + (C.slot0 / kGlueThreads) * kEBlockVals,
+                            C.ns_pad / kGlueThreads, sh);
     if (threadIdx.x == 0) {
-        const double M = m[0];
-        const double v1[3] = {vel[0], vel[1], vel[2]};
+        const int64_t hb = C.body0;
+        const double M = m[hb], G = C.G;
+        const double v1[3] = {vel[3 * hb], vel[3 * hb + 1], vel[3 * hb + 2]};
         const double smr = sh[8][0];
-        out[0] = sh[0][0] + 0.5 * M * (v1[0] * v1[0] + v1[1] * v1[1] + v1[2] * v1[2]);
-        out[1] = inv_c2 * (sh[1][0] + 0.5 * G * G * M * smr * smr);
+        double *o = out + 8 * (int64_t)blockIdx.x;
+        o[0] = sh[0][0] + 0.5 * M * (v1[0] * v1[0] + v1[1] * v1[1] + v1[2] * v1[2]);
+        o[1] = C.inv_c2 * (sh[1][0] + 0.5 * G * G * M * smr * smr);
         for (int k = 0; k < 3; ++k) {
-            out[2 + k] = sh[2 + k][0] + M * v1[k];
-            out[5 + k] = inv_c2 * sh[5 + k][0];
+            o[2 + k] = sh[2 + k][0] + M * v1[k];
+            o[5 + k] = C.inv_c2 * sh[5 + k][0];
         }
     }
 }
@@ -1289,6 +1372,8 @@ k_energy_final(const double *__restrict__ blk, int64_t nblk, const double *__res
 static int64_t glue_blocks(int64_t n) { return (n + kGlueThreads - 1) / kGlueThreads; }
 
 static void timing_begin(pn_ctx *c, int k, cudaEvent_t *end_out);
+
+static const int *blk_table(const pn_ctx *c) { return c->nclu > 1 ? c->blk_clu : nullptr; }
 
 cudaError_t launch_kick_drift(pn_ctx *c, double *x, double *v, const double *a, double dt)
 {
@@ -1315,61 +1400,38 @@ cudaError_t launch_rk4_stage(pn_ctx *c, int stage, double *x, double *v, const d
 cudaError_t launch_prologue(pn_ctx *c, const double *x, const double *vel, const double *m,
                             bool energy_records)
 {
-    const int64_t nb = glue_blocks(c->ns_pad);
-    const double eps2 = c->p.eps * c->p.eps;
-    const double r_near = c->p.r_near > 0.0 ? c->p.r_near : -1.0;
+    const int64_t nb = c->S / kGlueThreads;
+    const int *bc = blk_table(c);
     if (energy_records) {
         k_prologue<2><<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
-            c->ns, c->ns_pad, x, vel, m, c->p.G, eps2, r_near, c->mrec, c->drec, c->nflag, c->blk);
+            c->S, c->d_clu, bc, x, vel, m, c->mrec, c->drec, c->nflag, c->blk);
         return cudaGetLastError();
     }
     const bool mixed = c->p.precision == PN_MIXED;
     if (mixed)
         k_prologue<0><<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
-            c->ns, c->ns_pad, x, vel, m, c->p.G, eps2, r_near, c->mrec, c->drec, c->nflag, c->blk);
+            c->S, c->d_clu, bc, x, vel, m, c->mrec, c->drec, c->nflag, c->blk);
     else
         k_prologue<1><<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
-            c->ns, c->ns_pad, x, vel, m, c->p.G, eps2, r_near, c->mrec, c->drec, c->nflag, c->blk);
+            c->S, c->d_clu, bc, x, vel, m, c->mrec, c->drec, c->nflag, c->blk);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
     if (mixed)
-        k_global_sums<0><<<1, kGlueThreads, 0, c->stream>>>(c->blk, nb, c->glob, c->ncount,
-                                                            c->nrec, c->ndrec, c->nnear_cap);
+        k_global_sums<0><<<c->nclu, kGlueThreads, 0, c->stream>>>(
+            c->d_clu, c->nclu, c->blk, c->glob, c->ncount, c->nrec, c->ndrec, c->NC);
     else
-        k_global_sums<1><<<1, kGlueThreads, 0, c->stream>>>(c->blk, nb, c->glob, c->ncount,
-                                                            c->nrec, c->ndrec, c->nnear_cap);
-    if ((e = cudaGetLastError()) != cudaSuccess || r_near < 0.0)
+        k_global_sums<1><<<c->nclu, kGlueThreads, 0, c->stream>>>(
+            c->d_clu, c->nclu, c->blk, c->glob, c->ncount, c->nrec, c->ndrec, c->NC);
+    if ((e = cudaGetLastError()) != cudaSuccess || !c->any_near)
         return e;
     if (mixed)
         k_near_scatter<0><<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
-            c->ns, x, m, eps2, c->nflag, c->ncount, c->nrec, c->ndrec, c->nnear_cap);
+            c->d_clu, c->nclu, bc, x, m, c->nflag, c->ncount, c->nrec, c->ndrec, c->NC);
     else
         k_near_scatter<1><<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
-            c->ns, x, m, eps2, c->nflag, c->ncount, c->nrec, c->ndrec, c->nnear_cap);
+            c->d_clu, c->nclu, bc, x, m, c->nflag, c->ncount, c->nrec, c->ndrec, c->NC);
     return cudaGetLastError();
-}
-
-cudaError_t launch_pass1(pn_ctx *c)
-{
-    const double eps2 = c->p.eps * c->p.eps;
-    cudaEvent_t end = nullptr;
-    timing_begin(c, 0, &end);
-    if (c->p.precision == PN_MIXED) {
-        const Shape &s = c->mix;
-        dim3 grid((unsigned)s.nblk_i, (unsigned)s.jsplit);
-        k_pass_mixed<1><<<grid, kMixThreads, 0, c->stream>>>(c->mrec, c->ns_pad, s.ntiles,
-                                                             s.tiles_per_split, (float)eps2, c->part);
-    } else {
-        const Shape &s = c->f64;
-        dim3 grid((unsigned)s.nblk_i, (unsigned)s.jsplit);
-        k_pass_f64<1><<<grid, kF64Threads, 0, c->stream>>>(c->drec, c->ns_pad, s.ntiles,
-                                                           s.tiles_per_split, eps2, c->part);
-    }
-    cudaError_t e = cudaGetLastError();
-    if (end)
-        cudaEventRecord(end, c->stream);
-    return e;
 }
 
 bool use_fused(const pn_ctx *c)
@@ -1377,10 +1439,10 @@ bool use_fused(const pn_ctx *c)
     return c->p.precision == PN_MIXED && c->p.pair_kernel == PN_PAIR_FUSED;
 }
 
-// Where the pair partial sums live in c->part:
-//   two-pass: pass 1 [jsplit][5][ns_pad], pass 2 [jsplit][9][ns_pad], near [6][ns_pad]
-//   fused:    pass 1 [1][5][ns_pad], pass 2 [1][9][ns_pad], near [6][ns_pad],
-//             then the stream-K segments [G][segs][14][256]
+// Where the pair partial sums live in c->part (in units of S doubles):
+//   two-pass: pass 1 [jsplit][kP1Vals], pass 2 [jsplit][kP2Vals], near [kNearVals]
+//   fused:    pass 1 [kP1Vals], pass 2 [kP2Vals], near [kNearVals], then the
+//             stream-K segments [target blocks + G][kFusedVals][TI]
 struct Layout {
     int js;
     int64_t p1, p2, near, seg;
@@ -1389,7 +1451,7 @@ struct Layout {
 static Layout layout(const pn_ctx *c)
 {
     Layout L;
-    const int64_t np = c->ns_pad;
+    const int64_t S = c->S;
     if (use_fused(c)) {
         L.js = 1;
     } else {
@@ -1397,47 +1459,82 @@ static Layout layout(const pn_ctx *c)
         L.js = s.jsplit;
     }
     L.p1 = 0;
-    L.p2 = (int64_t)L.js * kP1Vals * np;
-    L.near = (int64_t)L.js * (kP1Vals + kP2Vals) * np;
-    L.seg = L.near + (int64_t)kNearVals * np;
+    L.p2 = (int64_t)L.js * kP1Vals * S;
+    L.near = (int64_t)L.js * (kP1Vals + kP2Vals) * S;
+    L.seg = L.near + (int64_t)kNearVals * S;
     return L;
 }
 
-static int64_t p2_offset(pn_ctx *c) { return layout(c).p2; }
-
-static int64_t near_offset(pn_ctx *c) { return layout(c).near; }
-
-int64_t fused_segments(int64_t ns_pad, int64_t G, int P)
+int64_t fused_units(const Clu *h, int nclu, int P, Clu *out)
 {
-    const int64_t ntiles = ns_pad / kMixTile;
-    const int64_t total = (ns_pad / (kMixThreads * P)) * ntiles;
-    const int64_t per = (total + G - 1) / G;
-    return per / ntiles + 2;
+    int64_t u = 0;
+    for (int k = 0; k < nclu; ++k) {
+        out[k] = h[k];
+        out[k].unit0 = u;
+        u += (h[k].ns_pad / (kMixThreads * P)) * (h[k].ns_pad / kMixTile);
+    }
+    return u;
+}
+
+cudaError_t launch_pass1(pn_ctx *c)
+{
+    const Layout L = layout(c);
+    cudaEvent_t end = nullptr;
+    timing_begin(c, 0, &end);
+    if (c->p.precision == PN_MIXED) {
+        dim3 grid((unsigned)(c->S / (kMixThreads * kMixTargets)), (unsigned)c->mix.jsplit);
+        k_pass_mixed<1><<<grid, kMixThreads, 0, c->stream>>>(c->mrec, c->S, c->d_clu,
+                                                             blk_table(c), c->part + L.p1);
+    } else {
+        dim3 grid((unsigned)(c->S / kF64Threads), (unsigned)c->f64.jsplit);
+        k_pass_f64<1><<<grid, kF64Threads, 0, c->stream>>>(c->drec, c->S, c->d_clu, blk_table(c),
+                                                           c->part + L.p1);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (end)
+        cudaEventRecord(end, c->stream);
+    return e;
+}
+
+cudaError_t launch_pass2(pn_ctx *c)
+{
+    const Layout L = layout(c);
+    cudaEvent_t end = nullptr;
+    timing_begin(c, 1, &end);
+    if (c->p.precision == PN_MIXED) {
+        dim3 grid((unsigned)(c->S / (kMixThreads * kMixTargets)), (unsigned)c->mix.jsplit);
+        k_pass_mixed<2><<<grid, kMixThreads, 0, c->stream>>>(c->mrec, c->S, c->d_clu,
+                                                             blk_table(c), c->part + L.p2);
+    } else {
+        dim3 grid((unsigned)(c->S / kF64Threads), (unsigned)c->f64.jsplit);
+        k_pass_f64<2><<<grid, kF64Threads, 0, c->stream>>>(c->drec, c->S, c->d_clu, blk_table(c),
+                                                           c->part + L.p2);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (end)
+        cudaEventRecord(end, c->stream);
+    return e;
 }
 
 template <int P, int UNROLL>
 static cudaError_t launch_fused_p(pn_ctx *c, const Layout &L)
 {
-    const int64_t np = c->ns_pad;
-    const int ntiles = (int)(np / kMixTile);
-    const int64_t total = (np / (kMixThreads * P)) * ntiles;
-    const float eps2 = (float)(c->p.eps * c->p.eps);
     cudaEvent_t end = nullptr;
     timing_begin(c, 1, &end);
     k_fused_mixed<P, UNROLL><<<(unsigned)c->fused_G, kMixThreads, 0, c->stream>>>(
-        c->mrec, np, ntiles, total, c->fused_segs, eps2, c->part + L.seg);
+        c->mrec, c->S, c->d_clu, c->nclu, c->fused_units, c->part + L.seg);
     cudaError_t e = cudaGetLastError();
     if (end)
         cudaEventRecord(end, c->stream);
     if (e != cudaSuccess)
         return e;
-    k_fused_gather<P><<<(unsigned)glue_blocks(np), kGlueThreads, 0, c->stream>>>(
-        c->part + L.seg, np, ntiles, total, c->fused_G, c->fused_segs, c->part + L.p1,
-        c->part + L.p2);
+    k_fused_gather<P><<<(unsigned)(c->S / kGlueThreads), kGlueThreads, 0, c->stream>>>(
+        c->part + L.seg, c->S, c->d_clu, blk_table(c), c->fused_units, c->fused_G,
+        c->part + L.p1, c->part + L.p2);
     return cudaGetLastError();
 }
 
-// Fused-kernel variants: targets per thread (1, 2, 4) x source-loop unroll (1, 2).
+// Fused-kernel variants: targets per thread (1, 2, 4) x source-loop unroll.
 cudaError_t launch_fused(pn_ctx *c)
 {
     const Layout L = layout(c);
@@ -1477,41 +1574,18 @@ cudaError_t fused_occupancy(int P, int unroll, int *occ)
 
 cudaError_t launch_near(pn_ctx *c)
 {
-    if (!(c->p.r_near > 0.0))
+    if (!c->any_near)
         return cudaSuccess;
-    const double eps2 = c->p.eps * c->p.eps;
-    double *pn = c->part + near_offset(c);
+    const Layout L = layout(c);
+    double *pn = c->part + L.near;
     cudaEvent_t end = nullptr;
     timing_begin(c, 2, &end);
     if (c->p.precision == PN_MIXED)
-        k_near_mixed<<<(unsigned)c->mix.nblk_i, kMixThreads, 0, c->stream>>>(
-            c->mrec, c->nrec, c->ncount, c->ns_pad, c->nnear_cap, (float)eps2, pn);
+        k_near_mixed<<<(unsigned)(c->S / (kMixThreads * kMixTargets)), kMixThreads, 0, c->stream>>>(
+            c->mrec, c->nrec, c->ncount, c->S, c->NC, c->d_clu, blk_table(c), pn);
     else
-        k_near_f64<<<(unsigned)c->f64.nblk_i, kF64Threads, 0, c->stream>>>(
-            c->drec, c->ndrec, c->ncount, c->ns_pad, c->nnear_cap, eps2, pn);
-    cudaError_t e = cudaGetLastError();
-    if (end)
-        cudaEventRecord(end, c->stream);
-    return e;
-}
-
-cudaError_t launch_pass2(pn_ctx *c)
-{
-    const double eps2 = c->p.eps * c->p.eps;
-    double *p2 = c->part + p2_offset(c);
-    cudaEvent_t end = nullptr;
-    timing_begin(c, 1, &end);
-    if (c->p.precision == PN_MIXED) {
-        const Shape &s = c->mix;
-        dim3 grid((unsigned)s.nblk_i, (unsigned)s.jsplit);
-        k_pass_mixed<2><<<grid, kMixThreads, 0, c->stream>>>(c->mrec, c->ns_pad, s.ntiles,
-                                                             s.tiles_per_split, (float)eps2, p2);
-    } else {
-        const Shape &s = c->f64;
-        dim3 grid((unsigned)s.nblk_i, (unsigned)s.jsplit);
-        k_pass_f64<2><<<grid, kF64Threads, 0, c->stream>>>(c->drec, c->ns_pad, s.ntiles,
-                                                           s.tiles_per_split, eps2, p2);
-    }
+        k_near_f64<<<(unsigned)(c->S / kF64Threads), kF64Threads, 0, c->stream>>>(
+            c->drec, c->ndrec, c->ncount, c->S, c->NC, c->d_clu, blk_table(c), pn);
     cudaError_t e = cudaGetLastError();
     if (end)
         cudaEventRecord(end, c->stream);
@@ -1522,17 +1596,16 @@ cudaError_t launch_epilogue(pn_ctx *c, const double *x, const double *vel, const
                             double *a, double *v, double h, unsigned long long step)
 {
     const Layout L = layout(c);
-    const int64_t nb = glue_blocks(c->ns_pad);
-    const double eps2 = c->p.eps * c->p.eps;
-    const double *pnear = c->p.r_near > 0.0 ? c->part + L.near : nullptr;
+    const int64_t nb = c->S / kGlueThreads;
+    const double *pnear = c->any_near ? c->part + L.near : nullptr;
     k_epilogue<<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
-        c->ns, c->ns_pad, x, vel, m, c->part + L.p1, L.js, c->part + L.p2, L.js, pnear,
-        c->nflag, c->glob, c->p.G, c->inv_c2, eps2, a, v, h, c->flag, c->flag_step, step, c->blk);
+        c->S, c->d_clu, blk_table(c), x, vel, m, c->part + L.p1, L.js, c->part + L.p2, L.js,
+        pnear, c->nflag, c->glob, a, v, h, c->flag, c->flag_step, step, c->blk);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
-    k_hole<<<1, kGlueThreads, 0, c->stream>>>(c->blk, nb, c->glob, c->p.G, c->inv_c2, a, v, h,
-                                              c->flag, c->flag_step, step);
+    k_hole<<<c->nclu, kGlueThreads, 0, c->stream>>>(c->d_clu, c->blk, c->glob, a, v, h, c->flag,
+                                                    c->flag_step, step);
     return cudaGetLastError();
 }
 
@@ -1541,21 +1614,37 @@ cudaError_t launch_energy(pn_ctx *c, const double *x, const double *v, const dou
     cudaError_t e = launch_prologue(c, x, v, m, true);
     if (e != cudaSuccess)
         return e;
-    const Shape &s = c->f64;
-    const double eps2 = c->p.eps * c->p.eps;
-    dim3 grid((unsigned)s.nblk_i, (unsigned)s.jsplit);
-    k_energy_pairs<<<grid, kF64Threads, 0, c->stream>>>(c->drec, c->ns_pad, s.ntiles,
-                                                        s.tiles_per_split, eps2, c->part);
+    k_energy_pairs<<<(unsigned)(c->S / kF64Threads), kF64Threads, 0, c->stream>>>(
+        c->drec, c->S, c->d_clu, blk_table(c), c->part);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
-    const int64_t nb = glue_blocks(c->ns_pad);
-    k_energy_epilogue<<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(c->ns, c->ns_pad, x, v, m,
-                                                                    c->part, s.jsplit, c->p.G,
-                                                                    c->blk);
+    k_energy_epilogue<<<(unsigned)(c->S / kGlueThreads), kGlueThreads, 0, c->stream>>>(
+        c->S, c->d_clu, blk_table(c), x, v, m, c->part, c->blk);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
-    k_energy_final<<<1, kGlueThreads, 0, c->stream>>>(c->blk, nb, v, m, c->p.G, c->inv_c2,
-                                                      c->eout);
+    k_energy_final<<<c->nclu, kGlueThreads, 0, c->stream>>>(c->d_clu, c->blk, v, m, c->eout);
+    return cudaGetLastError();
+}
+
+// The energy evaluation on scratch the caller provides, for one cluster whose
+// table entry `clu` is already in device memory.
+cudaError_t launch_energy_on(cudaStream_t st, int64_t S, const Clu *clu, const double *x,
+                             const double *v, const double *m, double4_32a *drec, double *part,
+                             double *blk, double *out)
+{
+    const int64_t nb = S / kGlueThreads;
+    k_prologue<2><<<(unsigned)nb, kGlueThreads, 0, st>>>(S, clu, nullptr, x, v, m, nullptr, drec,
+                                                         nullptr, nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    k_energy_pairs<<<(unsigned)(S / kF64Threads), kF64Threads, 0, st>>>(drec, S, clu, nullptr, part);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    k_energy_epilogue<<<(unsigned)nb, kGlueThreads, 0, st>>>(S, clu, nullptr, x, v, m, part, blk);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    k_energy_final<<<1, kGlueThreads, 0, st>>>(clu, blk, v, m, out);
     return cudaGetLastError();
 }
 
@@ -1565,7 +1654,7 @@ cudaError_t launch_energy(pn_ctx *c, const double *x, const double *v, const dou
 static void timing_begin(pn_ctx *c, int k, cudaEvent_t *end_out)
 {
     *end_out = nullptr;
-    if (!c->timing_on)
+    if (!c->timing_on || c->capturing)
         return;
     Timing &t = c->tm;
     if (t.count[k] == Timing::kRing) {
@@ -1584,7 +1673,8 @@ static void timing_begin(pn_ctx *c, int k, cudaEvent_t *end_out)
     t.count[k] += 1;
 }
 
-void shapes(int64_t ns_pad, int sm_count, int occ_mix, int occ_f64, Shape *mix, Shape *f64)
+void shapes(int64_t S, int64_t max_ns_pad, int sm_count, int occ_mix, int occ_f64, Shape *mix,
+            Shape *f64)
 {
     struct Cfg { int threads, targets, tile, occ; Shape *out; } cfg[2] = {
         {kMixThreads, kMixTargets, kMixTile, occ_mix, mix},
@@ -1595,17 +1685,16 @@ void shapes(int64_t ns_pad, int sm_count, int occ_mix, int occ_f64, Shape *mix, 
         s.targets = c.targets;
         s.tile = c.tile;
         s.occupancy = c.occ > 0 ? c.occ : 1;
-        s.nblk_i = ns_pad / (c.threads * c.targets);
-        s.ntiles = (int)(ns_pad / c.tile);
+        s.nblk_i = S / (c.threads * c.targets);
+        s.ntiles = (int)(max_ns_pad / c.tile);
         const int64_t resident = (int64_t)s.occupancy * sm_count;
         int64_t want = (8 * resident + s.nblk_i - 1) / s.nblk_i;   // splits for ~8 waves
         if (want < 1)
             want = 1;
-        int64_t tps = (s.ntiles + want - 1) / want;
-        if (tps < 1)
-            tps = 1;
-        s.tiles_per_split = (int)tps;
-        s.jsplit = (int)((s.ntiles + tps - 1) / tps);
+        if (want > s.ntiles)
+            want = s.ntiles;
+        s.jsplit = (int)want;
+        s.tiles_per_split = (s.ntiles + s.jsplit - 1) / s.jsplit;
     }
 }
 
@@ -1616,40 +1705,6 @@ cudaError_t occupancy(int *occ_mix, int *occ_f64)
     if (e != cudaSuccess)
         return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_f64, k_pass_f64<2>, kF64Threads, 0);
-}
-
-}  // namespace pn
-
-namespace pn {
-
-// The energy evaluation of launch_energy on scratch the caller provides
-// (records, pair partials, block partials) instead of a context's buffers;
-// the source range is split into at most `jsplit_max` parts.
-cudaError_t launch_energy_on(cudaStream_t st, int64_t ns, int64_t ns_pad, const double *x,
-                             const double *v, const double *m, double G, double inv_c2,
-                             double eps, int jsplit_max, double4_32a *drec, double *part,
-                             double *blk, double *out)
-{
-    const double eps2 = eps * eps;
-    const int64_t nb = glue_blocks(ns_pad);
-    k_prologue<2><<<(unsigned)nb, kGlueThreads, 0, st>>>(ns, ns_pad, x, v, m, G, eps2, -1.0,
-                                                         nullptr, drec, nullptr, nullptr);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess)
-        return e;
-    const int ntiles = (int)(ns_pad / kF64Tile);
-    const int tps = (ntiles + jsplit_max - 1) / jsplit_max;
-    const int jsplit = (ntiles + tps - 1) / tps;
-    dim3 grid((unsigned)(ns_pad / kF64Threads), (unsigned)jsplit);
-    k_energy_pairs<<<grid, kF64Threads, 0, st>>>(drec, ns_pad, ntiles, tps, eps2, part);
-    if ((e = cudaGetLastError()) != cudaSuccess)
-        return e;
-    k_energy_epilogue<<<(unsigned)nb, kGlueThreads, 0, st>>>(ns, ns_pad, x, v, m, part, jsplit, G,
-                                                             blk);
-    if ((e = cudaGetLastError()) != cudaSuccess)
-        return e;
-    k_energy_final<<<1, kGlueThreads, 0, st>>>(blk, nb, v, m, G, inv_c2, out);
-    return cudaGetLastError();
 }
 
 }  // namespace pn

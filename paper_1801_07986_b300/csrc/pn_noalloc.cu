@@ -26,12 +26,12 @@ namespace {
 
 constexpr int64_t kMaxBodies = 16384;                       // PN_NOALLOC_MAX_BODIES
 constexpr int64_t kPadMax = (kMaxBodies - 1 + pn::kPad - 1) / pn::kPad * pn::kPad;
-constexpr int kSplitMax = 4;                                // source splits of the pair kernel
 constexpr int64_t kRecBytes = 2 * kPadMax * (int64_t)sizeof(double4_32a);
-constexpr int64_t kPartBytes = (int64_t)kSplitMax * pn::kEVals * kPadMax * 8;
+constexpr int64_t kPartBytes = (int64_t)pn::kEVals * kPadMax * 8;
 constexpr int64_t kBlkBytes = (kPadMax / pn::kGlueThreads) * pn::kEBlockVals * 8;
 constexpr int64_t kAlign = 256;
-constexpr int64_t kRecOff = 0;
+constexpr int64_t kCluOff = 0;                              // the one-entry cluster table
+constexpr int64_t kRecOff = kAlign;
 constexpr int64_t kPartOff = (kRecOff + kRecBytes + kAlign - 1) / kAlign * kAlign;
 constexpr int64_t kBlkOff = (kPartOff + kPartBytes + kAlign - 1) / kAlign * kAlign;
 constexpr int64_t kScratchBytes = (kBlkOff + kBlkBytes + kAlign - 1) / kAlign * kAlign;
@@ -85,13 +85,23 @@ extern "C" pn_status pn_energy_noalloc(int device, void *cuda_stream, int64_t n,
         return fail(PN_ECUDA, "pn_energy_noalloc: cudaGetSymbolAddress: ", cudaGetErrorString(e));
     }
     unsigned char *b = static_cast<unsigned char *>(base);
-    const int64_t ns = n - 1;
-    const int64_t ns_pad = (ns + pn::kPad - 1) / pn::kPad * pn::kPad;
-    const double inv_c2 = std::isinf(c) ? 0.0 : 1.0 / (c * c);
-    e = pn::launch_energy_on((cudaStream_t)cuda_stream, ns, ns_pad, x, v, m, G, inv_c2, eps,
-                             kSplitMax, reinterpret_cast<double4_32a *>(b + kRecOff),
-                             reinterpret_cast<double *>(b + kPartOff),
-                             reinterpret_cast<double *>(b + kBlkOff), out);
+    pn::Clu clu = {};
+    clu.body0 = 0;
+    clu.ns = n - 1;
+    clu.ns_pad = (clu.ns + pn::kPad - 1) / pn::kPad * pn::kPad;
+    clu.slot0 = 0;
+    clu.G = G;
+    clu.inv_c2 = std::isinf(c) ? 0.0 : 1.0 / (c * c);
+    clu.eps2 = eps * eps;
+    clu.r_near = -1.0;
+    pn::Clu *dclu = reinterpret_cast<pn::Clu *>(b + kCluOff);
+    // the table entry is staged from this stack copy before the call returns
+    e = cudaMemcpyAsync(dclu, &clu, sizeof clu, cudaMemcpyHostToDevice, (cudaStream_t)cuda_stream);
+    if (e == cudaSuccess)
+        e = pn::launch_energy_on((cudaStream_t)cuda_stream, clu.ns_pad, dclu, x, v, m,
+                                 reinterpret_cast<double4_32a *>(b + kRecOff),
+                                 reinterpret_cast<double *>(b + kPartOff),
+                                 reinterpret_cast<double *>(b + kBlkOff), out);
     if (prev >= 0 && prev != device)
         cudaSetDevice(prev);
     if (e != cudaSuccess)

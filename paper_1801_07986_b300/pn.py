@@ -46,6 +46,10 @@ class PNError(RuntimeError):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
 
 
+class _Cluster(ctypes.Structure):
+    _fields_ = [("G", ctypes.c_double), ("c", ctypes.c_double), ("eps", ctypes.c_double)]
+
+
 class _Params(ctypes.Structure):
     _fields_ = [("G", ctypes.c_double), ("c", ctypes.c_double), ("eps", ctypes.c_double),
                 ("precision", ctypes.c_int), ("vel_mode", ctypes.c_int),
@@ -78,6 +82,9 @@ def _load():
             P, I64, I, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
             sig = {
                 "pn_init": [ctypes.POINTER(P), I64, ctypes.POINTER(_Params), I, P],
+                "pn_init_batched": [ctypes.POINTER(P), I, P, P, ctypes.POINTER(_Params), I, P],
+                "pn_step_graph": [P, P, P, P, P, D, I64],
+                "pn_tune": [P, P, P, P, P, P],
                 "pn_set_params": [P, ctypes.POINTER(_Params)],
                 "pn_set_stream": [P, P],
                 "pn_accel": [P, P, P, P, P],
@@ -135,11 +142,13 @@ def _params(G, c, eps, precision, vel_mode, r_near=R_NEAR_DEFAULT, pair_kernel="
 class Context:
     """Owns one pn_ctx handle (pn_destroy on close / garbage collection)."""
 
-    def __init__(self, handle: int, n: int, device: int, params: _Params):
+    def __init__(self, handle: int, n: int, device: int, params: _Params, offsets=None):
         self.handle = ctypes.c_void_p(handle)
         self.n = n
         self.device = device
         self.params = params
+        self.offsets = [0, n] if offsets is None else list(offsets)
+        self.n_clusters = len(self.offsets) - 1
 
     def close(self) -> None:
         if self.handle:
@@ -180,6 +189,36 @@ def pn_init(n: int, G: float = 1.0, c: float = math.inf, eps: float = 0.0,
     _check(lib.pn_init(ctypes.byref(h), int(n), ctypes.byref(p), int(device),
                        ctypes.c_void_p(_torch_stream(device, stream))))
     return Context(h.value, int(n), int(device), p)
+
+
+def pn_init_batched(offsets, G=1.0, c=math.inf, eps=0.0, precision="mixed",
+                    vel_mode="vpred_end", device: int | None = None, stream=None,
+                    r_near: float = R_NEAR_DEFAULT, pair_kernel="fused",
+                    integrator="kdk") -> Context:
+    """Context for independent clusters evaluated together: cluster k holds
+    bodies [offsets[k], offsets[k+1]) of the concatenated state, its hole
+    first.  G, c, eps may be scalars or per-cluster sequences."""
+    lib = _load()
+    if device is None:
+        import torch
+        device = torch.cuda.current_device()
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    k = off.shape[0] - 1
+    if k < 1:
+        raise ValueError("need at least one cluster")
+    cl = (_Cluster * k)()
+    Gs, cs, es = (np.broadcast_to(np.asarray(q, dtype=np.float64), (k,)) for q in (G, c, eps))
+    for i in range(k):
+        cl[i].G, cl[i].c, cl[i].eps = float(Gs[i]), float(cs[i]), float(es[i])
+    p = _params(float(Gs[0]), float(cs[0]), float(es[0]), precision, vel_mode, r_near,
+                pair_kernel, integrator)
+    h = ctypes.c_void_p()
+    _check(lib.pn_init_batched(ctypes.byref(h), k, off.ctypes.data_as(ctypes.c_void_p),
+                               ctypes.cast(cl, ctypes.c_void_p), ctypes.byref(p), int(device),
+                               ctypes.c_void_p(_torch_stream(device, stream))))
+    ctx = Context(h.value, int(off[-1]), int(device), p, offsets=off.tolist())
+    ctx.batched = True
+    return ctx
 
 
 def pn_set_params(ctx: Context, G=None, c=None, eps=None, precision=None, vel_mode=None,
@@ -229,6 +268,26 @@ def pn_step(ctx: Context, x, v, m, a, dt: float, nsteps: int = 1) -> None:
                            int(nsteps)))
 
 
+def pn_step_graph(ctx: Context, x, v, m, a, dt: float, nsteps: int) -> None:
+    """pn_step recorded once into a CUDA graph per (arrays, dt, nsteps) and
+    replayed with one launch."""
+    n = ctx.n
+    _check(_load().pn_step_graph(ctx.handle, _dev(ctx, x, (n, 3), "x"), _dev(ctx, v, (n, 3), "v"),
+                                 _dev(ctx, m, (n,), "m"), _dev(ctx, a, (n, 3), "a"), float(dt),
+                                 int(nsteps)))
+
+
+def pn_tune(ctx: Context, x, v, m, a) -> dict:
+    """Choose the fused kernel's launch shape by timing candidates on this
+    state (a is overwritten with A(x, v))."""
+    n = ctx.n
+    out = np.zeros(3, dtype=np.int64)
+    _check(_load().pn_tune(ctx.handle, _dev(ctx, x, (n, 3), "x"), _dev(ctx, v, (n, 3), "v"),
+                           _dev(ctx, m, (n,), "m"), _dev(ctx, a, (n, 3), "a"),
+                           out.ctypes.data_as(ctypes.c_void_p)))
+    return {"targets_per_thread": int(out[0]), "unroll": int(out[1]), "cached": bool(out[2])}
+
+
 def _host(arr, shape, name):
     if not isinstance(arr, np.ndarray) or arr.dtype != np.float64 or arr.shape != shape \
             or not arr.flags.c_contiguous or not arr.flags.writeable:
@@ -244,14 +303,19 @@ def pn_step_host(ctx: Context, x, v, m, a, dt: float, nsteps: int = 1) -> None:
                                 int(nsteps)))
 
 
-def pn_energy(ctx: Context, x, v, m) -> dict:
-    """Eq. 7 energy and Eq. 8 momentum (FP64), as a dict like the oracle's."""
+def pn_energy(ctx: Context, x, v, m):
+    """Eq. 7 energy and Eq. 8 momentum (FP64), as a dict like the oracle's
+    (a list of dicts, one per cluster, on a batched context)."""
     n = ctx.n
-    out = np.zeros(8)
+    out = np.zeros(8 * ctx.n_clusters)
     _check(_load().pn_energy(ctx.handle, _dev(ctx, x, (n, 3), "x"), _dev(ctx, v, (n, 3), "v"),
                              _dev(ctx, m, (n,), "m"), out.ctypes.data_as(ctypes.c_void_p)))
-    return {"E_N": out[0], "E_PN": out[1], "E": out[0] + out[1],
-            "P_N": out[2:5].copy(), "P_PN": out[5:8].copy(), "P": out[2:5] + out[5:8]}
+    res = []
+    for k in range(ctx.n_clusters):
+        o = out[8 * k:8 * k + 8]
+        res.append({"E_N": o[0], "E_PN": o[1], "E": o[0] + o[1], "P_N": o[2:5].copy(),
+                    "P_PN": o[5:8].copy(), "P": o[2:5] + o[5:8]})
+    return res if getattr(ctx, "batched", False) else res[0]
 
 
 def pn_energy_noalloc(x, v, m, out, G: float = 1.0, c: float = math.inf, eps: float = 0.0,

@@ -129,3 +129,23 @@ def test_python_binding_validates_before_calling(lib):
         pn._params(1.0, math.inf, 0.0, "mixed", "rk4")
     with pytest.raises(ValueError):
         pn._params(1.0, math.inf, 0.0, "mixed", "vhalf", 0.05, "three_pass")
+
+
+def test_batched_init_rejects_bad_offsets_on_host(lib):
+    from paper_1801_07986_b300.pn import _Cluster
+    p = _params()
+    h = ctypes.c_void_p()
+    cases = [([0, 1, 10], "cluster 0 has 1 bodies"), ([1, 10, 20], "offsets[0] must be 0"),
+             ([0, 10, 10], "cluster 1 has 0 bodies")]
+    for off, msg in cases:
+        arr = (ctypes.c_int64 * len(off))(*off)
+        st = lib.pn_init_batched(ctypes.byref(h), len(off) - 1, arr, None, ctypes.byref(p), 0, None)
+        assert st == 1 and msg in lib.pn_last_error().decode(), (off, lib.pn_last_error())
+    arr = (ctypes.c_int64 * 3)(0, 10, 20)
+    cl = (_Cluster * 2)()
+    cl[0].G, cl[0].c, cl[0].eps = 1.0, 10.0, 0.0
+    cl[1].G, cl[1].c, cl[1].eps = 1.0, -3.0, 0.0
+    st = lib.pn_init_batched(ctypes.byref(h), 2, arr, ctypes.cast(cl, ctypes.c_void_p),
+                             ctypes.byref(p), 0, None)
+    assert st == 1 and "cluster 1" in lib.pn_last_error().decode()
+    assert lib.pn_init_batched(ctypes.byref(h), 0, arr, None, ctypes.byref(p), 0, None) == 1

@@ -1,0 +1,136 @@
+"""Batched contexts: many independent clusters of uneven size in one set of
+launches (the pair kernel balances their work), checked cluster by cluster
+against the FP64 oracle, plus CUDA-graph stepping and the autotuner."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1801_07986_b300 import pn  # noqa: E402
+from paper_1801_07986_b300.inputs import make_cluster  # noqa: E402
+
+DEV = torch.device("cuda:0")
+FP64_TOL = 1e-12
+MIX_MED, MIX_MAX = 2e-7, 1e-5
+SIZES = [300, 1025, 77, 2048, 513, 4100]
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b, axis=-1) / np.linalg.norm(b, axis=-1)
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+def batch(sizes=SIZES, seed=900):
+    xs, vs, ms, Ms, cs, es = [], [], [], [], [], []
+    rng = np.random.default_rng(seed)
+    for k, n in enumerate(sizes):
+        M = float(rng.uniform(0.01, 0.2))
+        x, v, m = make_cluster(n, M, seed + k)
+        x = x + rng.normal(size=3) * 5.0          # clusters at different places
+        xs.append(x); vs.append(v); ms.append(m)
+        Ms.append(M)
+        cs.append(float(rng.uniform(20.0, 200.0)))
+        es.append(float(rng.choice([0.0, 1e-4, 1e-3])))
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    return (np.concatenate(xs), np.concatenate(vs), np.concatenate(ms), off,
+            np.array(cs), np.array(es))
+
+
+def oracle_accels(orc, x, v, m, off, cs, es):
+    return [orc.accel(x[a:b], v[a:b], m[a:b], c=c, eps=e)
+            for a, b, c, e in zip(off[:-1], off[1:], cs, es)]
+
+
+@pytest.mark.parametrize("precision,pair_kernel",
+                         [("fp64", "two_pass"), ("mixed", "fused"), ("mixed", "two_pass")])
+def test_batched_accel_matches_oracle_per_cluster(orc, precision, pair_kernel):
+    x, v, m, off, cs, es = batch()
+    ctx = pn.pn_init_batched(off, c=cs, eps=es, precision=precision, pair_kernel=pair_kernel,
+                             device=0)
+    X, V, M = dev(x), dev(v), dev(m)
+    A = torch.empty_like(X)
+    pn.pn_accel(ctx, X, V, M, A)
+    pn.pn_sync(ctx)
+    got = A.cpu().numpy()
+    for (a, b), want in zip(zip(off[:-1], off[1:]), oracle_accels(orc, x, v, m, off, cs, es)):
+        err = rel(got[a:b], want)
+        if precision == "fp64":
+            assert err.max() <= FP64_TOL, (a, b, err.max())
+        else:
+            assert np.median(err) <= MIX_MED and err.max() <= MIX_MAX, (a, b, np.median(err),
+                                                                         err.max())
+    ctx.close()
+
+
+def test_batched_energy_per_cluster(orc):
+    x, v, m, off, cs, es = batch()
+    ctx = pn.pn_init_batched(off, c=cs, eps=es, precision="mixed", device=0)
+    got = pn.pn_energy(ctx, dev(x), dev(v), dev(m))
+    assert len(got) == len(SIZES)
+    for k, (a, b) in enumerate(zip(off[:-1], off[1:])):
+        want = orc.energy(x[a:b], v[a:b], m[a:b], c=cs[k], eps=es[k])
+        for key in ("E_N", "E_PN"):
+            assert abs(got[k][key] - want[key]) <= 1e-12 * abs(want[key])
+    ctx.close()
+
+
+def test_batched_steps_match_oracle_and_graph_replays_bitwise(orc):
+    x, v, m, off, cs, es = batch(sizes=[300, 1025, 513])
+    dt = 1.0 / 2048
+    ctx = pn.pn_init_batched(off, c=cs, eps=es, precision="fp64", device=0)
+    X, V, M = dev(x), dev(v), dev(m)
+    A = torch.empty_like(X)
+    pn.pn_accel(ctx, X, V, M, A)
+    X2, V2, A2 = X.clone(), V.clone(), A.clone()
+    pn.pn_step(ctx, X, V, M, A, dt, 6)
+    pn.pn_step_graph(ctx, X2, V2, M, A2, dt, 3)     # capture + replay
+    pn.pn_step_graph(ctx, X2, V2, M, A2, dt, 3)     # replay of the same graph
+    pn.pn_sync(ctx)
+    assert torch.equal(X, X2) and torch.equal(V, V2) and torch.equal(A, A2)
+    xg = X.cpu().numpy()
+    for k, (a, b) in enumerate(zip(off[:-1], off[1:])):
+        a0 = orc.accel(x[a:b], v[a:b], m[a:b], c=cs[k], eps=es[k])
+        xo, vo, ao = orc.step(x[a:b], v[a:b], m[a:b], a0, dt, 6, c=cs[k], eps=es[k])
+        assert np.abs(xg[a:b] - xo).max() < 1e-12
+    ctx.close()
+
+
+def test_tune_keeps_parity(orc):
+    x, v, m, off, cs, es = batch()
+    ctx = pn.pn_init_batched(off, c=cs, eps=es, precision="mixed", device=0)
+    X, V, M = dev(x), dev(v), dev(m)
+    A = torch.empty_like(X)
+    choice = pn.pn_tune(ctx, X, V, M, A)
+    assert choice["targets_per_thread"] in (2, 4) and choice["unroll"] in (1, 2)
+    again = pn.pn_tune(ctx, X, V, M, A)
+    assert again["cached"] and again["targets_per_thread"] == choice["targets_per_thread"]
+    pn.pn_accel(ctx, X, V, M, A)
+    pn.pn_sync(ctx)
+    got = A.cpu().numpy()
+    for (a, b), want in zip(zip(off[:-1], off[1:]), oracle_accels(orc, x, v, m, off, cs, es)):
+        err = rel(got[a:b], want)
+        assert np.median(err) <= MIX_MED and err.max() <= MIX_MAX
+    ctx.close()
+
+
+def test_nonfinite_in_one_cluster_is_reported():
+    x, v, m, off, cs, es = batch(sizes=[300, 600])
+    x = x.copy()
+    x[off[1] + 7] = x[off[1]]          # a star of cluster 1 on its hole
+    ctx = pn.pn_init_batched(off, c=cs, eps=es, precision="mixed", device=0)
+    X, V, M = dev(x), dev(v), dev(m)
+    A = torch.empty_like(X)
+    pn.pn_accel(ctx, X, V, M, A)
+    with pytest.raises(pn.PNError) as ei:
+        pn.pn_sync(ctx)
+    assert ei.value.status == pn.PN_ENONFINITE
+    ctx.close()
