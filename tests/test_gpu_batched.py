@@ -134,3 +134,33 @@ def test_nonfinite_in_one_cluster_is_reported():
         pn.pn_sync(ctx)
     assert ei.value.status == pn.PN_ENONFINITE
     ctx.close()
+
+
+def test_batched64_workload_sampled(orc):
+    """The 64-cluster workload (N log-uniform in [512, 32768]) in one batched
+    context: sampled stars of every cluster, and the holes of the clusters
+    small enough for the oracle's O(N^2) hole sum, against the oracle."""
+    from paper_1801_07986_b300.inputs import batched_workloads
+    ws = batched_workloads()
+    xs, vs, ms = zip(*(w.state() for w in ws))
+    off = np.concatenate([[0], np.cumsum([w.n for w in ws])])
+    x, v, m = np.concatenate(xs), np.concatenate(vs), np.concatenate(ms)
+    ctx = pn.pn_init_batched(off, c=[w.c for w in ws], eps=[w.eps for w in ws],
+                             precision="mixed", device=0)
+    X, V, M = dev(x), dev(v), dev(m)
+    A = torch.empty_like(X)
+    pn.pn_accel(ctx, X, V, M, A)
+    pn.pn_sync(ctx)
+    got = A.cpu().numpy()
+    ctx.close()
+    rng = np.random.default_rng(64)
+    errs = []
+    for k, w in enumerate(ws):
+        a, b = off[k], off[k + 1]
+        rows = list(rng.choice(np.arange(1, w.n), 4, replace=False))
+        if w.n <= 4096:
+            rows.append(0)
+        want = orc.accel_rows(x[a:b], v[a:b], m[a:b], rows, c=w.c, eps=w.eps)
+        errs.append(rel(got[a:b][rows], want))
+    err = np.concatenate(errs)
+    assert np.median(err) <= MIX_MED and err.max() <= MIX_MAX, (np.median(err), err.max())
