@@ -282,6 +282,7 @@ def run_native(args, w):
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
     pn.pn_set_timing(ctx, True)
+    launches0 = pn.pn_launch_count(ctx)
     with ClockSampler(local) as clk:
         for k in range(steps):
             flush.zero_()
@@ -290,6 +291,7 @@ def run_native(args, w):
             ev1[k].record(stream)
         torch.cuda.synchronize(dev)
     pn.pn_sync(ctx)
+    launches = pn.pn_launch_count(ctx) - launches0
     kms, klaunch = pn.pn_get_timing(ctx)
     pn.pn_set_timing(ctx, False)
     ms = float(sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)))
@@ -341,7 +343,7 @@ def run_native(args, w):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.precision == "mixed" else "f64",
         "data": "synthetic", "config": config_of(w, args.precision, args),
-        "roofline": roof, "gpu_launches": (9 if fused else 9) * steps, "clocks": clocks,
+        "roofline": roof, "gpu_launches": launches, "clocks": clocks,
         "launch_shape": launch,
     }
 
@@ -439,9 +441,11 @@ def run_batched(local, stream, steps, warmup):
     capture_s = time.perf_counter() - t0
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    l0 = pn.pn_launch_count(ctx)
     e0.record(stream)
     pn.pn_step_graph(ctx, X, V, M, A, dt, steps)        # replay, timed
     e1.record(stream)
+    launches = pn.pn_launch_count(ctx) - l0
     e1.synchronize()
     pn.pn_sync(ctx)
     ms_tot = e0.elapsed_time(e1)
@@ -451,7 +455,8 @@ def run_batched(local, stream, steps, warmup):
             "n_min": int(min(w.n for w in ws)), "n_max": int(max(w.n for w in ws)),
             "steps": steps, "value": inter / (ms_tot * 1e-3), "unit": "interactions/s",
             "ms_per_step": ms_tot / steps, "graph": "all steps in one CUDA graph launch",
-            "graph_capture_and_first_run_s": capture_s, "autotuned": tuned}
+            "graph_capture_and_first_run_s": capture_s, "autotuned": tuned,
+            "gpu_launches": launches}
 
 
 def main():

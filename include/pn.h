@@ -234,6 +234,14 @@ pn_status pn_get_timing(pn_ctx *ctx, double ms[3], int64_t launches[3]);
 pn_status pn_get_launch(pn_ctx *ctx, int64_t out[7]);
 
 /*
+ * Number of CUDA kernels this context has launched since pn_init (host-side
+ * count, no synchronisation).  A pn_step_graph replay adds the kernels of the
+ * captured graph; capturing it adds nothing.  Takes a NULL count as
+ * PN_EINVAL.
+ */
+pn_status pn_launch_count(pn_ctx *ctx, int64_t *count);
+
+/*
  * Energy and momentum like pn_energy, for callers that cannot allocate
  * device memory (their GPU memory belongs to another allocator, or they
  * must not allocate after start-up): no context, no cudaMalloc.  The paper

@@ -533,12 +533,15 @@ pn_status pn_step_graph(pn_ctx *c, double *x, double *v, const double *m, double
         cudaStream_t user = c->stream;
         c->stream = c->cap_stream;
         c->capturing = true;
+        const int64_t before = c->launches;
         cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
         pn_status st = e == cudaSuccess ? run_steps(c, x, v, m, a, dt, nsteps) : PN_ECUDA;
         cudaGraph_t graph = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
         c->stream = user;
         c->capturing = false;
+        c->graph_launches = c->launches - before;   // captured, not yet run
+        c->launches = before;
         if (e != cudaSuccess || e2 != cudaSuccess || st != PN_OK) {
             if (graph)
                 cudaGraphDestroy(graph);
@@ -558,6 +561,7 @@ pn_status pn_step_graph(pn_ctx *c, double *x, double *v, const double *m, double
         c->graph_steps = nsteps;
     }
     PN_CUDA(cudaGraphLaunch(c->graph_exec, c->stream), "graph launch");
+    c->launches += c->graph_launches;
     return ok();
 }
 
@@ -692,6 +696,16 @@ pn_status pn_get_launch(pn_ctx *c, int64_t out[7])
     out[4] = fused ? c->fused_G : s.jsplit;
     out[5] = fused ? c->fused_occ : s.occupancy;
     out[6] = c->sm_count;
+    return ok();
+}
+
+pn_status pn_launch_count(pn_ctx *c, int64_t *count)
+{
+    if (check_ctx(c) != PN_OK)
+        return PN_EINVAL;
+    if (!count)
+        return fail(PN_EINVAL, "pn_launch_count: NULL output");
+    *count = c->launches;
     return ok();
 }
 

@@ -126,6 +126,8 @@ struct pn_ctx {
     const void *graph_key[4];
     double graph_dt;
     int64_t graph_steps;
+    int64_t launches;        // kernels launched (a graph replay adds its kernels)
+    int64_t graph_launches;  // kernels in the instantiated graph
 };
 
 namespace pn {

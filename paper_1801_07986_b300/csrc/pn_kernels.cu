@@ -1382,6 +1382,7 @@ cudaError_t launch_kick_drift(pn_ctx *c, double *x, double *v, const double *a, 
                                                                     : 4 * (int64_t)c->sm_count;
     k_kick_drift<<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(n3, x, v, a, c->vp, 0.5 * dt, dt,
                                                                c->p.vel_mode);
+    c->launches += 1;
     return cudaGetLastError();
 }
 
@@ -1394,6 +1395,7 @@ cudaError_t launch_rk4_stage(pn_ctx *c, int stage, double *x, double *v, const d
     k_rk4_stage<<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(stage, n3, x, v, a, c->rk_a,
                                                               c->rk_x, c->rk_v, c->rk_sx,
                                                               c->rk_sv, dt);
+    c->launches += 1;
     return cudaGetLastError();
 }
 
@@ -1405,6 +1407,7 @@ cudaError_t launch_prologue(pn_ctx *c, const double *x, const double *vel, const
     if (energy_records) {
         k_prologue<2><<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
             c->S, c->d_clu, bc, x, vel, m, c->mrec, c->drec, c->nflag, c->blk);
+        c->launches += 1;
         return cudaGetLastError();
     }
     const bool mixed = c->p.precision == PN_MIXED;
@@ -1414,6 +1417,7 @@ cudaError_t launch_prologue(pn_ctx *c, const double *x, const double *vel, const
     else
         k_prologue<1><<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
             c->S, c->d_clu, bc, x, vel, m, c->mrec, c->drec, c->nflag, c->blk);
+    c->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
@@ -1423,6 +1427,7 @@ cudaError_t launch_prologue(pn_ctx *c, const double *x, const double *vel, const
     else
         k_global_sums<1><<<c->nclu, kGlueThreads, 0, c->stream>>>(
             c->d_clu, c->nclu, c->blk, c->glob, c->ncount, c->nrec, c->ndrec, c->NC);
+    c->launches += 1;
     if ((e = cudaGetLastError()) != cudaSuccess || !c->any_near)
         return e;
     if (mixed)
@@ -1431,6 +1436,7 @@ cudaError_t launch_prologue(pn_ctx *c, const double *x, const double *vel, const
     else
         k_near_scatter<1><<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
             c->d_clu, c->nclu, bc, x, m, c->nflag, c->ncount, c->nrec, c->ndrec, c->NC);
+    c->launches += 1;
     return cudaGetLastError();
 }
 
@@ -1490,6 +1496,7 @@ cudaError_t launch_pass1(pn_ctx *c)
         k_pass_f64<1><<<grid, kF64Threads, 0, c->stream>>>(c->drec, c->S, c->d_clu, blk_table(c),
                                                            c->part + L.p1);
     }
+    c->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (end)
         cudaEventRecord(end, c->stream);
@@ -1510,6 +1517,7 @@ cudaError_t launch_pass2(pn_ctx *c)
         k_pass_f64<2><<<grid, kF64Threads, 0, c->stream>>>(c->drec, c->S, c->d_clu, blk_table(c),
                                                            c->part + L.p2);
     }
+    c->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (end)
         cudaEventRecord(end, c->stream);
@@ -1523,6 +1531,7 @@ static cudaError_t launch_fused_p(pn_ctx *c, const Layout &L)
     timing_begin(c, 1, &end);
     k_fused_mixed<P, UNROLL><<<(unsigned)c->fused_G, kMixThreads, 0, c->stream>>>(
         c->mrec, c->S, c->d_clu, c->nclu, c->fused_units, c->part + L.seg);
+    c->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (end)
         cudaEventRecord(end, c->stream);
@@ -1531,6 +1540,7 @@ static cudaError_t launch_fused_p(pn_ctx *c, const Layout &L)
     k_fused_gather<P><<<(unsigned)(c->S / kGlueThreads), kGlueThreads, 0, c->stream>>>(
         c->part + L.seg, c->S, c->d_clu, blk_table(c), c->fused_units, c->fused_G,
         c->part + L.p1, c->part + L.p2);
+    c->launches += 1;
     return cudaGetLastError();
 }
 
@@ -1586,6 +1596,7 @@ cudaError_t launch_near(pn_ctx *c)
     else
         k_near_f64<<<(unsigned)(c->S / kF64Threads), kF64Threads, 0, c->stream>>>(
             c->drec, c->ndrec, c->ncount, c->S, c->NC, c->d_clu, blk_table(c), pn);
+    c->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (end)
         cudaEventRecord(end, c->stream);
@@ -1601,11 +1612,13 @@ cudaError_t launch_epilogue(pn_ctx *c, const double *x, const double *vel, const
     k_epilogue<<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
         c->S, c->d_clu, blk_table(c), x, vel, m, c->part + L.p1, L.js, c->part + L.p2, L.js,
         pnear, c->nflag, c->glob, a, v, h, c->flag, c->flag_step, step, c->blk);
+    c->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
     k_hole<<<c->nclu, kGlueThreads, 0, c->stream>>>(c->d_clu, c->blk, c->glob, a, v, h, c->flag,
                                                     c->flag_step, step);
+    c->launches += 1;
     return cudaGetLastError();
 }
 
@@ -1616,13 +1629,16 @@ cudaError_t launch_energy(pn_ctx *c, const double *x, const double *v, const dou
         return e;
     k_energy_pairs<<<(unsigned)(c->S / kF64Threads), kF64Threads, 0, c->stream>>>(
         c->drec, c->S, c->d_clu, blk_table(c), c->part);
+    c->launches += 1;
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
     k_energy_epilogue<<<(unsigned)(c->S / kGlueThreads), kGlueThreads, 0, c->stream>>>(
         c->S, c->d_clu, blk_table(c), x, v, m, c->part, c->blk);
+    c->launches += 1;
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
     k_energy_final<<<c->nclu, kGlueThreads, 0, c->stream>>>(c->d_clu, c->blk, v, m, c->eout);
+    c->launches += 1;
     return cudaGetLastError();
 }
 

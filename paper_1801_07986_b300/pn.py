@@ -95,6 +95,7 @@ def _load():
                 "pn_set_timing": [P, I],
                 "pn_get_timing": [P, P, P],
                 "pn_get_launch": [P, P],
+                "pn_launch_count": [P, P],
                 "pn_energy_noalloc": [I, P, I64, D, D, D, P, P, P, P],
                 "pn_measure_peaks": [I, P, P],
             }
@@ -373,6 +374,13 @@ def pn_get_launch(ctx: Context) -> dict:
     _check(_load().pn_get_launch(ctx.handle, out.ctypes.data_as(ctypes.c_void_p)))
     keys = ("threads", "targets_per_thread", "tile", "blocks_i", "jsplit", "occupancy", "sms")
     return {k: int(v) for k, v in zip(keys, out)}
+
+
+def pn_launch_count(ctx: Context) -> int:
+    """Kernels the context has launched so far (graph replays included)."""
+    out = ctypes.c_int64(0)
+    _check(_load().pn_launch_count(ctx.handle, ctypes.byref(out)))
+    return int(out.value)
 
 
 def pn_destroy(ctx: Context) -> None:

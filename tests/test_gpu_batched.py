@@ -91,11 +91,18 @@ def test_batched_steps_match_oracle_and_graph_replays_bitwise(orc):
     A = torch.empty_like(X)
     pn.pn_accel(ctx, X, V, M, A)
     X2, V2, A2 = X.clone(), V.clone(), A.clone()
+    n0 = pn.pn_launch_count(ctx)
     pn.pn_step(ctx, X, V, M, A, dt, 6)
+    n1 = pn.pn_launch_count(ctx)
     pn.pn_step_graph(ctx, X2, V2, M, A2, dt, 3)     # capture + replay
     pn.pn_step_graph(ctx, X2, V2, M, A2, dt, 3)     # replay of the same graph
+    n2 = pn.pn_launch_count(ctx)
     pn.pn_sync(ctx)
     assert torch.equal(X, X2) and torch.equal(V, V2) and torch.equal(A, A2)
+    # one step = kick-drift, prologue, global sums, 2 pair passes, epilogue, hole
+    # (+ scatter and near pass when a star lies within r_near); replays count alike
+    assert n1 - n0 in (6 * 7, 6 * 9)
+    assert n2 - n1 == n1 - n0
     xg = X.cpu().numpy()
     for k, (a, b) in enumerate(zip(off[:-1], off[1:])):
         a0 = orc.accel(x[a:b], v[a:b], m[a:b], c=cs[k], eps=es[k])
