@@ -43,8 +43,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "1PN pair interactions/s at N=16k/128k, mixed vs FP64 on B300 at <=1e-5 rel err"
 FLOPS_PASS1 = 29   # hand count of the mixed pass-1 pair body (FMA = 2, rsqrt = 1)
-FLOPS_PASS2 = 70   # hand count of the mixed pass-2 pair body
-FLOPS_FUSED = 80   # hand count of the fused pair body (pass 1 + pass 2 sharing x, r, rsqrt)
+FLOPS_PASS2 = 67   # hand count of the mixed pass-2 pair body
+FLOPS_FUSED = 77   # hand count of the fused pair body (pass 1 + pass 2 sharing x, r, rsqrt)
 FP32_LANES_PER_SM = 128
 
 
@@ -207,10 +207,9 @@ def config_of(w, precision, args):
 # Source region of each measured kernel (from its first line to the next
 # section marker), so that a committed ncu traffic figure stays valid only
 # while that kernel's own source is unchanged.
-_KERNEL_REGIONS = {
-    "fused_mixed": ("// The pair terms, shared by the two-pass and the fused kernels.",
-                    "// ------------------------------------------------ pair kernels: double --"),
-}
+_FUSED_REGION = ("// The pair terms, shared by the two-pass and the fused kernels.",
+                 "// ------------------------------------------------ pair kernels: double --")
+_KERNEL_REGIONS = {"fused_mixed": _FUSED_REGION, "fused_packed": _FUSED_REGION}
 
 
 def kernel_source_hash(tag: str | None = None):
@@ -317,7 +316,10 @@ def run_native(args, w):
     flops = fpp * pairs
     achieved = flops / (per_launch_ms * 1e-3) / 1e12
     clocks = clk.summary()
-    tag = "fused_mixed" if fused else f"pass{k_dom + 1}_{args.precision}"
+    if fused:
+        tag = "fused_packed" if launch.get("packed") else "fused_mixed"
+    else:
+        tag = f"pass{k_dom + 1}_{args.precision}"
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": profiled_traffic(tag), "kernel": tag,
             "flops_per_pair": fpp,
@@ -333,6 +335,7 @@ def run_native(args, w):
         roof["fp32_fma_microbench_tflops"] = meas["fp32_fma_tflops"]
         roof["frac_of_fma_microbench"] = achieved / meas["fp32_fma_tflops"]
         roof["fp64_fma_microbench_tflops"] = meas["fp64_fma_tflops"]
+        roof["fp32x2_fma_microbench_tflops"] = meas["fp32x2_fma_tflops"]
     except Exception as e:  # reported, not required
         roof["fp32_fma_microbench_error"] = str(e)[:200]
     roof["flops_per_interaction"] = FLOPS_FUSED if fused else FLOPS_PASS1 + FLOPS_PASS2
@@ -397,7 +400,7 @@ def run_native(args, w):
 
     if rank == 0 and not args.no_cpu_baseline:
         try:
-            rows = max(64, min(w.n - 1, 4096))
+            rows = max(64, min(w.n - 1, 16384))
             r, secs, cores = oracle_rate(x, v, m, w, rows, rows)
             line["cpu_baseline"] = {
                 "value": r, "unit": "interactions/s", "cores": cores, "kind": "oracle",

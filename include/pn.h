@@ -180,14 +180,15 @@ pn_status pn_step_graph(pn_ctx *ctx, double *x, double *v, const double *m, doub
                         double dt, int64_t nsteps);
 
 /*
- * Autotuner of the fused pair kernel's launch shape (targets per thread x
- * source-loop unroll): times each candidate on the given state (a is
- * overwritten with A(x, v)) and keeps the fastest; results are cached per
- * workload size bucket for the process.  out (may be NULL): [0] targets per
- * thread, [1] unroll, [2] 1 if the result came from the cache.  Waits.
+ * Autotuner of the fused pair kernel's launch shape (scalar kernel: targets
+ * per thread x source-loop unroll; packed FP32x2 kernel: unroll): times each
+ * candidate on the given state (a is overwritten with A(x, v)) and keeps the
+ * fastest; results are cached per workload size bucket for the process.
+ * out (may be NULL): [0] targets per thread, [1] unroll, [2] 1 if the result
+ * came from the cache, [3] 1 for the packed FP32x2 kernel.  Waits.
  */
 pn_status pn_tune(pn_ctx *ctx, const double *x, const double *v, const double *m, double *a,
-                  int64_t out[3]);
+                  int64_t out[4]);
 
 /*
  * pn_step on HOST arrays: copies x, v, m, a to device buffers owned by the
@@ -229,9 +230,10 @@ pn_status pn_get_timing(pn_ctx *ctx, double ms[3], int64_t launches[3]);
  * Launch shape of the pair kernels for this context: out[0] threads per
  * block, out[1] targets per thread, out[2] sources per shared-memory tile,
  * out[3] blocks along targets, out[4] source splits (two-pass) or
- * persistent blocks (fused), out[5] resident blocks per SM, out[6] SM count.
+ * stream-K workers (fused), out[5] resident blocks per SM, out[6] SM count,
+ * out[7] 1 if the fused kernel is the packed FP32x2 one.
  */
-pn_status pn_get_launch(pn_ctx *ctx, int64_t out[7]);
+pn_status pn_get_launch(pn_ctx *ctx, int64_t out[8]);
 
 /*
  * Number of CUDA kernels this context has launched since pn_init (host-side
@@ -267,11 +269,12 @@ pn_status pn_energy_noalloc(int device, void *cuda_stream, int64_t n, double G, 
 /*
  * Roofline denominators measured on `device` now: out[0] FP32 FMA TFLOP/s,
  * out[1] FP64 FMA TFLOP/s, out[2] single-precision rsqrt Gop/s, out[3] SM
- * count (independent FMA chains on every SM, CUDA-event timed; allocates
- * and frees a small buffer; waits for the stream).  Errors: PN_EINVAL,
- * PN_ENOMEM, PN_ECUDA.
+ * count, out[4] packed FP32x2 FMA TFLOP/s (independent FMA chains on every
+ * SM, CUDA-event timed; allocates and frees a small buffer; waits for the
+ * stream).  The paper has no counterpart.  Errors: PN_EINVAL, PN_ENOMEM,
+ * PN_ECUDA.
  */
-pn_status pn_measure_peaks(int device, void *cuda_stream, double out[4]);
+pn_status pn_measure_peaks(int device, void *cuda_stream, double out[5]);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *pn_last_error(void);

@@ -116,7 +116,7 @@ void set_params(pn_ctx *c, const pn_params *p, bool all_physics)
 
 void free_all(pn_ctx *c)
 {
-    void *bufs[] = {c->vp, c->mrec, c->drec, c->part, c->blk, c->glob, c->eout, c->flag,
+    void *bufs[] = {c->vp, c->mrec, c->drec, c->part, c->blk, c->glob, c->eout, c->flag, c->wcount,
                     c->flag_step, c->hx, c->hv, c->hm, c->ha, c->nrec, c->ndrec, c->ncount,
                     c->nflag, c->rk_x, c->rk_v, c->rk_a, c->rk_sx, c->rk_sv, c->d_clu,
                     c->blk_clu};
@@ -316,11 +316,21 @@ static pn_status init_common(pn_ctx **out, int nclu, const int64_t *off, const p
     c->max_ns_pad = maxp;
     set_params(c, params, false);
 
-    int occ_mix = 0, occ_f64 = 0, occ_fused = 0;
+    int occ_mix = 0, occ_f64 = 0;
     cudaError_t e = pn::occupancy(&occ_mix, &occ_f64);
-    // fused-kernel variant; PN_FUSED_TARGETS / PN_FUSED_UNROLL override (tuning)
-    c->fused_P = 4;          // measured fastest on B300 at N = 131072 (4 targets x 2-way unroll)
+    // fused-kernel variant; PN_FUSED_PACKED / PN_FUSED_TARGETS / PN_FUSED_UNROLL /
+    // PN_FUSED_WORKERS override the default (tuning sweeps)
+    c->fused_packed = true;  // packed FP32x2 kernel, 4 targets per thread, 2-way unroll:
+    c->fused_P = 4;          // measured fastest on B300 at N = 131072
     c->fused_unroll = 2;
+    c->workers_max = pn::kPackWorkersMax;
+    if (const char *pw = std::getenv("PN_FUSED_WORKERS")) {
+        const int v = std::atoi(pw);
+        if (v >= 1 && v <= 64)
+            c->workers_max = v;
+    }
+    if (const char *pk = std::getenv("PN_FUSED_PACKED"))
+        c->fused_packed = std::atoi(pk) != 0;
     if (const char *tp = std::getenv("PN_FUSED_TARGETS")) {
         const int v = std::atoi(tp);
         if (v == 1 || v == 2 || v == 4)
@@ -331,17 +341,40 @@ static pn_status init_common(pn_ctx **out, int nclu, const int64_t *off, const p
         if (v >= 1 && v <= 4)
             c->fused_unroll = v;
     }
+    if (c->fused_packed && c->fused_P != 2)
+        c->fused_P = 4;             // packed kernel: 2 or 4 targets per thread
+    if (c->fused_packed && c->fused_unroll > 2)
+        c->fused_unroll = 2;
+    if (c->fused_P == 2 && c->fused_unroll == 3)
+        c->fused_unroll = 2;
+    if (c->fused_P == 1 && c->fused_unroll > 2)
+        c->fused_unroll = 2;
+    pn::FusedShape fs{};
+    // segment buffer: the largest over every fused variant (the tuner may switch)
+    int64_t seg_max = 0;
+    static const int variants[][3] = {{1, 1, 0}, {1, 2, 0}, {2, 1, 0}, {2, 2, 0}, {2, 4, 0},
+                                      {4, 1, 0}, {4, 2, 0}, {4, 3, 0}, {4, 4, 0},
+                                      {2, 1, 1}, {2, 2, 1}, {4, 1, 1}, {4, 2, 1}};
+    for (const auto &va : variants) {
+        if (e == cudaSuccess)
+            e = pn::fused_shape(c, va[0], va[1], va[2] != 0, &fs);
+        const int64_t seg = (c->S / (pn::kMixThreads * va[0]) + fs.G) * pn::kMixThreads * va[0];
+        if (seg > seg_max)
+            seg_max = seg;
+    }
     if (e == cudaSuccess)
-        e = pn::fused_occupancy(c->fused_P, c->fused_unroll, &occ_fused);
+        e = pn::fused_shape(c, c->fused_P, c->fused_unroll, c->fused_packed, &fs);
     if (e != cudaSuccess) {
         delete[] c->hclu;
         delete c;
         return fail(PN_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
     }
     pn::shapes(c->S, c->max_ns_pad, sms, occ_mix, occ_f64, &c->mix, &c->f64);
-    c->fused_occ = occ_fused > 0 ? occ_fused : 1;
-    c->fused_G = (int64_t)c->fused_occ * sms;
-    c->fused_units = pn::fused_units(c->hclu, nclu, c->fused_P, c->hclu);
+    c->fused_occ = fs.occ;
+    c->fused_grid = fs.grid;
+    c->fused_G = fs.G;
+    c->fused_seg_max = seg_max;
+    c->fused_units = pn::fused_units(c->hclu, nclu, c->fused_P, c->fused_packed, c->hclu);
 
     const int64_t S = c->S;
     int64_t part = (int64_t)c->mix.jsplit * (pn::kP1Vals + pn::kP2Vals) * S;
@@ -351,10 +384,9 @@ static pn_status init_common(pn_ctx **out, int nclu, const int64_t *off, const p
     if ((int64_t)pn::kEVals * S > part)
         part = (int64_t)pn::kEVals * S;
     part += (int64_t)pn::kNearVals * S;   // near-pass partials after both passes
-    // fused layout, for the largest target block (4 targets per thread)
-    const int64_t ti_max = pn::kMixThreads * 4;
+    // fused layout: pass sums, near sums, then the largest segment buffer
     const int64_t part_fused = (int64_t)(pn::kP1Vals + pn::kP2Vals + pn::kNearVals) * S +
-                               (S / pn::kMixThreads + c->fused_G) * pn::kFusedVals * ti_max;
+                               seg_max * pn::kFusedVals;
     if (part_fused > part)
         part = part_fused;
     c->part_len = part;
@@ -379,6 +411,7 @@ static pn_status init_common(pn_ctx **out, int nclu, const int64_t *off, const p
         {(void **)&c->nflag, (size_t)S},
         {(void **)&c->eout, sizeof(double) * 8 * (size_t)nclu},
         {(void **)&c->flag, sizeof(int)},
+        {(void **)&c->wcount, sizeof(int)},
         {(void **)&c->flag_step, sizeof(unsigned long long)},
         {(void **)&c->d_clu, sizeof(pn::Clu) * (size_t)nclu},
         {(void **)&c->blk_clu, sizeof(int) * (size_t)nglue},
@@ -681,7 +714,7 @@ pn_status pn_get_timing(pn_ctx *c, double ms[3], int64_t launches[3])
     return ok();
 }
 
-pn_status pn_get_launch(pn_ctx *c, int64_t out[7])
+pn_status pn_get_launch(pn_ctx *c, int64_t out[8])
 {
     if (check_ctx(c) != PN_OK)
         return PN_EINVAL;
@@ -691,11 +724,12 @@ pn_status pn_get_launch(pn_ctx *c, int64_t out[7])
     const bool fused = pn::use_fused(c);
     out[0] = s.threads;
     out[1] = fused ? c->fused_P : s.targets;
-    out[2] = s.tile;
+    out[2] = fused ? pn::fused_tile_size(c->fused_packed) : s.tile;
     out[3] = s.nblk_i;
     out[4] = fused ? c->fused_G : s.jsplit;
     out[5] = fused ? c->fused_occ : s.occupancy;
     out[6] = c->sm_count;
+    out[7] = fused && c->fused_packed ? 1 : 0;
     return ok();
 }
 
@@ -720,17 +754,25 @@ struct TuneKey {
     }
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, std::pair<int, int>> g_tune;
+struct Variant {
+    int P, unroll, packed;
+};
+std::map<TuneKey, Variant> g_tune;
 
-pn_status apply_variant(pn_ctx *c, int P, int unroll)
+pn_status apply_variant(pn_ctx *c, Variant va)
 {
-    int occ = 0;
-    PN_CUDA(pn::fused_occupancy(P, unroll, &occ), "occupancy");
-    c->fused_P = P;
-    c->fused_unroll = unroll;
-    c->fused_occ = occ > 0 ? occ : 1;
-    c->fused_G = (int64_t)c->fused_occ * c->sm_count;
-    c->fused_units = pn::fused_units(c->hclu, c->nclu, P, c->hclu);
+    pn::FusedShape fs{};
+    PN_CUDA(pn::fused_shape(c, va.P, va.unroll, va.packed != 0, &fs), "occupancy");
+    const int64_t seg = (c->S / (pn::kMixThreads * va.P) + fs.G) * pn::kMixThreads * va.P;
+    if (seg > c->fused_seg_max)
+        return fail(PN_EINVAL, "fused variant needs a larger segment buffer");
+    c->fused_P = va.P;
+    c->fused_unroll = va.unroll;
+    c->fused_packed = va.packed != 0;
+    c->fused_occ = fs.occ;
+    c->fused_grid = fs.grid;
+    c->fused_G = fs.G;
+    c->fused_units = pn::fused_units(c->hclu, c->nclu, va.P, c->fused_packed, c->hclu);
     if (c->graph_exec) {              // the captured graph holds the old launch shape
         cudaGraphExecDestroy(c->graph_exec);
         c->graph_exec = nullptr;
@@ -740,7 +782,7 @@ pn_status apply_variant(pn_ctx *c, int P, int unroll)
 }  // namespace
 
 pn_status pn_tune(pn_ctx *c, const double *x, const double *v, const double *m, double *a,
-                  int64_t out[3])
+                  int64_t out[4])
 {
     if (check_ctx(c) != PN_OK)
         return PN_EINVAL;
@@ -748,7 +790,8 @@ pn_status pn_tune(pn_ctx *c, const double *x, const double *v, const double *m, 
         return fail(PN_EINVAL, "pn_tune: NULL array");
     DeviceGuard g(c->device);
     PN_CUDA(g.err, "cudaSetDevice");
-    static const int cand[][2] = {{2, 1}, {2, 2}, {4, 1}, {4, 2}};
+    static const Variant cand[] = {{2, 1, 0}, {2, 2, 0}, {4, 1, 0}, {4, 2, 0},
+                                   {2, 1, 1}, {2, 2, 1}, {4, 1, 1}, {4, 2, 1}};
     int64_t work = 0;                         // pair work of all clusters, in tiles^2
     for (int k = 0; k < c->nclu; ++k)
         work += (c->hclu[k].ns_pad / pn::kMixTile) * (c->hclu[k].ns_pad / pn::kMixTile);
@@ -756,15 +799,14 @@ pn_status pn_tune(pn_ctx *c, const double *x, const double *v, const double *m, 
     for (int64_t u = work; u > 1; u >>= 1)
         ++bucket;
     const TuneKey key{bucket, c->nclu > 1 ? 1 : 0};
-    int bestP = c->fused_P, bestU = c->fused_unroll;
+    Variant best{c->fused_P, c->fused_unroll, c->fused_packed ? 1 : 0};
     double best_ms = -1.0;
     bool cached = false;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune.find(key);
         if (it != g_tune.end()) {
-            bestP = it->second.first;
-            bestU = it->second.second;
+            best = it->second;
             cached = true;
         }
     }
@@ -774,8 +816,8 @@ pn_status pn_tune(pn_ctx *c, const double *x, const double *v, const double *m, 
         PN_CUDA(cudaEventCreate(&e1), "event");
         const int was_timing = c->timing_on;
         c->timing_on = 0;
-        for (auto &cv : cand) {
-            pn_status st = apply_variant(c, cv[0], cv[1]);
+        for (const Variant &cv : cand) {
+            pn_status st = apply_variant(c, cv);
             if (st != PN_OK)
                 return st;
             PN_CUDA(cudaMemcpyAsync(c->vp, v, sizeof(double) * 3 * (size_t)c->n,
@@ -794,23 +836,23 @@ pn_status pn_tune(pn_ctx *c, const double *x, const double *v, const double *m, 
             PN_CUDA(cudaEventElapsedTime(&ms, e0, e1), "event time");
             if (best_ms < 0.0 || ms < best_ms) {
                 best_ms = ms;
-                bestP = cv[0];
-                bestU = cv[1];
+                best = cv;
             }
         }
         c->timing_on = was_timing;
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         std::lock_guard<std::mutex> lock(g_tune_mu);
-        g_tune[key] = {bestP, bestU};
+        g_tune[key] = best;
     }
-    pn_status st = apply_variant(c, bestP, bestU);
+    pn_status st = apply_variant(c, best);
     if (st != PN_OK)
         return st;
     if (out) {
-        out[0] = bestP;
-        out[1] = bestU;
+        out[0] = best.P;
+        out[1] = best.unroll;
         out[2] = cached ? 1 : 0;
+        out[3] = best.packed;
     }
     return ok();
 }

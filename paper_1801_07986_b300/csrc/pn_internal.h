@@ -13,6 +13,10 @@ namespace pn {
 constexpr int kMixThreads = 128;   // threads per block
 constexpr int kMixTargets = 2;     // targets held in registers per thread
 constexpr int kMixTile = 128;      // sources per shared-memory tile
+constexpr int kFlushTiles = 2;     // fused kernel: tiles per single-precision partial
+constexpr int kPackTile = 64;      // packed fused kernel: sources per shared-memory tile
+constexpr int kPackFlushTiles = 4; // packed fused kernel: tiles per single-precision partial
+constexpr int kPackWorkersMax = 4;  // packed fused kernel: stream-K workers per resident block (max)
 // Launch shape of the double-precision pair kernels (FP64 mode and energy).
 constexpr int kF64Threads = 128;
 constexpr int kF64Targets = 1;
@@ -25,7 +29,7 @@ constexpr int kGlueThreads = 256;
 
 // Values per star written by each pair kernel into its partial-sum buffer.
 constexpr int kP1Vals = 6;         // N (3), U, Z, Wr
-constexpr int kP2Vals = 9;         // V (3), H (3), E (3)
+constexpr int kP2Vals = 10;        // V' (3), Hs (1), Hv (3), E (3)
 constexpr int kEVals = 8;          // pot, Smv (3), Snn, Spx (3)
 constexpr int kFusedVals = kP1Vals + kP2Vals;
 // Near-source pass: sources per tile and values per target.
@@ -86,10 +90,15 @@ struct pn_ctx {
     int sm_count;
     pn::Shape mix, f64;
     int fused_P;             // targets per thread of the fused kernel (1, 2 or 4)
+    bool fused_packed;       // packed FP32x2 fused kernel (4 targets per thread)
     int fused_unroll;        // source-loop unroll of the fused kernel (1 or 2)
     int fused_occ;           // resident fused-kernel blocks per SM
-    int64_t fused_G;         // persistent blocks of the fused kernel
+    int64_t fused_grid;      // blocks of the persistent fused kernel (resident)
+    int64_t fused_G;         // stream-K workers of the fused kernel
+    int64_t fused_seg_max;   // segment buffer length (doubles / kFusedVals), all variants
     int64_t fused_units;     // work units of the fused kernel (all clusters)
+    int *wcount;             // next stream-K worker of the packed kernel (zeroed by the prologue)
+    int workers_max;         // packed kernel: stream-K workers per resident block, at most
 
     // scratch, all owned by the context
     double *vp;          // n x 3: velocity at which the force is evaluated
@@ -154,9 +163,15 @@ pn_status set_error(pn_status s, const char *fmt, ...);
 void shapes(int64_t S, int64_t max_ns_pad, int sm_count, int occ_mix, int occ_f64, Shape *mix,
             Shape *f64);
 cudaError_t occupancy(int *occ_mix, int *occ_f64);
-cudaError_t fused_occupancy(int P, int unroll, int *occ);
+cudaError_t fused_occupancy(int P, int unroll, bool packed, int *occ);
 cudaError_t launch_fused(pn_ctx *c);
 bool use_fused(const pn_ctx *c);
-int64_t fused_units(const Clu *h, int nclu, int P, Clu *out);
+int fused_tile_size(bool packed);
+struct FusedShape {
+    int occ;                 // resident blocks per SM
+    int64_t grid, G, units;  // blocks launched, stream-K workers, work units
+};
+cudaError_t fused_shape(const pn_ctx *c, int P, int unroll, bool packed, FusedShape *out);
+int64_t fused_units(const Clu *h, int nclu, int P, bool packed, Clu *out);
 
 }  // namespace pn

@@ -187,8 +187,9 @@ __device__ __forceinline__ int cluster_of_block(const int *__restrict__ blk_clu,
 //   Q = sum m_j v_j, W = sum w_j (all), W_far = sum_far w_j,
 //   SA_far = sum_far 5 m_j/(4 R_j), SB_far = sum_far m_j (R_j^2 + eps^2)/(4 R_j^3),
 //   Phi = sum m_j / R_j, and the number of near stars.
-// Records: mixed  A = (hi(d), m) B = (lo(d), R^2) C = (v, c/1.5) D = (e/1.5, 0) E = (w, 0)
-//          double A = (d, m)     B = (v, R^2)    C = (e/1.5, c/1.5) D = (w, 0)
+// Records, with C = c/1.5 - 4/3 |v|^2:
+//          mixed  A = (hi(d), m) B = (lo(d), R^2) C = (v, C) D = (-e/1.5, 0) E = (w, 0)
+//          double A = (d, m)     B = (v, R^2)    C = (-e/1.5, C)   D = (w, 0)
 // Energy records (double): A = (d, m), B = (v, 0).
 template <int MODE>   // 0 mixed, 1 double, 2 energy
 __global__ void __launch_bounds__(kGlueThreads)
@@ -196,10 +197,12 @@ k_prologue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
            const double *__restrict__ x, const double *__restrict__ vel,
            const double *__restrict__ m, float4 *__restrict__ mrec,
            double4_32a *__restrict__ drec, unsigned char *__restrict__ nflag,
-           double *__restrict__ blk)
+           double *__restrict__ blk, int *__restrict__ wcount)
 {
     __shared__ double sh[kGlobVals][kGlueThreads];
     const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
+    if (wcount && t == 0)
+        *wcount = 0;          // the packed pair kernel's worker counter, for this evaluation
     const Clu C = clu[cluster_of_block(blk_clu, blockIdx.x)];
     const int64_t lt = t - C.slot0;
     const double G = C.G, eps2 = C.eps2;
@@ -223,7 +226,8 @@ k_prologue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
         const double cj = far * G * M * (1.5 * iR + 0.25 * eps2 * iR3);
         const double ef = far * 0.5 * G * M * iR3;
         const double wf = mj * iR3;
-        const double c3 = cj / 1.5, e3 = ef / 1.5;
+        const double c3 = cj / 1.5 - (4.0 / 3.0) * (v0 * v0 + v1 * v1 + v2 * v2);
+        const double e3 = -ef / 1.5;
         if (MODE == 0) {
             const float h0 = (float)d0, h1 = (float)d1, h2 = (float)d2;
             mrec[t] = make_float4(h0, h1, h2, (float)mj);
@@ -236,7 +240,7 @@ k_prologue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
         } else if (MODE == 1) {
             drec[t] = make_double4_32a(d0, d1, d2, mj);
             drec[S + t] = make_double4_32a(v0, v1, v2, R2);
-            drec[2 * S + t] = make_double4_32a(e3 * d0, e3 * d1, e3 * d2, c3);
+            drec[2 * S + t] = make_double4_32a(e3 * d0, e3 * d1, e3 * d2, c3);   // (-e/1.5, C)
             drec[3 * S + t] = make_double4_32a(far * wf * d0, far * wf * d1, far * wf * d2, 0.0);
         } else {
             drec[t] = make_double4_32a(d0, d1, d2, mj);
@@ -399,13 +403,15 @@ k_near_scatter(const Clu *__restrict__ clu, int nclu, const int *__restrict__ bl
 
 struct MixTarget {
     float hx, hy, hz, lx, ly, lz;   // hi/lo split of d_i
-    float vx, vy, vz;               // velocity of target i (pass 2)
+    float vx, vy, vz;               // 8/3 v_i, v_i the velocity of target i (pass 2)
 };
 
 // The pair terms, shared by the two-pass and the fused kernels.  Records of
-// source j: A = (hi(d_j), m_j), B = (lo(d_j), R_j^2), C = (v_j, c_j/1.5),
-// D = (e_j/1.5, 0), E = (w_j, 0).  x_ij = (hi_i - hi_j) + (lo_i - lo_j)
-// keeps ~48 bits of the difference.
+// source j: A = (hi(d_j), m_j), B = (lo(d_j), R_j^2), C = (v_j, C_j),
+// D = (-e_j/1.5, 0), E = (w_j, 0) with C_j = c_j/1.5 - 4/3 |v_j|^2.
+// x_ij = (hi_i - hi_j) + (lo_i - lo_j) keeps ~48 bits of the difference.
+constexpr float kEightThirds = 8.0f / 3.0f;
+
 struct PairGeo {
     float dx, dy, dz, s2, is, mj, mis, mis3;
     float wx, wy, wz;
@@ -443,38 +449,42 @@ __device__ __forceinline__ void pass1_terms(const PairGeo &g, float Rj2, float *
     acc[5] = fmaf(g.mis3, Rj2, acc[5]);
 }
 
-// Pass-2 sums (velocities are those at which A is taken), with
-// kappa' = (v_j.x_ij)^2/r^2 + c_j/1.5 - (e_j/1.5).d_i - 4/3 |v_ij|^2:
-//   V' += m_j x_ij/r^3 kappa'                       (V = 3/2 V')
-//   H' += m_j/r^3 [x_ij.v_i - 3/4 x_ij.v_j] v_ij     (H = 4 H')
+// Pass-2 sums (velocities are those at which A is taken).  With
+// |v_ij|^2 = |v_i|^2 + |v_j|^2 - 2 v_i.v_j, the per-pair factor of Eq. 6
+// lines 3 and 6 is kappa_ij - 4/3 |v_i|^2, where
+//   kappa_ij = (v_j.x_ij)^2/r^2 + C_j - (e_j/1.5).d_i + 8/3 v_i.v_j,
+// and the |v_i|^2 part, a constant of target i, multiplies N_i (added by the
+// epilogue).  Sums:
+//   V' += m_j x_ij/r^3 kappa_ij                  (V = 3/2 (V' - 4/3 |v_i|^2 N_i))
+//   Hs += g_ij,  Hv += g_ij v_j,  g_ij = m_j/r^3 [x_ij.(8/3 v_i) - 2 x_ij.v_j]
+//                                                (H = 3/2 (Hs v_i - Hv))
 //   E  += w_j / r
 // V carries Eq. 6 line 3 (without its 4/R_i part) and line 6 (without its
 // v_i^2 part): with r_ij^2 - R_i^2 = R_j^2 + eps^2 - 2 d_i.d_j, line 3's
-// bracket is 4/R_i + (c_j - e_j.d_i)/(G M).  H is Eq. 6 line 7, E the 1/r_ij
-// part of line 4.
+// bracket is 4/R_i + (c_j - e_j.d_i)/(G M).  H is Eq. 6 line 7 (its bracket
+// x_ij.v_i - 3/4 x_ij.v_j is 3/8 of g's), E the 1/r_ij part of line 4.
 __device__ __forceinline__ void pass2_terms(const PairGeo &g, const MixTarget &tg,
                                             const float4 &C, const float4 &D, float wx, float wy,
                                             float wz, float *acc)
 {
     const float is2 = g.is * g.is;
-    const float ux = tg.vx - C.x, uy = tg.vy - C.y, uz = tg.vz - C.z;
-    const float u2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
     const float xvj = fmaf(g.dx, C.x, fmaf(g.dy, C.y, g.dz * C.z));
     const float xvi = fmaf(g.dx, tg.vx, fmaf(g.dy, tg.vy, g.dz * tg.vz));
-    const float ed = fmaf(D.x, tg.hx, fmaf(D.y, tg.hy, D.z * tg.hz));
+    float k = fmaf(tg.vx, C.x, fmaf(tg.vy, C.y, fmaf(tg.vz, C.z, C.w)));
+    k = fmaf(D.x, tg.hx, fmaf(D.y, tg.hy, fmaf(D.z, tg.hz, k)));
     const float h = xvj * is2;
-    const float kap = fmaf(h, xvj, fmaf(-4.0f / 3.0f, u2, C.w - ed));
-    const float f = g.mis3 * kap;
+    const float f = g.mis3 * fmaf(h, xvj, k);
     acc[0] = fmaf(f, g.dx, acc[0]);
     acc[1] = fmaf(f, g.dy, acc[1]);
     acc[2] = fmaf(f, g.dz, acc[2]);
-    const float gg = g.mis3 * fmaf(-0.75f, xvj, xvi);
-    acc[3] = fmaf(gg, ux, acc[3]);
-    acc[4] = fmaf(gg, uy, acc[4]);
-    acc[5] = fmaf(gg, uz, acc[5]);
-    acc[6] = fmaf(wx, g.is, acc[6]);
-    acc[7] = fmaf(wy, g.is, acc[7]);
-    acc[8] = fmaf(wz, g.is, acc[8]);
+    const float gg = g.mis3 * fmaf(-2.0f, xvj, xvi);
+    acc[3] += gg;
+    acc[4] = fmaf(gg, C.x, acc[4]);
+    acc[5] = fmaf(gg, C.y, acc[5]);
+    acc[6] = fmaf(gg, C.z, acc[6]);
+    acc[7] = fmaf(wx, g.is, acc[7]);
+    acc[8] = fmaf(wy, g.is, acc[8]);
+    acc[9] = fmaf(wz, g.is, acc[9]);
 }
 
 template <bool MASK>
@@ -553,7 +563,9 @@ k_pass_mixed(const float4 *__restrict__ rec, int64_t S, const Clu *__restrict__ 
         tg[p].lx = B.x; tg[p].ly = B.y; tg[p].lz = B.z;
         if constexpr (PASS == 2) {
             const float4 Cc = rec[2 * S + ti[p]];
-            tg[p].vx = Cc.x; tg[p].vy = Cc.y; tg[p].vz = Cc.z;
+            tg[p].vx = kEightThirds * Cc.x;
+            tg[p].vy = kEightThirds * Cc.y;
+            tg[p].vz = kEightThirds * Cc.z;
         } else {
             tg[p].vx = tg[p].vy = tg[p].vz = 0.0f;
         }
@@ -690,11 +702,19 @@ k_fused_mixed(const float4 *__restrict__ rec, int64_t S, const Clu *__restrict__
             const float4 Cc = rec[2 * S + ti[p]];
             tg[p].hx = A.x; tg[p].hy = A.y; tg[p].hz = A.z;
             tg[p].lx = B.x; tg[p].ly = B.y; tg[p].lz = B.z;
-            tg[p].vx = Cc.x; tg[p].vy = Cc.y; tg[p].vz = Cc.z;
+            tg[p].vx = kEightThirds * Cc.x;
+            tg[p].vy = kEightThirds * Cc.y;
+            tg[p].vz = kEightThirds * Cc.z;
 #pragma unroll
             for (int k = 0; k < kFusedVals; ++k)
                 run[k][p][threadIdx.x] = make_float2(0.0f, 0.0f);
         }
+        float acc[P][kFusedVals];
+#pragma unroll
+        for (int p = 0; p < P; ++p)
+#pragma unroll
+            for (int k = 0; k < kFusedVals; ++k)
+                acc[p][k] = 0.0f;
         for (; u < uend; ++u) {
             const int64_t j0 = C.slot0 + (u - ub) * kMixTile;
             __syncthreads();
@@ -704,25 +724,24 @@ k_fused_mixed(const float4 *__restrict__ rec, int64_t S, const Clu *__restrict__
                     sh[k][q] = rec[k * S + j0 + q];
             }
             __syncthreads();
-            float acc[P][kFusedVals];
-#pragma unroll
-            for (int p = 0; p < P; ++p)
-#pragma unroll
-                for (int k = 0; k < kFusedVals; ++k)
-                    acc[p][k] = 0.0f;
             const bool diag = (j0 < t0 + TI) && (t0 < j0 + kMixTile);
             if (diag)
                 fused_tile<P, UNROLL, true>(sh[0], sh[1], sh[2], sh[3], sh[4], j0, tg, ti, eps2, acc);
             else
                 fused_tile<P, UNROLL, false>(sh[0], sh[1], sh[2], sh[3], sh[4], j0, tg, ti, eps2, acc);
+            // single-precision partials span kFlushTiles tiles (aligned to the
+            // target block's tiles) before they go into the running sums
+            if (((u - ub + 1) % kFlushTiles) == 0 || u + 1 == uend) {
 #pragma unroll
-            for (int p = 0; p < P; ++p)
+                for (int p = 0; p < P; ++p)
 #pragma unroll
-                for (int k = 0; k < kFusedVals; ++k) {
-                    float2 r = run[k][p][threadIdx.x];
-                    ds_add(r.x, r.y, acc[p][k]);
-                    run[k][p][threadIdx.x] = r;
-                }
+                    for (int k = 0; k < kFusedVals; ++k) {
+                        float2 r = run[k][p][threadIdx.x];
+                        ds_add(r.x, r.y, acc[p][k]);
+                        run[k][p][threadIdx.x] = r;
+                        acc[p][k] = 0.0f;
+                    }
+            }
         }
         double *out = part + (t0 / TI + blockIdx.x) * (int64_t)(kFusedVals * TI);
 #pragma unroll
@@ -735,13 +754,226 @@ k_fused_mixed(const float4 *__restrict__ rec, int64_t S, const Clu *__restrict__
     }
 }
 
+// ------------------------------------- fused pair kernel: packed FP32x2 --
+
+// The fused pair terms on packed pairs of floats: lane x belongs to target
+// 2q, lane y to target 2q + 1 of the same thread, both against the same
+// source j.  fma.rn.f32x2 / add.rn.f32x2 / mul.rn.f32x2 (sm_100 family) do
+// two FP32 operations per instruction, so the pair arithmetic needs half the
+// instruction issue slots of the scalar kernel while the FP32 pipe does the
+// same work; the rounding of every operation is that of the scalar kernel.
+// Each source is staged in shared memory with every field duplicated
+// (f, f), so that a 128-bit load yields two ready packed operands:
+//   S0 = (-hx, -hy)  S1 = (-hz, m)   S2 = (-lx, -ly)  S3 = (-lz, R^2)
+//   S4 = (vx, vy)    S5 = (vz, C)    S6 = (Dx, Dy)    S7 = (Dz, wx)   S8 = (wy, wz)
+// (h, l = hi/lo split of d_j, D = -e_j/1.5, C = c_j/1.5 - 4/3 |v_j|^2, w = w_j).
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 lo2(const float4 &f) { return make_float2(f.x, f.y); }
+__device__ __forceinline__ float2 hi2(const float4 &f) { return make_float2(f.z, f.w); }
+
+struct PackTarget {
+    float2 hx, hy, hz, lx, ly, lz;   // hi/lo split of d_i (lanes: two targets)
+    float2 vx, vy, vz;               // 8/3 v_i
+};
+
+constexpr int kPackVals = 9;         // float4 per staged source
+
+template <bool MASK>
+__device__ __forceinline__ void packed_pair(const PackTarget &tg, const float4 *__restrict__ sq,
+                                            float2 eps2, bool selfx, bool selfy,
+                                            float2 (&acc)[kFusedVals])
+{
+    const float4 S0 = sq[0], S1 = sq[1], S2 = sq[2], S3 = sq[3];
+    const float2 dx = add2(add2(tg.hx, lo2(S0)), add2(tg.lx, lo2(S2)));
+    const float2 dy = add2(add2(tg.hy, hi2(S0)), add2(tg.ly, hi2(S2)));
+    const float2 dz = add2(add2(tg.hz, lo2(S1)), add2(tg.lz, lo2(S3)));
+    float2 s2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, eps2)));
+    float2 m = hi2(S1);
+    const float4 S7 = sq[7], S8 = sq[8];
+    float2 wx = hi2(S7), wy = lo2(S8), wz = hi2(S8);
+    if (MASK) {
+        if (selfx) {
+            s2.x = 1.0f; m.x = 0.0f; wx.x = 0.0f; wy.x = 0.0f; wz.x = 0.0f;
+        }
+        if (selfy) {
+            s2.y = 1.0f; m.y = 0.0f; wx.y = 0.0f; wy.y = 0.0f; wz.y = 0.0f;
+        }
+    }
+    const float2 is = make_float2(rsqrt_approx(s2.x), rsqrt_approx(s2.y));
+    const float2 is2 = mul2(is, is);
+    const float2 mis = mul2(m, is);
+    const float2 mis3 = mul2(mis, is2);
+    acc[0] = fma2(mis3, dx, acc[0]);
+    acc[1] = fma2(mis3, dy, acc[1]);
+    acc[2] = fma2(mis3, dz, acc[2]);
+    acc[3] = add2(acc[3], mis);
+    acc[4] = add2(acc[4], mis3);
+    acc[5] = fma2(mis3, hi2(S3), acc[5]);
+    const float4 S4 = sq[4], S5 = sq[5], S6 = sq[6];
+    const float2 vx = lo2(S4), vy = hi2(S4), vz = lo2(S5);
+    const float2 xvj = fma2(dx, vx, fma2(dy, vy, mul2(dz, vz)));
+    const float2 xvi = fma2(dx, tg.vx, fma2(dy, tg.vy, mul2(dz, tg.vz)));
+    float2 k = fma2(tg.vx, vx, fma2(tg.vy, vy, fma2(tg.vz, vz, hi2(S5))));
+    k = fma2(lo2(S6), tg.hx, fma2(hi2(S6), tg.hy, fma2(lo2(S7), tg.hz, k)));
+    const float2 h = mul2(xvj, is2);
+    const float2 f = mul2(mis3, fma2(h, xvj, k));
+    acc[6] = fma2(f, dx, acc[6]);
+    acc[7] = fma2(f, dy, acc[7]);
+    acc[8] = fma2(f, dz, acc[8]);
+    const float2 gg = mul2(mis3, fma2(make_float2(-2.0f, -2.0f), xvj, xvi));
+    acc[9] = add2(acc[9], gg);
+    acc[10] = fma2(gg, vx, acc[10]);
+    acc[11] = fma2(gg, vy, acc[11]);
+    acc[12] = fma2(gg, vz, acc[12]);
+    acc[13] = fma2(wx, is, acc[13]);
+    acc[14] = fma2(wy, is, acc[14]);
+    acc[15] = fma2(wz, is, acc[15]);
+}
+
+template <int NP, int UNROLL, bool MASK>
+__device__ __forceinline__ void packed_tile(const float4 (*__restrict__ sh)[kPackVals], int64_t j0,
+                                            int64_t t0, const PackTarget (&tg)[NP], float2 eps2,
+                                            float2 (&acc)[NP][kFusedVals])
+{
+#pragma unroll UNROLL
+    for (int q = 0; q < kPackTile; ++q) {
+        const int64_t j = j0 + q;
+#pragma unroll
+        for (int pp = 0; pp < NP; ++pp) {
+            const int64_t tx = t0 + (2 * pp) * kMixThreads + threadIdx.x;
+            const bool selfx = MASK && j == tx;
+            const bool selfy = MASK && j == tx + kMixThreads;
+            packed_pair<MASK>(tg[pp], sh[q], eps2, selfx, selfy, acc[pp]);
+        }
+    }
+}
+
+// Stream-K over G workers like k_fused_mixed (worker w owns units
+// [w T / G, (w+1) T / G) and writes its segments to slots (target block + w)),
+// with P = 2 NP targets per thread (target pairs (0, 1), (2, 3)) and source
+// tiles of kPackTile.  The resident blocks take workers from a counter
+// (zeroed by the prologue) instead of one fixed worker each: blocks that share
+// an SM advance at unequal rates under the warp scheduler's priorities, and
+// with fixed assignments an SM would end its share with a fraction of its
+// warps.  A worker's result does not depend on which block runs it, so the
+// sums stay deterministic.
+template <int NP, int UNROLL>
+__global__ void __launch_bounds__(kMixThreads, NP == 2 ? 3 : 5)
+k_fused_packed(const float4 *__restrict__ rec, int64_t S, const Clu *__restrict__ clu, int nclu,
+               int64_t total_units, int64_t G, int *__restrict__ wcount,
+               double *__restrict__ part)
+{
+    constexpr int P = 2 * NP, TI = kMixThreads * P;
+    __shared__ float4 sh[kPackTile][kPackVals];
+    __shared__ float2 run[kFusedVals][P][kMixThreads];
+    __shared__ int s_w;
+    for (;;) {
+        __syncthreads();                              // s_w and the tile are free
+        if (threadIdx.x == 0)
+            s_w = atomicAdd(wcount, 1);
+        __syncthreads();
+        const int64_t w = s_w;
+        if (w >= G)
+            break;
+        int64_t u = w * total_units / G;
+        const int64_t u1 = (w + 1) * total_units / G;
+        while (u < u1) {
+            const Clu C = clu[cluster_of_unit(clu, nclu, u)];
+            const int64_t ntiles = C.ns_pad / kPackTile;
+            const int64_t ib = (u - C.unit0) / ntiles;
+            const int64_t t0 = C.slot0 + ib * TI;
+            const int64_t ub = C.unit0 + ib * ntiles;
+            const int64_t uend = ub + ntiles < u1 ? ub + ntiles : u1;
+            const float e2 = (float)C.eps2;
+            const float2 eps2 = make_float2(e2, e2);
+            PackTarget tg[NP];
+#pragma unroll
+            for (int pp = 0; pp < NP; ++pp) {
+                const int64_t ta = t0 + (2 * pp) * kMixThreads + threadIdx.x, tb = ta + kMixThreads;
+                const float4 Aa = rec[ta], Ab = rec[tb];
+                const float4 Ba = rec[S + ta], Bb = rec[S + tb];
+                const float4 Ca = rec[2 * S + ta], Cb = rec[2 * S + tb];
+                tg[pp].hx = make_float2(Aa.x, Ab.x);
+                tg[pp].hy = make_float2(Aa.y, Ab.y);
+                tg[pp].hz = make_float2(Aa.z, Ab.z);
+                tg[pp].lx = make_float2(Ba.x, Bb.x);
+                tg[pp].ly = make_float2(Ba.y, Bb.y);
+                tg[pp].lz = make_float2(Ba.z, Bb.z);
+                tg[pp].vx = make_float2(kEightThirds * Ca.x, kEightThirds * Cb.x);
+                tg[pp].vy = make_float2(kEightThirds * Ca.y, kEightThirds * Cb.y);
+                tg[pp].vz = make_float2(kEightThirds * Ca.z, kEightThirds * Cb.z);
+            }
+#pragma unroll
+            for (int p = 0; p < P; ++p)
+#pragma unroll
+                for (int k = 0; k < kFusedVals; ++k)
+                    run[k][p][threadIdx.x] = make_float2(0.0f, 0.0f);
+            float2 acc[NP][kFusedVals];
+#pragma unroll
+            for (int pp = 0; pp < NP; ++pp)
+#pragma unroll
+                for (int k = 0; k < kFusedVals; ++k)
+                    acc[pp][k] = make_float2(0.0f, 0.0f);
+            for (; u < uend; ++u) {
+                const int64_t j0 = C.slot0 + (u - ub) * kPackTile;
+                __syncthreads();
+                if (threadIdx.x < kPackTile) {
+                    const int64_t j = j0 + threadIdx.x;
+                    const float4 A = rec[j], B = rec[S + j], Cs = rec[2 * S + j];
+                    const float4 D = rec[3 * S + j], E = rec[4 * S + j];
+                    float4 *o = sh[threadIdx.x];
+                    o[0] = make_float4(-A.x, -A.x, -A.y, -A.y);
+                    o[1] = make_float4(-A.z, -A.z, A.w, A.w);
+                    o[2] = make_float4(-B.x, -B.x, -B.y, -B.y);
+                    o[3] = make_float4(-B.z, -B.z, B.w, B.w);
+                    o[4] = make_float4(Cs.x, Cs.x, Cs.y, Cs.y);
+                    o[5] = make_float4(Cs.z, Cs.z, Cs.w, Cs.w);
+                    o[6] = make_float4(D.x, D.x, D.y, D.y);
+                    o[7] = make_float4(D.z, D.z, E.x, E.x);
+                    o[8] = make_float4(E.y, E.y, E.z, E.z);
+                }
+                __syncthreads();
+                const bool diag = (j0 < t0 + TI) && (t0 < j0 + kPackTile);
+                if (diag)
+                    packed_tile<NP, UNROLL, true>(sh, j0, t0, tg, eps2, acc);
+                else
+                    packed_tile<NP, UNROLL, false>(sh, j0, t0, tg, eps2, acc);
+                if (((u - ub + 1) % kPackFlushTiles) == 0 || u + 1 == uend) {
+#pragma unroll
+                    for (int pp = 0; pp < NP; ++pp)
+#pragma unroll
+                        for (int k = 0; k < kFusedVals; ++k) {
+                            float2 r = run[k][2 * pp][threadIdx.x];
+                            ds_add(r.x, r.y, acc[pp][k].x);
+                            run[k][2 * pp][threadIdx.x] = r;
+                            r = run[k][2 * pp + 1][threadIdx.x];
+                            ds_add(r.x, r.y, acc[pp][k].y);
+                            run[k][2 * pp + 1][threadIdx.x] = r;
+                            acc[pp][k] = make_float2(0.0f, 0.0f);
+                        }
+                }
+            }
+            double *out = part + (t0 / TI + w) * (int64_t)(kFusedVals * TI);
+#pragma unroll
+            for (int p = 0; p < P; ++p)
+#pragma unroll
+                for (int k = 0; k < kFusedVals; ++k) {
+                    const float2 r = run[k][p][threadIdx.x];
+                    out[k * TI + p * kMixThreads + threadIdx.x] = (double)r.x + (double)r.y;
+                }
+        }
+    }
+}
+
 // Sums, for every star slot, the stream-K segments that cover its target
 // block (in block order) into the pass-1 / pass-2 partial layout with one
 // split: p1[k][t] (k < kP1Vals), p2[k][t] (k < kP2Vals).
 template <int P>
 __global__ void __launch_bounds__(kGlueThreads)
 k_fused_gather(const double *__restrict__ part, int64_t S, const Clu *__restrict__ clu,
-               const int *__restrict__ blk_clu, int64_t total_units, int64_t G,
+               const int *__restrict__ blk_clu, int64_t total_units, int64_t G, int tile,
                double *__restrict__ p1, double *__restrict__ p2)
 {
     constexpr int TI = kMixThreads * P;
@@ -749,7 +981,7 @@ k_fused_gather(const double *__restrict__ part, int64_t S, const Clu *__restrict
     if (t >= S)
         return;
     const Clu C = clu[cluster_of_block(blk_clu, blockIdx.x)];
-    const int64_t ntiles = C.ns_pad / kMixTile;
+    const int64_t ntiles = C.ns_pad / tile;
     const int64_t ib = (t - C.slot0) / TI;
     const int64_t gtb = t / TI;                                 // global target block
     const int lt = (int)(t - gtb * TI);
@@ -783,7 +1015,8 @@ k_fused_gather(const double *__restrict__ part, int64_t S, const Clu *__restrict
 // ------------------------------------------------ pair kernels: double --
 
 // The same pair sums as pass 1 / pass 2 above, in double precision
-// (records A = (d, m), B = (v, R^2), C = (e/1.5, c/1.5), D = (w, 0)).
+// (records A = (d, m), B = (v, R^2), C = (-e/1.5, C), D = (w, 0); vi is
+// 8/3 times the target's velocity).
 template <int PASS, bool MASK>
 __device__ __forceinline__ void f64_tile(const double4_32a (*__restrict__ sh)[kF64Tile], int64_t j0,
                                          const double (&di)[3], const double (&vi)[3],
@@ -816,24 +1049,23 @@ __device__ __forceinline__ void f64_tile(const double4_32a (*__restrict__ sh)[kF
             const double4_32a C = sh[2][q];
             const double4_32a D = sh[3][q];
             const double wx = self ? 0.0 : D.x, wy = self ? 0.0 : D.y, wz = self ? 0.0 : D.z;
-            const double ux = vi[0] - B.x, uy = vi[1] - B.y, uz = vi[2] - B.z;
-            const double u2 = fma(ux, ux, fma(uy, uy, uz * uz));
             const double xvj = fma(dx, B.x, fma(dy, B.y, dz * B.z));
             const double xvi = fma(dx, vi[0], fma(dy, vi[1], dz * vi[2]));
-            const double ed = fma(C.x, di[0], fma(C.y, di[1], C.z * di[2]));
+            double k = fma(vi[0], B.x, fma(vi[1], B.y, fma(vi[2], B.z, C.w)));
+            k = fma(C.x, di[0], fma(C.y, di[1], fma(C.z, di[2], k)));
             const double h = xvj * is2;
-            const double kap = fma(h, xvj, fma(-4.0 / 3.0, u2, C.w - ed));
-            const double f = mis3 * kap;
+            const double f = mis3 * fma(h, xvj, k);
             acc[0] = fma(f, dx, acc[0]);
             acc[1] = fma(f, dy, acc[1]);
             acc[2] = fma(f, dz, acc[2]);
-            const double gg = mis3 * fma(-0.75, xvj, xvi);
-            acc[3] = fma(gg, ux, acc[3]);
-            acc[4] = fma(gg, uy, acc[4]);
-            acc[5] = fma(gg, uz, acc[5]);
-            acc[6] = fma(wx, is, acc[6]);
-            acc[7] = fma(wy, is, acc[7]);
-            acc[8] = fma(wz, is, acc[8]);
+            const double gg = mis3 * fma(-2.0, xvj, xvi);
+            acc[3] += gg;
+            acc[4] = fma(gg, B.x, acc[4]);
+            acc[5] = fma(gg, B.y, acc[5]);
+            acc[6] = fma(gg, B.z, acc[6]);
+            acc[7] = fma(wx, is, acc[7]);
+            acc[8] = fma(wy, is, acc[8]);
+            acc[9] = fma(wz, is, acc[9]);
         }
     }
 }
@@ -857,7 +1089,9 @@ k_pass_f64(const double4_32a *__restrict__ rec, int64_t S, const Clu *__restrict
     double vi[3] = {0.0, 0.0, 0.0};
     if (PASS == 2) {
         const double4_32a B = rec[S + ti];
-        vi[0] = B.x; vi[1] = B.y; vi[2] = B.z;
+        vi[0] = (8.0 / 3.0) * B.x;
+        vi[1] = (8.0 / 3.0) * B.y;
+        vi[2] = (8.0 / 3.0) * B.z;
     }
     double acc[kP2Vals];
 #pragma unroll
@@ -1136,6 +1370,8 @@ k_near_f64(const double4_32a *__restrict__ rec, const double4_32a *__restrict__ 
 //     + 5 G^2 m_i M d_i/R_i^4                                          [Eq. 6 l.1]
 //     + G^2 M d_i/R_i^3 S_i                                            [Eq. 6 l.2]
 //     + G [V_i + (4 G M/R_i + v_i^2) N_i]                              [l.3 + l.6]
+//       (V_i from pass 2 carries -4/3 of the v_i^2 part as -2 v_i^2 N_i, so
+//        the coefficient of N_i applied here is 4 G M/R_i - v_i^2)
 //     - 7/2 G^2 M [E_i - (W_far - w_i)/R_i]                            [l.4]
 //     - G/R_i^3 [4 (v_i.Q) d_i - 3 (Q.d_i) v_i - 4 (v_i.d_i) Q]        [l.1 + l.5]
 //     + G H_i                                                          [l.7]
@@ -1204,9 +1440,10 @@ k_epilogue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
         const double fi = nflag[t] ? 0.0 : 1.0;   // 1 if star i is a far source
         const double N[3] = {s1[0], s1[1], s1[2]};
         const double U = s1[3], Y = R2 * s1[4] - s1[5];
+        double Vv[3], H[3];
         for (int k = 0; k < 3; ++k) {
-            s2[k] *= 1.5;          // V = 3/2 V'
-            s2[3 + k] *= 4.0;      // H = 4 H'
+            Vv[k] = 1.5 * s2[k];                          // V = 3/2 V' (+ the N_i part below)
+            H[k] = 1.5 * (s2[3] * vv[k] - s2[4 + k]);     // H = 3/2 (Hs v_i - Hv)
         }
         const double Q[3] = {glob[0], glob[1], glob[2]};
         const double Wf[3] = {glob[6], glob[7], glob[8]};
@@ -1221,13 +1458,13 @@ k_epilogue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
         const double cd = GM * iR3 * (4.0 * GM * iR - v2) + 5.0 * G * GM * mi * iR3 * iR +
                           G * GM * iR3 * S - 4.0 * G * iR3 * vQ;
         const double cv = 4.0 * GM * iR3 * vd + 3.0 * G * iR3 * Qd;
-        const double cN = G * (4.0 * GM * iR + v2);
+        const double cN = G * (4.0 * GM * iR - v2);
         const double cQ = 4.0 * G * iR3 * vd;
         const double c7 = 3.5 * G * GM;
         double ai[3];
         for (int k = 0; k < 3; ++k) {
-            const double pn = cd * d[k] + cv * vv[k] + G * s2[k] + cN * N[k] -
-                              c7 * (s2[6 + k] - Wx[k] * iR) + cQ * Q[k] + G * s2[3 + k] +
+            const double pn = cd * d[k] + cv * vv[k] + G * Vv[k] + cN * N[k] -
+                              c7 * (s2[7 + k] - Wx[k] * iR) + cQ * Q[k] + G * H[k] +
                               G * GM * (sn[k] - 3.5 * sn[3 + k]);
             ai[k] = (-GM * iR3 * d[k] - G * N[k]) + inv_c2 * pn;
         }
@@ -1406,17 +1643,17 @@ cudaError_t launch_prologue(pn_ctx *c, const double *x, const double *vel, const
     const int *bc = blk_table(c);
     if (energy_records) {
         k_prologue<2><<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
-            c->S, c->d_clu, bc, x, vel, m, c->mrec, c->drec, c->nflag, c->blk);
+            c->S, c->d_clu, bc, x, vel, m, c->mrec, c->drec, c->nflag, c->blk, nullptr);
         c->launches += 1;
         return cudaGetLastError();
     }
     const bool mixed = c->p.precision == PN_MIXED;
     if (mixed)
         k_prologue<0><<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
-            c->S, c->d_clu, bc, x, vel, m, c->mrec, c->drec, c->nflag, c->blk);
+            c->S, c->d_clu, bc, x, vel, m, c->mrec, c->drec, c->nflag, c->blk, c->wcount);
     else
         k_prologue<1><<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
-            c->S, c->d_clu, bc, x, vel, m, c->mrec, c->drec, c->nflag, c->blk);
+            c->S, c->d_clu, bc, x, vel, m, c->mrec, c->drec, c->nflag, c->blk, c->wcount);
     c->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
@@ -1471,13 +1708,49 @@ static Layout layout(const pn_ctx *c)
     return L;
 }
 
-int64_t fused_units(const Clu *h, int nclu, int P, Clu *out)
+int fused_tile_size(bool packed) { return packed ? kPackTile : kMixTile; }
+
+// Work units of a fused-kernel variant over all clusters of the context.
+static int64_t fused_unit_count(const pn_ctx *c, int P, bool packed)
 {
+    const int tile = fused_tile_size(packed);
+    int64_t u = 0;
+    for (int k = 0; k < c->nclu; ++k)
+        u += (c->hclu[k].ns_pad / (kMixThreads * P)) * (c->hclu[k].ns_pad / tile);
+    return u;
+}
+
+// Launch shape of a fused-kernel variant: resident blocks per SM and in all,
+// stream-K workers, work units.  The scalar kernel runs one worker per
+// resident block; the packed kernel up to c->workers_max (default
+// kPackWorkersMax) per block, at least 64 units each, taken dynamically.
+cudaError_t fused_shape(const pn_ctx *c, int P, int unroll, bool packed, FusedShape *out)
+{
+    int occ = 0;
+    const cudaError_t e = fused_occupancy(P, unroll, packed, &occ);
+    if (e != cudaSuccess)
+        return e;
+    out->occ = occ > 0 ? occ : 1;
+    out->grid = (int64_t)out->occ * c->sm_count;
+    out->units = fused_unit_count(c, P, packed);
+    int64_t per = 1;
+    if (packed) {
+        const int64_t cap = c->workers_max > 0 ? c->workers_max : kPackWorkersMax;
+        per = out->units / (out->grid * 64);
+        per = per < 1 ? 1 : (per > cap ? cap : per);
+    }
+    out->G = out->grid * per;
+    return cudaSuccess;
+}
+
+int64_t fused_units(const Clu *h, int nclu, int P, bool packed, Clu *out)
+{
+    const int tile = fused_tile_size(packed);
     int64_t u = 0;
     for (int k = 0; k < nclu; ++k) {
         out[k] = h[k];
         out[k].unit0 = u;
-        u += (h[k].ns_pad / (kMixThreads * P)) * (h[k].ns_pad / kMixTile);
+        u += (h[k].ns_pad / (kMixThreads * P)) * (h[k].ns_pad / tile);
     }
     return u;
 }
@@ -1529,7 +1802,7 @@ static cudaError_t launch_fused_p(pn_ctx *c, const Layout &L)
 {
     cudaEvent_t end = nullptr;
     timing_begin(c, 1, &end);
-    k_fused_mixed<P, UNROLL><<<(unsigned)c->fused_G, kMixThreads, 0, c->stream>>>(
+    k_fused_mixed<P, UNROLL><<<(unsigned)c->fused_grid, kMixThreads, 0, c->stream>>>(
         c->mrec, c->S, c->d_clu, c->nclu, c->fused_units, c->part + L.seg);
     c->launches += 1;
     cudaError_t e = cudaGetLastError();
@@ -1538,17 +1811,43 @@ static cudaError_t launch_fused_p(pn_ctx *c, const Layout &L)
     if (e != cudaSuccess)
         return e;
     k_fused_gather<P><<<(unsigned)(c->S / kGlueThreads), kGlueThreads, 0, c->stream>>>(
-        c->part + L.seg, c->S, c->d_clu, blk_table(c), c->fused_units, c->fused_G,
+        c->part + L.seg, c->S, c->d_clu, blk_table(c), c->fused_units, c->fused_G, kMixTile,
         c->part + L.p1, c->part + L.p2);
     c->launches += 1;
     return cudaGetLastError();
 }
 
-// Fused-kernel variants: targets per thread (1, 2, 4) x source-loop unroll.
+template <int NP, int UNROLL>
+static cudaError_t launch_packed_u(pn_ctx *c, const Layout &L)
+{
+    cudaEvent_t end = nullptr;
+    timing_begin(c, 1, &end);
+    k_fused_packed<NP, UNROLL><<<(unsigned)c->fused_grid, kMixThreads, 0, c->stream>>>(
+        c->mrec, c->S, c->d_clu, c->nclu, c->fused_units, c->fused_G, c->wcount, c->part + L.seg);
+    c->launches += 1;
+    cudaError_t e = cudaGetLastError();
+    if (end)
+        cudaEventRecord(end, c->stream);
+    if (e != cudaSuccess)
+        return e;
+    k_fused_gather<2 * NP><<<(unsigned)(c->S / kGlueThreads), kGlueThreads, 0, c->stream>>>(
+        c->part + L.seg, c->S, c->d_clu, blk_table(c), c->fused_units, c->fused_G, kPackTile,
+        c->part + L.p1, c->part + L.p2);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+// Fused-kernel variants: scalar (targets per thread 1, 2, 4) or packed
+// FP32x2 (4 targets per thread) x source-loop unroll.
 cudaError_t launch_fused(pn_ctx *c)
 {
     const Layout L = layout(c);
     const int u = c->fused_unroll;
+    if (c->fused_packed) {
+        if (c->fused_P == 2)
+            return u == 2 ? launch_packed_u<1, 2>(c, L) : launch_packed_u<1, 1>(c, L);
+        return u == 2 ? launch_packed_u<2, 2>(c, L) : launch_packed_u<2, 1>(c, L);
+    }
     switch (c->fused_P) {
     case 1: return u == 2 ? launch_fused_p<1, 2>(c, L) : launch_fused_p<1, 1>(c, L);
     case 4:
@@ -1561,15 +1860,38 @@ cudaError_t launch_fused(pn_ctx *c)
     }
 }
 
+// The fused kernels hold 64-75 KB of shared memory per block; three blocks
+// per SM need the largest shared-memory carveout, which is requested here
+// (before the occupancy query and the first launch).
+template <typename K>
+static cudaError_t occ_with_carveout(K kernel, int *occ)
+{
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess)
+        return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kernel, kMixThreads, 0);
+}
+
 template <int P, int UNROLL>
 static cudaError_t occ_of(int *occ)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_fused_mixed<P, UNROLL>,
-                                                         kMixThreads, 0);
+    return occ_with_carveout(k_fused_mixed<P, UNROLL>, occ);
 }
 
-cudaError_t fused_occupancy(int P, int unroll, int *occ)
+template <int NP, int UNROLL>
+static cudaError_t occ_packed(int *occ)
 {
+    return occ_with_carveout(k_fused_packed<NP, UNROLL>, occ);
+}
+
+cudaError_t fused_occupancy(int P, int unroll, bool packed, int *occ)
+{
+    if (packed) {
+        if (P == 2)
+            return unroll == 2 ? occ_packed<1, 2>(occ) : occ_packed<1, 1>(occ);
+        return unroll == 2 ? occ_packed<2, 2>(occ) : occ_packed<2, 1>(occ);
+    }
     switch (P) {
     case 1: return unroll == 2 ? occ_of<1, 2>(occ) : occ_of<1, 1>(occ);
     case 4:
@@ -1650,7 +1972,7 @@ cudaError_t launch_energy_on(cudaStream_t st, int64_t S, const Clu *clu, const d
 {
     const int64_t nb = S / kGlueThreads;
     k_prologue<2><<<(unsigned)nb, kGlueThreads, 0, st>>>(S, clu, nullptr, x, v, m, nullptr, drec,
-                                                         nullptr, nullptr);
+                                                         nullptr, nullptr, nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;

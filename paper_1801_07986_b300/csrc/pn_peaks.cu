@@ -1,6 +1,7 @@
 // pn_peaks.cu -- pn_measure_peaks: FMA-chain microbenchmarks that give the
 // roofline denominators of this library's ALU-bound kernels on the device
-// at hand (FP32 FMA, FP64 FMA and single-precision rsqrt throughput).
+// at hand (FP32 FMA, packed FP32x2 FMA, FP64 FMA and single-precision rsqrt
+// throughput).
 #include <cstdio>
 
 #include "pn_internal.h"
@@ -27,6 +28,27 @@ __global__ void __launch_bounds__(kThreads) k_fma_chain(T *out, int iters, T a, 
 #pragma unroll
     for (int c = 0; c < kChains; ++c)
         s += acc[c];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// The same chains on packed pairs of floats: one fma.rn.f32x2 instruction
+// (sm_100 family) performs two FP32 FMAs.
+__global__ void __launch_bounds__(kThreads) k_fma2_chain(float *out, int iters, float a, float b)
+{
+    float2 acc[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c)
+        acc[c] = make_float2(1.0f + c + threadIdx.x * 1e-3f, 2.0f + c + threadIdx.x * 1e-3f);
+    const float2 a2 = make_float2(a, a), b2 = make_float2(b, b);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int c = 0; c < kChains; ++c)
+            acc[c] = __ffma2_rn(acc[c], a2, b2);
+    }
+    float s = 0;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c)
+        s += acc[c].x + acc[c].y;
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
@@ -74,10 +96,11 @@ double time_ms(cudaStream_t st, F launch, cudaError_t *err)
 
 /*
  * out[0] FP32 FMA TFLOP/s (2 flops per FMA), out[1] FP64 FMA TFLOP/s,
- * out[2] rsqrt.approx.f32 Gop/s, out[3] SM count; measured now on `device`
- * with independent FMA chains (every SM busy), timed by CUDA events.
+ * out[2] rsqrt.approx.f32 Gop/s, out[3] SM count, out[4] packed FP32x2 FMA
+ * TFLOP/s; measured now on `device` with independent FMA chains (every SM
+ * busy), timed by CUDA events.
  */
-extern "C" pn_status pn_measure_peaks(int device, void *cuda_stream, double out[4])
+extern "C" pn_status pn_measure_peaks(int device, void *cuda_stream, double out[5])
 {
     if (!out)
         return pn::set_error(PN_EINVAL, "pn_measure_peaks: NULL output");
@@ -109,6 +132,9 @@ extern "C" pn_status pn_measure_peaks(int device, void *cuda_stream, double out[
         const double msr = err ? 0.0 : time_ms(st, [&] {
             k_rsqrt_chain<<<blocks, kThreads, 0, st>>>((float *)buf, itr);
         }, &err);
+        const double ms2 = err ? 0.0 : time_ms(st, [&] {
+            k_fma2_chain<<<blocks, kThreads, 0, st>>>((float *)buf, it32 / 2, 0.9999f, 1e-7f);
+        }, &err);
         if (err != cudaSuccess) {
             status = pn::set_error(PN_ECUDA, "pn_measure_peaks: %s", cudaGetErrorString(err));
         } else {
@@ -116,6 +142,7 @@ extern "C" pn_status pn_measure_peaks(int device, void *cuda_stream, double out[
             out[1] = 2.0 * lanes * it64 / (ms64 * 1e-3) / 1e12;
             out[2] = lanes * itr / (msr * 1e-3) / 1e9;
             out[3] = sms;
+            out[4] = 4.0 * lanes * (it32 / 2) / (ms2 * 1e-3) / 1e12;
         }
         cudaFree(buf);
     }

@@ -282,11 +282,12 @@ def pn_tune(ctx: Context, x, v, m, a) -> dict:
     """Choose the fused kernel's launch shape by timing candidates on this
     state (a is overwritten with A(x, v))."""
     n = ctx.n
-    out = np.zeros(3, dtype=np.int64)
+    out = np.zeros(4, dtype=np.int64)
     _check(_load().pn_tune(ctx.handle, _dev(ctx, x, (n, 3), "x"), _dev(ctx, v, (n, 3), "v"),
                            _dev(ctx, m, (n,), "m"), _dev(ctx, a, (n, 3), "a"),
                            out.ctypes.data_as(ctypes.c_void_p)))
-    return {"targets_per_thread": int(out[0]), "unroll": int(out[1]), "cached": bool(out[2])}
+    return {"targets_per_thread": int(out[0]), "unroll": int(out[1]), "cached": bool(out[2]),
+            "packed": bool(out[3])}
 
 
 def _host(arr, shape, name):
@@ -340,15 +341,16 @@ def pn_energy_noalloc(x, v, m, out, G: float = 1.0, c: float = math.inf, eps: fl
 
 
 def pn_measure_peaks(device: int = 0, stream=None) -> dict:
-    """FP32 / FP64 FMA TFLOP/s and rsqrt Gop/s measured now on `device`."""
+    """FP32, packed FP32x2 and FP64 FMA TFLOP/s and rsqrt Gop/s measured now on
+    `device`."""
     import torch
-    out = np.zeros(4)
+    out = np.zeros(5)
     st = torch.cuda.current_stream(device).cuda_stream if stream is None \
         else getattr(stream, "cuda_stream", stream)
     _check(_load().pn_measure_peaks(int(device), ctypes.c_void_p(st),
                                     out.ctypes.data_as(ctypes.c_void_p)))
     return {"fp32_fma_tflops": out[0], "fp64_fma_tflops": out[1], "rsqrt_gops": out[2],
-            "sms": int(out[3])}
+            "sms": int(out[3]), "fp32x2_fma_tflops": out[4]}
 
 
 def pn_sync(ctx: Context) -> None:
@@ -370,9 +372,10 @@ def pn_get_timing(ctx: Context):
 
 
 def pn_get_launch(ctx: Context) -> dict:
-    out = np.zeros(7, dtype=np.int64)
+    out = np.zeros(8, dtype=np.int64)
     _check(_load().pn_get_launch(ctx.handle, out.ctypes.data_as(ctypes.c_void_p)))
-    keys = ("threads", "targets_per_thread", "tile", "blocks_i", "jsplit", "occupancy", "sms")
+    keys = ("threads", "targets_per_thread", "tile", "blocks_i", "jsplit", "occupancy", "sms",
+            "packed")
     return {k: int(v) for k, v in zip(keys, out)}
 
 

@@ -100,7 +100,7 @@ def test_batched_steps_match_oracle_and_graph_replays_bitwise(orc):
     pn.pn_sync(ctx)
     assert torch.equal(X, X2) and torch.equal(V, V2) and torch.equal(A, A2)
     # one step = kick-drift, prologue, global sums, 2 pair passes, epilogue, hole
-    # (+ scatter and near pass when a star lies within r_near); replays count alike
+    # (+ near scatter and near pass when r_near > 0); graph replays count alike
     assert n1 - n0 in (6 * 7, 6 * 9)
     assert n2 - n1 == n1 - n0
     xg = X.cpu().numpy()

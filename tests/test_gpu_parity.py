@@ -86,6 +86,38 @@ def test_mixed_matches_oracle(orc, n, pair_kernel):
     assert np.median(err) <= MIX_MED and err.max() <= MIX_MAX, (np.median(err), err.max())
 
 
+# fused-kernel variants (PN_FUSED_PACKED, PN_FUSED_TARGETS, PN_FUSED_UNROLL are
+# read by pn_init): the packed FP32x2 kernel and every scalar shape
+FUSED_VARIANTS = [("1", "4", "1"), ("1", "4", "2"), ("1", "2", "1"), ("1", "2", "2"),
+                  ("0", "4", "1"), ("0", "4", "2"),
+                  ("0", "4", "3"), ("0", "4", "4"), ("0", "2", "1"), ("0", "2", "2"),
+                  ("0", "2", "4"), ("0", "1", "1"), ("0", "1", "2")]
+
+
+@pytest.mark.parametrize("packed,targets,unroll", FUSED_VARIANTS)
+def test_fused_variants_match_oracle(orc, monkeypatch, packed, targets, unroll):
+    monkeypatch.setenv("PN_FUSED_PACKED", packed)
+    monkeypatch.setenv("PN_FUSED_TARGETS", targets)
+    monkeypatch.setenv("PN_FUSED_UNROLL", unroll)
+    n = 2 * 1024 + 130            # several target blocks and source tiles, ragged tail
+    x, v, m = cluster(n, 0.2, 4242)
+    x[5] = x[0] + np.array([0.01, 0.0, 0.0])     # a near source of the hole
+    want = orc.accel(x, v, m, c=15.0, eps=1e-4)
+    ctx = pn.pn_init(n, c=15.0, eps=1e-4, precision="mixed", device=0)
+    shape = pn.pn_get_launch(ctx)
+    assert shape["packed"] == (packed == "1")
+    want_p = (2 if targets == "2" else 4) if packed == "1" else int(targets)
+    assert shape["targets_per_thread"] == want_p
+    X, V, M = dev(x), dev(v), dev(m)
+    A = torch.empty_like(X)
+    pn.pn_accel(ctx, X, V, M, A)
+    pn.pn_sync(ctx)
+    got = A.cpu().numpy()
+    ctx.close()
+    err = rel(got, want)
+    assert np.median(err) <= MIX_MED and err.max() <= MIX_MAX, (np.median(err), err.max())
+
+
 def test_plummer1k_workload_fp64_every_body(orc):
     w = WORKLOADS["plummer1k_fp64"]
     x, v, m = w.state()
