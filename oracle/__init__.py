@@ -51,7 +51,9 @@ CFLAGS = ["-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", "-fno-fast
 
 def build(force: bool = False) -> str:
     """Compile pn_oracle.c into liboracle.so (gcc, -ffp-contract=off)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    srcs = (_SRC, os.path.join(_HERE, "pn_oracle_accel.inc"))
+    if force or not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(f)
+                                                for f in srcs):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.run(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"], check=True)
         os.replace(tmp, _LIB)
@@ -79,6 +81,8 @@ def _load():
             lib.orc_step.argtypes = [i64, p, p, p, p, d, d, d, d, i64, ctypes.c_int]
             lib.orc_eih_step.argtypes = [i64, p, p, p, p, d, d, d, i64, ctypes.c_int]
             lib.orc_rk4_step.argtypes = [i64, p, p, p, p, d, d, d, d, i64]
+            lib.orc_jerk.argtypes = [i64, p, p, p, d, d, d, p, p]
+            lib.orc_hermite_step.argtypes = [i64, p, p, p, p, d, d, d, d, i64]
             lib.orc_set_threads.argtypes = [ctypes.c_int]
             lib.orc_get_threads.restype = ctypes.c_int
             for f in ("orc_accel", "orc_accel_rows", "orc_bh_rows", "orc_newton_accel",
@@ -196,6 +200,34 @@ def rk4_step(x, v, m, a, dt, nsteps, G=1.0, c=np.inf, eps=0.0):
                               dt, int(nsteps))
     if rc:
         raise ValueError(f"orc_rk4_step failed ({rc})")
+    return x, v, a
+
+
+def jerk(x, v, m, a=None, G=1.0, c=np.inf, eps=0.0):
+    """Time derivative of the accelerations along the trajectory (Appendix A)
+    at (x, v), with `a` = A(x, v) (computed if None), by a complex step of
+    the oracle's own Eq. 1-6."""
+    x, v, m, n = _state(x, v, m)
+    if a is None:
+        a = accel(x, v, m, G=G, c=c, eps=eps)
+    a = _f64(a, (n, 3))
+    out = np.zeros((n, 3))
+    rc = _load().orc_jerk(n, _ptr(x), _ptr(v), _ptr(m), G, _inv_c2(c), eps, _ptr(a), _ptr(out))
+    if rc:
+        raise ValueError(f"orc_jerk failed ({rc})")
+    return out
+
+
+def hermite_step(x, v, m, a, dt, nsteps, G=1.0, c=np.inf, eps=0.0):
+    """Advance copies of (x, v, a) by nsteps fourth-order Hermite PEC steps;
+    `a` must hold A at the entry state; returns (x, v, a at the final state)."""
+    x, v, m, n = _state(x, v, m)
+    x, v = x.copy(), v.copy()
+    a = _f64(a, (n, 3)).copy()
+    rc = _load().orc_hermite_step(n, _ptr(x), _ptr(v), _ptr(m), _ptr(a), G, _inv_c2(c), eps,
+                                  dt, int(nsteps))
+    if rc:
+        raise ValueError(f"orc_hermite_step failed ({rc})")
     return x, v, a
 
 

@@ -45,9 +45,15 @@
  *      Eqs. 7-8 run over ordered pairs i != j.
  *  R9  Integrator: kick-drift-kick leapfrog whose force after the drift is
  *      evaluated at the predicted velocity v_half + (dt/2) a_old (vel_mode 0)
- *      or at v_half (vel_mode 1); and the paper's own classical RK4
- *      (Section 4), orc_rk4_step.
+ *      or at v_half (vel_mode 1); the paper's own classical RK4
+ *      (Section 4), orc_rk4_step; and the fourth-order Hermite scheme the
+ *      paper recommends (Section 5), orc_hermite_step, iterated once (two
+ *      evaluate-correct passes) because the force depends on velocity.
+ *  R10 The jerk (Appendix A) is the time derivative of the same Eq. 1-6
+ *      along the trajectory, with every a_j in it the full (1PN)
+ *      acceleration; the hole's own velocity enters through d/dt x_1j.
  */
+#include <complex.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -55,54 +61,6 @@
 #ifdef _OPENMP
 #include <omp.h>
 #endif
-
-/* ---------------------------------------------------------------- sums -- */
-
-typedef struct { double s, c; } ksum;              /* value = s + c */
-typedef struct { ksum k[3]; } ksum3;
-
-static void kadd(ksum *a, double x)
-{
-    /* Knuth's TwoSum: s + x = t + e exactly */
-    double t = a->s + x;
-    double bp = t - a->s;
-    double e = (a->s - (t - bp)) + (x - bp);
-    a->s = t;
-    a->c += e;
-}
-
-static double kval(const ksum *a) { return a->s + a->c; }
-
-/* acc += f * w (vector) */
-static void kadd3(ksum3 *a, double f, const double w[3])
-{
-    kadd(&a->k[0], f * w[0]);
-    kadd(&a->k[1], f * w[1]);
-    kadd(&a->k[2], f * w[2]);
-}
-
-static void kval3(const ksum3 *a, double out[3])
-{
-    out[0] = kval(&a->k[0]);
-    out[1] = kval(&a->k[1]);
-    out[2] = kval(&a->k[2]);
-}
-
-/* ------------------------------------------------------------- vectors -- */
-
-static double dot(const double a[3], const double b[3])
-{
-    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
-}
-
-static void sub(const double a[3], const double b[3], double out[3])
-{
-    out[0] = a[0] - b[0];
-    out[1] = a[1] - b[1];
-    out[2] = a[2] - b[2];
-}
-
-static const double *row(const double *p, int64_t i) { return p + 3 * i; }
 
 static int g_threads = 0;
 
@@ -117,213 +75,43 @@ int orc_get_threads(void)
 #endif
 }
 
-/* ============================================== limited 1PN, Section 2 == */
+/* The accelerations, Section 2 (pn_oracle_accel.inc), in double ... */
+#define REAL double
+#define SQRT sqrt
+#include "pn_oracle_accel.inc"
+#undef REAL
+#undef SQRT
 
-/*
- * Acceleration of star i (1 <= i < n), Eq. 4 with Eq. 5 and Eq. 6.
- * out = Newtonian part + inv_c2 * ([a_i]_BH + [a_i]_Cross).
- */
-static void star_accel(int64_t n, const double *x, const double *v,
-                       const double *m, double G, double inv_c2, double eps,
-                       int64_t i, double out[3])
-{
-    const double M = m[0];
-    const double *x1 = row(x, 0);
-    const double *xi = row(x, i), *vi = row(v, i);
-    const double mi = m[i];
-    double xi1[3];
-    sub(xi, x1, xi1);                                 /* x_i1 = x_i - x_1 */
-    const double ri1 = sqrt(dot(xi1, xi1));
-    const double ri1_2 = ri1 * ri1, ri1_3 = ri1_2 * ri1, ri1_4 = ri1_3 * ri1;
-    const double vi2 = dot(vi, vi);
-    const double vi_xi1 = dot(vi, xi1);
-    const double e2 = eps * eps;
-    ksum3 newt, pn;
-    memset(&newt, 0, sizeof newt);
-    memset(&pn, 0, sizeof pn);
-
-    /* Eq. 4, first term: -G M x_i1 / r_i1^3 */
-    kadd3(&newt, -G * M / ri1_3, xi1);
-
-    /* Eq. 5: [a_i]_BH = G M x_i1/r_i1^3 (4GM/r_i1 - v_i^2)
-     *                  + 4 G M/r_i1^3 (v_i . x_i1) v_i                       */
-    kadd3(&pn, G * M / ri1_3 * (4.0 * G * M / ri1 - vi2), xi1);
-    kadd3(&pn, 4.0 * G * M / ri1_3 * vi_xi1, vi);
-
-    /* Eq. 6, first line: 5 G^2 m_i M x_i1/r_i1^4
-     *                    - G m_i/r_i1^3 [4 v_i^2 x_i1 - 7 (v_i . x_i1) v_i]  */
-    kadd3(&pn, 5.0 * G * G * mi * M / ri1_4, xi1);
-    kadd3(&pn, -G * mi / ri1_3 * 4.0 * vi2, xi1);
-    kadd3(&pn, G * mi / ri1_3 * 7.0 * vi_xi1, vi);
-
-    for (int64_t j = 1; j < n; ++j) {
-        if (j == i)
-            continue;
-        const double *xj = row(x, j), *vj = row(v, j);
-        const double mj = m[j];
-        double xij[3], xj1[3], vij[3], w[3];
-        sub(xi, xj, xij);                             /* x_ij = x_i - x_j */
-        sub(xj, x1, xj1);                             /* x_j1 = x_j - x_1 */
-        sub(vi, vj, vij);                             /* v_ij = v_i - v_j */
-        /* Eq. 10: softened star-star separation */
-        const double rij_2 = dot(xij, xij) + e2;
-        const double rij = sqrt(rij_2);
-        const double rij_3 = rij_2 * rij;
-        const double rj1 = sqrt(dot(xj1, xj1));
-        const double rj1_3 = rj1 * rj1 * rj1;
-
-        /* Eq. 4, second term: -sum_j G m_j x_ij / r_ij^3 */
-        kadd3(&newt, -G * mj / rij_3, xij);
-
-        /* Eq. 6, second line:
-         * sum_j G^2 m_j M x_i1/r_i1^3
-         *      (4/r_ij + 5/(4 r_j1) + r_i1^2/(4 r_j1^3) - r_ij^2/(4 r_j1^3)) */
-        kadd3(&pn, G * G * mj * M / ri1_3 *
-                   (4.0 / rij + 5.0 / (4.0 * rj1) + ri1_2 / (4.0 * rj1_3)
-                    - rij_2 / (4.0 * rj1_3)), xi1);
-
-        /* Eq. 6, third line:
-         * sum_j G^2 m_j M x_ij/r_ij^3
-         *      (4/r_i1 + 5/(4 r_j1) - r_i1^2/(4 r_j1^3) + r_ij^2/(4 r_j1^3)) */
-        kadd3(&pn, G * G * mj * M / rij_3 *
-                   (4.0 / ri1 + 5.0 / (4.0 * rj1) - ri1_2 / (4.0 * rj1_3)
-                    + rij_2 / (4.0 * rj1_3)), xij);
-
-        /* Eq. 6, fourth line:
-         * -7/2 sum_j G^2 m_j M x_j1/r_j1^3 (1/r_ij - 1/r_i1)                 */
-        kadd3(&pn, -3.5 * G * G * mj * M / rj1_3 * (1.0 / rij - 1.0 / ri1), xj1);
-
-        /* Eq. 6, fifth line:
-         * -sum_j G m_j/r_i1^3 [4 (v_i . v_j) x_i1 - 3 (v_j . x_i1) v_i
-         *                      - 4 (v_i . x_i1) v_j]                         */
-        const double g5 = G * mj / ri1_3;
-        kadd3(&pn, -g5 * 4.0 * dot(vi, vj), xi1);
-        kadd3(&pn, g5 * 3.0 * dot(vj, xi1), vi);
-        kadd3(&pn, g5 * 4.0 * vi_xi1, vj);
-
-        /* Eq. 6, sixth line:
-         * sum_j G m_j x_ij/r_ij^3 [v_i^2 - 2 |v_ij|^2 + 3/2 (v_j . n_ij)^2]  */
-        const double vj_nij = dot(vj, xij) / rij;
-        kadd3(&pn, G * mj / rij_3 *
-                   (vi2 - 2.0 * dot(vij, vij) + 1.5 * vj_nij * vj_nij), xij);
-
-        /* Eq. 6, seventh line:
-         * sum_j G m_j/r_ij^3 [x_ij . (4 v_i - 3 v_j)] v_ij                    */
-        w[0] = 4.0 * vi[0] - 3.0 * vj[0];
-        w[1] = 4.0 * vi[1] - 3.0 * vj[1];
-        w[2] = 4.0 * vi[2] - 3.0 * vj[2];
-        kadd3(&pn, G * mj / rij_3 * dot(xij, w), vij);
-    }
-
-    double an[3], ap[3];
-    kval3(&newt, an);
-    kval3(&pn, ap);
-    out[0] = an[0] + inv_c2 * ap[0];
-    out[1] = an[1] + inv_c2 * ap[1];
-    out[2] = an[2] + inv_c2 * ap[2];
-}
-
-/*
- * Inner k-sums of the three double sums of Eq. 3 for one outer index j:
- *   sum_{k != j} G^2 m_j m_k x_1j/r_1j^3
- *        (4/r_1k + 5/(4 r_jk) - r_1k^2/(4 r_jk^3) + r_1j^2/(4 r_jk^3))
- * - 7/2 sum_{k != j} G^2 m_j m_k x_jk/(r_jk^3 r_1j)
- * - sum_k G m_j m_k/(M r_1j^3)
- *        [4 (v_j . v_k) x_1j - 3 (v_j . x_1j) v_k - 4 (v_k . x_1j) v_j]
- */
-static void bh_double_sum_row(int64_t n, const double *x, const double *v,
-                              const double *m, double G, double eps,
-                              int64_t j, double out[3])
-{
-    const double M = m[0];
-    const double *x1 = row(x, 0);
-    const double *xj = row(x, j), *vj = row(v, j);
-    const double mj = m[j];
-    const double e2 = eps * eps;
-    double x1j[3];
-    sub(x1, xj, x1j);                                 /* x_1j = x_1 - x_j */
-    const double r1j = sqrt(dot(x1j, x1j));
-    const double r1j_2 = r1j * r1j, r1j_3 = r1j_2 * r1j;
-    const double vj_x1j = dot(vj, x1j);
-    ksum3 acc;
-    memset(&acc, 0, sizeof acc);
-    for (int64_t k = 1; k < n; ++k) {
-        const double *xk = row(x, k), *vk = row(v, k);
-        const double mk = m[k];
-        double x1k[3];
-        sub(x1, xk, x1k);
-        /* terms that replace the heavy body's velocity: k = j included */
-        const double g = G * mj * mk / (M * r1j_3);
-        kadd3(&acc, -g * 4.0 * dot(vj, vk), x1j);
-        kadd3(&acc, g * 3.0 * vj_x1j, vk);
-        kadd3(&acc, g * 4.0 * dot(vk, x1j), vj);
-        if (k == j)
-            continue;
-        const double r1k_2 = dot(x1k, x1k);
-        const double r1k = sqrt(r1k_2);
-        double xjk[3];
-        sub(xj, xk, xjk);
-        const double rjk_2 = dot(xjk, xjk) + e2;      /* Eq. 10 */
-        const double rjk = sqrt(rjk_2);
-        const double rjk_3 = rjk_2 * rjk;
-        kadd3(&acc, G * G * mj * mk / r1j_3 *
-                    (4.0 / r1k + 5.0 / (4.0 * rjk) - r1k_2 / (4.0 * rjk_3)
-                     + r1j_2 / (4.0 * rjk_3)), x1j);
-        kadd3(&acc, -3.5 * G * G * mj * mk / (rjk_3 * r1j), xjk);
-    }
-    kval3(&acc, out);
-}
-
-/*
- * Acceleration of the heavy body, Eq. 1 with Eq. 2 and Eq. 3.
- * `rows` (length n, scratch) receives the per-j inner double sums.
- */
-static void bh_accel(int64_t n, const double *x, const double *v,
-                     const double *m, double G, double inv_c2, double eps,
-                     double *rows, double out[3])
-{
-    const double M = m[0];
-    const double *x1 = row(x, 0);
-    ksum3 newt, pn;
-    memset(&newt, 0, sizeof newt);
-    memset(&pn, 0, sizeof pn);
-
-    for (int64_t j = 1; j < n; ++j) {
-        const double *xj = row(x, j), *vj = row(v, j);
-        const double mj = m[j];
-        double x1j[3];
-        sub(x1, xj, x1j);
-        const double r1j = sqrt(dot(x1j, x1j));
-        const double r1j_3 = r1j * r1j * r1j, r1j_4 = r1j_3 * r1j;
-        const double vj_n = dot(vj, x1j) / r1j;
-        /* Eq. 1: -sum_j G m_j x_1j / r_1j^3 */
-        kadd3(&newt, -G * mj / r1j_3, x1j);
-        /* Eq. 2: sum_j G m_j x_1j/r_1j^3 (5GM/r_1j - 2 v_j^2 + 3/2 (v_j.n_1j)^2)
-         *        + 3 sum_j G m_j/r_1j^3 (v_j . x_1j) v_j                     */
-        kadd3(&pn, G * mj / r1j_3 *
-                   (5.0 * G * M / r1j - 2.0 * dot(vj, vj) + 1.5 * vj_n * vj_n), x1j);
-        kadd3(&pn, 3.0 * G * mj / r1j_3 * dot(vj, x1j), vj);
-        /* Eq. 3, first line: 4 sum_j G^2 m_j^2 x_1j / r_1j^4 */
-        kadd3(&pn, 4.0 * G * G * mj * mj / r1j_4, x1j);
-    }
-
-    /* Eq. 3, double sums: one row per outer index j, then added in j order */
-    int nt = orc_get_threads();
-#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
-    for (int64_t j = 1; j < n; ++j)
-        bh_double_sum_row(n, x, v, m, G, eps, j, rows + 3 * j);
-    for (int64_t j = 1; j < n; ++j) {
-        static const double one = 1.0;
-        kadd3(&pn, one, rows + 3 * j);
-    }
-
-    double an[3], ap[3];
-    kval3(&newt, an);
-    kval3(&pn, ap);
-    out[0] = an[0] + inv_c2 * ap[0];
-    out[1] = an[1] + inv_c2 * ap[1];
-    out[2] = an[2] + inv_c2 * ap[2];
-}
+/* ... and in double complex for the complex-step jerk (orc_jerk). */
+#define REAL double complex
+#define SQRT csqrt
+#define ksum ksum_cs
+#define ksum3 ksum3_cs
+#define kadd kadd_cs
+#define kval kval_cs
+#define kadd3 kadd3_cs
+#define kval3 kval3_cs
+#define dot dot_cs
+#define sub sub_cs
+#define row row_cs
+#define star_accel star_accel_cs
+#define bh_double_sum_row bh_double_sum_row_cs
+#define bh_accel bh_accel_cs
+#include "pn_oracle_accel.inc"
+#undef REAL
+#undef SQRT
+#undef ksum
+#undef ksum3
+#undef kadd
+#undef kval
+#undef kadd3
+#undef kval3
+#undef dot
+#undef sub
+#undef row
+#undef star_accel
+#undef bh_double_sum_row
+#undef bh_accel
 
 static int check_args(int64_t n, const void *x, const void *v, const void *m)
 {
@@ -348,6 +136,52 @@ int orc_accel(int64_t n, const double *x, const double *v, const double *m,
         star_accel(n, x, v, m, G, inv_c2, eps, i, a + 3 * i);
     free(rows);
     return 0;
+}
+
+/*
+ * Jerk: the time derivative of the accelerations of Eq. 1-6 along the
+ * trajectory (Appendix A), j = sum_k [dA/dx_k . v_k + dA/dv_k . a_k] with
+ * a = A(x, v) given.  Appendix A prints the expanded derivative, garbled in
+ * places; here the derivative is taken of the same equations the oracle
+ * evaluates, by a complex step: Im A(x + i h v, v + i h a) / h with
+ * h = 1e-20 (relative error O(h^2), no cancellation).
+ */
+int orc_jerk(int64_t n, const double *x, const double *v, const double *m,
+             double G, double inv_c2, double eps, const double *a, double *jerk)
+{
+    if (check_args(n, x, v, m) || !a || !jerk)
+        return 1;
+    const double h = 1e-20;
+    const size_t n3 = 3 * (size_t)n;
+    double complex *xc = (double complex *)malloc(sizeof(double complex) * n3);
+    double complex *vc = (double complex *)malloc(sizeof(double complex) * n3);
+    double complex *mc = (double complex *)malloc(sizeof(double complex) * (size_t)n);
+    double complex *ac = (double complex *)malloc(sizeof(double complex) * n3);
+    double complex *rows = (double complex *)calloc(n3, sizeof(double complex));
+    int rc = 0;
+    if (!xc || !vc || !mc || !ac || !rows) {
+        rc = 2;
+    } else {
+        for (size_t q = 0; q < n3; ++q) {
+            xc[q] = x[q] + I * (h * v[q]);
+            vc[q] = v[q] + I * (h * a[q]);
+        }
+        for (int64_t q = 0; q < n; ++q)
+            mc[q] = m[q];
+        bh_accel_cs(n, xc, vc, mc, G, inv_c2, eps, rows, ac);
+        int nt = orc_get_threads();
+#pragma omp parallel for schedule(dynamic, 8) num_threads(nt)
+        for (int64_t i = 1; i < n; ++i)
+            star_accel_cs(n, xc, vc, mc, G, inv_c2, eps, i, ac + 3 * i);
+        for (size_t q = 0; q < n3; ++q)
+            jerk[q] = cimag(ac[q]) / h;
+    }
+    free(xc);
+    free(vc);
+    free(mc);
+    free(ac);
+    free(rows);
+    return rc;
 }
 
 /* Accelerations of the listed targets only (index 0 = heavy body). */
@@ -808,6 +642,66 @@ int orc_rk4_step(int64_t n, double *x, double *v, const double *m, double *a,
             rc = orc_accel(n, x, v, m, G, inv_c2, eps, a);
     }
     for (int q = 0; q < 8; ++q)
+        free(bufs[q]);
+    return rc;
+}
+
+/*
+ * nsteps of the fourth-order Hermite scheme (the integrator the paper
+ * recommends for collisional runs, Section 5, with the jerk of Appendix A),
+ * for x' = v, v' = A(x, v), in the predict-(evaluate-correct)^2 form:
+ *   predict   x_p = x + dt v + dt^2/2 a + dt^3/6 j,   v_p = v + dt a + dt^2/2 j
+ *   evaluate  a_1 = A(x_e, v_e),  j_1 = jerk at (x_e, v_e, a_1)
+ *   correct   v' = v + dt/2 (a + a_1) + dt^2/12 (j - j_1)
+ *             x' = x + dt/2 (v + v') + dt^2/12 (a - a_1)
+ * with (x_e, v_e) the predicted state in the first pass and the corrected
+ * one in the second.  A depends on v, so one pass would leave an O(dt^3)
+ * velocity error inside a_1 (third order); the second pass restores fourth
+ * order.  The second pass's a_1, j_1 (taken one correction before the final
+ * state, an O(dt^5) difference) start the next step.  `a` holds A at the
+ * entry state, where the jerk is computed; on return it holds A evaluated at
+ * the final state.
+ */
+int orc_hermite_step(int64_t n, double *x, double *v, const double *m, double *a,
+                     double G, double inv_c2, double eps, double dt, int64_t nsteps)
+{
+    if (check_args(n, x, v, m) || !a || nsteps < 0 || !(dt > 0.0))
+        return 1;
+    const size_t b = sizeof(double) * 3 * (size_t)n;
+    double *j0 = (double *)malloc(b), *xe = (double *)malloc(b), *ve = (double *)malloc(b);
+    double *a1 = (double *)malloc(b), *j1 = (double *)malloc(b);
+    double *bufs[] = {j0, xe, ve, a1, j1};
+    int rc = 0;
+    for (int q = 0; q < 5; ++q)
+        if (!bufs[q])
+            rc = 2;
+    if (rc == 0 && nsteps > 0)
+        rc = orc_jerk(n, x, v, m, G, inv_c2, eps, a, j0);
+    const double dt2 = dt * dt, dt3 = dt2 * dt;
+    for (int64_t s = 0; s < nsteps && rc == 0; ++s) {
+        for (int64_t q = 0; q < 3 * n; ++q) {
+            xe[q] = x[q] + dt * v[q] + dt2 / 2.0 * a[q] + dt3 / 6.0 * j0[q];
+            ve[q] = v[q] + dt * a[q] + dt2 / 2.0 * j0[q];
+        }
+        for (int pass = 0; pass < 2 && rc == 0; ++pass) {
+            rc = orc_accel(n, xe, ve, m, G, inv_c2, eps, a1);
+            if (rc == 0)
+                rc = orc_jerk(n, xe, ve, m, G, inv_c2, eps, a1, j1);
+            for (int64_t q = 0; q < 3 * n && rc == 0; ++q) {
+                ve[q] = v[q] + dt / 2.0 * (a[q] + a1[q]) + dt2 / 12.0 * (j0[q] - j1[q]);
+                xe[q] = x[q] + dt / 2.0 * (v[q] + ve[q]) + dt2 / 12.0 * (a[q] - a1[q]);
+            }
+        }
+        for (int64_t q = 0; q < 3 * n && rc == 0; ++q) {
+            x[q] = xe[q];
+            v[q] = ve[q];
+            a[q] = a1[q];
+            j0[q] = j1[q];
+        }
+    }
+    if (rc == 0 && nsteps > 0)
+        rc = orc_accel(n, x, v, m, G, inv_c2, eps, a);
+    for (int q = 0; q < 5; ++q)
         free(bufs[q]);
     return rc;
 }

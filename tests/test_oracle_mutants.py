@@ -11,6 +11,7 @@ import pytest
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = os.path.join(ROOT, "oracle", "pn_oracle.c")
+INC = os.path.join(ROOT, "oracle", "pn_oracle_accel.inc")
 
 MUTANTS = [
     ("Eq.6 line 2: 5/(4 r_j1) -> 4/(4 r_j1)",
@@ -34,11 +35,11 @@ MUTANTS = [
      "kadd3(&acc, -3.5 * G * G * mj * mk / (rjk_3 * r1j), xjk);",
      "kadd3(&acc, -3.0 * G * G * mj * mk / (rjk_3 * r1j), xjk);"),
     ("Eq.3: k = j dropped from the velocity-replacement sum",
-     "        if (k == j)\n            continue;\n        const double r1k_2", "        const double r1k_2"),
+     "        if (k == j)\n            continue;\n        const REAL r1k_2", "        const REAL r1k_2"),
     ("softening on a hole-star separation (star equation)",
-     "const double rj1 = sqrt(dot(xj1, xj1));", "const double rj1 = sqrt(dot(xj1, xj1) + e2);"),
+     "const REAL rj1 = SQRT(dot(xj1, xj1));", "const REAL rj1 = SQRT(dot(xj1, xj1) + e2);"),
     ("softening on a hole-star separation (hole equation)",
-     "const double r1k = sqrt(r1k_2);", "const double r1k = sqrt(r1k_2 + e2);"),
+     "const REAL r1k = SQRT(r1k_2);", "const REAL r1k = SQRT(r1k_2 + e2);"),
     ("Eq.7: 6 v_i^2 -> 7 v_i^2", "0.25 * gmm * (6.0 * vi2", "0.25 * gmm * (7.0 * vi2"),
     ("Eq.7: i = j term of the last double sum dropped twice",
      "kadd(&ePN, 0.5 * o[3]);", "kadd(&ePN, o[3]);"),
@@ -47,16 +48,27 @@ MUTANTS = [
      "kadd3(&s_p, -0.5 * gmm, w);", "kadd3(&s_p, -1.0 * gmm, w);"),
     ("integrator: no velocity prediction",
      "vp[q] = vel_mode == 0 ? vh[q] + h * a[q] : vh[q];", "vp[q] = vel_mode == 0 ? vh[q] : vh[q];"),
+    ("jerk: velocity tangent (the a_j of Appendix A) dropped",
+     "vc[q] = v[q] + I * (h * a[q]);", "vc[q] = v[q];"),
+    ("Hermite corrector: dt^2/12 -> dt^2/10 in the velocity",
+     "dt2 / 12.0 * (j0[q] - j1[q]);", "dt2 / 10.0 * (j0[q] - j1[q]);"),
+    ("Hermite: a single evaluate-correct pass",
+     "for (int pass = 0; pass < 2 && rc == 0; ++pass)", "for (int pass = 0; pass < 1 && rc == 0; ++pass)"),
 ]
 
 
 @pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
 def test_pins_catch_mutant(tmp_path, name, old, new):
-    src = open(SRC).read()
-    assert old in src, f"mutation site vanished: {name}"
+    src, inc = open(SRC).read(), open(INC).read()
+    assert old in src or old in inc, f"mutation site vanished: {name}"
     c = tmp_path / "mutant.c"
     so = tmp_path / "mutant.so"
-    c.write_text(src.replace(old, new, 1))
+    if old in src:
+        src = src.replace(old, new, 1)
+    else:
+        inc = inc.replace(old, new, 1)
+    c.write_text(src)
+    (tmp_path / os.path.basename(INC)).write_text(inc)
     subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
                     "-o", str(so), str(c), "-lm"], check=True)
     env = dict(os.environ, PN_ORACLE_LIB=str(so), OMP_NUM_THREADS="2")

@@ -392,6 +392,64 @@ def test_rk4_is_fourth_order(orc):
     np.testing.assert_allclose(aa, orc.accel(xx, vv, m, c=c), rtol=0, atol=0)
 
 
+# -------------------------------------------------------- jerk, Hermite --
+
+def test_jerk_is_the_time_derivative_along_the_trajectory(orc):
+    """Appendix A: j = dA/dt along x' = v, v' = A.  Checked against a
+    Richardson-extrapolated central difference of A(x + h v, v + h a)."""
+    x, v, m = _random_state(24, 31, m_star=1e-2)
+    c, eps = 8.0, 1e-3
+    a = orc.accel(x, v, m, c=c, eps=eps)
+    j = orc.jerk(x, v, m, a, c=c, eps=eps)
+
+    def cd(h):
+        return (orc.accel(x + h * v, v + h * a, m, c=c, eps=eps)
+                - orc.accel(x - h * v, v - h * a, m, c=c, eps=eps)) / (2 * h)
+
+    fd = (4.0 * cd(5e-5) - cd(1e-4)) / 3.0
+    assert np.max(_rel(j, fd)) < 1e-9
+    # the 1PN part matters at this c: the jerk is not the Newtonian one
+    jn = orc.jerk(x, v, m, orc.accel(x, v, m, eps=eps), eps=eps)
+    assert np.median(_rel(j, jn)) > 1e-3
+
+
+def test_jerk_newtonian_closed_form(orc):
+    """c -> inf: d/dt of -G m_k x_ik / r^3 is -G m_k [v_ik/r^3 - 3 (x_ik.v_ik) x_ik/r^5]
+    (the first terms of Appendix A), r softened between stars only."""
+    x, v, m = _random_state(20, 32, m_star=1e-2)
+    G, eps = 1.3, 1e-2
+    j = orc.jerk(x, v, m, G=G, eps=eps)
+    n = len(m)
+    want = np.zeros_like(x)
+    for i in range(n):
+        for k in range(n):
+            if k == i:
+                continue
+            d, u = x[i] - x[k], v[i] - v[k]
+            r2 = d @ d + (eps * eps if (i and k) else 0.0)
+            want[i] += -G * m[k] * (u / r2 ** 1.5 - 3.0 * (d @ u) * d / r2 ** 2.5)
+    assert np.max(_rel(j, want)) < 1e-11
+
+
+@pytest.mark.parametrize("c", [4.0, math.inf])
+def test_hermite_is_fourth_order_and_matches_rk4(orc, c):
+    """The Hermite scheme (Section 5) with the jerk: self-convergence ratio
+    2^4 = 16 with the velocity-dependent 1PN force, and the same trajectory
+    as the paper's RK4 at small steps."""
+    x, v, m = _orbiting_stars(2, 1e-3, seed=4)
+    a = orc.accel(x, v, m, c=c)
+    T = 2.0
+    xs = []
+    for nst in (50, 100, 200):
+        xx, vv, aa = orc.hermite_step(x, v, m, a, T / nst, nst, c=c)
+        xs.append(xx)
+    r = np.linalg.norm(xs[0] - xs[1]) / np.linalg.norm(xs[1] - xs[2])
+    assert 14.0 < r < 18.0, r
+    np.testing.assert_allclose(aa, orc.accel(xx, vv, m, c=c), rtol=0, atol=0)
+    xr, _, _ = orc.rk4_step(x, v, m, a, T / 400, 400, c=c)
+    assert np.linalg.norm(xs[2] - xr) < 0.2 * np.linalg.norm(xs[1] - xs[2])
+
+
 # ------------------------------------------------------------ invariances --
 
 def test_rotation_and_translation_invariance(orc):
