@@ -56,7 +56,7 @@ typedef enum {
 enum { PN_FP64 = 0, PN_MIXED = 1 };            /* pn_params.precision */
 enum { PN_VPRED_END = 0, PN_VHALF = 1 };       /* pn_params.vel_mode  */
 enum { PN_PAIR_FUSED = 0, PN_PAIR_TWO_PASS = 1 };   /* pn_params.pair_kernel */
-enum { PN_KDK = 0, PN_RK4 = 1 };                   /* pn_params.integrator  */
+enum { PN_KDK = 0, PN_RK4 = 1, PN_HERMITE = 2 };   /* pn_params.integrator  */
 
 /*
  * Physical constants and evaluation mode.
@@ -89,7 +89,9 @@ enum { PN_KDK = 0, PN_RK4 = 1 };                   /* pn_params.integrator  */
  *   integrator PN_KDK: kick-drift-kick leapfrog (vel_mode applies), one
  *              force evaluation per step.  PN_RK4: classical fourth-order
  *              Runge-Kutta, the paper's own integrator (Section 4), four
- *              evaluations per step.
+ *              evaluations per step.  PN_HERMITE: fourth-order Hermite with
+ *              the jerk (the integrator Section 5 recommends, Appendix A),
+ *              two force and jerk evaluations per step.
  */
 typedef struct {
     double G;
@@ -159,6 +161,14 @@ pn_status pn_accel(pn_ctx *ctx, const double *x, const double *v, const double *
  *   a = A(x, v_p);  v = v_h + dt/2 a.
  * PN_RK4: k1 = (v, a), k2 = f(y + dt/2 k1), k3 = f(y + dt/2 k2),
  *   k4 = f(y + dt k3), y += dt/6 (k1 + 2 k2 + 2 k3 + k4), a = A(y).
+ * PN_HERMITE: j = jerk at the entry state, then per step
+ *   predict  x_p = x + dt v + dt^2/2 a + dt^3/6 j,  v_p = v + dt a + dt^2/2 j,
+ *   twice:   a_1 = A(x_e, v_e), j_1 = jerk(x_e, v_e, a_1),
+ *            v_e = v + dt/2 (a + a_1) + dt^2/12 (j - j_1),
+ *            x_e = x + dt/2 (v + v_e) + dt^2/12 (a - a_1)
+ *   ((x_e, v_e) = (x_p, v_p) in the first pass), and (x, v, a, j) =
+ *   (x_e, v_e, a_1, j_1); after the last step a = A(x, v).  The jerk is
+ *   always evaluated in double precision.
  * `a` is carried state: on entry it must hold the acceleration of the entry
  * state (call pn_accel once before the first pn_step); on return it holds
  * the acceleration of the final state.  Device pointers.
@@ -166,6 +176,20 @@ pn_status pn_accel(pn_ctx *ctx, const double *x, const double *v, const double *
  */
 pn_status pn_step(pn_ctx *ctx, double *x, double *v, const double *m, double *a,
                   double dt, int64_t nsteps);
+
+/*
+ * The jerk (Appendix A): writes a = A(x, v) (the context's precision) and
+ * jerk = dA/dt along the trajectory, sum_k [dA/dx_k . v_k + dA/dv_k . a_k],
+ * for every body, n x 3 each.  The derivative is taken in forward mode
+ * (dual numbers) of the same decomposition the acceleration kernels use, in
+ * double precision whatever the context's precision, with no near-source
+ * split.  Device pointers; a and jerk must not alias x, v or m.  Allocates
+ * its scratch on the first call.  Errors: PN_EINVAL (NULL pointer),
+ * PN_ENOMEM, PN_ECUDA; a non-finite jerk is reported by pn_sync as
+ * PN_ENONFINITE.
+ */
+pn_status pn_jerk(pn_ctx *ctx, const double *x, const double *v, const double *m, double *a,
+                  double *jerk);
 
 /*
  * pn_step captured into one CUDA graph and launched as a whole: the first

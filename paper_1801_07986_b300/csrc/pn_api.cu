@@ -78,8 +78,9 @@ bool params_ok(const pn_params *p)
     if (p->pair_kernel != PN_PAIR_FUSED && p->pair_kernel != PN_PAIR_TWO_PASS)
         return (void)fail(PN_EINVAL, "pair_kernel must be PN_PAIR_FUSED or PN_PAIR_TWO_PASS (got %d)",
                           p->pair_kernel), false;
-    if (p->integrator != PN_KDK && p->integrator != PN_RK4)
-        return (void)fail(PN_EINVAL, "integrator must be PN_KDK or PN_RK4 (got %d)", p->integrator),
+    if (p->integrator != PN_KDK && p->integrator != PN_RK4 && p->integrator != PN_HERMITE)
+        return (void)fail(PN_EINVAL, "integrator must be PN_KDK, PN_RK4 or PN_HERMITE (got %d)",
+                          p->integrator),
                false;
     return true;
 }
@@ -118,7 +119,8 @@ void free_all(pn_ctx *c)
 {
     void *bufs[] = {c->vp, c->mrec, c->drec, c->part, c->blk, c->glob, c->eout, c->flag, c->wcount,
                     c->flag_step, c->hx, c->hv, c->hm, c->ha, c->nrec, c->ndrec, c->ncount,
-                    c->nflag, c->rk_x, c->rk_v, c->rk_a, c->rk_sx, c->rk_sv, c->d_clu,
+                    c->nflag, c->rk_x, c->rk_v, c->rk_a, c->rk_sx, c->rk_sv, c->jbuf, c->hj0, c->hj1,
+                    c->d_clu,
                     c->blk_clu};
     for (void *b : bufs)
         if (b)
@@ -203,11 +205,68 @@ pn_status run_rk4(pn_ctx *c, double *x, double *v, const double *m, double *a, d
     return PN_OK;
 }
 
+// Scratch of the jerk and the Hermite steps, allocated on first use (never
+// inside a graph capture: pn_step_graph allocates it before capturing).
+pn_status ensure_jerk_buffers(pn_ctx *c)
+{
+    if (c->jbuf)
+        return PN_OK;
+    const size_t b3 = sizeof(double) * 3 * (size_t)c->n;
+    void **p[] = {(void **)&c->jbuf, (void **)&c->hj0, (void **)&c->hj1};
+    const size_t bytes[] = {sizeof(double) * pn::jerk_buffer_doubles(c), b3, b3};
+    for (int k = 0; k < 3; ++k) {
+        if (*p[k])
+            continue;
+        if (std::getenv("PN_FAIL_ALLOC") || cudaMalloc(p[k], bytes[k]) != cudaSuccess) {
+            cudaGetLastError();
+            for (int q = 0; q < 3; ++q)
+                if (*p[q]) {
+                    cudaFree(*p[q]);
+                    *p[q] = nullptr;
+                }
+            return fail(PN_ENOMEM, "cudaMalloc of %zu bytes for the jerk failed", bytes[k]);
+        }
+    }
+    return PN_OK;
+}
+
+// Fourth-order Hermite, predict-(evaluate-correct)^2; the stages are stated
+// with pn_step in pn.h.  rk_x / rk_v hold (x_e, v_e), rk_a a_1, hj0 / hj1
+// the jerks.
+pn_status run_hermite(pn_ctx *c, double *x, double *v, const double *m, double *a, double dt,
+                      int64_t nsteps)
+{
+    if (nsteps == 0)
+        return PN_OK;
+    pn_status st = ensure_jerk_buffers(c);
+    if (st != PN_OK)
+        return st;
+    PN_CUDA(pn::launch_jerk(c, x, v, m, a, c->hj0), "jerk launch");
+    for (int64_t s = 0; s < nsteps; ++s) {
+        c->step_counter += 1;
+        PN_CUDA(pn::launch_hermite(c, 0, x, v, a, c->hj0, nullptr, nullptr, c->rk_x, c->rk_v, dt),
+                "hermite predict launch");
+        for (int pass = 0; pass < 2; ++pass) {
+            st = evaluate(c, c->rk_x, c->rk_v, m, c->rk_a, nullptr, 0.0);
+            if (st != PN_OK)
+                return st;
+            PN_CUDA(pn::launch_jerk(c, c->rk_x, c->rk_v, m, c->rk_a, c->hj1), "jerk launch");
+            PN_CUDA(pn::launch_hermite(c, 1, x, v, a, c->hj0, c->rk_a, c->hj1, c->rk_x, c->rk_v,
+                                       dt), "hermite correct launch");
+        }
+        PN_CUDA(pn::launch_hermite(c, 2, x, v, a, c->hj0, c->rk_a, c->hj1, c->rk_x, c->rk_v, dt),
+                "hermite commit launch");
+    }
+    return evaluate(c, x, v, m, a, nullptr, 0.0);
+}
+
 pn_status run_steps(pn_ctx *c, double *x, double *v, const double *m, double *a, double dt,
                     int64_t nsteps)
 {
     if (c->p.integrator == PN_RK4)
         return run_rk4(c, x, v, m, a, dt, nsteps);
+    if (c->p.integrator == PN_HERMITE)
+        return run_hermite(c, x, v, m, a, dt, nsteps);
     for (int64_t s = 0; s < nsteps; ++s) {
         c->step_counter += 1;
         PN_CUDA(pn::launch_kick_drift(c, x, v, a, dt), "kick-drift launch");
@@ -522,6 +581,31 @@ pn_status pn_accel(pn_ctx *c, const double *x, const double *v, const double *m,
     return st == PN_OK ? ok() : st;
 }
 
+pn_status pn_jerk(pn_ctx *c, const double *x, const double *v, const double *m, double *a,
+                  double *jerk)
+{
+    if (check_ctx(c) != PN_OK)
+        return PN_EINVAL;
+    if (!x || !v || !m || !a || !jerk)
+        return fail(PN_EINVAL, "pn_jerk: NULL array");
+    const void *in[] = {x, v, m};
+    for (const void *q : in)
+        if (q == a || q == jerk)
+            return fail(PN_EINVAL, "pn_jerk: an output aliases an input");
+    if (a == jerk)
+        return fail(PN_EINVAL, "pn_jerk: a and jerk alias");
+    DeviceGuard g(c->device);
+    PN_CUDA(g.err, "cudaSetDevice");
+    pn_status st = ensure_jerk_buffers(c);
+    if (st != PN_OK)
+        return st;
+    st = evaluate(c, x, v, m, a, nullptr, 0.0);
+    if (st != PN_OK)
+        return st;
+    PN_CUDA(pn::launch_jerk(c, x, v, m, a, jerk), "jerk launch");
+    return ok();
+}
+
 pn_status pn_step(pn_ctx *c, double *x, double *v, const double *m, double *a, double dt,
                   int64_t nsteps)
 {
@@ -559,6 +643,11 @@ pn_status pn_step_graph(pn_ctx *c, double *x, double *v, const double *m, double
         if (c->graph_exec) {
             cudaGraphExecDestroy(c->graph_exec);
             c->graph_exec = nullptr;
+        }
+        if (c->p.integrator == PN_HERMITE) {
+            pn_status st = ensure_jerk_buffers(c);
+            if (st != PN_OK)
+                return st;
         }
         if (!c->cap_stream)
             PN_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking),

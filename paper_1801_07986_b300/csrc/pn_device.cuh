@@ -1,0 +1,199 @@
+// pn_device.cuh -- device helpers shared by the kernel files of libpn:
+// deterministic block reductions, the cluster lookup, the non-finite flag,
+// a forward-mode dual number, and the per-star assembly of Eq. 4-6 (and the
+// star's term of Eq. 1-3) written once over the scalar type.
+#pragma once
+
+#include <math.h>
+#include <stdint.h>
+
+#include "pn_internal.h"
+
+namespace pn {
+
+// Deterministic block sum of K doubles per thread (fixed tree, blockDim =
+// kGlueThreads); thread 0 ends with the totals in sh[k][0].
+template <int K>
+__device__ __forceinline__ void block_sum(double (&val)[K], double (*sh)[kGlueThreads])
+{
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        sh[k][t] = val[k];
+    __syncthreads();
+    for (int s = kGlueThreads / 2; s > 0; s >>= 1) {
+        if (t < s) {
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                sh[k][t] += sh[k][t + s];
+        }
+        __syncthreads();
+    }
+}
+
+// Sum per-block partials blk[b*K + k] over b in a fixed order (one block).
+template <int K>
+__device__ __forceinline__ void sum_blocks(const double *__restrict__ blk, int64_t nblk,
+                                           double (*sh)[kGlueThreads])
+{
+    double v[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        v[k] = 0.0;
+    for (int64_t b = threadIdx.x; b < nblk; b += kGlueThreads) {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            v[k] += blk[b * K + k];
+    }
+    block_sum<K>(v, sh);
+}
+
+__device__ __forceinline__ void flag_nonfinite(const double a[3], int *flag,
+                                               unsigned long long *flag_step,
+                                               unsigned long long step)
+{
+    if (!(isfinite(a[0]) && isfinite(a[1]) && isfinite(a[2]))) {
+        atomicOr(flag, 1);
+        atomicMin(flag_step, step);
+    }
+}
+
+// Clusters: the state arrays hold one or more independent clusters, each a
+// hole (body clu.body0) followed by clu.ns stars.  Star slots of all
+// clusters are laid end to end, each cluster padded to a multiple of kPad
+// (zero-mass far-away dummies), so every 256-slot block and every target
+// block lies inside one cluster; blk_clu[slot / 256] names it (nullptr:
+// a single cluster, index 0).
+__device__ __forceinline__ int cluster_of_block(const int *__restrict__ blk_clu, int64_t b)
+{
+    return blk_clu ? blk_clu[b] : 0;
+}
+
+// ------------------------------------------------------- dual numbers --
+
+// Forward-mode dual number v + d eps (eps^2 = 0): evaluating a function on
+// Duals gives its value and its derivative along the seeded direction.
+struct Dual {
+    double v, d;
+};
+
+__device__ __forceinline__ Dual operator+(Dual a, Dual b) { return {a.v + b.v, a.d + b.d}; }
+__device__ __forceinline__ Dual operator-(Dual a, Dual b) { return {a.v - b.v, a.d - b.d}; }
+__device__ __forceinline__ Dual operator-(Dual a) { return {-a.v, -a.d}; }
+__device__ __forceinline__ Dual operator*(Dual a, Dual b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+__device__ __forceinline__ Dual operator*(double s, Dual a) { return {s * a.v, s * a.d}; }
+__device__ __forceinline__ Dual operator*(Dual a, double s) { return {a.v * s, a.d * s}; }
+__device__ __forceinline__ Dual operator+(Dual a, double s) { return {a.v + s, a.d}; }
+__device__ __forceinline__ Dual operator+(double s, Dual a) { return {s + a.v, a.d}; }
+__device__ __forceinline__ Dual operator-(Dual a, double s) { return {a.v - s, a.d}; }
+__device__ __forceinline__ Dual operator-(double s, Dual a) { return {s - a.v, -a.d}; }
+__device__ __forceinline__ Dual operator/(double s, Dual a)
+{
+    const double r = s / a.v;
+    return {r, -r * a.d / a.v};
+}
+__device__ __forceinline__ Dual operator/(Dual a, double s) { return {a.v / s, a.d / s}; }
+__device__ __forceinline__ Dual &operator+=(Dual &a, Dual b)
+{
+    a.v += b.v;
+    a.d += b.d;
+    return a;
+}
+
+__device__ __forceinline__ double tsqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ Dual tsqrt(Dual a)
+{
+    const double s = sqrt(a.v);
+    return {s, 0.5 * a.d / s};
+}
+
+// ----------------------------------------------- per-star assembly --
+
+// Star i's acceleration (Eq. 4-6) and its term of the hole's 1PN
+// acceleration (Eq. 2-3, j = i), from the pair sums of passes 1 and 2, the
+// near-source sums and the cluster's global sums, over scalar type T
+// (double, or Dual for the jerk).  Velocities vv are those at which A is
+// taken; M and m_i are constants.
+//   a_i = -G M d_i/R_i^3 - G N_i + (1/c^2) {
+//       G M d_i/R_i^3 (4 G M/R_i - v_i^2) + 4 G M (v_i.d_i) v_i/R_i^3   [Eq. 5]
+//     + 5 G^2 m_i M d_i/R_i^4                                          [Eq. 6 l.1]
+//     + G^2 M d_i/R_i^3 S_i                                            [Eq. 6 l.2]
+//     + G [V_i + (4 G M/R_i + v_i^2) N_i]                              [l.3 + l.6]
+//     - 7/2 G^2 M [E_i - (W_far - w_i)/R_i]                            [l.4]
+//     - G/R_i^3 [4 (v_i.Q) d_i - 3 (Q.d_i) v_i - 4 (v_i.d_i) Q]        [l.1 + l.5]
+//     + G H_i                                                          [l.7]
+//     + G^2 M (P_i - 7/2 Ee_i) }                                       [near sources]
+// with V_i = 3/2 V'_i (pass 2 carries -4/3 of the v_i^2 part, as
+// -2 v_i^2 N_i, so the coefficient of N_i applied here is 4 G M/R_i - v_i^2),
+// H_i = 3/2 (Hs_i v_i - Hv_i), and over far sources j != i
+//   S_i = 4 U_i + sum_far m_j (5/(4R_j) + (R_i^2 - r_ij^2)/(4R_j^3))
+//       = 4 U_i + (SA_far - 5 m_i/(4R_i)) + d_i.(W_far - w_i)/2
+//         - (SB_far - m_i (R_i^2 + eps^2)/(4 R_i^3))
+// (R_i^2 - r_ij^2 = 2 d_i.d_j - R_j^2 - eps^2; the m_i / w_i self terms are
+// removed only when star i is itself a far source, fi = 1).  Line 1's self
+// term and line 5 together are the k-sum over all stars, hence Q.
+// The hole's term (Eq. 2 and Eq. 3 with j = i), Y_i = R_i^2 Z_i - Wr_i:
+//   -G w_j (5 G M/R_j - 2 v_j^2 + 3/2 (v_j.d_j)^2/R_j^2) - 3 G m_j/R_j^3 (v_j.d_j) v_j
+//   - 4 G^2 m_j w_j / R_j
+//   - G^2 w_j [4 (Phi - m_j/R_j) + 5/4 U_j + 1/4 Y_j]
+//   - 7/2 G^2 (m_j/R_j) N_j
+//   + G/M m_j/R_j^3 [4 (v_j.Q) d_j - 3 (v_j.d_j) Q - 4 (Q.d_j) v_j]
+template <class T>
+struct StarSums {
+    T N[3], U, Z, Wr;        // pass 1
+    T Vp[3], Hs, Hv[3], E[3];  // pass 2
+    T P[3], Ee[3];           // near-source pass (zero when unused)
+};
+
+template <class T>
+struct ClusterSums {
+    T Q[3], Wf[3], SA, SB, Phi;
+};
+
+template <class T>
+__device__ __forceinline__ void star_eqs(double G, double M, double mi, double eps2,
+                                         double inv_c2, double fi, const T (&d)[3],
+                                         const T (&vv)[3], const StarSums<T> &s,
+                                         const ClusterSums<T> &g, T (&ai)[3], T (&bh)[3])
+{
+    const double GM = G * M;
+    const T R2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const T R = tsqrt(R2);
+    const T iR = 1.0 / R;
+    const T iR3 = iR * iR * iR;
+    const T v2 = vv[0] * vv[0] + vv[1] * vv[1] + vv[2] * vv[2];
+    const T vd = vv[0] * d[0] + vv[1] * d[1] + vv[2] * d[2];
+    const T Y = R2 * s.Z - s.Wr;
+    T Vv[3], H[3];
+    for (int k = 0; k < 3; ++k) {
+        Vv[k] = 1.5 * s.Vp[k];
+        H[k] = 1.5 * (s.Hs * vv[k] - s.Hv[k]);
+    }
+    const T wi[3] = {mi * iR3 * d[0], mi * iR3 * d[1], mi * iR3 * d[2]};
+    const T Wx[3] = {g.Wf[0] - fi * wi[0], g.Wf[1] - fi * wi[1], g.Wf[2] - fi * wi[2]};
+    const T vQ = vv[0] * g.Q[0] + vv[1] * g.Q[1] + vv[2] * g.Q[2];
+    const T Qd = g.Q[0] * d[0] + g.Q[1] * d[1] + g.Q[2] * d[2];
+    const T S = 4.0 * s.U + (g.SA - fi * 1.25 * mi * iR) +
+                0.5 * (d[0] * Wx[0] + d[1] * Wx[1] + d[2] * Wx[2]) -
+                (g.SB - fi * 0.25 * mi * (R2 + eps2) * iR3);
+    const T cd = GM * iR3 * (4.0 * GM * iR - v2) + 5.0 * G * GM * mi * iR3 * iR +
+                 G * GM * iR3 * S - 4.0 * G * iR3 * vQ;
+    const T cv = 4.0 * GM * iR3 * vd + 3.0 * G * iR3 * Qd;
+    const T cN = G * (4.0 * GM * iR - v2);
+    const T cQ = 4.0 * G * iR3 * vd;
+    const double c7 = 3.5 * G * GM;
+    for (int k = 0; k < 3; ++k) {
+        const T pn = cd * d[k] + cv * vv[k] + G * Vv[k] + cN * s.N[k] -
+                     c7 * (s.E[k] - Wx[k] * iR) + cQ * g.Q[k] + G * H[k] +
+                     G * GM * (s.P[k] - 3.5 * s.Ee[k]);
+        ai[k] = (-GM * iR3 * d[k] - G * s.N[k]) + inv_c2 * pn;
+    }
+    const T b1 = -G * (5.0 * GM * iR - 2.0 * v2 + 1.5 * vd * vd * iR * iR) -
+                 4.0 * G * G * mi * iR - G * G * (4.0 * (g.Phi - mi * iR) + 1.25 * s.U + 0.25 * Y);
+    const T gmr3 = G * mi * iR3;
+    for (int k = 0; k < 3; ++k)
+        bh[k] = b1 * wi[k] - 3.0 * gmr3 * vd * vv[k] - 3.5 * G * G * mi * iR * s.N[k] +
+                (gmr3 / M) * (4.0 * vQ * d[k] - 3.0 * vd * g.Q[k] - 4.0 * Qd * vv[k]);
+}
+
+}  // namespace pn

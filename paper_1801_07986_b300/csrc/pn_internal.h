@@ -121,6 +121,8 @@ struct pn_ctx {
     // RK4 stage buffers (n x 3 each): stage position / velocity, stage
     // acceleration, and the running k-sums of x and v
     double *rk_x, *rk_v, *rk_a, *rk_sx, *rk_sv;
+    double *jbuf;            // jerk scratch (allocated by the first pn_jerk / Hermite step)
+    double *hj0, *hj1;       // Hermite: jerk at the current state and at the evaluation state
 
     // device copies used by pn_step_host
     double *hx, *hv, *hm, *ha;
@@ -146,6 +148,12 @@ namespace pn {
 cudaError_t launch_kick_drift(pn_ctx *c, double *x, double *v, const double *a, double dt);
 cudaError_t launch_rk4_stage(pn_ctx *c, int stage, double *x, double *v, const double *a,
                              double dt);
+size_t jerk_buffer_doubles(const pn_ctx *c);
+cudaError_t launch_jerk(pn_ctx *c, const double *x, const double *v, const double *m,
+                        const double *a, double *jerk);
+cudaError_t launch_hermite(pn_ctx *c, int stage, double *x, double *v, double *a, double *j,
+                           const double *a1, const double *j1, double *xe, double *ve,
+                           double dt);
 cudaError_t launch_prologue(pn_ctx *c, const double *x, const double *vel, const double *m,
                             bool energy_records);
 cudaError_t launch_pass1(pn_ctx *c);

@@ -25,7 +25,7 @@
 #include <math.h>
 #include <stdint.h>
 
-#include "pn_internal.h"
+#include "pn_device.cuh"
 
 namespace pn {
 
@@ -62,53 +62,6 @@ __device__ __forceinline__ double rsqrt_f64(double s2)
     y = y * fma(-h, y * y, 1.5);
     y = y * fma(-h, y * y, 1.5);
     return y;
-}
-
-// Deterministic block sum of K doubles per thread (fixed tree, blockDim =
-// kGlueThreads); thread 0 ends with the totals in sh[k][0].
-template <int K>
-__device__ __forceinline__ void block_sum(double (&val)[K], double (*sh)[kGlueThreads])
-{
-    const int t = threadIdx.x;
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-        sh[k][t] = val[k];
-    __syncthreads();
-    for (int s = kGlueThreads / 2; s > 0; s >>= 1) {
-        if (t < s) {
-#pragma unroll
-            for (int k = 0; k < K; ++k)
-                sh[k][t] += sh[k][t + s];
-        }
-        __syncthreads();
-    }
-}
-
-// Sum per-block partials blk[b*K + k] over b in a fixed order (one block).
-template <int K>
-__device__ __forceinline__ void sum_blocks(const double *__restrict__ blk, int64_t nblk,
-                                           double (*sh)[kGlueThreads])
-{
-    double v[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-        v[k] = 0.0;
-    for (int64_t b = threadIdx.x; b < nblk; b += kGlueThreads) {
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-            v[k] += blk[b * K + k];
-    }
-    block_sum<K>(v, sh);
-}
-
-__device__ __forceinline__ void flag_nonfinite(const double a[3], int *flag,
-                                               unsigned long long *flag_step,
-                                               unsigned long long step)
-{
-    if (!(isfinite(a[0]) && isfinite(a[1]) && isfinite(a[2]))) {
-        atomicOr(flag, 1);
-        atomicMin(flag_step, step);
-    }
 }
 
 // --------------------------------------------------------- integrator --
@@ -164,17 +117,6 @@ __global__ void k_rk4_stage(int stage, int64_t n3, double *__restrict__ x, doubl
 }
 
 // ------------------------------------------------------------ prologue --
-
-// Clusters: the state arrays hold one or more independent clusters, each a
-// hole (body clu.body0) followed by clu.ns stars.  Star slots of all
-// clusters are laid end to end, each cluster padded to a multiple of kPad
-// (zero-mass far-away dummies), so every 256-slot block and every target
-// block lies inside one cluster; blk_clu[slot / 256] names it (nullptr:
-// a single cluster, index 0).
-__device__ __forceinline__ int cluster_of_block(const int *__restrict__ blk_clu, int64_t b)
-{
-    return blk_clu ? blk_clu[b] : 0;
-}
 
 // Per star slot t of cluster k (star j = body0 + 1 + (t - slot0); slots past
 // the cluster's stars are padding):
@@ -1363,35 +1305,10 @@ k_near_f64(const double4_32a *__restrict__ rec, const double4_32a *__restrict__ 
 
 // ------------------------------------------------------------ epilogue --
 
-// Star i = t + 1 (double precision throughout), velocities v = those at
-// which A is taken:
-//   a_i = -G M d_i/R_i^3 - G N_i + (1/c^2) {
-//       G M d_i/R_i^3 (4 G M/R_i - v_i^2) + 4 G M (v_i.d_i) v_i/R_i^3   [Eq. 5]
-//     + 5 G^2 m_i M d_i/R_i^4                                          [Eq. 6 l.1]
-//     + G^2 M d_i/R_i^3 S_i                                            [Eq. 6 l.2]
-//     + G [V_i + (4 G M/R_i + v_i^2) N_i]                              [l.3 + l.6]
-//       (V_i from pass 2 carries -4/3 of the v_i^2 part as -2 v_i^2 N_i, so
-//        the coefficient of N_i applied here is 4 G M/R_i - v_i^2)
-//     - 7/2 G^2 M [E_i - (W_far - w_i)/R_i]                            [l.4]
-//     - G/R_i^3 [4 (v_i.Q) d_i - 3 (Q.d_i) v_i - 4 (v_i.d_i) Q]        [l.1 + l.5]
-//     + G H_i                                                          [l.7]
-//     + G^2 M (P_i - 7/2 Ee_i) }                                       [near sources]
-// with, over far sources j != i,
-//   S_i = 4 U_i + sum_far m_j (5/(4R_j) + (R_i^2 - r_ij^2)/(4R_j^3))
-//       = 4 U_i + (SA_far - 5 m_i/(4R_i)) + d_i.(W_far - w_i)/2
-//         - (SB_far - m_i (R_i^2 + eps^2)/(4 R_i^3))
-// (R_i^2 - r_ij^2 = 2 d_i.d_j - R_j^2 - eps^2; the m_i / w_i self terms are
-// removed only when star i is itself a far source).  Line 1's self term and
-// line 5 together are the k-sum over all stars, hence Q.
-//
-// The same thread also forms star i's term of the hole's 1PN acceleration
-// (Eq. 2 and Eq. 3, with j = i):
-//   -G w_j (5 G M/R_j - 2 v_j^2 + 3/2 (v_j.d_j)^2/R_j^2) - 3 G m_j/R_j^3 (v_j.d_j) v_j
-//   - 4 G^2 m_j w_j / R_j
-//   - G^2 w_j [4 (Phi - m_j/R_j) + 5/4 U_j + 1/4 Y_j]
-//   - 7/2 G^2 (m_j/R_j) N_j
-//   + G/M m_j/R_j^3 [4 (v_j.Q) d_j - 3 (v_j.d_j) Q - 4 (Q.d_j) v_j]
-// and the block's sum of these goes to blk (deterministic tree).
+// Star i = t + 1 (double precision throughout): sums the partials of every
+// pass for its slot and assembles its acceleration and its term of the
+// hole's acceleration with star_eqs (the formulas are stated there); the
+// block's sum of the hole terms goes to blk (deterministic tree).
 __global__ void __launch_bounds__(kGlueThreads)
 k_epilogue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_clu,
            const double *__restrict__ x, const double *__restrict__ vel,
@@ -1405,24 +1322,15 @@ k_epilogue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
     const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
     const int k_clu = cluster_of_block(blk_clu, blockIdx.x);
     const Clu Cl = clu[k_clu];
-    const double G = Cl.G, inv_c2 = Cl.inv_c2, eps2 = Cl.eps2;
     const double *glob = globs + (int64_t)k_clu * kGlobVals;
     const int64_t lt = t - Cl.slot0;
     double bh[3] = {0.0, 0.0, 0.0};
     if (lt < Cl.ns) {
         const int64_t i = Cl.body0 + 1 + lt, hb = Cl.body0;
-        const double M = m[hb], mi = m[i];
-        const double GM = G * M;
         const double d[3] = {x[3 * i] - x[3 * hb], x[3 * i + 1] - x[3 * hb + 1],
                              x[3 * i + 2] - x[3 * hb + 2]};
-        const double R2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-        const double R = sqrt(R2);
-        const double iR = 1.0 / R;
-        const double iR3 = iR * iR * iR;
         const double vv[3] = {vel[3 * i], vel[3 * i + 1], vel[3 * i + 2]};
-        const double v2 = vv[0] * vv[0] + vv[1] * vv[1] + vv[2] * vv[2];
-        const double vd = vv[0] * d[0] + vv[1] * d[1] + vv[2] * d[2];
-        double s1[kP1Vals], s2[kP2Vals], sn[kNearVals];
+        double s1[kP1Vals], s2[kP2Vals];
         for (int k = 0; k < kP1Vals; ++k) {
             double acc = 0.0;
             for (int s = 0; s < js1; ++s)
@@ -1435,46 +1343,30 @@ k_epilogue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
                 acc += p2[((int64_t)s * kP2Vals + k) * S + t];
             s2[k] = acc;
         }
-        for (int k = 0; k < kNearVals; ++k)
-            sn[k] = pnear ? pnear[(int64_t)k * S + t] : 0.0;
+        StarSums<double> ss;
+        for (int k = 0; k < 3; ++k) {
+            ss.N[k] = s1[k];
+            ss.Vp[k] = s2[k];
+            ss.Hv[k] = s2[4 + k];
+            ss.E[k] = s2[7 + k];
+            ss.P[k] = pnear ? pnear[(int64_t)k * S + t] : 0.0;
+            ss.Ee[k] = pnear ? pnear[(int64_t)(3 + k) * S + t] : 0.0;
+        }
+        ss.U = s1[3];
+        ss.Z = s1[4];
+        ss.Wr = s1[5];
+        ss.Hs = s2[3];
+        ClusterSums<double> gs;
+        for (int k = 0; k < 3; ++k) {
+            gs.Q[k] = glob[k];
+            gs.Wf[k] = glob[6 + k];
+        }
+        gs.SA = glob[9];
+        gs.SB = glob[10];
+        gs.Phi = glob[11];
         const double fi = nflag[t] ? 0.0 : 1.0;   // 1 if star i is a far source
-        const double N[3] = {s1[0], s1[1], s1[2]};
-        const double U = s1[3], Y = R2 * s1[4] - s1[5];
-        double Vv[3], H[3];
-        for (int k = 0; k < 3; ++k) {
-            Vv[k] = 1.5 * s2[k];                          // V = 3/2 V' (+ the N_i part below)
-            H[k] = 1.5 * (s2[3] * vv[k] - s2[4 + k]);     // H = 3/2 (Hs v_i - Hv)
-        }
-        const double Q[3] = {glob[0], glob[1], glob[2]};
-        const double Wf[3] = {glob[6], glob[7], glob[8]};
-        const double SA = glob[9], SB = glob[10], Phi = glob[11];
-        const double wi[3] = {mi * iR3 * d[0], mi * iR3 * d[1], mi * iR3 * d[2]};
-        const double Wx[3] = {Wf[0] - fi * wi[0], Wf[1] - fi * wi[1], Wf[2] - fi * wi[2]};
-        const double vQ = vv[0] * Q[0] + vv[1] * Q[1] + vv[2] * Q[2];
-        const double Qd = Q[0] * d[0] + Q[1] * d[1] + Q[2] * d[2];
-        const double S = 4.0 * U + (SA - fi * 1.25 * mi * iR) +
-                         0.5 * (d[0] * Wx[0] + d[1] * Wx[1] + d[2] * Wx[2]) -
-                         (SB - fi * 0.25 * mi * (R2 + eps2) * iR3);
-        const double cd = GM * iR3 * (4.0 * GM * iR - v2) + 5.0 * G * GM * mi * iR3 * iR +
-                          G * GM * iR3 * S - 4.0 * G * iR3 * vQ;
-        const double cv = 4.0 * GM * iR3 * vd + 3.0 * G * iR3 * Qd;
-        const double cN = G * (4.0 * GM * iR - v2);
-        const double cQ = 4.0 * G * iR3 * vd;
-        const double c7 = 3.5 * G * GM;
         double ai[3];
-        for (int k = 0; k < 3; ++k) {
-            const double pn = cd * d[k] + cv * vv[k] + G * Vv[k] + cN * N[k] -
-                              c7 * (s2[7 + k] - Wx[k] * iR) + cQ * Q[k] + G * H[k] +
-                              G * GM * (sn[k] - 3.5 * sn[3 + k]);
-            ai[k] = (-GM * iR3 * d[k] - G * N[k]) + inv_c2 * pn;
-        }
-        // hole's term from this star
-        const double b1 = -G * (5.0 * GM * iR - 2.0 * v2 + 1.5 * vd * vd * iR * iR) -
-                          4.0 * G * G * mi * iR - G * G * (4.0 * (Phi - mi * iR) + 1.25 * U + 0.25 * Y);
-        const double gmr3 = G * mi * iR3;
-        for (int k = 0; k < 3; ++k)
-            bh[k] = b1 * wi[k] - 3.0 * gmr3 * vd * vv[k] - 3.5 * G * G * mi * iR * N[k] +
-                    (gmr3 / M) * (4.0 * vQ * d[k] - 3.0 * vd * Q[k] - 4.0 * Qd * vv[k]);
+        star_eqs<double>(Cl.G, m[hb], m[i], Cl.eps2, Cl.inv_c2, fi, d, vv, ss, gs, ai, bh);
         flag_nonfinite(ai, flag, flag_step, step);
         for (int k = 0; k < 3; ++k) {
             a[3 * i + k] = ai[k];

@@ -28,14 +28,15 @@ STATUS_NAMES = {0: "PN_OK", 1: "PN_EINVAL", 2: "PN_ENOMEM", 3: "PN_ECUDA", 4: "P
 PN_FP64, PN_MIXED = 0, 1
 PN_VPRED_END, PN_VHALF = 0, 1
 PN_PAIR_FUSED, PN_PAIR_TWO_PASS = 0, 1
-PN_KDK, PN_RK4 = 0, 1
+PN_KDK, PN_RK4, PN_HERMITE = 0, 1, 2
 PN_NOALLOC_MAX_BODIES = 16384
 _PRECISION = {"fp64": PN_FP64, "mixed": PN_MIXED, PN_FP64: PN_FP64, PN_MIXED: PN_MIXED}
 _VEL_MODE = {"vpred_end": PN_VPRED_END, "vhalf": PN_VHALF, PN_VPRED_END: PN_VPRED_END,
              PN_VHALF: PN_VHALF}
 _PAIR = {"fused": PN_PAIR_FUSED, "two_pass": PN_PAIR_TWO_PASS, PN_PAIR_FUSED: PN_PAIR_FUSED,
          PN_PAIR_TWO_PASS: PN_PAIR_TWO_PASS}
-_INTEGRATOR = {"kdk": PN_KDK, "rk4": PN_RK4, PN_KDK: PN_KDK, PN_RK4: PN_RK4}
+_INTEGRATOR = {"kdk": PN_KDK, "rk4": PN_RK4, "hermite": PN_HERMITE, PN_KDK: PN_KDK,
+               PN_RK4: PN_RK4, PN_HERMITE: PN_HERMITE}
 
 
 class PNError(RuntimeError):
@@ -88,6 +89,7 @@ def _load():
                 "pn_set_params": [P, ctypes.POINTER(_Params)],
                 "pn_set_stream": [P, P],
                 "pn_accel": [P, P, P, P, P],
+                "pn_jerk": [P, P, P, P, P, P],
                 "pn_step": [P, P, P, P, P, D, I64],
                 "pn_step_host": [P, P, P, P, P, D, I64],
                 "pn_energy": [P, P, P, P, P],
@@ -135,7 +137,7 @@ def _params(G, c, eps, precision, vel_mode, r_near=R_NEAR_DEFAULT, pair_kernel="
     if pair_kernel not in _PAIR:
         raise ValueError(f"pair_kernel must be 'fused' or 'two_pass', got {pair_kernel!r}")
     if integrator not in _INTEGRATOR:
-        raise ValueError(f"integrator must be 'kdk' or 'rk4', got {integrator!r}")
+        raise ValueError(f"integrator must be 'kdk', 'rk4' or 'hermite', got {integrator!r}")
     return _Params(float(G), float(c), float(eps), _PRECISION[precision], _VEL_MODE[vel_mode],
                    float(r_near), _PAIR[pair_kernel], _INTEGRATOR[integrator])
 
@@ -259,6 +261,15 @@ def pn_accel(ctx: Context, x, v, m, a) -> None:
     n = ctx.n
     _check(_load().pn_accel(ctx.handle, _dev(ctx, x, (n, 3), "x"), _dev(ctx, v, (n, 3), "v"),
                             _dev(ctx, m, (n,), "m"), _dev(ctx, a, (n, 3), "a")))
+
+
+def pn_jerk(ctx: Context, x, v, m, a, jerk) -> None:
+    """a = A(x, v) and jerk = dA/dt along the trajectory (Appendix A), for
+    all bodies; the jerk is computed in double precision."""
+    n = ctx.n
+    _check(_load().pn_jerk(ctx.handle, _dev(ctx, x, (n, 3), "x"), _dev(ctx, v, (n, 3), "v"),
+                           _dev(ctx, m, (n,), "m"), _dev(ctx, a, (n, 3), "a"),
+                           _dev(ctx, jerk, (n, 3), "jerk")))
 
 
 def pn_step(ctx: Context, x, v, m, a, dt: float, nsteps: int = 1) -> None:
