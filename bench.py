@@ -45,6 +45,8 @@ METRIC = "1PN pair interactions/s at N=16k/128k, mixed vs FP64 on B300 at <=1e-5
 FLOPS_PASS1 = 29   # hand count of the mixed pass-1 pair body (FMA = 2, rsqrt = 1)
 FLOPS_PASS2 = 67   # hand count of the mixed pass-2 pair body
 FLOPS_FUSED = 77   # hand count of the fused pair body (pass 1 + pass 2 sharing x, r, rsqrt)
+FLOPS_JERK = 213   # hand count of the FP64 dual-number pair body of the jerk
+                   # (dual add 2, dual multiply 4, scalar x dual 2, rsqrt + its derivative 6)
 FP32_LANES_PER_SM = 128
 
 
@@ -64,6 +66,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=500)
+    ap.add_argument("--no-jerk", action="store_true")
     return ap.parse_args()
 
 
@@ -398,6 +401,12 @@ def run_native(args, w):
         except Exception as e:  # reported, not required
             line["batched"] = {"error": str(e)[:300]}
 
+    if not args.no_jerk and world == 1:
+        try:
+            line["jerk"] = run_jerk(local, stream, args.warmup)
+        except Exception as e:  # reported, not required
+            line["jerk"] = {"error": str(e)[:300]}
+
     if rank == 0 and not args.no_cpu_baseline:
         try:
             rows = max(64, min(w.n - 1, 16384))
@@ -460,6 +469,56 @@ def run_batched(local, stream, steps, warmup):
             "ms_per_step": ms_tot / steps, "graph": "all steps in one CUDA graph launch",
             "graph_capture_and_first_run_s": capture_s, "autotuned": tuned,
             "gpu_launches": launches}
+
+
+def run_jerk(local, stream, warmup, reps=5):
+    """The jerk (Appendix A) and the Hermite integrator on the 16k Plummer
+    workload: pn_jerk (A in mixed precision, then the FP64 dual-number jerk
+    pass) timed with CUDA events, and a Hermite step (two A + two jerk
+    evaluations)."""
+    import torch
+    from paper_1801_07986_b300 import pn
+    from paper_1801_07986_b300.inputs import WORKLOADS
+    w = WORKLOADS["plummer16k"]
+    x, v, m = w.state()
+    dev = torch.device(f"cuda:{local}")
+    X, V, M = (torch.tensor(a, device=dev) for a in (x, v, m))
+    A, J = torch.empty_like(X), torch.empty_like(X)
+    ctx = pn.pn_init(w.n, G=w.G, c=w.c, eps=w.eps, precision="mixed", integrator="hermite",
+                     device=local, stream=stream)
+    for _ in range(max(1, warmup)):
+        pn.pn_jerk(ctx, X, V, M, A, J)
+    pn.pn_sync(ctx)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        pn.pn_jerk(ctx, X, V, M, A, J)
+    e1.record(stream)
+    e1.synchronize()
+    ms_jerk = e0.elapsed_time(e1) / reps
+    pn.pn_step(ctx, X, V, M, A, w.dt, 1)
+    pn.pn_sync(ctx)
+    e0.record(stream)
+    pn.pn_step(ctx, X, V, M, A, w.dt, 2)
+    e1.record(stream)
+    e1.synchronize()
+    pn.pn_sync(ctx)
+    ms_step = e0.elapsed_time(e1) / 2
+    ctx.close()
+    pairs = float(w.n - 1) * (w.n - 2)
+    peaks = pn.pn_measure_peaks(local, stream)
+    achieved = FLOPS_JERK * pairs / (ms_jerk * 1e-3) / 1e12
+    return {"workload": "plummer16k", "n_bodies": w.n,
+            "value": float(w.n) * (w.n - 1) / (ms_jerk * 1e-3), "unit": "interactions/s",
+            "what": "pn_jerk: A (mixed) + jerk (FP64 dual numbers), per evaluation",
+            "ms_per_jerk": ms_jerk, "hermite_ms_per_step": ms_step,
+            "roofline": {"bound": "alu", "achieved": achieved,
+                         "peak": peaks["fp64_fma_tflops"], "unit": "TFLOP/s",
+                         "frac": achieved / peaks["fp64_fma_tflops"],
+                         "peak_basis": "FP64 FMA-chain microbenchmark (pn_measure_peaks)",
+                         "flops_per_pair": FLOPS_JERK,
+                         "note": "whole pn_jerk call timed (dual pair kernel dominates)"}}
 
 
 def main():
