@@ -83,6 +83,8 @@ def _load():
             lib.orc_rk4_step.argtypes = [i64, p, p, p, p, d, d, d, d, i64]
             lib.orc_jerk.argtypes = [i64, p, p, p, d, d, d, p, p]
             lib.orc_hermite_step.argtypes = [i64, p, p, p, p, d, d, d, d, i64]
+            lib.orc_traj_jvp.argtypes = [i64, p, p, p, d, d, d, d, i64, ctypes.c_int, p, p, d, d,
+                                         p, p, p, p]
             lib.orc_set_threads.argtypes = [ctypes.c_int]
             lib.orc_get_threads.restype = ctypes.c_int
             for f in ("orc_accel", "orc_accel_rows", "orc_bh_rows", "orc_newton_accel",
@@ -229,6 +231,23 @@ def hermite_step(x, v, m, a, dt, nsteps, G=1.0, c=np.inf, eps=0.0):
     if rc:
         raise ValueError(f"orc_hermite_step failed ({rc})")
     return x, v, a
+
+
+def traj_jvp(x0, v0, m, dt, nsteps, dx0, dv0, dM=0.0, dinv_c2=0.0, G=1.0, c=np.inf, eps=0.0,
+             vel_mode=0):
+    """Final state of nsteps KDK steps from (x0, v0) (entry acceleration
+    A(x0, v0)) and its derivative along the perturbation (dx0, dv0, dM of the
+    hole mass m[0], dinv_c2 of 1/c^2), by a complex step; returns
+    (x, v, dx, dv)."""
+    x0, v0, m, n = _state(x0, v0, m)
+    dx0, dv0 = _f64(dx0, (n, 3)), _f64(dv0, (n, 3))
+    x, v, dx, dv = (np.zeros((n, 3)) for _ in range(4))
+    rc = _load().orc_traj_jvp(n, _ptr(x0), _ptr(v0), _ptr(m), G, _inv_c2(c), eps, dt,
+                              int(nsteps), int(vel_mode), _ptr(dx0), _ptr(dv0), float(dM),
+                              float(dinv_c2), _ptr(x), _ptr(v), _ptr(dx), _ptr(dv))
+    if rc:
+        raise ValueError(f"orc_traj_jvp failed ({rc})")
+    return x, v, dx, dv
 
 
 def eih_accel(x, v, m, G=1.0, c=np.inf):

@@ -647,6 +647,82 @@ int orc_rk4_step(int64_t n, double *x, double *v, const double *m, double *a,
 }
 
 /*
+ * Forward-mode derivative of a kick-drift-kick trajectory (reading R9,
+ * vel_mode 0 or 1) by a complex step: the state, the hole mass m[0] and
+ * inv_c2 are perturbed by i h (dx0, dv0, dM, dinv_c2) with h = 1e-20, the
+ * entry acceleration is A(x0, v0) of the perturbed state, and the nsteps
+ * steps run in complex arithmetic.  x, v receive the final state, dx, dv its
+ * derivative along the perturbation.  The adjoint's checks contract this
+ * with a cotangent, one direction at a time.
+ */
+int orc_traj_jvp(int64_t n, const double *x0, const double *v0, const double *m,
+                 double G, double inv_c2, double eps, double dt, int64_t nsteps,
+                 int vel_mode, const double *dx0, const double *dv0, double dM,
+                 double dinv_c2, double *x, double *v, double *dx, double *dv)
+{
+    if (check_args(n, x0, v0, m) || !dx0 || !dv0 || !x || !v || !dx || !dv || nsteps < 0 ||
+        !(dt > 0.0) || (vel_mode != 0 && vel_mode != 1))
+        return 1;
+    const double h = 1e-20;
+    const size_t n3 = 3 * (size_t)n;
+    double complex *xc = (double complex *)malloc(sizeof(double complex) * n3);
+    double complex *vc = (double complex *)malloc(sizeof(double complex) * n3);
+    double complex *vh = (double complex *)malloc(sizeof(double complex) * n3);
+    double complex *vp = (double complex *)malloc(sizeof(double complex) * n3);
+    double complex *ac = (double complex *)malloc(sizeof(double complex) * n3);
+    double complex *mc = (double complex *)malloc(sizeof(double complex) * (size_t)n);
+    double complex *rows = (double complex *)calloc(n3, sizeof(double complex));
+    int rc = 0;
+    if (!xc || !vc || !vh || !vp || !ac || !mc || !rows)
+        rc = 2;
+    const double complex ic2 = inv_c2 + I * (h * dinv_c2);
+    if (rc == 0) {
+        for (size_t q = 0; q < n3; ++q) {
+            xc[q] = x0[q] + I * (h * dx0[q]);
+            vc[q] = v0[q] + I * (h * dv0[q]);
+        }
+        for (int64_t q = 0; q < n; ++q)
+            mc[q] = m[q];
+        mc[0] = m[0] + I * (h * dM);
+    }
+    const int nt = orc_get_threads();
+    /* entry acceleration, then the steps */
+    for (int64_t s = -1; s < nsteps && rc == 0; ++s) {
+        const double complex *xe = xc, *ve = vc;
+        if (s >= 0) {
+            for (size_t q = 0; q < n3; ++q) {
+                vh[q] = vc[q] + 0.5 * dt * ac[q];
+                xc[q] = xc[q] + dt * vh[q];
+                vp[q] = vel_mode == 0 ? vh[q] + 0.5 * dt * ac[q] : vh[q];
+            }
+            ve = vp;
+        }
+        bh_accel_cs(n, xe, ve, mc, G, ic2, eps, rows, ac);
+#pragma omp parallel for schedule(dynamic, 8) num_threads(nt)
+        for (int64_t i = 1; i < n; ++i)
+            star_accel_cs(n, xe, ve, mc, G, ic2, eps, i, ac + 3 * i);
+        if (s >= 0)
+            for (size_t q = 0; q < n3; ++q)
+                vc[q] = vh[q] + 0.5 * dt * ac[q];
+    }
+    if (rc == 0)
+        for (size_t q = 0; q < n3; ++q) {
+            x[q] = creal(xc[q]);
+            v[q] = creal(vc[q]);
+            dx[q] = cimag(xc[q]) / h;
+            dv[q] = cimag(vc[q]) / h;
+        }
+    free(xc);
+    free(vc);
+    free(vh);
+    free(vp);
+    free(ac);
+    free(mc);
+    free(rows);
+    return rc;
+}
+
+/*
  * nsteps of the fourth-order Hermite scheme (the integrator the paper
  * recommends for collisional runs, Section 5, with the jerk of Appendix A),
  * for x' = v, v' = A(x, v), in the predict-(evaluate-correct)^2 form:

@@ -52,6 +52,10 @@ MUTANTS = [
      "vc[q] = v[q] + I * (h * a[q]);", "vc[q] = v[q];"),
     ("Hermite corrector: dt^2/12 -> dt^2/10 in the velocity",
      "dt2 / 12.0 * (j0[q] - j1[q]);", "dt2 / 10.0 * (j0[q] - j1[q]);"),
+    ("trajectory derivative: KDK velocity prediction dropped",
+     "vp[q] = vel_mode == 0 ? vh[q] + 0.5 * dt * ac[q] : vh[q];", "vp[q] = vh[q];"),
+    ("trajectory derivative: hole-mass perturbation dropped",
+     "mc[0] = m[0] + I * (h * dM);", "mc[0] = m[0];"),
     ("Hermite: a single evaluate-correct pass",
      "for (int pass = 0; pass < 2 && rc == 0; ++pass)", "for (int pass = 0; pass < 1 && rc == 0; ++pass)"),
 ]

@@ -450,6 +450,41 @@ def test_hermite_is_fourth_order_and_matches_rk4(orc, c):
     assert np.linalg.norm(xs[2] - xr) < 0.2 * np.linalg.norm(xs[1] - xs[2])
 
 
+# ------------------------------------------------------------ adjoint --
+
+def test_trajectory_derivative_matches_central_differences(orc):
+    """The oracle's exact trajectory derivative (complex step through the KDK
+    steps) against a Richardson central difference of the double-precision
+    stepper, along a direction that moves positions, velocities, the hole
+    mass and 1/c^2 at once."""
+    x, v, m = _random_state(12, 41, m_bh=0.3, m_star=1e-2)
+    c, eps, dt, nst = 10.0, 1e-2, 1.0 / 256, 20
+    rng = np.random.default_rng(3)
+    dx, dv = rng.normal(size=x.shape), rng.normal(size=v.shape)
+    dM, dic2 = 0.7, -2e-3
+    xt, vt, jx, jv = orc.traj_jvp(x, v, m, dt, nst, dx, dv, dM, dic2, c=c, eps=eps)
+    x_ref, v_ref, _ = orc.step(x, v, m, orc.accel(x, v, m, c=c, eps=eps), dt, nst, c=c, eps=eps)
+    assert np.abs(xt - x_ref).max() < 1e-13 and np.abs(vt - v_ref).max() < 1e-12
+
+    def run(h):
+        mm = m.copy()
+        mm[0] += h * dM
+        ic2 = 1.0 / c ** 2 + h * dic2
+        cc = 1.0 / math.sqrt(ic2)
+        xx, vv = x + h * dx, v + h * dv
+        a = orc.accel(xx, vv, mm, c=cc, eps=eps)
+        return orc.step(xx, vv, mm, a, dt, nst, c=cc, eps=eps)[:2]
+
+    def cd(h):
+        (xp, vp), (xm, vm) = run(h), run(-h)
+        return (xp - xm) / (2 * h), (vp - vm) / (2 * h)
+
+    (fx1, fv1), (fx2, fv2) = cd(2e-5), cd(1e-5)
+    fx, fv = (4 * fx2 - fx1) / 3, (4 * fv2 - fv1) / 3
+    assert np.abs(jx - fx).max() < 1e-7 * np.abs(fx).max()
+    assert np.abs(jv - fv).max() < 1e-7 * np.abs(fv).max()
+
+
 # ------------------------------------------------------------ invariances --
 
 def test_rotation_and_translation_invariance(orc):
