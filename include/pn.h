@@ -192,6 +192,40 @@ pn_status pn_jerk(pn_ctx *ctx, const double *x, const double *v, const double *m
                   double *jerk);
 
 /*
+ * Adjoint (vector-Jacobian product) of the accelerations: for the state
+ * (x, v), with v the velocities at which A is taken, and a cotangent abar
+ * (n x 3) of A(x, v), writes xbar = abar . dA/dx and vbar = abar . dA/dv
+ * (n x 3 each, device) and, on the host, scal[2 k] = abar . dA/dM_k and
+ * scal[2 k + 1] = abar . dA/d(1/c_k^2) for the hole mass M_k and c_k of
+ * cluster k (dA/dc = -2/c^3 dA/d(1/c^2)).  Reverse mode over the same
+ * decomposition as the kernels, in double precision, without the
+ * near-source split.  The paper has no counterpart: it is the gradient of
+ * its Eq. 1-6.  Allocates its scratch on the first call; waits.  Errors:
+ * PN_EINVAL (NULL pointer, aliasing), PN_ENOMEM, PN_ECUDA.
+ */
+pn_status pn_accel_vjp(pn_ctx *ctx, const double *x, const double *v, const double *m,
+                       const double *abar, double *xbar, double *vbar, double *scal);
+
+/*
+ * Adjoint of nsteps PN_KDK steps (pn_step) from (x0, v0), whose entry
+ * acceleration is A(x0, v0): given cotangents xbar_T, vbar_T of the final
+ * positions and velocities, writes xbar0, vbar0 (the gradient with respect
+ * to x0, v0, device, n x 3) and on the host scal[2 k], scal[2 k + 1], the
+ * gradient with respect to the hole mass and 1/c^2 of cluster k.  The
+ * forward trajectory runs in the context's precision; each step's
+ * acceleration is differentiated in double precision (pn_accel_vjp).
+ * Checkpointing: the state is stored every `checkpoint` steps (0: the
+ * integer ceiling of sqrt(nsteps)) and each segment is recomputed once on
+ * the way back, so memory is (checkpoint + nsteps/checkpoint) x 9n doubles
+ * and the forward steps run twice.  Allocates and frees its scratch; waits.
+ * Errors: PN_EINVAL, PN_EUNSUPPORTED (integrator other than PN_KDK),
+ * PN_ENOMEM, PN_ECUDA, PN_ENONFINITE.
+ */
+pn_status pn_step_vjp(pn_ctx *ctx, const double *x0, const double *v0, const double *m,
+                      double dt, int64_t nsteps, int64_t checkpoint, const double *xbar_T,
+                      const double *vbar_T, double *xbar0, double *vbar0, double *scal);
+
+/*
  * pn_step captured into one CUDA graph and launched as a whole: the first
  * call for a given (x, v, m, a, dt, nsteps) records the nsteps steps (every
  * kernel launch of every step) into a graph; later calls with the same

@@ -82,6 +82,7 @@ def _load():
             lib.orc_eih_step.argtypes = [i64, p, p, p, p, d, d, d, i64, ctypes.c_int]
             lib.orc_rk4_step.argtypes = [i64, p, p, p, p, d, d, d, d, i64]
             lib.orc_jerk.argtypes = [i64, p, p, p, d, d, d, p, p]
+            lib.orc_accel_jvp.argtypes = [i64, p, p, p, d, d, d, p, p, d, d, p]
             lib.orc_hermite_step.argtypes = [i64, p, p, p, p, d, d, d, d, i64]
             lib.orc_traj_jvp.argtypes = [i64, p, p, p, d, d, d, d, i64, ctypes.c_int, p, p, d, d,
                                          p, p, p, p]
@@ -217,6 +218,19 @@ def jerk(x, v, m, a=None, G=1.0, c=np.inf, eps=0.0):
     rc = _load().orc_jerk(n, _ptr(x), _ptr(v), _ptr(m), G, _inv_c2(c), eps, _ptr(a), _ptr(out))
     if rc:
         raise ValueError(f"orc_jerk failed ({rc})")
+    return out
+
+
+def accel_jvp(x, v, m, dx, dv, dM=0.0, dinv_c2=0.0, G=1.0, c=np.inf, eps=0.0):
+    """Directional derivative of A(x, v; M = m[0], 1/c^2) along
+    (dx, dv, dM, dinv_c2), by a complex step of the oracle's Eq. 1-6."""
+    x, v, m, n = _state(x, v, m)
+    dx, dv = _f64(dx, (n, 3)), _f64(dv, (n, 3))
+    out = np.zeros((n, 3))
+    rc = _load().orc_accel_jvp(n, _ptr(x), _ptr(v), _ptr(m), G, _inv_c2(c), eps, _ptr(dx),
+                               _ptr(dv), float(dM), float(dinv_c2), _ptr(out))
+    if rc:
+        raise ValueError(f"orc_accel_jvp failed ({rc})")
     return out
 
 

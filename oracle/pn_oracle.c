@@ -139,17 +139,16 @@ int orc_accel(int64_t n, const double *x, const double *v, const double *m,
 }
 
 /*
- * Jerk: the time derivative of the accelerations of Eq. 1-6 along the
- * trajectory (Appendix A), j = sum_k [dA/dx_k . v_k + dA/dv_k . a_k] with
- * a = A(x, v) given.  Appendix A prints the expanded derivative, garbled in
- * places; here the derivative is taken of the same equations the oracle
- * evaluates, by a complex step: Im A(x + i h v, v + i h a) / h with
+ * Directional derivative of the accelerations of Eq. 1-6 along
+ * (dx, dv, dM of the hole mass m[0], dinv_c2 of 1/c^2), by a complex step:
+ * Im A(x + i h dx, v + i h dv; M + i h dM, inv_c2 + i h dinv_c2) / h with
  * h = 1e-20 (relative error O(h^2), no cancellation).
  */
-int orc_jerk(int64_t n, const double *x, const double *v, const double *m,
-             double G, double inv_c2, double eps, const double *a, double *jerk)
+int orc_accel_jvp(int64_t n, const double *x, const double *v, const double *m,
+                  double G, double inv_c2, double eps, const double *dx, const double *dv,
+                  double dM, double dinv_c2, double *out)
 {
-    if (check_args(n, x, v, m) || !a || !jerk)
+    if (check_args(n, x, v, m) || !dx || !dv || !out)
         return 1;
     const double h = 1e-20;
     const size_t n3 = 3 * (size_t)n;
@@ -163,18 +162,20 @@ int orc_jerk(int64_t n, const double *x, const double *v, const double *m,
         rc = 2;
     } else {
         for (size_t q = 0; q < n3; ++q) {
-            xc[q] = x[q] + I * (h * v[q]);
-            vc[q] = v[q] + I * (h * a[q]);
+            xc[q] = x[q] + I * (h * dx[q]);
+            vc[q] = v[q] + I * (h * dv[q]);
         }
         for (int64_t q = 0; q < n; ++q)
             mc[q] = m[q];
-        bh_accel_cs(n, xc, vc, mc, G, inv_c2, eps, rows, ac);
+        mc[0] = m[0] + I * (h * dM);
+        const double complex ic2 = inv_c2 + I * (h * dinv_c2);
+        bh_accel_cs(n, xc, vc, mc, G, ic2, eps, rows, ac);
         int nt = orc_get_threads();
 #pragma omp parallel for schedule(dynamic, 8) num_threads(nt)
         for (int64_t i = 1; i < n; ++i)
-            star_accel_cs(n, xc, vc, mc, G, inv_c2, eps, i, ac + 3 * i);
+            star_accel_cs(n, xc, vc, mc, G, ic2, eps, i, ac + 3 * i);
         for (size_t q = 0; q < n3; ++q)
-            jerk[q] = cimag(ac[q]) / h;
+            out[q] = cimag(ac[q]) / h;
     }
     free(xc);
     free(vc);
@@ -182,6 +183,21 @@ int orc_jerk(int64_t n, const double *x, const double *v, const double *m,
     free(ac);
     free(rows);
     return rc;
+}
+
+/*
+ * Jerk: the time derivative of the accelerations of Eq. 1-6 along the
+ * trajectory (Appendix A), j = sum_k [dA/dx_k . v_k + dA/dv_k . a_k] with
+ * a = A(x, v) given: the directional derivative along (v, a).  Appendix A
+ * prints the expanded derivative, garbled in places; here the derivative is
+ * taken of the same equations the oracle evaluates.
+ */
+int orc_jerk(int64_t n, const double *x, const double *v, const double *m,
+             double G, double inv_c2, double eps, const double *a, double *jerk)
+{
+    if (check_args(n, x, v, m) || !a || !jerk)
+        return 1;
+    return orc_accel_jvp(n, x, v, m, G, inv_c2, eps, v, a, 0.0, 0.0, jerk);
 }
 
 /* Accelerations of the listed targets only (index 0 = heavy body). */

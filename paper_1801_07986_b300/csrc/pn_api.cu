@@ -119,7 +119,7 @@ void free_all(pn_ctx *c)
 {
     void *bufs[] = {c->vp, c->mrec, c->drec, c->part, c->blk, c->glob, c->eout, c->flag, c->wcount,
                     c->flag_step, c->hx, c->hv, c->hm, c->ha, c->nrec, c->ndrec, c->ncount,
-                    c->nflag, c->rk_x, c->rk_v, c->rk_a, c->rk_sx, c->rk_sv, c->jbuf, c->hj0, c->hj1,
+                    c->nflag, c->rk_x, c->rk_v, c->rk_a, c->rk_sx, c->rk_sv, c->jbuf, c->hj0, c->hj1, c->abuf,
                     c->d_clu,
                     c->blk_clu};
     for (void *b : bufs)
@@ -226,6 +226,21 @@ pn_status ensure_jerk_buffers(pn_ctx *c)
                 }
             return fail(PN_ENOMEM, "cudaMalloc of %zu bytes for the jerk failed", bytes[k]);
         }
+    }
+    return PN_OK;
+}
+
+// Adjoint scratch (and the jerk's, whose records and sums it reuses).
+pn_status ensure_adjoint_buffers(pn_ctx *c)
+{
+    pn_status st = ensure_jerk_buffers(c);
+    if (st != PN_OK || c->abuf)
+        return st;
+    const size_t bytes = sizeof(double) * pn::adjoint_buffer_doubles(c);
+    if (std::getenv("PN_FAIL_ALLOC") || cudaMalloc((void **)&c->abuf, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        c->abuf = nullptr;
+        return fail(PN_ENOMEM, "cudaMalloc of %zu bytes for the adjoint failed", bytes);
     }
     return PN_OK;
 }
@@ -604,6 +619,148 @@ pn_status pn_jerk(pn_ctx *c, const double *x, const double *v, const double *m, 
         return st;
     PN_CUDA(pn::launch_jerk(c, x, v, m, a, jerk), "jerk launch");
     return ok();
+}
+
+pn_status pn_accel_vjp(pn_ctx *c, const double *x, const double *v, const double *m,
+                       const double *abar, double *xbar, double *vbar, double *scal)
+{
+    if (check_ctx(c) != PN_OK)
+        return PN_EINVAL;
+    if (!x || !v || !m || !abar || !xbar || !vbar || !scal)
+        return fail(PN_EINVAL, "pn_accel_vjp: NULL array");
+    const void *in[] = {x, v, m, abar};
+    for (const void *q : in)
+        if (q == xbar || q == vbar)
+            return fail(PN_EINVAL, "pn_accel_vjp: an output aliases an input");
+    if (xbar == vbar)
+        return fail(PN_EINVAL, "pn_accel_vjp: xbar and vbar alias");
+    DeviceGuard g(c->device);
+    PN_CUDA(g.err, "cudaSetDevice");
+    pn_status st = ensure_adjoint_buffers(c);
+    if (st != PN_OK)
+        return st;
+    double *dscal = nullptr;
+    PN_CUDA(cudaMalloc((void **)&dscal, sizeof(double) * 2 * c->nclu), "cudaMalloc");
+    cudaError_t e = pn::launch_accel_vjp(c, x, v, m, abar, xbar, vbar, dscal, false);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(scal, dscal, sizeof(double) * 2 * c->nclu, cudaMemcpyDeviceToHost,
+                            c->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(c->stream);
+    cudaFree(dscal);
+    PN_CUDA(e, "accel vjp");
+    return ok();
+}
+
+// Reverse of nsteps KDK steps from (x0, v0), checkpointed: the forward pass
+// stores (x, v, a) every K steps; the backward pass re-runs each segment
+// from its checkpoint, keeping the K pre-step states, and walks it in
+// reverse.  Memory (K + steps/K) 9n doubles.
+pn_status pn_step_vjp(pn_ctx *c, const double *x0, const double *v0, const double *m,
+                      double dt, int64_t nsteps, int64_t checkpoint, const double *xbar_T,
+                      const double *vbar_T, double *xbar0, double *vbar0, double *scal)
+{
+    if (check_ctx(c) != PN_OK)
+        return PN_EINVAL;
+    if (!x0 || !v0 || !m || !xbar_T || !vbar_T || !xbar0 || !vbar0 || !scal)
+        return fail(PN_EINVAL, "pn_step_vjp: NULL array");
+    if (!(std::isfinite(dt) && dt > 0.0))
+        return fail(PN_EINVAL, "pn_step_vjp: dt must be finite and > 0 (got %g)", dt);
+    if (nsteps < 0 || checkpoint < 0)
+        return fail(PN_EINVAL, "pn_step_vjp: nsteps and checkpoint must be >= 0");
+    if (c->p.integrator != PN_KDK)
+        return fail(PN_EUNSUPPORTED, "pn_step_vjp: only the PN_KDK integrator has an adjoint");
+    DeviceGuard g(c->device);
+    PN_CUDA(g.err, "cudaSetDevice");
+    pn_status st = ensure_adjoint_buffers(c);
+    if (st != PN_OK)
+        return st;
+    int64_t K = checkpoint;
+    if (K == 0) {
+        K = 1;
+        while (K * K < nsteps)
+            ++K;
+    }
+    const int64_t ncp = nsteps > 0 ? (nsteps + K - 1) / K : 0;
+    const size_t n3 = 3 * (size_t)c->n, b3 = sizeof(double) * n3;
+    // work: xs vs as | xp vp atot xbA vpbA | xb vb ab | checkpoints | segment
+    const size_t nwork = 11 * n3 + (size_t)(ncp + (nsteps > 0 ? K : 0)) * 3 * n3;
+    double *w = nullptr, *dscal = nullptr;
+    if (std::getenv("PN_FAIL_ALLOC") || cudaMalloc((void **)&w, sizeof(double) * nwork) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PN_ENOMEM, "cudaMalloc of %zu bytes for the adjoint failed",
+                    sizeof(double) * nwork);
+    }
+    if (cudaMalloc((void **)&dscal, sizeof(double) * 2 * c->nclu) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(w);
+        return fail(PN_ENOMEM, "cudaMalloc for the adjoint failed");
+    }
+    double *xs = w, *vs = xs + n3, *as = vs + n3, *xp = as + n3, *vp = xp + n3, *atot = vp + n3;
+    double *xbA = atot + n3, *vpbA = xbA + n3, *xb = vpbA + n3, *vb = xb + n3, *ab = vb + n3;
+    double *cp = ab + n3, *seg = cp + (size_t)ncp * 3 * n3;
+    auto run = [&]() -> pn_status {
+        PN_CUDA(cudaMemcpyAsync(xs, x0, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+        PN_CUDA(cudaMemcpyAsync(vs, v0, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+        pn_status s2 = evaluate(c, xs, vs, m, as, nullptr, 0.0);
+        if (s2 != PN_OK)
+            return s2;
+        for (int64_t s = 0; s < nsteps; ++s) {
+            if (s % K == 0) {
+                double *q = cp + (size_t)(s / K) * 3 * n3;
+                PN_CUDA(cudaMemcpyAsync(q, xs, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+                PN_CUDA(cudaMemcpyAsync(q + n3, vs, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+                PN_CUDA(cudaMemcpyAsync(q + 2 * n3, as, b3, cudaMemcpyDeviceToDevice, c->stream),
+                        "copy");
+            }
+            if ((s2 = run_steps(c, xs, vs, m, as, dt, 1)) != PN_OK)
+                return s2;
+        }
+        PN_CUDA(cudaMemcpyAsync(xb, xbar_T, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+        PN_CUDA(cudaMemcpyAsync(vb, vbar_T, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+        PN_CUDA(cudaMemsetAsync(ab, 0, b3, c->stream), "memset");
+        PN_CUDA(cudaMemsetAsync(dscal, 0, sizeof(double) * 2 * c->nclu, c->stream), "memset");
+        for (int64_t sg = ncp - 1; sg >= 0; --sg) {
+            const int64_t s0 = sg * K, s1 = s0 + K < nsteps ? s0 + K : nsteps;
+            const double *q = cp + (size_t)sg * 3 * n3;
+            PN_CUDA(cudaMemcpyAsync(xs, q, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+            PN_CUDA(cudaMemcpyAsync(vs, q + n3, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+            PN_CUDA(cudaMemcpyAsync(as, q + 2 * n3, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+            for (int64_t s = s0; s < s1; ++s) {
+                double *r = seg + (size_t)(s - s0) * 3 * n3;
+                PN_CUDA(cudaMemcpyAsync(r, xs, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+                PN_CUDA(cudaMemcpyAsync(r + n3, vs, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+                PN_CUDA(cudaMemcpyAsync(r + 2 * n3, as, b3, cudaMemcpyDeviceToDevice, c->stream),
+                        "copy");
+                if (s + 1 < s1 && (s2 = run_steps(c, xs, vs, m, as, dt, 1)) != PN_OK)
+                    return s2;
+            }
+            for (int64_t s = s1 - 1; s >= s0; --s) {
+                const double *r = seg + (size_t)(s - s0) * 3 * n3;
+                PN_CUDA(pn::launch_adj_kdk(c, 0, dt, r, r + n3, r + 2 * n3, xp, vp, xb, vb, ab,
+                                           atot, nullptr, nullptr), "adjoint step launch");
+                PN_CUDA(pn::launch_accel_vjp(c, xp, vp, m, atot, xbA, vpbA, dscal, true),
+                        "accel vjp launch");
+                PN_CUDA(pn::launch_adj_kdk(c, 1, dt, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                           xb, vb, ab, nullptr, xbA, vpbA), "adjoint step launch");
+            }
+        }
+        // the entry acceleration A(x0, v0)
+        PN_CUDA(pn::launch_accel_vjp(c, x0, v0, m, ab, xbA, vpbA, dscal, true), "accel vjp launch");
+        PN_CUDA(pn::launch_adj_kdk(c, 2, dt, nullptr, nullptr, nullptr, nullptr, nullptr, xb, vb,
+                                   ab, nullptr, xbA, vpbA), "adjoint step launch");
+        PN_CUDA(cudaMemcpyAsync(xbar0, xb, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+        PN_CUDA(cudaMemcpyAsync(vbar0, vb, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+        PN_CUDA(cudaMemcpyAsync(scal, dscal, sizeof(double) * 2 * c->nclu,
+                                cudaMemcpyDeviceToHost, c->stream), "copy");
+        PN_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
+        return PN_OK;
+    };
+    st = run();
+    cudaStreamSynchronize(c->stream);
+    cudaFree(w);
+    cudaFree(dscal);
+    return st == PN_OK ? ok() : st;
 }
 
 pn_status pn_step(pn_ctx *c, double *x, double *v, const double *m, double *a, double dt,

@@ -1,0 +1,915 @@
+// pn_deriv.cu -- derivatives of the accelerations of Eq. 1-6 (Tatekawa,
+// arXiv:1801.07986): the jerk of Appendix A (forward mode), the
+// fourth-order Hermite steps that use it (Section 5), and the adjoint
+// (vector-Jacobian product) of A and of kick-drift-kick steps (reverse
+// mode), all in double precision.
+//
+// The jerk is the time derivative along the trajectory,
+//   j = sum_k [dA/dx_k . v_k + dA/dv_k . a_k],   a = A(x, v).
+// Appendix A prints the expanded derivative (garbled in places).  Here the
+// derivative is taken of the same decomposition the acceleration kernels
+// evaluate, in forward mode: every quantity is a dual number (value,
+// derivative along x' = v, v' = a), in double precision, through the
+// records, the cluster sums, the pair sums (one pass with all 16 sums) and
+// the per-star assembly (star_eqs).  Stars near the hole are not split off
+// (that split only changes single-precision rounding).
+#include <math.h>
+#include <stdint.h>
+
+#include "pn_device.cuh"
+
+namespace pn {
+
+namespace {
+
+constexpr int kJRec = 8;         // double4 records per star slot
+constexpr int kJVals = 12;       // Dual cluster sums: Q (3), W (3), W_far (3), SA, SB, Phi
+constexpr int kJTile = 32;       // sources per shared-memory tile
+constexpr int kJThreads = 128;
+
+__device__ __forceinline__ Dual dual(double v, double d) { return {v, d}; }
+
+// Records per star slot t (zero-mass far-away padding past the stars):
+//   J0 = (d, m)  J1 = (d', 0)  J2 = (v, R^2)  J3 = (v', (R^2)')
+//   J4 = (-e/1.5, C)  J5 = (-(e/1.5)', C')  J6 = (w, 0)  J7 = (w', 0)
+// (primes: derivatives along the trajectory; C = c/1.5 - 4/3 |v|^2, c, e, w
+// as in the acceleration kernels).  Per-block Dual sums of the cluster sums.
+__global__ void __launch_bounds__(kGlueThreads)
+k_jerk_prologue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_clu,
+                const double *__restrict__ x, const double *__restrict__ v,
+                const double *__restrict__ m, const double *__restrict__ a,
+                double4_32a *__restrict__ rec, double *__restrict__ blk)
+// a == nullptr: values only (all derivatives zero), for the adjoint
+{
+    __shared__ double sh[2 * kJVals][kGlueThreads];
+    const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
+    const Clu C = clu[cluster_of_block(blk_clu, blockIdx.x)];
+    const int64_t lt = t - C.slot0;
+    double g[2 * kJVals];
+#pragma unroll
+    for (int k = 0; k < 2 * kJVals; ++k)
+        g[k] = 0.0;
+    if (lt < C.ns) {
+        const int64_t j = C.body0 + 1 + lt, h = C.body0;
+        const double GM = C.G * m[h], mj = m[j];
+        Dual d[3], vel[3];
+        for (int k = 0; k < 3; ++k) {
+            d[k] = dual(x[3 * j + k] - x[3 * h + k], a ? v[3 * j + k] - v[3 * h + k] : 0.0);
+            vel[k] = dual(v[3 * j + k], a ? a[3 * j + k] : 0.0);
+        }
+        const Dual R2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        const Dual iR = 1.0 / tsqrt(R2);
+        const Dual iR3 = iR * iR * iR;
+        const Dual c = GM * (1.5 * iR + 0.25 * C.eps2 * iR3);
+        const Dual Cc = c / 1.5 - (4.0 / 3.0) * (vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]);
+        const Dual ne = -(0.5 * GM / 1.5) * iR3;     // -e/1.5 = ne d
+        Dual e3[3], w[3];
+        for (int k = 0; k < 3; ++k) {
+            e3[k] = ne * d[k];
+            w[k] = mj * iR3 * d[k];
+        }
+        rec[t] = make_double4_32a(d[0].v, d[1].v, d[2].v, mj);
+        rec[S + t] = make_double4_32a(d[0].d, d[1].d, d[2].d, 0.0);
+        rec[2 * S + t] = make_double4_32a(vel[0].v, vel[1].v, vel[2].v, R2.v);
+        rec[3 * S + t] = make_double4_32a(vel[0].d, vel[1].d, vel[2].d, R2.d);
+        rec[4 * S + t] = make_double4_32a(e3[0].v, e3[1].v, e3[2].v, Cc.v);
+        rec[5 * S + t] = make_double4_32a(e3[0].d, e3[1].d, e3[2].d, Cc.d);
+        rec[6 * S + t] = make_double4_32a(w[0].v, w[1].v, w[2].v, 0.0);
+        rec[7 * S + t] = make_double4_32a(w[0].d, w[1].d, w[2].d, 0.0);
+        Dual q[kJVals];
+        for (int k = 0; k < 3; ++k) {
+            q[k] = mj * vel[k];
+            q[3 + k] = w[k];
+            q[6 + k] = w[k];
+        }
+        q[9] = 1.25 * mj * iR;
+        q[10] = 0.25 * mj * (R2 + C.eps2) * iR3;
+        q[11] = mj * iR;
+        for (int k = 0; k < kJVals; ++k) {
+            g[2 * k] = q[k].v;
+            g[2 * k + 1] = q[k].d;
+        }
+    } else {
+        const double px = 1.0e4 + (double)(lt - C.ns);
+        rec[t] = make_double4_32a(px, 0.0, 0.0, 0.0);
+        for (int k = 1; k < kJRec; ++k)
+            rec[k * S + t] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    }
+    block_sum<2 * kJVals>(g, sh);
+    if (threadIdx.x < 2 * kJVals)
+        blk[(int64_t)blockIdx.x * 2 * kJVals + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// One block per cluster: its Dual cluster sums, blocks in a fixed order.
+__global__ void __launch_bounds__(kGlueThreads)
+k_jerk_globals(const Clu *__restrict__ clu, const double *__restrict__ blk,
+               double *__restrict__ glob)
+{
+    __shared__ double sh[2 * kJVals][kGlueThreads];
+    const Clu C = clu[blockIdx.x];
+    sum_blocks<2 * kJVals>(blk + (C.slot0 / kGlueThreads) * 2 * kJVals,
+                           C.ns_pad / kGlueThreads, sh);
+    if (threadIdx.x < 2 * kJVals)
+        glob[(int64_t)blockIdx.x * 2 * kJVals + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+template <class T>
+__device__ __forceinline__ T mk(double v, double d);
+template <>
+__device__ __forceinline__ double mk<double>(double v, double) { return v; }
+template <>
+__device__ __forceinline__ Dual mk<Dual>(double v, double d) { return {v, d}; }
+
+__device__ __forceinline__ double rsq(double s2) { return 1.0 / sqrt(s2); }
+__device__ __forceinline__ Dual rsq(Dual s2)
+{
+    const double y = 1.0 / sqrt(s2.v);
+    return {y, -0.5 * y * y * y * s2.d};
+}
+
+// Pair sums of passes 1 and 2 (the 16 sums of the fused kernels), in double
+// (T = double: the adjoint's forward sums) or on Duals (the jerk), one target
+// per thread; grid (target blocks, source splits), split s of a target block
+// in cluster k sweeping tiles [s tps, (s+1) tps).  Output
+// part[split][value][slot] (double) or part[split][2 value + {0 value,
+// 1 derivative}][slot] (Dual).
+template <class T>
+__global__ void __launch_bounds__(kJThreads)
+k_dual_pairs(const double4_32a *__restrict__ rec, int64_t S, const Clu *__restrict__ clu,
+             const int *__restrict__ blk_clu, double *__restrict__ part)
+{
+    constexpr bool kDual = sizeof(T) == sizeof(Dual);
+    __shared__ double4_32a sh[kJRec][kJTile];
+    const int64_t t0 = (int64_t)blockIdx.x * kJThreads;
+    const Clu C = clu[cluster_of_block(blk_clu, t0 / kGlueThreads)];
+    const int ntiles = (int)(C.ns_pad / kJTile);
+    const int tps = (ntiles + (int)gridDim.y - 1) / (int)gridDim.y;
+    const int64_t ti = t0 + threadIdx.x;
+    const double4_32a T0 = rec[ti], T1 = rec[S + ti], T2 = rec[2 * S + ti], T3 = rec[3 * S + ti];
+    const T di[3] = {mk<T>(T0.x, T1.x), mk<T>(T0.y, T1.y), mk<T>(T0.z, T1.z)};
+    const T vi[3] = {mk<T>(8.0 / 3.0 * T2.x, 8.0 / 3.0 * T3.x),
+                     mk<T>(8.0 / 3.0 * T2.y, 8.0 / 3.0 * T3.y),
+                     mk<T>(8.0 / 3.0 * T2.z, 8.0 / 3.0 * T3.z)};
+    T acc[kFusedVals];
+#pragma unroll
+    for (int k = 0; k < kFusedVals; ++k)
+        acc[k] = mk<T>(0.0, 0.0);
+    const double eps2 = C.eps2;
+    const int tb = blockIdx.y * tps;
+    const int te = min(ntiles, tb + tps);
+    for (int tile = tb; tile < te; ++tile) {
+        const int64_t j0 = C.slot0 + (int64_t)tile * kJTile;
+        __syncthreads();
+        for (int q = threadIdx.x; q < kJRec * kJTile; q += kJThreads)
+            sh[q / kJTile][q % kJTile] = rec[(q / kJTile) * S + j0 + q % kJTile];
+        __syncthreads();
+#pragma unroll 1
+        for (int q = 0; q < kJTile; ++q) {
+            if (j0 + q == ti)
+                continue;
+            const double4_32a A0 = sh[0][q], A1 = sh[1][q], A2 = sh[2][q], A3 = sh[3][q];
+            const double4_32a A4 = sh[4][q], A5 = sh[5][q], A6 = sh[6][q], A7 = sh[7][q];
+            const T xx[3] = {di[0] - mk<T>(A0.x, A1.x), di[1] - mk<T>(A0.y, A1.y),
+                             di[2] - mk<T>(A0.z, A1.z)};
+            const T vj[3] = {mk<T>(A2.x, A3.x), mk<T>(A2.y, A3.y), mk<T>(A2.z, A3.z)};
+            const T s2 = xx[0] * xx[0] + xx[1] * xx[1] + xx[2] * xx[2] + eps2;
+            const T is = rsq(s2);
+            const T is2 = is * is;
+            const T mis = A0.w * is;
+            const T mis3 = mis * is2;
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                acc[k] += mis3 * xx[k];
+            acc[3] += mis;
+            acc[4] += mis3;
+            acc[5] += mis3 * mk<T>(A2.w, A3.w);
+            const T xvj = xx[0] * vj[0] + xx[1] * vj[1] + xx[2] * vj[2];
+            const T xvi = xx[0] * vi[0] + xx[1] * vi[1] + xx[2] * vi[2];
+            const T kk = mk<T>(A4.w, A5.w) + (vi[0] * vj[0] + vi[1] * vj[1] + vi[2] * vj[2]) +
+                         (mk<T>(A4.x, A5.x) * di[0] + mk<T>(A4.y, A5.y) * di[1] +
+                          mk<T>(A4.z, A5.z) * di[2]);
+            const T f = mis3 * (xvj * is2 * xvj + kk);
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                acc[6 + k] += f * xx[k];
+            const T gg = mis3 * (xvi - 2.0 * xvj);
+            acc[9] += gg;
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                acc[10 + k] += gg * vj[k];
+            acc[13] += mk<T>(A6.x, A7.x) * is;
+            acc[14] += mk<T>(A6.y, A7.y) * is;
+            acc[15] += mk<T>(A6.z, A7.z) * is;
+        }
+    }
+    if constexpr (kDual) {
+        double *out = part + (int64_t)blockIdx.y * 2 * kFusedVals * S;
+#pragma unroll
+        for (int k = 0; k < kFusedVals; ++k) {
+            const Dual &r = reinterpret_cast<const Dual &>(acc[k]);
+            out[(int64_t)(2 * k) * S + ti] = r.v;
+            out[(int64_t)(2 * k + 1) * S + ti] = r.d;
+        }
+    } else {
+        double *out = part + (int64_t)blockIdx.y * kFusedVals * S;
+#pragma unroll
+        for (int k = 0; k < kFusedVals; ++k)
+            out[(int64_t)k * S + ti] = reinterpret_cast<const double &>(acc[k]);
+    }
+}
+
+// Per star: the split partials summed, star_eqs on Duals; the value is the
+// acceleration and the derivative the jerk.  Per-block sums of the hole's
+// terms (3 values, 3 derivatives) go to blk.
+__global__ void __launch_bounds__(kGlueThreads)
+k_jerk_epilogue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_clu,
+                const double *__restrict__ x, const double *__restrict__ v,
+                const double *__restrict__ m, const double *__restrict__ a,
+                const double *__restrict__ part, int js, const double *__restrict__ globs,
+                double *__restrict__ jerk, int *flag, unsigned long long *flag_step,
+                unsigned long long step, double *__restrict__ blk)
+{
+    __shared__ double sh[6][kGlueThreads];
+    const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
+    const int k_clu = cluster_of_block(blk_clu, blockIdx.x);
+    const Clu Cl = clu[k_clu];
+    const double *glob = globs + (int64_t)k_clu * 2 * kJVals;
+    const int64_t lt = t - Cl.slot0;
+    double bh6[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    if (lt < Cl.ns) {
+        const int64_t i = Cl.body0 + 1 + lt, hb = Cl.body0;
+        Dual d[3], vv[3];
+        for (int k = 0; k < 3; ++k) {
+            d[k] = dual(x[3 * i + k] - x[3 * hb + k], v[3 * i + k] - v[3 * hb + k]);
+            vv[k] = dual(v[3 * i + k], a[3 * i + k]);
+        }
+        Dual s[kFusedVals];
+        for (int k = 0; k < kFusedVals; ++k) {
+            double sv = 0.0, sd = 0.0;
+            for (int q = 0; q < js; ++q) {
+                sv += part[((int64_t)q * 2 * kFusedVals + 2 * k) * S + t];
+                sd += part[((int64_t)q * 2 * kFusedVals + 2 * k + 1) * S + t];
+            }
+            s[k] = dual(sv, sd);
+        }
+        StarSums<Dual> ss;
+        for (int k = 0; k < 3; ++k) {
+            ss.N[k] = s[k];
+            ss.Vp[k] = s[6 + k];
+            ss.Hv[k] = s[10 + k];
+            ss.E[k] = s[13 + k];
+            ss.P[k] = dual(0.0, 0.0);
+            ss.Ee[k] = dual(0.0, 0.0);
+        }
+        ss.U = s[3];
+        ss.Z = s[4];
+        ss.Wr = s[5];
+        ss.Hs = s[9];
+        ClusterSums<Dual> gs;
+        for (int k = 0; k < 3; ++k) {
+            gs.Q[k] = dual(glob[2 * k], glob[2 * k + 1]);
+            gs.Wf[k] = dual(glob[2 * (6 + k)], glob[2 * (6 + k) + 1]);
+        }
+        gs.SA = dual(glob[18], glob[19]);
+        gs.SB = dual(glob[20], glob[21]);
+        gs.Phi = dual(glob[22], glob[23]);
+        Dual ai[3], bh[3];
+        star_eqs<Dual, double>(Cl.G, m[hb], m[i], Cl.eps2, Cl.inv_c2, 1.0, d, vv, ss, gs, ai, bh);
+        const double ji[3] = {ai[0].d, ai[1].d, ai[2].d};
+        flag_nonfinite(ji, flag, flag_step, step);
+        for (int k = 0; k < 3; ++k) {
+            jerk[3 * i + k] = ai[k].d;
+            bh6[k] = bh[k].v;
+            bh6[3 + k] = bh[k].d;
+        }
+    }
+    block_sum<6>(bh6, sh);
+    if (threadIdx.x < 6)
+        blk[(int64_t)blockIdx.x * 6 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// The hole of each cluster: jerk = d/dt [G W + (1/c^2) sum_j (star j's term)].
+__global__ void __launch_bounds__(kGlueThreads)
+k_jerk_hole(const Clu *__restrict__ clu, const double *__restrict__ blk,
+            const double *__restrict__ globs, double *__restrict__ jerk, int *flag,
+            unsigned long long *flag_step, unsigned long long step)
+{
+    __shared__ double sh[6][kGlueThreads];
+    const Clu C = clu[blockIdx.x];
+    sum_blocks<6>(blk + (C.slot0 / kGlueThreads) * 6, C.ns_pad / kGlueThreads, sh);
+    if (threadIdx.x == 0) {
+        const double *glob = globs + (int64_t)blockIdx.x * 2 * kJVals;
+        double j0[3];
+        for (int k = 0; k < 3; ++k)
+            j0[k] = C.G * glob[2 * (3 + k) + 1] + C.inv_c2 * sh[3 + k][0];
+        flag_nonfinite(j0, flag, flag_step, step);
+        for (int k = 0; k < 3; ++k)
+            jerk[3 * C.body0 + k] = j0[k];
+    }
+}
+
+// Hermite stages on all 3n coordinates (body = coordinate / 3):
+//   0 predict  xe = x + dt v + dt^2/2 a + dt^3/6 j,  ve = v + dt a + dt^2/2 j
+//   1 correct  ve = v + dt/2 (a + a1) + dt^2/12 (j - j1),
+//              xe = x + dt/2 (v + ve) + dt^2/12 (a - a1)
+//   2 commit   x = xe, v = ve, a = a1, j = j1
+__global__ void __launch_bounds__(kGlueThreads)
+k_hermite(int stage, int64_t n3, double *__restrict__ x, double *__restrict__ v,
+          double *__restrict__ a, double *__restrict__ j, const double *__restrict__ a1,
+          const double *__restrict__ j1, double *__restrict__ xe, double *__restrict__ ve,
+          double dt)
+{
+    const double dt2 = dt * dt, dt3 = dt2 * dt;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n3;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        if (stage == 0) {
+            xe[q] = x[q] + dt * v[q] + dt2 / 2.0 * a[q] + dt3 / 6.0 * j[q];
+            ve[q] = v[q] + dt * a[q] + dt2 / 2.0 * j[q];
+        } else if (stage == 1) {
+            const double vn = v[q] + dt / 2.0 * (a[q] + a1[q]) + dt2 / 12.0 * (j[q] - j1[q]);
+            ve[q] = vn;
+            xe[q] = x[q] + dt / 2.0 * (v[q] + vn) + dt2 / 12.0 * (a[q] - a1[q]);
+        } else {
+            x[q] = xe[q];
+            v[q] = ve[q];
+            a[q] = a1[q];
+            j[q] = j1[q];
+        }
+    }
+}
+
+// ------------------------------------------------------------ adjoint --
+//
+// Vector-Jacobian product of A: given a cotangent abar (n x 3) of the
+// accelerations, the cotangents of the positions, of the velocities at which
+// A is taken, of the hole mass M and of inv_c2 = 1/c^2.  Reverse mode over
+// the same decomposition, in double precision, without the near-source
+// split (far form throughout):
+//   star assembly (star_eqs): forward-mode Duals, one pass per input (33),
+//     contracted with the output cotangents (per star, O(n));
+//   pair sums: hand-derived reverse of the pair terms (below), one sweep
+//     over sources per target and one over targets per source (O(n^2));
+//   records and cluster sums: forward-mode Duals over (d_j, v_j, M), 7
+//     passes, contracted with their cotangents (per star, O(n)).
+//
+// Pair terms (target i, source j), x = d_i - d_j, s^2 = |x|^2 + eps^2,
+// is = 1/s, mis3 = m_j is^3, xvj = x.v_j, xvi = x.v'_i (v' = 8/3 v),
+// k = C_j + v'_i.v_j + D_j.d_i (D = -e/1.5), F = xvj^2 is^2 + k,
+// Gq = xvi - 2 xvj; with the sums' cotangents (Nb, Ub, Zb, Wrb, Vb, Hsb,
+// Hvb, Eb) of target i the pair contributes
+//   phi = mis3 (Nb.x + Zb + Wrb R_j^2) + Ub m_j is + mis3 F (Vb.x)
+//       + mis3 Gq (Hsb + Hvb.v_j) + is (Eb.w_j).
+// With P = Nb.x + Zb + Wrb R_j^2, Vx = Vb.x, Hb = Hsb + Hvb.v_j, Ew = Eb.w_j,
+// B = P + F Vx + Gq Hb:
+//   dphi/dx    = gx = cx x + mis3 [Nb + F Vb + Hb v'_i + (2 Vx xvj is^2 - 2 Hb) v_j],
+//                cx = -3 mis3 is^2 B - 2 mis3 Vx xvj^2 is^4 - Ub mis3 - Ew is^3
+//   dphi/dd_i  = gx + mis3 Vx D_j          dphi/dv'_i = mis3 (Hb x + Vx v_j)
+//   dphi/dd_j  = -gx (through x)           dphi/dv_j  = mis3 [Vx (2 xvj is^2 x + v'_i)
+//                                                       - 2 Hb x] + mis3 Gq Hvb
+//   dphi/dR_j^2 = mis3 Wrb   dphi/dC_j = mis3 Vx   dphi/dD_j = mis3 Vx d_i
+//   dphi/dw_j  = is Eb
+
+constexpr int kAdjGlob = 11;      // Qb (3), Wfb (3), SAb, SBb, Phib, Mb, ic2b
+constexpr int kAdjSrc = 14;       // source cotangents: d (3), v (3), R^2, C, D (3), w (3)
+
+struct PairAdj {
+    double x[3], is, is2, mis3, xvj, F, Gq, Vx, Hb, gx[3];
+};
+
+// The shared intermediate quantities and dphi/dx of one pair.
+__device__ __forceinline__ void pair_adj(const double (&di)[3], const double (&vpi)[3],
+                                         const double (&dj)[3], double mj, double R2j,
+                                         const double (&vj)[3], double Cj, const double (&Dj)[3],
+                                         const double (&wj)[3], double eps2,
+                                         const double (&sb)[kFusedVals], PairAdj &p)
+{
+    for (int k = 0; k < 3; ++k)
+        p.x[k] = di[k] - dj[k];
+    const double s2 = p.x[0] * p.x[0] + p.x[1] * p.x[1] + p.x[2] * p.x[2] + eps2;
+    p.is = 1.0 / sqrt(s2);
+    p.is2 = p.is * p.is;
+    p.mis3 = mj * p.is * p.is2;
+    p.xvj = p.x[0] * vj[0] + p.x[1] * vj[1] + p.x[2] * vj[2];
+    const double xvi = p.x[0] * vpi[0] + p.x[1] * vpi[1] + p.x[2] * vpi[2];
+    const double kk = Cj + (vpi[0] * vj[0] + vpi[1] * vj[1] + vpi[2] * vj[2]) +
+                      (Dj[0] * di[0] + Dj[1] * di[1] + Dj[2] * di[2]);
+    p.F = p.xvj * p.xvj * p.is2 + kk;
+    p.Gq = xvi - 2.0 * p.xvj;
+    const double P = sb[0] * p.x[0] + sb[1] * p.x[1] + sb[2] * p.x[2] + sb[4] + sb[5] * R2j;
+    p.Vx = sb[6] * p.x[0] + sb[7] * p.x[1] + sb[8] * p.x[2];
+    p.Hb = sb[9] + sb[10] * vj[0] + sb[11] * vj[1] + sb[12] * vj[2];
+    const double Ew = sb[13] * wj[0] + sb[14] * wj[1] + sb[15] * wj[2];
+    const double B = P + p.F * p.Vx + p.Gq * p.Hb;
+    const double cx = -3.0 * p.mis3 * p.is2 * B -
+                      2.0 * p.mis3 * p.Vx * p.xvj * p.xvj * p.is2 * p.is2 - sb[3] * p.mis3 -
+                      Ew * p.is * p.is2;
+    const double cv = 2.0 * p.Vx * p.xvj * p.is2 - 2.0 * p.Hb;
+    for (int k = 0; k < 3; ++k)
+        p.gx[k] = cx * p.x[k] +
+                  p.mis3 * (sb[k] + p.F * sb[6 + k] + p.Hb * vpi[k] + cv * vj[k]);
+}
+
+// Per star slot: the assembly's reverse.  Inputs: the forward sums (part,
+// split-major, double), the cluster sums (Dual layout, values used) and the
+// cotangent abar.  Outputs: the sums' cotangents sbar[16][slot], the direct
+// cotangents of d_i and of the velocity kbar[6][slot], and per block the
+// cotangents of the cluster sums, of M and of inv_c2 (kAdjGlob values).
+__global__ void __launch_bounds__(kGlueThreads)
+k_adj_star(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_clu,
+           const double *__restrict__ x, const double *__restrict__ v,
+           const double *__restrict__ m, const double *__restrict__ part, int js,
+           const double *__restrict__ globs, const double *__restrict__ abar,
+           double *__restrict__ sbar, double *__restrict__ kbar, double *__restrict__ blk)
+{
+    __shared__ double sh[kAdjGlob][kGlueThreads];
+    const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
+    const int k_clu = cluster_of_block(blk_clu, blockIdx.x);
+    const Clu Cl = clu[k_clu];
+    const double *glob = globs + (int64_t)k_clu * 2 * kJVals;
+    const int64_t lt = t - Cl.slot0;
+    double g[kAdjGlob];
+    for (int k = 0; k < kAdjGlob; ++k)
+        g[k] = 0.0;
+    double sb_out[kFusedVals], kb_out[6];
+    for (int k = 0; k < kFusedVals; ++k)
+        sb_out[k] = 0.0;
+    for (int k = 0; k < 6; ++k)
+        kb_out[k] = 0.0;
+    if (lt < Cl.ns) {
+        const int64_t i = Cl.body0 + 1 + lt, hb = Cl.body0;
+        double u[33];
+        for (int k = 0; k < 3; ++k) {
+            u[k] = x[3 * i + k] - x[3 * hb + k];
+            u[3 + k] = v[3 * i + k];
+        }
+        for (int k = 0; k < kFusedVals; ++k) {
+            double sv = 0.0;
+            for (int q = 0; q < js; ++q)
+                sv += part[((int64_t)q * kFusedVals + k) * S + t];
+            u[6 + k] = sv;
+        }
+        for (int k = 0; k < 3; ++k) {
+            u[22 + k] = glob[2 * k];            // Q
+            u[25 + k] = glob[2 * (6 + k)];      // W_far (= W: far form)
+        }
+        u[28] = glob[18];
+        u[29] = glob[20];
+        u[30] = glob[22];
+        u[31] = m[hb];
+        u[32] = Cl.inv_c2;
+        const double ab[3] = {abar[3 * i], abar[3 * i + 1], abar[3 * i + 2]};
+        const double bb[3] = {Cl.inv_c2 * abar[3 * hb], Cl.inv_c2 * abar[3 * hb + 1],
+                              Cl.inv_c2 * abar[3 * hb + 2]};
+        double ub[33];
+        double bh_val[3] = {0.0, 0.0, 0.0};
+        for (int q = 0; q < 33; ++q) {
+            Dual w[33];
+            for (int k = 0; k < 33; ++k)
+                w[k] = dual(u[k], k == q ? 1.0 : 0.0);
+            Dual d[3] = {w[0], w[1], w[2]}, vv[3] = {w[3], w[4], w[5]};
+            StarSums<Dual> ss;
+            for (int k = 0; k < 3; ++k) {
+                ss.N[k] = w[6 + k];
+                ss.Vp[k] = w[12 + k];
+                ss.Hv[k] = w[16 + k];
+                ss.E[k] = w[19 + k];
+                ss.P[k] = dual(0.0, 0.0);
+                ss.Ee[k] = dual(0.0, 0.0);
+            }
+            ss.U = w[9];
+            ss.Z = w[10];
+            ss.Wr = w[11];
+            ss.Hs = w[15];
+            ClusterSums<Dual> gs;
+            for (int k = 0; k < 3; ++k) {
+                gs.Q[k] = w[22 + k];
+                gs.Wf[k] = w[25 + k];
+            }
+            gs.SA = w[28];
+            gs.SB = w[29];
+            gs.Phi = w[30];
+            Dual ai[3], bh[3];
+            star_eqs<Dual, Dual>(Cl.G, w[31], m[i], Cl.eps2, w[32], 1.0, d, vv, ss, gs, ai, bh);
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k)
+                acc += ab[k] * ai[k].d + bb[k] * bh[k].d;
+            ub[q] = acc;
+            if (q == 0)
+                for (int k = 0; k < 3; ++k)
+                    bh_val[k] = bh[k].v;
+        }
+        for (int k = 0; k < kFusedVals; ++k)
+            sb_out[k] = ub[6 + k];
+        for (int k = 0; k < 6; ++k)
+            kb_out[k] = ub[k];
+        for (int k = 0; k < 9; ++k)
+            g[k] = ub[22 + k];
+        g[9] = ub[31];
+        g[10] = ub[32] + (abar[3 * hb] * bh_val[0] + abar[3 * hb + 1] * bh_val[1] +
+                          abar[3 * hb + 2] * bh_val[2]);
+    }
+    for (int k = 0; k < kFusedVals; ++k)
+        sbar[(int64_t)k * S + t] = sb_out[k];
+    for (int k = 0; k < 6; ++k)
+        kbar[(int64_t)k * S + t] = kb_out[k];
+    block_sum<kAdjGlob>(g, sh);
+    if (threadIdx.x < kAdjGlob)
+        blk[(int64_t)blockIdx.x * kAdjGlob + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// One block per cluster: its cotangent sums, blocks in a fixed order.
+__global__ void __launch_bounds__(kGlueThreads)
+k_adj_globals(const Clu *__restrict__ clu, const double *__restrict__ blk,
+              double *__restrict__ gbar)
+{
+    __shared__ double sh[kAdjGlob][kGlueThreads];
+    const Clu C = clu[blockIdx.x];
+    sum_blocks<kAdjGlob>(blk + (C.slot0 / kGlueThreads) * kAdjGlob, C.ns_pad / kGlueThreads, sh);
+    if (threadIdx.x < kAdjGlob)
+        gbar[(int64_t)blockIdx.x * kAdjGlob + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// Reverse pair sweep over sources for each target i (one per thread):
+// tpart[split][6][slot] = (dphi/dd_i (3), dphi/dv'_i (3)) summed over j.
+__global__ void __launch_bounds__(kJThreads)
+k_adj_targets(const double4_32a *__restrict__ rec, int64_t S, const Clu *__restrict__ clu,
+              const int *__restrict__ blk_clu, const double *__restrict__ sbar,
+              double *__restrict__ tpart)
+{
+    __shared__ double4_32a sh[4][kJTile];
+    const int64_t t0 = (int64_t)blockIdx.x * kJThreads;
+    const Clu C = clu[cluster_of_block(blk_clu, t0 / kGlueThreads)];
+    const int ntiles = (int)(C.ns_pad / kJTile);
+    const int tps = (ntiles + (int)gridDim.y - 1) / (int)gridDim.y;
+    const int64_t ti = t0 + threadIdx.x;
+    const double4_32a T0 = rec[ti], T2 = rec[2 * S + ti];
+    const double di[3] = {T0.x, T0.y, T0.z};
+    const double vpi[3] = {8.0 / 3.0 * T2.x, 8.0 / 3.0 * T2.y, 8.0 / 3.0 * T2.z};
+    double sb[kFusedVals];
+    for (int k = 0; k < kFusedVals; ++k)
+        sb[k] = sbar[(int64_t)k * S + ti];
+    double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    const int tb = blockIdx.y * tps;
+    const int te = min(ntiles, tb + tps);
+    for (int tile = tb; tile < te; ++tile) {
+        const int64_t j0 = C.slot0 + (int64_t)tile * kJTile;
+        __syncthreads();
+        for (int q = threadIdx.x; q < 4 * kJTile; q += kJThreads)
+            sh[q / kJTile][q % kJTile] = rec[(2 * (q / kJTile)) * S + j0 + q % kJTile];
+        __syncthreads();
+#pragma unroll 1
+        for (int q = 0; q < kJTile; ++q) {
+            if (j0 + q == ti)
+                continue;
+            const double4_32a A0 = sh[0][q], A2 = sh[1][q], A4 = sh[2][q], A6 = sh[3][q];
+            const double dj[3] = {A0.x, A0.y, A0.z}, vj[3] = {A2.x, A2.y, A2.z};
+            const double Dj[3] = {A4.x, A4.y, A4.z}, wj[3] = {A6.x, A6.y, A6.z};
+            PairAdj p;
+            pair_adj(di, vpi, dj, A0.w, A2.w, vj, A4.w, Dj, wj, C.eps2, sb, p);
+            for (int k = 0; k < 3; ++k) {
+                acc[k] += p.gx[k] + p.mis3 * p.Vx * Dj[k];
+                acc[3 + k] += p.mis3 * (p.Hb * p.x[k] + p.Vx * vj[k]);
+            }
+        }
+    }
+    double *out = tpart + (int64_t)blockIdx.y * 6 * S;
+    for (int k = 0; k < 6; ++k)
+        out[(int64_t)k * S + ti] = acc[k];
+}
+
+// Reverse pair sweep over targets for each source j (one per thread):
+// spart[split][14][slot] = cotangents of its record (d via x, v, R^2, C, D, w).
+__global__ void __launch_bounds__(kJThreads)
+k_adj_sources(const double4_32a *__restrict__ rec, int64_t S, const Clu *__restrict__ clu,
+              const int *__restrict__ blk_clu, const double *__restrict__ sbar,
+              double *__restrict__ spart)
+{
+    __shared__ double sd[kJTile][3], sv[kJTile][3], ssb[kJTile][kFusedVals];
+    const int64_t t0 = (int64_t)blockIdx.x * kJThreads;
+    const Clu C = clu[cluster_of_block(blk_clu, t0 / kGlueThreads)];
+    const int ntiles = (int)(C.ns_pad / kJTile);
+    const int tps = (ntiles + (int)gridDim.y - 1) / (int)gridDim.y;
+    const int64_t tj = t0 + threadIdx.x;
+    const double4_32a A0 = rec[tj], A2 = rec[2 * S + tj], A4 = rec[4 * S + tj],
+                      A6 = rec[6 * S + tj];
+    const double dj[3] = {A0.x, A0.y, A0.z}, vj[3] = {A2.x, A2.y, A2.z};
+    const double Dj[3] = {A4.x, A4.y, A4.z}, wj[3] = {A6.x, A6.y, A6.z};
+    double acc[kAdjSrc];
+    for (int k = 0; k < kAdjSrc; ++k)
+        acc[k] = 0.0;
+    const int tb = blockIdx.y * tps;
+    const int te = min(ntiles, tb + tps);
+    for (int tile = tb; tile < te; ++tile) {
+        const int64_t i0 = C.slot0 + (int64_t)tile * kJTile;
+        __syncthreads();
+        for (int q = threadIdx.x; q < kJTile; q += kJThreads) {
+            const double4_32a T0 = rec[i0 + q], T2 = rec[2 * S + i0 + q];
+            sd[q][0] = T0.x;
+            sd[q][1] = T0.y;
+            sd[q][2] = T0.z;
+            sv[q][0] = 8.0 / 3.0 * T2.x;
+            sv[q][1] = 8.0 / 3.0 * T2.y;
+            sv[q][2] = 8.0 / 3.0 * T2.z;
+        }
+        for (int q = threadIdx.x; q < kJTile * kFusedVals; q += kJThreads)
+            ssb[q % kJTile][q / kJTile] = sbar[(int64_t)(q / kJTile) * S + i0 + q % kJTile];
+        __syncthreads();
+#pragma unroll 1
+        for (int q = 0; q < kJTile; ++q) {
+            if (i0 + q == tj)
+                continue;
+            const double di[3] = {sd[q][0], sd[q][1], sd[q][2]};
+            const double vpi[3] = {sv[q][0], sv[q][1], sv[q][2]};
+            double sb[kFusedVals];
+            for (int k = 0; k < kFusedVals; ++k)
+                sb[k] = ssb[q][k];
+            PairAdj p;
+            pair_adj(di, vpi, dj, A0.w, A2.w, vj, A4.w, Dj, wj, C.eps2, sb, p);
+            const double gg = p.mis3 * p.Gq;
+            for (int k = 0; k < 3; ++k) {
+                acc[k] -= p.gx[k];
+                acc[3 + k] += p.mis3 * (p.Vx * (2.0 * p.xvj * p.is2 * p.x[k] + vpi[k]) -
+                                        2.0 * p.Hb * p.x[k]) + gg * sb[10 + k];
+                acc[8 + k] += p.mis3 * p.Vx * di[k];
+                acc[11 + k] += p.is * sb[13 + k];
+            }
+            acc[6] += p.mis3 * sb[5];
+            acc[7] += p.mis3 * p.Vx;
+        }
+    }
+    double *out = spart + (int64_t)blockIdx.y * kAdjSrc * S;
+    for (int k = 0; k < kAdjSrc; ++k)
+        out[(int64_t)k * S + tj] = acc[k];
+}
+
+// Per star slot: the records' and cluster sums' reverse (forward-mode Duals
+// over d_j (3), v_j (3), M), plus every cotangent gathered so far; writes
+// the star's xbar, vbar and, per block, -sum dbar (the hole's xbar) and the
+// M cotangent (4 values).
+__global__ void __launch_bounds__(kGlueThreads)
+k_adj_records(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_clu,
+              const double *__restrict__ x, const double *__restrict__ v,
+              const double *__restrict__ m, const double *__restrict__ abar,
+              const double *__restrict__ kbar, const double *__restrict__ tpart, int jst,
+              const double *__restrict__ spart, int jss, const double *__restrict__ gbar,
+              double *__restrict__ xbar, double *__restrict__ vbar, double *__restrict__ blk)
+{
+    __shared__ double sh[4][kGlueThreads];
+    const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
+    const int k_clu = cluster_of_block(blk_clu, blockIdx.x);
+    const Clu Cl = clu[k_clu];
+    const double *gb = gbar + (int64_t)k_clu * kAdjGlob;
+    const int64_t lt = t - Cl.slot0;
+    double h4[4] = {0.0, 0.0, 0.0, 0.0};
+    if (lt < Cl.ns) {
+        const int64_t j = Cl.body0 + 1 + lt, hb = Cl.body0;
+        const double mj = m[j], G = Cl.G, eps2 = Cl.eps2;
+        double tp[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, sp[kAdjSrc];
+        for (int k = 0; k < 6; ++k)
+            for (int q = 0; q < jst; ++q)
+                tp[k] += tpart[((int64_t)q * 6 + k) * S + t];
+        for (int k = 0; k < kAdjSrc; ++k) {
+            sp[k] = 0.0;
+            for (int q = 0; q < jss; ++q)
+                sp[k] += spart[((int64_t)q * kAdjSrc + k) * S + t];
+        }
+        // cotangents of this star's record and cluster-sum terms
+        const double Wb[3] = {gb[3] + G * abar[3 * hb], gb[4] + G * abar[3 * hb + 1],
+                              gb[5] + G * abar[3 * hb + 2]};
+        double u[7];
+        for (int k = 0; k < 3; ++k) {
+            u[k] = x[3 * j + k] - x[3 * hb + k];
+            u[3 + k] = v[3 * j + k];
+        }
+        u[6] = m[hb];
+        double ub[7];
+        for (int q = 0; q < 7; ++q) {
+            Dual w[7];
+            for (int k = 0; k < 7; ++k)
+                w[k] = dual(u[k], k == q ? 1.0 : 0.0);
+            const Dual R2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+            const Dual iR = 1.0 / tsqrt(R2);
+            const Dual iR3 = iR * iR * iR;
+            const Dual GM = G * w[6];
+            const Dual c = GM * (1.5 * iR + 0.25 * eps2 * iR3);
+            const Dual Cc = c / 1.5 - (4.0 / 3.0) * (w[3] * w[3] + w[4] * w[4] + w[5] * w[5]);
+            const Dual ne = -(GM / 3.0) * iR3;       // -e/1.5 = ne d
+            Dual acc = sp[6] * R2 + sp[7] * Cc;
+            for (int k = 0; k < 3; ++k) {
+                acc += sp[8 + k] * (ne * w[k]);
+                acc += (sp[11 + k] + Wb[k]) * (mj * iR3 * w[k]);
+                acc += gb[k] * (mj * w[3 + k]);
+            }
+            acc += gb[6] * (1.25 * mj * iR) + gb[7] * (0.25 * mj * (R2 + eps2) * iR3) +
+                   gb[8] * (mj * iR);
+            ub[q] = acc.d;
+        }
+        double dbar[3];
+        for (int k = 0; k < 3; ++k) {
+            dbar[k] = kbar[(int64_t)k * S + t] + tp[k] + sp[k] + ub[k];
+            xbar[3 * j + k] = dbar[k];
+            vbar[3 * j + k] = kbar[(int64_t)(3 + k) * S + t] + 8.0 / 3.0 * tp[3 + k] + sp[3 + k] +
+                              ub[3 + k];
+            h4[k] = -dbar[k];
+        }
+        h4[3] = ub[6];
+    }
+    block_sum<4>(h4, sh);
+    if (threadIdx.x < 4)
+        blk[(int64_t)blockIdx.x * 4 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// The hole of each cluster: its xbar (its velocity does not enter Eq. 1-6),
+// and the cluster's M and inv_c2 cotangents, scal[2 k] and scal[2 k + 1]
+// (added to scal's contents when `accumulate`).
+__global__ void __launch_bounds__(kGlueThreads)
+k_adj_hole(const Clu *__restrict__ clu, const double *__restrict__ blk,
+           const double *__restrict__ gbar, double *__restrict__ xbar, double *__restrict__ vbar,
+           double *__restrict__ scal, int accumulate)
+{
+    __shared__ double sh[4][kGlueThreads];
+    const Clu C = clu[blockIdx.x];
+    sum_blocks<4>(blk + (C.slot0 / kGlueThreads) * 4, C.ns_pad / kGlueThreads, sh);
+    if (threadIdx.x == 0) {
+        const double *gb = gbar + (int64_t)blockIdx.x * kAdjGlob;
+        for (int k = 0; k < 3; ++k) {
+            xbar[3 * C.body0 + k] = sh[k][0];
+            vbar[3 * C.body0 + k] = 0.0;
+        }
+        const double mb = sh[3][0] + gb[9], cb = gb[10];
+        scal[2 * blockIdx.x] = accumulate ? scal[2 * blockIdx.x] + mb : mb;
+        scal[2 * blockIdx.x + 1] = accumulate ? scal[2 * blockIdx.x + 1] + cb : cb;
+    }
+}
+
+// Reverse of one kick-drift-kick step (pn_step), coordinate-wise, h = dt/2:
+//   stage 0 (forward quantities): vh = v + h a, xp = x + dt vh,
+//            vp = vh + h a (vel_mode 0) or vh;
+//   stage 1 (given xb_A, vpb_A = VJP of A at (xp, vp) with cotangent
+//            ab + h vb): vhb = vb + vpb_A + dt (xb + xb_A);
+//            xb = xb + xb_A;  ab = h vhb + (vel_mode 0 ? h vpb_A : 0);  vb = vhb;
+//   stage 2: xb += xb_A, vb += vpb_A (the entry acceleration's VJP).
+__global__ void __launch_bounds__(kGlueThreads)
+k_adj_kdk(int stage, int64_t n3, int vel_mode, double dt, const double *__restrict__ x,
+          const double *__restrict__ v, const double *__restrict__ a, double *__restrict__ xp,
+          double *__restrict__ vp, double *__restrict__ xb, double *__restrict__ vb,
+          double *__restrict__ ab, double *__restrict__ atot, const double *__restrict__ xbA,
+          const double *__restrict__ vpbA)
+{
+    const double h = 0.5 * dt;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n3;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        if (stage == 0) {
+            const double vh = v[q] + h * a[q];   // forward quantities of the step
+            xp[q] = x[q] + dt * vh;
+            vp[q] = vel_mode == 0 ? vh + h * a[q] : vh;
+            atot[q] = ab[q] + h * vb[q];
+        } else if (stage == 2) {
+            xb[q] += xbA[q];
+            vb[q] += vpbA[q];
+        } else {
+            const double xnew = xb[q] + xbA[q];
+            const double vhb = vb[q] + vpbA[q] + dt * xnew;
+            xb[q] = xnew;
+            ab[q] = h * vhb + (vel_mode == 0 ? h * vpbA[q] : 0.0);
+            vb[q] = vhb;
+        }
+    }
+}
+
+}  // namespace
+
+// Buffers: rec 8 x S double4, part js x 32 x S, blk (S/256) x 24, glob
+// nclu x 24, hole terms (S/256) x 6.
+int64_t jerk_part_splits(const pn_ctx *c)
+{
+    const int64_t nb = c->S / kJThreads;
+    int64_t js = (8 * (int64_t)c->sm_count * 4 + nb - 1) / nb;   // ~8 waves of 4 blocks/SM
+    const int64_t tiles = c->max_ns_pad / kJTile;
+    js = js < 1 ? 1 : (js > tiles ? tiles : js);
+    return js > 64 ? 64 : js;
+}
+
+size_t jerk_buffer_doubles(const pn_ctx *c)
+{
+    const int64_t S = c->S, nglue = S / kGlueThreads;
+    return (size_t)(kJRec * 4 * S + jerk_part_splits(c) * 2 * kFusedVals * S +
+                    nglue * 2 * kJVals + (int64_t)c->nclu * 2 * kJVals + nglue * 6);
+}
+
+cudaError_t launch_jerk(pn_ctx *c, const double *x, const double *v, const double *m,
+                        const double *a, double *jerk)
+{
+    const int64_t S = c->S, nglue = S / kGlueThreads;
+    const int js = (int)jerk_part_splits(c);
+    double *base = c->jbuf;
+    double4_32a *rec = reinterpret_cast<double4_32a *>(base);
+    double *part = base + kJRec * 4 * S;
+    double *blk = part + (int64_t)js * 2 * kFusedVals * S;
+    double *glob = blk + nglue * 2 * kJVals;
+    double *bhb = glob + (int64_t)c->nclu * 2 * kJVals;
+    const int *bc = c->nclu > 1 ? c->blk_clu : nullptr;
+    const unsigned long long step = (unsigned long long)c->step_counter;
+    k_jerk_prologue<<<(unsigned)nglue, kGlueThreads, 0, c->stream>>>(S, c->d_clu, bc, x, v, m, a,
+                                                                    rec, blk);
+    c->launches += 1;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    k_jerk_globals<<<c->nclu, kGlueThreads, 0, c->stream>>>(c->d_clu, blk, glob);
+    c->launches += 1;
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    dim3 grid((unsigned)(S / kJThreads), (unsigned)js);
+    k_dual_pairs<Dual><<<grid, kJThreads, 0, c->stream>>>(rec, S, c->d_clu, bc, part);
+    c->launches += 1;
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    k_jerk_epilogue<<<(unsigned)nglue, kGlueThreads, 0, c->stream>>>(
+        S, c->d_clu, bc, x, v, m, a, part, js, glob, jerk, c->flag, c->flag_step, step, bhb);
+    c->launches += 1;
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    k_jerk_hole<<<c->nclu, kGlueThreads, 0, c->stream>>>(c->d_clu, bhb, glob, jerk, c->flag,
+                                                        c->flag_step, step);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+// Adjoint scratch (doubles): sbar 16 S, kbar 6 S, target partials js 6 S,
+// source partials js 14 S, block cotangents (S/256) 11, cluster cotangents
+// nclu 11, hole blocks (S/256) 4.
+size_t adjoint_buffer_doubles(const pn_ctx *c)
+{
+    const int64_t S = c->S, nglue = S / kGlueThreads, js = jerk_part_splits(c);
+    return (size_t)((16 + 6) * S + js * (6 + kAdjSrc) * S + nglue * (kAdjGlob + 4) +
+                    (int64_t)c->nclu * kAdjGlob);
+}
+
+cudaError_t launch_accel_vjp(pn_ctx *c, const double *x, const double *v, const double *m,
+                             const double *abar, double *xbar, double *vbar, double *scal,
+                             bool accumulate)
+{
+    const int64_t S = c->S, nglue = S / kGlueThreads;
+    const int js = (int)jerk_part_splits(c);
+    double4_32a *rec = reinterpret_cast<double4_32a *>(c->jbuf);
+    double *part = c->jbuf + kJRec * 4 * S;
+    double *jblk = part + (int64_t)js * 2 * kFusedVals * S;
+    double *jglob = jblk + nglue * 2 * kJVals;
+    double *sbar = c->abuf, *kbar = sbar + 16 * S, *tpart = kbar + 6 * S;
+    double *spart = tpart + (int64_t)js * 6 * S, *kblk = spart + (int64_t)js * kAdjSrc * S;
+    double *gbar = kblk + nglue * kAdjGlob, *hblk = gbar + (int64_t)c->nclu * kAdjGlob;
+    const int *bc = c->nclu > 1 ? c->blk_clu : nullptr;
+    dim3 grid((unsigned)(S / kJThreads), (unsigned)js);
+    cudaError_t e;
+    // forward: records and cluster sums (values), pair sums in double
+    k_jerk_prologue<<<(unsigned)nglue, kGlueThreads, 0, c->stream>>>(S, c->d_clu, bc, x, v, m,
+                                                                    nullptr, rec, jblk);
+    k_jerk_globals<<<c->nclu, kGlueThreads, 0, c->stream>>>(c->d_clu, jblk, jglob);
+    k_dual_pairs<double><<<grid, kJThreads, 0, c->stream>>>(rec, S, c->d_clu, bc, part);
+    c->launches += 3;
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    // reverse
+    k_adj_star<<<(unsigned)nglue, kGlueThreads, 0, c->stream>>>(S, c->d_clu, bc, x, v, m, part, js,
+                                                               jglob, abar, sbar, kbar, kblk);
+    k_adj_globals<<<c->nclu, kGlueThreads, 0, c->stream>>>(c->d_clu, kblk, gbar);
+    k_adj_targets<<<grid, kJThreads, 0, c->stream>>>(rec, S, c->d_clu, bc, sbar, tpart);
+    k_adj_sources<<<grid, kJThreads, 0, c->stream>>>(rec, S, c->d_clu, bc, sbar, spart);
+    k_adj_records<<<(unsigned)nglue, kGlueThreads, 0, c->stream>>>(
+        S, c->d_clu, bc, x, v, m, abar, kbar, tpart, js, spart, js, gbar, xbar, vbar, hblk);
+    k_adj_hole<<<c->nclu, kGlueThreads, 0, c->stream>>>(c->d_clu, hblk, gbar, xbar, vbar, scal,
+                                                       accumulate ? 1 : 0);
+    c->launches += 6;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_kdk(pn_ctx *c, int stage, double dt, const double *x, const double *v,
+                           const double *a, double *xp, double *vp, double *xb, double *vb,
+                           double *ab, double *atot, const double *xbA, const double *vpbA)
+{
+    const int64_t n3 = 3 * c->n;
+    int64_t nb = (n3 + kGlueThreads - 1) / kGlueThreads;
+    if (nb > 4 * (int64_t)c->sm_count)
+        nb = 4 * (int64_t)c->sm_count;
+    k_adj_kdk<<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(stage, n3, c->p.vel_mode, dt, x, v, a,
+                                                            xp, vp, xb, vb, ab, atot, xbA, vpbA);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hermite(pn_ctx *c, int stage, double *x, double *v, double *a, double *j,
+                           const double *a1, const double *j1, double *xe, double *ve,
+                           double dt)
+{
+    const int64_t n3 = 3 * c->n;
+    int64_t nb = (n3 + kGlueThreads - 1) / kGlueThreads;
+    if (nb > 4 * (int64_t)c->sm_count)
+        nb = 4 * (int64_t)c->sm_count;
+    k_hermite<<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(stage, n3, x, v, a, j, a1, j1, xe,
+                                                            ve, dt);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace pn

@@ -93,6 +93,11 @@ __device__ __forceinline__ Dual operator/(double s, Dual a)
     return {r, -r * a.d / a.v};
 }
 __device__ __forceinline__ Dual operator/(Dual a, double s) { return {a.v / s, a.d / s}; }
+__device__ __forceinline__ Dual operator/(Dual a, Dual b)
+{
+    const double r = a.v / b.v;
+    return {r, (a.d - r * b.d) / b.v};
+}
 __device__ __forceinline__ Dual &operator+=(Dual &a, Dual b)
 {
     a.v += b.v;
@@ -112,8 +117,9 @@ __device__ __forceinline__ Dual tsqrt(Dual a)
 // Star i's acceleration (Eq. 4-6) and its term of the hole's 1PN
 // acceleration (Eq. 2-3, j = i), from the pair sums of passes 1 and 2, the
 // near-source sums and the cluster's global sums, over scalar type T
-// (double, or Dual for the jerk).  Velocities vv are those at which A is
-// taken; M and m_i are constants.
+// (double, or Dual for the jerk and the adjoint).  Velocities vv are those
+// at which A is taken; m_i is a constant; the hole mass M and inv_c2 have
+// type TM (double, or Dual where they are differentiated).
 //   a_i = -G M d_i/R_i^3 - G N_i + (1/c^2) {
 //       G M d_i/R_i^3 (4 G M/R_i - v_i^2) + 4 G M (v_i.d_i) v_i/R_i^3   [Eq. 5]
 //     + 5 G^2 m_i M d_i/R_i^4                                          [Eq. 6 l.1]
@@ -150,13 +156,13 @@ struct ClusterSums {
     T Q[3], Wf[3], SA, SB, Phi;
 };
 
-template <class T>
-__device__ __forceinline__ void star_eqs(double G, double M, double mi, double eps2,
-                                         double inv_c2, double fi, const T (&d)[3],
+template <class T, class TM>
+__device__ __forceinline__ void star_eqs(double G, const TM &M, double mi, double eps2,
+                                         const TM &inv_c2, double fi, const T (&d)[3],
                                          const T (&vv)[3], const StarSums<T> &s,
                                          const ClusterSums<T> &g, T (&ai)[3], T (&bh)[3])
 {
-    const double GM = G * M;
+    const TM GM = G * M;
     const T R2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     const T R = tsqrt(R2);
     const T iR = 1.0 / R;
@@ -181,7 +187,7 @@ __device__ __forceinline__ void star_eqs(double G, double M, double mi, double e
     const T cv = 4.0 * GM * iR3 * vd + 3.0 * G * iR3 * Qd;
     const T cN = G * (4.0 * GM * iR - v2);
     const T cQ = 4.0 * G * iR3 * vd;
-    const double c7 = 3.5 * G * GM;
+    const TM c7 = 3.5 * G * GM;
     for (int k = 0; k < 3; ++k) {
         const T pn = cd * d[k] + cv * vv[k] + G * Vv[k] + cN * s.N[k] -
                      c7 * (s.E[k] - Wx[k] * iR) + cQ * g.Q[k] + G * H[k] +

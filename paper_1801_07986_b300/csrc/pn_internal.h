@@ -123,6 +123,7 @@ struct pn_ctx {
     double *rk_x, *rk_v, *rk_a, *rk_sx, *rk_sv;
     double *jbuf;            // jerk scratch (allocated by the first pn_jerk / Hermite step)
     double *hj0, *hj1;       // Hermite: jerk at the current state and at the evaluation state
+    double *abuf;            // adjoint scratch (allocated by the first VJP call)
 
     // device copies used by pn_step_host
     double *hx, *hv, *hm, *ha;
@@ -149,6 +150,13 @@ cudaError_t launch_kick_drift(pn_ctx *c, double *x, double *v, const double *a, 
 cudaError_t launch_rk4_stage(pn_ctx *c, int stage, double *x, double *v, const double *a,
                              double dt);
 size_t jerk_buffer_doubles(const pn_ctx *c);
+size_t adjoint_buffer_doubles(const pn_ctx *c);
+cudaError_t launch_accel_vjp(pn_ctx *c, const double *x, const double *v, const double *m,
+                             const double *abar, double *xbar, double *vbar, double *scal,
+                             bool accumulate);
+cudaError_t launch_adj_kdk(pn_ctx *c, int stage, double dt, const double *x, const double *v,
+                           const double *a, double *xp, double *vp, double *xb, double *vb,
+                           double *ab, double *atot, const double *xbA, const double *vpbA);
 cudaError_t launch_jerk(pn_ctx *c, const double *x, const double *v, const double *m,
                         const double *a, double *jerk);
 cudaError_t launch_hermite(pn_ctx *c, int stage, double *x, double *v, double *a, double *j,

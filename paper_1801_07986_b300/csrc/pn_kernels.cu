@@ -1366,7 +1366,7 @@ k_epilogue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
         gs.Phi = glob[11];
         const double fi = nflag[t] ? 0.0 : 1.0;   // 1 if star i is a far source
         double ai[3];
-        star_eqs<double>(Cl.G, m[hb], m[i], Cl.eps2, Cl.inv_c2, fi, d, vv, ss, gs, ai, bh);
+        star_eqs<double, double>(Cl.G, m[hb], m[i], Cl.eps2, Cl.inv_c2, fi, d, vv, ss, gs, ai, bh);
         flag_nonfinite(ai, flag, flag_step, step);
         for (int k = 0; k < 3; ++k) {
             a[3 * i + k] = ai[k];

@@ -90,6 +90,8 @@ def _load():
                 "pn_set_stream": [P, P],
                 "pn_accel": [P, P, P, P, P],
                 "pn_jerk": [P, P, P, P, P, P],
+                "pn_accel_vjp": [P, P, P, P, P, P, P, P],
+                "pn_step_vjp": [P, P, P, P, D, I64, I64, P, P, P, P, P],
                 "pn_step": [P, P, P, P, P, D, I64],
                 "pn_step_host": [P, P, P, P, P, D, I64],
                 "pn_energy": [P, P, P, P, P],
@@ -270,6 +272,89 @@ def pn_jerk(ctx: Context, x, v, m, a, jerk) -> None:
     _check(_load().pn_jerk(ctx.handle, _dev(ctx, x, (n, 3), "x"), _dev(ctx, v, (n, 3), "v"),
                            _dev(ctx, m, (n,), "m"), _dev(ctx, a, (n, 3), "a"),
                            _dev(ctx, jerk, (n, 3), "jerk")))
+
+
+def pn_accel_vjp(ctx: Context, x, v, m, abar, xbar, vbar) -> np.ndarray:
+    """xbar, vbar = abar . dA/dx, abar . dA/dv (device tensors); returns the
+    host array [M_bar, inv_c2_bar] per cluster, shape (n_clusters, 2)."""
+    n = ctx.n
+    scal = np.zeros(2 * ctx.n_clusters)
+    _check(_load().pn_accel_vjp(ctx.handle, _dev(ctx, x, (n, 3), "x"), _dev(ctx, v, (n, 3), "v"),
+                                _dev(ctx, m, (n,), "m"), _dev(ctx, abar, (n, 3), "abar"),
+                                _dev(ctx, xbar, (n, 3), "xbar"), _dev(ctx, vbar, (n, 3), "vbar"),
+                                scal.ctypes.data_as(ctypes.c_void_p)))
+    return scal.reshape(-1, 2)
+
+
+def pn_step_vjp(ctx: Context, x0, v0, m, dt: float, nsteps: int, xbar_T, vbar_T, xbar0, vbar0,
+                checkpoint: int = 0) -> np.ndarray:
+    """Gradient of <xbar_T, x_T> + <vbar_T, v_T> through nsteps KDK steps from
+    (x0, v0): writes xbar0, vbar0; returns [M_bar, inv_c2_bar] per cluster."""
+    n = ctx.n
+    scal = np.zeros(2 * ctx.n_clusters)
+    _check(_load().pn_step_vjp(ctx.handle, _dev(ctx, x0, (n, 3), "x0"), _dev(ctx, v0, (n, 3), "v0"),
+                               _dev(ctx, m, (n,), "m"), float(dt), int(nsteps), int(checkpoint),
+                               _dev(ctx, xbar_T, (n, 3), "xbar_T"),
+                               _dev(ctx, vbar_T, (n, 3), "vbar_T"),
+                               _dev(ctx, xbar0, (n, 3), "xbar0"), _dev(ctx, vbar0, (n, 3), "vbar0"),
+                               scal.ctypes.data_as(ctypes.c_void_p)))
+    return scal.reshape(-1, 2)
+
+
+def trajectory(ctx: Context, x0, v0, m, M, c, dt: float, nsteps: int, checkpoint: int = 0):
+    """Differentiable nsteps of KDK (single-cluster context): returns (x_T,
+    v_T) as torch tensors whose backward gives gradients with respect to x0,
+    v0, the hole mass M and c (0-d tensors); m[0] is replaced by M and the
+    context's c by c.  The forward runs pn_step, the backward pn_step_vjp."""
+    import torch
+    return _Trajectory.apply(x0, v0, M, c, m, ctx, float(dt), int(nsteps), int(checkpoint))
+
+
+def _trajectory_class():
+    import torch
+
+    class Trajectory(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, x0, v0, M, c, m, ctx, dt, nsteps, checkpoint):
+            mm = m.detach().clone()
+            mm[0] = M.detach()
+            cc = float(c.detach())
+            pn_set_params(ctx, c=cc)
+            x, v = x0.detach().clone(), v0.detach().clone()
+            a = torch.empty_like(x)
+            pn_accel(ctx, x, v, mm, a)
+            pn_step(ctx, x, v, mm, a, dt, nsteps)
+            pn_sync(ctx)
+            fctx.save_for_backward(x0.detach(), v0.detach(), mm)
+            fctx.args = (ctx, dt, nsteps, checkpoint, cc)
+            return x, v
+
+        @staticmethod
+        def backward(fctx, gx, gv):
+            x0, v0, mm = fctx.saved_tensors
+            ctx, dt, nsteps, checkpoint, cc = fctx.args
+            gx = torch.zeros_like(x0) if gx is None else gx.contiguous()
+            gv = torch.zeros_like(v0) if gv is None else gv.contiguous()
+            xb, vb = torch.empty_like(x0), torch.empty_like(v0)
+            pn_set_params(ctx, c=cc)
+            scal = pn_step_vjp(ctx, x0, v0, mm, dt, nsteps, gx, gv, xb, vb, checkpoint)
+            Mb = torch.tensor(scal[0, 0], dtype=x0.dtype, device=x0.device)
+            cb = torch.tensor(-2.0 * scal[0, 1] / cc ** 3, dtype=x0.dtype, device=x0.device)
+            return xb, vb, Mb, cb, None, None, None, None, None
+
+    return Trajectory
+
+
+class _LazyTrajectory:
+    _cls = None
+
+    def apply(self, *args):
+        if _LazyTrajectory._cls is None:
+            _LazyTrajectory._cls = _trajectory_class()
+        return _LazyTrajectory._cls.apply(*args)
+
+
+_Trajectory = _LazyTrajectory()
 
 
 def pn_step(ctx: Context, x, v, m, a, dt: float, nsteps: int = 1) -> None:

@@ -1,0 +1,202 @@
+"""The adjoint of the accelerations and of KDK steps (pn_accel_vjp,
+pn_step_vjp, the torch.autograd trajectory) against the FP64 oracle's exact
+directional derivatives (complex step), contracted with the same cotangents,
+and against central differences of the GPU's own FP64 path."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1801_07986_b300 import pn  # noqa: E402
+from paper_1801_07986_b300.inputs import make_cluster  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+def state(n, seed, m_bh=0.3):
+    rng = np.random.default_rng(seed)
+    x = rng.normal(size=(n, 3))
+    x[0] = 0.0
+    v = rng.normal(size=(n, 3)) * 0.4
+    v[0] = 0.0
+    m = np.full(n, 0.02)
+    m[0] = m_bh
+    return x, v, m
+
+
+def oracle_vjp_accel(orc, x, v, m, abar, c, eps):
+    """abar . J for every input direction (positions, velocities, M, 1/c^2)."""
+    n = len(m)
+    xb, vb = np.zeros((n, 3)), np.zeros((n, 3))
+    z = np.zeros((n, 3))
+    for i in range(n):
+        for k in range(3):
+            e = np.zeros((n, 3))
+            e[i, k] = 1.0
+            xb[i, k] = np.sum(abar * orc.accel_jvp(x, v, m, e, z, c=c, eps=eps))
+            vb[i, k] = np.sum(abar * orc.accel_jvp(x, v, m, z, e, c=c, eps=eps))
+    Mb = np.sum(abar * orc.accel_jvp(x, v, m, z, z, dM=1.0, c=c, eps=eps))
+    cb = np.sum(abar * orc.accel_jvp(x, v, m, z, z, dinv_c2=1.0, c=c, eps=eps))
+    return xb, vb, Mb, cb
+
+
+@pytest.mark.parametrize("n", [2, 3, 20, 40])
+def test_accel_vjp_matches_oracle(orc, n):
+    x, v, m = state(n, 700 + n)
+    c, eps = 6.0, 1e-2
+    abar = np.random.default_rng(n).normal(size=(n, 3))
+    want = oracle_vjp_accel(orc, x, v, m, abar, c, eps)
+    ctx = pn.pn_init(n, c=c, eps=eps, precision="fp64", device=0)
+    X, V, M, AB = dev(x), dev(v), dev(m), dev(abar)
+    XB, VB = torch.empty_like(X), torch.empty_like(X)
+    scal = pn.pn_accel_vjp(ctx, X, V, M, AB, XB, VB)
+    ctx.close()
+    xb, vb = XB.cpu().numpy(), VB.cpu().numpy()
+    assert np.abs(xb - want[0]).max() <= 1e-10 * np.abs(want[0]).max()
+    assert np.abs(vb - want[1]).max() <= 1e-10 * max(np.abs(want[1]).max(), 1e-300)
+    assert abs(scal[0, 0] - want[2]) <= 1e-10 * abs(want[2])
+    assert abs(scal[0, 1] - want[3]) <= 1e-10 * abs(want[3])
+
+
+def test_accel_vjp_larger_cluster_random_projections(orc):
+    """n spanning several tiles and splits: check <xbar, u> + <vbar, w> + M_bar
+    dM + c2_bar dc2 against abar . (directional derivative) for random
+    directions."""
+    x, v, m = make_cluster(1100, 0.1, 71)
+    c, eps = 15.0, 1e-3
+    rng = np.random.default_rng(9)
+    abar = rng.normal(size=x.shape)
+    ctx = pn.pn_init(1100, c=c, eps=eps, precision="fp64", device=0)
+    XB, VB = torch.empty((1100, 3), dtype=torch.float64, device=DEV), torch.empty(
+        (1100, 3), dtype=torch.float64, device=DEV)
+    scal = pn.pn_accel_vjp(ctx, dev(x), dev(v), dev(m), dev(abar), XB, VB)
+    ctx.close()
+    xb, vb = XB.cpu().numpy(), VB.cpu().numpy()
+    for trial in range(3):
+        u, w = rng.normal(size=x.shape), rng.normal(size=x.shape)
+        dM, dc2 = rng.normal(), 1e-3 * rng.normal()
+        lhs = np.sum(xb * u) + np.sum(vb * w) + scal[0, 0] * dM + scal[0, 1] * dc2
+        rhs = np.sum(abar * orc.accel_jvp(x, v, m, u, w, dM, dc2, c=c, eps=eps))
+        assert abs(lhs - rhs) <= 1e-9 * abs(rhs), (lhs, rhs)
+
+
+def oracle_step_grad(orc, x, v, m, dt, nst, xbT, vbT, c, eps, vel_mode=0):
+    n = len(m)
+    gx, gv = np.zeros((n, 3)), np.zeros((n, 3))
+    z = np.zeros((n, 3))
+
+    def proj(dx, dv, dM=0.0, dc2=0.0):
+        _, _, jx, jv = orc.traj_jvp(x, v, m, dt, nst, dx, dv, dM, dc2, c=c, eps=eps,
+                                    vel_mode=vel_mode)
+        return np.sum(xbT * jx) + np.sum(vbT * jv)
+
+    for i in range(n):
+        for k in range(3):
+            e = np.zeros((n, 3))
+            e[i, k] = 1.0
+            gx[i, k] = proj(e, z)
+            gv[i, k] = proj(z, e)
+    return gx, gv, proj(z, z, dM=1.0), proj(z, z, dc2=1.0)
+
+
+@pytest.mark.parametrize("vel_mode,checkpoint", [("vpred_end", 4), ("vpred_end", 0),
+                                                 ("vhalf", 3)])
+def test_step_vjp_matches_oracle(orc, vel_mode, checkpoint):
+    n, nst, dt = 12, 10, 1.0 / 128
+    x, v, m = state(n, 800)
+    c, eps = 6.0, 1e-2
+    rng = np.random.default_rng(11)
+    xbT, vbT = rng.normal(size=(n, 3)), rng.normal(size=(n, 3))
+    want = oracle_step_grad(orc, x, v, m, dt, nst, xbT, vbT, c, eps,
+                            vel_mode=0 if vel_mode == "vpred_end" else 1)
+    ctx = pn.pn_init(n, c=c, eps=eps, precision="fp64", vel_mode=vel_mode, device=0)
+    XB, VB = torch.empty((n, 3), dtype=torch.float64, device=DEV), torch.empty(
+        (n, 3), dtype=torch.float64, device=DEV)
+    scal = pn.pn_step_vjp(ctx, dev(x), dev(v), dev(m), dt, nst, dev(xbT), dev(vbT), XB, VB,
+                          checkpoint=checkpoint)
+    ctx.close()
+    xb, vb = XB.cpu().numpy(), VB.cpu().numpy()
+    assert np.abs(xb - want[0]).max() <= 1e-9 * np.abs(want[0]).max()
+    assert np.abs(vb - want[1]).max() <= 1e-9 * np.abs(want[1]).max()
+    assert abs(scal[0, 0] - want[2]) <= 1e-9 * abs(want[2])
+    assert abs(scal[0, 1] - want[3]) <= 1e-9 * abs(want[3])
+
+
+def test_step_vjp_mixed_trajectory(orc):
+    """Mixed-precision forward trajectory, FP64 derivatives: the gradient
+    differs from the FP64 one by the trajectory's rounding only."""
+    n, nst, dt = 300, 8, 1.0 / 256
+    x, v, m = make_cluster(n, 0.1, 81)
+    c, eps = 20.0, 1e-3
+    rng = np.random.default_rng(13)
+    xbT, vbT = rng.normal(size=(n, 3)), rng.normal(size=(n, 3))
+    out = {}
+    for prec in ("fp64", "mixed"):
+        ctx = pn.pn_init(n, c=c, eps=eps, precision=prec, device=0)
+        XB, VB = torch.empty((n, 3), dtype=torch.float64, device=DEV), torch.empty(
+            (n, 3), dtype=torch.float64, device=DEV)
+        scal = pn.pn_step_vjp(ctx, dev(x), dev(v), dev(m), dt, nst, dev(xbT), dev(vbT), XB, VB)
+        out[prec] = XB.cpu().numpy(), VB.cpu().numpy(), scal
+        ctx.close()
+    (x64, v64, s64), (xm, vm, sm) = out["fp64"], out["mixed"]
+    assert np.abs(xm - x64).max() <= 1e-5 * np.abs(x64).max()
+    assert np.abs(vm - v64).max() <= 1e-5 * np.abs(v64).max()
+    assert abs(sm[0, 0] - s64[0, 0]) <= 1e-5 * abs(s64[0, 0])
+    # and the FP64 one agrees with the oracle along random directions
+    for trial in range(2):
+        u, w = rng.normal(size=x.shape), rng.normal(size=x.shape)
+        _, _, jx, jv = orc.traj_jvp(x, v, m, dt, nst, u, w, c=c, eps=eps)
+        rhs = np.sum(xbT * jx) + np.sum(vbT * jv)
+        lhs = np.sum(x64 * u) + np.sum(v64 * w)
+        assert abs(lhs - rhs) <= 1e-8 * abs(rhs)
+
+
+def test_autograd_trajectory_loss_of_the_nearest_stars():
+    """The differentiable trajectory (forward pn_step, backward pn_step_vjp)
+    on the adjoint workload's loss, sum over the 16 stars nearest the hole of
+    |x(T)|^2, against central differences of the FP64 path in M and c."""
+    n, nst, dt = 2048, 40, 1.0 / 2048
+    x, v, m = make_cluster(n, 0.1, 91)
+    near = np.argsort(np.linalg.norm(x[1:] - x[0], axis=1))[:16] + 1
+    idx = torch.tensor(near, device=DEV)
+    ctx = pn.pn_init(n, c=50.0, eps=1e-4, precision="fp64", device=0)
+    X0 = dev(x).requires_grad_(True)
+    V0 = dev(v).requires_grad_(True)
+    Mt = torch.tensor(0.1, dtype=torch.float64, device=DEV, requires_grad=True)
+    ct = torch.tensor(50.0, dtype=torch.float64, device=DEV, requires_grad=True)
+    M = dev(m)
+    xT, vT = pn.trajectory(ctx, X0, V0, M, Mt, ct, dt, nst)
+    loss = (xT[idx] ** 2).sum()
+    loss.backward()
+
+    def L(Mv, cv, dx=None):
+        mm = m.copy()
+        mm[0] = Mv
+        xx = x.copy() if dx is None else x + dx
+        with torch.no_grad():
+            xt, _ = pn.trajectory(ctx, dev(xx), dev(v), dev(mm),
+                                  torch.tensor(Mv, dtype=torch.float64),
+                                  torch.tensor(cv, dtype=torch.float64), dt, nst)
+        return float((xt[idx] ** 2).sum())
+
+    h = 1e-6
+    gM = (L(0.1 + h, 50.0) - L(0.1 - h, 50.0)) / (2 * h)
+    gc = (L(0.1, 50.0 + h * 50) - L(0.1, 50.0 - h * 50)) / (2 * h * 50)
+    assert abs(Mt.grad.item() - gM) <= 1e-5 * abs(gM), (Mt.grad.item(), gM)
+    assert abs(ct.grad.item() - gc) <= 1e-4 * abs(gc) + 1e-12, (ct.grad.item(), gc)
+    j = int(near[0])
+    e = np.zeros_like(x)
+    e[j, 0] = h
+    gx = (L(0.1, 50.0, e) - L(0.1, 50.0, -e)) / (2 * h)
+    assert abs(X0.grad[j, 0].item() - gx) <= 1e-5 * abs(gx), (X0.grad[j, 0].item(), gx)
+    ctx.close()

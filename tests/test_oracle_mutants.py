@@ -49,7 +49,8 @@ MUTANTS = [
     ("integrator: no velocity prediction",
      "vp[q] = vel_mode == 0 ? vh[q] + h * a[q] : vh[q];", "vp[q] = vel_mode == 0 ? vh[q] : vh[q];"),
     ("jerk: velocity tangent (the a_j of Appendix A) dropped",
-     "vc[q] = v[q] + I * (h * a[q]);", "vc[q] = v[q];"),
+     "return orc_accel_jvp(n, x, v, m, G, inv_c2, eps, v, a, 0.0, 0.0, jerk);",
+     "return orc_accel_jvp(n, x, v, m, G, inv_c2, eps, v, v, 0.0, 0.0, jerk);"),
     ("Hermite corrector: dt^2/12 -> dt^2/10 in the velocity",
      "dt2 / 12.0 * (j0[q] - j1[q]);", "dt2 / 10.0 * (j0[q] - j1[q]);"),
     ("trajectory derivative: KDK velocity prediction dropped",

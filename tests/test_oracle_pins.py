@@ -452,6 +452,28 @@ def test_hermite_is_fourth_order_and_matches_rk4(orc, c):
 
 # ------------------------------------------------------------ adjoint --
 
+def test_accel_directional_derivative_matches_central_differences(orc):
+    """The oracle's exact directional derivative of A (complex step), along a
+    direction that moves positions, velocities, the hole mass and 1/c^2."""
+    x, v, m = _random_state(16, 43, m_bh=0.4, m_star=1e-2)
+    c, eps = 7.0, 1e-2
+    rng = np.random.default_rng(5)
+    dx, dv, dM, dic2 = rng.normal(size=x.shape), rng.normal(size=v.shape), 0.3, 1e-3
+    jv = orc.accel_jvp(x, v, m, dx, dv, dM, dic2, c=c, eps=eps)
+
+    def A(h):
+        mm = m.copy()
+        mm[0] += h * dM
+        return orc.accel(x + h * dx, v + h * dv, mm, c=1.0 / math.sqrt(1.0 / c ** 2 + h * dic2),
+                         eps=eps)
+
+    def cd(h):
+        return (A(h) - A(-h)) / (2 * h)
+
+    fd = (4 * cd(5e-6) - cd(1e-5)) / 3
+    assert np.abs(jv - fd).max() < 1e-8 * np.abs(fd).max()
+
+
 def test_trajectory_derivative_matches_central_differences(orc):
     """The oracle's exact trajectory derivative (complex step through the KDK
     steps) against a Richardson central difference of the double-precision
