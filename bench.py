@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=500)
     ap.add_argument("--no-jerk", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=1000)
     return ap.parse_args()
 
 
@@ -407,6 +409,12 @@ def run_native(args, w):
         except Exception as e:  # reported, not required
             line["jerk"] = {"error": str(e)[:300]}
 
+    if not args.no_adjoint and world == 1:
+        try:
+            line["adjoint"] = run_adjoint(local, stream, args.adjoint_steps)
+        except Exception as e:  # reported, not required
+            line["adjoint"] = {"error": str(e)[:300]}
+
     if rank == 0 and not args.no_cpu_baseline:
         try:
             rows = max(64, min(w.n - 1, 16384))
@@ -519,6 +527,58 @@ def run_jerk(local, stream, warmup, reps=5):
                          "peak_basis": "FP64 FMA-chain microbenchmark (pn_measure_peaks)",
                          "flops_per_pair": FLOPS_JERK,
                          "note": "whole pn_jerk call timed (dual pair kernel dominates)"}}
+
+
+def run_adjoint(local, stream, nsteps):
+    """The adjoint workload: N = 8192 Plummer cluster (M = 0.1, c = 50,
+    dt = 1/2048), loss = sum over the 16 stars nearest the hole at t = 0 of
+    |x(T)|^2 after nsteps KDK steps (mixed-precision forward, FP64
+    derivatives), gradient with respect to M, c, x0 and v0 through
+    pn_step_vjp with sqrt(T) checkpoints; timed with CUDA events."""
+    import torch
+    from paper_1801_07986_b300 import pn
+    from paper_1801_07986_b300.inputs import WORKLOADS
+    w = WORKLOADS["plummer8k_adjoint"]
+    x, v, m = w.state()
+    near = np.argsort(np.linalg.norm(x[1:] - x[0], axis=1))[:16] + 1
+    dev = torch.device(f"cuda:{local}")
+    X0, V0, M = (torch.tensor(a, device=dev) for a in (x, v, m))
+    ctx = pn.pn_init(w.n, G=w.G, c=w.c, eps=w.eps, precision="mixed", device=local,
+                     stream=stream)
+    X, V = X0.clone(), V0.clone()
+    A = torch.empty_like(X)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    pn.pn_accel(ctx, X, V, M, A)
+    pn.pn_step(ctx, X, V, M, A, w.dt, nsteps)
+    e1.record(stream)
+    e1.synchronize()
+    ms_fwd = e0.elapsed_time(e1)
+    xbT = torch.zeros_like(X)
+    xbT[near] = 2.0 * X[near]
+    vbT = torch.zeros_like(X)
+    XB, VB = torch.empty_like(X), torch.empty_like(X)
+    pn.pn_step_vjp(ctx, X0, V0, M, w.dt, 2, xbT, vbT, XB, VB)       # allocations, warm-up
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    scal = pn.pn_step_vjp(ctx, X0, V0, M, w.dt, nsteps, xbT, vbT, XB, VB)
+    e1.record(stream)
+    e1.synchronize()
+    wall = time.perf_counter() - t0
+    ms_grad = e0.elapsed_time(e1)
+    ctx.close()
+    pairs = float(w.n) * (w.n - 1) * nsteps
+    return {"workload": "plummer8k_adjoint", "n_bodies": w.n, "steps": nsteps,
+            "checkpoint": "every ceil(sqrt(steps)) steps",
+            "loss": "sum over the 16 stars nearest the hole at t=0 of |x(T)|^2",
+            "value": pairs / (ms_grad * 1e-3), "unit": "interactions/s",
+            "what": "trajectory steps differentiated per second x N(N-1)",
+            "gradient_s": ms_grad * 1e-3, "gradient_wall_s": wall,
+            "forward_s": ms_fwd * 1e-3, "gradient_over_forward": ms_grad / ms_fwd,
+            "dL_dM": float(scal[0, 0]), "dL_dc": float(-2.0 * scal[0, 1] / w.c ** 3),
+            "grad_x0_norm": float(torch.linalg.norm(XB)), "grad_v0_norm": float(torch.linalg.norm(VB))}
 
 
 def main():
