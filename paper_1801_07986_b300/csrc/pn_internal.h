@@ -15,7 +15,7 @@ constexpr int kMixTargets = 2;     // targets held in registers per thread
 constexpr int kMixTile = 128;      // sources per shared-memory tile
 constexpr int kFlushTiles = 2;     // fused kernel: tiles per single-precision partial
 constexpr int kPackTile = 64;      // packed fused kernel: sources per shared-memory tile
-constexpr int kPackFlushTiles = 4; // packed fused kernel: tiles per single-precision partial
+constexpr int kPackFlushTiles = 8; // packed fused kernel: tiles per single-precision partial
 constexpr int kPackWorkersMax = 4;  // packed fused kernel: stream-K workers per resident block (max)
 // Launch shape of the double-precision pair kernels (FP64 mode and energy).
 constexpr int kF64Threads = 128;
