@@ -642,6 +642,201 @@ k_adj_sources(const double4_32a *__restrict__ rec, int64_t S, const Clu *__restr
         out[(int64_t)k * S + tj] = acc[k];
 }
 
+// ------------------------------------------- adjoint: single precision --
+//
+// The two reverse pair sweeps in FP32 for mixed-precision contexts: the
+// same pair terms (pair_adj) with x_ij formed from hi/lo splits of the
+// hole-relative positions, FP32 partial sums over a tile folded into FP64.
+// Records (float4, per slot, far form): A = (hi d, m), B = (lo d, R^2),
+// C = (v, C), D = (-e/1.5, 0), E = (w, 0), made from the FP64 records.
+
+constexpr int kAdjTileF = 64;     // slots per shared-memory tile (FP32 sweeps)
+
+__global__ void __launch_bounds__(kGlueThreads)
+k_adj_frec(int64_t S, const double4_32a *__restrict__ rec, float4 *__restrict__ frec)
+{
+    const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
+    if (t >= S)
+        return;
+    const double4_32a A0 = rec[t], A2 = rec[2 * S + t], A4 = rec[4 * S + t], A6 = rec[6 * S + t];
+    const float h0 = (float)A0.x, h1 = (float)A0.y, h2 = (float)A0.z;
+    frec[t] = make_float4(h0, h1, h2, (float)A0.w);
+    frec[S + t] = make_float4((float)(A0.x - (double)h0), (float)(A0.y - (double)h1),
+                              (float)(A0.z - (double)h2), (float)A2.w);
+    frec[2 * S + t] = make_float4((float)A2.x, (float)A2.y, (float)A2.z, (float)A4.w);
+    frec[3 * S + t] = make_float4((float)A4.x, (float)A4.y, (float)A4.z, 0.0f);
+    frec[4 * S + t] = make_float4((float)A6.x, (float)A6.y, (float)A6.z, 0.0f);
+}
+
+struct PairAdjF {
+    float x[3], is, is2, mis3, xvj, F, Gq, Vx, Hb, gx[3];
+};
+
+// pair_adj in single precision; x = (hi_i - hi_j) + (lo_i - lo_j).
+__device__ __forceinline__ void pair_adj_f(const float (&hi)[3], const float (&lo)[3],
+                                           const float (&vpi)[3], const float4 &A,
+                                           const float4 &B, const float4 &C, const float4 &D,
+                                           const float4 &E, float eps2,
+                                           const float (&sb)[kFusedVals], PairAdjF &p)
+{
+    p.x[0] = (hi[0] - A.x) + (lo[0] - B.x);
+    p.x[1] = (hi[1] - A.y) + (lo[1] - B.y);
+    p.x[2] = (hi[2] - A.z) + (lo[2] - B.z);
+    const float s2 = fmaf(p.x[0], p.x[0], fmaf(p.x[1], p.x[1], fmaf(p.x[2], p.x[2], eps2)));
+    p.is = rsqrt_approx(s2);
+    p.is2 = p.is * p.is;
+    p.mis3 = A.w * p.is * p.is2;
+    p.xvj = fmaf(p.x[0], C.x, fmaf(p.x[1], C.y, p.x[2] * C.z));
+    const float xvi = fmaf(p.x[0], vpi[0], fmaf(p.x[1], vpi[1], p.x[2] * vpi[2]));
+    const float di[3] = {hi[0] + lo[0], hi[1] + lo[1], hi[2] + lo[2]};
+    const float kk = C.w + fmaf(vpi[0], C.x, fmaf(vpi[1], C.y, vpi[2] * C.z)) +
+                     fmaf(D.x, di[0], fmaf(D.y, di[1], D.z * di[2]));
+    p.F = p.xvj * p.xvj * p.is2 + kk;
+    p.Gq = xvi - 2.0f * p.xvj;
+    const float P = fmaf(sb[0], p.x[0], fmaf(sb[1], p.x[1], sb[2] * p.x[2])) + sb[4] + sb[5] * B.w;
+    p.Vx = fmaf(sb[6], p.x[0], fmaf(sb[7], p.x[1], sb[8] * p.x[2]));
+    p.Hb = sb[9] + fmaf(sb[10], C.x, fmaf(sb[11], C.y, sb[12] * C.z));
+    const float Ew = fmaf(sb[13], E.x, fmaf(sb[14], E.y, sb[15] * E.z));
+    const float B2 = P + p.F * p.Vx + p.Gq * p.Hb;
+    const float cx = -3.0f * p.mis3 * p.is2 * B2 -
+                     2.0f * p.mis3 * p.Vx * p.xvj * p.xvj * p.is2 * p.is2 - sb[3] * p.mis3 -
+                     Ew * p.is * p.is2;
+    const float cv = 2.0f * p.Vx * p.xvj * p.is2 - 2.0f * p.Hb;
+    const float cvec[3] = {C.x, C.y, C.z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        p.gx[k] = cx * p.x[k] + p.mis3 * (sb[k] + p.F * sb[6 + k] + p.Hb * vpi[k] + cv * cvec[k]);
+}
+
+__global__ void __launch_bounds__(kJThreads)
+k_adj_targets_f(const float4 *__restrict__ frec, int64_t S, const Clu *__restrict__ clu,
+                const int *__restrict__ blk_clu, const double *__restrict__ sbar,
+                double *__restrict__ tpart)
+{
+    __shared__ float4 sh[5][kAdjTileF];
+    const int64_t t0 = (int64_t)blockIdx.x * kJThreads;
+    const Clu C = clu[cluster_of_block(blk_clu, t0 / kGlueThreads)];
+    const int ntiles = (int)(C.ns_pad / kAdjTileF);
+    const int tps = (ntiles + (int)gridDim.y - 1) / (int)gridDim.y;
+    const int64_t ti = t0 + threadIdx.x;
+    const float4 TA = frec[ti], TB = frec[S + ti], TC = frec[2 * S + ti];
+    const float hi[3] = {TA.x, TA.y, TA.z}, lo[3] = {TB.x, TB.y, TB.z};
+    const float vpi[3] = {8.0f / 3.0f * TC.x, 8.0f / 3.0f * TC.y, 8.0f / 3.0f * TC.z};
+    float sb[kFusedVals];
+#pragma unroll
+    for (int k = 0; k < kFusedVals; ++k)
+        sb[k] = (float)sbar[(int64_t)k * S + ti];
+    const float eps2 = (float)C.eps2;
+    double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    const int tb = blockIdx.y * tps;
+    const int te = min(ntiles, tb + tps);
+    for (int tile = tb; tile < te; ++tile) {
+        const int64_t j0 = C.slot0 + (int64_t)tile * kAdjTileF;
+        __syncthreads();
+        for (int q = threadIdx.x; q < 5 * kAdjTileF; q += kJThreads)
+            sh[q / kAdjTileF][q % kAdjTileF] = frec[(q / kAdjTileF) * S + j0 + q % kAdjTileF];
+        __syncthreads();
+        float part[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 1
+        for (int q = 0; q < kAdjTileF; ++q) {
+            if (j0 + q == ti)
+                continue;
+            const float4 A = sh[0][q], B = sh[1][q], Cc = sh[2][q], D = sh[3][q], E = sh[4][q];
+            PairAdjF p;
+            pair_adj_f(hi, lo, vpi, A, B, Cc, D, E, eps2, sb, p);
+            const float Dv[3] = {D.x, D.y, D.z}, vj[3] = {Cc.x, Cc.y, Cc.z};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                part[k] += p.gx[k] + p.mis3 * p.Vx * Dv[k];
+                part[3 + k] += p.mis3 * (p.Hb * p.x[k] + p.Vx * vj[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            acc[k] += (double)part[k];
+    }
+    double *out = tpart + (int64_t)blockIdx.y * 6 * S;
+    for (int k = 0; k < 6; ++k)
+        out[(int64_t)k * S + ti] = acc[k];
+}
+
+__global__ void __launch_bounds__(kJThreads)
+k_adj_sources_f(const float4 *__restrict__ frec, int64_t S, const Clu *__restrict__ clu,
+                const int *__restrict__ blk_clu, const double *__restrict__ sbar,
+                double *__restrict__ spart)
+{
+    __shared__ float sdh[kAdjTileF][3], sdl[kAdjTileF][3], svp[kAdjTileF][3];
+    __shared__ float ssb[kAdjTileF][kFusedVals + 1];
+    const int64_t t0 = (int64_t)blockIdx.x * kJThreads;
+    const Clu C = clu[cluster_of_block(blk_clu, t0 / kGlueThreads)];
+    const int ntiles = (int)(C.ns_pad / kAdjTileF);
+    const int tps = (ntiles + (int)gridDim.y - 1) / (int)gridDim.y;
+    const int64_t tj = t0 + threadIdx.x;
+    const float4 A = frec[tj], B = frec[S + tj], Cc = frec[2 * S + tj], D = frec[3 * S + tj],
+                 E = frec[4 * S + tj];
+    const float eps2 = (float)C.eps2;
+    double acc[kAdjSrc];
+    for (int k = 0; k < kAdjSrc; ++k)
+        acc[k] = 0.0;
+    const int tb = blockIdx.y * tps;
+    const int te = min(ntiles, tb + tps);
+    for (int tile = tb; tile < te; ++tile) {
+        const int64_t i0 = C.slot0 + (int64_t)tile * kAdjTileF;
+        __syncthreads();
+        for (int q = threadIdx.x; q < kAdjTileF; q += kJThreads) {
+            const float4 TA = frec[i0 + q], TB = frec[S + i0 + q], TC = frec[2 * S + i0 + q];
+            sdh[q][0] = TA.x;
+            sdh[q][1] = TA.y;
+            sdh[q][2] = TA.z;
+            sdl[q][0] = TB.x;
+            sdl[q][1] = TB.y;
+            sdl[q][2] = TB.z;
+            svp[q][0] = 8.0f / 3.0f * TC.x;
+            svp[q][1] = 8.0f / 3.0f * TC.y;
+            svp[q][2] = 8.0f / 3.0f * TC.z;
+        }
+        for (int q = threadIdx.x; q < kAdjTileF * kFusedVals; q += kJThreads)
+            ssb[q % kAdjTileF][q / kAdjTileF] =
+                (float)sbar[(int64_t)(q / kAdjTileF) * S + i0 + q % kAdjTileF];
+        __syncthreads();
+        float part[kAdjSrc];
+#pragma unroll
+        for (int k = 0; k < kAdjSrc; ++k)
+            part[k] = 0.0f;
+#pragma unroll 1
+        for (int q = 0; q < kAdjTileF; ++q) {
+            if (i0 + q == tj)
+                continue;
+            const float hi[3] = {sdh[q][0], sdh[q][1], sdh[q][2]};
+            const float lo[3] = {sdl[q][0], sdl[q][1], sdl[q][2]};
+            const float vpi[3] = {svp[q][0], svp[q][1], svp[q][2]};
+            float sb[kFusedVals];
+#pragma unroll
+            for (int k = 0; k < kFusedVals; ++k)
+                sb[k] = ssb[q][k];
+            PairAdjF p;
+            pair_adj_f(hi, lo, vpi, A, B, Cc, D, E, eps2, sb, p);
+            const float gg = p.mis3 * p.Gq;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                part[k] -= p.gx[k];
+                part[3 + k] += p.mis3 * (p.Vx * (2.0f * p.xvj * p.is2 * p.x[k] + vpi[k]) -
+                                         2.0f * p.Hb * p.x[k]) + gg * sb[10 + k];
+                part[8 + k] += p.mis3 * p.Vx * (hi[k] + lo[k]);
+                part[11 + k] += p.is * sb[13 + k];
+            }
+            part[6] += p.mis3 * sb[5];
+            part[7] += p.mis3 * p.Vx;
+        }
+#pragma unroll
+        for (int k = 0; k < kAdjSrc; ++k)
+            acc[k] += (double)part[k];
+    }
+    double *out = spart + (int64_t)blockIdx.y * kAdjSrc * S;
+    for (int k = 0; k < kAdjSrc; ++k)
+        out[(int64_t)k * S + tj] = acc[k];
+}
+
 // Per star slot: the records' and cluster sums' reverse (forward-mode Duals
 // over d_j (3), v_j (3), M), plus every cotangent gathered so far; writes
 // the star's xbar, vbar and, per block, -sum dbar (the hole's xbar) and the
@@ -861,21 +1056,45 @@ cudaError_t launch_accel_vjp(pn_ctx *c, const double *x, const double *v, const 
     double *gbar = kblk + nglue * kAdjGlob, *hblk = gbar + (int64_t)c->nclu * kAdjGlob;
     const int *bc = c->nclu > 1 ? c->blk_clu : nullptr;
     dim3 grid((unsigned)(S / kJThreads), (unsigned)js);
+    const bool mixed = c->p.precision == PN_MIXED;
+    // mixed contexts: single-precision records (hi/lo positions, far form)
+    // in the upper half of the pair-sum region
+    float4 *frec = reinterpret_cast<float4 *>(part + (int64_t)js * kFusedVals * S);
     cudaError_t e;
-    // forward: records and cluster sums (values), pair sums in double
+    // forward: records and cluster sums (values); the 16 pair sums in double,
+    // or (mixed) by the fused pair kernel on the single-precision records
     k_jerk_prologue<<<(unsigned)nglue, kGlueThreads, 0, c->stream>>>(S, c->d_clu, bc, x, v, m,
                                                                     nullptr, rec, jblk);
     k_jerk_globals<<<c->nclu, kGlueThreads, 0, c->stream>>>(c->d_clu, jblk, jglob);
-    k_dual_pairs<double><<<grid, kJThreads, 0, c->stream>>>(rec, S, c->d_clu, bc, part);
-    c->launches += 3;
+    c->launches += 2;
+    const double *fwd = part;
+    int jsf = js;
+    if (mixed) {
+        k_adj_frec<<<(unsigned)nglue, kGlueThreads, 0, c->stream>>>(S, rec, frec);
+        c->launches += 1;
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            return e;
+        if ((e = launch_fused_on(c, frec)) != cudaSuccess)
+            return e;
+        fwd = c->part;
+        jsf = 1;
+    } else {
+        k_dual_pairs<double><<<grid, kJThreads, 0, c->stream>>>(rec, S, c->d_clu, bc, part);
+        c->launches += 1;
+    }
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
     // reverse
-    k_adj_star<<<(unsigned)nglue, kGlueThreads, 0, c->stream>>>(S, c->d_clu, bc, x, v, m, part, js,
+    k_adj_star<<<(unsigned)nglue, kGlueThreads, 0, c->stream>>>(S, c->d_clu, bc, x, v, m, fwd, jsf,
                                                                jglob, abar, sbar, kbar, kblk);
     k_adj_globals<<<c->nclu, kGlueThreads, 0, c->stream>>>(c->d_clu, kblk, gbar);
-    k_adj_targets<<<grid, kJThreads, 0, c->stream>>>(rec, S, c->d_clu, bc, sbar, tpart);
-    k_adj_sources<<<grid, kJThreads, 0, c->stream>>>(rec, S, c->d_clu, bc, sbar, spart);
+    if (mixed) {
+        k_adj_targets_f<<<grid, kJThreads, 0, c->stream>>>(frec, S, c->d_clu, bc, sbar, tpart);
+        k_adj_sources_f<<<grid, kJThreads, 0, c->stream>>>(frec, S, c->d_clu, bc, sbar, spart);
+    } else {
+        k_adj_targets<<<grid, kJThreads, 0, c->stream>>>(rec, S, c->d_clu, bc, sbar, tpart);
+        k_adj_sources<<<grid, kJThreads, 0, c->stream>>>(rec, S, c->d_clu, bc, sbar, spart);
+    }
     k_adj_records<<<(unsigned)nglue, kGlueThreads, 0, c->stream>>>(
         S, c->d_clu, bc, x, v, m, abar, kbar, tpart, js, spart, js, gbar, xbar, vbar, hblk);
     k_adj_hole<<<c->nclu, kGlueThreads, 0, c->stream>>>(c->d_clu, hblk, gbar, xbar, vbar, scal,

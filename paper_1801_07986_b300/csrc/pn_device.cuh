@@ -69,6 +69,17 @@ __device__ __forceinline__ int cluster_of_block(const int *__restrict__ blk_clu,
     return blk_clu ? blk_clu[b] : 0;
 }
 
+// 1/sqrt(s2) in single precision: the PTX approximate reciprocal square root
+// (one MUFU instruction; max relative error about 2^-23), flushing subnormal
+// inputs to zero -- pair distances squared are never subnormal (s2 >= eps^2,
+// and unsoftened pairs are far from 1e-38).
+__device__ __forceinline__ float rsqrt_approx(float s2)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(s2));
+    return y;
+}
+
 // ------------------------------------------------------- dual numbers --
 
 // Forward-mode dual number v + d eps (eps^2 = 0): evaluating a function on

@@ -181,6 +181,7 @@ void shapes(int64_t S, int64_t max_ns_pad, int sm_count, int occ_mix, int occ_f6
 cudaError_t occupancy(int *occ_mix, int *occ_f64);
 cudaError_t fused_occupancy(int P, int unroll, bool packed, int *occ);
 cudaError_t launch_fused(pn_ctx *c);
+cudaError_t launch_fused_on(pn_ctx *c, const float4 *rec);
 bool use_fused(const pn_ctx *c);
 int fused_tile_size(bool packed);
 struct FusedShape {

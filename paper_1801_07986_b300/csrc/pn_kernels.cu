@@ -42,17 +42,6 @@ __device__ __forceinline__ void ds_add(float &hi, float &lo, float p)
     lo += e;
 }
 
-// 1/sqrt(s2) in single precision: the PTX approximate reciprocal square root
-// (one MUFU instruction; max relative error about 2^-23), flushing subnormal
-// inputs to zero -- pair distances squared are never subnormal (s2 >= eps^2,
-// and unsoftened pairs are far from 1e-38).
-__device__ __forceinline__ float rsqrt_approx(float s2)
-{
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(s2));
-    return y;
-}
-
 // 1/sqrt(s2) in double: single-precision seed refined by two Newton steps
 // y <- y (3/2 - s2/2 y^2) (quadratic convergence: ~2^-22 -> 2^-44 -> round-off).
 __device__ __forceinline__ double rsqrt_f64(double s2)
@@ -1690,12 +1679,12 @@ cudaError_t launch_pass2(pn_ctx *c)
 }
 
 template <int P, int UNROLL>
-static cudaError_t launch_fused_p(pn_ctx *c, const Layout &L)
+static cudaError_t launch_fused_p(pn_ctx *c, const Layout &L, const float4 *rec)
 {
     cudaEvent_t end = nullptr;
     timing_begin(c, 1, &end);
     k_fused_mixed<P, UNROLL><<<(unsigned)c->fused_grid, kMixThreads, 0, c->stream>>>(
-        c->mrec, c->S, c->d_clu, c->nclu, c->fused_units, c->part + L.seg);
+        rec, c->S, c->d_clu, c->nclu, c->fused_units, c->part + L.seg);
     c->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (end)
@@ -1710,12 +1699,12 @@ static cudaError_t launch_fused_p(pn_ctx *c, const Layout &L)
 }
 
 template <int NP, int UNROLL>
-static cudaError_t launch_packed_u(pn_ctx *c, const Layout &L)
+static cudaError_t launch_packed_u(pn_ctx *c, const Layout &L, const float4 *rec)
 {
     cudaEvent_t end = nullptr;
     timing_begin(c, 1, &end);
     k_fused_packed<NP, UNROLL><<<(unsigned)c->fused_grid, kMixThreads, 0, c->stream>>>(
-        c->mrec, c->S, c->d_clu, c->nclu, c->fused_units, c->fused_G, c->wcount, c->part + L.seg);
+        rec, c->S, c->d_clu, c->nclu, c->fused_units, c->fused_G, c->wcount, c->part + L.seg);
     c->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (end)
@@ -1731,25 +1720,44 @@ static cudaError_t launch_packed_u(pn_ctx *c, const Layout &L)
 
 // Fused-kernel variants: scalar (targets per thread 1, 2, 4) or packed
 // FP32x2 (4 targets per thread) x source-loop unroll.
-cudaError_t launch_fused(pn_ctx *c)
+static cudaError_t launch_fused_with(pn_ctx *c, const Layout &L, const float4 *r)
 {
-    const Layout L = layout(c);
     const int u = c->fused_unroll;
     if (c->fused_packed) {
         if (c->fused_P == 2)
-            return u == 2 ? launch_packed_u<1, 2>(c, L) : launch_packed_u<1, 1>(c, L);
-        return u == 2 ? launch_packed_u<2, 2>(c, L) : launch_packed_u<2, 1>(c, L);
+            return u == 2 ? launch_packed_u<1, 2>(c, L, r) : launch_packed_u<1, 1>(c, L, r);
+        return u == 2 ? launch_packed_u<2, 2>(c, L, r) : launch_packed_u<2, 1>(c, L, r);
     }
     switch (c->fused_P) {
-    case 1: return u == 2 ? launch_fused_p<1, 2>(c, L) : launch_fused_p<1, 1>(c, L);
+    case 1: return u == 2 ? launch_fused_p<1, 2>(c, L, r) : launch_fused_p<1, 1>(c, L, r);
     case 4:
-        return u == 4 ? launch_fused_p<4, 4>(c, L)
-             : u == 3 ? launch_fused_p<4, 3>(c, L)
-             : u == 2 ? launch_fused_p<4, 2>(c, L) : launch_fused_p<4, 1>(c, L);
+        return u == 4 ? launch_fused_p<4, 4>(c, L, r)
+             : u == 3 ? launch_fused_p<4, 3>(c, L, r)
+             : u == 2 ? launch_fused_p<4, 2>(c, L, r) : launch_fused_p<4, 1>(c, L, r);
     default:
-        return u == 4 ? launch_fused_p<2, 4>(c, L)
-             : u == 2 ? launch_fused_p<2, 2>(c, L) : launch_fused_p<2, 1>(c, L);
+        return u == 4 ? launch_fused_p<2, 4>(c, L, r)
+             : u == 2 ? launch_fused_p<2, 2>(c, L, r) : launch_fused_p<2, 1>(c, L, r);
     }
+}
+
+cudaError_t launch_fused(pn_ctx *c) { return launch_fused_with(c, layout(c), c->mrec); }
+
+// The fused pair kernel on caller-built mixed records (same layout as the
+// prologue's), with the fused partial layout whatever the context's pair
+// kernel: the 16 pair sums land in c->part as [value][slot] (pass-1 values,
+// then pass-2 values).  Zeroes the packed kernel's worker counter first.
+cudaError_t launch_fused_on(pn_ctx *c, const float4 *rec)
+{
+    Layout L;
+    L.js = 1;
+    L.p1 = 0;
+    L.p2 = (int64_t)kP1Vals * c->S;
+    L.near = (int64_t)(kP1Vals + kP2Vals) * c->S;
+    L.seg = L.near + (int64_t)kNearVals * c->S;
+    cudaError_t e = cudaMemsetAsync(c->wcount, 0, sizeof(int), c->stream);
+    if (e != cudaSuccess)
+        return e;
+    return launch_fused_with(c, L, rec);
 }
 
 // The fused kernels hold 64-75 KB of shared memory per block; three blocks

@@ -90,6 +90,36 @@ def test_accel_vjp_larger_cluster_random_projections(orc):
         assert abs(lhs - rhs) <= 1e-9 * abs(rhs), (lhs, rhs)
 
 
+def test_accel_vjp_mixed_context(orc):
+    """Mixed contexts run the reverse pair sweeps in single precision (hi/lo
+    positions): the VJP stays within 1e-5 of the oracle's exact one."""
+    x, v, m = make_cluster(700, 0.1, 73)
+    x[3] = x[0] + np.array([0.004, 0.001, 0.0])        # a star close to the hole
+    c, eps = 15.0, 1e-3
+    rng = np.random.default_rng(19)
+    abar = rng.normal(size=x.shape)
+    ctx = pn.pn_init(700, c=c, eps=eps, precision="mixed", device=0)
+    XB, VB = torch.empty((700, 3), dtype=torch.float64, device=DEV), torch.empty(
+        (700, 3), dtype=torch.float64, device=DEV)
+    scal = pn.pn_accel_vjp(ctx, dev(x), dev(v), dev(m), dev(abar), XB, VB)
+    ctx.close()
+    xb, vb = XB.cpu().numpy(), VB.cpu().numpy()
+    for trial in range(3):
+        u, w = rng.normal(size=x.shape), rng.normal(size=x.shape)
+        dM, dc2 = rng.normal(), 1e-3 * rng.normal()
+        lhs = np.sum(xb * u) + np.sum(vb * w) + scal[0, 0] * dM + scal[0, 1] * dc2
+        rhs = np.sum(abar * orc.accel_jvp(x, v, m, u, w, dM, dc2, c=c, eps=eps))
+        assert abs(lhs - rhs) <= 1e-5 * abs(rhs), (lhs, rhs)
+    # per-body cotangents against the FP64 context
+    ctx = pn.pn_init(700, c=c, eps=eps, precision="fp64", device=0)
+    XB2, VB2 = torch.empty_like(XB), torch.empty_like(VB)
+    pn.pn_accel_vjp(ctx, dev(x), dev(v), dev(m), dev(abar), XB2, VB2)
+    ctx.close()
+    xb2 = XB2.cpu().numpy()
+    err = np.linalg.norm(xb - xb2, axis=1) / np.linalg.norm(xb2, axis=1)
+    assert np.median(err) <= 1e-6 and err.max() <= 1e-4, (np.median(err), err.max())
+
+
 def oracle_step_grad(orc, x, v, m, dt, nst, xbT, vbT, c, eps, vel_mode=0):
     n = len(m)
     gx, gv = np.zeros((n, 3)), np.zeros((n, 3))
@@ -200,3 +230,45 @@ def test_autograd_trajectory_loss_of_the_nearest_stars():
     gx = (L(0.1, 50.0, e) - L(0.1, 50.0, -e)) / (2 * h)
     assert abs(X0.grad[j, 0].item() - gx) <= 1e-5 * abs(gx), (X0.grad[j, 0].item(), gx)
     ctx.close()
+
+
+def test_adjoint_workload_gradient_matches_central_difference():
+    """The adjoint workload (N = 8192 Plummer, M = 0.1, c = 50, dt = 1/2048),
+    300 steps: dL/dM of the 16 nearest stars' |x(T)|^2, checkpointed adjoint
+    on the FP64 path and on the mixed path, against an FP64 central
+    difference (h = 1e-7; larger h carries visible curvature this late in a
+    collisional run)."""
+    from paper_1801_07986_b300.inputs import WORKLOADS
+    w = WORKLOADS["plummer8k_adjoint"]
+    x, v, m = w.state()
+    near = np.argsort(np.linalg.norm(x[1:] - x[0], axis=1))[:16] + 1
+    nst = 300
+    grads = {}
+    for prec in ("fp64", "mixed"):
+        ctx = pn.pn_init(w.n, c=w.c, eps=w.eps, precision=prec, device=0)
+        X, V, M = dev(x), dev(v), dev(m)
+        A = torch.empty_like(X)
+        pn.pn_accel(ctx, X, V, M, A)
+        pn.pn_step(ctx, X, V, M, A, w.dt, nst)
+        xbT = torch.zeros_like(X)
+        xbT[near] = 2.0 * X[near]
+        XB, VB = torch.empty_like(X), torch.empty_like(X)
+        grads[prec] = pn.pn_step_vjp(ctx, dev(x), dev(v), dev(m), w.dt, nst, xbT,
+                                     torch.zeros_like(X), XB, VB)[0, 0]
+        ctx.close()
+    ctx = pn.pn_init(w.n, c=w.c, eps=w.eps, precision="fp64", device=0)
+
+    def L(Mv):
+        mm = m.copy()
+        mm[0] = Mv
+        X, V, M = dev(x), dev(v), dev(mm)
+        A = torch.empty_like(X)
+        pn.pn_accel(ctx, X, V, M, A)
+        pn.pn_step(ctx, X, V, M, A, w.dt, nst)
+        return float((X.cpu().numpy()[near] ** 2).sum())
+
+    h = 1e-7
+    fd = (L(w.m_bh + h) - L(w.m_bh - h)) / (2 * h)
+    ctx.close()
+    assert abs(grads["fp64"] - fd) <= 1e-6 * abs(fd), (grads["fp64"], fd)
+    assert abs(grads["mixed"] - fd) <= 1e-5 * abs(fd), (grads["mixed"], fd)
