@@ -167,8 +167,8 @@ pn_status pn_accel(pn_ctx *ctx, const double *x, const double *v, const double *
  *            v_e = v + dt/2 (a + a_1) + dt^2/12 (j - j_1),
  *            x_e = x + dt/2 (v + v_e) + dt^2/12 (a - a_1)
  *   ((x_e, v_e) = (x_p, v_p) in the first pass), and (x, v, a, j) =
- *   (x_e, v_e, a_1, j_1); after the last step a = A(x, v).  The jerk is
- *   always evaluated in double precision.
+ *   (x_e, v_e, a_1, j_1); after the last step a = A(x, v).  The jerk's
+ *   precision follows pn_jerk.
  * `a` is carried state: on entry it must hold the acceleration of the entry
  * state (call pn_accel once before the first pn_step); on return it holds
  * the acceleration of the final state.  Device pointers.
@@ -181,9 +181,10 @@ pn_status pn_step(pn_ctx *ctx, double *x, double *v, const double *m, double *a,
  * The jerk (Appendix A): writes a = A(x, v) (the context's precision) and
  * jerk = dA/dt along the trajectory, sum_k [dA/dx_k . v_k + dA/dv_k . a_k],
  * for every body, n x 3 each.  The derivative is taken in forward mode
- * (dual numbers) of the same decomposition the acceleration kernels use, in
- * double precision whatever the context's precision, with no near-source
- * split.  Device pointers; a and jerk must not alias x, v or m.  Allocates
+ * (dual numbers) of the same decomposition the acceleration kernels use,
+ * with no near-source split: in double precision in PN_FP64 contexts; in
+ * PN_MIXED contexts the dual pair sums run in single precision (hi/lo
+ * positions) and everything O(n) in double.  Device pointers; a and jerk must not alias x, v or m.  Allocates
  * its scratch on the first call.  Errors: PN_EINVAL (NULL pointer),
  * PN_ENOMEM, PN_ECUDA; a non-finite jerk is reported by pn_sync as
  * PN_ENONFINITE.

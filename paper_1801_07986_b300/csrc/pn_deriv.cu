@@ -218,6 +218,147 @@ k_dual_pairs(const double4_32a *__restrict__ rec, int64_t S, const Clu *__restri
     }
 }
 
+// --------------------------------------------- jerk: single precision --
+//
+// The dual pair sums in FP32 for mixed-precision contexts (the jerk only
+// enters Hermite's predictor and corrector with dt^2 and dt^3 weights, so
+// single-precision pair terms are enough): value and derivative of every
+// pair term on float duals, x_ij's value from hi/lo splits of the
+// hole-relative positions, tile partials folded into FP64.  Same output
+// layout as k_dual_pairs<Dual>.  Records (float4 per slot, from the FP64
+// dual records): F0 = (hi d, m)  F1 = (lo d, R^2)  F2 = (d', (R^2)')
+// F3 = (v, C)  F4 = (v', C')  F5 = (-e/1.5, 0)  F6 = (-(e/1.5)', 0)
+// F7 = (w, 0)  F8 = (w', 0).
+
+constexpr int kJRecF = 9;
+constexpr int kJTileF = 64;
+
+struct DualF {
+    float v, d;
+};
+__device__ __forceinline__ DualF operator+(DualF a, DualF b) { return {a.v + b.v, a.d + b.d}; }
+__device__ __forceinline__ DualF operator-(DualF a, DualF b) { return {a.v - b.v, a.d - b.d}; }
+__device__ __forceinline__ DualF operator*(DualF a, DualF b)
+{
+    return {a.v * b.v, fmaf(a.d, b.v, a.v * b.d)};
+}
+__device__ __forceinline__ DualF operator*(float s, DualF a) { return {s * a.v, s * a.d}; }
+__device__ __forceinline__ DualF &operator+=(DualF &a, DualF b)
+{
+    a.v += b.v;
+    a.d += b.d;
+    return a;
+}
+
+__global__ void __launch_bounds__(kGlueThreads)
+k_jerk_frec(int64_t S, const double4_32a *__restrict__ rec, float4 *__restrict__ frec)
+{
+    const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
+    if (t >= S)
+        return;
+    const double4_32a J0 = rec[t], J1 = rec[S + t], J2 = rec[2 * S + t], J3 = rec[3 * S + t];
+    const double4_32a J4 = rec[4 * S + t], J5 = rec[5 * S + t], J6 = rec[6 * S + t],
+                      J7 = rec[7 * S + t];
+    const float h0 = (float)J0.x, h1 = (float)J0.y, h2 = (float)J0.z;
+    frec[t] = make_float4(h0, h1, h2, (float)J0.w);
+    frec[S + t] = make_float4((float)(J0.x - (double)h0), (float)(J0.y - (double)h1),
+                              (float)(J0.z - (double)h2), (float)J2.w);
+    frec[2 * S + t] = make_float4((float)J1.x, (float)J1.y, (float)J1.z, (float)J3.w);
+    frec[3 * S + t] = make_float4((float)J2.x, (float)J2.y, (float)J2.z, (float)J4.w);
+    frec[4 * S + t] = make_float4((float)J3.x, (float)J3.y, (float)J3.z, (float)J5.w);
+    frec[5 * S + t] = make_float4((float)J4.x, (float)J4.y, (float)J4.z, 0.0f);
+    frec[6 * S + t] = make_float4((float)J5.x, (float)J5.y, (float)J5.z, 0.0f);
+    frec[7 * S + t] = make_float4((float)J6.x, (float)J6.y, (float)J6.z, 0.0f);
+    frec[8 * S + t] = make_float4((float)J7.x, (float)J7.y, (float)J7.z, 0.0f);
+}
+
+__global__ void __launch_bounds__(kJThreads)
+k_dual_pairs_f(const float4 *__restrict__ frec, int64_t S, const Clu *__restrict__ clu,
+               const int *__restrict__ blk_clu, double *__restrict__ part)
+{
+    __shared__ float4 sh[kJRecF][kJTileF];
+    const int64_t t0 = (int64_t)blockIdx.x * kJThreads;
+    const Clu C = clu[cluster_of_block(blk_clu, t0 / kGlueThreads)];
+    const int ntiles = (int)(C.ns_pad / kJTileF);
+    const int tps = (ntiles + (int)gridDim.y - 1) / (int)gridDim.y;
+    const int64_t ti = t0 + threadIdx.x;
+    const float4 T0 = frec[ti], T1 = frec[S + ti], T2 = frec[2 * S + ti], T3 = frec[3 * S + ti],
+                 T4 = frec[4 * S + ti];
+    const float hi[3] = {T0.x, T0.y, T0.z}, lo[3] = {T1.x, T1.y, T1.z};
+    const DualF di[3] = {{T0.x + T1.x, T2.x}, {T0.y + T1.y, T2.y}, {T0.z + T1.z, T2.z}};
+    const float e3 = 8.0f / 3.0f;
+    const DualF vi[3] = {{e3 * T3.x, e3 * T4.x}, {e3 * T3.y, e3 * T4.y}, {e3 * T3.z, e3 * T4.z}};
+    const float eps2 = (float)C.eps2;
+    double acc[2 * kFusedVals];
+#pragma unroll
+    for (int k = 0; k < 2 * kFusedVals; ++k)
+        acc[k] = 0.0;
+    const int tb = blockIdx.y * tps;
+    const int te = min(ntiles, tb + tps);
+    for (int tile = tb; tile < te; ++tile) {
+        const int64_t j0 = C.slot0 + (int64_t)tile * kJTileF;
+        __syncthreads();
+        for (int q = threadIdx.x; q < kJRecF * kJTileF; q += kJThreads)
+            sh[q / kJTileF][q % kJTileF] = frec[(q / kJTileF) * S + j0 + q % kJTileF];
+        __syncthreads();
+        DualF p[kFusedVals];
+#pragma unroll
+        for (int k = 0; k < kFusedVals; ++k)
+            p[k] = {0.0f, 0.0f};
+#pragma unroll 1
+        for (int q = 0; q < kJTileF; ++q) {
+            if (j0 + q == ti)
+                continue;
+            const float4 A0 = sh[0][q], A1 = sh[1][q], A2 = sh[2][q], A3 = sh[3][q];
+            const float4 A4 = sh[4][q], A5 = sh[5][q], A6 = sh[6][q], A7 = sh[7][q],
+                         A8 = sh[8][q];
+            const DualF xx[3] = {{(hi[0] - A0.x) + (lo[0] - A1.x), di[0].d - A2.x},
+                                 {(hi[1] - A0.y) + (lo[1] - A1.y), di[1].d - A2.y},
+                                 {(hi[2] - A0.z) + (lo[2] - A1.z), di[2].d - A2.z}};
+            const DualF vj[3] = {{A3.x, A4.x}, {A3.y, A4.y}, {A3.z, A4.z}};
+            DualF s2 = xx[0] * xx[0] + xx[1] * xx[1] + xx[2] * xx[2];
+            s2.v += eps2;
+            const float y = rsqrt_approx(s2.v);
+            const DualF is = {y, -0.5f * y * y * y * s2.d};
+            const DualF is2 = is * is;
+            const DualF mis = A0.w * is;
+            const DualF mis3 = mis * is2;
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                p[k] += mis3 * xx[k];
+            p[3] += mis;
+            p[4] += mis3;
+            p[5] += mis3 * DualF{A1.w, A2.w};
+            const DualF xvj = xx[0] * vj[0] + xx[1] * vj[1] + xx[2] * vj[2];
+            const DualF xvi = xx[0] * vi[0] + xx[1] * vi[1] + xx[2] * vi[2];
+            const DualF kk = DualF{A3.w, A4.w} + (vi[0] * vj[0] + vi[1] * vj[1] + vi[2] * vj[2]) +
+                             (DualF{A5.x, A6.x} * di[0] + DualF{A5.y, A6.y} * di[1] +
+                              DualF{A5.z, A6.z} * di[2]);
+            const DualF f = mis3 * (xvj * is2 * xvj + kk);
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                p[6 + k] += f * xx[k];
+            const DualF gg = mis3 * (xvi - 2.0f * xvj);
+            p[9] += gg;
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                p[10 + k] += gg * vj[k];
+            p[13] += DualF{A7.x, A8.x} * is;
+            p[14] += DualF{A7.y, A8.y} * is;
+            p[15] += DualF{A7.z, A8.z} * is;
+        }
+#pragma unroll
+        for (int k = 0; k < kFusedVals; ++k) {
+            acc[2 * k] += (double)p[k].v;
+            acc[2 * k + 1] += (double)p[k].d;
+        }
+    }
+    double *out = part + (int64_t)blockIdx.y * 2 * kFusedVals * S;
+#pragma unroll
+    for (int k = 0; k < 2 * kFusedVals; ++k)
+        out[(int64_t)k * S + ti] = acc[k];
+}
+
 // Per star: the split partials summed, star_eqs on Duals; the value is the
 // acceleration and the derivative the jerk.  Per-block sums of the hole's
 // terms (3 values, 3 derivatives) go to blk.
@@ -975,7 +1116,7 @@ k_adj_kdk(int stage, int64_t n3, int vel_mode, double dt, const double *__restri
 }  // namespace
 
 // Buffers: rec 8 x S double4, part js x 32 x S, blk (S/256) x 24, glob
-// nclu x 24, hole terms (S/256) x 6.
+// nclu x 24, hole terms (S/256) x 6, float records 9 x S float4.
 int64_t jerk_part_splits(const pn_ctx *c)
 {
     const int64_t nb = c->S / kJThreads;
@@ -989,7 +1130,8 @@ size_t jerk_buffer_doubles(const pn_ctx *c)
 {
     const int64_t S = c->S, nglue = S / kGlueThreads;
     return (size_t)(kJRec * 4 * S + jerk_part_splits(c) * 2 * kFusedVals * S +
-                    nglue * 2 * kJVals + (int64_t)c->nclu * 2 * kJVals + nglue * 6);
+                    nglue * 2 * kJVals + (int64_t)c->nclu * 2 * kJVals + nglue * 6 +
+                    18 * S);   // + float records of the single-precision pass (9 float4)
 }
 
 cudaError_t launch_jerk(pn_ctx *c, const double *x, const double *v, const double *m,
@@ -1016,8 +1158,16 @@ cudaError_t launch_jerk(pn_ctx *c, const double *x, const double *v, const doubl
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
     dim3 grid((unsigned)(S / kJThreads), (unsigned)js);
-    k_dual_pairs<Dual><<<grid, kJThreads, 0, c->stream>>>(rec, S, c->d_clu, bc, part);
-    c->launches += 1;
+    if (c->p.precision == PN_MIXED) {
+        // single-precision dual pair sums on float records (after the hole terms)
+        float4 *frec = reinterpret_cast<float4 *>(bhb + nglue * 6);
+        k_jerk_frec<<<(unsigned)nglue, kGlueThreads, 0, c->stream>>>(S, rec, frec);
+        k_dual_pairs_f<<<grid, kJThreads, 0, c->stream>>>(frec, S, c->d_clu, bc, part);
+        c->launches += 2;
+    } else {
+        k_dual_pairs<Dual><<<grid, kJThreads, 0, c->stream>>>(rec, S, c->d_clu, bc, part);
+        c->launches += 1;
+    }
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
     k_jerk_epilogue<<<(unsigned)nglue, kGlueThreads, 0, c->stream>>>(

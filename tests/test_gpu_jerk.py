@@ -76,10 +76,22 @@ def test_jerk_strong_field_and_near_hole(orc):
     assert rel(j_want, jn).max() > 1e-2          # the 1PN jerk matters here
     _, j = gpu_jerk(x, v, m, c=c, eps=1e-4)
     assert rel(j, j_want).max() <= JERK_TOL
-    # mixed context: a in mixed precision, jerk in FP64 along that a
+    # mixed context: a in mixed precision, the jerk's pair sums in FP32 (the
+    # jerk enters Hermite's predictor and corrector with dt^2, dt^3 weights)
     a_mix, j_mix = gpu_jerk(x, v, m, precision="mixed", c=c, eps=1e-4)
     assert np.median(rel(a_mix, a_want)) <= 2e-7
-    assert rel(j_mix, j_want).max() <= 1e-5
+    err = rel(j_mix, j_want)
+    assert np.median(err) <= 2e-5 and err.max() <= 1e-3, (np.median(err), err.max())
+
+
+def test_jerk_mixed_plummer16k_against_fp64():
+    from paper_1801_07986_b300.inputs import WORKLOADS
+    w = WORKLOADS["plummer16k"]
+    x, v, m = w.state()
+    _, j64 = gpu_jerk(x, v, m, precision="fp64", c=w.c, eps=w.eps)
+    _, jm = gpu_jerk(x, v, m, precision="mixed", c=w.c, eps=w.eps)
+    err = rel(jm, j64)
+    assert np.median(err) <= 1e-6 and err.max() <= 1e-4, (np.median(err), err.max())
 
 
 def test_jerk_batched_per_cluster(orc):
