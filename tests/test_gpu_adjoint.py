@@ -272,3 +272,28 @@ def test_adjoint_workload_gradient_matches_central_difference():
     ctx.close()
     assert abs(grads["fp64"] - fd) <= 1e-6 * abs(fd), (grads["fp64"], fd)
     assert abs(grads["mixed"] - fd) <= 1e-5 * abs(fd), (grads["mixed"], fd)
+
+
+def test_error_paths():
+    x, v, m = state(40, 900)
+    X, V, M = dev(x), dev(v), dev(m)
+    XB, VB = torch.empty_like(X), torch.empty_like(X)
+    ctx = pn.pn_init(40, c=10.0, eps=1e-2, precision="fp64", integrator="rk4", device=0)
+    with pytest.raises(pn.PNError) as e:
+        pn.pn_step_vjp(ctx, X, V, M, 1e-3, 3, XB, VB, XB.clone(), VB.clone())
+    assert "PN_EUNSUPPORTED" in str(e.value)
+    with pytest.raises(pn.PNError) as e:
+        pn.pn_accel_vjp(ctx, X, V, M, X, X, VB)           # xbar aliases x
+    assert "PN_EINVAL" in str(e.value)
+    with pytest.raises(pn.PNError) as e:
+        pn.pn_jerk(ctx, X, V, M, XB, XB)                  # a aliases jerk
+    assert "PN_EINVAL" in str(e.value)
+    ctx.close()
+    # zero steps: the gradient of the entry state is the cotangent itself
+    # plus the entry acceleration's (zero) contribution
+    ctx = pn.pn_init(40, c=10.0, eps=1e-2, precision="fp64", device=0)
+    xbT, vbT = dev(np.ones((40, 3))), dev(2 * np.ones((40, 3)))
+    scal = pn.pn_step_vjp(ctx, X, V, M, 1e-3, 0, xbT, vbT, XB, VB)
+    assert torch.equal(XB, xbT) and torch.equal(VB, vbT)
+    assert np.all(scal == 0.0)
+    ctx.close()
