@@ -297,3 +297,32 @@ def test_error_paths():
     assert torch.equal(XB, xbT) and torch.equal(VB, vbT)
     assert np.all(scal == 0.0)
     ctx.close()
+
+
+def test_step_vjp_batched_per_cluster(orc):
+    """Batched context: one pn_step_vjp over three clusters with their own c
+    and eps; each cluster's gradient (positions, velocities, its hole mass and
+    1/c^2) equals the oracle's for that cluster alone."""
+    sizes, cs, es = [9, 14, 6], [6.0, 9.0, 15.0], [1e-2, 2e-2, 5e-3]
+    parts = [state(n, 950 + k, m_bh=0.2 + 0.1 * k) for k, n in enumerate(sizes)]
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    x = np.concatenate([p[0] for p in parts])
+    v = np.concatenate([p[1] for p in parts])
+    m = np.concatenate([p[2] for p in parts])
+    n, nst, dt = off[-1], 6, 1.0 / 128
+    rng = np.random.default_rng(23)
+    xbT, vbT = rng.normal(size=(n, 3)), rng.normal(size=(n, 3))
+    ctx = pn.pn_init_batched(off, c=cs, eps=es, precision="fp64", device=0)
+    XB, VB = torch.empty((n, 3), dtype=torch.float64, device=DEV), torch.empty(
+        (n, 3), dtype=torch.float64, device=DEV)
+    scal = pn.pn_step_vjp(ctx, dev(x), dev(v), dev(m), dt, nst, dev(xbT), dev(vbT), XB, VB,
+                          checkpoint=4)
+    ctx.close()
+    xb, vb = XB.cpu().numpy(), VB.cpu().numpy()
+    for k, (a, b) in enumerate(zip(off[:-1], off[1:])):
+        want = oracle_step_grad(orc, x[a:b], v[a:b], m[a:b], dt, nst, xbT[a:b], vbT[a:b], cs[k],
+                                es[k])
+        assert np.abs(xb[a:b] - want[0]).max() <= 1e-9 * np.abs(want[0]).max()
+        assert np.abs(vb[a:b] - want[1]).max() <= 1e-9 * np.abs(want[1]).max()
+        assert abs(scal[k, 0] - want[2]) <= 1e-9 * abs(want[2])
+        assert abs(scal[k, 1] - want[3]) <= 1e-9 * abs(want[3])

@@ -189,3 +189,25 @@ def test_hermite_is_more_accurate_than_kdk():
         assert np.abs(xh - xr).max() < 1e-3 * np.abs(xk - xr).max()
         if math.isinf(c):
             assert eh < 1e-2 * ek, (eh, ek)
+
+
+def test_hermite_batched_per_cluster(orc):
+    sizes, cs, es = [200, 77, 513], [10.0, 20.0, 40.0], [1e-3, 2e-3, 5e-4]
+    parts = [cluster(s, 0.05 + 0.05 * k, 620 + k) for k, s in enumerate(sizes)]
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    X = dev(np.concatenate([p[0] for p in parts]))
+    V = dev(np.concatenate([p[1] for p in parts]))
+    M = dev(np.concatenate([p[2] for p in parts]))
+    ctx = pn.pn_init_batched(off, c=cs, eps=es, precision="fp64", integrator="hermite", device=0)
+    A = torch.empty_like(X)
+    dt, nst = 1.0 / 1024, 4
+    pn.pn_accel(ctx, X, V, M, A)
+    pn.pn_step(ctx, X, V, M, A, dt, nst)
+    pn.pn_sync(ctx)
+    xg = X.cpu().numpy()
+    for k, (a, b) in enumerate(zip(off[:-1], off[1:])):
+        x, v, m = parts[k]
+        a0 = orc.accel(x, v, m, c=cs[k], eps=es[k])
+        xo, _, _ = orc.hermite_step(x, v, m, a0, dt, nst, c=cs[k], eps=es[k])
+        assert np.abs(xg[a:b] - xo).max() <= 1e-11 * np.abs(xo).max()
+    ctx.close()
