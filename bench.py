@@ -33,6 +33,7 @@ import math
 import os
 import re
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -99,7 +100,9 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{index}.csv")
+        # the raw samples: $PN_BENCH_CLOCKS_DIR (default: the system temp dir)
+        d = os.environ.get("PN_BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"pn_bench_clocks_gpu{index}.csv")
 
     def __enter__(self):
         try:
