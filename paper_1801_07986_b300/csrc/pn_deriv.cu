@@ -555,6 +555,10 @@ __device__ __forceinline__ void pair_adj(const double (&di)[3], const double (&v
 // cotangent abar.  Outputs: the sums' cotangents sbar[16][slot], the direct
 // cotangents of d_i and of the velocity kbar[6][slot], and per block the
 // cotangents of the cluster sums, of M and of inv_c2 (kAdjGlob values).
+// One warp per star slot: lane q evaluates the dual seeds q and q + 32 of
+// the 33 inputs, so the O(n) reverse keeps every SM busy.
+constexpr int kAdjStarWarps = kGlueThreads / 32;    // star slots per block
+
 __global__ void __launch_bounds__(kGlueThreads)
 k_adj_star(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_clu,
            const double *__restrict__ x, const double *__restrict__ v,
@@ -562,51 +566,46 @@ k_adj_star(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
            const double *__restrict__ globs, const double *__restrict__ abar,
            double *__restrict__ sbar, double *__restrict__ kbar, double *__restrict__ blk)
 {
-    __shared__ double sh[kAdjGlob][kGlueThreads];
-    const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
-    const int k_clu = cluster_of_block(blk_clu, blockIdx.x);
+    __shared__ double su[kAdjStarWarps][33];     // the star's inputs
+    __shared__ double sub[kAdjStarWarps][34];    // their cotangents (+ the hole's inv_c2 term)
+    const int wi = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int64_t t = (int64_t)blockIdx.x * kAdjStarWarps + wi;
+    const int k_clu = cluster_of_block(blk_clu, t / kGlueThreads);
     const Clu Cl = clu[k_clu];
     const double *glob = globs + (int64_t)k_clu * 2 * kJVals;
     const int64_t lt = t - Cl.slot0;
-    double g[kAdjGlob];
-    for (int k = 0; k < kAdjGlob; ++k)
-        g[k] = 0.0;
-    double sb_out[kFusedVals], kb_out[6];
-    for (int k = 0; k < kFusedVals; ++k)
-        sb_out[k] = 0.0;
-    for (int k = 0; k < 6; ++k)
-        kb_out[k] = 0.0;
-    if (lt < Cl.ns) {
-        const int64_t i = Cl.body0 + 1 + lt, hb = Cl.body0;
-        double u[33];
-        for (int k = 0; k < 3; ++k) {
-            u[k] = x[3 * i + k] - x[3 * hb + k];
-            u[3 + k] = v[3 * i + k];
+    const bool star = lt < Cl.ns;
+    const int64_t i = Cl.body0 + 1 + lt, hb = Cl.body0;
+    if (star) {
+        if (lane < 3) {
+            su[wi][lane] = x[3 * i + lane] - x[3 * hb + lane];
+            su[wi][3 + lane] = v[3 * i + lane];
+            su[wi][22 + lane] = glob[2 * lane];            // Q
+            su[wi][25 + lane] = glob[2 * (6 + lane)];      // W_far (= W: far form)
         }
-        for (int k = 0; k < kFusedVals; ++k) {
+        if (lane < kFusedVals) {
             double sv = 0.0;
             for (int q = 0; q < js; ++q)
-                sv += part[((int64_t)q * kFusedVals + k) * S + t];
-            u[6 + k] = sv;
+                sv += part[((int64_t)q * kFusedVals + lane) * S + t];
+            su[wi][6 + lane] = sv;
         }
-        for (int k = 0; k < 3; ++k) {
-            u[22 + k] = glob[2 * k];            // Q
-            u[25 + k] = glob[2 * (6 + k)];      // W_far (= W: far form)
+        if (lane == 0) {
+            su[wi][28] = glob[18];
+            su[wi][29] = glob[20];
+            su[wi][30] = glob[22];
+            su[wi][31] = m[hb];
+            su[wi][32] = Cl.inv_c2;
         }
-        u[28] = glob[18];
-        u[29] = glob[20];
-        u[30] = glob[22];
-        u[31] = m[hb];
-        u[32] = Cl.inv_c2;
+    }
+    __syncwarp();
+    if (star) {
         const double ab[3] = {abar[3 * i], abar[3 * i + 1], abar[3 * i + 2]};
         const double bb[3] = {Cl.inv_c2 * abar[3 * hb], Cl.inv_c2 * abar[3 * hb + 1],
                               Cl.inv_c2 * abar[3 * hb + 2]};
-        double ub[33];
-        double bh_val[3] = {0.0, 0.0, 0.0};
-        for (int q = 0; q < 33; ++q) {
+        for (int q = lane; q < 33; q += 32) {
             Dual w[33];
             for (int k = 0; k < 33; ++k)
-                w[k] = dual(u[k], k == q ? 1.0 : 0.0);
+                w[k] = dual(su[wi][k], k == q ? 1.0 : 0.0);
             Dual d[3] = {w[0], w[1], w[2]}, vv[3] = {w[3], w[4], w[5]};
             StarSums<Dual> ss;
             for (int k = 0; k < 3; ++k) {
@@ -634,28 +633,30 @@ k_adj_star(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
             double acc = 0.0;
             for (int k = 0; k < 3; ++k)
                 acc += ab[k] * ai[k].d + bb[k] * bh[k].d;
-            ub[q] = acc;
-            if (q == 0)
-                for (int k = 0; k < 3; ++k)
-                    bh_val[k] = bh[k].v;
+            sub[wi][q] = acc;
+            if (q == 0)   // the hole's inv_c2 term: abar_hole . (star i's term)
+                sub[wi][33] = abar[3 * hb] * bh[0].v + abar[3 * hb + 1] * bh[1].v +
+                              abar[3 * hb + 2] * bh[2].v;
         }
-        for (int k = 0; k < kFusedVals; ++k)
-            sb_out[k] = ub[6 + k];
-        for (int k = 0; k < 6; ++k)
-            kb_out[k] = ub[k];
-        for (int k = 0; k < 9; ++k)
-            g[k] = ub[22 + k];
-        g[9] = ub[31];
-        g[10] = ub[32] + (abar[3 * hb] * bh_val[0] + abar[3 * hb + 1] * bh_val[1] +
-                          abar[3 * hb + 2] * bh_val[2]);
     }
-    for (int k = 0; k < kFusedVals; ++k)
-        sbar[(int64_t)k * S + t] = sb_out[k];
-    for (int k = 0; k < 6; ++k)
-        kbar[(int64_t)k * S + t] = kb_out[k];
-    block_sum<kAdjGlob>(g, sh);
-    if (threadIdx.x < kAdjGlob)
-        blk[(int64_t)blockIdx.x * kAdjGlob + threadIdx.x] = sh[threadIdx.x][0];
+    __syncwarp();
+    if (lane < kFusedVals)
+        sbar[(int64_t)lane * S + t] = star ? sub[wi][6 + lane] : 0.0;
+    if (lane < 6)
+        kbar[(int64_t)lane * S + t] = star ? sub[wi][lane] : 0.0;
+    __syncthreads();
+    // per-block sums over the block's star slots, in slot order
+    if (threadIdx.x < kAdjGlob) {
+        const int k = threadIdx.x;
+        double g = 0.0;
+        for (int w2 = 0; w2 < kAdjStarWarps; ++w2) {
+            const int64_t t2 = (int64_t)blockIdx.x * kAdjStarWarps + w2;
+            if (t2 - Cl.slot0 >= Cl.ns)
+                continue;
+            g += k < 9 ? sub[w2][22 + k] : (k == 9 ? sub[w2][31] : sub[w2][32] + sub[w2][33]);
+        }
+        blk[(int64_t)blockIdx.x * kAdjGlob + k] = g;
+    }
 }
 
 // One block per cluster: its cotangent sums, blocks in a fixed order.
@@ -665,7 +666,7 @@ k_adj_globals(const Clu *__restrict__ clu, const double *__restrict__ blk,
 {
     __shared__ double sh[kAdjGlob][kGlueThreads];
     const Clu C = clu[blockIdx.x];
-    sum_blocks<kAdjGlob>(blk + (C.slot0 / kGlueThreads) * kAdjGlob, C.ns_pad / kGlueThreads, sh);
+    sum_blocks<kAdjGlob>(blk + (C.slot0 / kAdjStarWarps) * kAdjGlob, C.ns_pad / kAdjStarWarps, sh);
     if (threadIdx.x < kAdjGlob)
         gbar[(int64_t)blockIdx.x * kAdjGlob + threadIdx.x] = sh[threadIdx.x][0];
 }
@@ -1182,13 +1183,13 @@ cudaError_t launch_jerk(pn_ctx *c, const double *x, const double *v, const doubl
 }
 
 // Adjoint scratch (doubles): sbar 16 S, kbar 6 S, target partials js 6 S,
-// source partials js 14 S, block cotangents (S/256) 11, cluster cotangents
+// source partials js 14 S, block cotangents (S/8) 11, cluster cotangents
 // nclu 11, hole blocks (S/256) 4.
 size_t adjoint_buffer_doubles(const pn_ctx *c)
 {
     const int64_t S = c->S, nglue = S / kGlueThreads, js = jerk_part_splits(c);
-    return (size_t)((16 + 6) * S + js * (6 + kAdjSrc) * S + nglue * (kAdjGlob + 4) +
-                    (int64_t)c->nclu * kAdjGlob);
+    return (size_t)((16 + 6) * S + js * (6 + kAdjSrc) * S + (S / kAdjStarWarps) * kAdjGlob +
+                    nglue * 4 + (int64_t)c->nclu * kAdjGlob);
 }
 
 cudaError_t launch_accel_vjp(pn_ctx *c, const double *x, const double *v, const double *m,
@@ -1203,7 +1204,7 @@ cudaError_t launch_accel_vjp(pn_ctx *c, const double *x, const double *v, const 
     double *jglob = jblk + nglue * 2 * kJVals;
     double *sbar = c->abuf, *kbar = sbar + 16 * S, *tpart = kbar + 6 * S;
     double *spart = tpart + (int64_t)js * 6 * S, *kblk = spart + (int64_t)js * kAdjSrc * S;
-    double *gbar = kblk + nglue * kAdjGlob, *hblk = gbar + (int64_t)c->nclu * kAdjGlob;
+    double *gbar = kblk + (S / kAdjStarWarps) * kAdjGlob, *hblk = gbar + (int64_t)c->nclu * kAdjGlob;
     const int *bc = c->nclu > 1 ? c->blk_clu : nullptr;
     dim3 grid((unsigned)(S / kJThreads), (unsigned)js);
     const bool mixed = c->p.precision == PN_MIXED;
@@ -1235,7 +1236,7 @@ cudaError_t launch_accel_vjp(pn_ctx *c, const double *x, const double *v, const 
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
     // reverse
-    k_adj_star<<<(unsigned)nglue, kGlueThreads, 0, c->stream>>>(S, c->d_clu, bc, x, v, m, fwd, jsf,
+    k_adj_star<<<(unsigned)(S / kAdjStarWarps), kGlueThreads, 0, c->stream>>>(S, c->d_clu, bc, x, v, m, fwd, jsf,
                                                                jglob, abar, sbar, kbar, kblk);
     k_adj_globals<<<c->nclu, kGlueThreads, 0, c->stream>>>(c->d_clu, kblk, gbar);
     if (mixed) {
