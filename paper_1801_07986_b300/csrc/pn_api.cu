@@ -164,6 +164,8 @@ pn_status report_flag(pn_ctx *c)
         PN_CUDA(cudaMemcpyAsync(c->flag_step, &none, sizeof none, cudaMemcpyHostToDevice,
                                 c->stream), "clear flag step");
         PN_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
+        if (flag & 2)
+            return fail(PN_ETIMEOUT, "a bounded wait for a device copy gave up");
         return fail(PN_ENONFINITE, "non-finite acceleration produced (first at step %llu)", step);
     }
     return PN_OK;
@@ -474,7 +476,8 @@ static pn_status init_common(pn_ctx **out, int nclu, const int64_t *off, const p
         {(void **)&c->rk_a, sizeof(double) * 3 * (size_t)n},
         {(void **)&c->rk_sx, sizeof(double) * 3 * (size_t)n},
         {(void **)&c->rk_sv, sizeof(double) * 3 * (size_t)n},
-        {(void **)&c->mrec, sizeof(float4) * 5 * (size_t)S},
+        // mixed: 5 record arrays + the packed kernel's staged sources (9 per slot)
+        {(void **)&c->mrec, sizeof(float4) * (params->precision == PN_MIXED ? 14 : 5) * (size_t)S},
         {(void **)&c->drec, sizeof(double4_32a) * 4 * (size_t)S},
         {(void **)&c->part, sizeof(double) * (size_t)part},
         {(void **)&c->blk, sizeof(double) * (size_t)c->blk_len},

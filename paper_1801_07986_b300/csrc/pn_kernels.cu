@@ -107,6 +107,25 @@ __global__ void k_rk4_stage(int stage, int64_t n3, double *__restrict__ x, doubl
 
 // ------------------------------------------------------------ prologue --
 
+// Staged source records for k_fused_packed from mixed records rec (5 arrays
+// of S float4: (hi d, m), (lo d, R^2), (v, C), (-e/1.5, 0), (w, 0)):
+// srec[t][0..8] = (-h, -h) pairs of the position split, (m, m), (R^2, R^2),
+// and (f, f) for every other field.
+__device__ __forceinline__ void stage_source(float4 *__restrict__ o, float4 A, float4 B, float4 Cs,
+                                             float4 D, float4 E)
+{
+    o[0] = make_float4(-A.x, -A.x, -A.y, -A.y);
+    o[1] = make_float4(-A.z, -A.z, A.w, A.w);
+    o[2] = make_float4(-B.x, -B.x, -B.y, -B.y);
+    o[3] = make_float4(-B.z, -B.z, B.w, B.w);
+    o[4] = make_float4(Cs.x, Cs.x, Cs.y, Cs.y);
+    o[5] = make_float4(Cs.z, Cs.z, Cs.w, Cs.w);
+    o[6] = make_float4(D.x, D.x, D.y, D.y);
+    o[7] = make_float4(D.z, D.z, E.x, E.x);
+    o[8] = make_float4(E.y, E.y, E.z, E.z);
+}
+
+
 // Per star slot t of cluster k (star j = body0 + 1 + (t - slot0); slots past
 // the cluster's stars are padding):
 //   d_j = x_j - x_hole, R_j = |d_j|,
@@ -130,6 +149,9 @@ k_prologue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
            double4_32a *__restrict__ drec, unsigned char *__restrict__ nflag,
            double *__restrict__ blk, int *__restrict__ wcount)
 {
+    // mixed: the staged source records of the packed pair kernel follow the
+    // five record arrays
+    float4 *__restrict__ srec = mrec + 5 * S;
     __shared__ double sh[kGlobVals][kGlueThreads];
     const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
     if (wcount && t == 0)
@@ -168,6 +190,8 @@ k_prologue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
             mrec[3 * S + t] = make_float4((float)(e3 * d0), (float)(e3 * d1), (float)(e3 * d2), 0.0f);
             mrec[4 * S + t] = make_float4((float)(far * wf * d0), (float)(far * wf * d1),
                                           (float)(far * wf * d2), 0.0f);
+            stage_source(srec + 9 * t, mrec[t], mrec[S + t], mrec[2 * S + t], mrec[3 * S + t],
+                         mrec[4 * S + t]);
         } else if (MODE == 1) {
             drec[t] = make_double4_32a(d0, d1, d2, mj);
             drec[S + t] = make_double4_32a(v0, v1, v2, R2);
@@ -196,9 +220,11 @@ k_prologue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
         // padding: zero mass far away, distinct positions
         const double px = 1.0e4 + (double)(lt - C.ns);
         if (MODE == 0) {
+            const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             mrec[t] = make_float4((float)px, 0.0f, 0.0f, 0.0f);
             for (int k = 1; k < 5; ++k)
-                mrec[k * S + t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                mrec[k * S + t] = z;
+            stage_source(srec + 9 * t, mrec[t], z, z, z, z);
         } else {
             drec[t] = make_double4_32a(px, 0.0, 0.0, 0.0);
             const int nk = MODE == 1 ? 4 : 2;
@@ -781,6 +807,64 @@ __device__ __forceinline__ void packed_tile(const float4 (*__restrict__ sh)[kPac
     }
 }
 
+// ---- bulk-copy staging (TMA engine, mbarrier completion) ----
+constexpr int kTileBytes = kPackTile * kPackVals * 16;   // one staged source tile
+constexpr int kSpinLimit = 1 << 22;                      // try_wait polls before giving up
+constexpr int kFlagTimeout = 2;                          // flag bit: a bounded wait gave up
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Arms the barrier for `bytes` of transaction and starts one bulk copy of
+// `bytes` from global `src` to shared `dst` that completes on it.  Both
+// addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+
+// Waits for the barrier's phase `parity` to complete; false after
+// kSpinLimit unsuccessful polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
+{
+    const uint32_t a = smem_addr(bar);
+    for (int i = 0; i < kSpinLimit; ++i) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done) : "r"(a), "r"(parity) : "memory");
+        if (done)
+            return true;
+    }
+    return false;
+}
+
+// First source slot of stream-K unit u (its cluster's tile of kPackTile
+// sources).
+__device__ __forceinline__ int64_t unit_source(const Clu *__restrict__ clu, int nclu, int64_t u)
+{
+    const Clu C = clu[cluster_of_unit(clu, nclu, u)];
+    const int64_t ntiles = C.ns_pad / kPackTile;
+    const int64_t r = u - C.unit0;
+    return C.slot0 + (r - (r / ntiles) * ntiles) * kPackTile;
+}
+
 // Stream-K over G workers like k_fused_mixed (worker w owns units
 // [w T / G, (w+1) T / G) and writes its segments to slots (target block + w)),
 // with P = 2 NP targets per thread (target pairs (0, 1), (2, 3)) and source
@@ -790,18 +874,34 @@ __device__ __forceinline__ void packed_tile(const float4 (*__restrict__ sh)[kPac
 // with fixed assignments an SM would end its share with a fraction of its
 // warps.  A worker's result does not depend on which block runs it, so the
 // sums stay deterministic.
+//
+// Sources come from the staged records srec[slot][kPackVals] (every field
+// duplicated, positions negated), one contiguous 9 KB tile per unit, copied
+// by the bulk-copy engine into two shared buffers: the copy of unit u + 2
+// starts as soon as every warp is done with unit u, so the loads of the next
+// tile are in flight during the current one.  Targets are read from the same
+// records.  FP32 tile partials are added every kPackFlushTiles tiles into the
+// worker's segment slot in FP64 (each value is owned by one thread).  A copy
+// that does not complete within the poll limit sets kFlagTimeout in `flag`
+// and ends the block.
 template <int NP, int UNROLL>
 __global__ void __launch_bounds__(kMixThreads, NP == 2 ? 3 : 5)
-k_fused_packed(const float4 *__restrict__ rec, int64_t S, const Clu *__restrict__ clu, int nclu,
-               int64_t total_units, int64_t G, int *__restrict__ wcount,
+k_fused_packed(const float4 *__restrict__ srec, const Clu *__restrict__ clu, int nclu,
+               int64_t total_units, int64_t G, int *__restrict__ wcount, int *__restrict__ flag,
                double *__restrict__ part)
 {
     constexpr int P = 2 * NP, TI = kMixThreads * P;
-    __shared__ float4 sh[kPackTile][kPackVals];
-    __shared__ float2 run[kFusedVals][P][kMixThreads];
+    __shared__ __align__(128) float4 sh[2][kPackTile][kPackVals];
+    __shared__ __align__(8) uint64_t full[2];
     __shared__ int s_w;
+    if (threadIdx.x == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init_fence();
+    }
+    unsigned it = 0;                    // tiles this block has consumed
     for (;;) {
-        __syncthreads();                              // s_w and the tile are free
+        __syncthreads();                // s_w free; barriers initialised
         if (threadIdx.x == 0)
             s_w = atomicAdd(wcount, 1);
         __syncthreads();
@@ -810,6 +910,13 @@ k_fused_packed(const float4 *__restrict__ rec, int64_t S, const Clu *__restrict_
             break;
         int64_t u = w * total_units / G;
         const int64_t u1 = (w + 1) * total_units / G;
+        if (threadIdx.x == 0 && u < u1) {   // both buffers are free here
+            bulk_load(sh[it & 1], srec + unit_source(clu, nclu, u) * kPackVals, kTileBytes,
+                      &full[it & 1]);
+            if (u + 1 < u1)
+                bulk_load(sh[(it + 1) & 1], srec + unit_source(clu, nclu, u + 1) * kPackVals,
+                          kTileBytes, &full[(it + 1) & 1]);
+        }
         while (u < u1) {
             const Clu C = clu[cluster_of_unit(clu, nclu, u)];
             const int64_t ntiles = C.ns_pad / kPackTile;
@@ -823,79 +930,72 @@ k_fused_packed(const float4 *__restrict__ rec, int64_t S, const Clu *__restrict_
 #pragma unroll
             for (int pp = 0; pp < NP; ++pp) {
                 const int64_t ta = t0 + (2 * pp) * kMixThreads + threadIdx.x, tb = ta + kMixThreads;
-                const float4 Aa = rec[ta], Ab = rec[tb];
-                const float4 Ba = rec[S + ta], Bb = rec[S + tb];
-                const float4 Ca = rec[2 * S + ta], Cb = rec[2 * S + tb];
-                tg[pp].hx = make_float2(Aa.x, Ab.x);
-                tg[pp].hy = make_float2(Aa.y, Ab.y);
-                tg[pp].hz = make_float2(Aa.z, Ab.z);
-                tg[pp].lx = make_float2(Ba.x, Bb.x);
-                tg[pp].ly = make_float2(Ba.y, Bb.y);
-                tg[pp].lz = make_float2(Ba.z, Bb.z);
-                tg[pp].vx = make_float2(kEightThirds * Ca.x, kEightThirds * Cb.x);
-                tg[pp].vy = make_float2(kEightThirds * Ca.y, kEightThirds * Cb.y);
-                tg[pp].vz = make_float2(kEightThirds * Ca.z, kEightThirds * Cb.z);
+                const float4 *ra = srec + ta * kPackVals, *rb = srec + tb * kPackVals;
+                const float4 A0 = ra[0], A1 = ra[1], A2 = ra[2], A3 = ra[3], A4 = ra[4], A5 = ra[5];
+                const float4 B0 = rb[0], B1 = rb[1], B2 = rb[2], B3 = rb[3], B4 = rb[4], B5 = rb[5];
+                tg[pp].hx = make_float2(-A0.x, -B0.x);
+                tg[pp].hy = make_float2(-A0.z, -B0.z);
+                tg[pp].hz = make_float2(-A1.x, -B1.x);
+                tg[pp].lx = make_float2(-A2.x, -B2.x);
+                tg[pp].ly = make_float2(-A2.z, -B2.z);
+                tg[pp].lz = make_float2(-A3.x, -B3.x);
+                tg[pp].vx = make_float2(kEightThirds * A4.x, kEightThirds * B4.x);
+                tg[pp].vy = make_float2(kEightThirds * A4.z, kEightThirds * B4.z);
+                tg[pp].vz = make_float2(kEightThirds * A5.x, kEightThirds * B5.x);
             }
-#pragma unroll
-            for (int p = 0; p < P; ++p)
-#pragma unroll
-                for (int k = 0; k < kFusedVals; ++k)
-                    run[k][p][threadIdx.x] = make_float2(0.0f, 0.0f);
+            double *out = part + (t0 / TI + w) * (int64_t)(kFusedVals * TI);
+            bool first = true;
             float2 acc[NP][kFusedVals];
 #pragma unroll
             for (int pp = 0; pp < NP; ++pp)
 #pragma unroll
                 for (int k = 0; k < kFusedVals; ++k)
                     acc[pp][k] = make_float2(0.0f, 0.0f);
-            for (; u < uend; ++u) {
+            for (; u < uend; ++u, ++it) {
                 const int64_t j0 = C.slot0 + (u - ub) * kPackTile;
-                __syncthreads();
-                if (threadIdx.x < kPackTile) {
-                    const int64_t j = j0 + threadIdx.x;
-                    const float4 A = rec[j], B = rec[S + j], Cs = rec[2 * S + j];
-                    const float4 D = rec[3 * S + j], E = rec[4 * S + j];
-                    float4 *o = sh[threadIdx.x];
-                    o[0] = make_float4(-A.x, -A.x, -A.y, -A.y);
-                    o[1] = make_float4(-A.z, -A.z, A.w, A.w);
-                    o[2] = make_float4(-B.x, -B.x, -B.y, -B.y);
-                    o[3] = make_float4(-B.z, -B.z, B.w, B.w);
-                    o[4] = make_float4(Cs.x, Cs.x, Cs.y, Cs.y);
-                    o[5] = make_float4(Cs.z, Cs.z, Cs.w, Cs.w);
-                    o[6] = make_float4(D.x, D.x, D.y, D.y);
-                    o[7] = make_float4(D.z, D.z, E.x, E.x);
-                    o[8] = make_float4(E.y, E.y, E.z, E.z);
-                }
-                __syncthreads();
+                const int b = it & 1;
+                const bool ok = mbar_wait(&full[b], (it >> 1) & 1);
                 const bool diag = (j0 < t0 + TI) && (t0 < j0 + kPackTile);
                 if (diag)
-                    packed_tile<NP, UNROLL, true>(sh, j0, t0, tg, eps2, acc);
+                    packed_tile<NP, UNROLL, true>(sh[b], j0, t0, tg, eps2, acc);
                 else
-                    packed_tile<NP, UNROLL, false>(sh, j0, t0, tg, eps2, acc);
+                    packed_tile<NP, UNROLL, false>(sh[b], j0, t0, tg, eps2, acc);
                 if (((u - ub + 1) % kPackFlushTiles) == 0 || u + 1 == uend) {
 #pragma unroll
                     for (int pp = 0; pp < NP; ++pp)
 #pragma unroll
                         for (int k = 0; k < kFusedVals; ++k) {
-                            float2 r = run[k][2 * pp][threadIdx.x];
-                            ds_add(r.x, r.y, acc[pp][k].x);
-                            run[k][2 * pp][threadIdx.x] = r;
-                            r = run[k][2 * pp + 1][threadIdx.x];
-                            ds_add(r.x, r.y, acc[pp][k].y);
-                            run[k][2 * pp + 1][threadIdx.x] = r;
+                            double *o = out + k * TI + (2 * pp) * kMixThreads + threadIdx.x;
+                            o[0] = first ? (double)acc[pp][k].x : o[0] + (double)acc[pp][k].x;
+                            o[kMixThreads] = first ? (double)acc[pp][k].y
+                                                   : o[kMixThreads] + (double)acc[pp][k].y;
                             acc[pp][k] = make_float2(0.0f, 0.0f);
                         }
+                    first = false;
                 }
+                if (__syncthreads_or(!ok)) {     // every warp is done with buffer b
+                    if (threadIdx.x == 0) {
+                        atomicOr(flag, kFlagTimeout);
+                        if (u + 1 < u1)          // let the other copy land before exiting
+                            mbar_wait(&full[b ^ 1], ((it + 1) >> 1) & 1);
+                    }
+                    return;
+                }
+                if (threadIdx.x == 0 && u + 2 < u1)
+                    bulk_load(sh[b], srec + unit_source(clu, nclu, u + 2) * kPackVals, kTileBytes,
+                              &full[b]);
             }
-            double *out = part + (t0 / TI + w) * (int64_t)(kFusedVals * TI);
-#pragma unroll
-            for (int p = 0; p < P; ++p)
-#pragma unroll
-                for (int k = 0; k < kFusedVals; ++k) {
-                    const float2 r = run[k][p][threadIdx.x];
-                    out[k * TI + p * kMixThreads + threadIdx.x] = (double)r.x + (double)r.y;
-                }
         }
     }
+}
+
+__global__ void __launch_bounds__(kGlueThreads)
+k_stage_sources(int64_t S, const float4 *__restrict__ rec, float4 *__restrict__ srec)
+{
+    const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
+    if (t < S)
+        stage_source(srec + t * kPackVals, rec[t], rec[S + t], rec[2 * S + t], rec[3 * S + t],
+                     rec[4 * S + t]);
 }
 
 // Sums, for every star slot, the stream-K segments that cover its target
@@ -1701,10 +1801,16 @@ static cudaError_t launch_fused_p(pn_ctx *c, const Layout &L, const float4 *rec)
 template <int NP, int UNROLL>
 static cudaError_t launch_packed_u(pn_ctx *c, const Layout &L, const float4 *rec)
 {
+    const float4 *srec = c->mrec + 5 * c->S;
+    if (rec != c->mrec) {       // caller-built records: stage them first
+        k_stage_sources<<<(unsigned)(c->S / kGlueThreads), kGlueThreads, 0, c->stream>>>(
+            c->S, rec, c->mrec + 5 * c->S);
+        c->launches += 1;
+    }
     cudaEvent_t end = nullptr;
     timing_begin(c, 1, &end);
     k_fused_packed<NP, UNROLL><<<(unsigned)c->fused_grid, kMixThreads, 0, c->stream>>>(
-        rec, c->S, c->d_clu, c->nclu, c->fused_units, c->fused_G, c->wcount, c->part + L.seg);
+        srec, c->d_clu, c->nclu, c->fused_units, c->fused_G, c->wcount, c->flag, c->part + L.seg);
     c->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (end)
