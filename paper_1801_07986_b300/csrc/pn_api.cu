@@ -400,6 +400,12 @@ static pn_status init_common(pn_ctx **out, int nclu, const int64_t *off, const p
     c->fused_P = 4;          // measured fastest on B300 at N = 131072
     c->fused_unroll = 2;
     c->workers_max = pn::kPackWorkersMax;
+    // test hook: PN_INJECT_COPY_TIMEOUT=1 makes every tile barrier of the
+    // packed kernel expect 16 bytes that never arrive, so its bounded waits
+    // run out and pn_sync reports PN_ETIMEOUT
+    c->inject_tx = 0;
+    if (const char *ij = std::getenv("PN_INJECT_COPY_TIMEOUT"))
+        c->inject_tx = ij[0] == '1' ? 16u : 0u;
     if (const char *pw = std::getenv("PN_FUSED_WORKERS")) {
         const int v = std::atoi(pw);
         if (v >= 1 && v <= 64)

@@ -809,7 +809,7 @@ __device__ __forceinline__ void packed_tile(const float4 (*__restrict__ sh)[kPac
 
 // ---- bulk-copy staging (TMA engine, mbarrier completion) ----
 constexpr int kTileBytes = kPackTile * kPackVals * 16;   // one staged source tile
-constexpr int kSpinLimit = 1 << 22;                      // try_wait polls before giving up
+constexpr unsigned long long kWaitNs = 1000000000ull;    // a tile wait gives up after 1 s
 constexpr int kFlagTimeout = 2;                          // flag bit: a bounded wait gave up
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
@@ -828,31 +828,47 @@ __device__ __forceinline__ void mbar_init_fence()
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// Arms the barrier for `bytes` of transaction and starts one bulk copy of
-// `bytes` from global `src` to shared `dst` that completes on it.  Both
-// addresses 16-byte aligned, bytes a multiple of 16.
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+// Arms the barrier for `bytes` + `extra` of transaction and starts one bulk
+// copy of `bytes` from global `src` to shared `dst` that completes on it.
+// Both addresses 16-byte aligned, bytes a multiple of 16.  extra > 0 (a test
+// hook) leaves the phase incomplete, so the wait runs out.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar,
+                                          unsigned extra)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                 ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+                 ::"r"(smem_addr(bar)), "r"(bytes + extra) : "memory");
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                  ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
 }
 
-// Waits for the barrier's phase `parity` to complete; false after
-// kSpinLimit unsuccessful polls.
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the barrier's phase `parity` to complete; false once kWaitNs
+// have passed (checked every 256 polls).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
 {
     const uint32_t a = smem_addr(bar);
-    for (int i = 0; i < kSpinLimit; ++i) {
+    unsigned long long t0 = 0;
+    for (unsigned i = 0;; ++i) {
         uint32_t done;
         asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                      " selp.u32 %0, 1, 0, p;\n}"
                      : "=r"(done) : "r"(a), "r"(parity) : "memory");
         if (done)
             return true;
+        if ((i & 255) == 0) {
+            const unsigned long long t = global_ns();
+            if (i == 0)
+                t0 = t;
+            else if (t - t0 > kWaitNs)
+                return false;
+        }
     }
-    return false;
 }
 
 // First source slot of stream-K unit u (its cluster's tile of kPackTile
@@ -888,7 +904,7 @@ template <int NP, int UNROLL>
 __global__ void __launch_bounds__(kMixThreads, NP == 2 ? 3 : 5)
 k_fused_packed(const float4 *__restrict__ srec, const Clu *__restrict__ clu, int nclu,
                int64_t total_units, int64_t G, int *__restrict__ wcount, int *__restrict__ flag,
-               double *__restrict__ part)
+               unsigned extra_tx, double *__restrict__ part)
 {
     constexpr int P = 2 * NP, TI = kMixThreads * P;
     __shared__ __align__(128) float4 sh[2][kPackTile][kPackVals];
@@ -912,10 +928,10 @@ k_fused_packed(const float4 *__restrict__ srec, const Clu *__restrict__ clu, int
         const int64_t u1 = (w + 1) * total_units / G;
         if (threadIdx.x == 0 && u < u1) {   // both buffers are free here
             bulk_load(sh[it & 1], srec + unit_source(clu, nclu, u) * kPackVals, kTileBytes,
-                      &full[it & 1]);
+                      &full[it & 1], extra_tx);
             if (u + 1 < u1)
                 bulk_load(sh[(it + 1) & 1], srec + unit_source(clu, nclu, u + 1) * kPackVals,
-                          kTileBytes, &full[(it + 1) & 1]);
+                          kTileBytes, &full[(it + 1) & 1], extra_tx);
         }
         while (u < u1) {
             const Clu C = clu[cluster_of_unit(clu, nclu, u)];
@@ -983,7 +999,7 @@ k_fused_packed(const float4 *__restrict__ srec, const Clu *__restrict__ clu, int
                 }
                 if (threadIdx.x == 0 && u + 2 < u1)
                     bulk_load(sh[b], srec + unit_source(clu, nclu, u + 2) * kPackVals, kTileBytes,
-                              &full[b]);
+                              &full[b], extra_tx);
             }
         }
     }
@@ -1810,7 +1826,8 @@ static cudaError_t launch_packed_u(pn_ctx *c, const Layout &L, const float4 *rec
     cudaEvent_t end = nullptr;
     timing_begin(c, 1, &end);
     k_fused_packed<NP, UNROLL><<<(unsigned)c->fused_grid, kMixThreads, 0, c->stream>>>(
-        srec, c->d_clu, c->nclu, c->fused_units, c->fused_G, c->wcount, c->flag, c->part + L.seg);
+        srec, c->d_clu, c->nclu, c->fused_units, c->fused_G, c->wcount, c->flag, c->inject_tx,
+        c->part + L.seg);
     c->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (end)

@@ -303,6 +303,32 @@ def test_nonfinite_is_reported_and_cleared():
     ctx.close()
 
 
+def test_tile_copy_timeout_is_reported_and_device_stays_usable(orc, monkeypatch):
+    """The packed kernel's tile waits are bounded: with the test hook every
+    tile barrier expects 16 bytes that no copy delivers, the waits give up
+    after 1 s, and pn_sync reports PN_ETIMEOUT.  The device stays usable."""
+    import time
+    x, v, m = make_cluster(2048, 0.1, 83)
+    X, V, M = dev(x), dev(v), dev(m)
+    A = torch.empty_like(X)
+    monkeypatch.setenv("PN_INJECT_COPY_TIMEOUT", "1")
+    ctx = pn.pn_init(2048, c=20.0, eps=1e-4, precision="mixed", device=0)
+    monkeypatch.delenv("PN_INJECT_COPY_TIMEOUT")
+    t0 = time.time()
+    pn.pn_accel(ctx, X, V, M, A)
+    with pytest.raises(pn.PNError) as ei:
+        pn.pn_sync(ctx)
+    assert ei.value.status == pn.PN_ETIMEOUT
+    assert time.time() - t0 < 30.0
+    ctx.close()
+    ctx = pn.pn_init(2048, c=20.0, eps=1e-4, precision="mixed", device=0)
+    pn.pn_accel(ctx, X, V, M, A)
+    pn.pn_sync(ctx)
+    err = rel(A.cpu().numpy(), orc.accel(x, v, m, c=20.0, eps=1e-4))
+    assert np.median(err) <= MIX_MED and err.max() <= MIX_MAX
+    ctx.close()
+
+
 def test_step_host_equals_device_path():
     x, v, m = make_cluster(1500, 0.1, 91)
     dt = 1.0 / 1024
