@@ -223,35 +223,29 @@ k_dual_pairs(const double4_32a *__restrict__ rec, int64_t S, const Clu *__restri
 // The dual pair sums in FP32 for mixed-precision contexts (the jerk only
 // enters Hermite's predictor and corrector with dt^2 and dt^3 weights, so
 // single-precision pair terms are enough): value and derivative of every
-// pair term on float duals, x_ij's value from hi/lo splits of the
-// hole-relative positions, tile partials folded into FP64.  Same output
-// layout as k_dual_pairs<Dual>.  Records (float4 per slot, from the FP64
-// dual records): F0 = (hi d, m)  F1 = (lo d, R^2)  F2 = (d', (R^2)')
-// F3 = (v, C)  F4 = (v', C')  F5 = (-e/1.5, 0)  F6 = (-(e/1.5)', 0)
-// F7 = (w, 0)  F8 = (w', 0).
+// pair term, x_ij's value from hi/lo splits of the hole-relative positions,
+// partials of kJPackFlush tiles added into FP64 outputs.  Same output layout
+// as k_dual_pairs<Dual>.  Every arithmetic step is one f32x2 operation for
+// two targets (t, t + 128 of a 256-target block) against one source, on
+// duals P2 = (two values, two derivatives).  Staged source records, every
+// field duplicated (f, f) and the position terms negated (16 float4 per slot):
+//   S0 = (-hx, -hy)  S1 = (-hz, m)    S2 = (-lx, -ly)    S3 = (-lz, R^2)
+//   S4 = (-d'x, -d'y) S5 = (-d'z, (R^2)')  S6 = (vx, vy)  S7 = (vz, C)
+//   S8 = (ax, ay)    S9 = (az, C')   S10 = (Dx, Dy)     S11 = (Dz, D'x)
+//   S12 = (D'y, D'z) S13 = (wx, wy)  S14 = (wz, w'x)    S15 = (w'y, w'z)
+// (h, l = hi/lo split of d_j, primes: derivatives along the trajectory,
+// a = v', D = -e_j/1.5, C = c_j/1.5 - 4/3 |v_j|^2).  Tiles of kJPackTile
+// sources move by bulk copies into two shared buffers as in the
+// acceleration kernel.
 
-constexpr int kJRecF = 9;
-constexpr int kJTileF = 64;
-
-struct DualF {
-    float v, d;
-};
-__device__ __forceinline__ DualF operator+(DualF a, DualF b) { return {a.v + b.v, a.d + b.d}; }
-__device__ __forceinline__ DualF operator-(DualF a, DualF b) { return {a.v - b.v, a.d - b.d}; }
-__device__ __forceinline__ DualF operator*(DualF a, DualF b)
-{
-    return {a.v * b.v, fmaf(a.d, b.v, a.v * b.d)};
-}
-__device__ __forceinline__ DualF operator*(float s, DualF a) { return {s * a.v, s * a.d}; }
-__device__ __forceinline__ DualF &operator+=(DualF &a, DualF b)
-{
-    a.v += b.v;
-    a.d += b.d;
-    return a;
-}
+constexpr int kJPackVals = 16;      // float4 per staged source
+constexpr int kJPackTile = 64;      // sources per tile
+constexpr int kJPackFlush = 8;      // tiles per single-precision partial
+constexpr int kJPackTI = 2 * kMixThreads;   // targets per block
+constexpr int kJPackBytes = kJPackTile * kJPackVals * 16;
 
 __global__ void __launch_bounds__(kGlueThreads)
-k_jerk_frec(int64_t S, const double4_32a *__restrict__ rec, float4 *__restrict__ frec)
+k_jerk_stage(int64_t S, const double4_32a *__restrict__ rec, float4 *__restrict__ srec)
 {
     const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
     if (t >= S)
@@ -260,103 +254,239 @@ k_jerk_frec(int64_t S, const double4_32a *__restrict__ rec, float4 *__restrict__
     const double4_32a J4 = rec[4 * S + t], J5 = rec[5 * S + t], J6 = rec[6 * S + t],
                       J7 = rec[7 * S + t];
     const float h0 = (float)J0.x, h1 = (float)J0.y, h2 = (float)J0.z;
-    frec[t] = make_float4(h0, h1, h2, (float)J0.w);
-    frec[S + t] = make_float4((float)(J0.x - (double)h0), (float)(J0.y - (double)h1),
-                              (float)(J0.z - (double)h2), (float)J2.w);
-    frec[2 * S + t] = make_float4((float)J1.x, (float)J1.y, (float)J1.z, (float)J3.w);
-    frec[3 * S + t] = make_float4((float)J2.x, (float)J2.y, (float)J2.z, (float)J4.w);
-    frec[4 * S + t] = make_float4((float)J3.x, (float)J3.y, (float)J3.z, (float)J5.w);
-    frec[5 * S + t] = make_float4((float)J4.x, (float)J4.y, (float)J4.z, 0.0f);
-    frec[6 * S + t] = make_float4((float)J5.x, (float)J5.y, (float)J5.z, 0.0f);
-    frec[7 * S + t] = make_float4((float)J6.x, (float)J6.y, (float)J6.z, 0.0f);
-    frec[8 * S + t] = make_float4((float)J7.x, (float)J7.y, (float)J7.z, 0.0f);
+    const float l0 = (float)(J0.x - (double)h0), l1 = (float)(J0.y - (double)h1),
+                l2 = (float)(J0.z - (double)h2);
+    auto dup = [](double a, double b) {
+        return make_float4((float)a, (float)a, (float)b, (float)b);
+    };
+    float4 *o = srec + t * kJPackVals;
+    o[0] = make_float4(-h0, -h0, -h1, -h1);
+    o[1] = make_float4(-h2, -h2, (float)J0.w, (float)J0.w);
+    o[2] = make_float4(-l0, -l0, -l1, -l1);
+    o[3] = make_float4(-l2, -l2, (float)J2.w, (float)J2.w);
+    o[4] = dup(-J1.x, -J1.y);
+    o[5] = dup(-J1.z, J3.w);
+    o[6] = dup(J2.x, J2.y);
+    o[7] = dup(J2.z, J4.w);
+    o[8] = dup(J3.x, J3.y);
+    o[9] = dup(J3.z, J5.w);
+    o[10] = dup(J4.x, J4.y);
+    o[11] = dup(J4.z, J5.x);
+    o[12] = dup(J5.y, J5.z);
+    o[13] = dup(J6.x, J6.y);
+    o[14] = dup(J6.z, J7.x);
+    o[15] = dup(J7.y, J7.z);
 }
 
-__global__ void __launch_bounds__(kJThreads)
-k_dual_pairs_f(const float4 *__restrict__ frec, int64_t S, const Clu *__restrict__ clu,
-               const int *__restrict__ blk_clu, double *__restrict__ part)
+struct P2 {
+    float2 v, d;     // values and derivatives of two targets' duals
+};
+
+// acc += a b on duals (3 packed operations)
+__device__ __forceinline__ void p2_acc(P2 &acc, const P2 &a, const P2 &b)
 {
-    __shared__ float4 sh[kJRecF][kJTileF];
-    const int64_t t0 = (int64_t)blockIdx.x * kJThreads;
-    const Clu C = clu[cluster_of_block(blk_clu, t0 / kGlueThreads)];
-    const int ntiles = (int)(C.ns_pad / kJTileF);
-    const int tps = (ntiles + (int)gridDim.y - 1) / (int)gridDim.y;
-    const int64_t ti = t0 + threadIdx.x;
-    const float4 T0 = frec[ti], T1 = frec[S + ti], T2 = frec[2 * S + ti], T3 = frec[3 * S + ti],
-                 T4 = frec[4 * S + ti];
-    const float hi[3] = {T0.x, T0.y, T0.z}, lo[3] = {T1.x, T1.y, T1.z};
-    const DualF di[3] = {{T0.x + T1.x, T2.x}, {T0.y + T1.y, T2.y}, {T0.z + T1.z, T2.z}};
-    const float e3 = 8.0f / 3.0f;
-    const DualF vi[3] = {{e3 * T3.x, e3 * T4.x}, {e3 * T3.y, e3 * T4.y}, {e3 * T3.z, e3 * T4.z}};
-    const float eps2 = (float)C.eps2;
-    double acc[2 * kFusedVals];
-#pragma unroll
-    for (int k = 0; k < 2 * kFusedVals; ++k)
-        acc[k] = 0.0;
-    const int tb = blockIdx.y * tps;
-    const int te = min(ntiles, tb + tps);
-    for (int tile = tb; tile < te; ++tile) {
-        const int64_t j0 = C.slot0 + (int64_t)tile * kJTileF;
-        __syncthreads();
-        for (int q = threadIdx.x; q < kJRecF * kJTileF; q += kJThreads)
-            sh[q / kJTileF][q % kJTileF] = frec[(q / kJTileF) * S + j0 + q % kJTileF];
-        __syncthreads();
-        DualF p[kFusedVals];
-#pragma unroll
-        for (int k = 0; k < kFusedVals; ++k)
-            p[k] = {0.0f, 0.0f};
-#pragma unroll 1
-        for (int q = 0; q < kJTileF; ++q) {
-            if (j0 + q == ti)
-                continue;
-            const float4 A0 = sh[0][q], A1 = sh[1][q], A2 = sh[2][q], A3 = sh[3][q];
-            const float4 A4 = sh[4][q], A5 = sh[5][q], A6 = sh[6][q], A7 = sh[7][q],
-                         A8 = sh[8][q];
-            const DualF xx[3] = {{(hi[0] - A0.x) + (lo[0] - A1.x), di[0].d - A2.x},
-                                 {(hi[1] - A0.y) + (lo[1] - A1.y), di[1].d - A2.y},
-                                 {(hi[2] - A0.z) + (lo[2] - A1.z), di[2].d - A2.z}};
-            const DualF vj[3] = {{A3.x, A4.x}, {A3.y, A4.y}, {A3.z, A4.z}};
-            DualF s2 = xx[0] * xx[0] + xx[1] * xx[1] + xx[2] * xx[2];
-            s2.v += eps2;
-            const float y = rsqrt_approx(s2.v);
-            const DualF is = {y, -0.5f * y * y * y * s2.d};
-            const DualF is2 = is * is;
-            const DualF mis = A0.w * is;
-            const DualF mis3 = mis * is2;
-#pragma unroll
-            for (int k = 0; k < 3; ++k)
-                p[k] += mis3 * xx[k];
-            p[3] += mis;
-            p[4] += mis3;
-            p[5] += mis3 * DualF{A1.w, A2.w};
-            const DualF xvj = xx[0] * vj[0] + xx[1] * vj[1] + xx[2] * vj[2];
-            const DualF xvi = xx[0] * vi[0] + xx[1] * vi[1] + xx[2] * vi[2];
-            const DualF kk = DualF{A3.w, A4.w} + (vi[0] * vj[0] + vi[1] * vj[1] + vi[2] * vj[2]) +
-                             (DualF{A5.x, A6.x} * di[0] + DualF{A5.y, A6.y} * di[1] +
-                              DualF{A5.z, A6.z} * di[2]);
-            const DualF f = mis3 * (xvj * is2 * xvj + kk);
-#pragma unroll
-            for (int k = 0; k < 3; ++k)
-                p[6 + k] += f * xx[k];
-            const DualF gg = mis3 * (xvi - 2.0f * xvj);
-            p[9] += gg;
-#pragma unroll
-            for (int k = 0; k < 3; ++k)
-                p[10 + k] += gg * vj[k];
-            p[13] += DualF{A7.x, A8.x} * is;
-            p[14] += DualF{A7.y, A8.y} * is;
-            p[15] += DualF{A7.z, A8.z} * is;
+    acc.v = fma2(a.v, b.v, acc.v);
+    acc.d = fma2(a.d, b.v, fma2(a.v, b.d, acc.d));
+}
+
+__device__ __forceinline__ P2 p2_mul(const P2 &a, const P2 &b)
+{
+    return {mul2(a.v, b.v), fma2(a.d, b.v, mul2(a.v, b.d))};
+}
+
+struct JTarget {
+    float2 hx, hy, hz, lx, ly, lz;   // hi/lo split of d_i
+    float2 dx, dy, dz;               // d_i'
+    float2 vx, vy, vz, ax, ay, az;   // 8/3 v_i, 8/3 a_i
+};
+
+template <bool MASK>
+__device__ __forceinline__ void jerk_pair(const JTarget &tg, const float4 *__restrict__ sq,
+                                          float2 eps2, bool selfx, bool selfy, P2 (&acc)[kFusedVals])
+{
+    const float4 S0 = sq[0], S1 = sq[1], S2 = sq[2], S3 = sq[3], S4 = sq[4], S5 = sq[5];
+    const P2 x = {add2(add2(tg.hx, lo2(S0)), add2(tg.lx, lo2(S2))), add2(tg.dx, lo2(S4))};
+    const P2 y = {add2(add2(tg.hy, hi2(S0)), add2(tg.ly, hi2(S2))), add2(tg.dy, hi2(S4))};
+    const P2 z = {add2(add2(tg.hz, lo2(S1)), add2(tg.lz, lo2(S3))), add2(tg.dz, lo2(S5))};
+    float2 s2 = fma2(x.v, x.v, fma2(y.v, y.v, fma2(z.v, z.v, eps2)));
+    float2 m = hi2(S1);
+    const float4 S13 = sq[13], S14 = sq[14], S15 = sq[15];
+    P2 wx = {lo2(S13), hi2(S14)}, wy = {hi2(S13), lo2(S15)}, wz = {lo2(S14), hi2(S15)};
+    if (MASK) {
+        if (selfx) {
+            s2.x = 1.0f; m.x = 0.0f;
+            wx.v.x = wy.v.x = wz.v.x = wx.d.x = wy.d.x = wz.d.x = 0.0f;
         }
-#pragma unroll
-        for (int k = 0; k < kFusedVals; ++k) {
-            acc[2 * k] += (double)p[k].v;
-            acc[2 * k + 1] += (double)p[k].d;
+        if (selfy) {
+            s2.y = 1.0f; m.y = 0.0f;
+            wx.v.y = wy.v.y = wz.v.y = wx.d.y = wy.d.y = wz.d.y = 0.0f;
         }
     }
-    double *out = part + (int64_t)blockIdx.y * 2 * kFusedVals * S;
+    // r^-1 = y, (r^-1)' = -y^3 q, (r^-3)' = -3 y^5 q with q = x . x'
+    const float2 q = fma2(x.v, x.d, fma2(y.v, y.d, mul2(z.v, z.d)));
+    const float2 yy = make_float2(rsqrt_approx(s2.x), rsqrt_approx(s2.y));
+    const float2 y2 = mul2(yy, yy);
+    const float2 nq = mul2(q, make_float2(-1.0f, -1.0f));
+    const P2 is = {yy, mul2(mul2(y2, yy), nq)};
+    const P2 is2 = {y2, mul2(mul2(yy, is.d), make_float2(2.0f, 2.0f))};
+    const P2 mis = {mul2(m, yy), mul2(m, is.d)};
+    const float2 my3 = mul2(mis.v, y2);
+    const P2 mis3 = {my3, mul2(mul2(my3, mul2(y2, nq)), make_float2(3.0f, 3.0f))};
+    p2_acc(acc[0], mis3, x);
+    p2_acc(acc[1], mis3, y);
+    p2_acc(acc[2], mis3, z);
+    acc[3].v = add2(acc[3].v, mis.v);
+    acc[3].d = add2(acc[3].d, mis.d);
+    acc[4].v = add2(acc[4].v, mis3.v);
+    acc[4].d = add2(acc[4].d, mis3.d);
+    p2_acc(acc[5], mis3, P2{hi2(S3), hi2(S5)});
+    const float4 S6 = sq[6], S7 = sq[7], S8 = sq[8], S9 = sq[9];
+    const P2 vjx = {lo2(S6), lo2(S8)}, vjy = {hi2(S6), hi2(S8)}, vjz = {lo2(S7), lo2(S9)};
+    // x . v_j, x . (8/3) v_i
+    P2 xvj = p2_mul(x, vjx);
+    p2_acc(xvj, y, vjy);
+    p2_acc(xvj, z, vjz);
+    P2 xvi = p2_mul(x, P2{tg.vx, tg.ax});
+    p2_acc(xvi, y, P2{tg.vy, tg.ay});
+    p2_acc(xvi, z, P2{tg.vz, tg.az});
+    // kk = C_j + (8/3) v_i . v_j + D_j . h_i
+    const float4 S10 = sq[10], S11 = sq[11], S12 = sq[12];
+    P2 kk = {hi2(S7), hi2(S9)};
+    p2_acc(kk, P2{tg.vx, tg.ax}, vjx);
+    p2_acc(kk, P2{tg.vy, tg.ay}, vjy);
+    p2_acc(kk, P2{tg.vz, tg.az}, vjz);
+    p2_acc(kk, P2{lo2(S10), hi2(S11)}, P2{tg.hx, tg.dx});
+    p2_acc(kk, P2{hi2(S10), lo2(S12)}, P2{tg.hy, tg.dy});
+    p2_acc(kk, P2{lo2(S11), hi2(S12)}, P2{tg.hz, tg.dz});
+    const P2 h = p2_mul(xvj, is2);
+    p2_acc(kk, h, xvj);
+    const P2 f = p2_mul(mis3, kk);
+    p2_acc(acc[6], f, x);
+    p2_acc(acc[7], f, y);
+    p2_acc(acc[8], f, z);
+    const float2 m2 = make_float2(-2.0f, -2.0f);
+    const P2 u = {fma2(m2, xvj.v, xvi.v), fma2(m2, xvj.d, xvi.d)};
+    const P2 gg = p2_mul(mis3, u);
+    acc[9].v = add2(acc[9].v, gg.v);
+    acc[9].d = add2(acc[9].d, gg.d);
+    p2_acc(acc[10], gg, vjx);
+    p2_acc(acc[11], gg, vjy);
+    p2_acc(acc[12], gg, vjz);
+    p2_acc(acc[13], wx, is);
+    p2_acc(acc[14], wy, is);
+    p2_acc(acc[15], wz, is);
+}
+
+// One output value of a target: first flush writes, later ones add.
+__device__ __forceinline__ void jerk_out(double *o, float p, bool first)
+{
+    *o = first ? (double)p : *o + (double)p;
+}
+
+// Grid (target blocks of 256 slots, source splits); split s of a block in a
+// cluster with T tiles sweeps tiles [s T / js, (s+1) T / js).  A copy that
+// does not complete within the wait limit sets kFlagTimeout in `flag`.
+__global__ void __launch_bounds__(kMixThreads, 3)
+k_jerk_pairs_packed(const float4 *__restrict__ srec, int64_t S, const Clu *__restrict__ clu,
+                    const int *__restrict__ blk_clu, int *__restrict__ flag,
+                    double *__restrict__ part)
+{
+    __shared__ __align__(128) float4 sh[2][kJPackTile][kJPackVals];
+    __shared__ __align__(8) uint64_t full[2];
+    const int64_t t0 = (int64_t)blockIdx.x * kJPackTI;
+    const Clu C = clu[cluster_of_block(blk_clu, t0 / kGlueThreads)];
+    const int64_t ntiles = C.ns_pad / kJPackTile;
+    const int64_t js = gridDim.y, sp = blockIdx.y;
+    const int64_t tb = sp * ntiles / js, te = (sp + 1) * ntiles / js;
+    double *out = part + sp * 2 * kFusedVals * S;
+    const int64_t ta = t0 + threadIdx.x, tq = ta + kMixThreads;
+    if (te <= tb) {               // an empty split still owns its outputs
+        for (int k = 0; k < 2 * kFusedVals; ++k) {
+            out[k * S + ta] = 0.0;
+            out[k * S + tq] = 0.0;
+        }
+        return;
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bulk_load(sh[0], srec + (C.slot0 + tb * kJPackTile) * kJPackVals, kJPackBytes, &full[0], 0);
+        if (tb + 1 < te)
+            bulk_load(sh[1], srec + (C.slot0 + (tb + 1) * kJPackTile) * kJPackVals, kJPackBytes,
+                      &full[1], 0);
+    }
+    JTarget tg;
+    {
+        const float4 *ra = srec + ta * kJPackVals, *rb = srec + tq * kJPackVals;
+        const float4 A0 = ra[0], A1 = ra[1], A2 = ra[2], A3 = ra[3], A4 = ra[4], A5 = ra[5];
+        const float4 A6 = ra[6], A7 = ra[7], A8 = ra[8], A9 = ra[9];
+        const float4 B0 = rb[0], B1 = rb[1], B2 = rb[2], B3 = rb[3], B4 = rb[4], B5 = rb[5];
+        const float4 B6 = rb[6], B7 = rb[7], B8 = rb[8], B9 = rb[9];
+        const float e3 = 8.0f / 3.0f;
+        tg.hx = make_float2(-A0.x, -B0.x);
+        tg.hy = make_float2(-A0.z, -B0.z);
+        tg.hz = make_float2(-A1.x, -B1.x);
+        tg.lx = make_float2(-A2.x, -B2.x);
+        tg.ly = make_float2(-A2.z, -B2.z);
+        tg.lz = make_float2(-A3.x, -B3.x);
+        tg.dx = make_float2(-A4.x, -B4.x);
+        tg.dy = make_float2(-A4.z, -B4.z);
+        tg.dz = make_float2(-A5.x, -B5.x);
+        tg.vx = make_float2(e3 * A6.x, e3 * B6.x);
+        tg.vy = make_float2(e3 * A6.z, e3 * B6.z);
+        tg.vz = make_float2(e3 * A7.x, e3 * B7.x);
+        tg.ax = make_float2(e3 * A8.x, e3 * B8.x);
+        tg.ay = make_float2(e3 * A8.z, e3 * B8.z);
+        tg.az = make_float2(e3 * A9.x, e3 * B9.x);
+    }
+    const float e2 = (float)C.eps2;
+    const float2 eps2 = make_float2(e2, e2);
+    P2 acc[kFusedVals];
 #pragma unroll
-    for (int k = 0; k < 2 * kFusedVals; ++k)
-        out[(int64_t)k * S + ti] = acc[k];
+    for (int k = 0; k < kFusedVals; ++k)
+        acc[k] = P2{make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
+    bool first = true;
+    for (int64_t tile = tb; tile < te; ++tile) {
+        const int b = (int)((tile - tb) & 1);
+        const bool ok = mbar_wait(&full[b], (unsigned)(((tile - tb) >> 1) & 1));
+        const int64_t j0 = C.slot0 + tile * kJPackTile;
+        const bool diag = (j0 < t0 + kJPackTI) && (t0 < j0 + kJPackTile);
+        if (diag) {
+#pragma unroll 1
+            for (int q = 0; q < kJPackTile; ++q)
+                jerk_pair<true>(tg, sh[b][q], eps2, j0 + q == ta, j0 + q == tq, acc);
+        } else {
+#pragma unroll 1
+            for (int q = 0; q < kJPackTile; ++q)
+                jerk_pair<false>(tg, sh[b][q], eps2, false, false, acc);
+        }
+        if (((tile - tb + 1) % kJPackFlush) == 0 || tile + 1 == te) {
+#pragma unroll
+            for (int k = 0; k < kFusedVals; ++k) {
+                jerk_out(out + (2 * k) * S + ta, acc[k].v.x, first);
+                jerk_out(out + (2 * k) * S + tq, acc[k].v.y, first);
+                jerk_out(out + (2 * k + 1) * S + ta, acc[k].d.x, first);
+                jerk_out(out + (2 * k + 1) * S + tq, acc[k].d.y, first);
+                acc[k] = P2{make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
+            }
+            first = false;
+        }
+        if (__syncthreads_or(!ok)) {     // every warp is done with buffer b
+            if (threadIdx.x == 0) {
+                atomicOr(flag, kFlagTimeout);
+                if (tile + 1 < te)
+                    mbar_wait(&full[b ^ 1], (unsigned)(((tile - tb + 1) >> 1) & 1));
+            }
+            return;
+        }
+        if (threadIdx.x == 0 && tile + 2 < te)
+            bulk_load(sh[b], srec + (C.slot0 + (tile + 2) * kJPackTile) * kJPackVals, kJPackBytes,
+                      &full[b], 0);
+    }
 }
 
 // Per star: the split partials summed, star_eqs on Duals; the value is the
@@ -1127,12 +1257,26 @@ int64_t jerk_part_splits(const pn_ctx *c)
     return js > 64 ? 64 : js;
 }
 
+// Source splits of the packed FP32 jerk kernel: about four waves of 3 blocks
+// per SM over the 256-target blocks, at most one tile per split and never
+// more than the FP64 kernel's splits (the partial buffer holds those).
+static int64_t jerk_pack_splits(const pn_ctx *c)
+{
+    const int64_t nb = c->S / kJPackTI;
+    int64_t js = (4 * 3 * (int64_t)c->sm_count) / nb;
+    const int64_t tiles = c->max_ns_pad / kJPackTile;
+    const int64_t cap = jerk_part_splits(c);
+    js = js < 1 ? 1 : js;
+    js = js > tiles ? tiles : js;
+    return js > cap ? cap : js;
+}
+
 size_t jerk_buffer_doubles(const pn_ctx *c)
 {
     const int64_t S = c->S, nglue = S / kGlueThreads;
     return (size_t)(kJRec * 4 * S + jerk_part_splits(c) * 2 * kFusedVals * S +
                     nglue * 2 * kJVals + (int64_t)c->nclu * 2 * kJVals + nglue * 6 +
-                    18 * S);   // + float records of the single-precision pass (9 float4)
+                    32 * S);   // + staged float records of the packed pass (16 float4)
 }
 
 cudaError_t launch_jerk(pn_ctx *c, const double *x, const double *v, const double *m,
@@ -1159,12 +1303,23 @@ cudaError_t launch_jerk(pn_ctx *c, const double *x, const double *v, const doubl
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
     dim3 grid((unsigned)(S / kJThreads), (unsigned)js);
+    int jsum = js;
     if (c->p.precision == PN_MIXED) {
-        // single-precision dual pair sums on float records (after the hole terms)
-        float4 *frec = reinterpret_cast<float4 *>(bhb + nglue * 6);
-        k_jerk_frec<<<(unsigned)nglue, kGlueThreads, 0, c->stream>>>(S, rec, frec);
-        k_dual_pairs_f<<<grid, kJThreads, 0, c->stream>>>(frec, S, c->d_clu, bc, part);
+        // single-precision dual pair sums on staged float records (after the
+        // hole terms)
+        float4 *srec = reinterpret_cast<float4 *>(bhb + nglue * 6);
+        const int jp = (int)jerk_pack_splits(c);
+        static bool carveout = false;     // 3 blocks of 32 KB per SM
+        if (!carveout) {
+            cudaFuncSetAttribute(k_jerk_pairs_packed,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+            carveout = true;
+        }
+        k_jerk_stage<<<(unsigned)nglue, kGlueThreads, 0, c->stream>>>(S, rec, srec);
+        k_jerk_pairs_packed<<<dim3((unsigned)(S / kJPackTI), (unsigned)jp), kMixThreads, 0,
+                              c->stream>>>(srec, S, c->d_clu, bc, c->flag, part);
         c->launches += 2;
+        jsum = jp;
     } else {
         k_dual_pairs<Dual><<<grid, kJThreads, 0, c->stream>>>(rec, S, c->d_clu, bc, part);
         c->launches += 1;
@@ -1172,7 +1327,7 @@ cudaError_t launch_jerk(pn_ctx *c, const double *x, const double *v, const doubl
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
     k_jerk_epilogue<<<(unsigned)nglue, kGlueThreads, 0, c->stream>>>(
-        S, c->d_clu, bc, x, v, m, a, part, js, glob, jerk, c->flag, c->flag_step, step, bhb);
+        S, c->d_clu, bc, x, v, m, a, part, jsum, glob, jerk, c->flag, c->flag_step, step, bhb);
     c->launches += 1;
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;

@@ -213,4 +213,74 @@ __device__ __forceinline__ void star_eqs(double G, const TM &M, double mi, doubl
                 (gmr3 / M) * (4.0 * vQ * d[k] - 3.0 * vd * g.Q[k] - 4.0 * Qd * vv[k]);
 }
 
+// ---- packed FP32x2 arithmetic (two lanes per register pair) ----
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 lo2(const float4 &f) { return make_float2(f.x, f.y); }
+__device__ __forceinline__ float2 hi2(const float4 &f) { return make_float2(f.z, f.w); }
+
+// ---- bulk-copy staging (TMA engine, mbarrier completion) ----
+constexpr unsigned long long kWaitNs = 1000000000ull;    // a tile wait gives up after 1 s
+constexpr int kFlagTimeout = 2;                          // flag bit: a bounded wait gave up
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Arms the barrier for `bytes` + `extra` of transaction and starts one bulk
+// copy of `bytes` from global `src` to shared `dst` that completes on it.
+// Both addresses 16-byte aligned, bytes a multiple of 16.  extra > 0 (a test
+// hook) leaves the phase incomplete, so the wait runs out.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar,
+                                          unsigned extra)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(smem_addr(bar)), "r"(bytes + extra) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the barrier's phase `parity` to complete; false once kWaitNs
+// have passed (checked every 256 polls).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
+{
+    const uint32_t a = smem_addr(bar);
+    unsigned long long t0 = 0;
+    for (unsigned i = 0;; ++i) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done) : "r"(a), "r"(parity) : "memory");
+        if (done)
+            return true;
+        if ((i & 255) == 0) {
+            const unsigned long long t = global_ns();
+            if (i == 0)
+                t0 = t;
+            else if (t - t0 > kWaitNs)
+                return false;
+        }
+    }
+}
+
 }  // namespace pn
