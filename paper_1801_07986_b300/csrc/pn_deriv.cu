@@ -460,7 +460,7 @@ k_jerk_pairs_packed(const float4 *__restrict__ srec, int64_t S, const Clu *__res
             for (int q = 0; q < kJPackTile; ++q)
                 jerk_pair<true>(tg, sh[b][q], eps2, j0 + q == ta, j0 + q == tq, acc);
         } else {
-#pragma unroll 1
+#pragma unroll 2
             for (int q = 0; q < kJPackTile; ++q)
                 jerk_pair<false>(tg, sh[b][q], eps2, false, false, acc);
         }
@@ -1257,13 +1257,13 @@ int64_t jerk_part_splits(const pn_ctx *c)
     return js > 64 ? 64 : js;
 }
 
-// Source splits of the packed FP32 jerk kernel: about four waves of 3 blocks
-// per SM over the 256-target blocks, at most one tile per split and never
-// more than the FP64 kernel's splits (the partial buffer holds those).
+// Source splits of the packed FP32 jerk kernel: about eight waves of 3
+// blocks per SM over the 256-target blocks, at least one tile per split and
+// never more than the FP64 kernel's splits (the partial buffer holds those).
 static int64_t jerk_pack_splits(const pn_ctx *c)
 {
     const int64_t nb = c->S / kJPackTI;
-    int64_t js = (4 * 3 * (int64_t)c->sm_count) / nb;
+    int64_t js = (8 * 3 * (int64_t)c->sm_count) / nb;
     const int64_t tiles = c->max_ns_pad / kJPackTile;
     const int64_t cap = jerk_part_splits(c);
     js = js < 1 ? 1 : js;
