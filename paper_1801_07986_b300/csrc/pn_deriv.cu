@@ -514,15 +514,18 @@ k_jerk_epilogue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ 
             d[k] = dual(x[3 * i + k] - x[3 * hb + k], v[3 * i + k] - v[3 * hb + k]);
             vv[k] = dual(v[3 * i + k], a[3 * i + k]);
         }
+        // splits in order for every value; the 32 loads of one split are
+        // independent, so they are in flight together
+        double sv[2 * kFusedVals];
+        for (int k = 0; k < 2 * kFusedVals; ++k)
+            sv[k] = 0.0;
+        for (int q = 0; q < js; ++q)
+#pragma unroll
+            for (int k = 0; k < 2 * kFusedVals; ++k)
+                sv[k] += part[((int64_t)q * 2 * kFusedVals + k) * S + t];
         Dual s[kFusedVals];
-        for (int k = 0; k < kFusedVals; ++k) {
-            double sv = 0.0, sd = 0.0;
-            for (int q = 0; q < js; ++q) {
-                sv += part[((int64_t)q * 2 * kFusedVals + 2 * k) * S + t];
-                sd += part[((int64_t)q * 2 * kFusedVals + 2 * k + 1) * S + t];
-            }
-            s[k] = dual(sv, sd);
-        }
+        for (int k = 0; k < kFusedVals; ++k)
+            s[k] = dual(sv[2 * k], sv[2 * k + 1]);
         StarSums<Dual> ss;
         for (int k = 0; k < 3; ++k) {
             ss.N[k] = s[k];
@@ -732,7 +735,8 @@ k_adj_star(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
         const double ab[3] = {abar[3 * i], abar[3 * i + 1], abar[3 * i + 2]};
         const double bb[3] = {Cl.inv_c2 * abar[3 * hb], Cl.inv_c2 * abar[3 * hb + 1],
                               Cl.inv_c2 * abar[3 * hb + 2]};
-        for (int q = lane; q < 33; q += 32) {
+        {
+            const int q = lane;     // seeds 0..31; inv_c2 (32) from the 1PN bracket's value
             Dual w[33];
             for (int k = 0; k < 33; ++k)
                 w[k] = dual(su[wi][k], k == q ? 1.0 : 0.0);
@@ -758,15 +762,20 @@ k_adj_star(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
             gs.SA = w[28];
             gs.SB = w[29];
             gs.Phi = w[30];
-            Dual ai[3], bh[3];
-            star_eqs<Dual, Dual>(Cl.G, w[31], m[i], Cl.eps2, w[32], 1.0, d, vv, ss, gs, ai, bh);
+            Dual ai[3], bh[3], pn[3];
+            star_eqs<Dual, Dual>(Cl.G, w[31], m[i], Cl.eps2, w[32], 1.0, d, vv, ss, gs, ai, bh,
+                                 pn);
             double acc = 0.0;
             for (int k = 0; k < 3; ++k)
                 acc += ab[k] * ai[k].d + bb[k] * bh[k].d;
             sub[wi][q] = acc;
-            if (q == 0)   // the hole's inv_c2 term: abar_hole . (star i's term)
+            if (q == 0) {
+                // d/d(inv_c2): abar_i . (1PN bracket); bh does not depend on it
+                sub[wi][32] = ab[0] * pn[0].v + ab[1] * pn[1].v + ab[2] * pn[2].v;
+                // the hole's inv_c2 term: abar_hole . (star i's term)
                 sub[wi][33] = abar[3 * hb] * bh[0].v + abar[3 * hb + 1] * bh[1].v +
                               abar[3 * hb + 2] * bh[2].v;
+            }
         }
     }
     __syncwarp();
@@ -1131,15 +1140,19 @@ k_adj_records(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ bl
     if (lt < Cl.ns) {
         const int64_t j = Cl.body0 + 1 + lt, hb = Cl.body0;
         const double mj = m[j], G = Cl.G, eps2 = Cl.eps2;
+        // splits in order for every value, the values of a split loaded together
         double tp[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, sp[kAdjSrc];
-        for (int k = 0; k < 6; ++k)
-            for (int q = 0; q < jst; ++q)
+        for (int q = 0; q < jst; ++q)
+#pragma unroll
+            for (int k = 0; k < 6; ++k)
                 tp[k] += tpart[((int64_t)q * 6 + k) * S + t];
-        for (int k = 0; k < kAdjSrc; ++k) {
+#pragma unroll
+        for (int k = 0; k < kAdjSrc; ++k)
             sp[k] = 0.0;
-            for (int q = 0; q < jss; ++q)
+        for (int q = 0; q < jss; ++q)
+#pragma unroll
+            for (int k = 0; k < kAdjSrc; ++k)
                 sp[k] += spart[((int64_t)q * kAdjSrc + k) * S + t];
-        }
         // cotangents of this star's record and cluster-sum terms
         const double Wb[3] = {gb[3] + G * abar[3 * hb], gb[4] + G * abar[3 * hb + 1],
                               gb[5] + G * abar[3 * hb + 2]};
