@@ -927,11 +927,9 @@ k_adj_sources(const double4_32a *__restrict__ rec, int64_t S, const Clu *__restr
 //
 // The two reverse pair sweeps in FP32 for mixed-precision contexts: the
 // same pair terms (pair_adj) with x_ij formed from hi/lo splits of the
-// hole-relative positions, FP32 partial sums over a tile folded into FP64.
-// Records (float4, per slot, far form): A = (hi d, m), B = (lo d, R^2),
-// C = (v, C), D = (-e/1.5, 0), E = (w, 0), made from the FP64 records.
-
-constexpr int kAdjTileF = 64;     // slots per shared-memory tile (FP32 sweeps)
+// hole-relative positions.  Records (float4, per slot, far form): A = (hi d, m),
+// B = (lo d, R^2), C = (v, C), D = (-e/1.5, 0), E = (w, 0), made from the
+// FP64 records; the forward pair kernel stages them.
 
 __global__ void __launch_bounds__(kGlueThreads)
 k_adj_frec(int64_t S, const double4_32a *__restrict__ rec, float4 *__restrict__ frec)
@@ -949,173 +947,325 @@ k_adj_frec(int64_t S, const double4_32a *__restrict__ rec, float4 *__restrict__ 
     frec[4 * S + t] = make_float4((float)A6.x, (float)A6.y, (float)A6.z, 0.0f);
 }
 
-struct PairAdjF {
-    float x[3], is, is2, mis3, xvj, F, Gq, Vx, Hb, gx[3];
-};
+// ---- packed sweeps (two targets or two sources per f32x2 lane pair) ----
+//
+// The same two sweeps with every step of the pair body one f32x2 operation
+// for two lanes of the thread, tiles staged by bulk copies into two shared
+// buffers, FP32 partials of kAdjPackFlush tiles added into the FP64 outputs.
+// Grid (256-slot blocks, splits); split s of a block with T tiles sweeps
+// tiles [s T / js, (s+1) T / js).  Sources are the acceleration kernel's
+// staged records (9 float4 per slot, fields duplicated, positions negated);
+// targets of the source sweep come from k_adj_tstage: 13 float4 per slot,
+// (hi d, lo d, 8/3 v, the 16 sum cotangents with the fourth negated), fields
+// duplicated.
 
-// pair_adj in single precision; x = (hi_i - hi_j) + (lo_i - lo_j).
-__device__ __forceinline__ void pair_adj_f(const float (&hi)[3], const float (&lo)[3],
-                                           const float (&vpi)[3], const float4 &A,
-                                           const float4 &B, const float4 &C, const float4 &D,
-                                           const float4 &E, float eps2,
-                                           const float (&sb)[kFusedVals], PairAdjF &p)
-{
-    p.x[0] = (hi[0] - A.x) + (lo[0] - B.x);
-    p.x[1] = (hi[1] - A.y) + (lo[1] - B.y);
-    p.x[2] = (hi[2] - A.z) + (lo[2] - B.z);
-    const float s2 = fmaf(p.x[0], p.x[0], fmaf(p.x[1], p.x[1], fmaf(p.x[2], p.x[2], eps2)));
-    p.is = rsqrt_approx(s2);
-    p.is2 = p.is * p.is;
-    p.mis3 = A.w * p.is * p.is2;
-    p.xvj = fmaf(p.x[0], C.x, fmaf(p.x[1], C.y, p.x[2] * C.z));
-    const float xvi = fmaf(p.x[0], vpi[0], fmaf(p.x[1], vpi[1], p.x[2] * vpi[2]));
-    const float di[3] = {hi[0] + lo[0], hi[1] + lo[1], hi[2] + lo[2]};
-    const float kk = C.w + fmaf(vpi[0], C.x, fmaf(vpi[1], C.y, vpi[2] * C.z)) +
-                     fmaf(D.x, di[0], fmaf(D.y, di[1], D.z * di[2]));
-    p.F = p.xvj * p.xvj * p.is2 + kk;
-    p.Gq = xvi - 2.0f * p.xvj;
-    const float P = fmaf(sb[0], p.x[0], fmaf(sb[1], p.x[1], sb[2] * p.x[2])) + sb[4] + sb[5] * B.w;
-    p.Vx = fmaf(sb[6], p.x[0], fmaf(sb[7], p.x[1], sb[8] * p.x[2]));
-    p.Hb = sb[9] + fmaf(sb[10], C.x, fmaf(sb[11], C.y, sb[12] * C.z));
-    const float Ew = fmaf(sb[13], E.x, fmaf(sb[14], E.y, sb[15] * E.z));
-    const float B2 = P + p.F * p.Vx + p.Gq * p.Hb;
-    const float cx = -3.0f * p.mis3 * p.is2 * B2 -
-                     2.0f * p.mis3 * p.Vx * p.xvj * p.xvj * p.is2 * p.is2 - sb[3] * p.mis3 -
-                     Ew * p.is * p.is2;
-    const float cv = 2.0f * p.Vx * p.xvj * p.is2 - 2.0f * p.Hb;
-    const float cvec[3] = {C.x, C.y, C.z};
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-        p.gx[k] = cx * p.x[k] + p.mis3 * (sb[k] + p.F * sb[6 + k] + p.Hb * vpi[k] + cv * cvec[k]);
-}
+constexpr int kAdjPackTile = 64;
+constexpr int kAdjPackFlush = 8;
+constexpr int kAdjTVals = 13;
 
-__global__ void __launch_bounds__(kJThreads)
-k_adj_targets_f(const float4 *__restrict__ frec, int64_t S, const Clu *__restrict__ clu,
-                const int *__restrict__ blk_clu, const double *__restrict__ sbar,
-                double *__restrict__ tpart)
+__global__ void __launch_bounds__(kGlueThreads)
+k_adj_tstage(int64_t S, const float4 *__restrict__ frec, const double *__restrict__ sbar,
+             float4 *__restrict__ tst)
 {
-    __shared__ float4 sh[5][kAdjTileF];
-    const int64_t t0 = (int64_t)blockIdx.x * kJThreads;
-    const Clu C = clu[cluster_of_block(blk_clu, t0 / kGlueThreads)];
-    const int ntiles = (int)(C.ns_pad / kAdjTileF);
-    const int tps = (ntiles + (int)gridDim.y - 1) / (int)gridDim.y;
-    const int64_t ti = t0 + threadIdx.x;
-    const float4 TA = frec[ti], TB = frec[S + ti], TC = frec[2 * S + ti];
-    const float hi[3] = {TA.x, TA.y, TA.z}, lo[3] = {TB.x, TB.y, TB.z};
-    const float vpi[3] = {8.0f / 3.0f * TC.x, 8.0f / 3.0f * TC.y, 8.0f / 3.0f * TC.z};
+    const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
+    if (t >= S)
+        return;
+    const float4 A = frec[t], B = frec[S + t], C = frec[2 * S + t];
     float sb[kFusedVals];
 #pragma unroll
     for (int k = 0; k < kFusedVals; ++k)
-        sb[k] = (float)sbar[(int64_t)k * S + ti];
-    const float eps2 = (float)C.eps2;
-    double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    const int tb = blockIdx.y * tps;
-    const int te = min(ntiles, tb + tps);
-    for (int tile = tb; tile < te; ++tile) {
-        const int64_t j0 = C.slot0 + (int64_t)tile * kAdjTileF;
-        __syncthreads();
-        for (int q = threadIdx.x; q < 5 * kAdjTileF; q += kJThreads)
-            sh[q / kAdjTileF][q % kAdjTileF] = frec[(q / kAdjTileF) * S + j0 + q % kAdjTileF];
-        __syncthreads();
-        float part[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll 1
-        for (int q = 0; q < kAdjTileF; ++q) {
-            if (j0 + q == ti)
-                continue;
-            const float4 A = sh[0][q], B = sh[1][q], Cc = sh[2][q], D = sh[3][q], E = sh[4][q];
-            PairAdjF p;
-            pair_adj_f(hi, lo, vpi, A, B, Cc, D, E, eps2, sb, p);
-            const float Dv[3] = {D.x, D.y, D.z}, vj[3] = {Cc.x, Cc.y, Cc.z};
+        sb[k] = (float)sbar[(int64_t)k * S + t];
+    sb[3] = -sb[3];
+    const float e3 = 8.0f / 3.0f;
+    auto dup = [](float a, float b) { return make_float4(a, a, b, b); };
+    float4 *o = tst + t * kAdjTVals;
+    o[0] = dup(A.x, A.y);
+    o[1] = dup(A.z, B.x);
+    o[2] = dup(B.y, B.z);
+    o[3] = dup(e3 * C.x, e3 * C.y);
+    o[4] = dup(e3 * C.z, sb[0]);
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                part[k] += p.gx[k] + p.mis3 * p.Vx * Dv[k];
-                part[3 + k] += p.mis3 * (p.Hb * p.x[k] + p.Vx * vj[k]);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < 6; ++k)
-            acc[k] += (double)part[k];
-    }
-    double *out = tpart + (int64_t)blockIdx.y * 6 * S;
-    for (int k = 0; k < 6; ++k)
-        out[(int64_t)k * S + ti] = acc[k];
+    for (int k = 0; k < 7; ++k)
+        o[5 + k] = dup(sb[1 + 2 * k], sb[2 + 2 * k]);
+    o[12] = dup(sb[15], 0.0f);
 }
 
-__global__ void __launch_bounds__(kJThreads)
-k_adj_sources_f(const float4 *__restrict__ frec, int64_t S, const Clu *__restrict__ clu,
-                const int *__restrict__ blk_clu, const double *__restrict__ sbar,
-                double *__restrict__ spart)
+// Intermediates of one packed pair (two lanes), as in pair_adj:
+//   x = d_i - d_j (hi/lo), is = 1/s, mis3 = m_j is^3, h = xvj is^2,
+//   F = xvj h + k, Gq = xvi - 2 xvj, Vx, Hb, cv = 2 (Vx h - Hb), gx = dphi/dx.
+struct AdjP2 {
+    float2 x, y, z, is, mis3, F, Gq, Vx, Hb, cv, gx, gy, gz, dx, dy, dz;   // d = d_i (hi + lo)
+};
+
+// sb: the target's 16 cotangents with sb[3] negated.
+__device__ __forceinline__ void adj_pair2(float2 hx, float2 hy, float2 hz, float2 lx, float2 ly,
+                                          float2 lz, float2 vpx, float2 vpy, float2 vpz,
+                                          const float2 (&sb)[kFusedVals], float2 nhx, float2 nhy,
+                                          float2 nhz, float2 nlx, float2 nly, float2 nlz,
+                                          float2 m, float2 R2, float2 vjx, float2 vjy, float2 vjz,
+                                          float2 Cj, float2 Dx, float2 Dy, float2 Dz, float2 wx,
+                                          float2 wy, float2 wz, float2 eps2, bool selfx,
+                                          bool selfy, AdjP2 &p)
 {
-    __shared__ float sdh[kAdjTileF][3], sdl[kAdjTileF][3], svp[kAdjTileF][3];
-    __shared__ float ssb[kAdjTileF][kFusedVals + 1];
-    const int64_t t0 = (int64_t)blockIdx.x * kJThreads;
-    const Clu C = clu[cluster_of_block(blk_clu, t0 / kGlueThreads)];
-    const int ntiles = (int)(C.ns_pad / kAdjTileF);
-    const int tps = (ntiles + (int)gridDim.y - 1) / (int)gridDim.y;
-    const int64_t tj = t0 + threadIdx.x;
-    const float4 A = frec[tj], B = frec[S + tj], Cc = frec[2 * S + tj], D = frec[3 * S + tj],
-                 E = frec[4 * S + tj];
-    const float eps2 = (float)C.eps2;
-    double acc[kAdjSrc];
-    for (int k = 0; k < kAdjSrc; ++k)
-        acc[k] = 0.0;
-    const int tb = blockIdx.y * tps;
-    const int te = min(ntiles, tb + tps);
-    for (int tile = tb; tile < te; ++tile) {
-        const int64_t i0 = C.slot0 + (int64_t)tile * kAdjTileF;
-        __syncthreads();
-        for (int q = threadIdx.x; q < kAdjTileF; q += kJThreads) {
-            const float4 TA = frec[i0 + q], TB = frec[S + i0 + q], TC = frec[2 * S + i0 + q];
-            sdh[q][0] = TA.x;
-            sdh[q][1] = TA.y;
-            sdh[q][2] = TA.z;
-            sdl[q][0] = TB.x;
-            sdl[q][1] = TB.y;
-            sdl[q][2] = TB.z;
-            svp[q][0] = 8.0f / 3.0f * TC.x;
-            svp[q][1] = 8.0f / 3.0f * TC.y;
-            svp[q][2] = 8.0f / 3.0f * TC.z;
-        }
-        for (int q = threadIdx.x; q < kAdjTileF * kFusedVals; q += kJThreads)
-            ssb[q % kAdjTileF][q / kAdjTileF] =
-                (float)sbar[(int64_t)(q / kAdjTileF) * S + i0 + q % kAdjTileF];
-        __syncthreads();
-        float part[kAdjSrc];
-#pragma unroll
-        for (int k = 0; k < kAdjSrc; ++k)
-            part[k] = 0.0f;
-#pragma unroll 1
-        for (int q = 0; q < kAdjTileF; ++q) {
-            if (i0 + q == tj)
-                continue;
-            const float hi[3] = {sdh[q][0], sdh[q][1], sdh[q][2]};
-            const float lo[3] = {sdl[q][0], sdl[q][1], sdl[q][2]};
-            const float vpi[3] = {svp[q][0], svp[q][1], svp[q][2]};
-            float sb[kFusedVals];
-#pragma unroll
-            for (int k = 0; k < kFusedVals; ++k)
-                sb[k] = ssb[q][k];
-            PairAdjF p;
-            pair_adj_f(hi, lo, vpi, A, B, Cc, D, E, eps2, sb, p);
-            const float gg = p.mis3 * p.Gq;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                part[k] -= p.gx[k];
-                part[3 + k] += p.mis3 * (p.Vx * (2.0f * p.xvj * p.is2 * p.x[k] + vpi[k]) -
-                                         2.0f * p.Hb * p.x[k]) + gg * sb[10 + k];
-                part[8 + k] += p.mis3 * p.Vx * (hi[k] + lo[k]);
-                part[11 + k] += p.is * sb[13 + k];
-            }
-            part[6] += p.mis3 * sb[5];
-            part[7] += p.mis3 * p.Vx;
-        }
-#pragma unroll
-        for (int k = 0; k < kAdjSrc; ++k)
-            acc[k] += (double)part[k];
+    p.x = add2(add2(hx, nhx), add2(lx, nlx));
+    p.y = add2(add2(hy, nhy), add2(ly, nly));
+    p.z = add2(add2(hz, nhz), add2(lz, nlz));
+    float2 s2 = fma2(p.x, p.x, fma2(p.y, p.y, fma2(p.z, p.z, eps2)));
+    // a lane's own slot contributes nothing (is = 0 zeroes every term, the
+    // source sweep's is-weighted w cotangent included)
+    if (selfx) {
+        s2.x = 1.0f; m.x = 0.0f; wx.x = wy.x = wz.x = 0.0f;
     }
-    double *out = spart + (int64_t)blockIdx.y * kAdjSrc * S;
+    if (selfy) {
+        s2.y = 1.0f; m.y = 0.0f; wx.y = wy.y = wz.y = 0.0f;
+    }
+    p.is = make_float2(selfx ? 0.0f : rsqrt_approx(s2.x), selfy ? 0.0f : rsqrt_approx(s2.y));
+    const float2 is2 = mul2(p.is, p.is);
+    p.mis3 = mul2(mul2(m, p.is), is2);
+    const float2 xvj = fma2(p.x, vjx, fma2(p.y, vjy, mul2(p.z, vjz)));
+    const float2 xvi = fma2(p.x, vpx, fma2(p.y, vpy, mul2(p.z, vpz)));
+    float2 kk = fma2(vpx, vjx, fma2(vpy, vjy, fma2(vpz, vjz, Cj)));
+    // D_j . d_i with d_i = hi + lo: D_j is large for stars close to the hole
+    p.dx = add2(hx, lx);
+    p.dy = add2(hy, ly);
+    p.dz = add2(hz, lz);
+    kk = fma2(Dx, p.dx, fma2(Dy, p.dy, fma2(Dz, p.dz, kk)));
+    const float2 h = mul2(xvj, is2);
+    p.F = fma2(h, xvj, kk);
+    p.Gq = fma2(make_float2(-2.0f, -2.0f), xvj, xvi);
+    const float2 P = fma2(sb[0], p.x, fma2(sb[1], p.y, fma2(sb[2], p.z, fma2(sb[5], R2, sb[4]))));
+    p.Vx = fma2(sb[6], p.x, fma2(sb[7], p.y, mul2(sb[8], p.z)));
+    p.Hb = fma2(sb[10], vjx, fma2(sb[11], vjy, fma2(sb[12], vjz, sb[9])));
+    const float2 Ew = fma2(sb[13], wx, fma2(sb[14], wy, mul2(sb[15], wz)));
+    const float2 B = fma2(p.F, p.Vx, fma2(p.Gq, p.Hb, P));
+    const float2 b = mul2(p.Vx, h);
+    // cx = mis3 (-3 is^2 B - 2 Vx h^2 - sb3) - Ew is^3
+    float2 a = fma2(mul2(is2, make_float2(-3.0f, -3.0f)), B, sb[3]);
+    a = fma2(mul2(b, make_float2(-2.0f, -2.0f)), h, a);
+    const float2 cx = fma2(mul2(Ew, make_float2(-1.0f, -1.0f)), mul2(p.is, is2), mul2(p.mis3, a));
+    p.cv = fma2(b, make_float2(2.0f, 2.0f), mul2(p.Hb, make_float2(-2.0f, -2.0f)));
+    p.gx = fma2(cx, p.x, mul2(p.mis3, fma2(p.cv, vjx, fma2(p.Hb, vpx, fma2(p.F, sb[6], sb[0])))));
+    p.gy = fma2(cx, p.y, mul2(p.mis3, fma2(p.cv, vjy, fma2(p.Hb, vpy, fma2(p.F, sb[7], sb[1])))));
+    p.gz = fma2(cx, p.z, mul2(p.mis3, fma2(p.cv, vjz, fma2(p.Hb, vpz, fma2(p.F, sb[8], sb[2])))));
+}
+
+// Adds (first: stores) one FP32 partial into an FP64 output.
+__device__ __forceinline__ void adj_out(double *o, float p, bool first)
+{
+    *o = first ? (double)p : *o + (double)p;
+}
+
+// The bulk-copy tile pipeline shared by the two packed sweeps: tiles
+// [tb, te) of VALS float4 per slot starting at slot slot0 of `rec`, into two
+// shared buffers; body(tile, first slot) per tile, flush(first) every
+// kAdjPackFlush tiles and after the last.  False if a wait gave up (the
+// block must then exit: every thread returns false together).
+template <int VALS, class Body, class Flush>
+__device__ __forceinline__ bool adj_sweep(const float4 *__restrict__ rec, int64_t slot0,
+                                          int64_t tb, int64_t te,
+                                          float4 (*sh)[kAdjPackTile][VALS], uint64_t *full,
+                                          Body body, Flush flush)
+{
+    constexpr unsigned kBytes = kAdjPackTile * VALS * 16;
+    if (threadIdx.x == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bulk_load(sh[0], rec + (slot0 + tb * kAdjPackTile) * VALS, kBytes, &full[0], 0);
+        if (tb + 1 < te)
+            bulk_load(sh[1], rec + (slot0 + (tb + 1) * kAdjPackTile) * VALS, kBytes, &full[1], 0);
+    }
+    bool first = true;
+    for (int64_t tile = tb; tile < te; ++tile) {
+        const int b = (int)((tile - tb) & 1);
+        const bool ok = mbar_wait(&full[b], (unsigned)(((tile - tb) >> 1) & 1));
+        body(sh[b], slot0 + tile * kAdjPackTile);
+        if (((tile - tb + 1) % kAdjPackFlush) == 0 || tile + 1 == te) {
+            flush(first);
+            first = false;
+        }
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0 && tile + 1 < te)
+                mbar_wait(&full[b ^ 1], (unsigned)(((tile - tb + 1) >> 1) & 1));
+            return false;
+        }
+        if (threadIdx.x == 0 && tile + 2 < te)
+            bulk_load(sh[b], rec + (slot0 + (tile + 2) * kAdjPackTile) * VALS, kBytes, &full[b],
+                      0);
+    }
+    return true;
+}
+
+// Reverse sweep over sources for two targets per thread: tpart[split][6][slot]
+// = (dphi/dd_i, dphi/dv'_i) summed over the split's sources.
+__global__ void __launch_bounds__(kMixThreads, 4)
+k_adj_targets_packed(const float4 *__restrict__ srec, int64_t S, const Clu *__restrict__ clu,
+                     const int *__restrict__ blk_clu, const double *__restrict__ sbar,
+                     int *__restrict__ flag, double *__restrict__ tpart)
+{
+    __shared__ __align__(128) float4 sh[2][kAdjPackTile][kPackVals];
+    __shared__ __align__(8) uint64_t full[2];
+    const int64_t t0 = (int64_t)blockIdx.x * 2 * kMixThreads;
+    const Clu C = clu[cluster_of_block(blk_clu, t0 / kGlueThreads)];
+    const int64_t ntiles = C.ns_pad / kAdjPackTile, js = gridDim.y, sp = blockIdx.y;
+    const int64_t tb = sp * ntiles / js, te = (sp + 1) * ntiles / js;
+    double *out = tpart + sp * 6 * S;
+    const int64_t ta = t0 + threadIdx.x, tq = ta + kMixThreads;
+    if (te <= tb) {
+        for (int k = 0; k < 6; ++k) {
+            out[k * S + ta] = 0.0;
+            out[k * S + tq] = 0.0;
+        }
+        return;
+    }
+    const float4 *ra = srec + ta * kPackVals, *rq = srec + tq * kPackVals;
+    const float4 A0 = ra[0], A1 = ra[1], A2 = ra[2], A3 = ra[3], A4 = ra[4], A5 = ra[5];
+    const float4 B0 = rq[0], B1 = rq[1], B2 = rq[2], B3 = rq[3], B4 = rq[4], B5 = rq[5];
+    const float e3 = 8.0f / 3.0f;
+    const float2 hx = make_float2(-A0.x, -B0.x), hy = make_float2(-A0.z, -B0.z),
+                 hz = make_float2(-A1.x, -B1.x), lx = make_float2(-A2.x, -B2.x),
+                 ly = make_float2(-A2.z, -B2.z), lz = make_float2(-A3.x, -B3.x);
+    const float2 vpx = make_float2(e3 * A4.x, e3 * B4.x), vpy = make_float2(e3 * A4.z, e3 * B4.z),
+                 vpz = make_float2(e3 * A5.x, e3 * B5.x);
+    float2 sb[kFusedVals];
+#pragma unroll
+    for (int k = 0; k < kFusedVals; ++k)
+        sb[k] = make_float2((float)sbar[k * S + ta], (float)sbar[k * S + tq]);
+    sb[3] = make_float2(-sb[3].x, -sb[3].y);
+    const float e2 = (float)C.eps2;
+    const float2 eps2 = make_float2(e2, e2);
+    float2 acc[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+        acc[k] = make_float2(0.0f, 0.0f);
+    auto body = [&](const float4 (*tl)[kPackVals], int64_t j0) {
+        const bool diag = (j0 < t0 + 2 * kMixThreads) && (t0 < j0 + kAdjPackTile);
+#pragma unroll 1
+        for (int q = 0; q < kAdjPackTile; ++q) {
+            const float4 S0 = tl[q][0], S1 = tl[q][1], S2 = tl[q][2], S3 = tl[q][3],
+                         S4 = tl[q][4], S5 = tl[q][5], S6 = tl[q][6], S7 = tl[q][7],
+                         S8 = tl[q][8];
+            const bool sx = diag && j0 + q == ta, sy = diag && j0 + q == tq;
+            AdjP2 p;
+            adj_pair2(hx, hy, hz, lx, ly, lz, vpx, vpy, vpz, sb, lo2(S0), hi2(S0), lo2(S1),
+                      lo2(S2), hi2(S2), lo2(S3), hi2(S1), hi2(S3), lo2(S4), hi2(S4), lo2(S5),
+                      hi2(S5), lo2(S6), hi2(S6), lo2(S7), hi2(S7), lo2(S8), hi2(S8), eps2, sx, sy,
+                      p);
+            const float2 mVx = mul2(p.mis3, p.Vx), mHb = mul2(p.mis3, p.Hb);
+            acc[0] = fma2(mVx, lo2(S6), add2(acc[0], p.gx));
+            acc[1] = fma2(mVx, hi2(S6), add2(acc[1], p.gy));
+            acc[2] = fma2(mVx, lo2(S7), add2(acc[2], p.gz));
+            acc[3] = fma2(mHb, p.x, fma2(mVx, lo2(S4), acc[3]));
+            acc[4] = fma2(mHb, p.y, fma2(mVx, hi2(S4), acc[4]));
+            acc[5] = fma2(mHb, p.z, fma2(mVx, lo2(S5), acc[5]));
+        }
+    };
+    auto flush = [&](bool first) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            adj_out(out + k * S + ta, acc[k].x, first);
+            adj_out(out + k * S + tq, acc[k].y, first);
+            acc[k] = make_float2(0.0f, 0.0f);
+        }
+    };
+    if (!adj_sweep<kPackVals>(srec, C.slot0, tb, te, sh, full, body, flush) && threadIdx.x == 0)
+        atomicOr(flag, kFlagTimeout);
+}
+
+// Reverse sweep over targets for two sources per thread: spart[split][14][slot]
+// = cotangents of the source records (d via x, v, R^2, C, D, w).
+__global__ void __launch_bounds__(kMixThreads, 3)
+k_adj_sources_packed(const float4 *__restrict__ srec, const float4 *__restrict__ tst, int64_t S,
+                     const Clu *__restrict__ clu, const int *__restrict__ blk_clu,
+                     int *__restrict__ flag, double *__restrict__ spart)
+{
+    __shared__ __align__(128) float4 sh[2][kAdjPackTile][kAdjTVals];
+    __shared__ __align__(8) uint64_t full[2];
+    const int64_t t0 = (int64_t)blockIdx.x * 2 * kMixThreads;
+    const Clu C = clu[cluster_of_block(blk_clu, t0 / kGlueThreads)];
+    const int64_t ntiles = C.ns_pad / kAdjPackTile, js = gridDim.y, sp = blockIdx.y;
+    const int64_t tb = sp * ntiles / js, te = (sp + 1) * ntiles / js;
+    double *out = spart + sp * kAdjSrc * S;
+    const int64_t ja = t0 + threadIdx.x, jq = ja + kMixThreads;
+    if (te <= tb) {
+        for (int k = 0; k < kAdjSrc; ++k) {
+            out[k * S + ja] = 0.0;
+            out[k * S + jq] = 0.0;
+        }
+        return;
+    }
+    const float4 *ra = srec + ja * kPackVals, *rq = srec + jq * kPackVals;
+    float4 A[kPackVals], B[kPackVals];
+#pragma unroll
+    for (int k = 0; k < kPackVals; ++k) {
+        A[k] = ra[k];
+        B[k] = rq[k];
+    }
+    auto pr = [&](int k, bool high) {
+        return high ? make_float2(A[k].z, B[k].z) : make_float2(A[k].x, B[k].x);
+    };
+    const float2 nhx = pr(0, false), nhy = pr(0, true), nhz = pr(1, false), m = pr(1, true);
+    const float2 nlx = pr(2, false), nly = pr(2, true), nlz = pr(3, false), R2 = pr(3, true);
+    const float2 vjx = pr(4, false), vjy = pr(4, true), vjz = pr(5, false), Cj = pr(5, true);
+    const float2 Dx = pr(6, false), Dy = pr(6, true), Dz = pr(7, false), wx = pr(7, true);
+    const float2 wy = pr(8, false), wz = pr(8, true);
+    const float e2 = (float)C.eps2;
+    const float2 eps2 = make_float2(e2, e2);
+    float2 acc[kAdjSrc];
+#pragma unroll
     for (int k = 0; k < kAdjSrc; ++k)
-        out[(int64_t)k * S + tj] = acc[k];
+        acc[k] = make_float2(0.0f, 0.0f);
+    auto body = [&](const float4 (*tl)[kAdjTVals], int64_t i0) {
+        const bool diag = (i0 < t0 + 2 * kMixThreads) && (t0 < i0 + kAdjPackTile);
+#pragma unroll 1
+        for (int q = 0; q < kAdjPackTile; ++q) {
+            const float4 *T = tl[q];
+            const float4 T0 = T[0], T1 = T[1], T2 = T[2], T3 = T[3], T4 = T[4];
+            float2 sb[kFusedVals];
+            sb[0] = hi2(T4);
+#pragma unroll
+            for (int k = 0; k < 7; ++k) {
+                const float4 Tk = T[5 + k];
+                sb[1 + 2 * k] = lo2(Tk);
+                sb[2 + 2 * k] = hi2(Tk);
+            }
+            sb[15] = lo2(T[12]);
+            const bool sx = diag && i0 + q == ja, sy = diag && i0 + q == jq;
+            AdjP2 p;
+            adj_pair2(lo2(T0), hi2(T0), lo2(T1), hi2(T1), lo2(T2), hi2(T2), lo2(T3), hi2(T3),
+                      lo2(T4), sb, nhx, nhy, nhz, nlx, nly, nlz, m, R2, vjx, vjy, vjz, Cj, Dx, Dy,
+                      Dz, wx, wy, wz, eps2, sx, sy, p);
+            const float2 mVx = mul2(p.mis3, p.Vx), gg = mul2(p.mis3, p.Gq);
+            acc[0] = add2(acc[0], p.gx);         // negated at the flush
+            acc[1] = add2(acc[1], p.gy);
+            acc[2] = add2(acc[2], p.gz);
+            acc[3] = fma2(gg, sb[10], fma2(p.mis3, fma2(p.cv, p.x, mul2(p.Vx, lo2(T3))), acc[3]));
+            acc[4] = fma2(gg, sb[11], fma2(p.mis3, fma2(p.cv, p.y, mul2(p.Vx, hi2(T3))), acc[4]));
+            acc[5] = fma2(gg, sb[12], fma2(p.mis3, fma2(p.cv, p.z, mul2(p.Vx, lo2(T4))), acc[5]));
+            acc[6] = fma2(p.mis3, sb[5], acc[6]);
+            acc[7] = add2(acc[7], mVx);
+            acc[8] = fma2(mVx, p.dx, acc[8]);
+            acc[9] = fma2(mVx, p.dy, acc[9]);
+            acc[10] = fma2(mVx, p.dz, acc[10]);
+            acc[11] = fma2(p.is, sb[13], acc[11]);
+            acc[12] = fma2(p.is, sb[14], acc[12]);
+            acc[13] = fma2(p.is, sb[15], acc[13]);
+        }
+    };
+    auto flush = [&](bool first) {
+#pragma unroll
+        for (int k = 0; k < kAdjSrc; ++k) {
+            const float sgn = k < 3 ? -1.0f : 1.0f;
+            adj_out(out + k * S + ja, sgn * acc[k].x, first);
+            adj_out(out + k * S + jq, sgn * acc[k].y, first);
+            acc[k] = make_float2(0.0f, 0.0f);
+        }
+    };
+    if (!adj_sweep<kAdjTVals>(tst, C.slot0, tb, te, sh, full, body, flush) && threadIdx.x == 0)
+        atomicOr(flag, kFlagTimeout);
 }
 
 // Per star slot: the records' and cluster sums' reverse (forward-mode Duals
@@ -1353,11 +1503,25 @@ cudaError_t launch_jerk(pn_ctx *c, const double *x, const double *v, const doubl
 // Adjoint scratch (doubles): sbar 16 S, kbar 6 S, target partials js 6 S,
 // source partials js 14 S, block cotangents (S/8) 11, cluster cotangents
 // nclu 11, hole blocks (S/256) 4.
+// Splits of the packed adjoint sweeps: about eight waves of 3 blocks per SM
+// over the 256-slot blocks, at least one tile per split, at most the FP64
+// sweeps' splits (the partial buffers hold those).
+static int64_t adj_pack_splits(const pn_ctx *c)
+{
+    const int64_t nb = c->S / (2 * kMixThreads);
+    int64_t js = (8 * 3 * (int64_t)c->sm_count) / nb;
+    const int64_t tiles = c->max_ns_pad / kAdjPackTile;
+    const int64_t cap = jerk_part_splits(c);
+    js = js < 1 ? 1 : js;
+    js = js > tiles ? tiles : js;
+    return js > cap ? cap : js;
+}
+
 size_t adjoint_buffer_doubles(const pn_ctx *c)
 {
     const int64_t S = c->S, nglue = S / kGlueThreads, js = jerk_part_splits(c);
-    return (size_t)((16 + 6) * S + js * (6 + kAdjSrc) * S + (S / kAdjStarWarps) * kAdjGlob +
-                    nglue * 4 + (int64_t)c->nclu * kAdjGlob);
+    return (size_t)((16 + 6) * S + js * (6 + kAdjSrc) * S + kAdjTVals * 2 * S +
+                    (S / kAdjStarWarps) * kAdjGlob + nglue * 4 + (int64_t)c->nclu * kAdjGlob);
 }
 
 cudaError_t launch_accel_vjp(pn_ctx *c, const double *x, const double *v, const double *m,
@@ -1371,7 +1535,10 @@ cudaError_t launch_accel_vjp(pn_ctx *c, const double *x, const double *v, const 
     double *jblk = part + (int64_t)js * 2 * kFusedVals * S;
     double *jglob = jblk + nglue * 2 * kJVals;
     double *sbar = c->abuf, *kbar = sbar + 16 * S, *tpart = kbar + 6 * S;
-    double *spart = tpart + (int64_t)js * 6 * S, *kblk = spart + (int64_t)js * kAdjSrc * S;
+    double *spart = tpart + (int64_t)js * 6 * S;
+    // staged targets of the packed source sweep (13 float4 per slot, 16-byte aligned)
+    float4 *tst = reinterpret_cast<float4 *>(spart + (int64_t)js * kAdjSrc * S);
+    double *kblk = spart + (int64_t)js * kAdjSrc * S + kAdjTVals * 2 * S;
     double *gbar = kblk + (S / kAdjStarWarps) * kAdjGlob, *hblk = gbar + (int64_t)c->nclu * kAdjGlob;
     const int *bc = c->nclu > 1 ? c->blk_clu : nullptr;
     dim3 grid((unsigned)(S / kJThreads), (unsigned)js);
@@ -1407,15 +1574,35 @@ cudaError_t launch_accel_vjp(pn_ctx *c, const double *x, const double *v, const 
     k_adj_star<<<(unsigned)(S / kAdjStarWarps), kGlueThreads, 0, c->stream>>>(S, c->d_clu, bc, x, v, m, fwd, jsf,
                                                                jglob, abar, sbar, kbar, kblk);
     k_adj_globals<<<c->nclu, kGlueThreads, 0, c->stream>>>(c->d_clu, kblk, gbar);
+    int jsr = js;
     if (mixed) {
-        k_adj_targets_f<<<grid, kJThreads, 0, c->stream>>>(frec, S, c->d_clu, bc, sbar, tpart);
-        k_adj_sources_f<<<grid, kJThreads, 0, c->stream>>>(frec, S, c->d_clu, bc, sbar, spart);
+        // packed sweeps: sources from the staged records of the forward pass
+        const float4 *srec = c->mrec + 5 * S;
+        if (!c->fused_packed)          // the scalar forward kernel stages nothing
+            if ((e = launch_stage_sources(c, frec)) != cudaSuccess)
+                return e;
+        jsr = (int)adj_pack_splits(c);
+        static bool carveout = false;     // 4 and 3 blocks per SM need the large carveout
+        if (!carveout) {
+            cudaFuncSetAttribute(k_adj_targets_packed,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+            cudaFuncSetAttribute(k_adj_sources_packed,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+            carveout = true;
+        }
+        const dim3 pgrid((unsigned)(S / (2 * kMixThreads)), (unsigned)jsr);
+        k_adj_tstage<<<(unsigned)nglue, kGlueThreads, 0, c->stream>>>(S, frec, sbar, tst);
+        k_adj_targets_packed<<<pgrid, kMixThreads, 0, c->stream>>>(srec, S, c->d_clu, bc, sbar,
+                                                                  c->flag, tpart);
+        k_adj_sources_packed<<<pgrid, kMixThreads, 0, c->stream>>>(srec, tst, S, c->d_clu, bc,
+                                                                  c->flag, spart);
+        c->launches += 1;
     } else {
         k_adj_targets<<<grid, kJThreads, 0, c->stream>>>(rec, S, c->d_clu, bc, sbar, tpart);
         k_adj_sources<<<grid, kJThreads, 0, c->stream>>>(rec, S, c->d_clu, bc, sbar, spart);
     }
     k_adj_records<<<(unsigned)nglue, kGlueThreads, 0, c->stream>>>(
-        S, c->d_clu, bc, x, v, m, abar, kbar, tpart, js, spart, js, gbar, xbar, vbar, hblk);
+        S, c->d_clu, bc, x, v, m, abar, kbar, tpart, jsr, spart, jsr, gbar, xbar, vbar, hblk);
     k_adj_hole<<<c->nclu, kGlueThreads, 0, c->stream>>>(c->d_clu, hblk, gbar, xbar, vbar, scal,
                                                        accumulate ? 1 : 0);
     c->launches += 6;

@@ -15,6 +15,7 @@ constexpr int kMixTargets = 2;     // targets held in registers per thread
 constexpr int kMixTile = 128;      // sources per shared-memory tile
 constexpr int kFlushTiles = 2;     // fused kernel: tiles per single-precision partial
 constexpr int kPackTile = 64;      // packed fused kernel: sources per shared-memory tile
+constexpr int kPackVals = 9;       // packed kernels: float4 per staged source record
 constexpr int kPackFlushTiles = 8; // packed fused kernel: tiles per single-precision partial
 constexpr int kPackWorkersMax = 4;  // packed fused kernel: stream-K workers per resident block (max)
 // Launch shape of the double-precision pair kernels (FP64 mode and energy).
@@ -182,6 +183,7 @@ void shapes(int64_t S, int64_t max_ns_pad, int sm_count, int occ_mix, int occ_f6
 cudaError_t occupancy(int *occ_mix, int *occ_f64);
 cudaError_t fused_occupancy(int P, int unroll, bool packed, int *occ);
 cudaError_t launch_fused(pn_ctx *c);
+cudaError_t launch_stage_sources(pn_ctx *c, const float4 *rec);
 cudaError_t launch_fused_on(pn_ctx *c, const float4 *rec);
 bool use_fused(const pn_ctx *c);
 int fused_tile_size(bool packed);

@@ -730,7 +730,6 @@ struct PackTarget {
     float2 vx, vy, vz;               // 8/3 v_i
 };
 
-constexpr int kPackVals = 9;         // float4 per staged source
 
 template <bool MASK>
 __device__ __forceinline__ void packed_pair(const PackTarget &tg, const float4 *__restrict__ sq,
@@ -1798,6 +1797,16 @@ static cudaError_t launch_fused_with(pn_ctx *c, const Layout &L, const float4 *r
 }
 
 cudaError_t launch_fused(pn_ctx *c) { return launch_fused_with(c, layout(c), c->mrec); }
+
+// Staged source records (c->mrec + 5 S) of the packed kernels from mixed
+// records rec (the prologue writes them for c->mrec itself).
+cudaError_t launch_stage_sources(pn_ctx *c, const float4 *rec)
+{
+    k_stage_sources<<<(unsigned)(c->S / kGlueThreads), kGlueThreads, 0, c->stream>>>(
+        c->S, rec, c->mrec + 5 * c->S);
+    c->launches += 1;
+    return cudaGetLastError();
+}
 
 // The fused pair kernel on caller-built mixed records (same layout as the
 // prologue's), with the fused partial layout whatever the context's pair
