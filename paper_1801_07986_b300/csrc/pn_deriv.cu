@@ -683,14 +683,74 @@ __device__ __forceinline__ void pair_adj(const double (&di)[3], const double (&v
                   p.mis3 * (sb[k] + p.F * sb[6 + k] + p.Hb * vpi[k] + cv * vj[k]);
 }
 
+// Cotangents of the inputs that star_eqs uses linearly — the 16 pair sums
+// (N, U, Z, Wr, V', Hs, Hv, E) and the cluster sums (Q, W_far, SA, SB, Phi)
+// — contracted with ab (of a_i) and bb (of the hole's term, 1/c^2 included),
+// in closed form: every coefficient depends on d_i, v_i and M only.  With
+// al = ab/c^2 (the cotangent of the 1PN bracket), GM = G M, and the
+// bracket's coefficients cN = G (4 GM/R - v^2), cQ = 4 G (v.d)/R^3,
+// c7 = 7/2 G GM:
+//   Nb = -G ab + cN al - 7/2 G^2 m_i/R bb       Ub = 4 G GM/R^3 (al.d) - 5/4 G^2 (bb.w_i)
+//   Zb = -1/4 G^2 R^2 (bb.w_i)   Wrb = 1/4 G^2 (bb.w_i)   V'b = 3/2 G al
+//   Hsb = 3/2 G (al.v)   Hvb = -3/2 G al   Eb = -c7 al
+//   Qb = -4 G/R^3 (al.d) v + 3 G/R^3 (al.v) d + cQ al
+//        + G m_i/(M R^3) [4 (bb.d) v - 3 (v.d) bb - 4 (bb.v) d]
+//   Wfb = 1/2 G GM/R^3 (al.d) d + c7/R al    SAb = -SBb = G GM/R^3 (al.d)
+//   Phib = -4 G^2 (bb.w_i)
+// out: [0..15] the 16 sums' cotangents, [16..24] Q, W_far, SA, SB, Phi.
+__device__ __forceinline__ void star_lin_adj(double G, double M, double mi, double inv_c2,
+                                             const double (&d)[3], const double (&vv)[3],
+                                             const double (&ab)[3], const double (&bb)[3],
+                                             double (&out)[25])
+{
+    const double GM = G * M;
+    const double R2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const double iR = 1.0 / sqrt(R2);
+    const double iR3 = iR * iR * iR;
+    const double v2 = vv[0] * vv[0] + vv[1] * vv[1] + vv[2] * vv[2];
+    const double vd = vv[0] * d[0] + vv[1] * d[1] + vv[2] * d[2];
+    double al[3], wi[3];
+    for (int k = 0; k < 3; ++k) {
+        al[k] = inv_c2 * ab[k];
+        wi[k] = mi * iR3 * d[k];
+    }
+    const double ad = al[0] * d[0] + al[1] * d[1] + al[2] * d[2];
+    const double av = al[0] * vv[0] + al[1] * vv[1] + al[2] * vv[2];
+    const double bd = bb[0] * d[0] + bb[1] * d[1] + bb[2] * d[2];
+    const double bv = bb[0] * vv[0] + bb[1] * vv[1] + bb[2] * vv[2];
+    const double bw = bb[0] * wi[0] + bb[1] * wi[1] + bb[2] * wi[2];
+    const double cN = G * (4.0 * GM * iR - v2), cQ = 4.0 * G * iR3 * vd, c7 = 3.5 * G * GM;
+    const double G2 = G * G, gq = G * mi * iR3 / M, gs = G * GM * iR3 * ad;
+    for (int k = 0; k < 3; ++k) {
+        out[k] = -G * ab[k] + cN * al[k] - 3.5 * G2 * mi * iR * bb[k];     // N
+        out[6 + k] = 1.5 * G * al[k];                                       // V'
+        out[10 + k] = -1.5 * G * al[k];                                     // Hv
+        out[13 + k] = -c7 * al[k];                                          // E
+        out[16 + k] = -4.0 * G * iR3 * ad * vv[k] + 3.0 * G * iR3 * av * d[k] + cQ * al[k] +
+                      gq * (4.0 * bd * vv[k] - 3.0 * vd * bb[k] - 4.0 * bv * d[k]);   // Q
+        out[19 + k] = 0.5 * gs * d[k] + c7 * iR * al[k];                    // W_far
+    }
+    out[3] = 4.0 * gs - 1.25 * G2 * bw;          // U
+    out[4] = -0.25 * G2 * R2 * bw;               // Z
+    out[5] = 0.25 * G2 * bw;                     // Wr
+    out[9] = 1.5 * G * av;                       // Hs
+    out[22] = gs;                                // SA
+    out[23] = -gs;                               // SB
+    out[24] = -4.0 * G2 * bw;                    // Phi
+}
+
 // Per star slot: the assembly's reverse.  Inputs: the forward sums (part,
 // split-major, double), the cluster sums (Dual layout, values used) and the
 // cotangent abar.  Outputs: the sums' cotangents sbar[16][slot], the direct
 // cotangents of d_i and of the velocity kbar[6][slot], and per block the
 // cotangents of the cluster sums, of M and of inv_c2 (kAdjGlob values).
-// One warp per star slot: lane q evaluates the dual seeds q and q + 32 of
-// the 33 inputs, so the O(n) reverse keeps every SM busy.
-constexpr int kAdjStarWarps = kGlueThreads / 32;    // star slots per block
+// Eight lanes per star slot, four stars per warp: lanes 0..6 run star_eqs on
+// Duals seeded in d_i (3), v_i (3) and M, lane 7 unseeded; lane 7 then adds
+// the closed-form cotangents of the linearly entering sums (star_lin_adj),
+// and the 1/c^2 cotangent ab . (1PN bracket) from its pass (A is linear in
+// 1/c^2).
+constexpr int kAdjStarLanes = 8;
+constexpr int kAdjStarWarps = kGlueThreads / kAdjStarLanes;   // star slots per block
 
 __global__ void __launch_bounds__(kGlueThreads)
 k_adj_star(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_clu,
@@ -701,8 +761,8 @@ k_adj_star(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
 {
     __shared__ double su[kAdjStarWarps][33];     // the star's inputs
     __shared__ double sub[kAdjStarWarps][34];    // their cotangents (+ the hole's inv_c2 term)
-    const int wi = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int64_t t = (int64_t)blockIdx.x * kAdjStarWarps + wi;
+    const int st = threadIdx.x / kAdjStarLanes, sl = threadIdx.x % kAdjStarLanes;
+    const int64_t t = (int64_t)blockIdx.x * kAdjStarWarps + st;
     const int k_clu = cluster_of_block(blk_clu, t / kGlueThreads);
     const Clu Cl = clu[k_clu];
     const double *glob = globs + (int64_t)k_clu * 2 * kJVals;
@@ -710,24 +770,24 @@ k_adj_star(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
     const bool star = lt < Cl.ns;
     const int64_t i = Cl.body0 + 1 + lt, hb = Cl.body0;
     if (star) {
-        if (lane < 3) {
-            su[wi][lane] = x[3 * i + lane] - x[3 * hb + lane];
-            su[wi][3 + lane] = v[3 * i + lane];
-            su[wi][22 + lane] = glob[2 * lane];            // Q
-            su[wi][25 + lane] = glob[2 * (6 + lane)];      // W_far (= W: far form)
+        if (sl < 3) {
+            su[st][sl] = x[3 * i + sl] - x[3 * hb + sl];
+            su[st][3 + sl] = v[3 * i + sl];
+            su[st][22 + sl] = glob[2 * sl];            // Q
+            su[st][25 + sl] = glob[2 * (6 + sl)];      // W_far (= W: far form)
         }
-        if (lane < kFusedVals) {
+        for (int k = sl; k < kFusedVals; k += kAdjStarLanes) {
             double sv = 0.0;
             for (int q = 0; q < js; ++q)
-                sv += part[((int64_t)q * kFusedVals + lane) * S + t];
-            su[wi][6 + lane] = sv;
+                sv += part[((int64_t)q * kFusedVals + k) * S + t];
+            su[st][6 + k] = sv;
         }
-        if (lane == 0) {
-            su[wi][28] = glob[18];
-            su[wi][29] = glob[20];
-            su[wi][30] = glob[22];
-            su[wi][31] = m[hb];
-            su[wi][32] = Cl.inv_c2;
+        if (sl == 3) {
+            su[st][28] = glob[18];
+            su[st][29] = glob[20];
+            su[st][30] = glob[22];
+            su[st][31] = m[hb];
+            su[st][32] = Cl.inv_c2;
         }
     }
     __syncwarp();
@@ -735,54 +795,60 @@ k_adj_star(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
         const double ab[3] = {abar[3 * i], abar[3 * i + 1], abar[3 * i + 2]};
         const double bb[3] = {Cl.inv_c2 * abar[3 * hb], Cl.inv_c2 * abar[3 * hb + 1],
                               Cl.inv_c2 * abar[3 * hb + 2]};
-        {
-            const int q = lane;     // seeds 0..31; inv_c2 (32) from the 1PN bracket's value
-            Dual w[33];
-            for (int k = 0; k < 33; ++k)
-                w[k] = dual(su[wi][k], k == q ? 1.0 : 0.0);
-            Dual d[3] = {w[0], w[1], w[2]}, vv[3] = {w[3], w[4], w[5]};
-            StarSums<Dual> ss;
-            for (int k = 0; k < 3; ++k) {
-                ss.N[k] = w[6 + k];
-                ss.Vp[k] = w[12 + k];
-                ss.Hv[k] = w[16 + k];
-                ss.E[k] = w[19 + k];
-                ss.P[k] = dual(0.0, 0.0);
-                ss.Ee[k] = dual(0.0, 0.0);
-            }
-            ss.U = w[9];
-            ss.Z = w[10];
-            ss.Wr = w[11];
-            ss.Hs = w[15];
-            ClusterSums<Dual> gs;
-            for (int k = 0; k < 3; ++k) {
-                gs.Q[k] = w[22 + k];
-                gs.Wf[k] = w[25 + k];
-            }
-            gs.SA = w[28];
-            gs.SB = w[29];
-            gs.Phi = w[30];
-            Dual ai[3], bh[3], pn[3];
-            star_eqs<Dual, Dual>(Cl.G, w[31], m[i], Cl.eps2, w[32], 1.0, d, vv, ss, gs, ai, bh,
-                                 pn);
+        const int seed = sl < 6 ? sl : (sl == 6 ? 31 : -1);
+        Dual w[33];
+        for (int k = 0; k < 33; ++k)
+            w[k] = dual(su[st][k], k == seed ? 1.0 : 0.0);
+        Dual d[3] = {w[0], w[1], w[2]}, vv[3] = {w[3], w[4], w[5]};
+        StarSums<Dual> ss;
+        for (int k = 0; k < 3; ++k) {
+            ss.N[k] = w[6 + k];
+            ss.Vp[k] = w[12 + k];
+            ss.Hv[k] = w[16 + k];
+            ss.E[k] = w[19 + k];
+            ss.P[k] = dual(0.0, 0.0);
+            ss.Ee[k] = dual(0.0, 0.0);
+        }
+        ss.U = w[9];
+        ss.Z = w[10];
+        ss.Wr = w[11];
+        ss.Hs = w[15];
+        ClusterSums<Dual> gs;
+        for (int k = 0; k < 3; ++k) {
+            gs.Q[k] = w[22 + k];
+            gs.Wf[k] = w[25 + k];
+        }
+        gs.SA = w[28];
+        gs.SB = w[29];
+        gs.Phi = w[30];
+        Dual ai[3], bh[3], pn[3];
+        star_eqs<Dual, Dual>(Cl.G, w[31], m[i], Cl.eps2, w[32], 1.0, d, vv, ss, gs, ai, bh, pn);
+        if (seed >= 0) {
             double acc = 0.0;
             for (int k = 0; k < 3; ++k)
                 acc += ab[k] * ai[k].d + bb[k] * bh[k].d;
-            sub[wi][q] = acc;
-            if (q == 0) {
-                // d/d(inv_c2): abar_i . (1PN bracket); bh does not depend on it
-                sub[wi][32] = ab[0] * pn[0].v + ab[1] * pn[1].v + ab[2] * pn[2].v;
-                // the hole's inv_c2 term: abar_hole . (star i's term)
-                sub[wi][33] = abar[3 * hb] * bh[0].v + abar[3 * hb + 1] * bh[1].v +
-                              abar[3 * hb + 2] * bh[2].v;
-            }
+            sub[st][seed] = acc;
+        } else {
+            const double dv[3] = {su[st][0], su[st][1], su[st][2]};
+            const double vv0[3] = {su[st][3], su[st][4], su[st][5]};
+            double lin[25];
+            star_lin_adj(Cl.G, su[st][31], m[i], Cl.inv_c2, dv, vv0, ab, bb, lin);
+            for (int k = 0; k < kFusedVals; ++k)
+                sub[st][6 + k] = lin[k];
+            for (int k = 0; k < 9; ++k)
+                sub[st][22 + k] = lin[16 + k];
+            // d/d(inv_c2): abar_i . (1PN bracket); bh does not depend on it
+            sub[st][32] = ab[0] * pn[0].v + ab[1] * pn[1].v + ab[2] * pn[2].v;
+            // the hole's inv_c2 term: abar_hole . (star i's term)
+            sub[st][33] = abar[3 * hb] * bh[0].v + abar[3 * hb + 1] * bh[1].v +
+                          abar[3 * hb + 2] * bh[2].v;
         }
     }
     __syncwarp();
-    if (lane < kFusedVals)
-        sbar[(int64_t)lane * S + t] = star ? sub[wi][6 + lane] : 0.0;
-    if (lane < 6)
-        kbar[(int64_t)lane * S + t] = star ? sub[wi][lane] : 0.0;
+    for (int k = sl; k < kFusedVals; k += kAdjStarLanes)
+        sbar[(int64_t)k * S + t] = star ? sub[st][6 + k] : 0.0;
+    if (sl < 6)
+        kbar[(int64_t)sl * S + t] = star ? sub[st][sl] : 0.0;
     __syncthreads();
     // per-block sums over the block's star slots, in slot order
     if (threadIdx.x < kAdjGlob) {
@@ -798,7 +864,6 @@ k_adj_star(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
     }
 }
 
-// One block per cluster: its cotangent sums, blocks in a fixed order.
 __global__ void __launch_bounds__(kGlueThreads)
 k_adj_globals(const Clu *__restrict__ clu, const double *__restrict__ blk,
               double *__restrict__ gbar)
@@ -1271,7 +1336,9 @@ k_adj_sources_packed(const float4 *__restrict__ srec, const float4 *__restrict__
 // Per star slot: the records' and cluster sums' reverse (forward-mode Duals
 // over d_j (3), v_j (3), M), plus every cotangent gathered so far; writes
 // the star's xbar, vbar and, per block, -sum dbar (the hole's xbar) and the
-// M cotangent (4 values).
+// M cotangent (4 values).  Eight lanes per star slot (as k_adj_star): the
+// lanes first sum the split partials (each a share of the 20 values, splits
+// in order), then lanes 0..6 take one seed each.
 __global__ void __launch_bounds__(kGlueThreads)
 k_adj_records(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_clu,
               const double *__restrict__ x, const double *__restrict__ v,
@@ -1280,73 +1347,88 @@ k_adj_records(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ bl
               const double *__restrict__ spart, int jss, const double *__restrict__ gbar,
               double *__restrict__ xbar, double *__restrict__ vbar, double *__restrict__ blk)
 {
-    __shared__ double sh[4][kGlueThreads];
-    const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
-    const int k_clu = cluster_of_block(blk_clu, blockIdx.x);
+    constexpr int kNT = 6, kNV = kNT + kAdjSrc;       // target and source partials
+    __shared__ double sp_[kAdjStarWarps][kNV];
+    __shared__ double ub_[kAdjStarWarps][8];
+    __shared__ double h4_[kAdjStarWarps][4];
+    const int st = threadIdx.x / kAdjStarLanes, sl = threadIdx.x % kAdjStarLanes;
+    const int64_t t = (int64_t)blockIdx.x * kAdjStarWarps + st;
+    const int k_clu = cluster_of_block(blk_clu, t / kGlueThreads);
     const Clu Cl = clu[k_clu];
     const double *gb = gbar + (int64_t)k_clu * kAdjGlob;
     const int64_t lt = t - Cl.slot0;
-    double h4[4] = {0.0, 0.0, 0.0, 0.0};
-    if (lt < Cl.ns) {
-        const int64_t j = Cl.body0 + 1 + lt, hb = Cl.body0;
+    const bool star = lt < Cl.ns;
+    const int64_t j = Cl.body0 + 1 + lt, hb = Cl.body0;
+    if (star) {
+        // split sums: values sl, sl + 8, sl + 16 of (tp[6], sp[14])
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int q = 0; q < (jst > jss ? jst : jss); ++q)
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const int k = sl + 8 * r;
+                if (k < kNT) {
+                    if (q < jst)
+                        acc[r] += tpart[((int64_t)q * kNT + k) * S + t];
+                } else if (k < kNV) {
+                    if (q < jss)
+                        acc[r] += spart[((int64_t)q * kAdjSrc + (k - kNT)) * S + t];
+                }
+            }
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+            if (sl + 8 * r < kNV)
+                sp_[st][sl + 8 * r] = acc[r];
+    }
+    __syncwarp();
+    if (star && sl < 7) {
+        const double *sp = sp_[st] + kNT;
         const double mj = m[j], G = Cl.G, eps2 = Cl.eps2;
-        // splits in order for every value, the values of a split loaded together
-        double tp[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, sp[kAdjSrc];
-        for (int q = 0; q < jst; ++q)
-#pragma unroll
-            for (int k = 0; k < 6; ++k)
-                tp[k] += tpart[((int64_t)q * 6 + k) * S + t];
-#pragma unroll
-        for (int k = 0; k < kAdjSrc; ++k)
-            sp[k] = 0.0;
-        for (int q = 0; q < jss; ++q)
-#pragma unroll
-            for (int k = 0; k < kAdjSrc; ++k)
-                sp[k] += spart[((int64_t)q * kAdjSrc + k) * S + t];
-        // cotangents of this star's record and cluster-sum terms
         const double Wb[3] = {gb[3] + G * abar[3 * hb], gb[4] + G * abar[3 * hb + 1],
                               gb[5] + G * abar[3 * hb + 2]};
-        double u[7];
+        Dual w[7];
         for (int k = 0; k < 3; ++k) {
-            u[k] = x[3 * j + k] - x[3 * hb + k];
-            u[3 + k] = v[3 * j + k];
+            w[k] = dual(x[3 * j + k] - x[3 * hb + k], sl == k ? 1.0 : 0.0);
+            w[3 + k] = dual(v[3 * j + k], sl == 3 + k ? 1.0 : 0.0);
         }
-        u[6] = m[hb];
-        double ub[7];
-        for (int q = 0; q < 7; ++q) {
-            Dual w[7];
-            for (int k = 0; k < 7; ++k)
-                w[k] = dual(u[k], k == q ? 1.0 : 0.0);
-            const Dual R2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
-            const Dual iR = 1.0 / tsqrt(R2);
-            const Dual iR3 = iR * iR * iR;
-            const Dual GM = G * w[6];
-            const Dual c = GM * (1.5 * iR + 0.25 * eps2 * iR3);
-            const Dual Cc = c / 1.5 - (4.0 / 3.0) * (w[3] * w[3] + w[4] * w[4] + w[5] * w[5]);
-            const Dual ne = -(GM / 3.0) * iR3;       // -e/1.5 = ne d
-            Dual acc = sp[6] * R2 + sp[7] * Cc;
-            for (int k = 0; k < 3; ++k) {
-                acc += sp[8 + k] * (ne * w[k]);
-                acc += (sp[11 + k] + Wb[k]) * (mj * iR3 * w[k]);
-                acc += gb[k] * (mj * w[3 + k]);
-            }
-            acc += gb[6] * (1.25 * mj * iR) + gb[7] * (0.25 * mj * (R2 + eps2) * iR3) +
-                   gb[8] * (mj * iR);
-            ub[q] = acc.d;
-        }
-        double dbar[3];
+        w[6] = dual(m[hb], sl == 6 ? 1.0 : 0.0);
+        const Dual R2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+        const Dual iR = 1.0 / tsqrt(R2);
+        const Dual iR3 = iR * iR * iR;
+        const Dual GM = G * w[6];
+        const Dual c = GM * (1.5 * iR + 0.25 * eps2 * iR3);
+        const Dual Cc = c / 1.5 - (4.0 / 3.0) * (w[3] * w[3] + w[4] * w[4] + w[5] * w[5]);
+        const Dual ne = -(GM / 3.0) * iR3;       // -e/1.5 = ne d
+        Dual a = sp[6] * R2 + sp[7] * Cc;
         for (int k = 0; k < 3; ++k) {
-            dbar[k] = kbar[(int64_t)k * S + t] + tp[k] + sp[k] + ub[k];
-            xbar[3 * j + k] = dbar[k];
-            vbar[3 * j + k] = kbar[(int64_t)(3 + k) * S + t] + 8.0 / 3.0 * tp[3 + k] + sp[3 + k] +
-                              ub[3 + k];
-            h4[k] = -dbar[k];
+            a += sp[8 + k] * (ne * w[k]);
+            a += (sp[11 + k] + Wb[k]) * (mj * iR3 * w[k]);
+            a += gb[k] * (mj * w[3 + k]);
         }
-        h4[3] = ub[6];
+        a += gb[6] * (1.25 * mj * iR) + gb[7] * (0.25 * mj * (R2 + eps2) * iR3) +
+             gb[8] * (mj * iR);
+        ub_[st][sl] = a.d;
     }
-    block_sum<4>(h4, sh);
-    if (threadIdx.x < 4)
-        blk[(int64_t)blockIdx.x * 4 + threadIdx.x] = sh[threadIdx.x][0];
+    __syncwarp();
+    if (sl < 4)
+        h4_[st][sl] = 0.0;
+    if (star && sl < 3) {
+        const double *tp = sp_[st], *sp = sp_[st] + kNT;
+        const double dbar = kbar[(int64_t)sl * S + t] + tp[sl] + sp[sl] + ub_[st][sl];
+        xbar[3 * j + sl] = dbar;
+        vbar[3 * j + sl] = kbar[(int64_t)(3 + sl) * S + t] + 8.0 / 3.0 * tp[3 + sl] + sp[3 + sl] +
+                           ub_[st][3 + sl];
+        h4_[st][sl] = -dbar;
+    }
+    if (star && sl == 3)
+        h4_[st][3] = ub_[st][6];
+    __syncthreads();
+    // per-block sums over the block's star slots, in slot order
+    if (threadIdx.x < 4) {
+        double g = 0.0;
+        for (int w2 = 0; w2 < kAdjStarWarps; ++w2)
+            g += h4_[w2][threadIdx.x];
+        blk[(int64_t)blockIdx.x * 4 + threadIdx.x] = g;
+    }
 }
 
 // The hole of each cluster: its xbar (its velocity does not enter Eq. 1-6),
@@ -1359,7 +1441,7 @@ k_adj_hole(const Clu *__restrict__ clu, const double *__restrict__ blk,
 {
     __shared__ double sh[4][kGlueThreads];
     const Clu C = clu[blockIdx.x];
-    sum_blocks<4>(blk + (C.slot0 / kGlueThreads) * 4, C.ns_pad / kGlueThreads, sh);
+    sum_blocks<4>(blk + (C.slot0 / kAdjStarWarps) * 4, C.ns_pad / kAdjStarWarps, sh);
     if (threadIdx.x == 0) {
         const double *gb = gbar + (int64_t)blockIdx.x * kAdjGlob;
         for (int k = 0; k < 3; ++k) {
@@ -1500,9 +1582,6 @@ cudaError_t launch_jerk(pn_ctx *c, const double *x, const double *v, const doubl
     return cudaGetLastError();
 }
 
-// Adjoint scratch (doubles): sbar 16 S, kbar 6 S, target partials js 6 S,
-// source partials js 14 S, block cotangents (S/8) 11, cluster cotangents
-// nclu 11, hole blocks (S/256) 4.
 // Splits of the packed adjoint sweeps: about eight waves of 3 blocks per SM
 // over the 256-slot blocks, at least one tile per split, at most the FP64
 // sweeps' splits (the partial buffers hold those).
@@ -1517,11 +1596,15 @@ static int64_t adj_pack_splits(const pn_ctx *c)
     return js > cap ? cap : js;
 }
 
+// Adjoint scratch (doubles): sbar 16 S, kbar 6 S, target partials js 6 S,
+// source partials js 14 S, staged targets of the packed sweep 26 S (13
+// float4 per slot), block cotangents (S/32) 11, cluster cotangents nclu 11,
+// hole blocks (S/32) 4.
 size_t adjoint_buffer_doubles(const pn_ctx *c)
 {
-    const int64_t S = c->S, nglue = S / kGlueThreads, js = jerk_part_splits(c);
+    const int64_t S = c->S, js = jerk_part_splits(c);
     return (size_t)((16 + 6) * S + js * (6 + kAdjSrc) * S + kAdjTVals * 2 * S +
-                    (S / kAdjStarWarps) * kAdjGlob + nglue * 4 + (int64_t)c->nclu * kAdjGlob);
+                    (S / kAdjStarWarps) * (kAdjGlob + 4) + (int64_t)c->nclu * kAdjGlob);
 }
 
 cudaError_t launch_accel_vjp(pn_ctx *c, const double *x, const double *v, const double *m,
@@ -1601,7 +1684,7 @@ cudaError_t launch_accel_vjp(pn_ctx *c, const double *x, const double *v, const 
         k_adj_targets<<<grid, kJThreads, 0, c->stream>>>(rec, S, c->d_clu, bc, sbar, tpart);
         k_adj_sources<<<grid, kJThreads, 0, c->stream>>>(rec, S, c->d_clu, bc, sbar, spart);
     }
-    k_adj_records<<<(unsigned)nglue, kGlueThreads, 0, c->stream>>>(
+    k_adj_records<<<(unsigned)(S / kAdjStarWarps), kGlueThreads, 0, c->stream>>>(
         S, c->d_clu, bc, x, v, m, abar, kbar, tpart, jsr, spart, jsr, gbar, xbar, vbar, hblk);
     k_adj_hole<<<c->nclu, kGlueThreads, 0, c->stream>>>(c->d_clu, hblk, gbar, xbar, vbar, scal,
                                                        accumulate ? 1 : 0);
