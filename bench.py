@@ -45,7 +45,9 @@ sys.path.insert(0, ROOT)
 METRIC = "1PN pair interactions/s at N=16k/128k, mixed vs FP64 on B300 at <=1e-5 rel err"
 FLOPS_PASS1 = 29   # hand count of the mixed pass-1 pair body (FMA = 2, rsqrt = 1)
 FLOPS_PASS2 = 67   # hand count of the mixed pass-2 pair body
-FLOPS_FUSED = 77   # hand count of the fused pair body (pass 1 + pass 2 sharing x, r, rsqrt)
+FLOPS_FUSED = 77   # hand count of the scalar fused pair body (pass 1 + pass 2 sharing x, r, rsqrt)
+FLOPS_PACKED = 72  # hand count of the packed fused pair body, law-of-cosines form (r_near > 0)
+OPS_PACKED = 46    # FP32-pipe operations per pair of that body (FMA, add and mul count 1 each)
 FLOPS_JERK = 213   # hand count of the dual-number pair body of the jerk
                    # (dual add 2, dual multiply 4, scalar x dual 2, rsqrt + its derivative 6)
 FP32_LANES_PER_SM = 128
@@ -322,7 +324,9 @@ def run_native(args, w):
     per_launch_ms = kms[k_dom] / max(1, klaunch[k_dom])
     pairs = float(w.n - 1) * (w.n - 2)
     fused = args.precision == "mixed" and args.pair_kernel == "fused"
-    fpp = FLOPS_FUSED if fused else (FLOPS_PASS2 if k_dom == 1 else FLOPS_PASS1)
+    packed = fused and bool(launch.get("packed"))
+    fpp = (FLOPS_PACKED if packed else FLOPS_FUSED) if fused else (
+        FLOPS_PASS2 if k_dom == 1 else FLOPS_PASS1)
     flops = fpp * pairs
     achieved = flops / (per_launch_ms * 1e-3) / 1e12
     clocks = clk.summary()
@@ -340,6 +344,12 @@ def run_native(args, w):
                                 "near": kms[2] / ms}}
     if clocks and clocks.get("sm_mhz"):
         roof["frac_at_sampled_clock"] = achieved / (peak * clocks["sm_mhz"] / sm_max)
+    if packed:
+        # the FP32 pipe's own limit: operations issued per pair against its
+        # lane-operation rate (an FMA is one operation and two flops)
+        ops = OPS_PACKED * pairs / (per_launch_ms * 1e-3)
+        roof["fp32_pipe_ops_per_pair"] = OPS_PACKED
+        roof["fp32_pipe_frac"] = ops / (sms * FP32_LANES_PER_SM * sm_max * 1e6)
     try:
         meas = pn.pn_measure_peaks(local, stream)
         roof["fp32_fma_microbench_tflops"] = meas["fp32_fma_tflops"]
@@ -348,7 +358,7 @@ def run_native(args, w):
         roof["fp32x2_fma_microbench_tflops"] = meas["fp32x2_fma_tflops"]
     except Exception as e:  # reported, not required
         roof["fp32_fma_microbench_error"] = str(e)[:200]
-    roof["flops_per_interaction"] = FLOPS_FUSED if fused else FLOPS_PASS1 + FLOPS_PASS2
+    roof["flops_per_interaction"] = fpp if fused else FLOPS_PASS1 + FLOPS_PASS2
 
     line = {
         "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world,

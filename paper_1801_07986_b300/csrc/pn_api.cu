@@ -103,6 +103,7 @@ void set_params(pn_ctx *c, const pn_params *p, bool all_physics)
 {
     c->p = *p;
     c->any_near = false;
+    c->near_all = true;
     for (int k = 0; k < c->nclu; ++k) {
         if (all_physics) {
             c->hclu[k].G = p->G;
@@ -112,6 +113,8 @@ void set_params(pn_ctx *c, const pn_params *p, bool all_physics)
         }
         if (c->hclu[k].r_near > 0.0)
             c->any_near = true;
+        else
+            c->near_all = false;
     }
 }
 

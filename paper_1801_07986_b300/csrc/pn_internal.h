@@ -15,7 +15,8 @@ constexpr int kMixTargets = 2;     // targets held in registers per thread
 constexpr int kMixTile = 128;      // sources per shared-memory tile
 constexpr int kFlushTiles = 2;     // fused kernel: tiles per single-precision partial
 constexpr int kPackTile = 64;      // packed fused kernel: sources per shared-memory tile
-constexpr int kPackVals = 9;       // packed kernels: float4 per staged source record
+constexpr int kPackVals = 9;       // packed adjoint sweeps: float4 per staged source record
+constexpr int kFwdVals = 8;        // packed fused kernel: float4 per staged source record
 constexpr int kPackFlushTiles = 8; // packed fused kernel: tiles per single-precision partial
 constexpr int kPackWorkersMax = 4;  // packed fused kernel: stream-K workers per resident block (max)
 // Launch shape of the double-precision pair kernels (FP64 mode and energy).
@@ -33,6 +34,7 @@ constexpr int kP1Vals = 6;         // N (3), U, Z, Wr
 constexpr int kP2Vals = 10;        // V' (3), Hs (1), Hv (3), E (3)
 constexpr int kEVals = 8;          // pot, Smv (3), Snn, Spx (3)
 constexpr int kFusedVals = kP1Vals + kP2Vals;
+constexpr int kPackSums = kFusedVals - 1;   // packed fused kernel: the pass-1 sums without Wr
 // Near-source pass: sources per tile and values per target.
 constexpr int kNearTile = 128;
 constexpr int kNearVals = 6;       // P (3), Ee (3)
@@ -85,6 +87,7 @@ struct pn_ctx {
     pn::Clu *d_clu;          // device cluster table
     int *blk_clu;            // device: cluster of each 256-slot block
     bool any_near;           // some cluster has r_near > 0
+    bool near_all;           // every cluster has r_near > 0
     pn_params p;
     int device;
     cudaStream_t stream;
@@ -182,6 +185,9 @@ void shapes(int64_t S, int64_t max_ns_pad, int sm_count, int occ_mix, int occ_f6
             Shape *f64);
 cudaError_t occupancy(int *occ_mix, int *occ_f64);
 cudaError_t fused_occupancy(int P, int unroll, bool packed, int *occ);
+// The packed pair kernel runs its law-of-cosines form (every cluster splits
+// off its near sources); the prologue then stages that form's records.
+bool packed_loc(const pn_ctx *c);
 cudaError_t launch_fused(pn_ctx *c);
 cudaError_t launch_stage_sources(pn_ctx *c, const float4 *rec);
 cudaError_t launch_fused_on(pn_ctx *c, const float4 *rec);

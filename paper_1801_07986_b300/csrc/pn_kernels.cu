@@ -125,6 +125,23 @@ __device__ __forceinline__ void stage_source(float4 *__restrict__ o, float4 A, f
     o[8] = make_float4(E.y, E.y, E.z, E.z);
 }
 
+// Staged source records of the law-of-cosines form of k_fused_packed
+// (kFwdVals float4; the fields are stated above packed_pair) from the mixed
+// records A = (hi d, m), B = (lo d, R^2), C = (v, C), E = (w, 0) and the
+// hole-term coefficients a = -G M/(6 R^3), cp = C + a (R^2 + eps^2).
+__device__ __forceinline__ void stage_source_fwd(float4 *__restrict__ o, float4 A, float4 B,
+                                                 float4 Cs, float4 E, float a, float cp)
+{
+    o[0] = make_float4(-A.x, -A.x, -A.y, -A.y);
+    o[1] = make_float4(-A.z, -A.z, A.w, A.w);
+    o[2] = make_float4(-B.x, -B.x, -B.y, -B.y);
+    o[3] = make_float4(-B.z, -B.z, a, a);
+    o[4] = make_float4(Cs.x, Cs.x, Cs.y, Cs.y);
+    o[5] = make_float4(Cs.z, Cs.z, cp, cp);
+    o[6] = make_float4(E.x, E.x, E.y, E.y);
+    o[7] = make_float4(E.z, E.z, B.w, B.w);
+}
+
 
 // Per star slot t of cluster k (star j = body0 + 1 + (t - slot0); slots past
 // the cluster's stars are padding):
@@ -141,13 +158,15 @@ __device__ __forceinline__ void stage_source(float4 *__restrict__ o, float4 A, f
 //          mixed  A = (hi(d), m) B = (lo(d), R^2) C = (v, C) D = (-e/1.5, 0) E = (w, 0)
 //          double A = (d, m)     B = (v, R^2)    C = (-e/1.5, C)   D = (w, 0)
 // Energy records (double): A = (d, m), B = (v, 0).
+// Mixed mode also writes the packed kernel's staged records: the
+// law-of-cosines layout (stage_source_fwd) when `loc`, else stage_source's.
 template <int MODE>   // 0 mixed, 1 double, 2 energy
 __global__ void __launch_bounds__(kGlueThreads)
 k_prologue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_clu,
            const double *__restrict__ x, const double *__restrict__ vel,
            const double *__restrict__ m, float4 *__restrict__ mrec,
            double4_32a *__restrict__ drec, unsigned char *__restrict__ nflag,
-           double *__restrict__ blk, int *__restrict__ wcount)
+           double *__restrict__ blk, int *__restrict__ wcount, int loc)
 {
     // mixed: the staged source records of the packed pair kernel follow the
     // five record arrays
@@ -183,15 +202,25 @@ k_prologue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
         const double e3 = -ef / 1.5;
         if (MODE == 0) {
             const float h0 = (float)d0, h1 = (float)d1, h2 = (float)d2;
-            mrec[t] = make_float4(h0, h1, h2, (float)mj);
-            mrec[S + t] = make_float4((float)(d0 - (double)h0), (float)(d1 - (double)h1),
-                                      (float)(d2 - (double)h2), (float)R2);
-            mrec[2 * S + t] = make_float4((float)v0, (float)v1, (float)v2, (float)c3);
-            mrec[3 * S + t] = make_float4((float)(e3 * d0), (float)(e3 * d1), (float)(e3 * d2), 0.0f);
-            mrec[4 * S + t] = make_float4((float)(far * wf * d0), (float)(far * wf * d1),
+            const float4 rA = make_float4(h0, h1, h2, (float)mj);
+            const float4 rB = make_float4((float)(d0 - (double)h0), (float)(d1 - (double)h1),
+                                          (float)(d2 - (double)h2), (float)R2);
+            const float4 rC = make_float4((float)v0, (float)v1, (float)v2, (float)c3);
+            const float4 rD = make_float4((float)(e3 * d0), (float)(e3 * d1), (float)(e3 * d2), 0.0f);
+            const float4 rE = make_float4((float)(far * wf * d0), (float)(far * wf * d1),
                                           (float)(far * wf * d2), 0.0f);
-            stage_source(srec + 9 * t, mrec[t], mrec[S + t], mrec[2 * S + t], mrec[3 * S + t],
-                         mrec[4 * S + t]);
+            mrec[t] = rA;
+            mrec[S + t] = rB;
+            mrec[2 * S + t] = rC;
+            mrec[3 * S + t] = rD;
+            mrec[4 * S + t] = rE;
+            if (loc) {
+                const double a = 0.5 * e3;    // -G M/(6 R^3) (0 for near sources)
+                stage_source_fwd(srec + kFwdVals * t, rA, rB, rC, rE, (float)a,
+                                 (float)(c3 + a * (R2 + eps2)));
+            } else {
+                stage_source(srec + kPackVals * t, rA, rB, rC, rD, rE);
+            }
         } else if (MODE == 1) {
             drec[t] = make_double4_32a(d0, d1, d2, mj);
             drec[S + t] = make_double4_32a(v0, v1, v2, R2);
@@ -224,7 +253,10 @@ k_prologue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
             mrec[t] = make_float4((float)px, 0.0f, 0.0f, 0.0f);
             for (int k = 1; k < 5; ++k)
                 mrec[k * S + t] = z;
-            stage_source(srec + 9 * t, mrec[t], z, z, z, z);
+            if (loc)
+                stage_source_fwd(srec + kFwdVals * t, mrec[t], z, z, z, 0.0f, 0.0f);
+            else
+                stage_source(srec + kPackVals * t, mrec[t], z, z, z, z);
         } else {
             drec[t] = make_double4_32a(px, 0.0, 0.0, 0.0);
             const int nk = MODE == 1 ? 4 : 2;
@@ -718,32 +750,53 @@ k_fused_mixed(const float4 *__restrict__ rec, int64_t S, const Clu *__restrict__
 // source j.  fma.rn.f32x2 / add.rn.f32x2 / mul.rn.f32x2 (sm_100 family) do
 // two FP32 operations per instruction, so the pair arithmetic needs half the
 // instruction issue slots of the scalar kernel while the FP32 pipe does the
-// same work; the rounding of every operation is that of the scalar kernel.
-// Each source is staged in shared memory with every field duplicated
-// (f, f), so that a 128-bit load yields two ready packed operands:
-//   S0 = (-hx, -hy)  S1 = (-hz, m)   S2 = (-lx, -ly)  S3 = (-lz, R^2)
-//   S4 = (vx, vy)    S5 = (vz, C)    S6 = (Dx, Dy)    S7 = (Dz, wx)   S8 = (wy, wz)
-// (h, l = hi/lo split of d_j, D = -e_j/1.5, C = c_j/1.5 - 4/3 |v_j|^2, w = w_j).
+// same work.  Each source is staged in shared memory with every field
+// duplicated (f, f), so that a 128-bit load yields two ready packed operands
+// (stage_source_fwd):
+//   F0 = (-hx, -hy)  F1 = (-hz, m)  F2 = (-lx, -ly)  F3 = (-lz, a)
+//   F4 = (vx, vy)    F5 = (vz, C')  F6 = (wx, wy)    F7 = (wz, R^2)
+// (h, l = hi/lo split of d_j, w = w_j, a = -G M/(6 R_j^3) and
+// C' = C_j + a (R_j^2 + eps^2) for far sources, a = 0 and C' = C_j for near
+// ones; R^2 is read by the target side only).
+//
+// Two regroupings make the body cheaper than the scalar kernels' (exact in
+// real arithmetic):
+// - the hole term (-e_j/1.5).d_i of kappa_ij is a (R_i^2 - r_ij^2) + (C' - C):
+//   e_j/1.5 = -2 a d_j and, by the law of cosines,
+//   2 d_i.d_j = R_i^2 + R_j^2 + eps^2 - r_ij^2 (softened r_ij).  Far sources
+//   only (R_j >= r_near), so a stays bounded and R_i^2 - r_ij^2 = 2 d_i.d_j -
+//   R_j^2 - eps^2 is a difference of O(R_i^2) numbers only when the term is
+//   small anyway.
+// - Wr is not summed: R_i^2 - R_j^2 = 2 d_i.x_ij - (r_ij^2 - eps^2) gives
+//   Y_i = R_i^2 Z_i - Wr_i = 2 d_i.N_i - U_i + eps^2 Z_i, and k_fused_gather
+//   restores Wr from N, U and Z in double.
+// Sums (kPackSums): N (3), U, Z, V' (3), Hs, Hv (3), E (3).
 
 struct PackTarget {
     float2 hx, hy, hz, lx, ly, lz;   // hi/lo split of d_i (lanes: two targets)
     float2 vx, vy, vz;               // 8/3 v_i
+    float2 rr;                       // R_i^2
 };
 
-
-template <bool MASK>
+template <bool MASK, bool LOC>
 __device__ __forceinline__ void packed_pair(const PackTarget &tg, const float4 *__restrict__ sq,
                                             float2 eps2, bool selfx, bool selfy,
-                                            float2 (&acc)[kFusedVals])
+                                            float2 (&acc)[kPackSums])
 {
-    const float4 S0 = sq[0], S1 = sq[1], S2 = sq[2], S3 = sq[3];
-    const float2 dx = add2(add2(tg.hx, lo2(S0)), add2(tg.lx, lo2(S2)));
-    const float2 dy = add2(add2(tg.hy, hi2(S0)), add2(tg.ly, hi2(S2)));
-    const float2 dz = add2(add2(tg.hz, lo2(S1)), add2(tg.lz, lo2(S3)));
+    const float4 F0 = sq[0], F1 = sq[1], F2 = sq[2], F3 = sq[3];
+    const float2 dx = add2(add2(tg.hx, lo2(F0)), add2(tg.lx, lo2(F2)));
+    const float2 dy = add2(add2(tg.hy, hi2(F0)), add2(tg.ly, hi2(F2)));
+    const float2 dz = add2(add2(tg.hz, lo2(F1)), add2(tg.lz, lo2(F3)));
     float2 s2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, eps2)));
-    float2 m = hi2(S1);
-    const float4 S7 = sq[7], S8 = sq[8];
-    float2 wx = hi2(S7), wy = lo2(S8), wz = hi2(S8);
+    float2 m = hi2(F1);
+    float2 wx, wy, wz;
+    if (LOC) {
+        const float4 F6 = sq[6], F7 = sq[7];
+        wx = lo2(F6), wy = hi2(F6), wz = lo2(F7);
+    } else {
+        const float4 S7 = sq[7], S8 = sq[8];
+        wx = hi2(S7), wy = lo2(S8), wz = hi2(S8);
+    }
     if (MASK) {
         if (selfx) {
             s2.x = 1.0f; m.x = 0.0f; wx.x = 0.0f; wy.x = 0.0f; wz.x = 0.0f;
@@ -761,32 +814,41 @@ __device__ __forceinline__ void packed_pair(const PackTarget &tg, const float4 *
     acc[2] = fma2(mis3, dz, acc[2]);
     acc[3] = add2(acc[3], mis);
     acc[4] = add2(acc[4], mis3);
-    acc[5] = fma2(mis3, hi2(S3), acc[5]);
-    const float4 S4 = sq[4], S5 = sq[5], S6 = sq[6];
-    const float2 vx = lo2(S4), vy = hi2(S4), vz = lo2(S5);
+    const float4 F4 = sq[4], F5 = sq[5];
+    const float2 vx = lo2(F4), vy = hi2(F4), vz = lo2(F5);
     const float2 xvj = fma2(dx, vx, fma2(dy, vy, mul2(dz, vz)));
     const float2 xvi = fma2(dx, tg.vx, fma2(dy, tg.vy, mul2(dz, tg.vz)));
-    float2 k = fma2(tg.vx, vx, fma2(tg.vy, vy, fma2(tg.vz, vz, hi2(S5))));
-    k = fma2(lo2(S6), tg.hx, fma2(hi2(S6), tg.hy, fma2(lo2(S7), tg.hz, k)));
+    float2 k;
+    if (LOC) {         // C' + a (R_i^2 - r_ij^2)
+        k = fma2(hi2(F3), fma2(s2, make_float2(-1.0f, -1.0f), tg.rr), hi2(F5));
+    } else {           // C + D.h_i
+        const float4 S6 = sq[6], S7 = sq[7];
+        k = fma2(lo2(S6), tg.hx, fma2(hi2(S6), tg.hy, fma2(lo2(S7), tg.hz, hi2(F5))));
+    }
+    k = fma2(tg.vx, vx, fma2(tg.vy, vy, fma2(tg.vz, vz, k)));
     const float2 h = mul2(xvj, is2);
     const float2 f = mul2(mis3, fma2(h, xvj, k));
-    acc[6] = fma2(f, dx, acc[6]);
-    acc[7] = fma2(f, dy, acc[7]);
-    acc[8] = fma2(f, dz, acc[8]);
+    acc[5] = fma2(f, dx, acc[5]);
+    acc[6] = fma2(f, dy, acc[6]);
+    acc[7] = fma2(f, dz, acc[7]);
     const float2 gg = mul2(mis3, fma2(make_float2(-2.0f, -2.0f), xvj, xvi));
-    acc[9] = add2(acc[9], gg);
-    acc[10] = fma2(gg, vx, acc[10]);
-    acc[11] = fma2(gg, vy, acc[11]);
-    acc[12] = fma2(gg, vz, acc[12]);
-    acc[13] = fma2(wx, is, acc[13]);
-    acc[14] = fma2(wy, is, acc[14]);
-    acc[15] = fma2(wz, is, acc[15]);
+    acc[8] = add2(acc[8], gg);
+    acc[9] = fma2(gg, vx, acc[9]);
+    acc[10] = fma2(gg, vy, acc[10]);
+    acc[11] = fma2(gg, vz, acc[11]);
+    acc[12] = fma2(wx, is, acc[12]);
+    acc[13] = fma2(wy, is, acc[13]);
+    acc[14] = fma2(wz, is, acc[14]);
 }
 
-template <int NP, int UNROLL, bool MASK>
-__device__ __forceinline__ void packed_tile(const float4 (*__restrict__ sh)[kPackVals], int64_t j0,
-                                            int64_t t0, const PackTarget (&tg)[NP], float2 eps2,
-                                            float2 (&acc)[NP][kFusedVals])
+// Staged record length of the two forms.
+template <bool LOC>
+__host__ __device__ constexpr int pack_vals() { return LOC ? kFwdVals : kPackVals; }
+
+template <int NP, int UNROLL, bool MASK, bool LOC>
+__device__ __forceinline__ void packed_tile(const float4 (*__restrict__ sh)[pack_vals<LOC>()],
+                                            int64_t j0, int64_t t0, const PackTarget (&tg)[NP],
+                                            float2 eps2, float2 (&acc)[NP][kPackSums])
 {
 #pragma unroll UNROLL
     for (int q = 0; q < kPackTile; ++q) {
@@ -796,13 +858,14 @@ __device__ __forceinline__ void packed_tile(const float4 (*__restrict__ sh)[kPac
             const int64_t tx = t0 + (2 * pp) * kMixThreads + threadIdx.x;
             const bool selfx = MASK && j == tx;
             const bool selfy = MASK && j == tx + kMixThreads;
-            packed_pair<MASK>(tg[pp], sh[q], eps2, selfx, selfy, acc[pp]);
+            packed_pair<MASK, LOC>(tg[pp], sh[q], eps2, selfx, selfy, acc[pp]);
         }
     }
 }
 
 // One staged source tile (bulk-copy size)
-constexpr int kTileBytes = kPackTile * kPackVals * 16;
+template <bool LOC>
+__host__ __device__ constexpr unsigned tile_bytes() { return kPackTile * pack_vals<LOC>() * 16; }
 
 // First source slot of stream-K unit u (its cluster's tile of kPackTile
 // sources).
@@ -824,7 +887,7 @@ __device__ __forceinline__ int64_t unit_source(const Clu *__restrict__ clu, int 
 // warps.  A worker's result does not depend on which block runs it, so the
 // sums stay deterministic.
 //
-// Sources come from the staged records srec[slot][kPackVals] (every field
+// Sources come from the staged records srec[slot][pack_vals<LOC>()] (every field
 // duplicated, positions negated), one contiguous 9 KB tile per unit, copied
 // by the bulk-copy engine into two shared buffers: the copy of unit u + 2
 // starts as soon as every warp is done with unit u, so the loads of the next
@@ -833,14 +896,14 @@ __device__ __forceinline__ int64_t unit_source(const Clu *__restrict__ clu, int 
 // worker's segment slot in FP64 (each value is owned by one thread).  A copy
 // that does not complete within the poll limit sets kFlagTimeout in `flag`
 // and ends the block.
-template <int NP, int UNROLL>
+template <int NP, int UNROLL, bool LOC>
 __global__ void __launch_bounds__(kMixThreads, NP == 2 ? 3 : 5)
 k_fused_packed(const float4 *__restrict__ srec, const Clu *__restrict__ clu, int nclu,
                int64_t total_units, int64_t G, int *__restrict__ wcount, int *__restrict__ flag,
                unsigned extra_tx, double *__restrict__ part)
 {
-    constexpr int P = 2 * NP, TI = kMixThreads * P;
-    __shared__ __align__(128) float4 sh[2][kPackTile][kPackVals];
+    constexpr int P = 2 * NP, TI = kMixThreads * P, RV = pack_vals<LOC>();
+    __shared__ __align__(128) float4 sh[2][kPackTile][RV];
     __shared__ __align__(8) uint64_t full[2];
     __shared__ int s_w;
     if (threadIdx.x == 0) {
@@ -860,11 +923,11 @@ k_fused_packed(const float4 *__restrict__ srec, const Clu *__restrict__ clu, int
         int64_t u = w * total_units / G;
         const int64_t u1 = (w + 1) * total_units / G;
         if (threadIdx.x == 0 && u < u1) {   // both buffers are free here
-            bulk_load(sh[it & 1], srec + unit_source(clu, nclu, u) * kPackVals, kTileBytes,
+            bulk_load(sh[it & 1], srec + unit_source(clu, nclu, u) * RV, tile_bytes<LOC>(),
                       &full[it & 1], extra_tx);
             if (u + 1 < u1)
-                bulk_load(sh[(it + 1) & 1], srec + unit_source(clu, nclu, u + 1) * kPackVals,
-                          kTileBytes, &full[(it + 1) & 1], extra_tx);
+                bulk_load(sh[(it + 1) & 1], srec + unit_source(clu, nclu, u + 1) * RV,
+                          tile_bytes<LOC>(), &full[(it + 1) & 1], extra_tx);
         }
         while (u < u1) {
             const Clu C = clu[cluster_of_unit(clu, nclu, u)];
@@ -879,9 +942,11 @@ k_fused_packed(const float4 *__restrict__ srec, const Clu *__restrict__ clu, int
 #pragma unroll
             for (int pp = 0; pp < NP; ++pp) {
                 const int64_t ta = t0 + (2 * pp) * kMixThreads + threadIdx.x, tb = ta + kMixThreads;
-                const float4 *ra = srec + ta * kPackVals, *rb = srec + tb * kPackVals;
+                const float4 *ra = srec + ta * RV, *rb = srec + tb * RV;
                 const float4 A0 = ra[0], A1 = ra[1], A2 = ra[2], A3 = ra[3], A4 = ra[4], A5 = ra[5];
                 const float4 B0 = rb[0], B1 = rb[1], B2 = rb[2], B3 = rb[3], B4 = rb[4], B5 = rb[5];
+                if (LOC)
+                    tg[pp].rr = make_float2(ra[7].z, rb[7].z);
                 tg[pp].hx = make_float2(-A0.x, -B0.x);
                 tg[pp].hy = make_float2(-A0.z, -B0.z);
                 tg[pp].hz = make_float2(-A1.x, -B1.x);
@@ -892,13 +957,13 @@ k_fused_packed(const float4 *__restrict__ srec, const Clu *__restrict__ clu, int
                 tg[pp].vy = make_float2(kEightThirds * A4.z, kEightThirds * B4.z);
                 tg[pp].vz = make_float2(kEightThirds * A5.x, kEightThirds * B5.x);
             }
-            double *out = part + (t0 / TI + w) * (int64_t)(kFusedVals * TI);
+            double *out = part + (t0 / TI + w) * (int64_t)(kPackSums * TI);
             bool first = true;
-            float2 acc[NP][kFusedVals];
+            float2 acc[NP][kPackSums];
 #pragma unroll
             for (int pp = 0; pp < NP; ++pp)
 #pragma unroll
-                for (int k = 0; k < kFusedVals; ++k)
+                for (int k = 0; k < kPackSums; ++k)
                     acc[pp][k] = make_float2(0.0f, 0.0f);
             for (; u < uend; ++u, ++it) {
                 const int64_t j0 = C.slot0 + (u - ub) * kPackTile;
@@ -906,14 +971,14 @@ k_fused_packed(const float4 *__restrict__ srec, const Clu *__restrict__ clu, int
                 const bool ok = mbar_wait(&full[b], (it >> 1) & 1);
                 const bool diag = (j0 < t0 + TI) && (t0 < j0 + kPackTile);
                 if (diag)
-                    packed_tile<NP, UNROLL, true>(sh[b], j0, t0, tg, eps2, acc);
+                    packed_tile<NP, UNROLL, true, LOC>(sh[b], j0, t0, tg, eps2, acc);
                 else
-                    packed_tile<NP, UNROLL, false>(sh[b], j0, t0, tg, eps2, acc);
+                    packed_tile<NP, UNROLL, false, LOC>(sh[b], j0, t0, tg, eps2, acc);
                 if (((u - ub + 1) % kPackFlushTiles) == 0 || u + 1 == uend) {
 #pragma unroll
                     for (int pp = 0; pp < NP; ++pp)
 #pragma unroll
-                        for (int k = 0; k < kFusedVals; ++k) {
+                        for (int k = 0; k < kPackSums; ++k) {
                             double *o = out + k * TI + (2 * pp) * kMixThreads + threadIdx.x;
                             o[0] = first ? (double)acc[pp][k].x : o[0] + (double)acc[pp][k].x;
                             o[kMixThreads] = first ? (double)acc[pp][k].y
@@ -931,7 +996,7 @@ k_fused_packed(const float4 *__restrict__ srec, const Clu *__restrict__ clu, int
                     return;
                 }
                 if (threadIdx.x == 0 && u + 2 < u1)
-                    bulk_load(sh[b], srec + unit_source(clu, nclu, u + 2) * kPackVals, kTileBytes,
+                    bulk_load(sh[b], srec + unit_source(clu, nclu, u + 2) * RV, tile_bytes<LOC>(),
                               &full[b], extra_tx);
             }
         }
@@ -950,11 +1015,11 @@ k_stage_sources(int64_t S, const float4 *__restrict__ rec, float4 *__restrict__ 
 // Sums, for every star slot, the stream-K segments that cover its target
 // block (in block order) into the pass-1 / pass-2 partial layout with one
 // split: p1[k][t] (k < kP1Vals), p2[k][t] (k < kP2Vals).
-template <int P>
+template <int P, int NV, int RV>
 __global__ void __launch_bounds__(kGlueThreads)
 k_fused_gather(const double *__restrict__ part, int64_t S, const Clu *__restrict__ clu,
                const int *__restrict__ blk_clu, int64_t total_units, int64_t G, int tile,
-               double *__restrict__ p1, double *__restrict__ p2)
+               const float4 *__restrict__ srec, double *__restrict__ p1, double *__restrict__ p2)
 {
     constexpr int TI = kMixThreads * P;
     const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
@@ -969,9 +1034,9 @@ k_fused_gather(const double *__restrict__ part, int64_t S, const Clu *__restrict
     int64_t b = U0 * G / total_units;
     while (b + 1 < G && (b + 1) * total_units / G <= U0)
         ++b;
-    double acc[kFusedVals];
+    double acc[NV];
 #pragma unroll
-    for (int k = 0; k < kFusedVals; ++k)
+    for (int k = 0; k < NV; ++k)
         acc[k] = 0.0;
     for (; b < G; ++b) {
         const int64_t bu0 = b * total_units / G, bu1 = (b + 1) * total_units / G;
@@ -979,17 +1044,29 @@ k_fused_gather(const double *__restrict__ part, int64_t S, const Clu *__restrict
             break;
         if (bu1 <= U0 || bu0 == bu1)
             continue;
-        const double *in = part + (gtb + b) * (int64_t)(kFusedVals * TI);
+        const double *in = part + (gtb + b) * (int64_t)(NV * TI);
 #pragma unroll
-        for (int k = 0; k < kFusedVals; ++k)
+        for (int k = 0; k < NV; ++k)
             acc[k] += in[k * TI + lt];
     }
+    constexpr int o2 = NV - kP2Vals;     // first pass-2 value in the segment
 #pragma unroll
-    for (int k = 0; k < kP1Vals; ++k)
+    for (int k = 0; k < o2; ++k)
         p1[(int64_t)k * S + t] = acc[k];
+    if (o2 < kP1Vals) {
+        // Wr from the identity R_i^2 - R_j^2 = 2 d_i.x_ij - (r_ij^2 - eps^2):
+        // sum_j m_j (R_i^2 - R_j^2)/r_ij^3 = 2 d_i.N - U + eps^2 Z, so
+        // Wr = (R_i^2 - eps^2) Z - 2 d_i.N + U (d_i from the staged hi/lo split)
+        const float4 *r = srec + t * RV;
+        const double d0 = -((double)r[0].x + (double)r[2].x);
+        const double d1 = -((double)r[0].z + (double)r[2].z);
+        const double d2 = -((double)r[1].x + (double)r[3].x);
+        const double R2 = d0 * d0 + d1 * d1 + d2 * d2;
+        p1[(int64_t)5 * S + t] = (R2 - C.eps2) * acc[4] - 2.0 * (d0 * acc[0] + d1 * acc[1] + d2 * acc[2]) + acc[3];
+    }
 #pragma unroll
     for (int k = 0; k < kP2Vals; ++k)
-        p2[(int64_t)k * S + t] = acc[kP1Vals + k];
+        p2[(int64_t)k * S + t] = acc[o2 + k];
 }
 
 // ------------------------------------------------ pair kernels: double --
@@ -1573,17 +1650,18 @@ cudaError_t launch_prologue(pn_ctx *c, const double *x, const double *vel, const
     const int *bc = blk_table(c);
     if (energy_records) {
         k_prologue<2><<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
-            c->S, c->d_clu, bc, x, vel, m, c->mrec, c->drec, c->nflag, c->blk, nullptr);
+            c->S, c->d_clu, bc, x, vel, m, c->mrec, c->drec, c->nflag, c->blk, nullptr, 0);
         c->launches += 1;
         return cudaGetLastError();
     }
     const bool mixed = c->p.precision == PN_MIXED;
     if (mixed)
         k_prologue<0><<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
-            c->S, c->d_clu, bc, x, vel, m, c->mrec, c->drec, c->nflag, c->blk, c->wcount);
+            c->S, c->d_clu, bc, x, vel, m, c->mrec, c->drec, c->nflag, c->blk, c->wcount,
+            packed_loc(c) ? 1 : 0);
     else
         k_prologue<1><<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
-            c->S, c->d_clu, bc, x, vel, m, c->mrec, c->drec, c->nflag, c->blk, c->wcount);
+            c->S, c->d_clu, bc, x, vel, m, c->mrec, c->drec, c->nflag, c->blk, c->wcount, 0);
     c->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
@@ -1740,25 +1818,23 @@ static cudaError_t launch_fused_p(pn_ctx *c, const Layout &L, const float4 *rec)
         cudaEventRecord(end, c->stream);
     if (e != cudaSuccess)
         return e;
-    k_fused_gather<P><<<(unsigned)(c->S / kGlueThreads), kGlueThreads, 0, c->stream>>>(
+    k_fused_gather<P, kFusedVals, 0><<<(unsigned)(c->S / kGlueThreads), kGlueThreads, 0, c->stream>>>(
         c->part + L.seg, c->S, c->d_clu, blk_table(c), c->fused_units, c->fused_G, kMixTile,
-        c->part + L.p1, c->part + L.p2);
+        nullptr, c->part + L.p1, c->part + L.p2);
     c->launches += 1;
     return cudaGetLastError();
 }
 
-template <int NP, int UNROLL>
-static cudaError_t launch_packed_u(pn_ctx *c, const Layout &L, const float4 *rec)
+// The packed kernel on the staged records at c->mrec + 5 S: the
+// law-of-cosines form on the prologue's records when every cluster splits off
+// its near sources (packed_loc), else the D form; caller-built records (far
+// form: every source keeps its hole term) are staged in the D form first.
+template <int NP, int UNROLL, bool LOC>
+static cudaError_t launch_packed_form(pn_ctx *c, const Layout &L, const float4 *srec)
 {
-    const float4 *srec = c->mrec + 5 * c->S;
-    if (rec != c->mrec) {       // caller-built records: stage them first
-        k_stage_sources<<<(unsigned)(c->S / kGlueThreads), kGlueThreads, 0, c->stream>>>(
-            c->S, rec, c->mrec + 5 * c->S);
-        c->launches += 1;
-    }
     cudaEvent_t end = nullptr;
     timing_begin(c, 1, &end);
-    k_fused_packed<NP, UNROLL><<<(unsigned)c->fused_grid, kMixThreads, 0, c->stream>>>(
+    k_fused_packed<NP, UNROLL, LOC><<<(unsigned)c->fused_grid, kMixThreads, 0, c->stream>>>(
         srec, c->d_clu, c->nclu, c->fused_units, c->fused_G, c->wcount, c->flag, c->inject_tx,
         c->part + L.seg);
     c->launches += 1;
@@ -1767,11 +1843,28 @@ static cudaError_t launch_packed_u(pn_ctx *c, const Layout &L, const float4 *rec
         cudaEventRecord(end, c->stream);
     if (e != cudaSuccess)
         return e;
-    k_fused_gather<2 * NP><<<(unsigned)(c->S / kGlueThreads), kGlueThreads, 0, c->stream>>>(
-        c->part + L.seg, c->S, c->d_clu, blk_table(c), c->fused_units, c->fused_G, kPackTile,
-        c->part + L.p1, c->part + L.p2);
+    k_fused_gather<2 * NP, kPackSums, pack_vals<LOC>()>
+        <<<(unsigned)(c->S / kGlueThreads), kGlueThreads, 0, c->stream>>>(
+            c->part + L.seg, c->S, c->d_clu, blk_table(c), c->fused_units, c->fused_G, kPackTile,
+            srec, c->part + L.p1, c->part + L.p2);
     c->launches += 1;
     return cudaGetLastError();
+}
+
+bool packed_loc(const pn_ctx *c) { return c->fused_packed && c->near_all; }
+
+template <int NP, int UNROLL>
+static cudaError_t launch_packed_u(pn_ctx *c, const Layout &L, const float4 *rec)
+{
+    const float4 *srec = c->mrec + 5 * c->S;
+    if (rec == c->mrec && packed_loc(c))
+        return launch_packed_form<NP, UNROLL, true>(c, L, srec);
+    if (rec != c->mrec) {       // caller-built records: stage them first
+        k_stage_sources<<<(unsigned)(c->S / kGlueThreads), kGlueThreads, 0, c->stream>>>(
+            c->S, rec, c->mrec + 5 * c->S);
+        c->launches += 1;
+    }
+    return launch_packed_form<NP, UNROLL, false>(c, L, srec);
 }
 
 // Fused-kernel variants: scalar (targets per thread 1, 2, 4) or packed
@@ -1845,10 +1938,17 @@ static cudaError_t occ_of(int *occ)
     return occ_with_carveout(k_fused_mixed<P, UNROLL>, occ);
 }
 
+// Resident blocks of the packed kernel: the smaller of its two forms, so
+// that one launch shape serves both.
 template <int NP, int UNROLL>
 static cudaError_t occ_packed(int *occ)
 {
-    return occ_with_carveout(k_fused_packed<NP, UNROLL>, occ);
+    int o1 = 0, o2 = 0;
+    cudaError_t e = occ_with_carveout(k_fused_packed<NP, UNROLL, true>, &o1);
+    if (e == cudaSuccess)
+        e = occ_with_carveout(k_fused_packed<NP, UNROLL, false>, &o2);
+    *occ = o1 < o2 ? o1 : o2;
+    return e;
 }
 
 cudaError_t fused_occupancy(int P, int unroll, bool packed, int *occ)
@@ -1938,7 +2038,7 @@ cudaError_t launch_energy_on(cudaStream_t st, int64_t S, const Clu *clu, const d
 {
     const int64_t nb = S / kGlueThreads;
     k_prologue<2><<<(unsigned)nb, kGlueThreads, 0, st>>>(S, clu, nullptr, x, v, m, nullptr, drec,
-                                                         nullptr, nullptr, nullptr);
+                                                         nullptr, nullptr, nullptr, 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;

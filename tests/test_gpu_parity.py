@@ -223,6 +223,29 @@ def test_step_force_is_accel_at_predicted_velocity():
     ctx.close()
 
 
+@pytest.mark.parametrize("r_near", [0.05, 0.0])
+def test_packed_forms_match_oracle(orc, r_near):
+    """The packed kernel's two forms of the hole term of kappa_ij: with near
+    sources split off (r_near > 0) the law-of-cosines form a (R_i^2 - r_ij^2)
+    runs, without the split (r_near = 0) the dot-product form D_j.d_i.  Stars
+    at 0.01 and 0.06 from the hole and a ragged tail."""
+    n = 2 * 1024 + 130
+    x, v, m = cluster(n, 0.2, 4343)
+    x[5] = x[0] + np.array([0.01, 0.0, 0.0])
+    x[9] = x[0] + np.array([0.0, -0.06, 0.0])
+    want = orc.accel(x, v, m, c=15.0, eps=1e-4)
+    ctx = pn.pn_init(n, c=15.0, eps=1e-4, precision="mixed", device=0, r_near=r_near)
+    assert pn.pn_get_launch(ctx)["packed"] == 1
+    X, V, M = dev(x), dev(v), dev(m)
+    A = torch.empty_like(X)
+    pn.pn_accel(ctx, X, V, M, A)
+    pn.pn_sync(ctx)
+    got = A.cpu().numpy()
+    ctx.close()
+    err = rel(got, want)
+    assert np.median(err) <= MIX_MED and err.max() <= MIX_MAX, (np.median(err), err.max())
+
+
 @pytest.mark.parametrize("precision,pair_kernel",
                          [("fp64", "two_pass"), ("mixed", "fused"), ("mixed", "two_pass")])
 def test_plummer16k_sampled_targets_and_hole(orc, precision, pair_kernel):
