@@ -11,7 +11,8 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-SOURCES = [os.path.join(CSRC, f) for f in ("pn_kernels.cu", "pn_deriv.cu", "pn_api.cu", "pn_noalloc.cu", "pn_peaks.cu")]
+SOURCES = [os.path.join(CSRC, f) for f in ("pn_kernels.cu", "pn_order.cu", "pn_deriv.cu", "pn_api.cu", "pn_noalloc.cu",
+                                           "pn_peaks.cu")]
 HEADERS = [os.path.join(CSRC, "pn_internal.h"), os.path.join(CSRC, "pn_device.cuh"),
            os.path.join(os.path.dirname(HERE), "include", "pn.h")]
 LIB = os.path.join(HERE, "libpn.so")

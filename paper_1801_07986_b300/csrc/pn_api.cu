@@ -120,7 +120,7 @@ void set_params(pn_ctx *c, const pn_params *p, bool all_physics)
 
 void free_all(pn_ctx *c)
 {
-    void *bufs[] = {c->vp, c->mrec, c->drec, c->part, c->blk, c->glob, c->eout, c->flag, c->wcount,
+    void *bufs[] = {c->vp, c->mrec, c->sord, c->drec, c->part, c->blk, c->glob, c->eout, c->flag, c->wcount,
                     c->flag_step, c->hx, c->hv, c->hm, c->ha, c->nrec, c->ndrec, c->ncount,
                     c->nflag, c->rk_x, c->rk_v, c->rk_a, c->rk_sx, c->rk_sv, c->jbuf, c->hj0, c->hj1, c->abuf,
                     c->d_clu,
@@ -409,6 +409,16 @@ static pn_status init_common(pn_ctx **out, int nclu, const int64_t *off, const p
     c->inject_tx = 0;
     if (const char *ij = std::getenv("PN_INJECT_COPY_TIMEOUT"))
         c->inject_tx = ij[0] == '1' ? 16u : 0u;
+    // the packed law-of-cosines kernel runs on Hilbert-ordered slots
+    // (pn_order.cu) when the pair work is large enough to repay the sort's
+    // fixed cost (about ten short launches per evaluation);
+    // PN_SPATIAL=0 / 1 overrides
+    double pairs = 0.0;
+    for (int k = 0; k < nclu; ++k)
+        pairs += (double)c->hclu[k].ns_pad * (double)c->hclu[k].ns_pad;
+    c->spatial = pairs >= pn::kSpatialMinPairs;
+    if (const char *sp = std::getenv("PN_SPATIAL"))
+        c->spatial = sp[0] != '0';
     if (const char *pw = std::getenv("PN_FUSED_WORKERS")) {
         const int v = std::atoi(pw);
         if (v >= 1 && v <= 64)
@@ -485,9 +495,12 @@ static pn_status init_common(pn_ctx **out, int nclu, const int64_t *off, const p
         {(void **)&c->rk_a, sizeof(double) * 3 * (size_t)n},
         {(void **)&c->rk_sx, sizeof(double) * 3 * (size_t)n},
         {(void **)&c->rk_sv, sizeof(double) * 3 * (size_t)n},
-        // mixed: 5 record arrays + the packed kernel's staged sources (9 per slot)
-        {(void **)&c->mrec, sizeof(float4) * (params->precision == PN_MIXED ? 14 : 5) * (size_t)S},
+        // mixed: 5 record arrays + the packed kernel's staged sources (9 per slot);
+        // allocated whatever the precision, which pn_set_params may change
+        {(void **)&c->mrec, sizeof(float4) * 14 * (size_t)S},
         {(void **)&c->drec, sizeof(double4_32a) * 4 * (size_t)S},
+        // mixed: the spatial order of the packed kernel (sorted records, boxes, sort scratch)
+        {(void **)&c->sord, pn::order_buffer_bytes(S)},
         {(void **)&c->part, sizeof(double) * (size_t)part},
         {(void **)&c->blk, sizeof(double) * (size_t)c->blk_len},
         {(void **)&c->glob, sizeof(double) * pn::kGlobVals * (size_t)nclu},

@@ -19,6 +19,9 @@ constexpr int kPackVals = 9;       // packed adjoint sweeps: float4 per staged s
 constexpr int kFwdVals = 8;        // packed fused kernel: float4 per staged source record
 constexpr int kPackFlushTiles = 8; // packed fused kernel: tiles per single-precision partial
 constexpr int kPackWorkersMax = 4;  // packed fused kernel: stream-K workers per resident block (max)
+// Spatial order of the packed kernel by default from this many target-source
+// slot pairs per evaluation (sum over clusters of ns_pad^2) on.
+constexpr double kSpatialMinPairs = 4294967296.0;
 // Launch shape of the double-precision pair kernels (FP64 mode and energy).
 constexpr int kF64Threads = 128;
 constexpr int kF64Targets = 1;
@@ -40,8 +43,10 @@ constexpr int kNearTile = 128;
 constexpr int kNearVals = 6;       // P (3), Ee (3)
 // Global O(n) sums computed by the prologue (block partials, then totals):
 //   Q (3), W over all stars (3), W over far stars (3), SA_far, SB_far, Phi,
-//   near-star count (as a double in the block partials).
-constexpr int kGlobVals = 13;
+//   near-star count (as a double in the block partials), sum of |d_j| (the
+//   length scale of the spatial order).
+constexpr int kGlobVals = 14;
+constexpr int kGlobMeanR = 13;
 // Per-block values of the energy epilogue.
 constexpr int kEBlockVals = 9;     // eN, ePN, pN (3), pPN (3), sum m/R
 
@@ -88,6 +93,7 @@ struct pn_ctx {
     int *blk_clu;            // device: cluster of each 256-slot block
     bool any_near;           // some cluster has r_near > 0
     bool near_all;           // every cluster has r_near > 0
+    bool spatial;            // packed law-of-cosines kernel on Hilbert-ordered slots
     pn_params p;
     int device;
     cudaStream_t stream;
@@ -108,6 +114,7 @@ struct pn_ctx {
     // scratch, all owned by the context
     double *vp;          // n x 3: velocity at which the force is evaluated
     float4 *mrec;        // mixed records: 5 arrays of S float4
+    void *sord;          // mixed: spatial order (pn_order.cu: sorted records, boxes, sort scratch)
     double4_32a *drec;   // double records: 4 arrays of S double4_32a
     double *part;        // pair partial sums [jsplit][vals][S] (+ fused segments)
     int64_t part_len;    // doubles in `part`
@@ -199,5 +206,18 @@ struct FusedShape {
 };
 cudaError_t fused_shape(const pn_ctx *c, int P, int unroll, bool packed, FusedShape *out);
 int64_t fused_units(const Clu *h, int nclu, int P, bool packed, Clu *out);
+
+// Spatial order of the star slots (pn_order.cu).
+struct Order {
+    float4 *ssrec;     // staged records in sorted order (kFwdVals per slot)
+    float4 *box;       // per tile of kPackTile sorted sources: (min d, 0), (max d, max |d|)
+    unsigned *keys;    // 2 S sort keys
+    int *vals;         // 2 S sort values
+    int *perm;         // S: slot of sorted position k (second half of vals)
+    int *hist;         // per sort block and digit: counts, then scatter offsets
+};
+size_t order_buffer_bytes(int64_t S);
+Order order_of(pn_ctx *c);
+cudaError_t launch_spatial_order(pn_ctx *c);
 
 }  // namespace pn

@@ -245,6 +245,7 @@ k_prologue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
         g[10] = far * 0.25 * mj * (R2 + eps2) * iR3;
         g[11] = mj * iR;
         g[12] = near ? 1.0 : 0.0;
+        g[kGlobMeanR] = R;
     } else {
         // padding: zero mass far away, distinct positions
         const double px = 1.0e4 + (double)(lt - C.ns);
@@ -772,21 +773,30 @@ k_fused_mixed(const float4 *__restrict__ rec, int64_t S, const Clu *__restrict__
 //   restores Wr from N, U and Z in double.
 // Sums (kPackSums): N (3), U, Z, V' (3), Hs, Hv (3), E (3).
 
+// Far-unit criterion of the spatial form of k_fused_packed.
+constexpr float kFarTheta = 0.1f;
+
 struct PackTarget {
     float2 hx, hy, hz, lx, ly, lz;   // hi/lo split of d_i (lanes: two targets)
     float2 vx, vy, vz;               // 8/3 v_i
     float2 rr;                       // R_i^2
 };
 
-template <bool MASK, bool LOC>
+// HI: the separation from the high parts alone (x_ij = h_i - h_j), for units
+// of the spatial order whose boxes are far apart (k_fused_packed).
+template <bool MASK, bool LOC, bool HI>
 __device__ __forceinline__ void packed_pair(const PackTarget &tg, const float4 *__restrict__ sq,
                                             float2 eps2, bool selfx, bool selfy,
                                             float2 (&acc)[kPackSums])
 {
-    const float4 F0 = sq[0], F1 = sq[1], F2 = sq[2], F3 = sq[3];
-    const float2 dx = add2(add2(tg.hx, lo2(F0)), add2(tg.lx, lo2(F2)));
-    const float2 dy = add2(add2(tg.hy, hi2(F0)), add2(tg.ly, hi2(F2)));
-    const float2 dz = add2(add2(tg.hz, lo2(F1)), add2(tg.lz, lo2(F3)));
+    const float4 F0 = sq[0], F1 = sq[1], F3 = sq[3];
+    float2 dx = add2(tg.hx, lo2(F0)), dy = add2(tg.hy, hi2(F0)), dz = add2(tg.hz, lo2(F1));
+    if (!HI) {
+        const float4 F2 = sq[2];
+        dx = add2(dx, add2(tg.lx, lo2(F2)));
+        dy = add2(dy, add2(tg.ly, hi2(F2)));
+        dz = add2(dz, add2(tg.lz, lo2(F3)));
+    }
     float2 s2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, eps2)));
     float2 m = hi2(F1);
     float2 wx, wy, wz;
@@ -841,11 +851,20 @@ __device__ __forceinline__ void packed_pair(const PackTarget &tg, const float4 *
     acc[14] = fma2(wz, is, acc[14]);
 }
 
+// Local index (within the target block of 2 NP kMixThreads targets) of the
+// thread's k-th target: warp w owns the 64 NP contiguous targets from
+// 64 NP w, lane l takes l, l + 32, l + 64, ...; packed pair pp holds targets
+// 2 pp (lane x) and 2 pp + 1 (lane y), 32 apart.
+__device__ __forceinline__ int packed_target(int NP, int k)
+{
+    return 64 * NP * (int)(threadIdx.x / 32) + 32 * k + (int)(threadIdx.x % 32);
+}
+
 // Staged record length of the two forms.
 template <bool LOC>
 __host__ __device__ constexpr int pack_vals() { return LOC ? kFwdVals : kPackVals; }
 
-template <int NP, int UNROLL, bool MASK, bool LOC>
+template <int NP, int UNROLL, bool MASK, bool LOC, bool HI>
 __device__ __forceinline__ void packed_tile(const float4 (*__restrict__ sh)[pack_vals<LOC>()],
                                             int64_t j0, int64_t t0, const PackTarget (&tg)[NP],
                                             float2 eps2, float2 (&acc)[NP][kPackSums])
@@ -855,10 +874,10 @@ __device__ __forceinline__ void packed_tile(const float4 (*__restrict__ sh)[pack
         const int64_t j = j0 + q;
 #pragma unroll
         for (int pp = 0; pp < NP; ++pp) {
-            const int64_t tx = t0 + (2 * pp) * kMixThreads + threadIdx.x;
+            const int64_t tx = t0 + packed_target(NP, 2 * pp);
             const bool selfx = MASK && j == tx;
-            const bool selfy = MASK && j == tx + kMixThreads;
-            packed_pair<MASK, LOC>(tg[pp], sh[q], eps2, selfx, selfy, acc[pp]);
+            const bool selfy = MASK && j == tx + 32;
+            packed_pair<MASK, LOC, HI>(tg[pp], sh[q], eps2, selfx, selfy, acc[pp]);
         }
     }
 }
@@ -896,12 +915,24 @@ __device__ __forceinline__ int64_t unit_source(const Clu *__restrict__ clu, int 
 // worker's segment slot in FP64 (each value is owned by one thread).  A copy
 // that does not complete within the poll limit sets kFlagTimeout in `flag`
 // and ends the block.
-template <int NP, int UNROLL, bool LOC>
+//
+// FORM 0: the D form of the hole term on stage_source records; 1: the
+// law-of-cosines form on stage_source_fwd records; 2: form 1 on records in
+// the spatial order of pn_order.cu, with a box per tile (`box`).  In form 2
+// a unit whose target-block box and source-tile box are at least
+// kFarTheta (R_B + R_T) apart (R the largest |d| in either box) takes the
+// separation from the high parts alone: the dropped low parts change x_ij by
+// at most 2^-24 (|d_i| + |d_j|) <= 2^-24 (R_B + R_T), i.e. by at most
+// 2^-24 / kFarTheta ~ 6e-7 of |x_ij| for the nearest such pairs and less for
+// the rest -- pairs that far apart carry a small share of a star's force.
+// Near units, and the units that hold self pairs, keep the full separation.
+template <int NP, int UNROLL, int FORM>
 __global__ void __launch_bounds__(kMixThreads, NP == 2 ? 3 : 5)
 k_fused_packed(const float4 *__restrict__ srec, const Clu *__restrict__ clu, int nclu,
                int64_t total_units, int64_t G, int *__restrict__ wcount, int *__restrict__ flag,
-               unsigned extra_tx, double *__restrict__ part)
+               unsigned extra_tx, const float4 *__restrict__ box, double *__restrict__ part)
 {
+    constexpr bool LOC = FORM >= 1, SPATIAL = FORM == 2;
     constexpr int P = 2 * NP, TI = kMixThreads * P, RV = pack_vals<LOC>();
     __shared__ __align__(128) float4 sh[2][kPackTile][RV];
     __shared__ __align__(8) uint64_t full[2];
@@ -941,7 +972,7 @@ k_fused_packed(const float4 *__restrict__ srec, const Clu *__restrict__ clu, int
             PackTarget tg[NP];
 #pragma unroll
             for (int pp = 0; pp < NP; ++pp) {
-                const int64_t ta = t0 + (2 * pp) * kMixThreads + threadIdx.x, tb = ta + kMixThreads;
+                const int64_t ta = t0 + packed_target(NP, 2 * pp), tb = ta + 32;
                 const float4 *ra = srec + ta * RV, *rb = srec + tb * RV;
                 const float4 A0 = ra[0], A1 = ra[1], A2 = ra[2], A3 = ra[3], A4 = ra[4], A5 = ra[5];
                 const float4 B0 = rb[0], B1 = rb[1], B2 = rb[2], B3 = rb[3], B4 = rb[4], B5 = rb[5];
@@ -957,6 +988,19 @@ k_fused_packed(const float4 *__restrict__ srec, const Clu *__restrict__ clu, int
                 tg[pp].vy = make_float2(kEightThirds * A4.z, kEightThirds * B4.z);
                 tg[pp].vz = make_float2(kEightThirds * A5.x, kEightThirds * B5.x);
             }
+            float4 blo = make_float4(0.0f, 0.0f, 0.0f, 0.0f), bhi = blo;
+            if (SPATIAL) {      // box of the warp's targets: union of their tiles' boxes
+                const float4 *bb = box + 2 * ((t0 + packed_target(NP, 0) - threadIdx.x % 32) / kPackTile);
+                blo = bb[0];
+                bhi = bb[1];
+#pragma unroll
+                for (int q = 1; q < 2 * NP * 32 / kPackTile; ++q) {
+                    const float4 l = bb[2 * q], h = bb[2 * q + 1];
+                    blo = make_float4(fminf(blo.x, l.x), fminf(blo.y, l.y), fminf(blo.z, l.z), 0.0f);
+                    bhi = make_float4(fmaxf(bhi.x, h.x), fmaxf(bhi.y, h.y), fmaxf(bhi.z, h.z),
+                                      fmaxf(bhi.w, h.w));
+                }
+            }
             double *out = part + (t0 / TI + w) * (int64_t)(kPackSums * TI);
             bool first = true;
             float2 acc[NP][kPackSums];
@@ -970,19 +1014,29 @@ k_fused_packed(const float4 *__restrict__ srec, const Clu *__restrict__ clu, int
                 const int b = it & 1;
                 const bool ok = mbar_wait(&full[b], (it >> 1) & 1);
                 const bool diag = (j0 < t0 + TI) && (t0 < j0 + kPackTile);
+                bool far = false;
+                if (SPATIAL && !diag) {
+                    const float4 l = box[2 * (j0 / kPackTile)], h = box[2 * (j0 / kPackTile) + 1];
+                    const float gx = fmaxf(0.0f, fmaxf(l.x - bhi.x, blo.x - h.x));
+                    const float gy = fmaxf(0.0f, fmaxf(l.y - bhi.y, blo.y - h.y));
+                    const float gz = fmaxf(0.0f, fmaxf(l.z - bhi.z, blo.z - h.z));
+                    const float lim = kFarTheta * (bhi.w + h.w);
+                    far = gx * gx + gy * gy + gz * gz >= lim * lim;
+                }
                 if (diag)
-                    packed_tile<NP, UNROLL, true, LOC>(sh[b], j0, t0, tg, eps2, acc);
+                    packed_tile<NP, UNROLL, true, LOC, false>(sh[b], j0, t0, tg, eps2, acc);
+                else if (SPATIAL && far)
+                    packed_tile<NP, UNROLL, false, LOC, true>(sh[b], j0, t0, tg, eps2, acc);
                 else
-                    packed_tile<NP, UNROLL, false, LOC>(sh[b], j0, t0, tg, eps2, acc);
+                    packed_tile<NP, UNROLL, false, LOC, false>(sh[b], j0, t0, tg, eps2, acc);
                 if (((u - ub + 1) % kPackFlushTiles) == 0 || u + 1 == uend) {
 #pragma unroll
                     for (int pp = 0; pp < NP; ++pp)
 #pragma unroll
                         for (int k = 0; k < kPackSums; ++k) {
-                            double *o = out + k * TI + (2 * pp) * kMixThreads + threadIdx.x;
+                            double *o = out + k * TI + packed_target(NP, 2 * pp);
                             o[0] = first ? (double)acc[pp][k].x : o[0] + (double)acc[pp][k].x;
-                            o[kMixThreads] = first ? (double)acc[pp][k].y
-                                                   : o[kMixThreads] + (double)acc[pp][k].y;
+                            o[32] = first ? (double)acc[pp][k].y : o[32] + (double)acc[pp][k].y;
                             acc[pp][k] = make_float2(0.0f, 0.0f);
                         }
                     first = false;
@@ -1014,12 +1068,16 @@ k_stage_sources(int64_t S, const float4 *__restrict__ rec, float4 *__restrict__ 
 
 // Sums, for every star slot, the stream-K segments that cover its target
 // block (in block order) into the pass-1 / pass-2 partial layout with one
-// split: p1[k][t] (k < kP1Vals), p2[k][t] (k < kP2Vals).
+// split: p1[k][t] (k < kP1Vals), p2[k][t] (k < kP2Vals).  NV values per
+// segment (fewer than kFusedVals: the packed kernel's, without Wr), RV float4
+// per staged record; with `perm` the kernel ran on the spatial order and
+// position t belongs to slot perm[t].
 template <int P, int NV, int RV>
 __global__ void __launch_bounds__(kGlueThreads)
 k_fused_gather(const double *__restrict__ part, int64_t S, const Clu *__restrict__ clu,
                const int *__restrict__ blk_clu, int64_t total_units, int64_t G, int tile,
-               const float4 *__restrict__ srec, double *__restrict__ p1, double *__restrict__ p2)
+               const float4 *__restrict__ srec, const int *__restrict__ perm,
+               double *__restrict__ p1, double *__restrict__ p2)
 {
     constexpr int TI = kMixThreads * P;
     const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
@@ -1050,9 +1108,10 @@ k_fused_gather(const double *__restrict__ part, int64_t S, const Clu *__restrict
             acc[k] += in[k * TI + lt];
     }
     constexpr int o2 = NV - kP2Vals;     // first pass-2 value in the segment
+    const int64_t ts = perm ? (int64_t)perm[t] : t;
 #pragma unroll
     for (int k = 0; k < o2; ++k)
-        p1[(int64_t)k * S + t] = acc[k];
+        p1[(int64_t)k * S + ts] = acc[k];
     if (o2 < kP1Vals) {
         // Wr from the identity R_i^2 - R_j^2 = 2 d_i.x_ij - (r_ij^2 - eps^2):
         // sum_j m_j (R_i^2 - R_j^2)/r_ij^3 = 2 d_i.N - U + eps^2 Z, so
@@ -1062,11 +1121,12 @@ k_fused_gather(const double *__restrict__ part, int64_t S, const Clu *__restrict
         const double d1 = -((double)r[0].z + (double)r[2].z);
         const double d2 = -((double)r[1].x + (double)r[3].x);
         const double R2 = d0 * d0 + d1 * d1 + d2 * d2;
-        p1[(int64_t)5 * S + t] = (R2 - C.eps2) * acc[4] - 2.0 * (d0 * acc[0] + d1 * acc[1] + d2 * acc[2]) + acc[3];
+        p1[(int64_t)5 * S + ts] =
+            (R2 - C.eps2) * acc[4] - 2.0 * (d0 * acc[0] + d1 * acc[1] + d2 * acc[2]) + acc[3];
     }
 #pragma unroll
     for (int k = 0; k < kP2Vals; ++k)
-        p2[(int64_t)k * S + t] = acc[o2 + k];
+        p2[(int64_t)k * S + ts] = acc[o2 + k];
 }
 
 // ------------------------------------------------ pair kernels: double --
@@ -1820,7 +1880,7 @@ static cudaError_t launch_fused_p(pn_ctx *c, const Layout &L, const float4 *rec)
         return e;
     k_fused_gather<P, kFusedVals, 0><<<(unsigned)(c->S / kGlueThreads), kGlueThreads, 0, c->stream>>>(
         c->part + L.seg, c->S, c->d_clu, blk_table(c), c->fused_units, c->fused_G, kMixTile,
-        nullptr, c->part + L.p1, c->part + L.p2);
+        nullptr, nullptr, c->part + L.p1, c->part + L.p2);
     c->launches += 1;
     return cudaGetLastError();
 }
@@ -1829,42 +1889,57 @@ static cudaError_t launch_fused_p(pn_ctx *c, const Layout &L, const float4 *rec)
 // law-of-cosines form on the prologue's records when every cluster splits off
 // its near sources (packed_loc), else the D form; caller-built records (far
 // form: every source keeps its hole term) are staged in the D form first.
-template <int NP, int UNROLL, bool LOC>
-static cudaError_t launch_packed_form(pn_ctx *c, const Layout &L, const float4 *srec)
+// Form FORM of the packed kernel (k_fused_packed) on staged records `srec`
+// (boxes and the sorted-to-slot map for form 2), then the gather.
+template <int NP, int UNROLL, int FORM>
+static cudaError_t launch_packed_form(pn_ctx *c, const Layout &L, const float4 *srec,
+                                      const float4 *box, const int *perm)
 {
     cudaEvent_t end = nullptr;
     timing_begin(c, 1, &end);
-    k_fused_packed<NP, UNROLL, LOC><<<(unsigned)c->fused_grid, kMixThreads, 0, c->stream>>>(
+    k_fused_packed<NP, UNROLL, FORM><<<(unsigned)c->fused_grid, kMixThreads, 0, c->stream>>>(
         srec, c->d_clu, c->nclu, c->fused_units, c->fused_G, c->wcount, c->flag, c->inject_tx,
-        c->part + L.seg);
+        box, c->part + L.seg);
     c->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (end)
         cudaEventRecord(end, c->stream);
     if (e != cudaSuccess)
         return e;
-    k_fused_gather<2 * NP, kPackSums, pack_vals<LOC>()>
+    k_fused_gather<2 * NP, kPackSums, pack_vals<(FORM >= 1)>()>
         <<<(unsigned)(c->S / kGlueThreads), kGlueThreads, 0, c->stream>>>(
             c->part + L.seg, c->S, c->d_clu, blk_table(c), c->fused_units, c->fused_G, kPackTile,
-            srec, c->part + L.p1, c->part + L.p2);
+            srec, perm, c->part + L.p1, c->part + L.p2);
     c->launches += 1;
     return cudaGetLastError();
 }
 
 bool packed_loc(const pn_ctx *c) { return c->fused_packed && c->near_all; }
 
+// The packed kernel on the staged records at c->mrec + 5 S: on the
+// prologue's records the law-of-cosines form when every cluster splits off
+// its near sources (packed_loc; in the spatial order when c->spatial), else
+// the D form; caller-built records (far form: every source keeps its hole
+// term) are staged in the D form first.
 template <int NP, int UNROLL>
 static cudaError_t launch_packed_u(pn_ctx *c, const Layout &L, const float4 *rec)
 {
     const float4 *srec = c->mrec + 5 * c->S;
-    if (rec == c->mrec && packed_loc(c))
-        return launch_packed_form<NP, UNROLL, true>(c, L, srec);
+    if (rec == c->mrec && packed_loc(c)) {
+        if (!c->spatial)
+            return launch_packed_form<NP, UNROLL, 1>(c, L, srec, nullptr, nullptr);
+        const cudaError_t e = launch_spatial_order(c);
+        if (e != cudaSuccess)
+            return e;
+        const Order o = order_of(c);
+        return launch_packed_form<NP, UNROLL, 2>(c, L, o.ssrec, o.box, o.perm);
+    }
     if (rec != c->mrec) {       // caller-built records: stage them first
         k_stage_sources<<<(unsigned)(c->S / kGlueThreads), kGlueThreads, 0, c->stream>>>(
             c->S, rec, c->mrec + 5 * c->S);
         c->launches += 1;
     }
-    return launch_packed_form<NP, UNROLL, false>(c, L, srec);
+    return launch_packed_form<NP, UNROLL, 0>(c, L, srec, nullptr, nullptr);
 }
 
 // Fused-kernel variants: scalar (targets per thread 1, 2, 4) or packed
@@ -1943,11 +2018,14 @@ static cudaError_t occ_of(int *occ)
 template <int NP, int UNROLL>
 static cudaError_t occ_packed(int *occ)
 {
-    int o1 = 0, o2 = 0;
-    cudaError_t e = occ_with_carveout(k_fused_packed<NP, UNROLL, true>, &o1);
+    int o[3] = {0, 0, 0};
+    cudaError_t e = occ_with_carveout(k_fused_packed<NP, UNROLL, 0>, &o[0]);
     if (e == cudaSuccess)
-        e = occ_with_carveout(k_fused_packed<NP, UNROLL, false>, &o2);
-    *occ = o1 < o2 ? o1 : o2;
+        e = occ_with_carveout(k_fused_packed<NP, UNROLL, 1>, &o[1]);
+    if (e == cudaSuccess)
+        e = occ_with_carveout(k_fused_packed<NP, UNROLL, 2>, &o[2]);
+    *occ = o[0] < o[1] ? o[0] : o[1];
+    *occ = o[2] < *occ ? o[2] : *occ;
     return e;
 }
 

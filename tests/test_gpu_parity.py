@@ -246,6 +246,49 @@ def test_packed_forms_match_oracle(orc, r_near):
     assert np.median(err) <= MIX_MED and err.max() <= MIX_MAX, (np.median(err), err.max())
 
 
+@pytest.mark.parametrize("spatial", ["1", "0"])
+def test_spatial_order_with_tight_pairs(orc, monkeypatch, spatial):
+    """The packed kernel on Morton-ordered slots (PN_SPATIAL=1, the default)
+    or in slot order: tight pairs (separations 1e-4 .. 1e-3) planted at 1 to 6
+    from the hole, where the high parts alone would lose the separation, and
+    stars near the hole; every body against the oracle."""
+    monkeypatch.setenv("PN_SPATIAL", spatial)
+    n = 6 * 1024 + 77
+    x, v, m = cluster(n, 0.3, 4444)
+    rng = np.random.default_rng(44)
+    for k in range(40):
+        a, b = 10 + 2 * k, 11 + 2 * k
+        u = rng.normal(size=3)
+        x[a] = x[0] + u / np.linalg.norm(u) * rng.uniform(1.0, 6.0)
+        w = rng.normal(size=3)
+        x[b] = x[a] + w / np.linalg.norm(w) * 10.0 ** rng.uniform(-4.0, -3.0)
+    x[100] = x[0] + np.array([0.003, 0.0, 0.0])
+    x[101] = x[0] + np.array([0.0, 0.03, 0.0])
+    want = orc.accel(x, v, m, c=25.0, eps=2e-5)
+    got = gpu_accel(x, v, m, "mixed", c=25.0, eps=2e-5)
+    err = rel(got, want)
+    assert np.median(err) <= MIX_MED and err.max() <= MIX_MAX, (np.median(err), err.max())
+
+
+def test_precision_switch_after_init(orc):
+    """A context created in FP64 and switched to mixed by pn_set_params uses
+    the mixed records (allocated at pn_init whatever the precision)."""
+    n = 1500
+    x, v, m = cluster(n, 0.1, 4545)
+    want = orc.accel(x, v, m, c=30.0, eps=1e-4)
+    ctx = pn.pn_init(n, c=30.0, eps=1e-4, precision="fp64", device=0)
+    X, V, M = dev(x), dev(v), dev(m)
+    A = torch.empty_like(X)
+    for prec, ok in (("fp64", lambda e: e.max() <= FP64_TOL),
+                     ("mixed", lambda e: np.median(e) <= MIX_MED and e.max() <= MIX_MAX)):
+        pn.pn_set_params(ctx, precision=prec)
+        pn.pn_accel(ctx, X, V, M, A)
+        pn.pn_sync(ctx)
+        err = rel(A.cpu().numpy(), want)
+        assert ok(err), (prec, np.median(err), err.max())
+    ctx.close()
+
+
 @pytest.mark.parametrize("precision,pair_kernel",
                          [("fp64", "two_pass"), ("mixed", "fused"), ("mixed", "two_pass")])
 def test_plummer16k_sampled_targets_and_hole(orc, precision, pair_kernel):
