@@ -48,6 +48,8 @@ FLOPS_PASS2 = 67   # hand count of the mixed pass-2 pair body
 FLOPS_FUSED = 77   # hand count of the scalar fused pair body (pass 1 + pass 2 sharing x, r, rsqrt)
 FLOPS_PACKED = 72  # hand count of the packed fused pair body, law-of-cosines form (r_near > 0)
 OPS_PACKED = 46    # FP32-pipe operations per pair of that body (FMA, add and mul count 1 each)
+FLOPS_PACKED_FAR = 66  # the same body on far units of the spatial order (x_ij from the high parts)
+OPS_PACKED_FAR = 40
 FLOPS_JERK = 213   # hand count of the dual-number pair body of the jerk
                    # (dual add 2, dual multiply 4, scalar x dual 2, rsqrt + its derivative 6)
 FP32_LANES_PER_SM = 128
@@ -304,6 +306,7 @@ def run_native(args, w):
     pn.pn_sync(ctx)
     launches = pn.pn_launch_count(ctx) - launches0
     kms, klaunch = pn.pn_get_timing(ctx)
+    far_units, all_units = pn.pn_get_pair_stats(ctx)
     pn.pn_set_timing(ctx, False)
     ms = float(sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)))
     if world > 1:
@@ -325,8 +328,11 @@ def run_native(args, w):
     pairs = float(w.n - 1) * (w.n - 2)
     fused = args.precision == "mixed" and args.pair_kernel == "fused"
     packed = fused and bool(launch.get("packed"))
-    fpp = (FLOPS_PACKED if packed else FLOPS_FUSED) if fused else (
-        FLOPS_PASS2 if k_dom == 1 else FLOPS_PASS1)
+    # share of the pairs the spatially ordered packed kernel took through its
+    # far-unit body (device counters; 0 without the spatial order)
+    far_frac = far_units / all_units if packed and all_units else 0.0
+    fpp = (FLOPS_PACKED - far_frac * (FLOPS_PACKED - FLOPS_PACKED_FAR) if packed else FLOPS_FUSED) \
+        if fused else (FLOPS_PASS2 if k_dom == 1 else FLOPS_PASS1)
     flops = fpp * pairs
     achieved = flops / (per_launch_ms * 1e-3) / 1e12
     clocks = clk.summary()
@@ -347,8 +353,10 @@ def run_native(args, w):
     if packed:
         # the FP32 pipe's own limit: operations issued per pair against its
         # lane-operation rate (an FMA is one operation and two flops)
-        ops = OPS_PACKED * pairs / (per_launch_ms * 1e-3)
-        roof["fp32_pipe_ops_per_pair"] = OPS_PACKED
+        opp = OPS_PACKED - far_frac * (OPS_PACKED - OPS_PACKED_FAR)
+        ops = opp * pairs / (per_launch_ms * 1e-3)
+        roof["far_unit_fraction"] = far_frac
+        roof["fp32_pipe_ops_per_pair"] = opp
         roof["fp32_pipe_frac"] = ops / (sms * FP32_LANES_PER_SM * sm_max * 1e6)
     try:
         meas = pn.pn_measure_peaks(local, stream)

@@ -286,6 +286,17 @@ pn_status pn_set_timing(pn_ctx *ctx, int enable);
 pn_status pn_get_timing(pn_ctx *ctx, double ms[3], int64_t launches[3]);
 
 /*
+ * Work split of the mixed-precision packed pair kernel when it runs on the
+ * spatial (Hilbert) order of the stars: out[0] the (warp, source tile) units
+ * whose target and source boxes were far enough apart for the pair
+ * separation from the high single-precision parts alone, out[1] all units,
+ * counted on the device since pn_init or the last pn_set_timing(ctx, 1).
+ * Each unit is 64 x (2 x targets per thread x 32) pairs.  Waits for the
+ * stream.  Errors: PN_EINVAL (NULL out), PN_ECUDA.
+ */
+pn_status pn_get_pair_stats(pn_ctx *ctx, int64_t out[2]);
+
+/*
  * Launch shape of the pair kernels for this context: out[0] threads per
  * block, out[1] targets per thread, out[2] sources per shared-memory tile,
  * out[3] blocks along targets, out[4] source splits (two-pass) or

@@ -419,6 +419,12 @@ static pn_status init_common(pn_ctx **out, int nclu, const int64_t *off, const p
     c->spatial = pairs >= pn::kSpatialMinPairs;
     if (const char *sp = std::getenv("PN_SPATIAL"))
         c->spatial = sp[0] != '0';
+    c->far_theta = pn::kFarTheta;
+    if (const char *ft = std::getenv("PN_FAR_THETA")) {
+        const double v = std::atof(ft);
+        if (v >= 0.02 && v <= 10.0)
+            c->far_theta = (float)v;
+    }
     if (const char *pw = std::getenv("PN_FUSED_WORKERS")) {
         const int v = std::atoi(pw);
         if (v >= 1 && v <= 64)
@@ -511,6 +517,7 @@ static pn_status init_common(pn_ctx **out, int nclu, const int64_t *off, const p
         {(void **)&c->eout, sizeof(double) * 8 * (size_t)nclu},
         {(void **)&c->flag, sizeof(int)},
         {(void **)&c->wcount, sizeof(int)},
+        {(void **)&c->units_cnt, 2 * sizeof(unsigned long long)},
         {(void **)&c->flag_step, sizeof(unsigned long long)},
         {(void **)&c->d_clu, sizeof(pn::Clu) * (size_t)nclu},
         {(void **)&c->blk_clu, sizeof(int) * (size_t)nglue},
@@ -546,6 +553,8 @@ static pn_status init_common(pn_ctx **out, int nclu, const int64_t *off, const p
         e = cudaMemcpy(c->flag_step, &none, sizeof none, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemset(c->ncount, 0, sizeof(int) * (size_t)(nclu + nglue));
+    if (e == cudaSuccess)
+        e = cudaMemset(c->units_cnt, 0, 2 * sizeof(unsigned long long));
     if (e != cudaSuccess) {
         free_all(c);
         delete c;
@@ -956,6 +965,26 @@ pn_status pn_set_timing(pn_ctx *c, int enable)
         c->tm.launches[k] = 0;
     }
     c->timing_on = enable ? 1 : 0;
+    if (enable)
+        PN_CUDA(cudaMemsetAsync(c->units_cnt, 0, 2 * sizeof(unsigned long long), c->stream),
+                "reset of the pair statistics");
+    return ok();
+}
+
+pn_status pn_get_pair_stats(pn_ctx *c, int64_t out[2])
+{
+    if (check_ctx(c) != PN_OK)
+        return PN_EINVAL;
+    if (!out)
+        return fail(PN_EINVAL, "pn_get_pair_stats: NULL output");
+    DeviceGuard g(c->device);
+    PN_CUDA(g.err, "cudaSetDevice");
+    unsigned long long h[2] = {0, 0};
+    PN_CUDA(cudaMemcpyAsync(h, c->units_cnt, sizeof h, cudaMemcpyDeviceToHost, c->stream),
+            "read of the pair statistics");
+    PN_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
+    out[0] = (int64_t)h[0];
+    out[1] = (int64_t)h[1];
     return ok();
 }
 

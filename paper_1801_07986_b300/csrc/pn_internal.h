@@ -22,6 +22,9 @@ constexpr int kPackWorkersMax = 4;  // packed fused kernel: stream-K workers per
 // Spatial order of the packed kernel by default from this many target-source
 // slot pairs per evaluation (sum over clusters of ns_pad^2) on.
 constexpr double kSpatialMinPairs = 4294967296.0;
+// Far-unit criterion of the spatial order (k_fused_packed): box gap at least
+// kFarTheta times the sum of the boxes' largest |d|.
+constexpr float kFarTheta = 0.05f;
 // Launch shape of the double-precision pair kernels (FP64 mode and energy).
 constexpr int kF64Threads = 128;
 constexpr int kF64Targets = 1;
@@ -94,6 +97,8 @@ struct pn_ctx {
     bool any_near;           // some cluster has r_near > 0
     bool near_all;           // every cluster has r_near > 0
     bool spatial;            // packed law-of-cosines kernel on Hilbert-ordered slots
+    float far_theta;         // spatial order: far-unit criterion (k_fused_packed)
+    unsigned long long *units_cnt;  // spatial order: [0] far warp-units, [1] all warp-units
     pn_params p;
     int device;
     cudaStream_t stream;

@@ -773,9 +773,6 @@ k_fused_mixed(const float4 *__restrict__ rec, int64_t S, const Clu *__restrict__
 //   restores Wr from N, U and Z in double.
 // Sums (kPackSums): N (3), U, Z, V' (3), Hs, Hv (3), E (3).
 
-// Far-unit criterion of the spatial form of k_fused_packed.
-constexpr float kFarTheta = 0.1f;
-
 struct PackTarget {
     float2 hx, hy, hz, lx, ly, lz;   // hi/lo split of d_i (lanes: two targets)
     float2 vx, vy, vz;               // 8/3 v_i
@@ -919,20 +916,25 @@ __device__ __forceinline__ int64_t unit_source(const Clu *__restrict__ clu, int 
 // FORM 0: the D form of the hole term on stage_source records; 1: the
 // law-of-cosines form on stage_source_fwd records; 2: form 1 on records in
 // the spatial order of pn_order.cu, with a box per tile (`box`).  In form 2
-// a unit whose target-block box and source-tile box are at least
-// kFarTheta (R_B + R_T) apart (R the largest |d| in either box) takes the
-// separation from the high parts alone: the dropped low parts change x_ij by
-// at most 2^-24 (|d_i| + |d_j|) <= 2^-24 (R_B + R_T), i.e. by at most
-// 2^-24 / kFarTheta ~ 6e-7 of |x_ij| for the nearest such pairs and less for
-// the rest -- pairs that far apart carry a small share of a star's force.
-// Near units, and the units that hold self pairs, keep the full separation.
+// each warp tests its own 64 NP contiguous targets against the tile: when
+// their box and the tile's are at least theta (R_B + R_T) apart (R the
+// largest |d| in either box, theta = kFarTheta = 0.05 unless tuned) the warp
+// takes the separation from the high parts alone: the dropped low parts
+// change x_ij by at most 2^-24 (|d_i| + |d_j|) <= 2^-24 (R_B + R_T), i.e. by
+// at most 2^-24 / theta ~ 1.2e-6 of |x_ij| for the nearest such pairs and
+// less for the rest -- pairs that far apart carry a small share of a star's
+// force (measured on the 128k eccentric workload: the median error against
+// the FP64 oracle goes from 1.1e-8 to 2.2e-8 for any theta in 0.03 .. 0.2).  Near units, and the units that hold self pairs, keep the full
+// separation.  units_cnt[0] / [1] count far / all warp-units.
 template <int NP, int UNROLL, int FORM>
 __global__ void __launch_bounds__(kMixThreads, NP == 2 ? 3 : 5)
 k_fused_packed(const float4 *__restrict__ srec, const Clu *__restrict__ clu, int nclu,
                int64_t total_units, int64_t G, int *__restrict__ wcount, int *__restrict__ flag,
-               unsigned extra_tx, const float4 *__restrict__ box, double *__restrict__ part)
+               unsigned extra_tx, const float4 *__restrict__ box, float far_theta,
+               unsigned long long *__restrict__ units_cnt, double *__restrict__ part)
 {
     constexpr bool LOC = FORM >= 1, SPATIAL = FORM == 2;
+    unsigned n_far = 0, n_all = 0;      // this warp's units (form 2)
     constexpr int P = 2 * NP, TI = kMixThreads * P, RV = pack_vals<LOC>();
     __shared__ __align__(128) float4 sh[2][kPackTile][RV];
     __shared__ __align__(8) uint64_t full[2];
@@ -949,8 +951,13 @@ k_fused_packed(const float4 *__restrict__ srec, const Clu *__restrict__ clu, int
             s_w = atomicAdd(wcount, 1);
         __syncthreads();
         const int64_t w = s_w;
-        if (w >= G)
+        if (w >= G) {
+            if (SPATIAL && threadIdx.x % 32 == 0) {
+                atomicAdd(&units_cnt[0], (unsigned long long)n_far);
+                atomicAdd(&units_cnt[1], (unsigned long long)n_all);
+            }
             break;
+        }
         int64_t u = w * total_units / G;
         const int64_t u1 = (w + 1) * total_units / G;
         if (threadIdx.x == 0 && u < u1) {   // both buffers are free here
@@ -1020,8 +1027,12 @@ k_fused_packed(const float4 *__restrict__ srec, const Clu *__restrict__ clu, int
                     const float gx = fmaxf(0.0f, fmaxf(l.x - bhi.x, blo.x - h.x));
                     const float gy = fmaxf(0.0f, fmaxf(l.y - bhi.y, blo.y - h.y));
                     const float gz = fmaxf(0.0f, fmaxf(l.z - bhi.z, blo.z - h.z));
-                    const float lim = kFarTheta * (bhi.w + h.w);
+                    const float lim = far_theta * (bhi.w + h.w);
                     far = gx * gx + gy * gy + gz * gz >= lim * lim;
+                }
+                if (SPATIAL) {
+                    n_far += far ? 1u : 0u;
+                    n_all += 1u;
                 }
                 if (diag)
                     packed_tile<NP, UNROLL, true, LOC, false>(sh[b], j0, t0, tg, eps2, acc);
@@ -1899,7 +1910,7 @@ static cudaError_t launch_packed_form(pn_ctx *c, const Layout &L, const float4 *
     timing_begin(c, 1, &end);
     k_fused_packed<NP, UNROLL, FORM><<<(unsigned)c->fused_grid, kMixThreads, 0, c->stream>>>(
         srec, c->d_clu, c->nclu, c->fused_units, c->fused_G, c->wcount, c->flag, c->inject_tx,
-        box, c->part + L.seg);
+        box, c->far_theta, c->units_cnt, c->part + L.seg);
     c->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (end)

@@ -99,6 +99,7 @@ def _load():
                 "pn_set_timing": [P, I],
                 "pn_get_timing": [P, P, P],
                 "pn_get_launch": [P, P],
+                "pn_get_pair_stats": [P, P],
                 "pn_launch_count": [P, P],
                 "pn_energy_noalloc": [I, P, I64, D, D, D, P, P, P, P],
                 "pn_measure_peaks": [I, P, P],
@@ -465,6 +466,14 @@ def pn_get_timing(ctx: Context):
     _check(_load().pn_get_timing(ctx.handle, ms.ctypes.data_as(ctypes.c_void_p),
                                  nl.ctypes.data_as(ctypes.c_void_p)))
     return ms, nl
+
+
+def pn_get_pair_stats(ctx: Context) -> tuple[int, int]:
+    """(far units, all units) of the spatially ordered packed kernel since
+    pn_init or the last pn_set_timing(ctx, True)."""
+    out = np.zeros(2, dtype=np.int64)
+    _check(_load().pn_get_pair_stats(ctx.handle, out.ctypes.data_as(ctypes.c_void_p)))
+    return int(out[0]), int(out[1])
 
 
 def pn_get_launch(ctx: Context) -> dict:

@@ -270,6 +270,33 @@ def test_spatial_order_with_tight_pairs(orc, monkeypatch, spatial):
     assert np.median(err) <= MIX_MED and err.max() <= MIX_MAX, (np.median(err), err.max())
 
 
+@pytest.mark.parametrize("spatial", ["1", "0"])
+def test_pair_stats_count_the_units(monkeypatch, spatial):
+    """pn_get_pair_stats: every (warp, tile) unit of the spatially ordered
+    packed kernel is counted once per evaluation; none without the order."""
+    monkeypatch.setenv("PN_SPATIAL", spatial)
+    n = 6 * 1024 + 77
+    x, v, m = cluster(n, 0.3, 4646)
+    ctx = pn.pn_init(n, c=25.0, eps=2e-5, precision="mixed", device=0)
+    shape = pn.pn_get_launch(ctx)
+    X, V, M = dev(x), dev(v), dev(m)
+    A = torch.empty_like(X)
+    pn.pn_set_timing(ctx, True)
+    for _ in range(2):
+        pn.pn_accel(ctx, X, V, M, A)
+    far, allu = pn.pn_get_pair_stats(ctx)
+    pn.pn_set_timing(ctx, False)
+    ctx.close()
+    ns_pad = (n - 1 + 511) // 512 * 512
+    ti = shape["threads"] * shape["targets_per_thread"]
+    warps = shape["threads"] // 32
+    if spatial == "1":
+        assert allu == 2 * warps * (ns_pad // ti) * (ns_pad // shape["tile"])
+        assert 0 < far < allu
+    else:
+        assert far == 0 and allu == 0
+
+
 def test_precision_switch_after_init(orc):
     """A context created in FP64 and switched to mixed by pn_set_params uses
     the mixed records (allocated at pn_init whatever the precision)."""
