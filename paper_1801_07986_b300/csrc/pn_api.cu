@@ -120,7 +120,7 @@ void set_params(pn_ctx *c, const pn_params *p, bool all_physics)
 
 void free_all(pn_ctx *c)
 {
-    void *bufs[] = {c->vp, c->mrec, c->sord, c->drec, c->part, c->blk, c->glob, c->eout, c->flag, c->wcount,
+    void *bufs[] = {c->vp, c->mrec, c->sord, c->bal, c->drec, c->part, c->blk, c->glob, c->eout, c->flag, c->wcount,
                     c->flag_step, c->hx, c->hv, c->hm, c->ha, c->nrec, c->ndrec, c->ncount,
                     c->nflag, c->rk_x, c->rk_v, c->rk_a, c->rk_sx, c->rk_sv, c->jbuf, c->hj0, c->hj1, c->abuf,
                     c->d_clu,
@@ -420,6 +420,9 @@ static pn_status init_common(pn_ctx **out, int nclu, const int64_t *off, const p
     if (const char *sp = std::getenv("PN_SPATIAL"))
         c->spatial = sp[0] != '0';
     c->far_theta = pn::kFarTheta;
+    c->balance = true;          // PN_BALANCE=0: equal unit counts per worker
+    if (const char *bl = std::getenv("PN_BALANCE"))
+        c->balance = bl[0] != '0';
     if (const char *ft = std::getenv("PN_FAR_THETA")) {
         const double v = std::atof(ft);
         if (v >= 0.02 && v <= 10.0)
@@ -462,6 +465,12 @@ static pn_status init_common(pn_ctx **out, int nclu, const int64_t *off, const p
         const int64_t seg = (c->S / (pn::kMixThreads * va[0]) + fs.G) * pn::kMixThreads * va[0];
         if (seg > seg_max)
             seg_max = seg;
+        if (va[2]) {            // packed variants: sizes of the worker-balance scratch
+            if (fs.units > c->bal_units)
+                c->bal_units = fs.units;
+            if (fs.G > c->bal_G)
+                c->bal_G = fs.G;
+        }
     }
     if (e == cudaSuccess)
         e = pn::fused_shape(c, c->fused_P, c->fused_unroll, c->fused_packed, &fs);
@@ -507,6 +516,8 @@ static pn_status init_common(pn_ctx **out, int nclu, const int64_t *off, const p
         {(void **)&c->drec, sizeof(double4_32a) * 4 * (size_t)S},
         // mixed: the spatial order of the packed kernel (sorted records, boxes, sort scratch)
         {(void **)&c->sord, pn::order_buffer_bytes(S)},
+        // and its cost-balanced worker boundaries
+        {(void **)&c->bal, pn::balance_buffer_bytes(S, c->bal_units, c->bal_G)},
         {(void **)&c->part, sizeof(double) * (size_t)part},
         {(void **)&c->blk, sizeof(double) * (size_t)c->blk_len},
         {(void **)&c->glob, sizeof(double) * pn::kGlobVals * (size_t)nclu},

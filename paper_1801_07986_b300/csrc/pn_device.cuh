@@ -69,6 +69,21 @@ __device__ __forceinline__ int cluster_of_block(const int *__restrict__ blk_clu,
     return blk_clu ? blk_clu[b] : 0;
 }
 
+// Cluster of work unit u of the fused pair kernels (units are laid out
+// cluster-major; clu[k].unit0 is cluster k's first).
+__device__ __forceinline__ int cluster_of_unit(const Clu *__restrict__ clu, int nclu, int64_t u)
+{
+    int lo = 0, hi = nclu - 1;
+    while (lo < hi) {                        // last cluster with unit0 <= u
+        const int mid = (lo + hi + 1) >> 1;
+        if (clu[mid].unit0 <= u)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
 // 1/sqrt(s2) in single precision: the PTX approximate reciprocal square root
 // (one MUFU instruction; max relative error about 2^-23), flushing subnormal
 // inputs to zero -- pair distances squared are never subnormal (s2 >= eps^2,

@@ -98,6 +98,7 @@ struct pn_ctx {
     bool near_all;           // every cluster has r_near > 0
     bool spatial;            // packed law-of-cosines kernel on Hilbert-ordered slots
     float far_theta;         // spatial order: far-unit criterion (k_fused_packed)
+    bool balance;            // spatial order: cost-balanced stream-K workers
     unsigned long long *units_cnt;  // spatial order: [0] far warp-units, [1] all warp-units
     pn_params p;
     int device;
@@ -120,6 +121,8 @@ struct pn_ctx {
     double *vp;          // n x 3: velocity at which the force is evaluated
     float4 *mrec;        // mixed records: 5 arrays of S float4
     void *sord;          // mixed: spatial order (pn_order.cu: sorted records, boxes, sort scratch)
+    void *bal;           // mixed: cost-balanced stream-K worker boundaries (pn_order.cu)
+    int64_t bal_units, bal_G;   // largest unit and worker counts of the packed variants
     double4_32a *drec;   // double records: 4 arrays of S double4_32a
     double *part;        // pair partial sums [jsplit][vals][S] (+ fused segments)
     int64_t part_len;    // doubles in `part`
@@ -224,5 +227,9 @@ struct Order {
 size_t order_buffer_bytes(int64_t S);
 Order order_of(pn_ctx *c);
 cudaError_t launch_spatial_order(pn_ctx *c);
+// Cost-balanced worker boundaries of the packed kernel (NP target pairs per
+// thread) on the spatial order: *wb receives the device array wb[0..G].
+size_t balance_buffer_bytes(int64_t S, int64_t units, int64_t G);
+cudaError_t launch_worker_balance(pn_ctx *c, int NP, const int64_t **wb);
 
 }  // namespace pn

@@ -648,19 +648,6 @@ __device__ __forceinline__ void fused_tile(const float4 *__restrict__ sA,
 // (global target block + b) of the segment buffer, which holds
 // (target blocks + G) entries of [value][TI targets]; the gather kernel sums
 // the segments of each target block in block order.
-__device__ __forceinline__ int cluster_of_unit(const Clu *__restrict__ clu, int nclu, int64_t u)
-{
-    int lo = 0, hi = nclu - 1;
-    while (lo < hi) {                        // last cluster with unit0 <= u
-        const int mid = (lo + hi + 1) >> 1;
-        if (clu[mid].unit0 <= u)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
-}
-
 template <int P, int UNROLL>
 __global__ void __launch_bounds__(kMixThreads, P == 4 ? (UNROLL == 3 ? 2 : 3) : (P == 2 ? 5 : 8))
 k_fused_mixed(const float4 *__restrict__ rec, int64_t S, const Clu *__restrict__ clu, int nclu,
@@ -931,7 +918,8 @@ __global__ void __launch_bounds__(kMixThreads, NP == 2 ? 3 : 5)
 k_fused_packed(const float4 *__restrict__ srec, const Clu *__restrict__ clu, int nclu,
                int64_t total_units, int64_t G, int *__restrict__ wcount, int *__restrict__ flag,
                unsigned extra_tx, const float4 *__restrict__ box, float far_theta,
-               unsigned long long *__restrict__ units_cnt, double *__restrict__ part)
+               unsigned long long *__restrict__ units_cnt, const int64_t *__restrict__ wb,
+               double *__restrict__ part)
 {
     constexpr bool LOC = FORM >= 1, SPATIAL = FORM == 2;
     unsigned n_far = 0, n_all = 0;      // this warp's units (form 2)
@@ -958,8 +946,8 @@ k_fused_packed(const float4 *__restrict__ srec, const Clu *__restrict__ clu, int
             }
             break;
         }
-        int64_t u = w * total_units / G;
-        const int64_t u1 = (w + 1) * total_units / G;
+        int64_t u = wb ? wb[w] : w * total_units / G;
+        const int64_t u1 = wb ? wb[w + 1] : (w + 1) * total_units / G;
         if (threadIdx.x == 0 && u < u1) {   // both buffers are free here
             bulk_load(sh[it & 1], srec + unit_source(clu, nclu, u) * RV, tile_bytes<LOC>(),
                       &full[it & 1], extra_tx);
@@ -1088,7 +1076,7 @@ __global__ void __launch_bounds__(kGlueThreads)
 k_fused_gather(const double *__restrict__ part, int64_t S, const Clu *__restrict__ clu,
                const int *__restrict__ blk_clu, int64_t total_units, int64_t G, int tile,
                const float4 *__restrict__ srec, const int *__restrict__ perm,
-               double *__restrict__ p1, double *__restrict__ p2)
+               const int64_t *__restrict__ wb, double *__restrict__ p1, double *__restrict__ p2)
 {
     constexpr int TI = kMixThreads * P;
     const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
@@ -1100,15 +1088,31 @@ k_fused_gather(const double *__restrict__ part, int64_t S, const Clu *__restrict
     const int64_t gtb = t / TI;                                 // global target block
     const int lt = (int)(t - gtb * TI);
     const int64_t U0 = C.unit0 + ib * ntiles, U1 = U0 + ntiles;
-    int64_t b = U0 * G / total_units;
-    while (b + 1 < G && (b + 1) * total_units / G <= U0)
-        ++b;
+    // worker b owns units [bound(b), bound(b + 1)): equal counts, or the
+    // cost-balanced boundaries wb of the spatial order
+    auto bound = [&](int64_t q) { return wb ? wb[q] : q * total_units / G; };
+    int64_t b;
+    if (wb) {                                   // last worker with wb[b] <= U0
+        int64_t lo = 0, hi = G - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (wb[mid] <= U0)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        b = lo;
+    } else {
+        b = U0 * G / total_units;
+        while (b + 1 < G && (b + 1) * total_units / G <= U0)
+            ++b;
+    }
     double acc[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k)
         acc[k] = 0.0;
     for (; b < G; ++b) {
-        const int64_t bu0 = b * total_units / G, bu1 = (b + 1) * total_units / G;
+        const int64_t bu0 = bound(b), bu1 = bound(b + 1);
         if (bu0 >= U1)
             break;
         if (bu1 <= U0 || bu0 == bu1)
@@ -1891,7 +1895,7 @@ static cudaError_t launch_fused_p(pn_ctx *c, const Layout &L, const float4 *rec)
         return e;
     k_fused_gather<P, kFusedVals, 0><<<(unsigned)(c->S / kGlueThreads), kGlueThreads, 0, c->stream>>>(
         c->part + L.seg, c->S, c->d_clu, blk_table(c), c->fused_units, c->fused_G, kMixTile,
-        nullptr, nullptr, c->part + L.p1, c->part + L.p2);
+        nullptr, nullptr, nullptr, c->part + L.p1, c->part + L.p2);
     c->launches += 1;
     return cudaGetLastError();
 }
@@ -1904,13 +1908,13 @@ static cudaError_t launch_fused_p(pn_ctx *c, const Layout &L, const float4 *rec)
 // (boxes and the sorted-to-slot map for form 2), then the gather.
 template <int NP, int UNROLL, int FORM>
 static cudaError_t launch_packed_form(pn_ctx *c, const Layout &L, const float4 *srec,
-                                      const float4 *box, const int *perm)
+                                      const float4 *box, const int *perm, const int64_t *wb)
 {
     cudaEvent_t end = nullptr;
     timing_begin(c, 1, &end);
     k_fused_packed<NP, UNROLL, FORM><<<(unsigned)c->fused_grid, kMixThreads, 0, c->stream>>>(
         srec, c->d_clu, c->nclu, c->fused_units, c->fused_G, c->wcount, c->flag, c->inject_tx,
-        box, c->far_theta, c->units_cnt, c->part + L.seg);
+        box, c->far_theta, c->units_cnt, wb, c->part + L.seg);
     c->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (end)
@@ -1920,7 +1924,7 @@ static cudaError_t launch_packed_form(pn_ctx *c, const Layout &L, const float4 *
     k_fused_gather<2 * NP, kPackSums, pack_vals<(FORM >= 1)>()>
         <<<(unsigned)(c->S / kGlueThreads), kGlueThreads, 0, c->stream>>>(
             c->part + L.seg, c->S, c->d_clu, blk_table(c), c->fused_units, c->fused_G, kPackTile,
-            srec, perm, c->part + L.p1, c->part + L.p2);
+            srec, perm, wb, c->part + L.p1, c->part + L.p2);
     c->launches += 1;
     return cudaGetLastError();
 }
@@ -1938,19 +1942,22 @@ static cudaError_t launch_packed_u(pn_ctx *c, const Layout &L, const float4 *rec
     const float4 *srec = c->mrec + 5 * c->S;
     if (rec == c->mrec && packed_loc(c)) {
         if (!c->spatial)
-            return launch_packed_form<NP, UNROLL, 1>(c, L, srec, nullptr, nullptr);
-        const cudaError_t e = launch_spatial_order(c);
+            return launch_packed_form<NP, UNROLL, 1>(c, L, srec, nullptr, nullptr, nullptr);
+        cudaError_t e = launch_spatial_order(c);
+        const int64_t *wb = nullptr;
+        if (e == cudaSuccess && c->balance)
+            e = launch_worker_balance(c, NP, &wb);
         if (e != cudaSuccess)
             return e;
         const Order o = order_of(c);
-        return launch_packed_form<NP, UNROLL, 2>(c, L, o.ssrec, o.box, o.perm);
+        return launch_packed_form<NP, UNROLL, 2>(c, L, o.ssrec, o.box, o.perm, wb);
     }
     if (rec != c->mrec) {       // caller-built records: stage them first
         k_stage_sources<<<(unsigned)(c->S / kGlueThreads), kGlueThreads, 0, c->stream>>>(
             c->S, rec, c->mrec + 5 * c->S);
         c->launches += 1;
     }
-    return launch_packed_form<NP, UNROLL, 0>(c, L, srec, nullptr, nullptr);
+    return launch_packed_form<NP, UNROLL, 0>(c, L, srec, nullptr, nullptr, nullptr);
 }
 
 // Fused-kernel variants: scalar (targets per thread 1, 2, 4) or packed

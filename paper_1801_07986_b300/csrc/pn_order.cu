@@ -26,6 +26,21 @@
 //
 // Any permutation gives the same sums up to rounding; the order only decides
 // how many units qualify for the cheaper pair body.
+//
+// Cost-balanced stream-K workers.  On the spatial order a unit costs more
+// when it is near (the full separation) than when it is far, and the near
+// units gather in the dense core, so workers of equal unit counts differ in
+// cost and the last ones to finish leave the GPU partly idle.  After the
+// permutation, every unit gets the FP32-pipe operations per pair of the body
+// its block will run (kOpsNear when any warp of the target block is near or
+// the unit holds self pairs -- the block's warps meet at every tile -- else
+// kOpsFar), and the worker boundaries are cut at equal shares of the total:
+//   k_unit_cost      one block per target-block row: costs, in-row prefix,
+//                    row total;
+//   k_row_scan       prefix over the rows;
+//   k_worker_bounds  worker w starts at the first unit whose prefix reaches
+//                    w total / G (binary search).
+// The boundaries depend on the positions alone, so results stay reproducible.
 #include "pn_device.cuh"
 
 namespace pn {
@@ -273,6 +288,140 @@ k_sort_permute(const float4 *__restrict__ srec, const int *__restrict__ perm,
     }
 }
 
+constexpr int kOpsFar = 40, kOpsNear = 46;     // FP32-pipe operations per pair of the two bodies
+constexpr int kRowThreads = 256;
+constexpr int kScanThreads = 1024;
+
+// Global target-block row r (slots [r TI, (r + 1) TI)) of the packed kernel
+// with NP target pairs per thread: unit costs, their exclusive prefix within
+// the row (prefix[u]) and the row total (rowsum[r]).
+template <int NP>
+__global__ void __launch_bounds__(kRowThreads)
+k_unit_cost(const Clu *__restrict__ clu, const int *__restrict__ blk_clu,
+            const float4 *__restrict__ box, float theta, int *__restrict__ prefix,
+            int *__restrict__ rowsum)
+{
+    constexpr int TI = 2 * NP * kMixThreads, NW = kMixThreads / 32, WG = 64 * NP;
+    __shared__ float4 wlo[NW], whi[NW];
+    __shared__ int part[kRowThreads];
+    const int64_t r = blockIdx.x;
+    const Clu C = clu[cluster_of_block(blk_clu, r * TI / kGlueThreads)];
+    const int64_t ntiles = C.ns_pad / kPackTile;
+    const int64_t u0 = C.unit0 + (r * TI - C.slot0) / TI * ntiles;
+    if (threadIdx.x < NW) {             // each warp's target box (union of its tiles' boxes)
+        const float4 *bb = box + 2 * ((r * TI + WG * threadIdx.x) / kPackTile);
+        float4 lo = bb[0], hi = bb[1];
+        for (int q = 1; q < WG / kPackTile; ++q) {
+            const float4 l = bb[2 * q], h = bb[2 * q + 1];
+            lo = make_float4(fminf(lo.x, l.x), fminf(lo.y, l.y), fminf(lo.z, l.z), 0.0f);
+            hi = make_float4(fmaxf(hi.x, h.x), fmaxf(hi.y, h.y), fmaxf(hi.z, h.z), fmaxf(hi.w, h.w));
+        }
+        wlo[threadIdx.x] = lo;
+        whi[threadIdx.x] = hi;
+    }
+    __syncthreads();
+    // thread k: tiles [k ch, (k + 1) ch) of the row
+    const int64_t ch = (ntiles + kRowThreads - 1) / kRowThreads;
+    const int64_t q0 = threadIdx.x * ch, q1 = q0 + ch < ntiles ? q0 + ch : ntiles;
+    auto cost = [&](int64_t q) {
+        const int64_t j0 = C.slot0 + q * kPackTile;
+        if (j0 < r * TI + TI && r * TI < j0 + kPackTile)
+            return kOpsNear;            // self pairs: full separation
+        const float4 l = box[2 * (j0 / kPackTile)], h = box[2 * (j0 / kPackTile) + 1];
+        for (int g = 0; g < NW; ++g) {
+            const float4 bl = wlo[g], bh = whi[g];
+            const float gx = fmaxf(0.0f, fmaxf(l.x - bh.x, bl.x - h.x));
+            const float gy = fmaxf(0.0f, fmaxf(l.y - bh.y, bl.y - h.y));
+            const float gz = fmaxf(0.0f, fmaxf(l.z - bh.z, bl.z - h.z));
+            const float lim = theta * (bh.w + h.w);
+            if (!(gx * gx + gy * gy + gz * gz >= lim * lim))
+                return kOpsNear;
+        }
+        return kOpsFar;
+    };
+    int s = 0;
+    for (int64_t q = q0; q < q1; ++q)
+        s += cost(q);
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int k = 0; k < kRowThreads; ++k) {
+            const int c = part[k];
+            part[k] = run;
+            run += c;
+        }
+        rowsum[r] = run;
+    }
+    __syncthreads();
+    int run = part[threadIdx.x];
+    for (int64_t q = q0; q < q1; ++q) {
+        prefix[u0 + q] = run;
+        run += cost(q);
+    }
+}
+
+// Exclusive prefix of the row totals (one block): rowbase[r], rowbase[R] = total.
+__global__ void __launch_bounds__(kScanThreads)
+k_row_scan(int64_t R, const int *__restrict__ rowsum, int64_t *__restrict__ rowbase)
+{
+    __shared__ int64_t part[kScanThreads];
+    const int64_t ch = (R + kScanThreads - 1) / kScanThreads;
+    const int64_t r0 = threadIdx.x * ch, r1 = r0 + ch < R ? r0 + ch : R;
+    int64_t s = 0;
+    for (int64_t r = r0; r < r1; ++r)
+        s += rowsum[r];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t run = 0;
+        for (int k = 0; k < kScanThreads; ++k) {
+            const int64_t c = part[k];
+            part[k] = run;
+            run += c;
+        }
+        rowbase[R] = run;
+    }
+    __syncthreads();
+    int64_t run = part[threadIdx.x];
+    for (int64_t r = r0; r < r1; ++r) {
+        rowbase[r] = run;
+        run += rowsum[r];
+    }
+}
+
+// Worker boundaries wb[0..G]: wb[w] = first unit u with cost prefix
+// rowbase[row(u)] + prefix[u] >= w total / G (wb[G] = T).
+template <int NP>
+__global__ void __launch_bounds__(kGlueThreads)
+k_worker_bounds(const Clu *__restrict__ clu, int nclu, int64_t T, int64_t G, int64_t R,
+                const int *__restrict__ prefix, const int64_t *__restrict__ rowbase,
+                int64_t *__restrict__ wb)
+{
+    constexpr int TI = 2 * NP * kMixThreads;
+    const int64_t w = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
+    if (w > G)
+        return;
+    const int64_t total = rowbase[R];
+    const int64_t want = w * total / G;       // total < 2^40, w <= 2^20
+    auto cum = [&](int64_t u) -> int64_t {
+        if (u >= T)
+            return total;
+        const Clu C = clu[cluster_of_unit(clu, nclu, u)];
+        const int64_t ntiles = C.ns_pad / kPackTile;
+        return rowbase[C.slot0 / TI + (u - C.unit0) / ntiles] + prefix[u];
+    };
+    int64_t lo = 0, hi = T;                   // first u in [0, T] with cum(u) >= want
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (cum(mid) >= want)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    wb[w] = w == G ? T : lo;
+}
+
 size_t order_buffer_bytes(int64_t S)
 {
     return sizeof(float4) * (size_t)(kFwdVals * S + 2 * (S / kPackTile)) +
@@ -296,6 +445,42 @@ Order order_of(pn_ctx *c)
     o.hist = reinterpret_cast<int *>(p);
     o.perm = o.vals + S;          // the last pass (2) writes the second half
     return o;
+}
+
+size_t balance_buffer_bytes(int64_t S, int64_t units, int64_t G)
+{
+    const int64_t R = S / kGlueThreads;       // target-block rows, at most (TI >= 256)
+    return sizeof(int64_t) * (size_t)(R + 1 + G + 1) + sizeof(int) * (size_t)(R + units);
+}
+
+cudaError_t launch_worker_balance(pn_ctx *c, int NP, const int64_t **wb_out)
+{
+    const int64_t S = c->S, TI = 2 * NP * kMixThreads, R = S / TI;
+    const int64_t T = c->fused_units, G = c->fused_G;
+    const int64_t Rmax = S / kGlueThreads;
+    int64_t *rowbase = reinterpret_cast<int64_t *>(c->bal);
+    int64_t *wb = rowbase + Rmax + 1;
+    int *rowsum = reinterpret_cast<int *>(wb + c->bal_G + 1);
+    int *prefix = rowsum + Rmax;
+    const int *bc = c->nclu > 1 ? c->blk_clu : nullptr;
+    const Order o = order_of(c);
+    if (NP == 2)
+        k_unit_cost<2><<<(unsigned)R, kRowThreads, 0, c->stream>>>(c->d_clu, bc, o.box, c->far_theta,
+                                                                   prefix, rowsum);
+    else
+        k_unit_cost<1><<<(unsigned)R, kRowThreads, 0, c->stream>>>(c->d_clu, bc, o.box, c->far_theta,
+                                                                   prefix, rowsum);
+    k_row_scan<<<1, kScanThreads, 0, c->stream>>>(R, rowsum, rowbase);
+    const unsigned nb = (unsigned)((G + 1 + kGlueThreads - 1) / kGlueThreads);
+    if (NP == 2)
+        k_worker_bounds<2><<<nb, kGlueThreads, 0, c->stream>>>(c->d_clu, c->nclu, T, G, R, prefix,
+                                                               rowbase, wb);
+    else
+        k_worker_bounds<1><<<nb, kGlueThreads, 0, c->stream>>>(c->d_clu, c->nclu, T, G, R, prefix,
+                                                               rowbase, wb);
+    c->launches += 3;
+    *wb_out = wb;
+    return cudaGetLastError();
 }
 
 // Hilbert order of the current staged records (c->mrec + 5 S, written by the

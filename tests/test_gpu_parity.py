@@ -246,13 +246,15 @@ def test_packed_forms_match_oracle(orc, r_near):
     assert np.median(err) <= MIX_MED and err.max() <= MIX_MAX, (np.median(err), err.max())
 
 
-@pytest.mark.parametrize("spatial", ["1", "0"])
-def test_spatial_order_with_tight_pairs(orc, monkeypatch, spatial):
-    """The packed kernel on Morton-ordered slots (PN_SPATIAL=1, the default)
-    or in slot order: tight pairs (separations 1e-4 .. 1e-3) planted at 1 to 6
-    from the hole, where the high parts alone would lose the separation, and
-    stars near the hole; every body against the oracle."""
+@pytest.mark.parametrize("spatial,balance", [("1", "1"), ("1", "0"), ("0", "1")])
+def test_spatial_order_with_tight_pairs(orc, monkeypatch, spatial, balance):
+    """The packed kernel on Hilbert-ordered slots (PN_SPATIAL=1, the default
+    for large systems; with cost-balanced workers or, PN_BALANCE=0, equal
+    unit counts) or in slot order: tight pairs (separations 1e-4 .. 1e-3)
+    planted at 1 to 6 from the hole, where the high parts alone would lose the
+    separation, and stars near the hole; every body against the oracle."""
     monkeypatch.setenv("PN_SPATIAL", spatial)
+    monkeypatch.setenv("PN_BALANCE", balance)
     n = 6 * 1024 + 77
     x, v, m = cluster(n, 0.3, 4444)
     rng = np.random.default_rng(44)
