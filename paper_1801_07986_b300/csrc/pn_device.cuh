@@ -12,16 +12,16 @@
 namespace pn {
 
 // Deterministic block sum of K doubles per thread (fixed tree, blockDim =
-// kGlueThreads); thread 0 ends with the totals in sh[k][0].
-template <int K>
-__device__ __forceinline__ void block_sum(double (&val)[K], double (*sh)[kGlueThreads])
+// BT); thread 0 ends with the totals in sh[k][0].
+template <int K, int BT = kGlueThreads>
+__device__ __forceinline__ void block_sum(double (&val)[K], double (*sh)[BT])
 {
     const int t = threadIdx.x;
 #pragma unroll
     for (int k = 0; k < K; ++k)
         sh[k][t] = val[k];
     __syncthreads();
-    for (int s = kGlueThreads / 2; s > 0; s >>= 1) {
+    for (int s = BT / 2; s > 0; s >>= 1) {
         if (t < s) {
 #pragma unroll
             for (int k = 0; k < K; ++k)

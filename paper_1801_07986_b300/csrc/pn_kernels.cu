@@ -1070,7 +1070,9 @@ k_stage_sources(int64_t S, const float4 *__restrict__ rec, float4 *__restrict__ 
 // split: p1[k][t] (k < kP1Vals), p2[k][t] (k < kP2Vals).  NV values per
 // segment (fewer than kFusedVals: the packed kernel's, without Wr), RV float4
 // per staged record; with `perm` the kernel ran on the spatial order and
-// position t belongs to slot perm[t].
+// position t belongs to slot perm[t].  blockIdx.y splits a star's values
+// over three threads: 0 the pass-1 values (and Wr), 1 and 2 five pass-2
+// values each.
 template <int P, int NV, int RV>
 __global__ void __launch_bounds__(kGlueThreads)
 k_fused_gather(const double *__restrict__ part, int64_t S, const Clu *__restrict__ clu,
@@ -1107,9 +1109,14 @@ k_fused_gather(const double *__restrict__ part, int64_t S, const Clu *__restrict
         while (b + 1 < G && (b + 1) * total_units / G <= U0)
             ++b;
     }
-    double acc[NV];
+    constexpr int o2 = NV - kP2Vals;     // first pass-2 value in the segment
+    constexpr int NG = o2 > kP2Vals / 2 ? o2 : kP2Vals / 2;   // values per thread, at most
+    const int g = blockIdx.y;
+    const int k0 = g == 0 ? 0 : o2 + (g - 1) * (kP2Vals / 2);
+    const int nk = g == 0 ? o2 : kP2Vals / 2;
+    double acc[NG];
 #pragma unroll
-    for (int k = 0; k < NV; ++k)
+    for (int k = 0; k < NG; ++k)
         acc[k] = 0.0;
     for (; b < G; ++b) {
         const int64_t bu0 = bound(b), bu1 = bound(b + 1);
@@ -1117,16 +1124,24 @@ k_fused_gather(const double *__restrict__ part, int64_t S, const Clu *__restrict
             break;
         if (bu1 <= U0 || bu0 == bu1)
             continue;
-        const double *in = part + (gtb + b) * (int64_t)(NV * TI);
+        const double *in = part + (gtb + b) * (int64_t)(NV * TI) + (int64_t)k0 * TI + lt;
 #pragma unroll
-        for (int k = 0; k < NV; ++k)
-            acc[k] += in[k * TI + lt];
+        for (int k = 0; k < NG; ++k)
+            if (k < nk)
+                acc[k] += in[k * TI];
     }
-    constexpr int o2 = NV - kP2Vals;     // first pass-2 value in the segment
     const int64_t ts = perm ? (int64_t)perm[t] : t;
+    if (g > 0) {
 #pragma unroll
-    for (int k = 0; k < o2; ++k)
-        p1[(int64_t)k * S + ts] = acc[k];
+        for (int k = 0; k < NG; ++k)
+            if (k < nk)
+                p2[(int64_t)(k0 - o2 + k) * S + ts] = acc[k];
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < NG; ++k)
+        if (k < o2)
+            p1[(int64_t)k * S + ts] = acc[k];
     if (o2 < kP1Vals) {
         // Wr from the identity R_i^2 - R_j^2 = 2 d_i.x_ij - (r_ij^2 - eps^2):
         // sum_j m_j (R_i^2 - R_j^2)/r_ij^3 = 2 d_i.N - U + eps^2 Z, so
@@ -1139,9 +1154,6 @@ k_fused_gather(const double *__restrict__ part, int64_t S, const Clu *__restrict
         p1[(int64_t)5 * S + ts] =
             (R2 - C.eps2) * acc[4] - 2.0 * (d0 * acc[0] + d1 * acc[1] + d2 * acc[2]) + acc[3];
     }
-#pragma unroll
-    for (int k = 0; k < kP2Vals; ++k)
-        p2[(int64_t)k * S + ts] = acc[o2 + k];
 }
 
 // ------------------------------------------------ pair kernels: double --
@@ -1338,6 +1350,12 @@ k_energy_pairs(const double4_32a *__restrict__ rec, int64_t S, const Clu *__rest
 // with 1/s - 1/R_i = q / (s R_i (R_i + s)) and
 // 1/R_i^3 - 1/s^3 = -(1/s - 1/R_i)(1/R_i^2 + 1/(R_i s) + 1/s^2).
 // Accumulators: P (3) = sum m_j [...], Ee (3) = sum w_j (1/s - 1/R_i).
+// The quotient by R_i + s: correctly rounded in double, by the approximate
+// reciprocal (__fdividef, 2 ulp) in single precision, whose sums carry FP32
+// rounding anyway.
+__device__ __forceinline__ double near_div(double a, double b) { return a / b; }
+__device__ __forceinline__ float near_div(float a, float b) { return __fdividef(a, b); }
+
 template <typename R_t>
 struct NearMath {
     __device__ __forceinline__ static void pair(R_t dx, R_t dy, R_t dz, R_t s2, R_t is,
@@ -1350,7 +1368,7 @@ struct NearMath {
         const R_t is3 = is2 * is;
         const R_t sd = s2 * is;                                  // s
         const R_t q = (R_t)2 * (dj[0] * di[0] + dj[1] * di[1] + dj[2] * di[2]) - Rj2e;
-        const R_t dis = q * is * iR / (Ri + sd);                 // 1/s - 1/R_i
+        const R_t dis = near_div(q * is * iR, Ri + sd);          // 1/s - 1/R_i
         const R_t d3 = -dis * (iR * iR + iR * is + is2);         // 1/R_i^3 - 1/s^3
         const R_t ca = mj * A;
         const R_t cb = mj * B * q;
@@ -1409,8 +1427,9 @@ k_near_mixed(const float4 *__restrict__ rec, const float4 *__restrict__ nrec,
 #pragma unroll
             for (int k = 0; k < kNearVals; ++k)
                 acc[p][k] = 0.0f;
+        const int qn = nn - tile * kNearTile < kNearTile ? nn - tile * kNearTile : kNearTile;
 #pragma unroll 1
-        for (int q = 0; q < kNearTile; ++q) {
+        for (int q = 0; q < qn; ++q) {      // the tile's near sources (padding skipped)
             const float4 A = sh[0][q], B = sh[1][q], Cn = sh[2][q], D = sh[3][q];
             const float dj[3] = {A.x, A.y, A.z};
 #pragma unroll
@@ -1473,8 +1492,9 @@ k_near_f64(const double4_32a *__restrict__ rec, const double4_32a *__restrict__ 
                 sh[k][q] = nrec[k * NC + j0 + q];
         }
         __syncthreads();
+        const int qn = nn - tile * TILE < TILE ? nn - tile * TILE : TILE;
 #pragma unroll 1
-        for (int q = 0; q < TILE; ++q) {
+        for (int q = 0; q < qn; ++q) {      // the tile's near sources (padding skipped)
             const double4_32a A = sh[0][q], B = sh[1][q], Cn = sh[2][q];
             const double dj[3] = {A.x, A.y, A.z};
             const double dx = di[0] - A.x, dy = di[1] - A.y, dz = di[2] - A.z;
@@ -1498,8 +1518,9 @@ k_near_f64(const double4_32a *__restrict__ rec, const double4_32a *__restrict__ 
 // Star i = t + 1 (double precision throughout): sums the partials of every
 // pass for its slot and assembles its acceleration and its term of the
 // hole's acceleration with star_eqs (the formulas are stated there); the
-// block's sum of the hole terms goes to blk (deterministic tree).
-__global__ void __launch_bounds__(kGlueThreads)
+// block's sum of the hole terms goes to blk (deterministic tree), one entry
+// per kEpiThreads slots.
+__global__ void __launch_bounds__(kEpiThreads)
 k_epilogue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_clu,
            const double *__restrict__ x, const double *__restrict__ vel,
            const double *__restrict__ m, const double *__restrict__ p1, int js1,
@@ -1508,9 +1529,9 @@ k_epilogue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
            double *__restrict__ a, double *__restrict__ v, double h, int *flag,
            unsigned long long *flag_step, unsigned long long step, double *__restrict__ blk)
 {
-    __shared__ double sh[3][kGlueThreads];
-    const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
-    const int k_clu = cluster_of_block(blk_clu, blockIdx.x);
+    __shared__ double sh[3][kEpiThreads];
+    const int64_t t = (int64_t)blockIdx.x * kEpiThreads + threadIdx.x;
+    const int k_clu = cluster_of_block(blk_clu, (int64_t)blockIdx.x * kEpiThreads / kGlueThreads);
     const Clu Cl = clu[k_clu];
     const double *glob = globs + (int64_t)k_clu * kGlobVals;
     const int64_t lt = t - Cl.slot0;
@@ -1564,7 +1585,7 @@ k_epilogue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
                 v[3 * i + k] = fma(h, ai[k], v[3 * i + k]);
         }
     }
-    block_sum<3>(bh, sh);
+    block_sum<3, kEpiThreads>(bh, sh);
     if (threadIdx.x < 3)
         blk[(int64_t)blockIdx.x * 3 + threadIdx.x] = sh[threadIdx.x][0];
 }
@@ -1578,7 +1599,7 @@ k_hole(const Clu *__restrict__ clu, const double *__restrict__ blk,
 {
     __shared__ double sh[3][kGlueThreads];
     const Clu C = clu[blockIdx.x];
-    sum_blocks<3>(blk + (C.slot0 / kGlueThreads) * 3, C.ns_pad / kGlueThreads, sh);
+    sum_blocks<3>(blk + (C.slot0 / kEpiThreads) * 3, C.ns_pad / kEpiThreads, sh);
     if (threadIdx.x == 0) {
         const double *glob = globs + (int64_t)blockIdx.x * kGlobVals;
         const int64_t hb = C.body0;
@@ -1893,7 +1914,7 @@ static cudaError_t launch_fused_p(pn_ctx *c, const Layout &L, const float4 *rec)
         cudaEventRecord(end, c->stream);
     if (e != cudaSuccess)
         return e;
-    k_fused_gather<P, kFusedVals, 0><<<(unsigned)(c->S / kGlueThreads), kGlueThreads, 0, c->stream>>>(
+    k_fused_gather<P, kFusedVals, 0><<<dim3((unsigned)(c->S / kGlueThreads), 3), kGlueThreads, 0, c->stream>>>(
         c->part + L.seg, c->S, c->d_clu, blk_table(c), c->fused_units, c->fused_G, kMixTile,
         nullptr, nullptr, nullptr, c->part + L.p1, c->part + L.p2);
     c->launches += 1;
@@ -1922,7 +1943,7 @@ static cudaError_t launch_packed_form(pn_ctx *c, const Layout &L, const float4 *
     if (e != cudaSuccess)
         return e;
     k_fused_gather<2 * NP, kPackSums, pack_vals<(FORM >= 1)>()>
-        <<<(unsigned)(c->S / kGlueThreads), kGlueThreads, 0, c->stream>>>(
+        <<<dim3((unsigned)(c->S / kGlueThreads), 3), kGlueThreads, 0, c->stream>>>(
             c->part + L.seg, c->S, c->d_clu, blk_table(c), c->fused_units, c->fused_G, kPackTile,
             srec, perm, wb, c->part + L.p1, c->part + L.p2);
     c->launches += 1;
@@ -2091,9 +2112,9 @@ cudaError_t launch_epilogue(pn_ctx *c, const double *x, const double *vel, const
                             double *a, double *v, double h, unsigned long long step)
 {
     const Layout L = layout(c);
-    const int64_t nb = c->S / kGlueThreads;
+    const int64_t nb = c->S / kEpiThreads;
     const double *pnear = c->any_near ? c->part + L.near : nullptr;
-    k_epilogue<<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
+    k_epilogue<<<(unsigned)nb, kEpiThreads, 0, c->stream>>>(
         c->S, c->d_clu, blk_table(c), x, vel, m, c->part + L.p1, L.js, c->part + L.p2, L.js,
         pnear, c->nflag, c->glob, a, v, h, c->flag, c->flag_step, step, c->blk);
     c->launches += 1;
