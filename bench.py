@@ -291,6 +291,8 @@ def run_native(args, w):
 
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    # the state the timed steps start from (the end-to-end run repeats them)
+    start_state = None if args.no_e2e else (X.cpu().numpy(), V.cpu().numpy(), A.cpu().numpy())
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
@@ -378,15 +380,17 @@ def run_native(args, w):
         "launch_shape": launch,
     }
 
-    # end to end through the host-array entry point, copies inside the timing
+    # end to end through the host-array entry point, copies inside the timing:
+    # the first e2e_steps of the timed run again, from the same state, so that
+    # they compare with the device-timed ms of those steps
     if not args.no_e2e:
-        xh = torch.tensor(x).pin_memory().numpy()
-        vh = torch.tensor(v).pin_memory().numpy()
-        mh = torch.tensor(m).pin_memory().numpy()
-        ah = torch.empty((w.n, 3), dtype=torch.float64).pin_memory().numpy()
-        ah[:] = A.cpu().numpy()
         e2e_steps = max(3, min(steps, 50))
-        pn.pn_step_host(ctx, xh, vh, mh, ah, w.dt, 1)
+        dev_ms = float(sum(a.elapsed_time(b) for a, b in zip(ev0[:e2e_steps], ev1[:e2e_steps])))
+        pin = lambda a: torch.tensor(a).pin_memory().numpy()
+        xh, vh, mh = pin(x), pin(v), pin(m)
+        ah = pin(A.cpu().numpy())
+        pn.pn_step_host(ctx, xh, vh, mh, ah, w.dt, 1)     # warm-up of the host path
+        xh[:], vh[:], ah[:] = start_state
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         tot = 0.0
@@ -399,7 +403,10 @@ def run_native(args, w):
             tot += e0.elapsed_time(e1)
         line["e2e"] = {"value": float(w.n) * (w.n - 1) * e2e_steps / (tot * 1e-3),
                        "unit": "interactions/s", "h2d_bytes_per_step": 80 * w.n,
-                       "d2h_bytes_per_step": 72 * w.n, "steps": e2e_steps}
+                       "d2h_bytes_per_step": 72 * w.n, "steps": e2e_steps,
+                       "device_value_same_steps": float(w.n) * (w.n - 1) * e2e_steps
+                       / (dev_ms * 1e-3),
+                       "steps_note": "the first steps of the timed run, again from its start state"}
 
     # the same workload on the FP64 path (a few steps) for the mixed/FP64 ratio
     if args.precision == "mixed" and not args.no_fp64_compare:

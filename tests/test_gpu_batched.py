@@ -50,9 +50,14 @@ def oracle_accels(orc, x, v, m, off, cs, es):
             for a, b, c, e in zip(off[:-1], off[1:], cs, es)]
 
 
-@pytest.mark.parametrize("precision,pair_kernel",
-                         [("fp64", "two_pass"), ("mixed", "fused"), ("mixed", "two_pass")])
-def test_batched_accel_matches_oracle_per_cluster(orc, precision, pair_kernel):
+@pytest.mark.parametrize("precision,pair_kernel,spatial",
+                         [("fp64", "two_pass", "0"), ("mixed", "fused", "0"),
+                          ("mixed", "fused", "1"), ("mixed", "two_pass", "0")])
+def test_batched_accel_matches_oracle_per_cluster(orc, monkeypatch, precision, pair_kernel,
+                                                  spatial):
+    """spatial = 1: the packed kernel on the Hilbert order of every cluster
+    (sorted within each cluster's slot range) with cost-balanced workers."""
+    monkeypatch.setenv("PN_SPATIAL", spatial)
     x, v, m, off, cs, es = batch()
     ctx = pn.pn_init_batched(off, c=cs, eps=es, precision=precision, pair_kernel=pair_kernel,
                              device=0)
