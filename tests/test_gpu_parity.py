@@ -363,9 +363,14 @@ def test_plummer128k_newtonian_momentum_balance():
     assert np.all(np.abs(f) <= 1e-6 * scale)
 
 
-@pytest.mark.parametrize("precision,pair_kernel",
-                         [("fp64", "two_pass"), ("mixed", "fused"), ("mixed", "two_pass")])
-def test_deterministic(precision, pair_kernel):
+@pytest.mark.parametrize("precision,pair_kernel,spatial",
+                         [("fp64", "two_pass", "0"), ("mixed", "fused", "0"),
+                          ("mixed", "fused", "1"), ("mixed", "two_pass", "0")])
+def test_deterministic(monkeypatch, precision, pair_kernel, spatial):
+    """Two contexts give bitwise equal accelerations; with the spatial order
+    (sort, permutation and balanced worker boundaries decided by the
+    positions alone) as without."""
+    monkeypatch.setenv("PN_SPATIAL", spatial)
     x, v, m = make_cluster(3000, 0.1, 61)
     a1 = gpu_accel(x, v, m, precision, c=30.0, eps=1e-4, pair_kernel=pair_kernel)
     a2 = gpu_accel(x, v, m, precision, c=30.0, eps=1e-4, pair_kernel=pair_kernel)
