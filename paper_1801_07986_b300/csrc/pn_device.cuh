@@ -278,6 +278,24 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
+// Waits for the barrier's phase `parity` until %globaltimer passes t_end
+// (checked every 256 polls); false if it did not complete by then.
+__device__ __forceinline__ bool mbar_wait_until(uint64_t *bar, unsigned parity,
+                                                unsigned long long t_end)
+{
+    const uint32_t a = smem_addr(bar);
+    for (unsigned i = 0;; ++i) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done) : "r"(a), "r"(parity) : "memory");
+        if (done)
+            return true;
+        if ((i & 255) == 0 && global_ns() > t_end)
+            return false;
+    }
+}
+
 // Waits for the barrier's phase `parity` to complete; false once kWaitNs
 // have passed (checked every 256 polls).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)

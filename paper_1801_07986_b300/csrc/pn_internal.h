@@ -19,6 +19,8 @@ constexpr int kPackVals = 9;       // packed adjoint sweeps: float4 per staged s
 constexpr int kFwdVals = 8;        // packed fused kernel: float4 per staged source record
 constexpr int kPackFlushTiles = 8; // packed fused kernel: tiles per single-precision partial
 constexpr int kPackWorkersMax = 4;  // packed fused kernel: stream-K workers per resident block (max)
+constexpr int kPackStages = 6;     // packed fused kernel: one-tile shared buffers
+constexpr int kPackRound = 3;      // packed fused kernel: tiles between block barriers (at most)
 // Spatial order of the packed kernel by default from this many target-source
 // slot pairs per evaluation (sum over clusters of ns_pad^2) on.
 constexpr double kSpatialMinPairs = 4294967296.0;

@@ -924,12 +924,14 @@ k_fused_packed(const float4 *__restrict__ srec, const Clu *__restrict__ clu, int
     constexpr bool LOC = FORM >= 1, SPATIAL = FORM == 2;
     unsigned n_far = 0, n_all = 0;      // this warp's units (form 2)
     constexpr int P = 2 * NP, TI = kMixThreads * P, RV = pack_vals<LOC>();
-    __shared__ __align__(128) float4 sh[2][kPackTile][RV];
-    __shared__ __align__(8) uint64_t full[2];
+    constexpr int ST = kPackStages;
+    static_assert(kPackRound <= ST / 2, "a round's buffers are refilled while the next round's are read");
+    __shared__ __align__(128) float4 sh[ST][kPackTile][RV];
+    __shared__ __align__(8) uint64_t full[ST];
     __shared__ int s_w;
     if (threadIdx.x == 0) {
-        mbar_init(&full[0], 1);
-        mbar_init(&full[1], 1);
+        for (int q = 0; q < ST; ++q)
+            mbar_init(&full[q], 1);
         mbar_init_fence();
     }
     unsigned it = 0;                    // tiles this block has consumed
@@ -948,13 +950,10 @@ k_fused_packed(const float4 *__restrict__ srec, const Clu *__restrict__ clu, int
         }
         int64_t u = wb ? wb[w] : w * total_units / G;
         const int64_t u1 = wb ? wb[w + 1] : (w + 1) * total_units / G;
-        if (threadIdx.x == 0 && u < u1) {   // both buffers are free here
-            bulk_load(sh[it & 1], srec + unit_source(clu, nclu, u) * RV, tile_bytes<LOC>(),
-                      &full[it & 1], extra_tx);
-            if (u + 1 < u1)
-                bulk_load(sh[(it + 1) & 1], srec + unit_source(clu, nclu, u + 1) * RV,
-                          tile_bytes<LOC>(), &full[(it + 1) & 1], extra_tx);
-        }
+        if (threadIdx.x == 0)               // every buffer is free here
+            for (int q = 0; q < ST && u + q < u1; ++q)
+                bulk_load(sh[(it + q) % ST], srec + unit_source(clu, nclu, u + q) * RV,
+                          tile_bytes<LOC>(), &full[(it + q) % ST], extra_tx);
         while (u < u1) {
             const Clu C = clu[cluster_of_unit(clu, nclu, u)];
             const int64_t ntiles = C.ns_pad / kPackTile;
@@ -1004,53 +1003,69 @@ k_fused_packed(const float4 *__restrict__ srec, const Clu *__restrict__ clu, int
 #pragma unroll
                 for (int k = 0; k < kPackSums; ++k)
                     acc[pp][k] = make_float2(0.0f, 0.0f);
-            for (; u < uend; ++u, ++it) {
-                const int64_t j0 = C.slot0 + (u - ub) * kPackTile;
-                const int b = it & 1;
-                const bool ok = mbar_wait(&full[b], (it >> 1) & 1);
-                const bool diag = (j0 < t0 + TI) && (t0 < j0 + kPackTile);
-                bool far = false;
-                if (SPATIAL && !diag) {
-                    const float4 l = box[2 * (j0 / kPackTile)], h = box[2 * (j0 / kPackTile) + 1];
-                    const float gx = fmaxf(0.0f, fmaxf(l.x - bhi.x, blo.x - h.x));
-                    const float gy = fmaxf(0.0f, fmaxf(l.y - bhi.y, blo.y - h.y));
-                    const float gz = fmaxf(0.0f, fmaxf(l.z - bhi.z, blo.z - h.z));
-                    const float lim = far_theta * (bhi.w + h.w);
-                    far = gx * gx + gy * gy + gz * gz >= lim * lim;
-                }
-                if (SPATIAL) {
-                    n_far += far ? 1u : 0u;
-                    n_all += 1u;
-                }
-                if (diag)
-                    packed_tile<NP, UNROLL, true, LOC, false>(sh[b], j0, t0, tg, eps2, acc);
-                else if (SPATIAL && far)
-                    packed_tile<NP, UNROLL, false, LOC, true>(sh[b], j0, t0, tg, eps2, acc);
-                else
-                    packed_tile<NP, UNROLL, false, LOC, false>(sh[b], j0, t0, tg, eps2, acc);
-                if (((u - ub + 1) % kPackFlushTiles) == 0 || u + 1 == uend) {
+            // rounds of up to kPackRound tiles of this target block between
+            // block barriers; tile it goes to buffer it % ST
+            while (u < uend) {
+                const int nr = (int)(uend - u < kPackRound ? uend - u : kPackRound);
+                bool ok = true;
+                for (int q = 0; q < nr && ok; ++q) {
+                    const int64_t uq = u + q;
+                    const unsigned itq = it + q;
+                    const int b = (int)(itq % ST);
+                    ok = mbar_wait(&full[b], (itq / ST) & 1);
+                    if (!ok)
+                        break;
+                    const int64_t j0 = C.slot0 + (uq - ub) * kPackTile;
+                    const bool diag = (j0 < t0 + TI) && (t0 < j0 + kPackTile);
+                    bool far = false;
+                    if (SPATIAL && !diag) {
+                        const float4 l = box[2 * (j0 / kPackTile)], h = box[2 * (j0 / kPackTile) + 1];
+                        const float gx = fmaxf(0.0f, fmaxf(l.x - bhi.x, blo.x - h.x));
+                        const float gy = fmaxf(0.0f, fmaxf(l.y - bhi.y, blo.y - h.y));
+                        const float gz = fmaxf(0.0f, fmaxf(l.z - bhi.z, blo.z - h.z));
+                        const float lim = far_theta * (bhi.w + h.w);
+                        far = gx * gx + gy * gy + gz * gz >= lim * lim;
+                    }
+                    if (SPATIAL) {
+                        n_far += far ? 1u : 0u;
+                        n_all += 1u;
+                    }
+                    if (diag)
+                        packed_tile<NP, UNROLL, true, LOC, false>(sh[b], j0, t0, tg, eps2, acc);
+                    else if (SPATIAL && far)
+                        packed_tile<NP, UNROLL, false, LOC, true>(sh[b], j0, t0, tg, eps2, acc);
+                    else
+                        packed_tile<NP, UNROLL, false, LOC, false>(sh[b], j0, t0, tg, eps2, acc);
+                    if (((uq - ub + 1) % kPackFlushTiles) == 0 || uq + 1 == uend) {
 #pragma unroll
-                    for (int pp = 0; pp < NP; ++pp)
+                        for (int pp = 0; pp < NP; ++pp)
 #pragma unroll
-                        for (int k = 0; k < kPackSums; ++k) {
-                            double *o = out + k * TI + packed_target(NP, 2 * pp);
-                            o[0] = first ? (double)acc[pp][k].x : o[0] + (double)acc[pp][k].x;
-                            o[32] = first ? (double)acc[pp][k].y : o[32] + (double)acc[pp][k].y;
-                            acc[pp][k] = make_float2(0.0f, 0.0f);
-                        }
-                    first = false;
+                            for (int k = 0; k < kPackSums; ++k) {
+                                double *o = out + k * TI + packed_target(NP, 2 * pp);
+                                o[0] = first ? (double)acc[pp][k].x : o[0] + (double)acc[pp][k].x;
+                                o[32] = first ? (double)acc[pp][k].y : o[32] + (double)acc[pp][k].y;
+                                acc[pp][k] = make_float2(0.0f, 0.0f);
+                            }
+                        first = false;
+                    }
                 }
-                if (__syncthreads_or(!ok)) {     // every warp is done with buffer b
+                if (__syncthreads_or(!ok)) {     // every warp is done with this round's buffers
                     if (threadIdx.x == 0) {
                         atomicOr(flag, kFlagTimeout);
-                        if (u + 1 < u1)          // let the other copy land before exiting
-                            mbar_wait(&full[b ^ 1], ((it + 1) >> 1) & 1);
+                        // let the copies still in flight land before exiting (one
+                        // shared time limit)
+                        const unsigned long long t_end = global_ns() + kWaitNs;
+                        for (int q = 0; q < ST && u + q < u1; ++q)
+                            mbar_wait_until(&full[(it + q) % ST], ((it + q) / ST) & 1, t_end);
                     }
                     return;
                 }
-                if (threadIdx.x == 0 && u + 2 < u1)
-                    bulk_load(sh[b], srec + unit_source(clu, nclu, u + 2) * RV, tile_bytes<LOC>(),
-                              &full[b], extra_tx);
+                if (threadIdx.x == 0)            // refill the round's buffers, ST tiles ahead
+                    for (int q = 0; q < nr && u + q + ST < u1; ++q)
+                        bulk_load(sh[(it + q) % ST], srec + unit_source(clu, nclu, u + q + ST) * RV,
+                                  tile_bytes<LOC>(), &full[(it + q) % ST], extra_tx);
+                u += nr;
+                it += nr;
             }
         }
     }
