@@ -386,10 +386,18 @@ def test_translation_invariance_mixed(orc):
     assert np.median(err) <= MIX_MED and err.max() <= MIX_MAX
 
 
-def test_nonfinite_is_reported_and_cleared():
+@pytest.mark.parametrize("spatial,bad", [("0", "on_hole"), ("1", "on_hole"), ("1", "nan")])
+def test_nonfinite_is_reported_and_cleared(monkeypatch, spatial, bad):
+    """A star on the hole (r = 0) or at a NaN position gives non-finite
+    accelerations, reported as PN_ENONFINITE; with the spatial order the NaN
+    also reaches the sort keys and the tile boxes (in slot order otherwise)."""
+    monkeypatch.setenv("PN_SPATIAL", spatial)
     x, v, m = make_cluster(300, 0.1, 81)
     x = x.copy()
-    x[5] = x[0]                      # a star on top of the hole: r = 0
+    if bad == "on_hole":
+        x[5] = x[0]                  # a star on top of the hole: r = 0
+    else:
+        x[5] = np.nan
     ctx = pn.pn_init(300, c=20.0, eps=1e-4, precision="mixed", device=0)
     X, V, M = dev(x), dev(v), dev(m)
     A = torch.empty_like(X)
