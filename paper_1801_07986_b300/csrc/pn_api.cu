@@ -403,6 +403,12 @@ static pn_status init_common(pn_ctx **out, int nclu, const int64_t *off, const p
     c->fused_P = 4;          // measured fastest on B300 at N = 131072
     c->fused_unroll = 2;
     c->workers_max = pn::kPackWorkersMax;
+    c->worker_units = 64;
+    if (const char *wu = std::getenv("PN_WORKER_UNITS")) {
+        const int v = std::atoi(wu);
+        if (v >= 1 && v <= 4096)
+            c->worker_units = v;
+    }
     // test hook: PN_INJECT_COPY_TIMEOUT=1 makes every tile barrier of the
     // packed kernel expect 16 bytes that never arrive, so its bounded waits
     // run out and pn_sync reports PN_ETIMEOUT

@@ -118,6 +118,7 @@ struct pn_ctx {
     int64_t fused_units;     // work units of the fused kernel (all clusters)
     int *wcount;             // next stream-K worker of the packed kernel (zeroed by the prologue)
     int workers_max;         // packed kernel: stream-K workers per resident block, at most
+    int worker_units;        // packed kernel: work units per stream-K worker, at least
     unsigned inject_tx;      // test hook: extra bytes each tile's mbarrier expects (0)
 
     // scratch, all owned by the context

@@ -1855,7 +1855,7 @@ cudaError_t fused_shape(const pn_ctx *c, int P, int unroll, bool packed, FusedSh
     int64_t per = 1;
     if (packed) {
         const int64_t cap = c->workers_max > 0 ? c->workers_max : kPackWorkersMax;
-        per = out->units / (out->grid * 64);
+        per = out->units / (out->grid * (int64_t)c->worker_units);
         per = per < 1 ? 1 : (per > cap ? cap : per);
     }
     out->G = out->grid * per;
