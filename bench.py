@@ -226,6 +226,17 @@ _FUSED_REGION = ("// The pair terms, shared by the two-pass and the fused kernel
 _KERNEL_REGIONS = {"fused_mixed": _FUSED_REGION, "fused_packed": _FUSED_REGION}
 
 
+def _code_only(text: str) -> str:
+    """Source text without // comments and blank lines, so that a committed
+    measurement stays tied to the code it measured, not to its comments."""
+    out = []
+    for line in text.splitlines():
+        code = line.split("//", 1)[0].rstrip()
+        if code:
+            out.append(code)
+    return "\n".join(out)
+
+
 def kernel_source_hash(tag: str | None = None):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1801_07986_b300", "csrc")
@@ -235,7 +246,7 @@ def kernel_source_hash(tag: str | None = None):
         i0 = text.find(a)
         i1 = text.find(b, i0)
         if i0 >= 0 and i1 > i0:
-            h.update(text[i0:i1].encode())
+            h.update(_code_only(text[i0:i1]).encode())
             hdr = open(os.path.join(csrc, "pn_internal.h")).read().splitlines()
             h.update("\n".join(l for l in hdr if l.startswith("constexpr")).encode())
             return h.hexdigest()[:16]

@@ -890,15 +890,19 @@ __device__ __forceinline__ int64_t unit_source(const Clu *__restrict__ clu, int 
 // warps.  A worker's result does not depend on which block runs it, so the
 // sums stay deterministic.
 //
-// Sources come from the staged records srec[slot][pack_vals<LOC>()] (every field
-// duplicated, positions negated), one contiguous 9 KB tile per unit, copied
-// by the bulk-copy engine into two shared buffers: the copy of unit u + 2
-// starts as soon as every warp is done with unit u, so the loads of the next
-// tile are in flight during the current one.  Targets are read from the same
-// records.  FP32 tile partials are added every kPackFlushTiles tiles into the
-// worker's segment slot in FP64 (each value is owned by one thread).  A copy
-// that does not complete within the poll limit sets kFlagTimeout in `flag`
-// and ends the block.
+// Sources come from the staged records srec[slot][pack_vals<LOC>()] (every
+// field duplicated, positions negated), one contiguous 8 or 9 KB tile per
+// unit, copied by the bulk-copy engine into kPackStages one-tile shared
+// buffers (tile k of the block into buffer k % kPackStages).  The tiles of a
+// target block are consumed in rounds of up to kPackRound between block
+// barriers; after a round's barrier thread 0 refills its buffers with the
+// tiles kPackStages ahead, so loads are in flight during arithmetic and the
+// warps, which may take different pair bodies, meet once per round.  Targets
+// are read from the same records.  FP32 tile partials are added every
+// kPackFlushTiles tiles into the worker's segment slot in FP64 (each value is
+// owned by one thread).  A copy that does not complete within the wait limit
+// sets kFlagTimeout in `flag`; the block then waits (one shared 1 s limit)
+// for the copies still in flight and ends.
 //
 // FORM 0: the D form of the hole term on stage_source records; 1: the
 // law-of-cosines form on stage_source_fwd records; 2: form 1 on records in
