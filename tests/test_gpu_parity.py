@@ -89,6 +89,7 @@ def test_mixed_matches_oracle(orc, n, pair_kernel):
 # fused-kernel variants (PN_FUSED_PACKED, PN_FUSED_TARGETS, PN_FUSED_UNROLL are
 # read by pn_init): the packed FP32x2 kernel and every scalar shape
 FUSED_VARIANTS = [("1", "4", "1"), ("1", "4", "2"), ("1", "2", "1"), ("1", "2", "2"),
+                  ("1s", "4", "1"), ("1s", "4", "2"), ("1s", "2", "1"), ("1s", "2", "2"),
                   ("0", "4", "1"), ("0", "4", "2"),
                   ("0", "4", "3"), ("0", "4", "4"), ("0", "2", "1"), ("0", "2", "2"),
                   ("0", "2", "4"), ("0", "1", "1"), ("0", "1", "2")]
@@ -96,6 +97,9 @@ FUSED_VARIANTS = [("1", "4", "1"), ("1", "4", "2"), ("1", "2", "1"), ("1", "2", 
 
 @pytest.mark.parametrize("packed,targets,unroll", FUSED_VARIANTS)
 def test_fused_variants_match_oracle(orc, monkeypatch, packed, targets, unroll):
+    """Every fused-kernel shape; "1s": the packed kernel on the spatial order."""
+    monkeypatch.setenv("PN_SPATIAL", "1" if packed == "1s" else "0")
+    packed = packed[0]
     monkeypatch.setenv("PN_FUSED_PACKED", packed)
     monkeypatch.setenv("PN_FUSED_TARGETS", targets)
     monkeypatch.setenv("PN_FUSED_UNROLL", unroll)
