@@ -481,10 +481,12 @@ def run_native(args, w):
 
 def run_16k(local, stream, warmup, steps, fp64_steps=10):
     """The 16k Plummer workload (M = 0.05, c = 50, eps = 1e-4, dt = 1/2048):
-    `steps` KDK steps in mixed precision and `fp64_steps` in FP64, each timed
-    as one pn_step call with CUDA events on the launching stream (inputs are
-    L2-resident at this size: 1.3 MB of records); the mixed run's relative
-    energy change (Eq. 7, FP64) over its steps."""
+    `steps` KDK steps in mixed precision and `fp64_steps` in FP64, timed with
+    CUDA events on the launching stream (inputs are L2-resident at this size:
+    1.3 MB of records); the mixed run's relative energy change (Eq. 7, FP64)
+    over its steps.  The mixed steps run as pn_step_graph replays of a
+    100-step CUDA graph (the first 100, which capture it, untimed) and, for
+    comparison, as one eager pn_step call; the FP64 steps as one pn_step."""
     import torch
     from paper_1801_07986_b300 import pn
     from paper_1801_07986_b300.inputs import WORKLOADS
@@ -492,8 +494,11 @@ def run_16k(local, stream, warmup, steps, fp64_steps=10):
     x, v, m = w.state()
     dev = torch.device(f"cuda:{local}")
     out = {"workload": "plummer16k", "n_bodies": w.n, "unit": "interactions/s",
-           "l2": "inputs L2-resident (timed as one multi-step call)"}
-    for prec, nst in (("mixed", steps), ("fp64", fp64_steps)):
+           "l2": "inputs L2-resident (each run's steps timed together)"}
+    graph_steps = 100
+    for key, prec, nst, graph in (("mixed", "mixed", steps, steps > graph_steps),
+                                  ("mixed_eager", "mixed", steps, False),
+                                  ("fp64", "fp64", fp64_steps, False)):
         X, V, M = (torch.tensor(a, device=dev) for a in (x, v, m))
         A = torch.empty_like(X)
         ctx = pn.pn_init(w.n, G=w.G, c=w.c, eps=w.eps, precision=prec, device=local,
@@ -504,16 +509,28 @@ def run_16k(local, stream, warmup, steps, fp64_steps=10):
         E0 = pn.pn_energy(ctx, X, V, M)["E"]
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        pn.pn_step(ctx, X, V, M, A, w.dt, nst)
-        e1.record(stream)
+        timed = nst
+        if graph:
+            pn.pn_step_graph(ctx, X, V, M, A, w.dt, graph_steps)     # capture + first run
+            timed = (nst - graph_steps) // graph_steps * graph_steps
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            for _ in range(timed // graph_steps):
+                pn.pn_step_graph(ctx, X, V, M, A, w.dt, graph_steps)
+            e1.record(stream)
+        else:
+            e0.record(stream)
+            pn.pn_step(ctx, X, V, M, A, w.dt, nst)
+            e1.record(stream)
         e1.synchronize()
         pn.pn_sync(ctx)
         ms = e0.elapsed_time(e1)
         E1 = pn.pn_energy(ctx, X, V, M)["E"]
         ctx.close()
-        out[prec] = {"value": float(w.n) * (w.n - 1) * nst / (ms * 1e-3), "steps": nst,
-                     "ms_per_step": ms / nst, "dE_over_E": (E1 - E0) / abs(E0)}
+        out[key] = {"value": float(w.n) * (w.n - 1) * timed / (ms * 1e-3),
+                     "steps": graph_steps + timed if graph else nst, "timed_steps": timed,
+                     "ms_per_step": ms / timed, "dE_over_E": (E1 - E0) / abs(E0),
+                     "launch": "pn_step_graph replays" if graph else "one pn_step call"}
     out["value"] = out["mixed"]["value"]
     out["mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
     out["note"] = ("dE_over_E is the integrator's on this workload: between steps 100 and 200 "
