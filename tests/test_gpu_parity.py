@@ -76,9 +76,13 @@ def test_fp64_matches_oracle(orc, n):
 PAIR_KERNELS = ["fused", "two_pass"]
 
 
-@pytest.mark.parametrize("pair_kernel", PAIR_KERNELS)
+@pytest.mark.parametrize("pair_kernel", PAIR_KERNELS + ["fused_spatial"])
 @pytest.mark.parametrize("n", [2, 3, 300, 1024, 4097])
-def test_mixed_matches_oracle(orc, n, pair_kernel):
+def test_mixed_matches_oracle(orc, monkeypatch, n, pair_kernel):
+    """fused_spatial: the fused kernel with the spatial order forced on (its
+    sort blocks and tile boxes mostly padding at the smallest sizes)."""
+    monkeypatch.setenv("PN_SPATIAL", "1" if pair_kernel == "fused_spatial" else "0")
+    pair_kernel = pair_kernel.replace("_spatial", "")
     x, v, m = cluster(n, 0.1, 200 + n)
     want = orc.accel(x, v, m, c=20.0, eps=1e-4)
     got = gpu_accel(x, v, m, "mixed", c=20.0, eps=1e-4, pair_kernel=pair_kernel)
