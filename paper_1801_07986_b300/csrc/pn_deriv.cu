@@ -1339,6 +1339,35 @@ k_adj_sources_packed(const float4 *__restrict__ srec, const float4 *__restrict__
 // M cotangent (4 values).  Eight lanes per star slot (as k_adj_star): the
 // lanes first sum the split partials (each a share of the 20 values, splits
 // in order), then lanes 0..6 take one seed each.
+// Split partials of the reverse sweeps summed in place: part holds js
+// splits of nv values of S slots ([split][value][slot]); thread (k, t) adds
+// the js partials of value k of slot t, in split order, into split 0.  One
+// thread per value and slot with eight loads in flight, so the sum runs at
+// L2 bandwidth (the per-star kernel that reads the totals has eight lanes
+// per star and stalled on these loads).
+__global__ void __launch_bounds__(kGlueThreads)
+k_split_sum(int64_t S, int nv, int js, double *__restrict__ part)
+{
+    const int64_t e = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
+    if (e >= nv * S)
+        return;
+    const int64_t stride = (int64_t)nv * S;
+    double acc = part[e];
+    int q = 1;
+    for (; q + 8 <= js; q += 8) {
+        double p[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+            p[r] = part[(int64_t)(q + r) * stride + e];
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+            acc += p[r];
+    }
+    for (; q < js; ++q)
+        acc += part[(int64_t)q * stride + e];
+    part[e] = acc;
+}
+
 __global__ void __launch_bounds__(kGlueThreads)
 k_adj_records(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_clu,
               const double *__restrict__ x, const double *__restrict__ v,
@@ -1684,8 +1713,15 @@ cudaError_t launch_accel_vjp(pn_ctx *c, const double *x, const double *v, const 
         k_adj_targets<<<grid, kJThreads, 0, c->stream>>>(rec, S, c->d_clu, bc, sbar, tpart);
         k_adj_sources<<<grid, kJThreads, 0, c->stream>>>(rec, S, c->d_clu, bc, sbar, spart);
     }
+    if (jsr > 1) {              // the sweeps' split partials, summed into split 0
+        k_split_sum<<<(unsigned)((6 * S + kGlueThreads - 1) / kGlueThreads), kGlueThreads, 0,
+                      c->stream>>>(S, 6, jsr, tpart);
+        k_split_sum<<<(unsigned)((kAdjSrc * S + kGlueThreads - 1) / kGlueThreads), kGlueThreads,
+                      0, c->stream>>>(S, kAdjSrc, jsr, spart);
+        c->launches += 2;
+    }
     k_adj_records<<<(unsigned)(S / kAdjStarWarps), kGlueThreads, 0, c->stream>>>(
-        S, c->d_clu, bc, x, v, m, abar, kbar, tpart, jsr, spart, jsr, gbar, xbar, vbar, hblk);
+        S, c->d_clu, bc, x, v, m, abar, kbar, tpart, 1, spart, 1, gbar, xbar, vbar, hblk);
     k_adj_hole<<<c->nclu, kGlueThreads, 0, c->stream>>>(c->d_clu, hblk, gbar, xbar, vbar, scal,
                                                        accumulate ? 1 : 0);
     c->launches += 6;
