@@ -1339,12 +1339,12 @@ k_adj_sources_packed(const float4 *__restrict__ srec, const float4 *__restrict__
 // M cotangent (4 values).  Eight lanes per star slot (as k_adj_star): the
 // lanes first sum the split partials (each a share of the 20 values, splits
 // in order), then lanes 0..6 take one seed each.
-// Split partials of the reverse sweeps summed in place: part holds js
-// splits of nv values of S slots ([split][value][slot]); thread (k, t) adds
-// the js partials of value k of slot t, in split order, into split 0.  One
-// thread per value and slot with eight loads in flight, so the sum runs at
-// L2 bandwidth (the per-star kernel that reads the totals has eight lanes
-// per star and stalled on these loads).
+// Split partials of the jerk's and the reverse sweeps' pair kernels summed in
+// place: part holds js splits of nv values of S slots ([split][value][slot]);
+// thread (k, t) adds the js partials of value k of slot t, in split order,
+// into split 0.  One thread per value and slot with eight loads in flight,
+// so the sum runs at L2 bandwidth (the per-star kernels that read the totals
+// stalled on these loads).
 __global__ void __launch_bounds__(kGlueThreads)
 k_split_sum(int64_t S, int nv, int js, double *__restrict__ part)
 {
@@ -1600,8 +1600,13 @@ cudaError_t launch_jerk(pn_ctx *c, const double *x, const double *v, const doubl
     }
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
+    if (jsum > 1) {
+        k_split_sum<<<(unsigned)((2 * kFusedVals * S + kGlueThreads - 1) / kGlueThreads),
+                      kGlueThreads, 0, c->stream>>>(S, 2 * kFusedVals, jsum, part);
+        c->launches += 1;
+    }
     k_jerk_epilogue<<<(unsigned)nglue, kGlueThreads, 0, c->stream>>>(
-        S, c->d_clu, bc, x, v, m, a, part, jsum, glob, jerk, c->flag, c->flag_step, step, bhb);
+        S, c->d_clu, bc, x, v, m, a, part, 1, glob, jerk, c->flag, c->flag_step, step, bhb);
     c->launches += 1;
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
