@@ -46,6 +46,7 @@ METRIC = "1PN pair interactions/s at N=16k/128k, mixed vs FP64 on B300 at <=1e-5
 FLOPS_PASS1 = 29   # hand count of the mixed pass-1 pair body (FMA = 2, rsqrt = 1)
 FLOPS_PASS2 = 67   # hand count of the mixed pass-2 pair body
 FLOPS_FUSED = 77   # hand count of the scalar fused pair body (pass 1 + pass 2 sharing x, r, rsqrt)
+FLOPS_F64_FUSED = 71   # hand count of the fused double-precision pair body (rsqrt counted as 1)
 FLOPS_PACKED = 72  # hand count of the packed fused pair body, law-of-cosines form (r_near > 0)
 OPS_PACKED = 46    # FP32-pipe operations per pair of that body (FMA, add and mul count 1 each)
 FLOPS_PACKED_FAR = 66  # the same body on far units of the spatial order (x_ij from the high parts)
@@ -340,17 +341,20 @@ def run_native(args, w):
     per_launch_ms = kms[k_dom] / max(1, klaunch[k_dom])
     pairs = float(w.n - 1) * (w.n - 2)
     fused = args.precision == "mixed" and args.pair_kernel == "fused"
+    f64_fused = args.precision == "fp64" and args.pair_kernel == "fused"
     packed = fused and bool(launch.get("packed"))
     # share of the pairs the spatially ordered packed kernel took through its
     # far-unit body (device counters; 0 without the spatial order)
     far_frac = far_units / all_units if packed and all_units else 0.0
     fpp = (FLOPS_PACKED - far_frac * (FLOPS_PACKED - FLOPS_PACKED_FAR) if packed else FLOPS_FUSED) \
-        if fused else (FLOPS_PASS2 if k_dom == 1 else FLOPS_PASS1)
+        if fused else (FLOPS_F64_FUSED if f64_fused else (FLOPS_PASS2 if k_dom == 1 else FLOPS_PASS1))
     flops = fpp * pairs
     achieved = flops / (per_launch_ms * 1e-3) / 1e12
     clocks = clk.summary()
     if fused:
         tag = "fused_packed" if launch.get("packed") else "fused_mixed"
+    elif f64_fused:
+        tag = "fused_f64"
     else:
         tag = f"pass{k_dom + 1}_{args.precision}"
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -377,9 +381,16 @@ def run_native(args, w):
         roof["frac_of_fma_microbench"] = achieved / meas["fp32_fma_tflops"]
         roof["fp64_fma_microbench_tflops"] = meas["fp64_fma_tflops"]
         roof["fp32x2_fma_microbench_tflops"] = meas["fp32x2_fma_tflops"]
+        if args.precision == "fp64":
+            # the double-precision path is bound by the FP64 pipe: its peak
+            # is the measured FP64 FMA rate (no nominal FP64 figure is given)
+            roof["peak"] = meas["fp64_fma_tflops"]
+            roof["frac"] = achieved / roof["peak"]
+            roof["peak_basis"] = "FP64 FMA-chain microbenchmark on this device (pn_measure_peaks)"
+            roof.pop("frac_at_sampled_clock", None)
     except Exception as e:  # reported, not required
         roof["fp32_fma_microbench_error"] = str(e)[:200]
-    roof["flops_per_interaction"] = fpp if fused else FLOPS_PASS1 + FLOPS_PASS2
+    roof["flops_per_interaction"] = fpp if (fused or f64_fused) else FLOPS_PASS1 + FLOPS_PASS2
 
     line = {
         "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world,

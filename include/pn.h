@@ -80,12 +80,12 @@ enum { PN_KDK = 0, PN_RK4 = 1, PN_HERMITE = 2 };   /* pn_params.integrator  */
  *              separate cancellation-free pair form instead of through
  *              global sums.  The result is the same in exact arithmetic;
  *              only rounding changes.  0 disables the split.
- *   pair_kernel (PN_MIXED only) PN_PAIR_FUSED: one persistent kernel
- *              computes the pass-1 and pass-2 pair sums in a single sweep
- *              over the sources; PN_PAIR_TWO_PASS: pass 1 (Newtonian sums
- *              and the hole's accumulators) and pass 2 (1PN pair sums) as
- *              two kernels.  Same sums, same epilogue.  PN_FP64 always runs
- *              the two-pass kernels.
+ *   pair_kernel PN_PAIR_FUSED: the pass-1 and pass-2 pair sums in a
+ *              single sweep over the sources (PN_MIXED: one persistent
+ *              kernel; PN_FP64: one double-precision sweep);
+ *              PN_PAIR_TWO_PASS: pass 1 (Newtonian sums and the hole's
+ *              accumulators) and pass 2 (1PN pair sums) as two kernels.
+ *              Same sums, same epilogue (in PN_FP64 bitwise the same).
  *   integrator PN_KDK: kick-drift-kick leapfrog (vel_mode applies), one
  *              force evaluation per step.  PN_RK4: classical fourth-order
  *              Runge-Kutta, the paper's own integrator (Section 4), four

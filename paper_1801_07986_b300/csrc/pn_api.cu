@@ -181,6 +181,8 @@ pn_status evaluate(pn_ctx *c, const double *x, const double *vel, const double *
     PN_CUDA(pn::launch_prologue(c, x, vel, m, false), "prologue launch");
     if (pn::use_fused(c)) {
         PN_CUDA(pn::launch_fused(c), "fused pair launch");
+    } else if (pn::use_fused_f64(c)) {
+        PN_CUDA(pn::launch_fused_f64(c), "fused FP64 pair launch");
     } else {
         PN_CUDA(pn::launch_pass1(c), "pass-1 launch");
         PN_CUDA(pn::launch_pass2(c), "pass-2 launch");

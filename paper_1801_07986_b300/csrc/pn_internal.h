@@ -211,6 +211,8 @@ cudaError_t launch_fused(pn_ctx *c);
 cudaError_t launch_stage_sources(pn_ctx *c, const float4 *rec);
 cudaError_t launch_fused_on(pn_ctx *c, const float4 *rec);
 bool use_fused(const pn_ctx *c);
+bool use_fused_f64(const pn_ctx *c);
+cudaError_t launch_fused_f64(pn_ctx *c);
 int fused_tile_size(bool packed);
 struct FusedShape {
     int occ;                 // resident blocks per SM

@@ -1179,12 +1179,14 @@ k_fused_gather(const double *__restrict__ part, int64_t S, const Clu *__restrict
 
 // The same pair sums as pass 1 / pass 2 above, in double precision
 // (records A = (d, m), B = (v, R^2), C = (-e/1.5, C), D = (w, 0); vi is
-// 8/3 times the target's velocity).
-template <int PASS, bool MASK>
+// 8/3 times the target's velocity).  PASS 3: both passes' sums from one
+// separation, distance and rsqrt per pair (pass-1 values first).
+template <int PASS, bool MASK, int NACC>
 __device__ __forceinline__ void f64_tile(const double4_32a (*__restrict__ sh)[kF64Tile], int64_t j0,
                                          const double (&di)[3], const double (&vi)[3],
-                                         int64_t ti, double eps2, double (&acc)[kP2Vals])
+                                         int64_t ti, double eps2, double (&acc)[NACC])
 {
+    constexpr int o2 = PASS == 3 ? kP1Vals : 0;     // first pass-2 value in acc
 #pragma unroll 1
     for (int q = 0; q < kF64Tile; ++q) {
         const double4_32a A = sh[0][q];
@@ -1200,14 +1202,15 @@ __device__ __forceinline__ void f64_tile(const double4_32a (*__restrict__ sh)[kF
         const double is2 = is * is;
         const double mis = mj * is;
         const double mis3 = mis * is2;
-        if constexpr (PASS == 1) {
+        if constexpr (PASS != 2) {
             acc[0] = fma(mis3, dx, acc[0]);
             acc[1] = fma(mis3, dy, acc[1]);
             acc[2] = fma(mis3, dz, acc[2]);
             acc[3] += mis;
             acc[4] += mis3;
             acc[5] = fma(mis3, sh[1][q].w, acc[5]);
-        } else {
+        }
+        if constexpr (PASS != 1) {
             const double4_32a B = sh[1][q];
             const double4_32a C = sh[2][q];
             const double4_32a D = sh[3][q];
@@ -1218,27 +1221,31 @@ __device__ __forceinline__ void f64_tile(const double4_32a (*__restrict__ sh)[kF
             k = fma(C.x, di[0], fma(C.y, di[1], fma(C.z, di[2], k)));
             const double h = xvj * is2;
             const double f = mis3 * fma(h, xvj, k);
-            acc[0] = fma(f, dx, acc[0]);
-            acc[1] = fma(f, dy, acc[1]);
-            acc[2] = fma(f, dz, acc[2]);
+            acc[o2 + 0] = fma(f, dx, acc[o2 + 0]);
+            acc[o2 + 1] = fma(f, dy, acc[o2 + 1]);
+            acc[o2 + 2] = fma(f, dz, acc[o2 + 2]);
             const double gg = mis3 * fma(-2.0, xvj, xvi);
-            acc[3] += gg;
-            acc[4] = fma(gg, B.x, acc[4]);
-            acc[5] = fma(gg, B.y, acc[5]);
-            acc[6] = fma(gg, B.z, acc[6]);
-            acc[7] = fma(wx, is, acc[7]);
-            acc[8] = fma(wy, is, acc[8]);
-            acc[9] = fma(wz, is, acc[9]);
+            acc[o2 + 3] += gg;
+            acc[o2 + 4] = fma(gg, B.x, acc[o2 + 4]);
+            acc[o2 + 5] = fma(gg, B.y, acc[o2 + 5]);
+            acc[o2 + 6] = fma(gg, B.z, acc[o2 + 6]);
+            acc[o2 + 7] = fma(wx, is, acc[o2 + 7]);
+            acc[o2 + 8] = fma(wy, is, acc[o2 + 8]);
+            acc[o2 + 9] = fma(wz, is, acc[o2 + 9]);
         }
     }
 }
 
+// Grid (target blocks of kF64Threads, source splits); split s sweeps tiles
+// [s tps, (s+1) tps) of the target block's cluster and writes its partials
+// to part[s][value][slot] (PASS 3: pass-1 values to part, pass-2 values to
+// part2, each in its pass's layout).
 template <int PASS>
 __global__ void __launch_bounds__(kF64Threads)
 k_pass_f64(const double4_32a *__restrict__ rec, int64_t S, const Clu *__restrict__ clu,
-           const int *__restrict__ blk_clu, double *__restrict__ part)
+           const int *__restrict__ blk_clu, double *__restrict__ part, double *__restrict__ part2)
 {
-    constexpr int NV = PASS == 1 ? kP1Vals : kP2Vals;
+    constexpr int NV = PASS == 1 ? kP1Vals : (PASS == 2 ? kP2Vals : kFusedVals);
     constexpr int NA = PASS == 1 ? 2 : 4;
     __shared__ double4_32a sh[4][kF64Tile];
     const int64_t t0 = (int64_t)blockIdx.x * kF64Threads;
@@ -1250,15 +1257,15 @@ k_pass_f64(const double4_32a *__restrict__ rec, int64_t S, const Clu *__restrict
     const double4_32a A = rec[ti];
     const double di[3] = {A.x, A.y, A.z};
     double vi[3] = {0.0, 0.0, 0.0};
-    if (PASS == 2) {
+    if (PASS != 1) {
         const double4_32a B = rec[S + ti];
         vi[0] = (8.0 / 3.0) * B.x;
         vi[1] = (8.0 / 3.0) * B.y;
         vi[2] = (8.0 / 3.0) * B.z;
     }
-    double acc[kP2Vals];
+    double acc[NV];
 #pragma unroll
-    for (int k = 0; k < kP2Vals; ++k)
+    for (int k = 0; k < NV; ++k)
         acc[k] = 0.0;
     const int tb = blockIdx.y * tps;
     const int te = min(ntiles, tb + tps);
@@ -1273,13 +1280,22 @@ k_pass_f64(const double4_32a *__restrict__ rec, int64_t S, const Clu *__restrict
         __syncthreads();
         const bool diag = (j0 < t0 + kF64Threads) && (t0 < j0 + kF64Tile);
         if (diag)
-            f64_tile<PASS, true>(sh, j0, di, vi, ti, eps2, acc);
+            f64_tile<PASS, true, NV>(sh, j0, di, vi, ti, eps2, acc);
         else
-            f64_tile<PASS, false>(sh, j0, di, vi, ti, eps2, acc);
+            f64_tile<PASS, false, NV>(sh, j0, di, vi, ti, eps2, acc);
     }
+    if (PASS == 3) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k)
-        part[((int64_t)blockIdx.y * NV + k) * S + ti] = acc[k];
+        for (int k = 0; k < kP1Vals; ++k)
+            part[((int64_t)blockIdx.y * kP1Vals + k) * S + ti] = acc[k];
+#pragma unroll
+        for (int k = 0; k < kP2Vals; ++k)
+            part2[((int64_t)blockIdx.y * kP2Vals + k) * S + ti] = acc[kP1Vals + k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+            part[((int64_t)blockIdx.y * NV + k) * S + ti] = acc[k];
+    }
 }
 
 // Energy pair sums, double precision, records A = (d, m), B = (v, 0):
@@ -1890,7 +1906,7 @@ cudaError_t launch_pass1(pn_ctx *c)
     } else {
         dim3 grid((unsigned)(c->S / kF64Threads), (unsigned)c->f64.jsplit);
         k_pass_f64<1><<<grid, kF64Threads, 0, c->stream>>>(c->drec, c->S, c->d_clu, blk_table(c),
-                                                           c->part + L.p1);
+                                                           c->part + L.p1, nullptr);
     }
     c->launches += 1;
     cudaError_t e = cudaGetLastError();
@@ -1911,8 +1927,30 @@ cudaError_t launch_pass2(pn_ctx *c)
     } else {
         dim3 grid((unsigned)(c->S / kF64Threads), (unsigned)c->f64.jsplit);
         k_pass_f64<2><<<grid, kF64Threads, 0, c->stream>>>(c->drec, c->S, c->d_clu, blk_table(c),
-                                                           c->part + L.p2);
+                                                           c->part + L.p2, nullptr);
     }
+    c->launches += 1;
+    cudaError_t e = cudaGetLastError();
+    if (end)
+        cudaEventRecord(end, c->stream);
+    return e;
+}
+
+bool use_fused_f64(const pn_ctx *c)
+{
+    return c->p.precision == PN_FP64 && c->p.pair_kernel == PN_PAIR_FUSED;
+}
+
+// FP64 contexts with the fused pair kernel: both passes' sums in one sweep
+// (k_pass_f64<3>), into the two-pass partial layout; timed as kernel 1.
+cudaError_t launch_fused_f64(pn_ctx *c)
+{
+    const Layout L = layout(c);
+    cudaEvent_t end = nullptr;
+    timing_begin(c, 1, &end);
+    dim3 grid((unsigned)(c->S / kF64Threads), (unsigned)c->f64.jsplit);
+    k_pass_f64<3><<<grid, kF64Threads, 0, c->stream>>>(c->drec, c->S, c->d_clu, blk_table(c),
+                                                       c->part + L.p1, c->part + L.p2);
     c->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (end)

@@ -126,6 +126,15 @@ def test_fused_variants_match_oracle(orc, monkeypatch, packed, targets, unroll):
     assert np.median(err) <= MIX_MED and err.max() <= MIX_MAX, (np.median(err), err.max())
 
 
+def test_fp64_fused_equals_two_pass():
+    """In FP64 the fused sweep and the two passes form the same sums in the
+    same order: bitwise equal accelerations."""
+    x, v, m = make_cluster(3000, 0.1, 62)
+    a1 = gpu_accel(x, v, m, "fp64", c=30.0, eps=1e-4, pair_kernel="fused")
+    a2 = gpu_accel(x, v, m, "fp64", c=30.0, eps=1e-4, pair_kernel="two_pass")
+    assert np.array_equal(a1, a2)
+
+
 def test_plummer1k_workload_fp64_every_body(orc):
     w = WORKLOADS["plummer1k_fp64"]
     x, v, m = w.state()
