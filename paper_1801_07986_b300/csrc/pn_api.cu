@@ -120,7 +120,8 @@ void set_params(pn_ctx *c, const pn_params *p, bool all_physics)
 
 void free_all(pn_ctx *c)
 {
-    void *bufs[] = {c->vp, c->mrec, c->sord, c->bal, c->drec, c->part, c->blk, c->glob, c->eout, c->flag, c->wcount,
+    void *bufs[] = {c->vp, c->mrec, c->sord, c->bal, c->drec, c->part, c->blk, c->glob, c->eout,
+                    c->flag, c->wcount, c->units_cnt,
                     c->flag_step, c->hx, c->hv, c->hm, c->ha, c->nrec, c->ndrec, c->ncount,
                     c->nflag, c->rk_x, c->rk_v, c->rk_a, c->rk_sx, c->rk_sv, c->jbuf, c->hj0, c->hj1, c->abuf,
                     c->d_clu,

@@ -15,8 +15,8 @@ constexpr int kMixTargets = 2;     // targets held in registers per thread
 constexpr int kMixTile = 128;      // sources per shared-memory tile
 constexpr int kFlushTiles = 2;     // fused kernel: tiles per single-precision partial
 constexpr int kPackTile = 64;      // packed fused kernel: sources per shared-memory tile
-constexpr int kPackVals = 9;       // packed adjoint sweeps: float4 per staged source record
-constexpr int kFwdVals = 8;        // packed fused kernel: float4 per staged source record
+constexpr int kPackVals = 9;       // dot-product staged layout (packed kernel form 0, adjoint sweeps): float4 per source
+constexpr int kFwdVals = 8;        // law-of-cosines staged layout (packed kernel forms 1, 2): float4 per source
 constexpr int kPackFlushTiles = 8; // packed fused kernel: tiles per single-precision partial
 constexpr int kPackWorkersMax = 4;  // packed fused kernel: stream-K workers per resident block (max)
 constexpr int kPackStages = 6;     // packed fused kernel: one-tile shared buffers
