@@ -249,7 +249,7 @@ def kernel_source_hash(tag: str | None = None):
         if i0 >= 0 and i1 > i0:
             h.update(_code_only(text[i0:i1]).encode())
             hdr = open(os.path.join(csrc, "pn_internal.h")).read().splitlines()
-            h.update("\n".join(l for l in hdr if l.startswith("constexpr")).encode())
+            h.update(_code_only("\n".join(l for l in hdr if l.startswith("constexpr"))).encode())
             return h.hexdigest()[:16]
     for f in ("pn_kernels.cu", "pn_internal.h"):
         with open(os.path.join(csrc, f), "rb") as fh:
