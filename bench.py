@@ -177,6 +177,35 @@ def oracle_rate(x, v, m, w, star_rows: int, hole_rows: int, seed: int = 0):
     return n * (n - 1) / per_eval, t2 - t0, oracle.threads()
 
 
+def oracle_extra(x, v, m, w, one_core_rows: int = 256):
+    """The oracle on one host core (a smaller row sample of the same
+    evaluation), and whole evaluations of the 1k and 16k workloads on all
+    cores, in interactions/s: N(N - 1) over the time of one full oracle.accel
+    call, the hole's double sum included."""
+    import oracle
+    from paper_1801_07986_b300.inputs import WORKLOADS
+    cores = oracle.threads()
+    out = {}
+    try:
+        oracle.set_threads(1)
+        r1, secs1, _ = oracle_rate(x, v, m, w, one_core_rows, one_core_rows, seed=7)
+        out["one_core"] = {"value": r1, "cores": 1,
+                           "sample": f"{one_core_rows} star rows + {one_core_rows} hole "
+                                     f"double-sum rows of the N={w.n} evaluation ({secs1:.1f} s)"}
+    finally:
+        oracle.set_threads(cores)
+    full = {}
+    for name in ("plummer1k_fp64", "plummer16k"):
+        wk = WORKLOADS[name]
+        xk, vk, mk = wk.state()
+        t0 = time.perf_counter()
+        oracle.accel(xk, vk, mk, G=wk.G, c=wk.c, eps=wk.eps)
+        t = time.perf_counter() - t0
+        full[name] = {"n_bodies": wk.n, "value": wk.n * (wk.n - 1) / t, "seconds": t}
+    out["full_evaluations"] = full
+    return out
+
+
 def run_reference(args, w):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -481,6 +510,7 @@ def run_native(args, w):
                 "value": r, "unit": "interactions/s", "cores": cores, "kind": "oracle",
                 "sample": f"{rows} star rows + {rows} hole double-sum rows of the N={w.n} "
                           f"evaluation ({secs:.1f} s), scaled by (N-1)/{rows}"}
+            line["cpu_baseline"].update(oracle_extra(x, v, m, w))
         except Exception as e:  # the baseline is reported, not required
             line["cpu_baseline"] = {"value": None, "error": str(e)[:200]}
     ctx.close()
