@@ -276,9 +276,16 @@ def kernel_source_hash(tag: str | None = None):
         i0 = text.find(a)
         i1 = text.find(b, i0)
         if i0 >= 0 and i1 > i0:
-            h.update(_code_only(text[i0:i1]).encode())
+            region = _code_only(text[i0:i1])
+            h.update(region.encode())
+            # the header's compile-time tunables that the region names
             hdr = open(os.path.join(csrc, "pn_internal.h")).read().splitlines()
-            h.update(_code_only("\n".join(l for l in hdr if l.startswith("constexpr"))).encode())
+            used = []
+            for l in hdr:
+                m = re.match(r"constexpr\s+[\w:<>\s]+?\b(\w+)\s*=", l)
+                if m and re.search(rf"\b{m.group(1)}\b", region):
+                    used.append(l)
+            h.update(_code_only("\n".join(used)).encode())
             return h.hexdigest()[:16]
     for f in ("pn_kernels.cu", "pn_internal.h"):
         with open(os.path.join(csrc, f), "rb") as fh:

@@ -514,7 +514,7 @@ static pn_status init_common(pn_ctx **out, int nclu, const int64_t *off, const p
         part = part_fused;
     c->part_len = part;
     const int64_t nglue = S / pn::kGlueThreads;
-    c->blk_len = nglue * pn::kGlobVals;
+    c->blk_len = S / pn::kProThreads * pn::kGlobVals;     // the largest per-block partial table
 
     struct Req { void **p; size_t bytes; } req[] = {
         {(void **)&c->vp, sizeof(double) * 3 * (size_t)n},

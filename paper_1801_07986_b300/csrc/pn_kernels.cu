@@ -161,7 +161,7 @@ __device__ __forceinline__ void stage_source_fwd(float4 *__restrict__ o, float4 
 // Mixed mode also writes the packed kernel's staged records: the
 // law-of-cosines layout (stage_source_fwd) when `loc`, else stage_source's.
 template <int MODE>   // 0 mixed, 1 double, 2 energy
-__global__ void __launch_bounds__(kGlueThreads)
+__global__ void __launch_bounds__(kProThreads)
 k_prologue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_clu,
            const double *__restrict__ x, const double *__restrict__ vel,
            const double *__restrict__ m, float4 *__restrict__ mrec,
@@ -171,11 +171,11 @@ k_prologue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
     // mixed: the staged source records of the packed pair kernel follow the
     // five record arrays
     float4 *__restrict__ srec = mrec + 5 * S;
-    __shared__ double sh[kGlobVals][kGlueThreads];
-    const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
+    __shared__ double sh[kGlobVals][kProThreads];
+    const int64_t t = (int64_t)blockIdx.x * kProThreads + threadIdx.x;
     if (wcount && t == 0)
         *wcount = 0;          // the packed pair kernel's worker counter, for this evaluation
-    const Clu C = clu[cluster_of_block(blk_clu, blockIdx.x)];
+    const Clu C = clu[cluster_of_block(blk_clu, (int64_t)blockIdx.x * kProThreads / kGlueThreads)];
     const int64_t lt = t - C.slot0;
     const double G = C.G, eps2 = C.eps2;
     double g[kGlobVals];
@@ -269,13 +269,14 @@ k_prologue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
     }
     if (MODE == 2)
         return;   // block-uniform
-    block_sum<kGlobVals>(g, sh);
+    block_sum<kGlobVals, kProThreads>(g, sh);
     if (threadIdx.x < kGlobVals)
         blk[(int64_t)blockIdx.x * kGlobVals + threadIdx.x] = sh[threadIdx.x][0];
 }
 
-// One block per cluster: totals of its prologue blocks (fixed order) into
-// glob[k][.], the exclusive prefix of its per-block near-star counts into
+// One block per cluster: totals of its prologue blocks (kProThreads slots
+// each, fixed order) into glob[k][.], the exclusive prefix of the near-star
+// counts of its kGlueThreads-slot blocks (the near scatter's blocks) into
 // ncount[nclu + b], the count into ncount[k], and zero-mass padding of its
 // near-record slice up to the next multiple of kNearTile.
 template <int MODE>   // 0 mixed, 1 double
@@ -285,41 +286,55 @@ k_global_sums(const Clu *__restrict__ clu, int nclu, const double *__restrict__ 
               double4_32a *__restrict__ ndrec, int64_t NC)
 {
     __shared__ double sh[kGlobVals][kGlueThreads];
-    __shared__ int scan[kGlueThreads];
+    __shared__ int wsum[kGlueThreads / 32];
+    constexpr int kSub = kGlueThreads / kProThreads;    // prologue blocks per near-scatter block
     const int k = blockIdx.x;
     const Clu C = clu[k];
     const int64_t b0 = C.slot0 / kGlueThreads;
     const int64_t nblk = C.ns_pad / kGlueThreads;
-    const double *cb = blk + b0 * kGlobVals;
-    sum_blocks<kGlobVals>(cb, nblk, sh);
+    const double *cb = blk + b0 * kSub * kGlobVals;
+    sum_blocks<kGlobVals>(cb, nblk * kSub, sh);
     if (threadIdx.x < kGlobVals)
         glob[(int64_t)k * kGlobVals + threadIdx.x] = sh[threadIdx.x][0];
-    // exclusive prefix of block counts: each thread owns a contiguous chunk
+    // near-star count of near-scatter block b
+    auto count_of = [&](int64_t b) {
+        int n = 0;
+#pragma unroll
+        for (int q = 0; q < kSub; ++q)
+            n += (int)cb[(b * kSub + q) * kGlobVals + 12];
+        return n;
+    };
+    // exclusive prefix of block counts: each thread owns a contiguous chunk;
+    // the chunk totals are scanned by warp shuffles, then across the warps
     const int64_t chunk = (nblk + kGlueThreads - 1) / kGlueThreads;
     const int64_t c0 = threadIdx.x * chunk;
     const int64_t c1 = c0 + chunk < nblk ? c0 + chunk : nblk;
     int local = 0;
     for (int64_t b = c0; b < c1; ++b)
-        local += (int)cb[b * kGlobVals + 12];
-    scan[threadIdx.x] = local;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int run = 0;
-        for (int q = 0; q < kGlueThreads; ++q) {
-            const int cnt = scan[q];
-            scan[q] = run;
-            run += cnt;
-        }
-        ncount[k] = run;
+        local += count_of(b);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o)
+            incl += y;
     }
+    if (lane == 31)
+        wsum[wid] = incl;
     __syncthreads();
-    int run = scan[threadIdx.x];
+    int run = incl - local, nn = 0;
+#pragma unroll
+    for (int q = 0; q < kGlueThreads / 32; ++q) {
+        run += q < wid ? wsum[q] : 0;
+        nn += wsum[q];
+    }
+    if (threadIdx.x == 0)
+        ncount[k] = nn;
     for (int64_t b = c0; b < c1; ++b) {
         ncount[nclu + b0 + b] = run;
-        run += (int)cb[b * kGlobVals + 12];
+        run += count_of(b);
     }
-    __syncthreads();
-    const int nn = ncount[k];
     const int npad = (int)((nn + kNearTile - 1) / kNearTile * kNearTile);
     for (int q = nn + threadIdx.x; q < npad; q += kGlueThreads) {
         const int64_t e = C.near0 + q;
@@ -1777,21 +1792,21 @@ cudaError_t launch_rk4_stage(pn_ctx *c, int stage, double *x, double *v, const d
 cudaError_t launch_prologue(pn_ctx *c, const double *x, const double *vel, const double *m,
                             bool energy_records)
 {
-    const int64_t nb = c->S / kGlueThreads;
+    const int64_t nb = c->S / kGlueThreads, npb = c->S / kProThreads;
     const int *bc = blk_table(c);
     if (energy_records) {
-        k_prologue<2><<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
+        k_prologue<2><<<(unsigned)npb, kProThreads, 0, c->stream>>>(
             c->S, c->d_clu, bc, x, vel, m, c->mrec, c->drec, c->nflag, c->blk, nullptr, 0);
         c->launches += 1;
         return cudaGetLastError();
     }
     const bool mixed = c->p.precision == PN_MIXED;
     if (mixed)
-        k_prologue<0><<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
+        k_prologue<0><<<(unsigned)npb, kProThreads, 0, c->stream>>>(
             c->S, c->d_clu, bc, x, vel, m, c->mrec, c->drec, c->nflag, c->blk, c->wcount,
             packed_loc(c) ? 1 : 0);
     else
-        k_prologue<1><<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
+        k_prologue<1><<<(unsigned)npb, kProThreads, 0, c->stream>>>(
             c->S, c->d_clu, bc, x, vel, m, c->mrec, c->drec, c->nflag, c->blk, c->wcount, 0);
     c->launches += 1;
     cudaError_t e = cudaGetLastError();
@@ -2210,8 +2225,8 @@ cudaError_t launch_energy_on(cudaStream_t st, int64_t S, const Clu *clu, const d
                              const double *v, const double *m, double4_32a *drec, double *part,
                              double *blk, double *out)
 {
-    const int64_t nb = S / kGlueThreads;
-    k_prologue<2><<<(unsigned)nb, kGlueThreads, 0, st>>>(S, clu, nullptr, x, v, m, nullptr, drec,
+    const int64_t nb = S / kProThreads;
+    k_prologue<2><<<(unsigned)nb, kProThreads, 0, st>>>(S, clu, nullptr, x, v, m, nullptr, drec,
                                                          nullptr, nullptr, nullptr, 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
