@@ -31,21 +31,41 @@ __device__ __forceinline__ void block_sum(double (&val)[K], double (*sh)[BT])
     }
 }
 
-// Sum per-block partials blk[b*K + k] over b in a fixed order (one block).
+// Sum per-block partials blk[b*K + k] over b in a fixed order (one block of
+// kGlueThreads threads; the totals land in sh[k][0]).  Warp w sums the
+// columns k = w, w + 8, ...: lane l adds rows l, l + 32, ... into four
+// accumulators (row index mod 128 picks one), which are combined and then
+// reduced across the lanes by shuffles -- one block barrier in all, where a
+// shared-memory tree over the threads waits at eight.
 template <int K>
 __device__ __forceinline__ void sum_blocks(const double *__restrict__ blk, int64_t nblk,
                                            double (*sh)[kGlueThreads])
 {
-    double v[K];
+    constexpr int NW = kGlueThreads / 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = wid; k < K; k += NW) {
+        double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+        int64_t b = lane;
+        for (; b + 96 < nblk; b += 128) {
+            v0 += blk[b * K + k];
+            v1 += blk[(b + 32) * K + k];
+            v2 += blk[(b + 64) * K + k];
+            v3 += blk[(b + 96) * K + k];
+        }
+        if (b < nblk)
+            v0 += blk[b * K + k];
+        if (b + 32 < nblk)
+            v1 += blk[(b + 32) * K + k];
+        if (b + 64 < nblk)
+            v2 += blk[(b + 64) * K + k];
+        double v = (v0 + v1) + (v2 + v3);
 #pragma unroll
-    for (int k = 0; k < K; ++k)
-        v[k] = 0.0;
-    for (int64_t b = threadIdx.x; b < nblk; b += kGlueThreads) {
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-            v[k] += blk[b * K + k];
+        for (int o = 16; o > 0; o >>= 1)
+            v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0)
+            sh[k][0] = v;
     }
-    block_sum<K>(v, sh);
+    __syncthreads();
 }
 
 __device__ __forceinline__ void flag_nonfinite(const double a[3], int *flag,

@@ -1592,17 +1592,28 @@ k_epilogue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
                              x[3 * i + 2] - x[3 * hb + 2]};
         const double vv[3] = {vel[3 * i], vel[3 * i + 1], vel[3 * i + 2]};
         double s1[kP1Vals], s2[kP2Vals];
-        for (int k = 0; k < kP1Vals; ++k) {
-            double acc = 0.0;
-            for (int s = 0; s < js1; ++s)
-                acc += p1[((int64_t)s * kP1Vals + k) * S + t];
-            s1[k] = acc;
-        }
-        for (int k = 0; k < kP2Vals; ++k) {
-            double acc = 0.0;
-            for (int s = 0; s < js2; ++s)
-                acc += p2[((int64_t)s * kP2Vals + k) * S + t];
-            s2[k] = acc;
+        if (js1 == 1 && js2 == 1) {
+            // one partial set per pass (the fused kernels): every load issued
+            // before the first use
+#pragma unroll
+            for (int k = 0; k < kP1Vals; ++k)
+                s1[k] = p1[(int64_t)k * S + t];
+#pragma unroll
+            for (int k = 0; k < kP2Vals; ++k)
+                s2[k] = p2[(int64_t)k * S + t];
+        } else {
+            for (int k = 0; k < kP1Vals; ++k) {
+                double acc = 0.0;
+                for (int s = 0; s < js1; ++s)
+                    acc += p1[((int64_t)s * kP1Vals + k) * S + t];
+                s1[k] = acc;
+            }
+            for (int k = 0; k < kP2Vals; ++k) {
+                double acc = 0.0;
+                for (int s = 0; s < js2; ++s)
+                    acc += p2[((int64_t)s * kP2Vals + k) * S + t];
+                s2[k] = acc;
+            }
         }
         StarSums<double> ss;
         for (int k = 0; k < 3; ++k) {
