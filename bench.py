@@ -252,7 +252,7 @@ def config_of(w, precision, args):
 # section marker), so that a committed ncu traffic figure stays valid only
 # while that kernel's own source is unchanged.
 _FUSED_REGION = ("// The pair terms, shared by the two-pass and the fused kernels.",
-                 "// ------------------------------------------------ pair kernels: double --")
+                 "// Sums, for every star slot, the stream-K segments that cover its target")
 _KERNEL_REGIONS = {"fused_mixed": _FUSED_REGION, "fused_packed": _FUSED_REGION}
 
 

@@ -38,6 +38,7 @@ constexpr int kPad = 512;
 constexpr int kGlueThreads = 256;
 constexpr int kEpiThreads = 64;    // epilogue blocks: FP64-heavy per star, so spread over every SM
 constexpr int kProThreads = 64;    // prologue blocks, likewise (one partial-sum row per block)
+constexpr int kGatherThreads = 64; // stream-K gather blocks, likewise
 
 // Values per star written by each pair kernel into its partial-sum buffer.
 constexpr int kP1Vals = 6;         // N (3), U, Z, Wr

@@ -1106,27 +1106,28 @@ k_stage_sources(int64_t S, const float4 *__restrict__ rec, float4 *__restrict__ 
 // per staged record; with `perm` the kernel ran on the spatial order and
 // position t belongs to slot perm[t].  blockIdx.y splits a star's values
 // over three threads: 0 the pass-1 values (and Wr), 1 and 2 five pass-2
-// values each.
+// values each.  Blocks of kGatherThreads slots: the FP64 adds of the segment
+// sums spread over every SM at small N.
 template <int P, int NV, int RV>
-__global__ void __launch_bounds__(kGlueThreads)
+__global__ void __launch_bounds__(kGatherThreads)
 k_fused_gather(const double *__restrict__ part, int64_t S, const Clu *__restrict__ clu,
                const int *__restrict__ blk_clu, int64_t total_units, int64_t G, int tile,
                const float4 *__restrict__ srec, const int *__restrict__ perm,
                const int64_t *__restrict__ wb, double *__restrict__ p1, double *__restrict__ p2)
 {
     constexpr int TI = kMixThreads * P;
-    const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
+    const int64_t t = (int64_t)blockIdx.x * kGatherThreads + threadIdx.x;
     if (t >= S)
         return;
-    const Clu C = clu[cluster_of_block(blk_clu, blockIdx.x)];
+    const Clu C = clu[cluster_of_block(blk_clu, (int64_t)blockIdx.x * kGatherThreads / kGlueThreads)];
     const int64_t ntiles = C.ns_pad / tile;
     const int64_t ib = (t - C.slot0) / TI;
     const int64_t gtb = t / TI;                                 // global target block
     const int lt = (int)(t - gtb * TI);
     const int64_t U0 = C.unit0 + ib * ntiles, U1 = U0 + ntiles;
-    // worker b owns units [bound(b), bound(b + 1)): equal counts, or the
-    // cost-balanced boundaries wb of the spatial order
-    auto bound = [&](int64_t q) { return wb ? wb[q] : q * total_units / G; };
+    // worker b owns units [bound(b), bound(b + 1)): equal counts,
+    // bound(q) = q * total_units / G, or the cost-balanced boundaries wb of
+    // the spatial order
     int64_t b;
     if (wb) {                                   // last worker with wb[b] <= U0
         int64_t lo = 0, hi = G - 1;
@@ -1152,17 +1153,53 @@ k_fused_gather(const double *__restrict__ part, int64_t S, const Clu *__restrict
 #pragma unroll
     for (int k = 0; k < NG; ++k)
         acc[k] = 0.0;
-    for (; b < G; ++b) {
-        const int64_t bu0 = bound(b), bu1 = bound(b + 1);
-        if (bu0 >= U1)
-            break;
-        if (bu1 <= U0 || bu0 == bu1)
-            continue;
-        const double *in = part + (gtb + b) * (int64_t)(NV * TI) + (int64_t)k0 * TI + lt;
+    // equal counts: bound(q + 1) from bound(q) by the quotient and remainder
+    // of total_units / G (no 64-bit division per worker)
+    int64_t bu0, r = 0, base = 0, rem = 0;
+    if (wb) {
+        bu0 = wb[b];
+    } else {
+        const int64_t num = b * total_units;
+        bu0 = num / G;
+        r = num - bu0 * G;
+        base = total_units / G;
+        rem = total_units - base * G;
+    }
+    // four workers' segments loaded before they are added, in worker order
+    // (a worker that does not cover the block, or owns no unit, adds zeros)
+    constexpr int kBatch = 4;
+    for (bool more = true; more && b < G; b += kBatch) {
+        double tmp[kBatch][NG];
 #pragma unroll
-        for (int k = 0; k < NG; ++k)
-            if (k < nk)
-                acc[k] += in[k * TI];
+        for (int u = 0; u < kBatch; ++u) {
+            const int64_t w = b + u;
+            int64_t bu1 = bu0;
+            if (w < G) {
+                if (wb) {
+                    bu1 = wb[w + 1];
+                } else {
+                    bu1 = bu0 + base;
+                    r += rem;
+                    if (r >= G) {
+                        r -= G;
+                        ++bu1;
+                    }
+                }
+            }
+            const bool ok = w < G && bu0 < U1 && bu1 > U0 && bu1 > bu0;
+            if (w + 1 >= G || bu1 >= U1)
+                more = false;
+            const double *in = part + (gtb + w) * (int64_t)(NV * TI) + (int64_t)k0 * TI + lt;
+#pragma unroll
+            for (int k = 0; k < NG; ++k)
+                tmp[u][k] = ok && k < nk ? in[k * TI] : 0.0;
+            bu0 = bu1;
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u)
+#pragma unroll
+            for (int k = 0; k < NG; ++k)
+                acc[k] += tmp[u][k];
     }
     const int64_t ts = perm ? (int64_t)perm[t] : t;
     if (g > 0) {
@@ -1997,7 +2034,7 @@ static cudaError_t launch_fused_p(pn_ctx *c, const Layout &L, const float4 *rec)
         cudaEventRecord(end, c->stream);
     if (e != cudaSuccess)
         return e;
-    k_fused_gather<P, kFusedVals, 0><<<dim3((unsigned)(c->S / kGlueThreads), 3), kGlueThreads, 0, c->stream>>>(
+    k_fused_gather<P, kFusedVals, 0><<<dim3((unsigned)(c->S / kGatherThreads), 3), kGatherThreads, 0, c->stream>>>(
         c->part + L.seg, c->S, c->d_clu, blk_table(c), c->fused_units, c->fused_G, kMixTile,
         nullptr, nullptr, nullptr, c->part + L.p1, c->part + L.p2);
     c->launches += 1;
@@ -2026,7 +2063,7 @@ static cudaError_t launch_packed_form(pn_ctx *c, const Layout &L, const float4 *
     if (e != cudaSuccess)
         return e;
     k_fused_gather<2 * NP, kPackSums, pack_vals<(FORM >= 1)>()>
-        <<<dim3((unsigned)(c->S / kGlueThreads), 3), kGlueThreads, 0, c->stream>>>(
+        <<<dim3((unsigned)(c->S / kGatherThreads), 3), kGatherThreads, 0, c->stream>>>(
             c->part + L.seg, c->S, c->d_clu, blk_table(c), c->fused_units, c->fused_G, kPackTile,
             srec, perm, wb, c->part + L.p1, c->part + L.p2);
     c->launches += 1;
