@@ -102,7 +102,8 @@ class ClockSampler:
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,"
+              "clocks.mem")
 
     def __init__(self, index: int):
         self.index = index
@@ -136,7 +137,7 @@ class ClockSampler:
     def summary(self):
         if self.proc is None or not os.path.exists(self.path):
             return None
-        sm, smax, reasons = [], [], set()
+        sm, smax, mem, reasons = [], [], [], set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
@@ -150,11 +151,19 @@ class ClockSampler:
             for name, val in zip(names, parts[4:8]):
                 if val.lower().startswith("active"):
                     reasons.add(name)
+            if len(parts) > 8:
+                try:
+                    mem.append(float(parts[8]))
+                except ValueError:
+                    pass
         if not sm:
             return None
         load = [s for s in sm if s > 0.5 * max(sm)]
-        return {"sm_mhz": float(np.median(load)), "sm_max_mhz": float(max(smax)),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        out = {"sm_mhz": float(np.median(load)), "sm_max_mhz": float(max(smax)),
+               "reasons": sorted(reasons), "samples": len(sm)}
+        if mem:
+            out["mem_mhz"] = float(np.median(mem))
+        return out
 
 
 # ---------------------------------------------------------- CPU oracle --
