@@ -33,17 +33,18 @@ __device__ __forceinline__ Dual dual(double v, double d) { return {v, d}; }
 //   J0 = (d, m)  J1 = (d', 0)  J2 = (v, R^2)  J3 = (v', (R^2)')
 //   J4 = (-e/1.5, C)  J5 = (-(e/1.5)', C')  J6 = (w, 0)  J7 = (w', 0)
 // (primes: derivatives along the trajectory; C = c/1.5 - 4/3 |v|^2, c, e, w
-// as in the acceleration kernels).  Per-block Dual sums of the cluster sums.
-__global__ void __launch_bounds__(kGlueThreads)
+// as in the acceleration kernels).  Per-block Dual sums of the cluster sums
+// (blocks of kProThreads slots, spread over every SM).
+__global__ void __launch_bounds__(kProThreads)
 k_jerk_prologue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_clu,
                 const double *__restrict__ x, const double *__restrict__ v,
                 const double *__restrict__ m, const double *__restrict__ a,
                 double4_32a *__restrict__ rec, double *__restrict__ blk)
 // a == nullptr: values only (all derivatives zero), for the adjoint
 {
-    __shared__ double sh[2 * kJVals][kGlueThreads];
-    const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
-    const Clu C = clu[cluster_of_block(blk_clu, blockIdx.x)];
+    __shared__ double sh[2 * kJVals][kProThreads];
+    const int64_t t = (int64_t)blockIdx.x * kProThreads + threadIdx.x;
+    const Clu C = clu[cluster_of_block(blk_clu, (int64_t)blockIdx.x * kProThreads / kGlueThreads)];
     const int64_t lt = t - C.slot0;
     double g[2 * kJVals];
 #pragma unroll
@@ -95,7 +96,7 @@ k_jerk_prologue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ 
         for (int k = 1; k < kJRec; ++k)
             rec[k * S + t] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
     }
-    block_sum<2 * kJVals>(g, sh);
+    block_sum<2 * kJVals, kProThreads>(g, sh);
     if (threadIdx.x < 2 * kJVals)
         blk[(int64_t)blockIdx.x * 2 * kJVals + threadIdx.x] = sh[threadIdx.x][0];
 }
@@ -107,8 +108,8 @@ k_jerk_globals(const Clu *__restrict__ clu, const double *__restrict__ blk,
 {
     __shared__ double sh[2 * kJVals][kGlueThreads];
     const Clu C = clu[blockIdx.x];
-    sum_blocks<2 * kJVals>(blk + (C.slot0 / kGlueThreads) * 2 * kJVals,
-                           C.ns_pad / kGlueThreads, sh);
+    sum_blocks<2 * kJVals>(blk + (C.slot0 / kProThreads) * 2 * kJVals,
+                           C.ns_pad / kProThreads, sh);
     if (threadIdx.x < 2 * kJVals)
         glob[(int64_t)blockIdx.x * 2 * kJVals + threadIdx.x] = sh[threadIdx.x][0];
 }
@@ -491,8 +492,8 @@ k_jerk_pairs_packed(const float4 *__restrict__ srec, int64_t S, const Clu *__res
 
 // Per star: the split partials summed, star_eqs on Duals; the value is the
 // acceleration and the derivative the jerk.  Per-block sums of the hole's
-// terms (3 values, 3 derivatives) go to blk.
-__global__ void __launch_bounds__(kGlueThreads)
+// terms (3 values, 3 derivatives) go to blk, one row per kProThreads slots.
+__global__ void __launch_bounds__(kProThreads)
 k_jerk_epilogue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_clu,
                 const double *__restrict__ x, const double *__restrict__ v,
                 const double *__restrict__ m, const double *__restrict__ a,
@@ -500,9 +501,9 @@ k_jerk_epilogue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ 
                 double *__restrict__ jerk, int *flag, unsigned long long *flag_step,
                 unsigned long long step, double *__restrict__ blk)
 {
-    __shared__ double sh[6][kGlueThreads];
-    const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
-    const int k_clu = cluster_of_block(blk_clu, blockIdx.x);
+    __shared__ double sh[6][kProThreads];
+    const int64_t t = (int64_t)blockIdx.x * kProThreads + threadIdx.x;
+    const int k_clu = cluster_of_block(blk_clu, (int64_t)blockIdx.x * kProThreads / kGlueThreads);
     const Clu Cl = clu[k_clu];
     const double *glob = globs + (int64_t)k_clu * 2 * kJVals;
     const int64_t lt = t - Cl.slot0;
@@ -557,7 +558,7 @@ k_jerk_epilogue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ 
             bh6[3 + k] = bh[k].d;
         }
     }
-    block_sum<6>(bh6, sh);
+    block_sum<6, kProThreads>(bh6, sh);
     if (threadIdx.x < 6)
         blk[(int64_t)blockIdx.x * 6 + threadIdx.x] = sh[threadIdx.x][0];
 }
@@ -570,7 +571,7 @@ k_jerk_hole(const Clu *__restrict__ clu, const double *__restrict__ blk,
 {
     __shared__ double sh[6][kGlueThreads];
     const Clu C = clu[blockIdx.x];
-    sum_blocks<6>(blk + (C.slot0 / kGlueThreads) * 6, C.ns_pad / kGlueThreads, sh);
+    sum_blocks<6>(blk + (C.slot0 / kProThreads) * 6, C.ns_pad / kProThreads, sh);
     if (threadIdx.x == 0) {
         const double *glob = globs + (int64_t)blockIdx.x * 2 * kJVals;
         double j0[3];
@@ -1547,9 +1548,9 @@ static int64_t jerk_pack_splits(const pn_ctx *c)
 
 size_t jerk_buffer_doubles(const pn_ctx *c)
 {
-    const int64_t S = c->S, nglue = S / kGlueThreads;
+    const int64_t S = c->S, npb = S / kProThreads;
     return (size_t)(kJRec * 4 * S + jerk_part_splits(c) * 2 * kFusedVals * S +
-                    nglue * 2 * kJVals + (int64_t)c->nclu * 2 * kJVals + nglue * 6 +
+                    npb * 2 * kJVals + (int64_t)c->nclu * 2 * kJVals + npb * 6 +
                     32 * S);   // + staged float records of the packed pass (16 float4)
 }
 
@@ -1561,13 +1562,14 @@ cudaError_t launch_jerk(pn_ctx *c, const double *x, const double *v, const doubl
     double *base = c->jbuf;
     double4_32a *rec = reinterpret_cast<double4_32a *>(base);
     double *part = base + kJRec * 4 * S;
+    const int64_t npb = S / kProThreads;      // prologue / epilogue blocks
     double *blk = part + (int64_t)js * 2 * kFusedVals * S;
-    double *glob = blk + nglue * 2 * kJVals;
+    double *glob = blk + npb * 2 * kJVals;
     double *bhb = glob + (int64_t)c->nclu * 2 * kJVals;
     const int *bc = c->nclu > 1 ? c->blk_clu : nullptr;
     const unsigned long long step = (unsigned long long)c->step_counter;
-    k_jerk_prologue<<<(unsigned)nglue, kGlueThreads, 0, c->stream>>>(S, c->d_clu, bc, x, v, m, a,
-                                                                    rec, blk);
+    k_jerk_prologue<<<(unsigned)npb, kProThreads, 0, c->stream>>>(S, c->d_clu, bc, x, v, m, a,
+                                                                  rec, blk);
     c->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
@@ -1581,7 +1583,7 @@ cudaError_t launch_jerk(pn_ctx *c, const double *x, const double *v, const doubl
     if (c->p.precision == PN_MIXED) {
         // single-precision dual pair sums on staged float records (after the
         // hole terms)
-        float4 *srec = reinterpret_cast<float4 *>(bhb + nglue * 6);
+        float4 *srec = reinterpret_cast<float4 *>(bhb + npb * 6);
         const int jp = (int)jerk_pack_splits(c);
         static bool carveout = false;     // 3 blocks of 32 KB per SM
         if (!carveout) {
@@ -1605,7 +1607,7 @@ cudaError_t launch_jerk(pn_ctx *c, const double *x, const double *v, const doubl
                       kGlueThreads, 0, c->stream>>>(S, 2 * kFusedVals, jsum, part);
         c->launches += 1;
     }
-    k_jerk_epilogue<<<(unsigned)nglue, kGlueThreads, 0, c->stream>>>(
+    k_jerk_epilogue<<<(unsigned)npb, kProThreads, 0, c->stream>>>(
         S, c->d_clu, bc, x, v, m, a, part, 1, glob, jerk, c->flag, c->flag_step, step, bhb);
     c->launches += 1;
     if ((e = cudaGetLastError()) != cudaSuccess)
@@ -1650,7 +1652,7 @@ cudaError_t launch_accel_vjp(pn_ctx *c, const double *x, const double *v, const 
     double4_32a *rec = reinterpret_cast<double4_32a *>(c->jbuf);
     double *part = c->jbuf + kJRec * 4 * S;
     double *jblk = part + (int64_t)js * 2 * kFusedVals * S;
-    double *jglob = jblk + nglue * 2 * kJVals;
+    double *jglob = jblk + S / kProThreads * 2 * kJVals;
     double *sbar = c->abuf, *kbar = sbar + 16 * S, *tpart = kbar + 6 * S;
     double *spart = tpart + (int64_t)js * 6 * S;
     // staged targets of the packed source sweep (13 float4 per slot, 16-byte aligned)
@@ -1666,8 +1668,8 @@ cudaError_t launch_accel_vjp(pn_ctx *c, const double *x, const double *v, const 
     cudaError_t e;
     // forward: records and cluster sums (values); the 16 pair sums in double,
     // or (mixed) by the fused pair kernel on the single-precision records
-    k_jerk_prologue<<<(unsigned)nglue, kGlueThreads, 0, c->stream>>>(S, c->d_clu, bc, x, v, m,
-                                                                    nullptr, rec, jblk);
+    k_jerk_prologue<<<(unsigned)(S / kProThreads), kProThreads, 0, c->stream>>>(
+        S, c->d_clu, bc, x, v, m, nullptr, rec, jblk);
     k_jerk_globals<<<c->nclu, kGlueThreads, 0, c->stream>>>(c->d_clu, jblk, jglob);
     c->launches += 2;
     const double *fwd = part;
