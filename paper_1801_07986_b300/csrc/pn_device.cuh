@@ -21,13 +21,41 @@ __device__ __forceinline__ void block_sum(double (&val)[K], double (*sh)[BT])
     for (int k = 0; k < K; ++k)
         sh[k][t] = val[k];
     __syncthreads();
-    for (int s = BT / 2; s > 0; s >>= 1) {
-        if (t < s) {
-#pragma unroll
-            for (int k = 0; k < K; ++k)
-                sh[k][t] += sh[k][t + s];
+    // NPART row segments of RP rows per column, every segment starting
+    // inside the block (NPART * K <= BT threads)
+    constexpr int NP0 = BT / K;
+    constexpr int RP = NP0 >= 1 ? (BT + NP0 - 1) / NP0 : BT;
+    constexpr int NPART = (BT + RP - 1) / RP;
+    static_assert(NPART * K <= BT || NP0 < 2, "segment threads exceed the block");
+    if constexpr (NP0 >= 2) {
+        // thread (q, k) sums rows [q RP, (q + 1) RP) of column k in order,
+        // then thread k adds the segment sums in order: two barriers, and
+        // every thread of the first K * NPART does FP64 work
+        if (t < K * NPART) {
+            const int k = t % K, q = t / K;
+            const int r0 = q * RP, r1 = r0 + RP < BT ? r0 + RP : BT;
+            double acc = sh[k][r0];
+            for (int r = r0 + 1; r < r1; ++r)
+                acc += sh[k][r];
+            sh[k][r0] = acc;
         }
         __syncthreads();
+        if (t < K) {
+            double acc = sh[t][0];
+            for (int q = 1; q < NPART; ++q)
+                acc += sh[t][q * RP];
+            sh[t][0] = acc;
+        }
+        __syncthreads();
+    } else {
+        for (int s = BT / 2; s > 0; s >>= 1) {
+            if (t < s) {
+#pragma unroll
+                for (int k = 0; k < K; ++k)
+                    sh[k][t] += sh[k][t + s];
+            }
+            __syncthreads();
+        }
     }
 }
 
