@@ -327,9 +327,15 @@ pn_status pn_launch_count(pn_ctx *ctx, int64_t *count);
  * without waiting.  The scratch is a fixed array inside the library (about
  * 5 MiB on every device that loads libpn, held until exit), shared by all
  * calls: calls whose work overlaps on the GPU race on it and must be
- * serialised by the caller.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  Errors: PN_EINVAL, PN_ECUDA.
+ * serialised by the caller; each call writes every scratch byte it reads,
+ * so nothing carries over from the previous call.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) and
+ * caches it for the process; make that first call before any stream
+ * capture, and do not call this entry point on a device after
+ * cudaDeviceReset (the cached address then no longer exists).  The call
+ * reads no host memory after it returns: its one-cluster table is passed
+ * by value to a kernel.  Errors: PN_EINVAL (bad arguments, n too large),
+ * PN_ECUDA.
  */
 #define PN_NOALLOC_MAX_BODIES 16384
 pn_status pn_energy_noalloc(int device, void *cuda_stream, int64_t n, double G, double c,

@@ -2282,7 +2282,9 @@ cudaError_t launch_energy_on(cudaStream_t st, int64_t S, const Clu *clu, const d
     k_energy_pairs<<<(unsigned)(S / kF64Threads), kF64Threads, 0, st>>>(drec, S, clu, nullptr, part);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
-    k_energy_epilogue<<<(unsigned)nb, kGlueThreads, 0, st>>>(S, clu, nullptr, x, v, m, part, blk);
+    // one kGlueThreads-slot block per row of blk (S / kGlueThreads rows)
+    k_energy_epilogue<<<(unsigned)(S / kGlueThreads), kGlueThreads, 0, st>>>(S, clu, nullptr, x, v,
+                                                                            m, part, blk);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
     k_energy_final<<<1, kGlueThreads, 0, st>>>(clu, blk, v, m, out);

@@ -13,10 +13,14 @@
 // libpn holds it (kScratchBytes, about 5 MiB) until the process exits.  Its
 // host-side name is only a stand-in, so its device address is looked up
 // with cudaGetSymbolAddress once per device (on the first call on that
-// device, with that device current) and cached.  Every call shares the
-// array; each call writes every scratch byte it later reads, so nothing
-// needs clearing, but calls whose work overlaps on the GPU (other streams,
-// or another thread) race on the array.
+// device, with that device current) and cached; cudaDeviceReset on that
+// device invalidates the cached address, so the entry point must not be
+// called on a device after it was reset.  Every call shares the array;
+// each call writes every scratch byte it later reads, so nothing needs
+// clearing, but calls whose work overlaps on the GPU (other streams, or
+// another thread) race on the array.  The one-entry cluster table is
+// written by a kernel that takes it by value, so no call reads host memory
+// after it returns.
 #include <cmath>
 #include <mutex>
 
@@ -36,7 +40,29 @@ constexpr int64_t kPartOff = (kRecOff + kRecBytes + kAlign - 1) / kAlign * kAlig
 constexpr int64_t kBlkOff = (kPartOff + kPartBytes + kAlign - 1) / kAlign * kAlign;
 constexpr int64_t kScratchBytes = (kBlkOff + kBlkBytes + kAlign - 1) / kAlign * kAlign;
 
+// Each region holds what launch_energy_on writes for the largest padded
+// star count: the energy records (2 double4 per slot), the pair sums
+// (kEVals per slot) and one row of kEBlockVals per kGlueThreads-slot block.
+static_assert(kPadMax % pn::kGlueThreads == 0 && kPadMax % pn::kF64Threads == 0,
+              "launch_energy_on's grids cover whole blocks of the padded slots");
+static_assert(kRecOff + kRecBytes <= kPartOff && kPartOff + kPartBytes <= kBlkOff &&
+                  kBlkOff + kBlkBytes <= kScratchBytes,
+              "scratch regions must not overlap");
+static_assert((int64_t)sizeof(pn::Clu) <= kRecOff, "cluster table fits before the records");
+
 static __device__ __align__(256) unsigned char g_energy_scratch[kScratchBytes];
+
+// Bytes that launch_energy_on writes into each region for S padded slots
+// (kept next to its launch shapes: records 2 S double4, pair sums kEVals S
+// doubles, epilogue rows S / kGlueThreads of kEBlockVals doubles).
+bool regions_fit(int64_t S)
+{
+    return 2 * S * (int64_t)sizeof(double4_32a) <= kRecBytes &&
+           (int64_t)pn::kEVals * S * 8 <= kPartBytes &&
+           (S / pn::kGlueThreads) * pn::kEBlockVals * 8 <= kBlkBytes;
+}
+
+__global__ void k_put_clu(pn::Clu *dst, pn::Clu src) { *dst = src; }
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
@@ -94,9 +120,14 @@ extern "C" pn_status pn_energy_noalloc(int device, void *cuda_stream, int64_t n,
     clu.inv_c2 = std::isinf(c) ? 0.0 : 1.0 / (c * c);
     clu.eps2 = eps * eps;
     clu.r_near = -1.0;
+    if (!regions_fit(clu.ns_pad)) {
+        if (prev >= 0 && prev != device)
+            cudaSetDevice(prev);
+        return fail(PN_EINVAL, "pn_energy_noalloc: padded size exceeds the scratch regions");
+    }
     pn::Clu *dclu = reinterpret_cast<pn::Clu *>(b + kCluOff);
-    // the table entry is staged from this stack copy before the call returns
-    e = cudaMemcpyAsync(dclu, &clu, sizeof clu, cudaMemcpyHostToDevice, (cudaStream_t)cuda_stream);
+    k_put_clu<<<1, 1, 0, (cudaStream_t)cuda_stream>>>(dclu, clu);
+    e = cudaGetLastError();
     if (e == cudaSuccess)
         e = pn::launch_energy_on((cudaStream_t)cuda_stream, clu.ns_pad, dclu, x, v, m,
                                  reinterpret_cast<double4_32a *>(b + kRecOff),

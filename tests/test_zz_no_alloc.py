@@ -50,18 +50,38 @@ def _check(got, want, v, m):
     assert np.abs(got[2:] - want[2:]).max() <= TOL * pscale
 
 
+def _state(n, seed):
+    x, v, m = make_cluster(n, 0.1, seed)
+    v = v.copy()
+    v[0] = [0.01, -0.005, 0.02]          # a moving hole exercises the v_1 terms
+    return x, v, m
+
+
 def test_noalloc_matches_pn_energy_on_two_calls_in_a_row():
     states = []
     for n, seed, c, eps in ((1500, 3, 12.0, 1e-3), (777, 4, math.inf, 1e-4)):
-        x, v, m = make_cluster(n, 0.1, seed)
-        v = v.copy()
-        v[0] = [0.01, -0.005, 0.02]
+        x, v, m = _state(n, seed)
         states.append((torch.tensor(x, device=DEV), torch.tensor(v, device=DEV),
                        torch.tensor(m, device=DEV), c, eps))
     # the larger call first, so stale scratch would show in the second one
     for X, V, M, c, eps in states:
         want = _ref(X, V, M, c, eps)
         got = _noalloc_c_abi(X, V, M, c, eps)
+        _check(got, want, V, M)
+
+
+def test_noalloc_at_the_maximum_size_then_above_4096_against_oracle():
+    """The full scratch (PN_NOALLOC_MAX_BODIES bodies) and then a size above
+    4096 bodies, in that order: each against pn_energy and the FP64 oracle
+    (Eq. 7 and Eq. 8)."""
+    import oracle
+    for n, seed, c, eps in ((pn.PN_NOALLOC_MAX_BODIES, 5, 50.0, 1e-4), (5000, 6, 20.0, 1e-3)):
+        x, v, m = _state(n, seed)
+        X, V, M = (torch.tensor(a, device=DEV) for a in (x, v, m))
+        got = _noalloc_c_abi(X, V, M, c, eps)
+        _check(got, _ref(X, V, M, c, eps), V, M)
+        o = oracle.energy(x, v, m, c=c, eps=eps)
+        want = np.concatenate([[o["E_N"], o["E_PN"]], o["P_N"], o["P_PN"]])
         _check(got, want, V, M)
 
 
