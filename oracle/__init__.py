@@ -14,6 +14,7 @@ Functions follow the paper (Tatekawa, arXiv:1801.07986):
 
 * :func:`accel`      Section 2, Eq. 1-6 (Eq. 10 softening between stars)
 * :func:`accel_rows` the same for selected targets
+* :func:`bh_partial` the hole's sums of Eq. 1-3 over a range of outer stars
 * :func:`energy`     Section 2, Eq. 7 and Eq. 8
 * :func:`step`       kick-drift-kick leapfrog, force at the predicted velocity
 * :func:`rk4_step`   the paper's classical fourth-order Runge-Kutta (Section 4)
@@ -74,6 +75,7 @@ def _load():
             lib.orc_accel.argtypes = [i64, p, p, p, d, d, d, p]
             lib.orc_accel_rows.argtypes = [i64, p, p, p, d, d, d, i64, p, p]
             lib.orc_bh_rows.argtypes = [i64, p, p, p, d, d, i64, p, p]
+            lib.orc_bh_partial.argtypes = [i64, p, p, p, d, d, i64, i64, p]
             lib.orc_newton_accel.argtypes = [i64, p, p, d, d, p]
             lib.orc_energy.argtypes = [i64, p, p, p, d, d, d, p]
             lib.orc_eih_accel.argtypes = [i64, p, p, p, d, d, p]
@@ -157,6 +159,19 @@ def bh_rows(x, v, m, js, G=1.0, eps=0.0):
     if rc:
         raise ValueError(f"orc_bh_rows failed ({rc})")
     return out
+
+
+def bh_partial(x, v, m, j0, j1, G=1.0, eps=0.0):
+    """The hole's sums of Eq. 1-3 over the outer stars j in [j0, j1): (the
+    Newtonian sum, the 1PN sums before 1/c^2), each a 3-vector.  Over
+    [1, n) the hole's acceleration is newt + pn / c^2."""
+    x, v, m, n = _state(x, v, m)
+    out = np.empty(6)
+    rc = _load().orc_bh_partial(n, _ptr(x), _ptr(v), _ptr(m), G, eps, int(j0), int(j1),
+                                _ptr(out))
+    if rc:
+        raise ValueError("orc_bh_partial failed")
+    return out[:3].copy(), out[3:].copy()
 
 
 def newton_accel(x, m, G=1.0, eps=0.0):

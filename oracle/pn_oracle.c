@@ -97,6 +97,7 @@ int orc_get_threads(void)
 #define star_accel star_accel_cs
 #define bh_double_sum_row bh_double_sum_row_cs
 #define bh_accel bh_accel_cs
+#define bh_partial bh_partial_cs
 #include "pn_oracle_accel.inc"
 #undef REAL
 #undef SQRT
@@ -112,6 +113,7 @@ int orc_get_threads(void)
 #undef star_accel
 #undef bh_double_sum_row
 #undef bh_accel
+#undef bh_partial
 
 static int check_args(int64_t n, const void *x, const void *v, const void *m)
 {
@@ -224,6 +226,23 @@ int orc_accel_rows(int64_t n, const double *x, const double *v, const double *m,
     for (int64_t r = 0; r < nrows; ++r)
         if (targets[r] != 0)
             star_accel(n, x, v, m, G, inv_c2, eps, targets[r], a_rows + 3 * r);
+    return 0;
+}
+
+/* The heavy body's sums of Eq. 1-3 over the outer stars j in [j0, j1):
+ * out[0..2] the Newtonian sum, out[3..5] the 1PN sums before the 1/c^2
+ * factor (the hole's acceleration over [1, n) is out[0..2] + inv_c2
+ * out[3..5]).  Ranges that partition [1, n) add up to the whole. */
+int orc_bh_partial(int64_t n, const double *x, const double *v, const double *m,
+                   double G, double eps, int64_t j0, int64_t j1, double *out)
+{
+    if (check_args(n, x, v, m) || !out || j0 < 1 || j1 > n || j0 > j1)
+        return 1;
+    double *rows = (double *)calloc((size_t)(3 * n), sizeof(double));
+    if (!rows)
+        return 2;
+    bh_partial(n, x, v, m, G, eps, j0, j1, rows, out, out + 3);
+    free(rows);
     return 0;
 }
 

@@ -533,3 +533,28 @@ def test_thread_count_does_not_change_results(orc):
     a2 = orc.accel(x, v, m, c=10.0, eps=1e-3)
     e2 = orc.energy(x, v, m, c=10.0, eps=1e-3)["E"]
     assert np.array_equal(a1, a2) and e1 == e2
+
+
+def test_hole_partial_sums_partition_the_hole_acceleration(orc):
+    """The hole's sums of Eq. 1-3 over a range of outer stars: over every star
+    they are exactly the hole's acceleration (same operations), disjoint
+    ranges add up to it within rounding, and a range's Newtonian part equals
+    the Newtonian pull of those stars written out directly (Eq. 1)."""
+    n, c, eps = 400, 9.0, 1e-3
+    x, v, m = make_cluster(n, 0.1, 31)
+    a_hole = orc.accel(x, v, m, c=c, eps=eps)[0]
+    newt, pn = orc.bh_partial(x, v, m, 1, n, eps=eps)
+    inv_c2 = 1.0 / (c * c)
+    assert np.array_equal(newt + inv_c2 * pn, a_hole)
+    cuts = [1, 97, 250, 251, n]
+    parts = [orc.bh_partial(x, v, m, a, b, eps=eps) for a, b in zip(cuts[:-1], cuts[1:])]
+    nsum = sum(p[0] for p in parts)
+    psum = sum(p[1] for p in parts)
+    scale = sum(np.abs(p[0]) + inv_c2 * np.abs(p[1]) for p in parts)
+    assert np.all(np.abs(nsum + inv_c2 * psum - a_hole) <= 1e-14 * scale)
+    d = x[97:250] - x[0]
+    direct = (m[97:250, None] * d / np.linalg.norm(d, axis=1)[:, None] ** 3).sum(axis=0)
+    assert np.allclose(orc.bh_partial(x, v, m, 97, 250, eps=eps)[0], direct, rtol=1e-13,
+                       atol=0)
+    empty = orc.bh_partial(x, v, m, 5, 5, eps=eps)
+    assert not np.any(empty[0]) and not np.any(empty[1])
