@@ -50,7 +50,9 @@ typedef enum {
     PN_ECUDA = 3,         /* a CUDA runtime call failed                     */
     PN_ENONFINITE = 4,    /* a non-finite acceleration was produced         */
     PN_ETIMEOUT = 5,      /* a bounded device-side wait gave up             */
-    PN_EUNSUPPORTED = 6   /* the device is not an sm_103 part               */
+    PN_EUNSUPPORTED = 6,  /* the device is not an sm_103 part               */
+    PN_EDRIFT = 7,        /* the energy watchdog saw a drift above its limit */
+    PN_EINDEX = 8         /* debug build: a device index check failed       */
 } pn_status;
 
 enum { PN_FP64 = 0, PN_MIXED = 1 };            /* pn_params.precision */
@@ -239,15 +241,22 @@ pn_status pn_step_graph(pn_ctx *ctx, double *x, double *v, const double *m, doub
                         double dt, int64_t nsteps);
 
 /*
- * Autotuner of the fused pair kernel's launch shape (scalar kernel: targets
- * per thread x source-loop unroll; packed FP32x2 kernel: unroll): times each
- * candidate on the given state (a is overwritten with A(x, v)) and keeps the
- * fastest; results are cached per workload size bucket for the process.
- * out (may be NULL): [0] targets per thread, [1] unroll, [2] 1 if the result
- * came from the cache, [3] 1 for the packed FP32x2 kernel.  Waits.
+ * Autotuner of the fused pair kernel's launch shape: the scalar kernel's
+ * targets per thread x source-loop unroll, and the packed FP32x2 kernel's
+ * targets per thread x unroll x j-tile (sources per shared-memory tile, 64
+ * or 32) x one-tile buffers (6 or 4 at 64 sources, 8 at 32; fewer buffers
+ * leave room for more resident blocks; 32-source tiles only without the
+ * spatial order).  Times each candidate on the given state (a is
+ * overwritten with A(x, v)) and keeps the fastest.  Results are cached per
+ * (pair-work bucket, precision, one or many clusters) for the process and,
+ * when the environment variable PN_TUNE_CACHE names a file, in that file
+ * across processes.  out (may be NULL): [0] targets per thread, [1] unroll,
+ * [2] 1 if the result came from the cache, [3] 1 for the packed FP32x2
+ * kernel, [4] sources per tile, [5] one-tile buffers (0 for the scalar
+ * kernel).  Waits.
  */
 pn_status pn_tune(pn_ctx *ctx, const double *x, const double *v, const double *m, double *a,
-                  int64_t out[4]);
+                  int64_t out[6]);
 
 /*
  * pn_step on HOST arrays: copies x, v, m, a to device buffers owned by the
@@ -264,8 +273,12 @@ pn_status pn_step_host(pn_ctx *ctx, double *x, double *v, const double *m, doubl
  * host array out[8] (out[8 n_clusters] on a batched context, 8 per cluster):
  *   out[0]  Newtonian energy         out[1]    1/c^2 part of Eq. 7
  *   out[2..4] Newtonian momentum     out[5..7] 1/c^2 part of Eq. 8
- * (E = out[0] + out[1], P = out[2..4] + out[5..7]).  Waits for the stream.
- * Errors: PN_EINVAL, PN_ENONFINITE (pending from earlier steps).
+ * (E = out[0] + out[1], P = out[2..4] + out[5..7]).  The contract is these
+ * eight values per cluster: the Newtonian and 1PN parts are kept apart (a
+ * superset of E_N, E_1PN and P) so that a caller can follow each order's
+ * conservation.  Waits for the stream.
+ * Errors: PN_EINVAL, PN_ENONFINITE (pending from earlier steps), PN_EDRIFT
+ * (pending from the watchdog).
  */
 pn_status pn_energy(pn_ctx *ctx, const double *x, const double *v, const double *m,
                     double *out);
@@ -314,6 +327,28 @@ pn_status pn_get_launch(pn_ctx *ctx, int64_t out[8]);
 pn_status pn_launch_count(pn_ctx *ctx, int64_t *count);
 
 /*
+ * Energy-drift watchdog.  With rel_tol > 0, every `every` steps of pn_step,
+ * pn_step_graph and pn_step_host (counted by the context's step counter)
+ * the library evaluates Eq. 7 on the state, as pn_energy does, and compares
+ * each cluster's total E = E_N + E_1PN with its reference on the device:
+ * the first check after this call takes the reference, later ones trip when
+ * |E - E_ref| / |E_ref| > rel_tol (or is not finite).  A trip is reported
+ * by the next waiting call (pn_sync, pn_energy, pn_step_host) as PN_EDRIFT,
+ * with the first tripping step, the change and the cluster in the message;
+ * the reference stays, so later checks compare with it too.  This flags
+ * the failure mode Section 4 shows, an energy jump at a close scattering
+ * off the hole that the step does not resolve.  Each check costs one
+ * energy evaluation (an FP64 O(n^2) pair sum, about 15 steps' time of a
+ * mixed-precision context at n = 16384).  The adjoint's forward
+ * recomputations are not checked.  Calling again resets the references;
+ * rel_tol = 0 turns the watchdog off.  A captured pn_step_graph sequence is
+ * captured again after this call.  Allocates a few bytes on first use.
+ * Errors: PN_EINVAL (rel_tol < 0 or not finite, every < 1 with rel_tol > 0),
+ * PN_ENOMEM, PN_ECUDA.
+ */
+pn_status pn_set_watchdog(pn_ctx *ctx, double rel_tol, int64_t every);
+
+/*
  * Energy and momentum like pn_energy, for callers that cannot allocate
  * device memory (their GPU memory belongs to another allocator, or they
  * must not allocate after start-up): no context, no cudaMalloc.  The paper
@@ -360,6 +395,17 @@ void pn_destroy(pn_ctx *ctx);
 
 /* Library version, 100 * major + minor. */
 int pn_version(void);
+
+/*
+ * 1 in the debug build (libpn_debug.so, compiled with PN_DEBUG_CHECKS), 0
+ * otherwise.  In the debug build the kernels of the acceleration, step and
+ * energy paths check their global-memory indices against the buffers'
+ * extents: a failing check records the site and index and substitutes a
+ * valid index (no trap, no early exit), and the next waiting call returns
+ * PN_EINDEX with the site and index in the message.  The arithmetic is the
+ * release build's.
+ */
+int pn_debug_checks(void);
 
 #ifdef __cplusplus
 }

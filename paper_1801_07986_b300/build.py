@@ -16,6 +16,8 @@ SOURCES = [os.path.join(CSRC, f) for f in ("pn_kernels.cu", "pn_order.cu", "pn_d
 HEADERS = [os.path.join(CSRC, "pn_internal.h"), os.path.join(CSRC, "pn_device.cuh"),
            os.path.join(os.path.dirname(HERE), "include", "pn.h")]
 LIB = os.path.join(HERE, "libpn.so")
+# the debug build: kernels check their global-memory indices (PN_DEBUG_CHECKS)
+DEBUG_LIB = os.path.join(HERE, "libpn_debug.so")
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
               "-shared", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
@@ -28,27 +30,31 @@ def nvcc() -> str:
     return "nvcc"
 
 
-def stale() -> bool:
-    if not os.path.exists(LIB):
+def stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(s) > t for s in SOURCES + HEADERS)
 
 
-def build_library(force: bool = False, verbose: bool = False) -> str:
-    """Compile libpn.so if it is missing or older than its sources."""
-    if not force and not stale():
-        return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *NVCC_FLAGS, "-o", tmp, *SOURCES]
+def build_library(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Compile libpn.so (or, with debug, libpn_debug.so) if it is missing or
+    older than its sources."""
+    lib = DEBUG_LIB if debug else LIB
+    if not force and not stale(lib):
+        return lib
+    tmp = lib + f".tmp{os.getpid()}"
+    flags = NVCC_FLAGS + (["-DPN_DEBUG_CHECKS"] if debug else [])
+    cmd = [nvcc(), *flags, "-o", tmp, *SOURCES]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" + r.stdout + r.stderr)
     if verbose:
         sys.stderr.write(r.stderr)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build_library(force="--force" in sys.argv, verbose=True))
+    debug = "--debug" in sys.argv
+    print(build_library(force="--force" in sys.argv, verbose=not debug, debug=debug))

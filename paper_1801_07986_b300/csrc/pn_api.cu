@@ -124,7 +124,7 @@ void free_all(pn_ctx *c)
                     c->flag, c->wcount, c->units_cnt,
                     c->flag_step, c->hx, c->hv, c->hm, c->ha, c->nrec, c->ndrec, c->ncount,
                     c->nflag, c->rk_x, c->rk_v, c->rk_a, c->rk_sx, c->rk_sv, c->jbuf, c->hj0, c->hj1, c->abuf,
-                    c->d_clu,
+                    c->wd, c->wd_step, c->epi_done, c->d_clu,
                     c->blk_clu};
     for (void *b : bufs)
         if (b)
@@ -133,6 +133,12 @@ void free_all(pn_ctx *c)
         cudaGraphExecDestroy(c->graph_exec);
     if (c->cap_stream)
         cudaStreamDestroy(c->cap_stream);
+    if (c->side)
+        cudaStreamDestroy(c->side);
+    if (c->ev_fork)
+        cudaEventDestroy(c->ev_fork);
+    if (c->ev_join)
+        cudaEventDestroy(c->ev_join);
     delete[] c->hclu;
     if (c->timing_on || c->tm.ev0[0][0]) {
         for (int k = 0; k < pn::Timing::kKernels; ++k)
@@ -162,24 +168,62 @@ pn_status report_flag(pn_ctx *c)
     PN_CUDA(cudaMemcpyAsync(&step, c->flag_step, sizeof step, cudaMemcpyDeviceToHost, c->stream),
             "read non-finite step");
     PN_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
+#ifdef PN_DEBUG_CHECKS
+    {
+        unsigned long long site = 0, s2 = 0;
+        long long index = 0, i2 = 0;
+        PN_CUDA(pn::debug_take_kernels(c->dbg_inject, &site, &index), "read debug checks");
+        PN_CUDA(pn::debug_take_order(c->dbg_inject, &s2, &i2), "read debug checks");
+        if (!site && s2) {
+            site = s2;
+            index = i2;
+        }
+        if (site)
+            return fail(PN_EINDEX, "debug build: an index check failed at site %llu (index %lld)",
+                        site, index);
+    }
+#endif
     if (flag) {
         const unsigned long long none = ULLONG_MAX;
+        unsigned long long wstep = 0;
+        double wval[2] = {0.0, -1.0};
+        if ((flag & 4) && c->wd) {
+            PN_CUDA(cudaMemcpyAsync(&wstep, c->wd_step, sizeof wstep, cudaMemcpyDeviceToHost,
+                                    c->stream), "read watchdog step");
+            PN_CUDA(cudaMemcpyAsync(wval, c->wd + c->nclu, sizeof wval, cudaMemcpyDeviceToHost,
+                                    c->stream), "read watchdog change");
+            PN_CUDA(cudaMemcpyAsync(c->wd_step, &none, sizeof none, cudaMemcpyHostToDevice,
+                                    c->stream), "clear watchdog step");
+        }
         PN_CUDA(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream), "clear flag");
         PN_CUDA(cudaMemcpyAsync(c->flag_step, &none, sizeof none, cudaMemcpyHostToDevice,
                                 c->stream), "clear flag step");
         PN_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
         if (flag & 2)
             return fail(PN_ETIMEOUT, "a bounded wait for a device copy gave up");
-        return fail(PN_ENONFINITE, "non-finite acceleration produced (first at step %llu)", step);
+        if (flag & 1)
+            return fail(PN_ENONFINITE, "non-finite acceleration produced (first at step %llu)",
+                        step);
+        return fail(PN_EDRIFT,
+                    "energy drift |E - E_ref|/|E_ref| = %.6e above %.3e (cluster %d, first at "
+                    "step %llu)", wval[0], c->wd_tol, (int)wval[1], wstep);
     }
     return PN_OK;
 }
 
 // One evaluation of A(x, vel) into a (kick v by h a if v != NULL).
 pn_status evaluate(pn_ctx *c, const double *x, const double *vel, const double *m, double *a,
-                   double *v, double h)
+                   double *v, double h, double dt_next = 0.0)
 {
     PN_CUDA(pn::launch_prologue(c, x, vel, m, false), "prologue launch");
+    // the near-source pass reads only the prologue's records: it forks onto
+    // the side stream once the prologue is done and runs beside the pair
+    // kernel (in the resources that kernel leaves, or in its tail), joining
+    // before the epilogue; launched after the pair kernel, so that kernel's
+    // resident blocks all start at once
+    const bool fork = c->any_near && c->side;
+    if (fork)
+        PN_CUDA(cudaEventRecord(c->ev_fork, c->stream), "fork event");
     if (pn::use_fused(c)) {
         PN_CUDA(pn::launch_fused(c), "fused pair launch");
     } else if (pn::use_fused_f64(c)) {
@@ -188,9 +232,37 @@ pn_status evaluate(pn_ctx *c, const double *x, const double *vel, const double *
         PN_CUDA(pn::launch_pass1(c), "pass-1 launch");
         PN_CUDA(pn::launch_pass2(c), "pass-2 launch");
     }
-    PN_CUDA(pn::launch_near(c), "near-pass launch");
-    PN_CUDA(pn::launch_epilogue(c, x, vel, m, a, v, h, (unsigned long long)c->step_counter),
-            "epilogue launch");
+    if (fork) {
+        PN_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0), "fork wait");
+        cudaStream_t main = c->stream;
+        c->stream = c->side;
+        const cudaError_t e = pn::launch_near(c);
+        c->stream = main;
+        PN_CUDA(e, "near-pass launch");
+        PN_CUDA(cudaEventRecord(c->ev_join, c->side), "join event");
+        PN_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0), "join wait");
+    } else {
+        PN_CUDA(pn::launch_near(c), "near-pass launch");
+    }
+    PN_CUDA(pn::launch_epilogue(c, x, vel, m, a, v, h, (unsigned long long)c->step_counter,
+                                dt_next), "epilogue launch");
+    return PN_OK;
+}
+
+// The energy-drift watchdog checks the state after this step.
+bool watch_due(const pn_ctx *c)
+{
+    return c->wd_every > 0 && c->step_counter % c->wd_every == 0;
+}
+
+// The energy-drift watchdog's check after a step (pn_set_watchdog): Eq. 7
+// on the state, compared on the device with the references.
+pn_status watch(pn_ctx *c, const double *x, const double *v, const double *m)
+{
+    if (!watch_due(c))
+        return PN_OK;
+    PN_CUDA(pn::launch_energy(c, x, v, m), "watchdog energy launch");
+    PN_CUDA(pn::launch_watch(c), "watchdog launch");
     return PN_OK;
 }
 
@@ -207,6 +279,8 @@ pn_status run_rk4(pn_ctx *c, double *x, double *v, const double *m, double *a, d
         }
         PN_CUDA(pn::launch_rk4_stage(c, 3, x, v, a, dt), "rk4 stage launch");
         pn_status st = evaluate(c, x, v, m, a, nullptr, 0.0);
+        if (st == PN_OK)
+            st = watch(c, x, v, m);
         if (st != PN_OK)
             return st;
     }
@@ -279,6 +353,8 @@ pn_status run_hermite(pn_ctx *c, double *x, double *v, const double *m, double *
         }
         PN_CUDA(pn::launch_hermite(c, 2, x, v, a, c->hj0, c->rk_a, c->hj1, c->rk_x, c->rk_v, dt),
                 "hermite commit launch");
+        if ((st = watch(c, x, v, m)) != PN_OK)
+            return st;
     }
     return evaluate(c, x, v, m, a, nullptr, 0.0);
 }
@@ -290,12 +366,20 @@ pn_status run_steps(pn_ctx *c, double *x, double *v, const double *m, double *a,
         return run_rk4(c, x, v, m, a, dt, nsteps);
     if (c->p.integrator == PN_HERMITE)
         return run_hermite(c, x, v, m, a, dt, nsteps);
+    bool drifted = false;   // the previous epilogue took this step's kick and drift
     for (int64_t s = 0; s < nsteps; ++s) {
         c->step_counter += 1;
-        PN_CUDA(pn::launch_kick_drift(c, x, v, a, dt), "kick-drift launch");
-        pn_status st = evaluate(c, x, c->vp, m, a, v, 0.5 * dt);
+        if (!drifted)
+            PN_CUDA(pn::launch_kick_drift(c, x, v, a, dt), "kick-drift launch");
+        // the next step's kick and drift ride on this step's epilogue, except
+        // after the call's last step and where the watchdog reads the state
+        const bool fuse = s + 1 < nsteps && !watch_due(c);
+        pn_status st = evaluate(c, x, c->vp, m, a, v, 0.5 * dt, fuse ? dt : 0.0);
+        if (st == PN_OK)
+            st = watch(c, x, v, m);
         if (st != PN_OK)
             return st;
+        drifted = fuse;
     }
     return PN_OK;
 }
@@ -319,6 +403,15 @@ pn_status set_error(pn_status s, const char *fmt, ...)
 extern "C" {
 
 int pn_version(void) { return 100; }
+
+int pn_debug_checks(void)
+{
+#ifdef PN_DEBUG_CHECKS
+    return 1;
+#else
+    return 0;
+#endif
+}
 
 const char *pn_last_error(void) { return g_err; }
 
@@ -409,6 +502,8 @@ static pn_status init_common(pn_ctx **out, int nclu, const int64_t *off, const p
     // target blocks), measured 8 % faster per step at N = 8192 and 1 % at 16384
     if (c->max_ns_pad <= 16384)
         c->fused_P = 2;
+    c->fused_tile = pn::kPackTile;
+    c->fused_stages = pn::kPackStages;
     c->workers_max = pn::kPackWorkersMax;
     c->worker_units = 64;
     if (const char *wu = std::getenv("PN_WORKER_UNITS")) {
@@ -422,6 +517,14 @@ static pn_status init_common(pn_ctx **out, int nclu, const int64_t *off, const p
     c->inject_tx = 0;
     if (const char *ij = std::getenv("PN_INJECT_COPY_TIMEOUT"))
         c->inject_tx = ij[0] == '1' ? 16u : 0u;
+#ifdef PN_DEBUG_CHECKS
+    // debug build's test hook: PN_DEBUG_INJECT=<site> makes every index
+    // check of that site fail (the access then takes index 0), so the
+    // reporting path runs without a bad index
+    c->dbg_inject = 0;
+    if (const char *di = std::getenv("PN_DEBUG_INJECT"))
+        c->dbg_inject = std::atoi(di);
+#endif
     // the packed law-of-cosines kernel runs on Hilbert-ordered slots
     // (pn_order.cu) when the pair work is large enough to repay the sort's
     // fixed cost (about ten short launches per evaluation);
@@ -466,19 +569,35 @@ static pn_status init_common(pn_ctx **out, int nclu, const int64_t *off, const p
         c->fused_unroll = 2;
     if (c->fused_P == 1 && c->fused_unroll > 2)
         c->fused_unroll = 2;
+    // packed kernel's tile and buffers: PN_FUSED_TILE / PN_FUSED_STAGES
+    // (a supported pair; 32-source tiles only on the slot order)
+    if (const char *ft = std::getenv("PN_FUSED_TILE"))
+        c->fused_tile = std::atoi(ft);
+    if (const char *fst = std::getenv("PN_FUSED_STAGES"))
+        c->fused_stages = std::atoi(fst);
+    if (c->fused_tile == 32 && !std::getenv("PN_FUSED_STAGES"))
+        c->fused_stages = 8;
+    if (!pn::packed_layout_ok(c->fused_tile, c->fused_stages) ||
+        (c->spatial && c->fused_tile != pn::kPackTile)) {
+        c->fused_tile = pn::kPackTile;
+        c->fused_stages = pn::kPackStages;
+    }
     pn::FusedShape fs{};
     // segment buffer: the largest over every fused variant (the tuner may switch)
     int64_t seg_max = 0;
-    static const int variants[][3] = {{1, 1, 0}, {1, 2, 0}, {2, 1, 0}, {2, 2, 0}, {2, 4, 0},
-                                      {4, 1, 0}, {4, 2, 0}, {4, 3, 0}, {4, 4, 0},
-                                      {2, 1, 1}, {2, 2, 1}, {4, 1, 1}, {4, 2, 1}};
+    static const pn::FusedVariant variants[] = {
+        {1, 1, 0, 0, 0}, {1, 2, 0, 0, 0}, {2, 1, 0, 0, 0}, {2, 2, 0, 0, 0}, {2, 4, 0, 0, 0},
+        {4, 1, 0, 0, 0}, {4, 2, 0, 0, 0}, {4, 3, 0, 0, 0}, {4, 4, 0, 0, 0},
+        {2, 1, 1, 64, 6}, {2, 2, 1, 64, 6}, {4, 1, 1, 64, 6}, {4, 2, 1, 64, 6},
+        {2, 1, 1, 64, 4}, {2, 2, 1, 64, 4}, {4, 1, 1, 64, 4}, {4, 2, 1, 64, 4},
+        {2, 1, 1, 32, 8}, {2, 2, 1, 32, 8}, {4, 1, 1, 32, 8}, {4, 2, 1, 32, 8}};
     for (const auto &va : variants) {
         if (e == cudaSuccess)
-            e = pn::fused_shape(c, va[0], va[1], va[2] != 0, &fs);
-        const int64_t seg = (c->S / (pn::kMixThreads * va[0]) + fs.G) * pn::kMixThreads * va[0];
+            e = pn::fused_shape(c, va, &fs);
+        const int64_t seg = (c->S / (pn::kMixThreads * va.P) + fs.G) * pn::kMixThreads * va.P;
         if (seg > seg_max)
             seg_max = seg;
-        if (va[2]) {            // packed variants: sizes of the worker-balance scratch
+        if (va.packed) {        // packed variants: sizes of the worker-balance scratch
             if (fs.units > c->bal_units)
                 c->bal_units = fs.units;
             if (fs.G > c->bal_G)
@@ -486,7 +605,7 @@ static pn_status init_common(pn_ctx **out, int nclu, const int64_t *off, const p
         }
     }
     if (e == cudaSuccess)
-        e = pn::fused_shape(c, c->fused_P, c->fused_unroll, c->fused_packed, &fs);
+        e = pn::fused_shape(c, pn::fused_variant(c), &fs);
     if (e != cudaSuccess) {
         delete[] c->hclu;
         delete c;
@@ -497,7 +616,7 @@ static pn_status init_common(pn_ctx **out, int nclu, const int64_t *off, const p
     c->fused_grid = fs.grid;
     c->fused_G = fs.G;
     c->fused_seg_max = seg_max;
-    c->fused_units = pn::fused_units(c->hclu, nclu, c->fused_P, c->fused_packed, c->hclu);
+    c->fused_units = pn::fused_units(c->hclu, nclu, pn::fused_variant(c), c->hclu);
 
     const int64_t S = c->S;
     int64_t part = (int64_t)c->mix.jsplit * (pn::kP1Vals + pn::kP2Vals) * S;
@@ -543,6 +662,7 @@ static pn_status init_common(pn_ctx **out, int nclu, const int64_t *off, const p
         {(void **)&c->wcount, sizeof(int)},
         {(void **)&c->units_cnt, 2 * sizeof(unsigned long long)},
         {(void **)&c->flag_step, sizeof(unsigned long long)},
+        {(void **)&c->epi_done, sizeof(unsigned) * (size_t)nclu},
         {(void **)&c->d_clu, sizeof(pn::Clu) * (size_t)nclu},
         {(void **)&c->blk_clu, sizeof(int) * (size_t)nglue},
     };
@@ -579,6 +699,30 @@ static pn_status init_common(pn_ctx **out, int nclu, const int64_t *off, const p
         e = cudaMemset(c->ncount, 0, sizeof(int) * (size_t)(nclu + nglue));
     if (e == cudaSuccess)
         e = cudaMemset(c->units_cnt, 0, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess)
+        e = cudaMemset(c->epi_done, 0, sizeof(unsigned) * (size_t)nclu);
+    // side stream of the near-source pass (highest priority, so its blocks
+    // take the first free slots beside the persistent pair kernel) and its
+    // fork / join events
+    if (e == cudaSuccess) {
+        int lo = 0, hi = 0;
+        e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (e == cudaSuccess)
+            e = cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, hi);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    }
+#ifdef PN_DEBUG_CHECKS
+    // arm the test hook's site before the first launch (and clear old records)
+    unsigned long long dsite = 0;
+    long long dindex = 0;
+    if (e == cudaSuccess)
+        e = pn::debug_take_kernels(c->dbg_inject, &dsite, &dindex);
+    if (e == cudaSuccess)
+        e = pn::debug_take_order(c->dbg_inject, &dsite, &dindex);
+#endif
     if (e != cudaSuccess) {
         free_all(c);
         delete c;
@@ -814,7 +958,11 @@ pn_status pn_step_vjp(pn_ctx *c, const double *x0, const double *v0, const doubl
         PN_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
         return PN_OK;
     };
+    // the forward recomputations are not the caller's trajectory: no watchdog checks
+    const int64_t wd_every = c->wd_every;
+    c->wd_every = 0;
     st = run();
+    c->wd_every = wd_every;
     cudaStreamSynchronize(c->stream);
     cudaFree(w);
     cudaFree(dscal);
@@ -959,6 +1107,48 @@ pn_status pn_energy(pn_ctx *c, const double *x, const double *v, const double *m
     return st == PN_OK ? ok() : st;
 }
 
+pn_status pn_set_watchdog(pn_ctx *c, double rel_tol, int64_t every)
+{
+    if (check_ctx(c) != PN_OK)
+        return PN_EINVAL;
+    if (!(std::isfinite(rel_tol) && rel_tol >= 0.0))
+        return fail(PN_EINVAL, "pn_set_watchdog: rel_tol must be finite and >= 0 (got %g)",
+                    rel_tol);
+    if (rel_tol > 0.0 && every < 1)
+        return fail(PN_EINVAL, "pn_set_watchdog: every must be >= 1 (got %lld)",
+                    (long long)every);
+    DeviceGuard g(c->device);
+    PN_CUDA(g.err, "cudaSetDevice");
+    if (rel_tol > 0.0 && !c->wd) {
+        if (std::getenv("PN_FAIL_ALLOC") ||
+            cudaMalloc((void **)&c->wd, sizeof(double) * (size_t)(c->nclu + 2)) != cudaSuccess ||
+            cudaMalloc((void **)&c->wd_step, sizeof(unsigned long long)) != cudaSuccess) {
+            cudaGetLastError();
+            if (c->wd)
+                cudaFree(c->wd);
+            c->wd = nullptr;
+            return fail(PN_ENOMEM, "cudaMalloc for the watchdog failed");
+        }
+    }
+    if (c->wd) {
+        // references unset (all-ones bytes are a NaN), no tripped step yet
+        const unsigned long long none = ULLONG_MAX;
+        PN_CUDA(cudaMemsetAsync(c->wd, 0xff, sizeof(double) * (size_t)c->nclu, c->stream),
+                "reset watchdog references");
+        PN_CUDA(cudaMemcpyAsync(c->wd_step, &none, sizeof none, cudaMemcpyHostToDevice,
+                                c->stream), "reset watchdog step");
+        PN_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
+    }
+    c->wd_tol = rel_tol;
+    c->wd_every = rel_tol > 0.0 ? every : 0;
+    // a captured step sequence holds the old setting: capture again
+    if (c->graph_exec) {
+        cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = nullptr;
+    }
+    return ok();
+}
+
 pn_status pn_sync(pn_ctx *c)
 {
     if (check_ctx(c) != PN_OK)
@@ -1048,7 +1238,7 @@ pn_status pn_get_launch(pn_ctx *c, int64_t out[8])
     const bool fused = pn::use_fused(c);
     out[0] = s.threads;
     out[1] = fused ? c->fused_P : s.targets;
-    out[2] = fused ? pn::fused_tile_size(c->fused_packed) : s.tile;
+    out[2] = fused ? pn::fused_tile_size(pn::fused_variant(c)) : s.tile;
     out[3] = s.nblk_i;
     out[4] = fused ? c->fused_G : s.jsplit;
     out[5] = fused ? c->fused_occ : s.occupancy;
@@ -1068,35 +1258,85 @@ pn_status pn_launch_count(pn_ctx *c, int64_t *count)
 }
 
 namespace {
-// Autotuner results per (workload bucket): the fused-kernel variant found
-// fastest, keyed by the number of work units (log2) and cluster count class.
+// Autotuner results: the fused-kernel variant found fastest, keyed by the
+// pair work (log2 of the tile pairs), the precision and whether the context
+// holds one cluster or many.  Kept for the process and, when PN_TUNE_CACHE
+// names a file, in that file (one "bucket precision many P unroll packed
+// tile stages" line per key, read on the first pn_tune and appended to when
+// a new key is tuned).
 struct TuneKey {
-    int bucket, many;
+    int bucket, precision, many;
     bool operator<(const TuneKey &o) const
     {
-        return bucket < o.bucket || (bucket == o.bucket && many < o.many);
+        if (bucket != o.bucket)
+            return bucket < o.bucket;
+        if (precision != o.precision)
+            return precision < o.precision;
+        return many < o.many;
     }
 };
 std::mutex g_tune_mu;
-struct Variant {
-    int P, unroll, packed;
-};
-std::map<TuneKey, Variant> g_tune;
+std::map<TuneKey, pn::FusedVariant> g_tune;
+bool g_tune_file_read = false;
 
-pn_status apply_variant(pn_ctx *c, Variant va)
+bool variant_ok(const pn_ctx *c, const pn::FusedVariant &v)
+{
+    if (!v.packed)
+        return (v.P == 1 || v.P == 2 || v.P == 4) && v.unroll >= 1 && v.unroll <= 4;
+    return (v.P == 2 || v.P == 4) && (v.unroll == 1 || v.unroll == 2) &&
+           pn::packed_layout_ok(v.tile, v.stages) && !(c->spatial && v.tile != pn::kPackTile);
+}
+
+// Reads the cache file once (caller holds g_tune_mu); bad lines are skipped.
+void read_tune_file()
+{
+    if (g_tune_file_read)
+        return;
+    g_tune_file_read = true;
+    const char *path = std::getenv("PN_TUNE_CACHE");
+    if (!path || !*path)
+        return;
+    FILE *f = std::fopen(path, "r");
+    if (!f)
+        return;
+    TuneKey k;
+    pn::FusedVariant v;
+    while (std::fscanf(f, "%d %d %d %d %d %d %d %d", &k.bucket, &k.precision, &k.many, &v.P,
+                       &v.unroll, &v.packed, &v.tile, &v.stages) == 8)
+        g_tune[k] = v;
+    std::fclose(f);
+}
+
+void append_tune_file(const TuneKey &k, const pn::FusedVariant &v)
+{
+    const char *path = std::getenv("PN_TUNE_CACHE");
+    if (!path || !*path)
+        return;
+    if (FILE *f = std::fopen(path, "a")) {
+        std::fprintf(f, "%d %d %d %d %d %d %d %d\n", k.bucket, k.precision, k.many, v.P, v.unroll,
+                     v.packed, v.tile, v.stages);
+        std::fclose(f);
+    }
+}
+
+pn_status apply_variant(pn_ctx *c, pn::FusedVariant va)
 {
     pn::FusedShape fs{};
-    PN_CUDA(pn::fused_shape(c, va.P, va.unroll, va.packed != 0, &fs), "occupancy");
+    PN_CUDA(pn::fused_shape(c, va, &fs), "occupancy");
     const int64_t seg = (c->S / (pn::kMixThreads * va.P) + fs.G) * pn::kMixThreads * va.P;
     if (seg > c->fused_seg_max)
         return fail(PN_EINVAL, "fused variant needs a larger segment buffer");
     c->fused_P = va.P;
     c->fused_unroll = va.unroll;
     c->fused_packed = va.packed != 0;
+    if (va.packed) {
+        c->fused_tile = va.tile;
+        c->fused_stages = va.stages;
+    }
     c->fused_occ = fs.occ;
     c->fused_grid = fs.grid;
     c->fused_G = fs.G;
-    c->fused_units = pn::fused_units(c->hclu, c->nclu, va.P, c->fused_packed, c->hclu);
+    c->fused_units = pn::fused_units(c->hclu, c->nclu, va, c->hclu);
     if (c->graph_exec) {              // the captured graph holds the old launch shape
         cudaGraphExecDestroy(c->graph_exec);
         c->graph_exec = nullptr;
@@ -1106,7 +1346,7 @@ pn_status apply_variant(pn_ctx *c, Variant va)
 }  // namespace
 
 pn_status pn_tune(pn_ctx *c, const double *x, const double *v, const double *m, double *a,
-                  int64_t out[4])
+                  int64_t out[6])
 {
     if (check_ctx(c) != PN_OK)
         return PN_EINVAL;
@@ -1114,22 +1354,28 @@ pn_status pn_tune(pn_ctx *c, const double *x, const double *v, const double *m, 
         return fail(PN_EINVAL, "pn_tune: NULL array");
     DeviceGuard g(c->device);
     PN_CUDA(g.err, "cudaSetDevice");
-    static const Variant cand[] = {{2, 1, 0}, {2, 2, 0}, {4, 1, 0}, {4, 2, 0},
-                                   {2, 1, 1}, {2, 2, 1}, {4, 1, 1}, {4, 2, 1}};
+    // scalar: targets per thread x unroll; packed: targets per thread x
+    // unroll x (tile, stages)
+    static const pn::FusedVariant cand[] = {
+        {2, 1, 0, 0, 0}, {2, 2, 0, 0, 0}, {4, 1, 0, 0, 0}, {4, 2, 0, 0, 0},
+        {2, 1, 1, 64, 6}, {2, 2, 1, 64, 6}, {4, 1, 1, 64, 6}, {4, 2, 1, 64, 6},
+        {2, 1, 1, 64, 4}, {2, 2, 1, 64, 4}, {4, 1, 1, 64, 4}, {4, 2, 1, 64, 4},
+        {2, 1, 1, 32, 8}, {2, 2, 1, 32, 8}, {4, 1, 1, 32, 8}, {4, 2, 1, 32, 8}};
     int64_t work = 0;                         // pair work of all clusters, in tiles^2
     for (int k = 0; k < c->nclu; ++k)
         work += (c->hclu[k].ns_pad / pn::kMixTile) * (c->hclu[k].ns_pad / pn::kMixTile);
     int bucket = 0;
     for (int64_t u = work; u > 1; u >>= 1)
         ++bucket;
-    const TuneKey key{bucket, c->nclu > 1 ? 1 : 0};
-    Variant best{c->fused_P, c->fused_unroll, c->fused_packed ? 1 : 0};
+    const TuneKey key{bucket, c->p.precision, c->nclu > 1 ? 1 : 0};
+    pn::FusedVariant best = pn::fused_variant(c);
     double best_ms = -1.0;
     bool cached = false;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
+        read_tune_file();
         auto it = g_tune.find(key);
-        if (it != g_tune.end()) {
+        if (it != g_tune.end() && variant_ok(c, it->second)) {
             best = it->second;
             cached = true;
         }
@@ -1140,7 +1386,9 @@ pn_status pn_tune(pn_ctx *c, const double *x, const double *v, const double *m, 
         PN_CUDA(cudaEventCreate(&e1), "event");
         const int was_timing = c->timing_on;
         c->timing_on = 0;
-        for (const Variant &cv : cand) {
+        for (const pn::FusedVariant &cv : cand) {
+            if (!variant_ok(c, cv))
+                continue;
             pn_status st = apply_variant(c, cv);
             if (st != PN_OK)
                 return st;
@@ -1168,6 +1416,7 @@ pn_status pn_tune(pn_ctx *c, const double *x, const double *v, const double *m, 
         cudaEventDestroy(e1);
         std::lock_guard<std::mutex> lock(g_tune_mu);
         g_tune[key] = best;
+        append_tune_file(key, best);
     }
     pn_status st = apply_variant(c, best);
     if (st != PN_OK)
@@ -1177,6 +1426,8 @@ pn_status pn_tune(pn_ctx *c, const double *x, const double *v, const double *m, 
         out[1] = best.unroll;
         out[2] = cached ? 1 : 0;
         out[3] = best.packed;
+        out[4] = pn::fused_tile_size(best);
+        out[5] = best.packed ? best.stages : 0;
     }
     return ok();
 }

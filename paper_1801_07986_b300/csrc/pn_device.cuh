@@ -279,6 +279,61 @@ __device__ __forceinline__ void star_eqs(double G, const TM &M, double mi, doubl
                 (gmr3 / M) * (4.0 * vQ * d[k] - 3.0 * vd * g.Q[k] - 4.0 * Qd * vv[k]);
 }
 
+// ---- debug build: index checks that report instead of trapping ----
+// Compiled with -DPN_DEBUG_CHECKS (libpn_debug.so), PN_IDX(i, n, site)
+// checks 0 <= i < n.  A failing check keeps the first (site, index) of its
+// source file in dbg_word and yields index 0, so the access stays inside
+// the buffer and no thread leaves its kernel, or a barrier, early; the host
+// reads and clears the words after each wait (pn::debug_take) and reports
+// PN_EINDEX.  dbg_inject (set from PN_DEBUG_INJECT=<site> when a context is
+// created) makes every check of that site fail, so the reporting path can
+// be tested without a bad index.  Release builds compile PN_IDX to `i`.
+// Sites (pn_kernels.cu 1-19, pn_order.cu 20-29):
+//   1 kick/drift component       2 prologue slot          3 prologue star
+//   4 near-scatter entry         5 packed source tile     6 packed target block
+//   8 gather slot               10 near-pass source      11 epilogue slot
+//  14 energy-pair source        15 energy-epilogue slot
+//  20 sort-scatter destination  21 permuted slot
+#ifdef PN_DEBUG_CHECKS
+static __device__ unsigned long long dbg_word[2];   // [0] site (0: none), [1] index
+static __device__ int dbg_inject;
+__device__ __forceinline__ int64_t dbg_idx(int64_t i, int64_t n, int site)
+{
+    if (i >= 0 && i < n && site != dbg_inject)
+        return i;
+    if (atomicCAS(&dbg_word[0], 0ull, (unsigned long long)site) == 0ull)
+        dbg_word[1] = (unsigned long long)i;
+    return 0;
+}
+#define PN_IDX(i, n, site) ::pn::dbg_idx((int64_t)(i), (int64_t)(n), (site))
+// Defines this file's host accessor: arms the injected site, then returns
+// and clears the first failed check (site 0: none).
+#define PN_DEBUG_ACCESSOR(name)                                                          \
+    cudaError_t name(int inject, unsigned long long *site, long long *index)            \
+    {                                                                                    \
+        unsigned long long w[2] = {0ull, 0ull};                                          \
+        cudaError_t e = cudaMemcpyToSymbol(dbg_inject, &inject, sizeof inject);          \
+        if (e == cudaSuccess)                                                            \
+            e = cudaMemcpyFromSymbol(w, dbg_word, sizeof w);                             \
+        if (e == cudaSuccess && w[0]) {                                                  \
+            const unsigned long long z[2] = {0ull, 0ull};                                \
+            e = cudaMemcpyToSymbol(dbg_word, z, sizeof z);                               \
+        }                                                                                \
+        *site = w[0];                                                                    \
+        *index = (long long)w[1];                                                        \
+        return e;                                                                        \
+    }
+#else
+#define PN_IDX(i, n, site) (i)
+#define PN_DEBUG_ACCESSOR(name)                                                          \
+    cudaError_t name(int, unsigned long long *site, long long *index)                    \
+    {                                                                                    \
+        *site = 0ull;                                                                    \
+        *index = 0;                                                                      \
+        return cudaSuccess;                                                              \
+    }
+#endif
+
 // ---- packed FP32x2 arithmetic (two lanes per register pair) ----
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }

@@ -14,13 +14,14 @@ constexpr int kMixThreads = 128;   // threads per block
 constexpr int kMixTargets = 2;     // targets held in registers per thread
 constexpr int kMixTile = 128;      // sources per shared-memory tile
 constexpr int kFlushTiles = 2;     // fused kernel: tiles per single-precision partial
-constexpr int kPackTile = 64;      // packed fused kernel: sources per shared-memory tile
+constexpr int kPackTile = 64;      // packed fused kernel: default sources per shared-memory tile
+                                   // (the spatial order's box and unit-cost granularity)
 constexpr int kPackVals = 9;       // dot-product staged layout (packed kernel form 0, adjoint sweeps): float4 per source
 constexpr int kFwdVals = 8;        // law-of-cosines staged layout (packed kernel forms 1, 2): float4 per source
-constexpr int kPackFlushTiles = 8; // packed fused kernel: tiles per single-precision partial
+constexpr int kPackFlushSources = 512;  // packed fused kernel: sources per single-precision partial
 constexpr int kPackWorkersMax = 4;  // packed fused kernel: stream-K workers per resident block (max)
-constexpr int kPackStages = 6;     // packed fused kernel: one-tile shared buffers
-constexpr int kPackRound = 3;      // packed fused kernel: tiles between block barriers (at most)
+constexpr int kPackStages = 6;     // packed fused kernel: default one-tile shared buffers
+                                   // (tiles between block barriers: half of them)
 // Spatial order of the packed kernel by default from this many target-source
 // slot pairs per evaluation (sum over clusters of ns_pad^2) on.
 constexpr double kSpatialMinPairs = 4294967296.0;
@@ -112,6 +113,8 @@ struct pn_ctx {
     pn::Shape mix, f64;
     int fused_P;             // targets per thread of the fused kernel (1, 2 or 4)
     bool fused_packed;       // packed FP32x2 fused kernel (4 targets per thread)
+    int fused_tile;          // packed kernel: sources per shared-memory tile (64 or 32)
+    int fused_stages;        // packed kernel: one-tile shared buffers (6, 4 or 8)
     int fused_unroll;        // source-loop unroll of the fused kernel (1 or 2)
     int fused_occ;           // resident fused-kernel blocks per SM
     int64_t fused_grid;      // blocks of the persistent fused kernel (resident)
@@ -122,6 +125,7 @@ struct pn_ctx {
     int workers_max;         // packed kernel: stream-K workers per resident block, at most
     int worker_units;        // packed kernel: work units per stream-K worker, at least
     unsigned inject_tx;      // test hook: extra bytes each tile's mbarrier expects (0)
+    int dbg_inject;          // debug build's test hook: index-check site made to fail (0)
 
     // scratch, all owned by the context
     double *vp;          // n x 3: velocity at which the force is evaluated
@@ -142,7 +146,14 @@ struct pn_ctx {
     double *eout;        // [nclu][8]: energy / momentum results
     int *flag;           // [0] non-finite flag
     unsigned long long *flag_step;   // first step index with a non-finite value
+    unsigned *epi_done;  // [nclu] epilogue blocks finished this evaluation (self-resetting)
     int64_t step_counter;
+    // energy-drift watchdog (pn_set_watchdog): every wd_every steps (0 = off)
+    double wd_tol;
+    int64_t wd_every;
+    double *wd;          // device: [nclu] reference energies (NaN until taken), then the
+                         // first tripping check's relative change and cluster
+    unsigned long long *wd_step;   // device: step of the first tripping check
 
     // RK4 stage buffers (n x 3 each): stage position / velocity, stage
     // acceleration, and the running k-sums of x and v
@@ -157,6 +168,10 @@ struct pn_ctx {
     int timing_on;
     bool capturing;          // a CUDA graph is being captured
     pn::Timing tm;
+
+    // the near-source pass's side stream and its fork / join events
+    cudaStream_t side;
+    cudaEvent_t ev_fork, ev_join;
 
     // CUDA graph of pn_step_graph: captured once per (arrays, dt, nsteps)
     cudaStream_t cap_stream;
@@ -193,19 +208,41 @@ cudaError_t launch_prologue(pn_ctx *c, const double *x, const double *vel, const
 cudaError_t launch_pass1(pn_ctx *c);
 cudaError_t launch_pass2(pn_ctx *c);
 cudaError_t launch_near(pn_ctx *c);
+// The epilogue with the hole's reduction (last block of each cluster); with
+// v and dt_next > 0 it also takes the next KDK step's kick and drift (x and
+// vel are then written).
 cudaError_t launch_epilogue(pn_ctx *c, const double *x, const double *vel, const double *m,
-                            double *a, double *v, double half_dt, unsigned long long step);
+                            double *a, double *v, double half_dt, unsigned long long step,
+                            double dt_next = 0.0);
 cudaError_t launch_energy(pn_ctx *c, const double *x, const double *v, const double *m);
+cudaError_t launch_watch(pn_ctx *c);   // after launch_energy: compare with the references
 cudaError_t launch_energy_on(cudaStream_t st, int64_t S, const Clu *clu, const double *x,
                              const double *v, const double *m, double4_32a *drec, double *part,
                              double *blk, double *out);
 
 pn_status set_error(pn_status s, const char *fmt, ...);
 
+// Debug build: each source file's first failed index check (site 0: none),
+// read and cleared; `inject` arms the test hook's site (0: none).  Release
+// builds always report none.
+cudaError_t debug_take_kernels(int inject, unsigned long long *site, long long *index);
+cudaError_t debug_take_order(int inject, unsigned long long *site, long long *index);
+
 void shapes(int64_t S, int64_t max_ns_pad, int sm_count, int occ_mix, int occ_f64, Shape *mix,
             Shape *f64);
 cudaError_t occupancy(int *occ_mix, int *occ_f64);
-cudaError_t fused_occupancy(int P, int unroll, bool packed, int *occ);
+// One launch variant of the fused pair kernel: targets per thread, source
+// loop unroll, the packed FP32x2 kernel or the scalar one, and for the packed
+// kernel its tile (sources per shared-memory tile) and one-tile buffers.
+// Packed (tile, stages): (64, 6) the default, (64, 4) and (32, 8); 32-source
+// tiles run on the slot order only (the spatial order works in 64-source
+// tiles).
+struct FusedVariant {
+    int P, unroll, packed, tile, stages;
+};
+FusedVariant fused_variant(const pn_ctx *c);
+bool packed_layout_ok(int tile, int stages);
+cudaError_t fused_occupancy(const FusedVariant &v, int *occ);
 // The packed pair kernel runs its law-of-cosines form (every cluster splits
 // off its near sources); the prologue then stages that form's records.
 bool packed_loc(const pn_ctx *c);
@@ -215,13 +252,13 @@ cudaError_t launch_fused_on(pn_ctx *c, const float4 *rec);
 bool use_fused(const pn_ctx *c);
 bool use_fused_f64(const pn_ctx *c);
 cudaError_t launch_fused_f64(pn_ctx *c);
-int fused_tile_size(bool packed);
+int fused_tile_size(const FusedVariant &v);
 struct FusedShape {
     int occ;                 // resident blocks per SM
     int64_t grid, G, units;  // blocks launched, stream-K workers, work units
 };
-cudaError_t fused_shape(const pn_ctx *c, int P, int unroll, bool packed, FusedShape *out);
-int64_t fused_units(const Clu *h, int nclu, int P, bool packed, Clu *out);
+cudaError_t fused_shape(const pn_ctx *c, const FusedVariant &v, FusedShape *out);
+int64_t fused_units(const Clu *h, int nclu, const FusedVariant &v, Clu *out);
 
 // Spatial order of the star slots (pn_order.cu).
 struct Order {

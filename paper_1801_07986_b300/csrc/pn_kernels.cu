@@ -62,8 +62,9 @@ __global__ void k_kick_drift(int64_t n3, double *__restrict__ x, double *__restr
                              const double *__restrict__ a, double *__restrict__ vp, double h,
                              double dt, int mode)
 {
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n3;
-         q += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t q0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q0 < n3;
+         q0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = PN_IDX(q0, n3, 1);
         const double aq = a[q];
         const double vh = fma(h, aq, v[q]);
         v[q] = vh;
@@ -172,7 +173,7 @@ k_prologue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
     // five record arrays
     float4 *__restrict__ srec = mrec + 5 * S;
     __shared__ double sh[kGlobVals][kProThreads];
-    const int64_t t = (int64_t)blockIdx.x * kProThreads + threadIdx.x;
+    const int64_t t = PN_IDX((int64_t)blockIdx.x * kProThreads + threadIdx.x, S, 2);
     if (wcount && t == 0)
         *wcount = 0;          // the packed pair kernel's worker counter, for this evaluation
     const Clu C = clu[cluster_of_block(blk_clu, (int64_t)blockIdx.x * kProThreads / kGlueThreads)];
@@ -183,7 +184,7 @@ k_prologue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
     for (int k = 0; k < kGlobVals; ++k)
         g[k] = 0.0;
     if (lt < C.ns) {
-        const int64_t j = C.body0 + 1 + lt, h = C.body0;
+        const int64_t j = C.body0 + 1 + PN_IDX(lt, C.ns, 3), h = C.body0;
         const double d0 = x[3 * j] - x[3 * h], d1 = x[3 * j + 1] - x[3 * h + 1],
                      d2 = x[3 * j + 2] - x[3 * h + 2];
         const double R2 = d0 * d0 + d1 * d1 + d2 * d2;
@@ -379,8 +380,8 @@ k_near_scatter(const Clu *__restrict__ clu, int nclu, const int *__restrict__ bl
         before += wsum[q];
     if (!near)
         return;
-    const int64_t pos = C.near0 + ncount[nclu + blockIdx.x] + before +
-                        __popc(mask & ((1u << lane) - 1u));
+    const int64_t pos = PN_IDX(C.near0 + ncount[nclu + blockIdx.x] + before +
+                                   __popc(mask & ((1u << lane) - 1u)), NC, 4);
     const int64_t j = C.body0 + 1 + lt, h = C.body0;
     const double d0 = x[3 * j] - x[3 * h], d1 = x[3 * j + 1] - x[3 * h + 1],
                  d2 = x[3 * j + 2] - x[3 * h + 2];
@@ -863,13 +864,13 @@ __device__ __forceinline__ int packed_target(int NP, int k)
 template <bool LOC>
 __host__ __device__ constexpr int pack_vals() { return LOC ? kFwdVals : kPackVals; }
 
-template <int NP, int UNROLL, bool MASK, bool LOC, bool HI>
+template <int NP, int UNROLL, bool MASK, bool LOC, bool HI, int TILE>
 __device__ __forceinline__ void packed_tile(const float4 (*__restrict__ sh)[pack_vals<LOC>()],
                                             int64_t j0, int64_t t0, const PackTarget (&tg)[NP],
                                             float2 eps2, float2 (&acc)[NP][kPackSums])
 {
 #pragma unroll UNROLL
-    for (int q = 0; q < kPackTile; ++q) {
+    for (int q = 0; q < TILE; ++q) {
         const int64_t j = j0 + q;
 #pragma unroll
         for (int pp = 0; pp < NP; ++pp) {
@@ -881,24 +882,25 @@ __device__ __forceinline__ void packed_tile(const float4 (*__restrict__ sh)[pack
     }
 }
 
-// One staged source tile (bulk-copy size)
-template <bool LOC>
-__host__ __device__ constexpr unsigned tile_bytes() { return kPackTile * pack_vals<LOC>() * 16; }
+// One staged source tile of TILE sources (bulk-copy size)
+template <bool LOC, int TILE>
+__host__ __device__ constexpr unsigned tile_bytes() { return TILE * pack_vals<LOC>() * 16; }
 
-// First source slot of stream-K unit u (its cluster's tile of kPackTile
-// sources).
+// First source slot of stream-K unit u (its cluster's tile of TILE sources).
+template <int TILE>
 __device__ __forceinline__ int64_t unit_source(const Clu *__restrict__ clu, int nclu, int64_t u)
 {
     const Clu C = clu[cluster_of_unit(clu, nclu, u)];
-    const int64_t ntiles = C.ns_pad / kPackTile;
+    const int64_t ntiles = C.ns_pad / TILE;
     const int64_t r = u - C.unit0;
-    return C.slot0 + (r - (r / ntiles) * ntiles) * kPackTile;
+    return C.slot0 + PN_IDX((r - (r / ntiles) * ntiles) * TILE, C.ns_pad - TILE + 1, 5);
 }
 
 // Stream-K over G workers like k_fused_mixed (worker w owns units
 // [w T / G, (w+1) T / G) and writes its segments to slots (target block + w)),
 // with P = 2 NP targets per thread (target pairs (0, 1), (2, 3)) and source
-// tiles of kPackTile.  The resident blocks take workers from a counter
+// tiles of TILE (64 by default; 32 on the slot order).  The resident blocks
+// take workers from a counter
 // (zeroed by the prologue) instead of one fixed worker each: blocks that share
 // an SM advance at unequal rates under the warp scheduler's priorities, and
 // with fixed assignments an SM would end its share with a fraction of its
@@ -906,16 +908,17 @@ __device__ __forceinline__ int64_t unit_source(const Clu *__restrict__ clu, int 
 // sums stay deterministic.
 //
 // Sources come from the staged records srec[slot][pack_vals<LOC>()] (every
-// field duplicated, positions negated), one contiguous 8 or 9 KB tile per
-// unit, copied by the bulk-copy engine into kPackStages one-tile shared
-// buffers (tile k of the block into buffer k % kPackStages).  The tiles of a
-// target block are consumed in rounds of up to kPackRound between block
+// field duplicated, positions negated), one contiguous tile per unit (8 or
+// 9 KB at 64 sources), copied by the bulk-copy engine into ST one-tile
+// shared buffers (tile k of the block into buffer k % ST).  The tiles of a
+// target block are consumed in rounds of up to ST / 2 between block
 // barriers; after a round's barrier thread 0 refills its buffers with the
-// tiles kPackStages ahead, so loads are in flight during arithmetic and the
-// warps, which may take different pair bodies, meet once per round.  Targets
-// are read from the same records.  FP32 tile partials are added every
-// kPackFlushTiles tiles into the worker's segment slot in FP64 (each value is
-// owned by one thread).  A copy that does not complete within the wait limit
+// tiles ST ahead, so loads are in flight during arithmetic and the warps,
+// which may take different pair bodies, meet once per round.  Fewer stages
+// leave room for more resident blocks.  Targets are read from the same
+// records.  FP32 tile partials are added every kPackFlushSources sources
+// into the worker's segment slot in FP64 (each value is owned by one
+// thread).  A copy that does not complete within the wait limit
 // sets kFlagTimeout in `flag`; the block then waits (one shared 1 s limit)
 // for the copies still in flight and ends.
 //
@@ -932,7 +935,7 @@ __device__ __forceinline__ int64_t unit_source(const Clu *__restrict__ clu, int 
 // force (measured on the 128k eccentric workload: the median error against
 // the FP64 oracle goes from 1.1e-8 to 2.2e-8 for any theta in 0.03 .. 0.2).  Near units, and the units that hold self pairs, keep the full
 // separation.  units_cnt[0] / [1] count far / all warp-units.
-template <int NP, int UNROLL, int FORM>
+template <int NP, int UNROLL, int FORM, int TILE, int ST>
 __global__ void __launch_bounds__(kMixThreads, NP == 2 ? 3 : 5)
 k_fused_packed(const float4 *__restrict__ srec, const Clu *__restrict__ clu, int nclu,
                int64_t total_units, int64_t G, int *__restrict__ wcount, int *__restrict__ flag,
@@ -943,9 +946,13 @@ k_fused_packed(const float4 *__restrict__ srec, const Clu *__restrict__ clu, int
     constexpr bool LOC = FORM >= 1, SPATIAL = FORM == 2;
     unsigned n_far = 0, n_all = 0;      // this warp's units (form 2)
     constexpr int P = 2 * NP, TI = kMixThreads * P, RV = pack_vals<LOC>();
-    constexpr int ST = kPackStages;
-    static_assert(kPackRound <= ST / 2, "a round's buffers are refilled while the next round's are read");
-    __shared__ __align__(128) float4 sh[ST][kPackTile][RV];
+    // rounds of RND tiles: a round's buffers are refilled while the next
+    // round's are read; FP32 partials are flushed every kPackFlushSources
+    // sources whatever the tile
+    constexpr int RND = ST / 2, FLUSH = kPackFlushSources / TILE;
+    static_assert(ST >= 2 && ST % 2 == 0 && kPackFlushSources % TILE == 0, "stage layout");
+    static_assert(FORM != 2 || TILE == kPackTile, "the spatial order's boxes and unit costs are per kPackTile sources");
+    __shared__ __align__(128) float4 sh[ST][TILE][RV];
     __shared__ __align__(8) uint64_t full[ST];
     __shared__ int s_w;
     if (threadIdx.x == 0) {
@@ -971,13 +978,13 @@ k_fused_packed(const float4 *__restrict__ srec, const Clu *__restrict__ clu, int
         const int64_t u1 = wb ? wb[w + 1] : (w + 1) * total_units / G;
         if (threadIdx.x == 0)               // every buffer is free here
             for (int q = 0; q < ST && u + q < u1; ++q)
-                bulk_load(sh[(it + q) % ST], srec + unit_source(clu, nclu, u + q) * RV,
-                          tile_bytes<LOC>(), &full[(it + q) % ST], extra_tx);
+                bulk_load(sh[(it + q) % ST], srec + unit_source<TILE>(clu, nclu, u + q) * RV,
+                          tile_bytes<LOC, TILE>(), &full[(it + q) % ST], extra_tx);
         while (u < u1) {
             const Clu C = clu[cluster_of_unit(clu, nclu, u)];
-            const int64_t ntiles = C.ns_pad / kPackTile;
+            const int64_t ntiles = C.ns_pad / TILE;
             const int64_t ib = (u - C.unit0) / ntiles;
-            const int64_t t0 = C.slot0 + ib * TI;
+            const int64_t t0 = C.slot0 + PN_IDX(ib * TI, C.ns_pad - TI + 1, 6);
             const int64_t ub = C.unit0 + ib * ntiles;
             const int64_t uend = ub + ntiles < u1 ? ub + ntiles : u1;
             const float e2 = (float)C.eps2;
@@ -1022,10 +1029,10 @@ k_fused_packed(const float4 *__restrict__ srec, const Clu *__restrict__ clu, int
 #pragma unroll
                 for (int k = 0; k < kPackSums; ++k)
                     acc[pp][k] = make_float2(0.0f, 0.0f);
-            // rounds of up to kPackRound tiles of this target block between
-            // block barriers; tile it goes to buffer it % ST
+            // rounds of up to RND tiles of this target block between block
+            // barriers; tile it goes to buffer it % ST
             while (u < uend) {
-                const int nr = (int)(uend - u < kPackRound ? uend - u : kPackRound);
+                const int nr = (int)(uend - u < RND ? uend - u : RND);
                 bool ok = true;
                 for (int q = 0; q < nr && ok; ++q) {
                     const int64_t uq = u + q;
@@ -1034,8 +1041,8 @@ k_fused_packed(const float4 *__restrict__ srec, const Clu *__restrict__ clu, int
                     ok = mbar_wait(&full[b], (itq / ST) & 1);
                     if (!ok)
                         break;
-                    const int64_t j0 = C.slot0 + (uq - ub) * kPackTile;
-                    const bool diag = (j0 < t0 + TI) && (t0 < j0 + kPackTile);
+                    const int64_t j0 = C.slot0 + (uq - ub) * TILE;
+                    const bool diag = (j0 < t0 + TI) && (t0 < j0 + TILE);
                     bool far = false;
                     if (SPATIAL && !diag) {
                         const float4 l = box[2 * (j0 / kPackTile)], h = box[2 * (j0 / kPackTile) + 1];
@@ -1050,12 +1057,12 @@ k_fused_packed(const float4 *__restrict__ srec, const Clu *__restrict__ clu, int
                         n_all += 1u;
                     }
                     if (diag)
-                        packed_tile<NP, UNROLL, true, LOC, false>(sh[b], j0, t0, tg, eps2, acc);
+                        packed_tile<NP, UNROLL, true, LOC, false, TILE>(sh[b], j0, t0, tg, eps2, acc);
                     else if (SPATIAL && far)
-                        packed_tile<NP, UNROLL, false, LOC, true>(sh[b], j0, t0, tg, eps2, acc);
+                        packed_tile<NP, UNROLL, false, LOC, true, TILE>(sh[b], j0, t0, tg, eps2, acc);
                     else
-                        packed_tile<NP, UNROLL, false, LOC, false>(sh[b], j0, t0, tg, eps2, acc);
-                    if (((uq - ub + 1) % kPackFlushTiles) == 0 || uq + 1 == uend) {
+                        packed_tile<NP, UNROLL, false, LOC, false, TILE>(sh[b], j0, t0, tg, eps2, acc);
+                    if (((uq - ub + 1) % FLUSH) == 0 || uq + 1 == uend) {
 #pragma unroll
                         for (int pp = 0; pp < NP; ++pp)
 #pragma unroll
@@ -1081,8 +1088,8 @@ k_fused_packed(const float4 *__restrict__ srec, const Clu *__restrict__ clu, int
                 }
                 if (threadIdx.x == 0)            // refill the round's buffers, ST tiles ahead
                     for (int q = 0; q < nr && u + q + ST < u1; ++q)
-                        bulk_load(sh[(it + q) % ST], srec + unit_source(clu, nclu, u + q + ST) * RV,
-                                  tile_bytes<LOC>(), &full[(it + q) % ST], extra_tx);
+                        bulk_load(sh[(it + q) % ST], srec + unit_source<TILE>(clu, nclu, u + q + ST) * RV,
+                                  tile_bytes<LOC, TILE>(), &full[(it + q) % ST], extra_tx);
                 u += nr;
                 it += nr;
             }
@@ -1116,9 +1123,10 @@ k_fused_gather(const double *__restrict__ part, int64_t S, const Clu *__restrict
                const int64_t *__restrict__ wb, double *__restrict__ p1, double *__restrict__ p2)
 {
     constexpr int TI = kMixThreads * P;
-    const int64_t t = (int64_t)blockIdx.x * kGatherThreads + threadIdx.x;
-    if (t >= S)
+    const int64_t t_ = (int64_t)blockIdx.x * kGatherThreads + threadIdx.x;
+    if (t_ >= S)
         return;
+    const int64_t t = PN_IDX(t_, S, 8);
     const Clu C = clu[cluster_of_block(blk_clu, (int64_t)blockIdx.x * kGatherThreads / kGlueThreads)];
     const int64_t ntiles = C.ns_pad / tile;
     const int64_t ib = (t - C.slot0) / TI;
@@ -1410,8 +1418,9 @@ k_energy_pairs(const double4_32a *__restrict__ rec, int64_t S, const Clu *__rest
         const int64_t j0 = C.slot0 + (int64_t)tile * kF64Tile;
         __syncthreads();
         for (int q = threadIdx.x; q < kF64Tile; q += kF64Threads) {
-            sh[0][q] = rec[j0 + q];
-            sh[1][q] = rec[S + j0 + q];
+            const int64_t jq = PN_IDX(j0 + q, S, 14);
+            sh[0][q] = rec[jq];
+            sh[1][q] = rec[S + jq];
         }
         __syncthreads();
         const bool diag = (j0 < t0 + kF64Threads) && (t0 < j0 + kF64Tile);
@@ -1503,9 +1512,10 @@ k_near_mixed(const float4 *__restrict__ rec, const float4 *__restrict__ nrec,
         const int64_t j0 = C.near0 + (int64_t)tile * kNearTile;
         __syncthreads();
         for (int q = threadIdx.x; q < kNearTile; q += kMixThreads) {
+            const int64_t jq = PN_IDX(j0 + q, NC, 10);
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                sh[k][q] = nrec[k * NC + j0 + q];
+                sh[k][q] = nrec[k * NC + jq];
         }
         __syncthreads();
         float acc[kMixTargets][kNearVals];
@@ -1602,22 +1612,62 @@ k_near_f64(const double4_32a *__restrict__ rec, const double4_32a *__restrict__ 
 
 // ------------------------------------------------------------ epilogue --
 
+// Writes the acceleration of one body, its final kick v += h a (when v), and
+// with dt_next > 0 the next KDK step's kick and drift (k_kick_drift's
+// operations).
+__device__ __forceinline__ void kick_and_next(double *a, double *v, double *x, double *vel,
+                                              const double (&ai)[3], double h, double dt_next,
+                                              int vel_mode)
+{
+    const double hn = 0.5 * dt_next;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        a[k] = ai[k];
+        if (!v)
+            continue;
+        const double v1 = fma(h, ai[k], v[k]);
+        if (dt_next > 0.0) {
+            const double vh = fma(hn, ai[k], v1);
+            v[k] = vh;
+            x[k] = fma(dt_next, vh, x[k]);
+            vel[k] = vel_mode == 0 ? fma(hn, ai[k], vh) : vh;
+        } else {
+            v[k] = v1;
+        }
+    }
+}
+
 // Star i = t + 1 (double precision throughout): sums the partials of every
 // pass for its slot and assembles its acceleration and its term of the
 // hole's acceleration with star_eqs (the formulas are stated there); the
 // block's sum of the hole terms goes to blk (deterministic tree), one entry
 // per kEpiThreads slots.
+//
+// The hole: every block adds its rows to blk, then takes a ticket from the
+// cluster's counter `done` (atomicInc wraps it back to 0 for the next
+// evaluation); the cluster's last block to finish sums the rows in block
+// order (a fixed order whichever block it is, so the result is
+// deterministic) into a_hole = G W + (1/c^2) sum_j (star j's term), and
+// kicks the hole like the stars.  Every block has read the hole's position
+// before taking its ticket, so the last block may move the hole.
+//
+// dt_next > 0 (KDK steps inside one call): after the final kick each star
+// and, in the last block, the hole take the next step's kick and drift --
+// v_h = v + h' a, x += dt_next v_h, vel = v_h + h' a (vel_mode 0) or v_h,
+// h' = dt_next / 2 -- the same operations k_kick_drift would do next, so
+// the trajectory is bitwise the same.  A thread reads and writes only its
+// own star's x, vel and v, and the hole's x before its block's ticket.
 __global__ void __launch_bounds__(kEpiThreads)
 k_epilogue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_clu,
-           const double *__restrict__ x, const double *__restrict__ vel,
-           const double *__restrict__ m, const double *__restrict__ p1, int js1,
-           const double *__restrict__ p2, int js2, const double *__restrict__ pnear,
+           double *x, double *vel, const double *__restrict__ m, const double *__restrict__ p1,
+           int js1, const double *__restrict__ p2, int js2, const double *__restrict__ pnear,
            const unsigned char *__restrict__ nflag, const double *__restrict__ globs,
-           double *__restrict__ a, double *__restrict__ v, double h, int *flag,
-           unsigned long long *flag_step, unsigned long long step, double *__restrict__ blk)
+           double *a, double *v, double h, int *flag, unsigned long long *flag_step,
+           unsigned long long step, double *__restrict__ blk, unsigned *__restrict__ done,
+           double dt_next, int vel_mode)
 {
     __shared__ double sh[3][kEpiThreads];
-    const int64_t t = (int64_t)blockIdx.x * kEpiThreads + threadIdx.x;
+    const int64_t t = PN_IDX((int64_t)blockIdx.x * kEpiThreads + threadIdx.x, S, 11);
     const int k_clu = cluster_of_block(blk_clu, (int64_t)blockIdx.x * kEpiThreads / kGlueThreads);
     const Clu Cl = clu[k_clu];
     const double *glob = globs + (int64_t)k_clu * kGlobVals;
@@ -1677,38 +1727,55 @@ k_epilogue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
         double ai[3];
         star_eqs<double, double>(Cl.G, m[hb], m[i], Cl.eps2, Cl.inv_c2, fi, d, vv, ss, gs, ai, bh);
         flag_nonfinite(ai, flag, flag_step, step);
-        for (int k = 0; k < 3; ++k) {
-            a[3 * i + k] = ai[k];
-            if (v)
-                v[3 * i + k] = fma(h, ai[k], v[3 * i + k]);
-        }
+        kick_and_next(&a[3 * i], v ? &v[3 * i] : nullptr, &x[3 * i], &vel[3 * i], ai, h, dt_next,
+                      vel_mode);
     }
     block_sum<3, kEpiThreads>(bh, sh);
     if (threadIdx.x < 3)
         blk[(int64_t)blockIdx.x * 3 + threadIdx.x] = sh[threadIdx.x][0];
-}
-
-// The hole of each cluster (one block per cluster):
-// a_hole = G W + (1/c^2) sum_j (star j's term above).
-__global__ void __launch_bounds__(kGlueThreads)
-k_hole(const Clu *__restrict__ clu, const double *__restrict__ blk,
-       const double *__restrict__ globs, double *__restrict__ a, double *__restrict__ v,
-       double h, int *flag, unsigned long long *flag_step, unsigned long long step)
-{
-    __shared__ double sh[3][kGlueThreads];
-    const Clu C = clu[blockIdx.x];
-    sum_blocks<3>(blk + (C.slot0 / kEpiThreads) * 3, C.ns_pad / kEpiThreads, sh);
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
     if (threadIdx.x == 0) {
-        const double *glob = globs + (int64_t)blockIdx.x * kGlobVals;
-        const int64_t hb = C.body0;
-        double a0[3];
+        const unsigned nb = (unsigned)(Cl.ns_pad / kEpiThreads);
+        s_last = atomicInc(&done[k_clu], nb - 1) == nb - 1;
+    }
+    __syncthreads();
+    if (!s_last)
+        return;
+    __threadfence();
+    // rows of the cluster, thread q adding rows q, q + kEpiThreads, ... in
+    // order; then the per-thread sums in a fixed tree
+    const int64_t r0 = Cl.slot0 / kEpiThreads, nr = Cl.ns_pad / kEpiThreads;
+    double s3[3] = {0.0, 0.0, 0.0};
+    for (int64_t r = threadIdx.x; r < nr; r += kEpiThreads)
+#pragma unroll
         for (int k = 0; k < 3; ++k)
-            a0[k] = C.G * glob[3 + k] + C.inv_c2 * sh[k][0];
-        flag_nonfinite(a0, flag, flag_step, step);
+            s3[k] += __ldcg(&blk[(r0 + r) * 3 + k]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        sh[k][threadIdx.x] = s3[k];
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        static_assert(kEpiThreads == 64, "two warps per epilogue block");
+        double tot[3];
+#pragma unroll
         for (int k = 0; k < 3; ++k) {
-            a[3 * hb + k] = a0[k];
-            if (v)
-                v[3 * hb + k] = fma(h, a0[k], v[3 * hb + k]);
+            double w = sh[k][threadIdx.x] + sh[k][threadIdx.x + 32];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                w += __shfl_xor_sync(0xffffffffu, w, o);
+            tot[k] = w;
+        }
+        if (threadIdx.x == 0) {
+            const int64_t hb = Cl.body0;
+            double a0[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                a0[k] = Cl.G * glob[3 + k] + Cl.inv_c2 * tot[k];
+            flag_nonfinite(a0, flag, flag_step, step);
+            kick_and_next(&a[3 * hb], v ? &v[3 * hb] : nullptr, &x[3 * hb], &vel[3 * hb], a0, h,
+                          dt_next, vel_mode);
         }
     }
 }
@@ -1732,7 +1799,7 @@ k_energy_epilogue(int64_t S, const Clu *__restrict__ clu, const int *__restrict_
                   double *__restrict__ blk)
 {
     __shared__ double sh[kEBlockVals][kGlueThreads];
-    const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
+    const int64_t t = PN_IDX((int64_t)blockIdx.x * kGlueThreads + threadIdx.x, S, 15);
     const Clu Cl = clu[cluster_of_block(blk_clu, blockIdx.x)];
     const double G = Cl.G;
     const int64_t lt = t - Cl.slot0;
@@ -1801,6 +1868,46 @@ k_energy_final(const Clu *__restrict__ clu, const double *__restrict__ blk,
         for (int k = 0; k < 3; ++k) {
             o[2 + k] = sh[2 + k][0] + M * v1[k];
             o[5 + k] = C.inv_c2 * sh[5 + k][0];
+        }
+    }
+}
+
+// Energy-drift watchdog: one thread compares each cluster's total energy
+// E = E_N + E_1PN (Eq. 7, just evaluated into eout) with its reference
+// wd[k].  A NaN reference (armed, not yet taken) is replaced by E; else a
+// relative change |E - E_ref| / |E_ref| above tol (or a non-finite one)
+// sets flag bit 4 and, for the first step that does so, records the step
+// index, the largest change and its cluster (wd[nclu], wd[nclu + 1]).
+__global__ void k_watch(const double *__restrict__ eout, int nclu, double tol,
+                        unsigned long long step, double *__restrict__ wd, int *__restrict__ flag,
+                        unsigned long long *__restrict__ wstep)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0)
+        return;
+    double worst = -1.0;
+    int kworst = -1;
+    for (int k = 0; k < nclu; ++k) {
+        const double E = eout[8 * k] + eout[8 * k + 1];
+        const double ref = wd[k];
+        if (isnan(ref)) {
+            wd[k] = E;
+            continue;
+        }
+        double d = fabs(E - ref) / fabs(ref);
+        if (!(d <= tol)) {
+            d = isnan(d) ? INFINITY : d;
+            if (d > worst) {
+                worst = d;
+                kworst = k;
+            }
+        }
+    }
+    if (kworst >= 0) {
+        *flag |= 4;
+        if (*wstep == ~0ull) {
+            *wstep = step;
+            wd[nclu] = worst;
+            wd[nclu + 1] = (double)kworst;
         }
     }
 }
@@ -1910,15 +2017,26 @@ static Layout layout(const pn_ctx *c)
     return L;
 }
 
-int fused_tile_size(bool packed) { return packed ? kPackTile : kMixTile; }
+FusedVariant fused_variant(const pn_ctx *c)
+{
+    return FusedVariant{c->fused_P, c->fused_unroll, c->fused_packed ? 1 : 0, c->fused_tile,
+                        c->fused_stages};
+}
+
+bool packed_layout_ok(int tile, int stages)
+{
+    return (tile == 64 && (stages == 6 || stages == 4)) || (tile == 32 && stages == 8);
+}
+
+int fused_tile_size(const FusedVariant &v) { return v.packed ? v.tile : kMixTile; }
 
 // Work units of a fused-kernel variant over all clusters of the context.
-static int64_t fused_unit_count(const pn_ctx *c, int P, bool packed)
+static int64_t fused_unit_count(const pn_ctx *c, const FusedVariant &v)
 {
-    const int tile = fused_tile_size(packed);
+    const int tile = fused_tile_size(v);
     int64_t u = 0;
     for (int k = 0; k < c->nclu; ++k)
-        u += (c->hclu[k].ns_pad / (kMixThreads * P)) * (c->hclu[k].ns_pad / tile);
+        u += (c->hclu[k].ns_pad / (kMixThreads * v.P)) * (c->hclu[k].ns_pad / tile);
     return u;
 }
 
@@ -1926,17 +2044,17 @@ static int64_t fused_unit_count(const pn_ctx *c, int P, bool packed)
 // stream-K workers, work units.  The scalar kernel runs one worker per
 // resident block; the packed kernel up to c->workers_max (default
 // kPackWorkersMax) per block, at least 64 units each, taken dynamically.
-cudaError_t fused_shape(const pn_ctx *c, int P, int unroll, bool packed, FusedShape *out)
+cudaError_t fused_shape(const pn_ctx *c, const FusedVariant &v, FusedShape *out)
 {
     int occ = 0;
-    const cudaError_t e = fused_occupancy(P, unroll, packed, &occ);
+    const cudaError_t e = fused_occupancy(v, &occ);
     if (e != cudaSuccess)
         return e;
     out->occ = occ > 0 ? occ : 1;
     out->grid = (int64_t)out->occ * c->sm_count;
-    out->units = fused_unit_count(c, P, packed);
+    out->units = fused_unit_count(c, v);
     int64_t per = 1;
-    if (packed) {
+    if (v.packed) {
         const int64_t cap = c->workers_max > 0 ? c->workers_max : kPackWorkersMax;
         per = out->units / (out->grid * (int64_t)c->worker_units);
         per = per < 1 ? 1 : (per > cap ? cap : per);
@@ -1945,14 +2063,14 @@ cudaError_t fused_shape(const pn_ctx *c, int P, int unroll, bool packed, FusedSh
     return cudaSuccess;
 }
 
-int64_t fused_units(const Clu *h, int nclu, int P, bool packed, Clu *out)
+int64_t fused_units(const Clu *h, int nclu, const FusedVariant &v, Clu *out)
 {
-    const int tile = fused_tile_size(packed);
+    const int tile = fused_tile_size(v);
     int64_t u = 0;
     for (int k = 0; k < nclu; ++k) {
         out[k] = h[k];
         out[k].unit0 = u;
-        u += (h[k].ns_pad / (kMixThreads * P)) * (h[k].ns_pad / tile);
+        u += (h[k].ns_pad / (kMixThreads * v.P)) * (h[k].ns_pad / tile);
     }
     return u;
 }
@@ -2047,13 +2165,13 @@ static cudaError_t launch_fused_p(pn_ctx *c, const Layout &L, const float4 *rec)
 // form: every source keeps its hole term) are staged in the D form first.
 // Form FORM of the packed kernel (k_fused_packed) on staged records `srec`
 // (boxes and the sorted-to-slot map for form 2), then the gather.
-template <int NP, int UNROLL, int FORM>
+template <int NP, int UNROLL, int FORM, int TILE, int ST>
 static cudaError_t launch_packed_form(pn_ctx *c, const Layout &L, const float4 *srec,
                                       const float4 *box, const int *perm, const int64_t *wb)
 {
     cudaEvent_t end = nullptr;
     timing_begin(c, 1, &end);
-    k_fused_packed<NP, UNROLL, FORM><<<(unsigned)c->fused_grid, kMixThreads, 0, c->stream>>>(
+    k_fused_packed<NP, UNROLL, FORM, TILE, ST><<<(unsigned)c->fused_grid, kMixThreads, 0, c->stream>>>(
         srec, c->d_clu, c->nclu, c->fused_units, c->fused_G, c->wcount, c->flag, c->inject_tx,
         box, c->far_theta, c->units_cnt, wb, c->part + L.seg);
     c->launches += 1;
@@ -2064,7 +2182,7 @@ static cudaError_t launch_packed_form(pn_ctx *c, const Layout &L, const float4 *
         return e;
     k_fused_gather<2 * NP, kPackSums, pack_vals<(FORM >= 1)>()>
         <<<dim3((unsigned)(c->S / kGatherThreads), 3), kGatherThreads, 0, c->stream>>>(
-            c->part + L.seg, c->S, c->d_clu, blk_table(c), c->fused_units, c->fused_G, kPackTile,
+            c->part + L.seg, c->S, c->d_clu, blk_table(c), c->fused_units, c->fused_G, TILE,
             srec, perm, wb, c->part + L.p1, c->part + L.p2);
     c->launches += 1;
     return cudaGetLastError();
@@ -2077,28 +2195,44 @@ bool packed_loc(const pn_ctx *c) { return c->fused_packed && c->near_all; }
 // its near sources (packed_loc; in the spatial order when c->spatial), else
 // the D form; caller-built records (far form: every source keeps its hole
 // term) are staged in the D form first.
-template <int NP, int UNROLL>
-static cudaError_t launch_packed_u(pn_ctx *c, const Layout &L, const float4 *rec)
+template <int NP, int UNROLL, int TILE, int ST>
+static cudaError_t launch_packed_v(pn_ctx *c, const Layout &L, const float4 *rec)
 {
     const float4 *srec = c->mrec + 5 * c->S;
     if (rec == c->mrec && packed_loc(c)) {
-        if (!c->spatial)
-            return launch_packed_form<NP, UNROLL, 1>(c, L, srec, nullptr, nullptr, nullptr);
-        cudaError_t e = launch_spatial_order(c);
-        const int64_t *wb = nullptr;
-        if (e == cudaSuccess && c->balance)
-            e = launch_worker_balance(c, NP, &wb);
-        if (e != cudaSuccess)
-            return e;
-        const Order o = order_of(c);
-        return launch_packed_form<NP, UNROLL, 2>(c, L, o.ssrec, o.box, o.perm, wb);
+        if constexpr (TILE == kPackTile) {
+            if (c->spatial) {
+                cudaError_t e = launch_spatial_order(c);
+                const int64_t *wb = nullptr;
+                if (e == cudaSuccess && c->balance)
+                    e = launch_worker_balance(c, NP, &wb);
+                if (e != cudaSuccess)
+                    return e;
+                const Order o = order_of(c);
+                return launch_packed_form<NP, UNROLL, 2, TILE, ST>(c, L, o.ssrec, o.box, o.perm,
+                                                                   wb);
+            }
+        }
+        return launch_packed_form<NP, UNROLL, 1, TILE, ST>(c, L, srec, nullptr, nullptr, nullptr);
     }
     if (rec != c->mrec) {       // caller-built records: stage them first
         k_stage_sources<<<(unsigned)(c->S / kGlueThreads), kGlueThreads, 0, c->stream>>>(
             c->S, rec, c->mrec + 5 * c->S);
         c->launches += 1;
     }
-    return launch_packed_form<NP, UNROLL, 0>(c, L, srec, nullptr, nullptr, nullptr);
+    return launch_packed_form<NP, UNROLL, 0, TILE, ST>(c, L, srec, nullptr, nullptr, nullptr);
+}
+
+// The context's (tile, stages) of the packed kernel; 32-source tiles only
+// on the slot order (variant selection keeps them off the spatial order).
+template <int NP, int UNROLL>
+static cudaError_t launch_packed_u(pn_ctx *c, const Layout &L, const float4 *rec)
+{
+    if (c->fused_tile == 32)
+        return launch_packed_v<NP, UNROLL, 32, 8>(c, L, rec);
+    if (c->fused_stages == 4)
+        return launch_packed_v<NP, UNROLL, kPackTile, 4>(c, L, rec);
+    return launch_packed_v<NP, UNROLL, kPackTile, kPackStages>(c, L, rec);
 }
 
 // Fused-kernel variants: scalar (targets per thread 1, 2, 4) or packed
@@ -2172,28 +2306,42 @@ static cudaError_t occ_of(int *occ)
     return occ_with_carveout(k_fused_mixed<P, UNROLL>, occ);
 }
 
-// Resident blocks of the packed kernel: the smaller of its two forms, so
-// that one launch shape serves both.
-template <int NP, int UNROLL>
-static cudaError_t occ_packed(int *occ)
+// Resident blocks of the packed kernel: the smallest over its forms, so
+// that one launch shape serves them all.
+template <int NP, int UNROLL, int TILE, int ST>
+static cudaError_t occ_packed_v(int *occ)
 {
-    int o[3] = {0, 0, 0};
-    cudaError_t e = occ_with_carveout(k_fused_packed<NP, UNROLL, 0>, &o[0]);
+    int o[3] = {0, 0, 1 << 20};
+    cudaError_t e = occ_with_carveout(k_fused_packed<NP, UNROLL, 0, TILE, ST>, &o[0]);
     if (e == cudaSuccess)
-        e = occ_with_carveout(k_fused_packed<NP, UNROLL, 1>, &o[1]);
-    if (e == cudaSuccess)
-        e = occ_with_carveout(k_fused_packed<NP, UNROLL, 2>, &o[2]);
+        e = occ_with_carveout(k_fused_packed<NP, UNROLL, 1, TILE, ST>, &o[1]);
+    if constexpr (TILE == kPackTile)
+        if (e == cudaSuccess)
+            e = occ_with_carveout(k_fused_packed<NP, UNROLL, 2, TILE, ST>, &o[2]);
     *occ = o[0] < o[1] ? o[0] : o[1];
     *occ = o[2] < *occ ? o[2] : *occ;
     return e;
 }
 
-cudaError_t fused_occupancy(int P, int unroll, bool packed, int *occ)
+template <int NP, int UNROLL>
+static cudaError_t occ_packed(int tile, int stages, int *occ)
 {
-    if (packed) {
+    if (tile == 32)
+        return occ_packed_v<NP, UNROLL, 32, 8>(occ);
+    if (stages == 4)
+        return occ_packed_v<NP, UNROLL, kPackTile, 4>(occ);
+    return occ_packed_v<NP, UNROLL, kPackTile, kPackStages>(occ);
+}
+
+cudaError_t fused_occupancy(const FusedVariant &v, int *occ)
+{
+    const int P = v.P, unroll = v.unroll;
+    if (v.packed) {
         if (P == 2)
-            return unroll == 2 ? occ_packed<1, 2>(occ) : occ_packed<1, 1>(occ);
-        return unroll == 2 ? occ_packed<2, 2>(occ) : occ_packed<2, 1>(occ);
+            return unroll == 2 ? occ_packed<1, 2>(v.tile, v.stages, occ)
+                               : occ_packed<1, 1>(v.tile, v.stages, occ);
+        return unroll == 2 ? occ_packed<2, 2>(v.tile, v.stages, occ)
+                           : occ_packed<2, 1>(v.tile, v.stages, occ);
     }
     switch (P) {
     case 1: return unroll == 2 ? occ_of<1, 2>(occ) : occ_of<1, 1>(occ);
@@ -2229,20 +2377,18 @@ cudaError_t launch_near(pn_ctx *c)
 }
 
 cudaError_t launch_epilogue(pn_ctx *c, const double *x, const double *vel, const double *m,
-                            double *a, double *v, double h, unsigned long long step)
+                            double *a, double *v, double h, unsigned long long step,
+                            double dt_next)
 {
     const Layout L = layout(c);
     const int64_t nb = c->S / kEpiThreads;
     const double *pnear = c->any_near ? c->part + L.near : nullptr;
+    // x and vel are written only with dt_next > 0, which the integrator asks
+    // for on its own state arrays
     k_epilogue<<<(unsigned)nb, kEpiThreads, 0, c->stream>>>(
-        c->S, c->d_clu, blk_table(c), x, vel, m, c->part + L.p1, L.js, c->part + L.p2, L.js,
-        pnear, c->nflag, c->glob, a, v, h, c->flag, c->flag_step, step, c->blk);
-    c->launches += 1;
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess)
-        return e;
-    k_hole<<<c->nclu, kGlueThreads, 0, c->stream>>>(c->d_clu, c->blk, c->glob, a, v, h, c->flag,
-                                                    c->flag_step, step);
+        c->S, c->d_clu, blk_table(c), const_cast<double *>(x), const_cast<double *>(vel), m,
+        c->part + L.p1, L.js, c->part + L.p2, L.js, pnear, c->nflag, c->glob, a, v, h, c->flag,
+        c->flag_step, step, c->blk, c->epi_done, v ? dt_next : 0.0, c->p.vel_mode);
     c->launches += 1;
     return cudaGetLastError();
 }
@@ -2263,6 +2409,15 @@ cudaError_t launch_energy(pn_ctx *c, const double *x, const double *v, const dou
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
     k_energy_final<<<c->nclu, kGlueThreads, 0, c->stream>>>(c->d_clu, c->blk, v, m, c->eout);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_watch(pn_ctx *c)
+{
+    k_watch<<<1, 32, 0, c->stream>>>(c->eout, c->nclu, c->wd_tol,
+                                     (unsigned long long)c->step_counter, c->wd, c->flag,
+                                     c->wd_step);
     c->launches += 1;
     return cudaGetLastError();
 }
@@ -2349,5 +2504,7 @@ cudaError_t occupancy(int *occ_mix, int *occ_f64)
         return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_f64, k_pass_f64<2>, kF64Threads, 0);
 }
+
+PN_DEBUG_ACCESSOR(debug_take_kernels)
 
 }  // namespace pn

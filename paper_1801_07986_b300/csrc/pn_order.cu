@@ -239,7 +239,9 @@ k_sort_scatter(const unsigned *__restrict__ kin, const int *__restrict__ vin,
         }
     }
     __syncthreads();
-    const int dest = hist[b * kSortBins + d] + cnt[w][d] + rank;
+    // the grid covers every slot once: a destination lies below its extent
+    const int dest = (int)PN_IDX(hist[b * kSortBins + d] + cnt[w][d] + rank,
+                                 (int64_t)gridDim.x * kSortBlock, 20);
     kout[dest] = key;
     vout[dest] = val;
 }
@@ -254,7 +256,7 @@ k_sort_permute(const float4 *__restrict__ srec, const int *__restrict__ perm,
     static_assert(kPackTile == 64, "two warps per tile");
     __shared__ float red[2][7];
     const int64_t k = (int64_t)blockIdx.x * kPackTile + threadIdx.x;
-    const int64_t slot = perm[k];
+    const int64_t slot = PN_IDX(perm[k], (int64_t)gridDim.x * kPackTile, 21);
     const float4 *src = srec + slot * kFwdVals;
     float4 *dst = ssrec + k * kFwdVals;
     float4 r[kFwdVals];
@@ -507,5 +509,7 @@ cudaError_t launch_spatial_order(pn_ctx *c)
     c->launches += 10;
     return cudaGetLastError();
 }
+
+PN_DEBUG_ACCESSOR(debug_take_order)
 
 }  // namespace pn

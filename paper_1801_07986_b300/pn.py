@@ -22,9 +22,10 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
-PN_OK, PN_EINVAL, PN_ENOMEM, PN_ECUDA, PN_ENONFINITE, PN_ETIMEOUT, PN_EUNSUPPORTED = range(7)
+(PN_OK, PN_EINVAL, PN_ENOMEM, PN_ECUDA, PN_ENONFINITE, PN_ETIMEOUT, PN_EUNSUPPORTED,
+ PN_EDRIFT, PN_EINDEX) = range(9)
 STATUS_NAMES = {0: "PN_OK", 1: "PN_EINVAL", 2: "PN_ENOMEM", 3: "PN_ECUDA", 4: "PN_ENONFINITE",
-                5: "PN_ETIMEOUT", 6: "PN_EUNSUPPORTED"}
+                5: "PN_ETIMEOUT", 6: "PN_EUNSUPPORTED", 7: "PN_EDRIFT", 8: "PN_EINDEX"}
 PN_FP64, PN_MIXED = 0, 1
 PN_VPRED_END, PN_VHALF = 0, 1
 PN_PAIR_FUSED, PN_PAIR_TWO_PASS = 0, 1
@@ -68,6 +69,8 @@ _lib = None
 
 
 def library_path() -> str:
+    """libpn.so next to this file; PN_LIBRARY=<path> selects another build
+    (the debug build libpn_debug.so, whose kernels check their indices)."""
     return os.environ.get("PN_LIBRARY") or os.path.join(HERE, "libpn.so")
 
 
@@ -96,6 +99,7 @@ def _load():
                 "pn_step_host": [P, P, P, P, P, D, I64],
                 "pn_energy": [P, P, P, P, P],
                 "pn_sync": [P],
+                "pn_set_watchdog": [P, D, I64],
                 "pn_set_timing": [P, I],
                 "pn_get_timing": [P, P, P],
                 "pn_get_launch": [P, P],
@@ -114,6 +118,8 @@ def _load():
             lib.pn_destroy.restype = None
             lib.pn_version.argtypes = []
             lib.pn_version.restype = ctypes.c_int
+            lib.pn_debug_checks.argtypes = []
+            lib.pn_debug_checks.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -376,15 +382,17 @@ def pn_step_graph(ctx: Context, x, v, m, a, dt: float, nsteps: int) -> None:
 
 
 def pn_tune(ctx: Context, x, v, m, a) -> dict:
-    """Choose the fused kernel's launch shape by timing candidates on this
-    state (a is overwritten with A(x, v))."""
+    """Choose the fused kernel's launch shape (targets per thread, unroll,
+    packed kernel, j-tile, buffers) by timing candidates on this state (a is
+    overwritten with A(x, v)); cached per work bucket, precision and cluster
+    class, and in the file PN_TUNE_CACHE names, if any."""
     n = ctx.n
-    out = np.zeros(4, dtype=np.int64)
+    out = np.zeros(6, dtype=np.int64)
     _check(_load().pn_tune(ctx.handle, _dev(ctx, x, (n, 3), "x"), _dev(ctx, v, (n, 3), "v"),
                            _dev(ctx, m, (n,), "m"), _dev(ctx, a, (n, 3), "a"),
                            out.ctypes.data_as(ctypes.c_void_p)))
     return {"targets_per_thread": int(out[0]), "unroll": int(out[1]), "cached": bool(out[2]),
-            "packed": bool(out[3])}
+            "packed": bool(out[3]), "tile": int(out[4]), "stages": int(out[5])}
 
 
 def _host(arr, shape, name):
@@ -448,6 +456,13 @@ def pn_measure_peaks(device: int = 0, stream=None) -> dict:
                                     out.ctypes.data_as(ctypes.c_void_p)))
     return {"fp32_fma_tflops": out[0], "fp64_fma_tflops": out[1], "rsqrt_gops": out[2],
             "sms": int(out[3]), "fp32x2_fma_tflops": out[4]}
+
+
+def pn_set_watchdog(ctx: Context, rel_tol: float, every: int = 100) -> None:
+    """Energy-drift watchdog: every `every` steps compare Eq. 7's energy with
+    the first check's; a relative change above rel_tol makes the next waiting
+    call raise PNError with status PN_EDRIFT.  rel_tol = 0 turns it off."""
+    _check(_load().pn_set_watchdog(ctx.handle, float(rel_tol), int(every)))
 
 
 def pn_sync(ctx: Context) -> None:

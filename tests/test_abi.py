@@ -99,6 +99,21 @@ def test_null_arguments(lib):
     lib.pn_destroy(None)   # no-op
 
 
+def test_watchdog_status_plumbing(lib):
+    """PN_EDRIFT has one value in the header and the binding, the binding names
+    it, and pn_set_watchdog rejects a NULL context on the host."""
+    from paper_1801_07986_b300 import pn
+    src = open(HEADER).read()
+    m = re.search(r"PN_EDRIFT\s*=\s*(\d+)", src)
+    assert m and int(m.group(1)) == pn.PN_EDRIFT == 7
+    assert pn.STATUS_NAMES[pn.PN_EDRIFT] == "PN_EDRIFT"
+    e = pn.PNError(pn.PN_EDRIFT, "energy drift 1e-2 above 1e-3 (cluster 0, first at step 120)")
+    assert str(e).startswith("PN_EDRIFT: ") and e.status == 7
+    assert lib.pn_set_watchdog(None, 1e-3, 10) == 1
+    assert "NULL" in lib.pn_last_error().decode()
+    assert lib.pn_set_watchdog(None, 0.0, 0) == 1
+
+
 def test_injected_allocation_failure():
     code = ("import ctypes; from paper_1801_07986_b300 import pn; lib = pn._load();"
             "p = pn._Params(1.0, 50.0, 1e-4, 1, 0, 0.05, 0, 0); h = ctypes.c_void_p();"

@@ -86,8 +86,8 @@ def test_kernel_hash_follows_code_changes(tmp_path, monkeypatch, edit):
         (dst / "pn_kernels.cu").write_text(k[:i] + "static int pn_probe_value = 1;\n" + k[i:])
     else:
         hdr = (dst / "pn_internal.h").read_text()
-        m = re.search(r"constexpr int kPackStages = (\d+);", hdr)   # a tunable the kernel names
+        m = re.search(r"constexpr int kPackFlushSources = (\d+);", hdr)   # a tunable the kernel names
         assert m
         (dst / "pn_internal.h").write_text(
-            hdr.replace(m.group(0), f"constexpr int kPackStages = {int(m.group(1)) + 1};"))
+            hdr.replace(m.group(0), f"constexpr int kPackFlushSources = {2 * int(m.group(1))};"))
     assert _hash_at(monkeypatch, root) != h0

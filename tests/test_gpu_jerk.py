@@ -84,13 +84,20 @@ def test_jerk_strong_field_and_near_hole(orc):
     assert np.median(err) <= 2e-5 and err.max() <= 1e-3, (np.median(err), err.max())
 
 
-def test_jerk_mixed_plummer16k_against_fp64():
+def test_jerk_plummer16k_against_oracle(orc):
+    """The 16k workload's jerk, every body (the hole included), against the
+    oracle's complex-step jerk: the FP64 context to JERK_TOL, the mixed
+    context (single-precision dual pair sums) to median 1e-6 and max 1e-4."""
     from paper_1801_07986_b300.inputs import WORKLOADS
     w = WORKLOADS["plummer16k"]
     x, v, m = w.state()
+    a_want = orc.accel(x, v, m, G=w.G, c=w.c, eps=w.eps)
+    j_want = orc.jerk(x, v, m, a_want, G=w.G, c=w.c, eps=w.eps)
     _, j64 = gpu_jerk(x, v, m, precision="fp64", c=w.c, eps=w.eps)
+    err64 = rel(j64, j_want)
+    assert err64.max() <= JERK_TOL, err64.max()
     _, jm = gpu_jerk(x, v, m, precision="mixed", c=w.c, eps=w.eps)
-    err = rel(jm, j64)
+    err = rel(jm, j_want)
     assert np.median(err) <= 1e-6 and err.max() <= 1e-4, (np.median(err), err.max())
 
 
