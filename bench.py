@@ -47,9 +47,11 @@ FLOPS_PASS1 = 29   # hand count of the mixed pass-1 pair body (FMA = 2, rsqrt = 
 FLOPS_PASS2 = 67   # hand count of the mixed pass-2 pair body
 FLOPS_FUSED = 77   # hand count of the scalar fused pair body (pass 1 + pass 2 sharing x, r, rsqrt)
 FLOPS_F64_FUSED = 71   # hand count of the fused double-precision pair body (rsqrt counted as 1)
-FLOPS_PACKED = 72  # hand count of the packed fused pair body, law-of-cosines form (r_near > 0)
+FLOPS_PACKED = 73  # hand count of the packed fused pair body, law-of-cosines form (r_near > 0):
+                   # 46 FP32-pipe operations, 26 of them FMA, + 1 rsqrt
 OPS_PACKED = 46    # FP32-pipe operations per pair of that body (FMA, add and mul count 1 each)
-FLOPS_PACKED_FAR = 66  # the same body on far units of the spatial order (x_ij from the high parts)
+FLOPS_PACKED_FAR = 67  # the same body on far units of the spatial order (x_ij from the high
+                       # parts: 6 adds fewer)
 OPS_PACKED_FAR = 40
 FLOPS_JERK = 213   # hand count of the dual-number pair body of the jerk
                    # (dual add 2, dual multiply 4, scalar x dual 2, rsqrt + its derivative 6)
@@ -77,6 +79,10 @@ def parse():
     ap.add_argument("--no-jerk", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--adjoint-steps", type=int, default=1000)
+    ap.add_argument("--no-adjoint-fd", action="store_true",
+                    help="skip the FP64 central-difference check of the adjoint")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the per-workload accuracy report against the oracle")
     return ap.parse_args()
 
 
@@ -223,7 +229,10 @@ def run_reference(args, w):
     oracle.build()
     x, v, m = w.state()
     steps = args.steps if args.steps is not None else 20
-    rows = 16
+    # each step a bounded sample of the evaluation: `rows` star rows and
+    # `rows` rows of the hole's double sum (each row a full O(N) sum), so the
+    # K + W steps end within a few minutes on the host cores
+    rows = max(16, min(w.n - 1, 1024))
     for _ in range(args.warmup):
         oracle_rate(x, v, m, w, rows, rows, seed=1)
     rates, secs = [], 0.0
@@ -233,11 +242,14 @@ def run_reference(args, w):
         secs += t
     value = len(rates) / sum(1.0 / r for r in rates)
     sample = (f"each step: {rows} star rows + {rows} hole double-sum rows of the N={w.n} "
-              f"evaluation, scaled by (N-1)/rows")
+              f"evaluation ({1e3 * secs / steps:.0f} ms, the line's ms_per_step), scaled to "
+              f"interactions/s by (N-1)/rows; a whole evaluation would take "
+              f"{w.n * (w.n - 1) / value:.0f} s")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "interactions/s",
         "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * w.n * (w.n - 1) / value, "higher_is_better": True,
+        "ms_per_step": 1e3 * secs / steps,
+        "interactions_per_step": 2.0 * rows * (w.n - 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_of(w, "fp64", args),
         "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": cores,
@@ -514,9 +526,16 @@ def run_native(args, w):
 
     if not args.no_adjoint and world == 1:
         try:
-            line["adjoint"] = run_adjoint(local, stream, args.adjoint_steps)
+            line["adjoint"] = run_adjoint(local, stream, args.adjoint_steps,
+                                          fd=not args.no_adjoint_fd)
         except Exception as e:  # reported, not required
             line["adjoint"] = {"error": str(e)[:300]}
+
+    if rank == 0 and world == 1 and not args.no_accuracy:
+        try:
+            line["accuracy"] = run_accuracy(local, stream)
+        except Exception as e:  # reported, not required
+            line["accuracy"] = {"error": str(e)[:300]}
 
     if rank == 0 and not args.no_cpu_baseline:
         try:
@@ -683,6 +702,7 @@ def run_jerk(local, stream, warmup, reps=5):
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
     peak = 148 * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved = FLOPS_JERK * pairs / (ms_jerk * 1e-3) / 1e12
+    both = (FLOPS_JERK + FLOPS_PACKED) * pairs / (ms_jerk * 1e-3) / 1e12
     return {"workload": "plummer16k", "n_bodies": w.n,
             "value": float(w.n) * (w.n - 1) / (ms_jerk * 1e-3), "unit": "interactions/s",
             "what": "pn_jerk in a mixed context: A + dual-number jerk (FP32 pair sums), "
@@ -693,24 +713,283 @@ def run_jerk(local, stream, warmup, reps=5):
                          "peak_basis": f"148 SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                        f"{sm_max:.0f} MHz",
                          "flops_per_pair": FLOPS_JERK,
-                         "note": "whole pn_jerk call timed (A + the dual pair kernel)"}}
+                         "note": "whole pn_jerk call timed (A + the dual pair kernel); the "
+                                 "jerk's flops only",
+                         "achieved_with_A": both, "frac_with_A": both / peak,
+                         "flops_per_pair_with_A": FLOPS_JERK + FLOPS_PACKED,
+                         "note_with_A": "the call's whole work: the A evaluation it returns "
+                                        "(packed pair body) and the dual jerk body"}}
 
 
-def run_adjoint(local, stream, nsteps):
+def run_adjoint(local, stream, nsteps, fd=True):
     """The adjoint workload: N = 8192 Plummer cluster (M = 0.1, c = 50,
     dt = 1/2048), loss = sum over the 16 stars nearest the hole at t = 0 of
-    |x(T)|^2 after nsteps KDK steps (mixed-precision forward, FP64
-    derivatives), gradient with respect to M, c, x0 and v0 through
-    pn_step_vjp with sqrt(T) checkpoints; timed with CUDA events."""
-    import torch
-    from paper_1801_07986_b300 import pn
+    |x(T)|^2 after nsteps KDK steps (mixed-precision forward, single-
+    precision pair sums in the reverse sweeps), gradient with respect to M,
+    c, x0 and v0 through pn_step_vjp with sqrt(T) checkpoints, timed with
+    CUDA events.  With `fd`: the same gradient on the FP64 path, both against
+    FP64 central differences (adjoint_fd_check), and the mixed gradient
+    against the FP64 one over every component."""
     from paper_1801_07986_b300.inputs import WORKLOADS
     w = WORKLOADS["plummer8k_adjoint"]
-    x, v, m = w.state()
+    state = w.state()
+    x = state[0]
     near = np.argsort(np.linalg.norm(x[1:] - x[0], axis=1))[:16] + 1
+    xb, vb, gM, gc, s_grad, s_fwd = adjoint_gradient(local, stream, w, state, near, nsteps,
+                                                     "mixed")
+    pairs = float(w.n) * (w.n - 1) * nsteps
+    out = {"workload": "plummer8k_adjoint", "n_bodies": w.n, "steps": nsteps,
+           "checkpoint": "every ceil(sqrt(steps)) steps",
+           "loss": "sum over the 16 stars nearest the hole at t=0 of |x(T)|^2",
+           "value": pairs / s_grad, "unit": "interactions/s",
+           "what": "trajectory steps differentiated per second x N(N-1)",
+           "gradient_s": s_grad, "forward_s": s_fwd, "gradient_over_forward": s_grad / s_fwd,
+           "dL_dM": gM, "dL_dc": gc, "grad_x0_norm": float(np.linalg.norm(xb)),
+           "grad_v0_norm": float(np.linalg.norm(vb))}
+    if fd:
+        try:
+            x6, v6, gM6, gc6, s6, _ = adjoint_gradient(local, stream, w, state, near, nsteps,
+                                                       "fp64")
+            out["fp64_gradient_s"] = s6
+            out["mixed_vs_fp64_adjoint"] = {
+                "x0_rel_norm": float(np.linalg.norm(xb - x6) / np.linalg.norm(x6)),
+                "v0_rel_norm": float(np.linalg.norm(vb - v6) / np.linalg.norm(v6)),
+                "M_rel": abs(gM - gM6) / abs(gM6), "c_rel": abs(gc - gc6) / abs(gc6)}
+            out["fd_check"] = adjoint_fd_check(
+                local, stream, nsteps, {"mixed": (xb, vb, gM, gc), "fp64": (x6, v6, gM6, gc6)},
+                near)
+        except Exception as e:  # reported, not required
+            out["fd_check"] = {"error": str(e)[:300]}
+    return out
+
+
+# ----------------------------------------------------------- accuracy --
+
+def _rel(a, b):
+    """Per-body relative error |a - b| / |b| (rows of n x 3 arrays)."""
+    return np.linalg.norm(a - b, axis=-1) / np.linalg.norm(b, axis=-1)
+
+
+def _stats(err):
+    err = np.asarray(err, dtype=np.float64)
+    return {"median": float(np.median(err)), "max": float(np.max(err)), "bodies": int(err.size)}
+
+
+def _divergence(x, v, xr, vr):
+    """Trajectory divergence of (x, v) from the reference (xr, vr): the largest
+    position and velocity differences, relative to the largest reference
+    coordinate."""
+    return {"x": float(np.abs(x - xr).max() / np.abs(xr).max()),
+            "v": float(np.abs(v - vr).max() / np.abs(vr).max())}
+
+
+class _GpuRun:
+    """One workload stepped through pn_step; accel() is A on the current state
+    (a separate buffer, so the carried acceleration is untouched)."""
+
+    def __init__(self, w, precision, local, stream, state=None):
+        import torch
+        from paper_1801_07986_b300 import pn
+        self.pn, self.w = pn, w
+        x, v, m = w.state() if state is None else state
+        self.m = m
+        dev = torch.device(f"cuda:{local}")
+        self.ctx = pn.pn_init(w.n, G=w.G, c=w.c, eps=w.eps, precision=precision, device=local,
+                              stream=stream)
+        self.X, self.V, self.M = (torch.tensor(a, device=dev) for a in (x, v, m))
+        self.A = torch.empty_like(self.X)
+        self.B = torch.empty_like(self.X)
+        pn.pn_accel(self.ctx, self.X, self.V, self.M, self.A)
+
+    def step(self, k):
+        self.pn.pn_step(self.ctx, self.X, self.V, self.M, self.A, self.w.dt, k)
+
+    def state(self):
+        self.pn.pn_sync(self.ctx)
+        return self.X.cpu().numpy(), self.V.cpu().numpy()
+
+    def accel(self):
+        self.pn.pn_accel(self.ctx, self.X, self.V, self.M, self.B)
+        self.pn.pn_sync(self.ctx)
+        return self.B.cpu().numpy()
+
+    def energy(self):
+        return self.pn.pn_energy(self.ctx, self.X, self.V, self.M)["E"]
+
+    def close(self):
+        self.ctx.close()
+
+
+def accuracy_c1(local, stream, oracle_traj):
+    """1k FP64 workload, as configured (100 steps): the same-state force error
+    against the oracle at every step (every body), the divergence of the
+    final state from the oracle's own 100 steps, and the energy change."""
+    import oracle
+    from paper_1801_07986_b300.inputs import WORKLOADS
+    w = WORKLOADS["plummer1k_fp64"]
+    r = _GpuRun(w, "fp64", local, stream)
+    worst, per_step = 0.0, []
+    E0 = r.energy()
+    for s in range(w.steps + 1):
+        if s:
+            r.step(1)
+        x, v = r.state()
+        err = _rel(r.accel(), oracle.accel(x, v, r.m, G=w.G, c=w.c, eps=w.eps))
+        per_step.append(float(err.max()))
+        worst = max(worst, float(err.max()))
+    E1 = r.energy()
+    r.close()
+    xo, vo = oracle_traj.result()
+    return {"precision": "fp64", "steps": w.steps, "bodies_checked_per_step": w.n,
+            "force_err_max_all_steps": worst,
+            "force_err_median_of_step_max": float(np.median(per_step)),
+            "divergence_vs_oracle_trajectory": _divergence(x, v, xo, vo),
+            "dE_over_E": (E1 - E0) / abs(E0), "tolerance": 1e-12}
+
+
+def accuracy_c2(local, stream, oracle_prefix, prefix_steps, rows=256):
+    """16k workload, 1000 steps in mixed precision and in FP64: the same-state
+    force error at steps 0, 100, ..., 1000 (sampled stars; the hole at the
+    first and last check), the energy change, the divergence of both runs
+    from the oracle's own trajectory over its first `prefix_steps` steps, and
+    the divergence of the mixed run from the FP64 run every 100 steps."""
+    import oracle
+    from paper_1801_07986_b300.inputs import WORKLOADS
+    w = WORKLOADS["plummer16k"]
+    out = {"steps": w.steps, "rows_per_check": rows, "hole_checked_at": [0, w.steps]}
+    traj = {}
+    for prec in ("mixed", "fp64"):
+        r = _GpuRun(w, prec, local, stream)
+        rng = np.random.default_rng(16)
+        checks, states = [], {}
+        E0 = r.energy()
+        s = 0
+        marks = sorted(set([0, prefix_steps] + list(range(100, w.steps + 1, 100))))
+        for target in marks:
+            if target > s:
+                r.step(target - s)
+                s = target
+            x, v = r.state()
+            states[s] = (x, v)
+            if s % 100:
+                continue
+            idx = list(rng.choice(np.arange(1, w.n), rows, replace=False))
+            if s in (0, w.steps):
+                idx = [0] + idx
+            err = _rel(r.accel()[idx], oracle.accel_rows(x, v, r.m, idx, G=w.G, c=w.c,
+                                                         eps=w.eps))
+            checks.append({"step": s, **_stats(err)})
+        E1 = r.energy()
+        r.close()
+        traj[prec] = states
+        out[prec] = {"same_state_force_err": checks,
+                     "force_err_median_max_over_checks": max(c["median"] for c in checks),
+                     "force_err_max_over_checks": max(c["max"] for c in checks),
+                     "dE_over_E": (E1 - E0) / abs(E0)}
+    xo, vo = oracle_prefix.result()
+    for prec in ("mixed", "fp64"):
+        x, v = traj[prec][prefix_steps]
+        out[prec]["divergence_vs_oracle_trajectory"] = {"steps": prefix_steps,
+                                                        **_divergence(x, v, xo, vo)}
+    out["mixed_vs_fp64_divergence"] = [
+        {"step": s, **_divergence(*traj["mixed"][s], *traj["fp64"][s])}
+        for s in range(100, w.steps + 1, 100)]
+    out["tolerance"] = {"fp64": 1e-12, "mixed_median": 2e-7, "mixed_max": 1e-5}
+    return out
+
+
+def accuracy_c3(local, stream, prefix_steps=3, rows_ecc=64, rows_plummer=192):
+    """128k eccentric workload, 200 mixed steps: the same-state force error at
+    steps 0, 50, ..., 200 on sampled stars of both populations (the hole's
+    O(N^2) double sum is left out: a full oracle evaluation of it takes
+    minutes on the host), and the divergence of the mixed run from the FP64
+    run over the first `prefix_steps` steps (its trajectories are outside
+    the 1PN regime and chaotic, so only same-state parity is a gate)."""
+    import oracle
+    from paper_1801_07986_b300.inputs import WORKLOADS
+    w = WORKLOADS["plummer128k_ecc"]
+    n_ecc = int(round(w.ecc_frac * (w.n - 1)))
+    r = _GpuRun(w, "mixed", local, stream)
+    rng = np.random.default_rng(128)
+    checks, s, pref = [], 0, None
+    for target in sorted(set([prefix_steps] + list(range(0, w.steps + 1, 50)))):
+        if target > s:
+            r.step(target - s)
+            s = target
+        x, v = r.state()
+        if s == prefix_steps:
+            pref = (x, v)
+        if s % 50:
+            continue
+        idx = np.concatenate([rng.choice(np.arange(1, n_ecc + 1), rows_ecc, replace=False),
+                              rng.choice(np.arange(n_ecc + 1, w.n), rows_plummer, replace=False)])
+        got = r.accel()[idx]
+        want = oracle.accel_rows(x, v, r.m, idx, G=w.G, c=w.c, eps=w.eps)
+        err = _rel(got, want)
+        checks.append({"step": s, **_stats(err), "eccentric": _stats(err[:rows_ecc])})
+    r.close()
+    f = _GpuRun(w, "fp64", local, stream)
+    f.step(prefix_steps)
+    xf, vf = f.state()
+    f.close()
+    return {"steps": w.steps, "rows_per_check": rows_ecc + rows_plummer,
+            "same_state_force_err": checks,
+            "force_err_median_max_over_checks": max(c["median"] for c in checks),
+            "force_err_max_over_checks": max(c["max"] for c in checks),
+            "divergence_vs_fp64_gpu": {"steps": prefix_steps, **_divergence(*pref, xf, vf)},
+            "tolerance": {"mixed_median": 2e-7, "mixed_max": 1e-5}}
+
+
+def run_accuracy(local, stream, prefix_16k=10):
+    """Every configured workload's accuracy against the FP64 oracle, as
+    configured (not timed).  The oracle's own trajectories (1k: 100 steps;
+    16k: the first `prefix_16k` steps) run on the host cores in a thread
+    while the GPU runs."""
+    import concurrent.futures as cf
+    import oracle
+    from paper_1801_07986_b300.inputs import WORKLOADS
+    w1, w2 = WORKLOADS["plummer1k_fp64"], WORKLOADS["plummer16k"]
+
+    def own(w, nst):
+        x, v, m = w.state()
+        a = oracle.accel(x, v, m, G=w.G, c=w.c, eps=w.eps)
+        xo, vo, _ = oracle.step(x, v, m, a, w.dt, nst, G=w.G, c=w.c, eps=w.eps)
+        return xo, vo
+
+    out = {}
+    with cf.ThreadPoolExecutor(max_workers=1) as ex:
+        f1 = ex.submit(own, w1, w1.steps)
+        f2 = ex.submit(own, w2, prefix_16k)
+        for key, fn in (("plummer1k_fp64", lambda: accuracy_c1(local, stream, f1)),
+                        ("plummer16k", lambda: accuracy_c2(local, stream, f2, prefix_16k)),
+                        ("plummer128k_ecc", lambda: accuracy_c3(local, stream))):
+            try:
+                out[key] = fn()
+            except Exception as e:  # reported, not required
+                out[key] = {"error": str(e)[:300]}
+    return out
+
+
+# Central-difference steps of the adjoint check: absolute in the hole mass,
+# the initial positions and the initial velocities; relative in c, whose
+# gradient is five orders smaller than dL/dM on the adjoint workload, so
+# its difference takes a larger step to stay above the FP64 rounding of the
+# perturbed runs.
+ADJ_FD_H = 1e-8
+ADJ_FD_H_C = 1e-6
+
+
+def adjoint_gradient(local, stream, w, state, near, nsteps, precision):
+    """Gradient of the adjoint workload's loss (sum over the stars `near` of
+    |x(T)|^2 after nsteps KDK steps) by pn_step_vjp with sqrt(T)
+    checkpoints: (xbar0, vbar0, dL/dM, dL/dc, gradient seconds, forward
+    seconds), CUDA-event timed on the launching stream."""
+    import torch
+    from paper_1801_07986_b300 import pn
+    x, v, m = state
     dev = torch.device(f"cuda:{local}")
     X0, V0, M = (torch.tensor(a, device=dev) for a in (x, v, m))
-    ctx = pn.pn_init(w.n, G=w.G, c=w.c, eps=w.eps, precision="mixed", device=local,
+    ctx = pn.pn_init(w.n, G=w.G, c=w.c, eps=w.eps, precision=precision, device=local,
                      stream=stream)
     X, V = X0.clone(), V0.clone()
     A = torch.empty_like(X)
@@ -728,24 +1007,113 @@ def run_adjoint(local, stream, nsteps):
     XB, VB = torch.empty_like(X), torch.empty_like(X)
     pn.pn_step_vjp(ctx, X0, V0, M, w.dt, 2, xbT, vbT, XB, VB)       # allocations, warm-up
     torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
     e0.record(stream)
     scal = pn.pn_step_vjp(ctx, X0, V0, M, w.dt, nsteps, xbT, vbT, XB, VB)
     e1.record(stream)
     e1.synchronize()
-    wall = time.perf_counter() - t0
     ms_grad = e0.elapsed_time(e1)
     ctx.close()
-    pairs = float(w.n) * (w.n - 1) * nsteps
-    return {"workload": "plummer8k_adjoint", "n_bodies": w.n, "steps": nsteps,
-            "checkpoint": "every ceil(sqrt(steps)) steps",
-            "loss": "sum over the 16 stars nearest the hole at t=0 of |x(T)|^2",
-            "value": pairs / (ms_grad * 1e-3), "unit": "interactions/s",
-            "what": "trajectory steps differentiated per second x N(N-1)",
-            "gradient_s": ms_grad * 1e-3, "gradient_wall_s": wall,
-            "forward_s": ms_fwd * 1e-3, "gradient_over_forward": ms_grad / ms_fwd,
-            "dL_dM": float(scal[0, 0]), "dL_dc": float(-2.0 * scal[0, 1] / w.c ** 3),
-            "grad_x0_norm": float(torch.linalg.norm(XB)), "grad_v0_norm": float(torch.linalg.norm(VB))}
+    return (XB.cpu().numpy(), VB.cpu().numpy(), float(scal[0, 0]),
+            float(-2.0 * scal[0, 1] / w.c ** 3), ms_grad * 1e-3, ms_fwd * 1e-3)
+
+
+def adjoint_fd_check(local, stream, nsteps, grads, near, h=ADJ_FD_H):
+    """Gradients of the adjoint workload's loss against FP64 central
+    differences.  `grads` maps a name ("mixed", "fp64") to (xbar0, vbar0,
+    dL/dM, dL/dc) from pn_step_vjp; the first entry picks the components.
+    Checked: dL/dM, dL/dc, and four components each of dL/dx0 and dL/dv0 --
+    the two largest of tagged stars (the 16 nearest the hole) and the two
+    largest of the untagged stars: a difference over a chaotic 1000-step run
+    carries the two perturbed runs' FP64 rounding grown by the dynamics
+    (about 3e-3 absolute at h = 1e-8 on this workload), so only components
+    well above that are resolved to 1e-6.  Every perturbed trajectory is one cluster of a single
+    batched FP64 context (all of them advance in the same launches); dL/dM
+    is also differenced at 2h, whose gap to the h difference bounds the
+    difference's truncation error.  With two gradient sets each checked
+    component also gets their mutual difference."""
+    import torch
+    from paper_1801_07986_b300 import pn
+    from paper_1801_07986_b300.inputs import WORKLOADS
+    w = WORKLOADS["plummer8k_adjoint"]
+    x, v, m = w.state()
+    names = list(grads)
+    xb = grads[names[0]][0]
+    vb = grads[names[0]][1]
+    tagged = set(int(j) for j in near)
+    untag = np.array([j for j in range(1, w.n) if j not in tagged])
+    tag = np.array(sorted(tagged))
+    params = [("M", 0, 0, h), ("M", 0, 0, 2 * h), ("c", 0, 0, ADJ_FD_H_C)]
+    for name, g in (("x0", xb), ("v0", vb)):
+        for rows in (tag, untag):
+            flat = np.abs(g[rows]).ravel()
+            for q in np.argsort(flat)[::-1][:2]:
+                params.append((name, int(rows[q // 3]), int(q % 3), h))
+    xs, vs, ms, cs = [], [], [], []
+    for name, j, k, hh in params:
+        for sgn in (1.0, -1.0):
+            xx, vv, mm, cc = x.copy(), v.copy(), m.copy(), w.c
+            if name == "M":
+                mm[0] += sgn * hh
+            elif name == "c":
+                cc = w.c * (1.0 + sgn * hh)
+            elif name == "x0":
+                xx[j, k] += sgn * hh
+            else:
+                vv[j, k] += sgn * hh
+            xs.append(xx), vs.append(vv), ms.append(mm), cs.append(cc)
+    nc = len(xs)
+    off = np.arange(nc + 1) * w.n
+    dev = torch.device(f"cuda:{local}")
+    X = torch.tensor(np.concatenate(xs), device=dev)
+    V = torch.tensor(np.concatenate(vs), device=dev)
+    M = torch.tensor(np.concatenate(ms), device=dev)
+    A = torch.empty_like(X)
+    ctx = pn.pn_init_batched(off, G=w.G, c=cs, eps=w.eps, precision="fp64", device=local,
+                             stream=stream)
+    t0 = time.perf_counter()
+    pn.pn_accel(ctx, X, V, M, A)
+    pn.pn_step(ctx, X, V, M, A, w.dt, nsteps)
+    pn.pn_sync(ctx)
+    secs = time.perf_counter() - t0
+    ctx.close()
+    xT = X.cpu().numpy().reshape(nc, w.n, 3)
+    L = (xT[:, near, :] ** 2).sum(axis=(1, 2))
+
+    def value(gs, name, j, k):
+        if name == "M":
+            return gs[2]
+        if name == "c":
+            return gs[3]
+        return (gs[0] if name == "x0" else gs[1])[j, k]
+
+    checks, fdM = [], {}
+    for q, (name, j, k, hh) in enumerate(params):
+        fd = (L[2 * q] - L[2 * q + 1]) / (2 * hh * (w.c if name == "c" else 1.0))
+        if name == "M":
+            fdM[hh] = fd
+            if hh != h:
+                continue
+        row = {"param": name if name in ("M", "c") else f"{name}[{j},{k}]",
+               "tagged": j in tagged, "central_difference": float(fd)}
+        for nm in names:
+            g = value(grads[nm], name, j, k)
+            row[nm] = float(g)
+            row[f"rel_err_{nm}"] = float(abs(g - fd) / abs(fd))
+        if len(names) > 1:
+            g0, g1 = value(grads[names[0]], name, j, k), value(grads[names[1]], name, j, k)
+            row[f"rel_{names[0]}_vs_{names[1]}"] = float(abs(g0 - g1) / abs(g1))
+        checks.append(row)
+    out = {"steps": nsteps, "h": h, "h_c": ADJ_FD_H_C,
+           "h_note": "absolute in M, x0 and v0; relative in c",
+           "fd_path": "fp64 (batched context, one cluster per perturbed trajectory)",
+           "fd_seconds": secs, "checks": checks,
+           "fd_dL_dM_h_vs_2h_rel": float(abs(fdM[h] - fdM[2 * h]) / abs(fdM[h]))}
+    for nm in names:
+        out[f"max_rel_err_{nm}"] = max(c[f"rel_err_{nm}"] for c in checks)
+    if len(names) > 1:
+        key = f"rel_{names[0]}_vs_{names[1]}"
+        out[f"max_{key}"] = max(c[key] for c in checks)
+    return out
 
 
 def main():
