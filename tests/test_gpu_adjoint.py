@@ -205,6 +205,23 @@ def test_step_vjp_mixed_trajectory(orc):
         rhs = np.sum(xbT * jx) + np.sum(vbT * jv)
         lhs = np.sum(x64 * u) + np.sum(v64 * w)
         assert abs(lhs - rhs) <= 1e-8 * abs(rhs)
+    # the mixed gradient per body against the oracle's exact derivative of
+    # the trajectory (complex step) along each unit direction: 12 bodies, the
+    # hole among them, all six components
+    bodies = [0] + list(rng.choice(np.arange(1, n), 11, replace=False))
+    z = np.zeros_like(x)
+    xw, vw = np.zeros((len(bodies), 3)), np.zeros((len(bodies), 3))
+    for q, i in enumerate(bodies):
+        for k in range(3):
+            e = np.zeros_like(x)
+            e[i, k] = 1.0
+            _, _, jx, jv = orc.traj_jvp(x, v, m, dt, nst, e, z, c=c, eps=eps)
+            xw[q, k] = np.sum(xbT * jx) + np.sum(vbT * jv)
+            _, _, jx, jv = orc.traj_jvp(x, v, m, dt, nst, z, e, c=c, eps=eps)
+            vw[q, k] = np.sum(xbT * jx) + np.sum(vbT * jv)
+    for got, want in ((xm[bodies], xw), (vm[bodies], vw)):
+        err = np.linalg.norm(got - want, axis=1) / np.linalg.norm(want, axis=1)
+        assert np.median(err) <= 1e-6 and err.max() <= 1e-4, (np.median(err), err.max())
 
 
 def test_autograd_trajectory_loss_of_the_nearest_stars():
