@@ -137,6 +137,41 @@ def test_tune_keeps_parity(orc):
     ctx.close()
 
 
+TUNE_CHILD = r"""
+import sys, torch
+from paper_1801_07986_b300 import pn
+from paper_1801_07986_b300.inputs import make_cluster
+x, v, m = make_cluster(3000, 0.1, 77)
+X, V, M = (torch.tensor(a, device="cuda:0") for a in (x, v, m))
+A = torch.empty_like(X)
+ctx = pn.pn_init(3000, c=30.0, eps=1e-4, precision="mixed", device=0)
+t = pn.pn_tune(ctx, X, V, M, A)
+print(int(t["cached"]), t["targets_per_thread"], t["unroll"], int(t["packed"]), t["tile"], t["stages"])
+"""
+
+
+def test_tune_reports_tile_and_keeps_its_choice_in_the_cache_file(tmp_path):
+    """pn_tune searches the packed kernel's j-tile and buffers too, reports
+    them, and with PN_TUNE_CACHE a later process takes the choice from the
+    file without timing again."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, PYTHONPATH=root, PN_TUNE_CACHE=str(tmp_path / "tune.txt"))
+    runs = [subprocess.run([sys.executable, "-c", TUNE_CHILD], env=env, capture_output=True,
+                           text=True, timeout=600, cwd=root) for _ in range(2)]
+    for r in runs:
+        assert r.returncode == 0, r.stderr[-2000:]
+    first, second = (r.stdout.split() for r in runs)
+    assert first[0] == "0" and second[0] == "1"           # timed, then read from the file
+    assert first[1:] == second[1:]
+    P, unroll, packed, tile, stages = (int(q) for q in first[1:])
+    assert (tile, stages) in ((64, 6), (64, 4), (32, 8)) if packed else stages == 0
+    lines = (tmp_path / "tune.txt").read_text().split("\n")
+    assert len([q for q in lines if q.strip()]) == 1
+
+
 def test_nonfinite_in_one_cluster_is_reported():
     x, v, m, off, cs, es = batch(sizes=[300, 600])
     x = x.copy()

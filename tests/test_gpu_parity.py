@@ -126,6 +126,36 @@ def test_fused_variants_match_oracle(orc, monkeypatch, packed, targets, unroll):
     assert np.median(err) <= MIX_MED and err.max() <= MIX_MAX, (np.median(err), err.max())
 
 
+# the packed kernel's j-tile and buffer variants (PN_FUSED_TILE,
+# PN_FUSED_STAGES): (spatial order, tile, buffers, targets per thread)
+TILE_VARIANTS = [("0", 64, 4, "2"), ("0", 64, 4, "4"), ("0", 32, 8, "2"), ("0", 32, 8, "4"),
+                 ("1", 64, 4, "2"), ("1", 64, 4, "4")]
+
+
+@pytest.mark.parametrize("spatial,tile,stages,targets", TILE_VARIANTS)
+def test_packed_tile_variants_match_oracle(orc, monkeypatch, spatial, tile, stages, targets):
+    monkeypatch.setenv("PN_SPATIAL", spatial)
+    monkeypatch.setenv("PN_FUSED_PACKED", "1")
+    monkeypatch.setenv("PN_FUSED_TARGETS", targets)
+    monkeypatch.setenv("PN_FUSED_TILE", str(tile))
+    monkeypatch.setenv("PN_FUSED_STAGES", str(stages))
+    n = 2 * 1024 + 130
+    x, v, m = cluster(n, 0.2, 4343)
+    x[5] = x[0] + np.array([0.01, 0.0, 0.0])
+    want = orc.accel(x, v, m, c=15.0, eps=1e-4)
+    ctx = pn.pn_init(n, c=15.0, eps=1e-4, precision="mixed", device=0)
+    shape = pn.pn_get_launch(ctx)
+    assert shape["packed"] and shape["tile"] == tile
+    X, V, M = dev(x), dev(v), dev(m)
+    A = torch.empty_like(X)
+    pn.pn_accel(ctx, X, V, M, A)
+    pn.pn_sync(ctx)
+    got = A.cpu().numpy()
+    ctx.close()
+    err = rel(got, want)
+    assert np.median(err) <= MIX_MED and err.max() <= MIX_MAX, (np.median(err), err.max())
+
+
 def test_fp64_fused_equals_two_pass():
     """In FP64 the fused sweep and the two passes form the same sums in the
     same order: bitwise equal accelerations."""

@@ -558,3 +558,37 @@ def test_hole_partial_sums_partition_the_hole_acceleration(orc):
                        atol=0)
     empty = orc.bh_partial(x, v, m, 5, 5, eps=eps)
     assert not np.any(empty[0]) and not np.any(empty[1])
+
+
+def test_eih_step_is_second_order_and_follows_the_limited_trajectory(orc):
+    """The KDK integrator driven by the general EIH accelerations (the
+    cross-check's integrator): second-order self-convergence, and over a few
+    steps its trajectory departs from the limited equations' one by the
+    dropped orders only (halving the star masses divides the position
+    difference by 4, the degree of the star terms that Section 2 drops)."""
+    x, v, m = _orbiting_stars(2, 1e-3, seed=4)
+    c = 4.0
+    v = _zero_momentum(v, m)
+    a = orc.eih_accel(x, v, m, c=c)
+    T = 2.0
+    xs = []
+    for nst in (200, 400, 800):
+        xx, _, _ = orc.eih_step(x, v, m, a, T / nst, nst, c=c)
+        xs.append(xx)
+    r = np.linalg.norm(xs[0] - xs[1]) / np.linalg.norm(xs[1] - xs[2])
+    assert 3.6 < r < 4.4, r
+
+    xr, vr, mr = _random_state(6, 11, m_bh=1.0, m_star=0.02, vscale=0.3)
+
+    def gap(scale):
+        mm = mr.copy()
+        mm[1:] *= scale
+        vv = _zero_momentum(vr, mm)
+        a_l = orc.accel(xr, vv, mm, c=c)
+        a_e = orc.eih_accel(xr, vv, mm, c=c)
+        x_l, _, _ = orc.step(xr, vv, mm, a_l, 1e-3, 5, c=c)
+        x_e, _, _ = orc.eih_step(xr, vv, mm, a_e, 1e-3, 5, c=c)
+        return np.linalg.norm(x_l[1:] - x_e[1:])
+
+    g1, g2, g3 = gap(1.0), gap(0.5), gap(0.25)
+    assert 3.5 < g1 / g2 < 4.5 and 3.5 < g2 / g3 < 4.5, (g1 / g2, g2 / g3)
