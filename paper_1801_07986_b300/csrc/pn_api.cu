@@ -216,12 +216,19 @@ pn_status evaluate(pn_ctx *c, const double *x, const double *vel, const double *
                    double *v, double h, double dt_next = 0.0)
 {
     PN_CUDA(pn::launch_prologue(c, x, vel, m, false), "prologue launch");
-    // the near-source pass reads only the prologue's records: it forks onto
-    // the side stream once the prologue is done and runs beside the pair
-    // kernel (in the resources that kernel leaves, or in its tail), joining
-    // before the epilogue; launched after the pair kernel, so that kernel's
-    // resident blocks all start at once
-    const bool fork = c->any_near && c->side;
+    // The pair kernels read only the prologue's records: the cluster sums,
+    // the near-source records and the near-source pass fork onto the side
+    // stream once the prologue is done and run beside the pair kernel (in
+    // the resources that kernel leaves, or in its tail), joining before the
+    // epilogue, which reads them all; they are launched after the pair
+    // kernel, so that kernel's resident blocks all start at once.  (The
+    // spatial order's sort reads the cluster sums: there they come first.)
+    const bool sums_first = pn::pairs_need_sums(c);
+    if (sums_first || !c->side)
+        PN_CUDA(pn::launch_global_sums(c), "global sums launch");
+    const bool fork = c->side != nullptr;
+    if (!fork)
+        PN_CUDA(pn::launch_near_scatter(c, x, m), "near scatter launch");
     if (fork)
         PN_CUDA(cudaEventRecord(c->ev_fork, c->stream), "fork event");
     if (pn::use_fused(c)) {
@@ -236,9 +243,13 @@ pn_status evaluate(pn_ctx *c, const double *x, const double *vel, const double *
         PN_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0), "fork wait");
         cudaStream_t main = c->stream;
         c->stream = c->side;
-        const cudaError_t e = pn::launch_near(c);
+        cudaError_t e = sums_first ? cudaSuccess : pn::launch_global_sums(c);
+        if (e == cudaSuccess)
+            e = pn::launch_near_scatter(c, x, m);
+        if (e == cudaSuccess)
+            e = pn::launch_near(c);
         c->stream = main;
-        PN_CUDA(e, "near-pass launch");
+        PN_CUDA(e, "side-stream launch");
         PN_CUDA(cudaEventRecord(c->ev_join, c->side), "join event");
         PN_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0), "join wait");
     } else {

@@ -203,8 +203,15 @@ cudaError_t launch_jerk(pn_ctx *c, const double *x, const double *v, const doubl
 cudaError_t launch_hermite(pn_ctx *c, int stage, double *x, double *v, double *a, double *j,
                            const double *a1, const double *j1, double *xe, double *ve,
                            double dt);
+// The records of an evaluation (k_prologue; with energy_records the energy's
+// double records); then the cluster sums (k_global_sums: totals, near-star
+// counts) and the near-source records (k_near_scatter), which the pair
+// kernels do not read (except the spatial order's sort: pairs_need_sums).
 cudaError_t launch_prologue(pn_ctx *c, const double *x, const double *vel, const double *m,
                             bool energy_records);
+cudaError_t launch_global_sums(pn_ctx *c);
+cudaError_t launch_near_scatter(pn_ctx *c, const double *x, const double *m);
+bool pairs_need_sums(const pn_ctx *c);
 cudaError_t launch_pass1(pn_ctx *c);
 cudaError_t launch_pass2(pn_ctx *c);
 cudaError_t launch_near(pn_ctx *c);

@@ -1947,7 +1947,7 @@ cudaError_t launch_rk4_stage(pn_ctx *c, int stage, double *x, double *v, const d
 cudaError_t launch_prologue(pn_ctx *c, const double *x, const double *vel, const double *m,
                             bool energy_records)
 {
-    const int64_t nb = c->S / kGlueThreads, npb = c->S / kProThreads;
+    const int64_t npb = c->S / kProThreads;
     const int *bc = blk_table(c);
     if (energy_records) {
         k_prologue<2><<<(unsigned)npb, kProThreads, 0, c->stream>>>(
@@ -1964,19 +1964,28 @@ cudaError_t launch_prologue(pn_ctx *c, const double *x, const double *vel, const
         k_prologue<1><<<(unsigned)npb, kProThreads, 0, c->stream>>>(
             c->S, c->d_clu, bc, x, vel, m, c->mrec, c->drec, c->nflag, c->blk, c->wcount, 0);
     c->launches += 1;
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess)
-        return e;
-    if (mixed)
+    return cudaGetLastError();
+}
+
+cudaError_t launch_global_sums(pn_ctx *c)
+{
+    if (c->p.precision == PN_MIXED)
         k_global_sums<0><<<c->nclu, kGlueThreads, 0, c->stream>>>(
             c->d_clu, c->nclu, c->blk, c->glob, c->ncount, c->nrec, c->ndrec, c->NC);
     else
         k_global_sums<1><<<c->nclu, kGlueThreads, 0, c->stream>>>(
             c->d_clu, c->nclu, c->blk, c->glob, c->ncount, c->nrec, c->ndrec, c->NC);
     c->launches += 1;
-    if ((e = cudaGetLastError()) != cudaSuccess || !c->any_near)
-        return e;
-    if (mixed)
+    return cudaGetLastError();
+}
+
+cudaError_t launch_near_scatter(pn_ctx *c, const double *x, const double *m)
+{
+    if (!c->any_near)
+        return cudaSuccess;
+    const int64_t nb = c->S / kGlueThreads;
+    const int *bc = blk_table(c);
+    if (c->p.precision == PN_MIXED)
         k_near_scatter<0><<<(unsigned)nb, kGlueThreads, 0, c->stream>>>(
             c->d_clu, c->nclu, bc, x, m, c->nflag, c->ncount, c->nrec, c->ndrec, c->NC);
     else
@@ -1984,6 +1993,13 @@ cudaError_t launch_prologue(pn_ctx *c, const double *x, const double *vel, const
             c->d_clu, c->nclu, bc, x, m, c->nflag, c->ncount, c->nrec, c->ndrec, c->NC);
     c->launches += 1;
     return cudaGetLastError();
+}
+
+// The spatial order's sort keys read the cluster sums (the mean |d|), so the
+// pair kernel depends on them there; elsewhere it reads only the records.
+bool pairs_need_sums(const pn_ctx *c)
+{
+    return use_fused(c) && c->fused_packed && c->spatial && packed_loc(c);
 }
 
 bool use_fused(const pn_ctx *c)
