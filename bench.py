@@ -735,8 +735,8 @@ def run_adjoint(local, stream, nsteps, fd=True):
     state = w.state()
     x = state[0]
     near = np.argsort(np.linalg.norm(x[1:] - x[0], axis=1))[:16] + 1
-    xb, vb, gM, gc, s_grad, s_fwd = adjoint_gradient(local, stream, w, state, near, nsteps,
-                                                     "mixed")
+    xb, vb, gM, gc, s_grad, s_fwd, s_x0 = adjoint_gradient(local, stream, w, state, near,
+                                                           nsteps, "mixed", from_x0=True)
     pairs = float(w.n) * (w.n - 1) * nsteps
     out = {"workload": "plummer8k_adjoint", "n_bodies": w.n, "steps": nsteps,
            "checkpoint": "every ceil(sqrt(steps)) steps",
@@ -744,12 +744,17 @@ def run_adjoint(local, stream, nsteps, fd=True):
            "value": pairs / s_grad, "unit": "interactions/s",
            "what": "trajectory steps differentiated per second x N(N-1)",
            "gradient_s": s_grad, "forward_s": s_fwd, "gradient_over_forward": s_grad / s_fwd,
+           "gradient_note": "forward = pn_accel + pn_step_save (the steps keeping the "
+                            "checkpoints); gradient = pn_step_vjp_saved (re-runs each segment "
+                            "once, then the reverse); gradient_from_x0_s = pn_step_vjp, which "
+                            "runs the forward itself first (same result, checked bitwise)",
+           "gradient_from_x0_s": s_x0,
            "dL_dM": gM, "dL_dc": gc, "grad_x0_norm": float(np.linalg.norm(xb)),
            "grad_v0_norm": float(np.linalg.norm(vb))}
     if fd:
         try:
-            x6, v6, gM6, gc6, s6, _ = adjoint_gradient(local, stream, w, state, near, nsteps,
-                                                       "fp64")
+            x6, v6, gM6, gc6, s6, _, _ = adjoint_gradient(local, stream, w, state, near,
+                                                          nsteps, "fp64")
             out["fp64_gradient_s"] = s6
             out["mixed_vs_fp64_adjoint"] = {
                 "x0_rel_norm": float(np.linalg.norm(xb - x6) / np.linalg.norm(x6)),
@@ -986,11 +991,14 @@ ADJ_FD_SMALL_G = 1e3
 ADJ_FD_H_SMALL = 1e-6
 
 
-def adjoint_gradient(local, stream, w, state, near, nsteps, precision):
+def adjoint_gradient(local, stream, w, state, near, nsteps, precision, from_x0=False):
     """Gradient of the adjoint workload's loss (sum over the stars `near` of
-    |x(T)|^2 after nsteps KDK steps) by pn_step_vjp with sqrt(T)
-    checkpoints: (xbar0, vbar0, dL/dM, dL/dc, gradient seconds, forward
-    seconds), CUDA-event timed on the launching stream."""
+    |x(T)|^2 after nsteps KDK steps) with sqrt(T) checkpoints: the forward
+    keeps its checkpoints (pn_step_save), the backward starts from them
+    (pn_step_vjp_saved).  Returns (xbar0, vbar0, dL/dM, dL/dc, backward
+    seconds, forward seconds, and with from_x0 the seconds of pn_step_vjp,
+    which runs the forward again itself, else None), CUDA-event timed on the
+    launching stream."""
     import torch
     from paper_1801_07986_b300 import pn
     x, v, m = state
@@ -998,30 +1006,44 @@ def adjoint_gradient(local, stream, w, state, near, nsteps, precision):
     X0, V0, M = (torch.tensor(a, device=dev) for a in (x, v, m))
     ctx = pn.pn_init(w.n, G=w.G, c=w.c, eps=w.eps, precision=precision, device=local,
                      stream=stream)
-    X, V = X0.clone(), V0.clone()
-    A = torch.empty_like(X)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    XB, VB = torch.empty_like(X0), torch.empty_like(X0)
+    # warm-up: allocations of both halves
+    X, V, A = X0.clone(), V0.clone(), torch.empty_like(X0)
+    pn.pn_accel(ctx, X, V, M, A)
+    ck = pn.pn_step_save(ctx, X, V, M, A, w.dt, 2)
+    pn.pn_step_vjp_saved(ctx, ck, M, w.dt, 2, X, V, XB, VB)
+    del ck
+    X, V = X0.clone(), V0.clone()
+    torch.cuda.synchronize(dev)
     e0.record(stream)
     pn.pn_accel(ctx, X, V, M, A)
-    pn.pn_step(ctx, X, V, M, A, w.dt, nsteps)
+    ckpt = pn.pn_step_save(ctx, X, V, M, A, w.dt, nsteps)
     e1.record(stream)
     e1.synchronize()
     ms_fwd = e0.elapsed_time(e1)
     xbT = torch.zeros_like(X)
     xbT[near] = 2.0 * X[near]
     vbT = torch.zeros_like(X)
-    XB, VB = torch.empty_like(X), torch.empty_like(X)
-    pn.pn_step_vjp(ctx, X0, V0, M, w.dt, 2, xbT, vbT, XB, VB)       # allocations, warm-up
-    torch.cuda.synchronize(dev)
     e0.record(stream)
-    scal = pn.pn_step_vjp(ctx, X0, V0, M, w.dt, nsteps, xbT, vbT, XB, VB)
+    scal = pn.pn_step_vjp_saved(ctx, ckpt, M, w.dt, nsteps, xbT, vbT, XB, VB)
     e1.record(stream)
     e1.synchronize()
     ms_grad = e0.elapsed_time(e1)
+    s_x0 = None
+    if from_x0:
+        XB2, VB2 = torch.empty_like(X0), torch.empty_like(X0)
+        e0.record(stream)
+        scal2 = pn.pn_step_vjp(ctx, X0, V0, M, w.dt, nsteps, xbT, vbT, XB2, VB2)
+        e1.record(stream)
+        e1.synchronize()
+        s_x0 = e0.elapsed_time(e1) * 1e-3
+        if not (torch.equal(XB, XB2) and torch.equal(VB, VB2) and np.array_equal(scal, scal2)):
+            raise RuntimeError("pn_step_vjp and pn_step_vjp_saved differ")
     ctx.close()
     return (XB.cpu().numpy(), VB.cpu().numpy(), float(scal[0, 0]),
-            float(-2.0 * scal[0, 1] / w.c ** 3), ms_grad * 1e-3, ms_fwd * 1e-3)
+            float(-2.0 * scal[0, 1] / w.c ** 3), ms_grad * 1e-3, ms_fwd * 1e-3, s_x0)
 
 
 def adjoint_fd_check(local, stream, nsteps, grads, near, h=ADJ_FD_H):

@@ -229,6 +229,29 @@ pn_status pn_step_vjp(pn_ctx *ctx, const double *x0, const double *v0, const dou
                       const double *vbar_T, double *xbar0, double *vbar0, double *scal);
 
 /*
+ * The forward half of pn_step_vjp, for callers that run the forward anyway:
+ * nsteps PN_KDK steps in place exactly as pn_step (same trajectory, bit for
+ * bit), storing the state (x, v, a, n x 3 each) before steps 0, K, 2K, ...
+ * into ckpt, K = checkpoint (0: the integer ceiling of sqrt(nsteps)).  ckpt
+ * is a caller-owned DEVICE array of ceil(nsteps / K) x 9n doubles; a must
+ * hold A(x, v) on entry.  Errors: as pn_step, plus PN_EUNSUPPORTED
+ * (integrator other than PN_KDK).
+ */
+pn_status pn_step_save(pn_ctx *ctx, double *x, double *v, const double *m, double *a, double dt,
+                       int64_t nsteps, int64_t checkpoint, double *ckpt);
+
+/*
+ * The backward half of pn_step_vjp from the checkpoints pn_step_save wrote
+ * for the same (m, dt, nsteps, checkpoint): each segment is recomputed once
+ * on the way back (K x 9n doubles of scratch), then differentiated as in
+ * pn_step_vjp; the result equals pn_step_vjp's from the same start state.
+ * Allocates and frees its scratch; waits.  Errors: as pn_step_vjp.
+ */
+pn_status pn_step_vjp_saved(pn_ctx *ctx, const double *ckpt, const double *m, double dt,
+                            int64_t nsteps, int64_t checkpoint, const double *xbar_T,
+                            const double *vbar_T, double *xbar0, double *vbar0, double *scal);
+
+/*
  * pn_step captured into one CUDA graph and launched as a whole: the first
  * call for a given (x, v, m, a, dt, nsteps) records the nsteps steps (every
  * kernel launch of every step) into a graph; later calls with the same

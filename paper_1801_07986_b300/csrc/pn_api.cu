@@ -869,6 +869,242 @@ pn_status pn_accel_vjp(pn_ctx *c, const double *x, const double *v, const double
 // stores (x, v, a) every K steps; the backward pass re-runs each segment
 // from its checkpoint, keeping the K pre-step states, and walks it in
 // reverse.  Memory (K + steps/K) 9n doubles.
+namespace {
+// Workspace of the KDK adjoint: one step's states and cotangents and one
+// segment of K pre-step states.
+struct AdjWork {
+    double *xs, *vs, *as, *xp, *vp, *atot, *xbA, *vpbA, *xb, *vb, *ab, *seg, *dscal;
+    double *w;
+    // mixed contexts with the fused kernel: each recomputed step's 16
+    // forward pair sums (16 S doubles) and staged source records (9 S
+    // float4), for the reverse of that step (nullptr otherwise)
+    double *sums;
+    float4 *srec;
+};
+
+// The recomputed segments keep their pair sums for the reverse (see
+// AdjWork) where the forward pair kernel is the fused one.
+bool adj_saves_sums(const pn_ctx *c) { return pn::use_fused(c); }
+
+constexpr int64_t kAdjSumVals = 16;                       // pair sums per slot
+constexpr int64_t kAdjSrecDoubles = 2 * pn::kPackVals;     // 9 float4 per slot
+
+int64_t checkpoint_interval(int64_t nsteps, int64_t checkpoint)
+{
+    int64_t K = checkpoint;
+    if (K == 0) {
+        K = 1;
+        while (K * K < nsteps)
+            ++K;
+    }
+    return K;
+}
+
+// Allocates the workspace, with room for ncp checkpoints after ab when
+// own_checkpoints (returned in *cp).
+pn_status adj_alloc(pn_ctx *c, int64_t K, int64_t ncp, bool own_checkpoints, AdjWork *W,
+                    double **cp)
+{
+    const size_t n3 = 3 * (size_t)c->n;
+    const size_t per_step = adj_saves_sums(c) ? (size_t)(kAdjSumVals + kAdjSrecDoubles) * c->S : 0;
+    // (+ 16 doubles: the saved regions start 128-byte aligned)
+    const size_t nwork = 11 * n3 + (size_t)((own_checkpoints ? ncp : 0) + K) * 3 * n3 +
+                         (size_t)K * per_step + (per_step ? 16 : 0);
+    W->w = nullptr;
+    W->dscal = nullptr;
+    W->sums = nullptr;
+    W->srec = nullptr;
+    if (std::getenv("PN_FAIL_ALLOC") ||
+        cudaMalloc((void **)&W->w, sizeof(double) * nwork) != cudaSuccess) {
+        cudaGetLastError();
+        W->w = nullptr;
+        return fail(PN_ENOMEM, "cudaMalloc of %zu bytes for the adjoint failed",
+                    sizeof(double) * nwork);
+    }
+    if (cudaMalloc((void **)&W->dscal, sizeof(double) * 2 * c->nclu) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(W->w);
+        W->w = nullptr;
+        W->dscal = nullptr;
+        return fail(PN_ENOMEM, "cudaMalloc for the adjoint failed");
+    }
+    W->xs = W->w;
+    W->vs = W->xs + n3;
+    W->as = W->vs + n3;
+    W->xp = W->as + n3;
+    W->vp = W->xp + n3;
+    W->atot = W->vp + n3;
+    W->xbA = W->atot + n3;
+    W->vpbA = W->xbA + n3;
+    W->xb = W->vpbA + n3;
+    W->vb = W->xb + n3;
+    W->ab = W->vb + n3;
+    double *after = W->ab + n3;
+    if (own_checkpoints) {
+        *cp = after;
+        after += (size_t)ncp * 3 * n3;
+    }
+    W->seg = after;
+    after += (size_t)K * 3 * n3;
+    if (per_step) {
+        // S is a multiple of 512, so the records follow the sums aligned too
+        const uintptr_t a = (reinterpret_cast<uintptr_t>(after) + 127) & ~(uintptr_t)127;
+        W->sums = reinterpret_cast<double *>(a);
+        W->srec = reinterpret_cast<float4 *>(W->sums + (size_t)K * kAdjSumVals * c->S);
+    }
+    return PN_OK;
+}
+
+// Switches the near-source split off for the adjoint's recomputed segments
+// (every cluster's r_near < 0: the evaluation then uses the form the
+// reverse differentiates, and its pair sums serve the reverse directly)
+// and back on.
+struct FarForm {
+    pn_ctx *c = nullptr;
+    double *saved = nullptr;
+    pn_status enter(pn_ctx *ctx)
+    {
+        c = ctx;
+        if (!c->any_near)
+            return PN_OK;
+        saved = new (std::nothrow) double[(size_t)c->nclu];
+        if (!saved)
+            return fail(PN_ENOMEM, "host allocation failed");
+        for (int k = 0; k < c->nclu; ++k) {
+            saved[k] = c->hclu[k].r_near;
+            c->hclu[k].r_near = -1.0;
+        }
+        set_params(c, &c->p, false);
+        return upload_clusters(c);
+    }
+    pn_status leave()
+    {
+        if (!saved)
+            return PN_OK;
+        for (int k = 0; k < c->nclu; ++k)
+            c->hclu[k].r_near = saved[k];
+        delete[] saved;
+        saved = nullptr;
+        set_params(c, &c->p, false);
+        return upload_clusters(c);
+    }
+};
+
+void adj_free(pn_ctx *c, AdjWork *W)
+{
+    cudaStreamSynchronize(c->stream);
+    if (W->w)
+        cudaFree(W->w);
+    if (W->dscal)
+        cudaFree(W->dscal);
+}
+
+// The forward KDK steps from (x, v, a) in place, writing (x, v, a) before
+// steps 0, K, 2K, ... into cp (9 n doubles each); the steps between two
+// checkpoints run as one pn_step sequence.
+pn_status kdk_forward_checkpoints(pn_ctx *c, double *x, double *v, const double *m, double *a,
+                                  double dt, int64_t nsteps, int64_t K, double *cp)
+{
+    const size_t n3 = 3 * (size_t)c->n, b3 = sizeof(double) * n3;
+    for (int64_t s = 0; s < nsteps; s += K) {
+        double *q = cp + (size_t)(s / K) * 3 * n3;
+        PN_CUDA(cudaMemcpyAsync(q, x, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+        PN_CUDA(cudaMemcpyAsync(q + n3, v, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+        PN_CUDA(cudaMemcpyAsync(q + 2 * n3, a, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+        const pn_status st = run_steps(c, x, v, m, a, dt, s + K < nsteps ? K : nsteps - s);
+        if (st != PN_OK)
+            return st;
+    }
+    return PN_OK;
+}
+
+// The reverse of nsteps KDK steps from their checkpoints cp (the states
+// before steps 0, K, 2K, ...): each segment is run forward once more keeping
+// its pre-step states, then walked back; last the entry acceleration
+// A(x0, v0), x0 and v0 the state before step 0.  Writes xbar0, vbar0 and the
+// host array scal.
+pn_status kdk_backward(pn_ctx *c, const double *cp, int64_t K, const double *x0,
+                       const double *v0, const double *m, double dt, int64_t nsteps,
+                       const double *xbar_T, const double *vbar_T, double *xbar0, double *vbar0,
+                       double *scal, const AdjWork &W)
+{
+    const size_t n3 = 3 * (size_t)c->n, b3 = sizeof(double) * n3;
+    const int64_t ncp = nsteps > 0 ? (nsteps + K - 1) / K : 0;
+    double *xs = W.xs, *vs = W.vs, *as = W.as, *xp = W.xp, *vp = W.vp, *atot = W.atot;
+    double *xbA = W.xbA, *vpbA = W.vpbA, *xb = W.xb, *vb = W.vb, *ab = W.ab, *seg = W.seg;
+    double *dscal = W.dscal;
+    pn_status s2 = PN_OK;
+    PN_CUDA(cudaMemcpyAsync(xb, xbar_T, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+    PN_CUDA(cudaMemcpyAsync(vb, vbar_T, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+    PN_CUDA(cudaMemsetAsync(ab, 0, b3, c->stream), "memset");
+    PN_CUDA(cudaMemsetAsync(dscal, 0, sizeof(double) * 2 * c->nclu, c->stream), "memset");
+    for (int64_t sg = ncp - 1; sg >= 0; --sg) {
+        const int64_t s0 = sg * K, s1 = s0 + K < nsteps ? s0 + K : nsteps;
+        const double *q = cp + (size_t)sg * 3 * n3;
+        PN_CUDA(cudaMemcpyAsync(xs, q, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+        PN_CUDA(cudaMemcpyAsync(vs, q + n3, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+        PN_CUDA(cudaMemcpyAsync(as, q + 2 * n3, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+        for (int64_t s = s0; s < s1; ++s) {
+            double *r = seg + (size_t)(s - s0) * 3 * n3;
+            PN_CUDA(cudaMemcpyAsync(r, xs, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+            PN_CUDA(cudaMemcpyAsync(r + n3, vs, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+            PN_CUDA(cudaMemcpyAsync(r + 2 * n3, as, b3, cudaMemcpyDeviceToDevice, c->stream),
+                    "copy");
+            // the segment's last step too when its evaluation's sums are kept
+            if (s + 1 < s1 || W.sums) {
+                if ((s2 = run_steps(c, xs, vs, m, as, dt, 1)) != PN_OK)
+                    return s2;
+            }
+            if (W.sums) {
+                const size_t S = (size_t)c->S;
+                PN_CUDA(cudaMemcpyAsync(W.sums + (size_t)(s - s0) * kAdjSumVals * S, c->part,
+                                        sizeof(double) * kAdjSumVals * S,
+                                        cudaMemcpyDeviceToDevice, c->stream), "copy sums");
+                PN_CUDA(cudaMemcpyAsync(W.srec + (size_t)(s - s0) * pn::kPackVals * S,
+                                        c->mrec + 5 * S, sizeof(float4) * pn::kPackVals * S,
+                                        cudaMemcpyDeviceToDevice, c->stream), "copy records");
+            }
+        }
+        for (int64_t s = s1 - 1; s >= s0; --s) {
+            const double *r = seg + (size_t)(s - s0) * 3 * n3;
+            const size_t S = (size_t)c->S;
+            const double *fs = W.sums ? W.sums + (size_t)(s - s0) * kAdjSumVals * S : nullptr;
+            const float4 *fr = W.sums ? W.srec + (size_t)(s - s0) * pn::kPackVals * S : nullptr;
+            PN_CUDA(pn::launch_adj_kdk(c, 0, dt, r, r + n3, r + 2 * n3, xp, vp, xb, vb, ab,
+                                       atot, nullptr, nullptr), "adjoint step launch");
+            PN_CUDA(pn::launch_accel_vjp(c, xp, vp, m, atot, xbA, vpbA, dscal, true, fs, fr),
+                    "accel vjp launch");
+            PN_CUDA(pn::launch_adj_kdk(c, 1, dt, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                       xb, vb, ab, nullptr, xbA, vpbA), "adjoint step launch");
+        }
+    }
+    // the entry acceleration A(x0, v0)
+    if (x0) {
+        PN_CUDA(pn::launch_accel_vjp(c, x0, v0, m, ab, xbA, vpbA, dscal, true),
+                "accel vjp launch");
+        PN_CUDA(pn::launch_adj_kdk(c, 2, dt, nullptr, nullptr, nullptr, nullptr, nullptr, xb, vb,
+                                   ab, nullptr, xbA, vpbA), "adjoint step launch");
+    }
+    PN_CUDA(cudaMemcpyAsync(xbar0, xb, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+    PN_CUDA(cudaMemcpyAsync(vbar0, vb, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+    PN_CUDA(cudaMemcpyAsync(scal, dscal, sizeof(double) * 2 * c->nclu, cudaMemcpyDeviceToHost,
+                            c->stream), "copy");
+    PN_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
+    return PN_OK;
+}
+
+pn_status vjp_args(pn_ctx *c, const char *name, double dt, int64_t nsteps, int64_t checkpoint)
+{
+    if (!(std::isfinite(dt) && dt > 0.0))
+        return fail(PN_EINVAL, "%s: dt must be finite and > 0 (got %g)", name, dt);
+    if (nsteps < 0 || checkpoint < 0)
+        return fail(PN_EINVAL, "%s: nsteps and checkpoint must be >= 0", name);
+    if (c->p.integrator != PN_KDK)
+        return fail(PN_EUNSUPPORTED, "%s: only the PN_KDK integrator has an adjoint", name);
+    return PN_OK;
+}
+}  // namespace
+
 pn_status pn_step_vjp(pn_ctx *c, const double *x0, const double *v0, const double *m,
                       double dt, int64_t nsteps, int64_t checkpoint, const double *xbar_T,
                       const double *vbar_T, double *xbar0, double *vbar0, double *scal)
@@ -877,106 +1113,102 @@ pn_status pn_step_vjp(pn_ctx *c, const double *x0, const double *v0, const doubl
         return PN_EINVAL;
     if (!x0 || !v0 || !m || !xbar_T || !vbar_T || !xbar0 || !vbar0 || !scal)
         return fail(PN_EINVAL, "pn_step_vjp: NULL array");
-    if (!(std::isfinite(dt) && dt > 0.0))
-        return fail(PN_EINVAL, "pn_step_vjp: dt must be finite and > 0 (got %g)", dt);
-    if (nsteps < 0 || checkpoint < 0)
-        return fail(PN_EINVAL, "pn_step_vjp: nsteps and checkpoint must be >= 0");
-    if (c->p.integrator != PN_KDK)
-        return fail(PN_EUNSUPPORTED, "pn_step_vjp: only the PN_KDK integrator has an adjoint");
-    DeviceGuard g(c->device);
-    PN_CUDA(g.err, "cudaSetDevice");
-    pn_status st = ensure_adjoint_buffers(c);
+    pn_status st = vjp_args(c, "pn_step_vjp", dt, nsteps, checkpoint);
     if (st != PN_OK)
         return st;
-    int64_t K = checkpoint;
-    if (K == 0) {
-        K = 1;
-        while (K * K < nsteps)
-            ++K;
-    }
+    DeviceGuard g(c->device);
+    PN_CUDA(g.err, "cudaSetDevice");
+    if ((st = ensure_adjoint_buffers(c)) != PN_OK)
+        return st;
+    const int64_t K = checkpoint_interval(nsteps, checkpoint);
     const int64_t ncp = nsteps > 0 ? (nsteps + K - 1) / K : 0;
     const size_t n3 = 3 * (size_t)c->n, b3 = sizeof(double) * n3;
-    // work: xs vs as | xp vp atot xbA vpbA | xb vb ab | checkpoints | segment
-    const size_t nwork = 11 * n3 + (size_t)(ncp + (nsteps > 0 ? K : 0)) * 3 * n3;
-    double *w = nullptr, *dscal = nullptr;
-    if (std::getenv("PN_FAIL_ALLOC") || cudaMalloc((void **)&w, sizeof(double) * nwork) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(PN_ENOMEM, "cudaMalloc of %zu bytes for the adjoint failed",
-                    sizeof(double) * nwork);
-    }
-    if (cudaMalloc((void **)&dscal, sizeof(double) * 2 * c->nclu) != cudaSuccess) {
-        cudaGetLastError();
-        cudaFree(w);
-        return fail(PN_ENOMEM, "cudaMalloc for the adjoint failed");
-    }
-    double *xs = w, *vs = xs + n3, *as = vs + n3, *xp = as + n3, *vp = xp + n3, *atot = vp + n3;
-    double *xbA = atot + n3, *vpbA = xbA + n3, *xb = vpbA + n3, *vb = xb + n3, *ab = vb + n3;
-    double *cp = ab + n3, *seg = cp + (size_t)ncp * 3 * n3;
-    auto run = [&]() -> pn_status {
-        PN_CUDA(cudaMemcpyAsync(xs, x0, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
-        PN_CUDA(cudaMemcpyAsync(vs, v0, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
-        pn_status s2 = evaluate(c, xs, vs, m, as, nullptr, 0.0);
-        if (s2 != PN_OK)
-            return s2;
-        for (int64_t s = 0; s < nsteps; ++s) {
-            if (s % K == 0) {
-                double *q = cp + (size_t)(s / K) * 3 * n3;
-                PN_CUDA(cudaMemcpyAsync(q, xs, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
-                PN_CUDA(cudaMemcpyAsync(q + n3, vs, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
-                PN_CUDA(cudaMemcpyAsync(q + 2 * n3, as, b3, cudaMemcpyDeviceToDevice, c->stream),
-                        "copy");
-            }
-            if ((s2 = run_steps(c, xs, vs, m, as, dt, 1)) != PN_OK)
-                return s2;
-        }
-        PN_CUDA(cudaMemcpyAsync(xb, xbar_T, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
-        PN_CUDA(cudaMemcpyAsync(vb, vbar_T, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
-        PN_CUDA(cudaMemsetAsync(ab, 0, b3, c->stream), "memset");
-        PN_CUDA(cudaMemsetAsync(dscal, 0, sizeof(double) * 2 * c->nclu, c->stream), "memset");
-        for (int64_t sg = ncp - 1; sg >= 0; --sg) {
-            const int64_t s0 = sg * K, s1 = s0 + K < nsteps ? s0 + K : nsteps;
-            const double *q = cp + (size_t)sg * 3 * n3;
-            PN_CUDA(cudaMemcpyAsync(xs, q, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
-            PN_CUDA(cudaMemcpyAsync(vs, q + n3, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
-            PN_CUDA(cudaMemcpyAsync(as, q + 2 * n3, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
-            for (int64_t s = s0; s < s1; ++s) {
-                double *r = seg + (size_t)(s - s0) * 3 * n3;
-                PN_CUDA(cudaMemcpyAsync(r, xs, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
-                PN_CUDA(cudaMemcpyAsync(r + n3, vs, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
-                PN_CUDA(cudaMemcpyAsync(r + 2 * n3, as, b3, cudaMemcpyDeviceToDevice, c->stream),
-                        "copy");
-                if (s + 1 < s1 && (s2 = run_steps(c, xs, vs, m, as, dt, 1)) != PN_OK)
-                    return s2;
-            }
-            for (int64_t s = s1 - 1; s >= s0; --s) {
-                const double *r = seg + (size_t)(s - s0) * 3 * n3;
-                PN_CUDA(pn::launch_adj_kdk(c, 0, dt, r, r + n3, r + 2 * n3, xp, vp, xb, vb, ab,
-                                           atot, nullptr, nullptr), "adjoint step launch");
-                PN_CUDA(pn::launch_accel_vjp(c, xp, vp, m, atot, xbA, vpbA, dscal, true),
-                        "accel vjp launch");
-                PN_CUDA(pn::launch_adj_kdk(c, 1, dt, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                           xb, vb, ab, nullptr, xbA, vpbA), "adjoint step launch");
-            }
-        }
-        // the entry acceleration A(x0, v0)
-        PN_CUDA(pn::launch_accel_vjp(c, x0, v0, m, ab, xbA, vpbA, dscal, true), "accel vjp launch");
-        PN_CUDA(pn::launch_adj_kdk(c, 2, dt, nullptr, nullptr, nullptr, nullptr, nullptr, xb, vb,
-                                   ab, nullptr, xbA, vpbA), "adjoint step launch");
-        PN_CUDA(cudaMemcpyAsync(xbar0, xb, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
-        PN_CUDA(cudaMemcpyAsync(vbar0, vb, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
-        PN_CUDA(cudaMemcpyAsync(scal, dscal, sizeof(double) * 2 * c->nclu,
-                                cudaMemcpyDeviceToHost, c->stream), "copy");
-        PN_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
-        return PN_OK;
-    };
+    AdjWork W;
+    double *cp = nullptr;
+    if ((st = adj_alloc(c, K, ncp, true, &W, &cp)) != PN_OK)
+        return st;
     // the forward recomputations are not the caller's trajectory: no watchdog checks
     const int64_t wd_every = c->wd_every;
     c->wd_every = 0;
+    auto run = [&]() -> pn_status {
+        PN_CUDA(cudaMemcpyAsync(W.xs, x0, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+        PN_CUDA(cudaMemcpyAsync(W.vs, v0, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+        pn_status s2 = evaluate(c, W.xs, W.vs, m, W.as, nullptr, 0.0);
+        if (s2 == PN_OK)
+            s2 = kdk_forward_checkpoints(c, W.xs, W.vs, m, W.as, dt, nsteps, K, cp);
+        if (s2 == PN_OK) {
+            FarForm far;
+            if (W.sums)
+                s2 = far.enter(c);
+            if (s2 == PN_OK)
+                s2 = kdk_backward(c, cp, K, x0, v0, m, dt, nsteps, xbar_T, vbar_T, xbar0, vbar0,
+                                  scal, W);
+            const pn_status s3 = far.leave();
+            if (s2 == PN_OK)
+                s2 = s3;
+        }
+        return s2;
+    };
     st = run();
     c->wd_every = wd_every;
-    cudaStreamSynchronize(c->stream);
-    cudaFree(w);
-    cudaFree(dscal);
+    adj_free(c, &W);
+    return st == PN_OK ? ok() : st;
+}
+
+pn_status pn_step_save(pn_ctx *c, double *x, double *v, const double *m, double *a, double dt,
+                       int64_t nsteps, int64_t checkpoint, double *ckpt)
+{
+    if (check_ctx(c) != PN_OK)
+        return PN_EINVAL;
+    if (!x || !v || !m || !a || (nsteps > 0 && !ckpt))
+        return fail(PN_EINVAL, "pn_step_save: NULL array");
+    pn_status st = vjp_args(c, "pn_step_save", dt, nsteps, checkpoint);
+    if (st != PN_OK)
+        return st;
+    DeviceGuard g(c->device);
+    PN_CUDA(g.err, "cudaSetDevice");
+    const int64_t K = checkpoint_interval(nsteps, checkpoint);
+    st = kdk_forward_checkpoints(c, x, v, m, a, dt, nsteps, K, ckpt);
+    return st == PN_OK ? ok() : st;
+}
+
+pn_status pn_step_vjp_saved(pn_ctx *c, const double *ckpt, const double *m, double dt,
+                            int64_t nsteps, int64_t checkpoint, const double *xbar_T,
+                            const double *vbar_T, double *xbar0, double *vbar0, double *scal)
+{
+    if (check_ctx(c) != PN_OK)
+        return PN_EINVAL;
+    if ((nsteps > 0 && !ckpt) || !m || !xbar_T || !vbar_T || !xbar0 || !vbar0 || !scal)
+        return fail(PN_EINVAL, "pn_step_vjp_saved: NULL array");
+    pn_status st = vjp_args(c, "pn_step_vjp_saved", dt, nsteps, checkpoint);
+    if (st != PN_OK)
+        return st;
+    DeviceGuard g(c->device);
+    PN_CUDA(g.err, "cudaSetDevice");
+    if ((st = ensure_adjoint_buffers(c)) != PN_OK)
+        return st;
+    const int64_t K = checkpoint_interval(nsteps, checkpoint);
+    const size_t n3 = 3 * (size_t)c->n;
+    AdjWork W;
+    if ((st = adj_alloc(c, K, 0, false, &W, nullptr)) != PN_OK)
+        return st;
+    const int64_t wd_every = c->wd_every;
+    c->wd_every = 0;
+    // x0, v0: the state of checkpoint 0 (none without steps: the entry
+    // acceleration then has a zero cotangent and is skipped)
+    const double *x0 = nsteps > 0 ? ckpt : nullptr;
+    const double *v0 = nsteps > 0 ? ckpt + n3 : nullptr;
+    FarForm far;
+    if (W.sums)
+        st = far.enter(c);
+    if (st == PN_OK)
+        st = kdk_backward(c, ckpt, K, x0, v0, m, dt, nsteps, xbar_T, vbar_T, xbar0, vbar0, scal,
+                          W);
+    const pn_status s3 = far.leave();
+    if (st == PN_OK)
+        st = s3;
+    c->wd_every = wd_every;
+    adj_free(c, &W);
     return st == PN_OK ? ok() : st;
 }
 

@@ -1645,7 +1645,7 @@ size_t adjoint_buffer_doubles(const pn_ctx *c)
 
 cudaError_t launch_accel_vjp(pn_ctx *c, const double *x, const double *v, const double *m,
                              const double *abar, double *xbar, double *vbar, double *scal,
-                             bool accumulate)
+                             bool accumulate, const double *fwd_saved, const float4 *srec_saved)
 {
     const int64_t S = c->S, nglue = S / kGlueThreads;
     const int js = (int)jerk_part_splits(c);
@@ -1679,9 +1679,15 @@ cudaError_t launch_accel_vjp(pn_ctx *c, const double *x, const double *v, const 
         c->launches += 1;
         if ((e = cudaGetLastError()) != cudaSuccess)
             return e;
-        if ((e = launch_fused_on(c, frec)) != cudaSuccess)
-            return e;
-        fwd = c->part;
+        // the forward pair sums: given by the caller (an evaluation at this
+        // state without the near-source split, fused layout), or computed here
+        if (fwd_saved) {
+            fwd = fwd_saved;
+        } else {
+            if ((e = launch_fused_on(c, frec)) != cudaSuccess)
+                return e;
+            fwd = c->part;
+        }
         jsf = 1;
     } else {
         k_dual_pairs<double><<<grid, kJThreads, 0, c->stream>>>(rec, S, c->d_clu, bc, part);
@@ -1696,8 +1702,8 @@ cudaError_t launch_accel_vjp(pn_ctx *c, const double *x, const double *v, const 
     int jsr = js;
     if (mixed) {
         // packed sweeps: sources from the staged records of the forward pass
-        const float4 *srec = c->mrec + 5 * S;
-        if (!c->fused_packed)          // the scalar forward kernel stages nothing
+        const float4 *srec = srec_saved ? srec_saved : c->mrec + 5 * S;
+        if (!srec_saved && !c->fused_packed)   // the scalar forward kernel stages nothing
             if ((e = launch_stage_sources(c, frec)) != cudaSuccess)
                 return e;
         jsr = (int)adj_pack_splits(c);

@@ -192,9 +192,14 @@ cudaError_t launch_rk4_stage(pn_ctx *c, int stage, double *x, double *v, const d
                              double dt);
 size_t jerk_buffer_doubles(const pn_ctx *c);
 size_t adjoint_buffer_doubles(const pn_ctx *c);
+// fwd_saved / srec_saved (mixed contexts with the fused kernel): the 16
+// forward pair sums ([value][slot], fused layout) and the staged D-form
+// source records of an evaluation at (x, v) without the near-source split;
+// nullptr: computed here.
 cudaError_t launch_accel_vjp(pn_ctx *c, const double *x, const double *v, const double *m,
                              const double *abar, double *xbar, double *vbar, double *scal,
-                             bool accumulate);
+                             bool accumulate, const double *fwd_saved = nullptr,
+                             const float4 *srec_saved = nullptr);
 cudaError_t launch_adj_kdk(pn_ctx *c, int stage, double dt, const double *x, const double *v,
                            const double *a, double *xp, double *vp, double *xb, double *vb,
                            double *ab, double *atot, const double *xbA, const double *vpbA);

@@ -95,6 +95,8 @@ def _load():
                 "pn_jerk": [P, P, P, P, P, P],
                 "pn_accel_vjp": [P, P, P, P, P, P, P, P],
                 "pn_step_vjp": [P, P, P, P, D, I64, I64, P, P, P, P, P],
+                "pn_step_save": [P, P, P, P, P, D, I64, I64, P],
+                "pn_step_vjp_saved": [P, P, P, D, I64, I64, P, P, P, P, P],
                 "pn_step": [P, P, P, P, P, D, I64],
                 "pn_step_host": [P, P, P, P, P, D, I64],
                 "pn_energy": [P, P, P, P, P],
@@ -308,11 +310,55 @@ def pn_step_vjp(ctx: Context, x0, v0, m, dt: float, nsteps: int, xbar_T, vbar_T,
     return scal.reshape(-1, 2)
 
 
+def checkpoint_interval(nsteps: int, checkpoint: int = 0) -> int:
+    """Steps between the checkpoints of pn_step_save / pn_step_vjp: checkpoint,
+    or for 0 the integer ceiling of sqrt(nsteps)."""
+    if checkpoint:
+        return int(checkpoint)
+    k = 1
+    while k * k < nsteps:
+        k += 1
+    return k
+
+
+def pn_step_save(ctx: Context, x, v, m, a, dt: float, nsteps: int, checkpoint: int = 0):
+    """pn_step that also keeps the adjoint's checkpoints: returns a device
+    tensor of ceil(nsteps / K) x 3 x n x 3 doubles (x, v, a before steps 0,
+    K, 2K, ...) for pn_step_vjp_saved."""
+    import torch
+    n = ctx.n
+    k = checkpoint_interval(nsteps, checkpoint)
+    ncp = (nsteps + k - 1) // k if nsteps > 0 else 0
+    ckpt = torch.empty((max(ncp, 1), 3, n, 3), dtype=torch.float64, device=f"cuda:{ctx.device}")
+    _check(_load().pn_step_save(ctx.handle, _dev(ctx, x, (n, 3), "x"), _dev(ctx, v, (n, 3), "v"),
+                                _dev(ctx, m, (n,), "m"), _dev(ctx, a, (n, 3), "a"), float(dt),
+                                int(nsteps), int(checkpoint), ckpt.data_ptr()))
+    return ckpt
+
+
+def pn_step_vjp_saved(ctx: Context, ckpt, m, dt: float, nsteps: int, xbar_T, vbar_T, xbar0,
+                      vbar0, checkpoint: int = 0) -> np.ndarray:
+    """pn_step_vjp from the checkpoints pn_step_save returned (same m, dt,
+    nsteps, checkpoint): writes xbar0, vbar0; returns [M_bar, inv_c2_bar]
+    per cluster."""
+    n = ctx.n
+    scal = np.zeros(2 * ctx.n_clusters)
+    _check(_load().pn_step_vjp_saved(ctx.handle, ckpt.data_ptr(), _dev(ctx, m, (n,), "m"),
+                                     float(dt), int(nsteps), int(checkpoint),
+                                     _dev(ctx, xbar_T, (n, 3), "xbar_T"),
+                                     _dev(ctx, vbar_T, (n, 3), "vbar_T"),
+                                     _dev(ctx, xbar0, (n, 3), "xbar0"),
+                                     _dev(ctx, vbar0, (n, 3), "vbar0"),
+                                     scal.ctypes.data_as(ctypes.c_void_p)))
+    return scal.reshape(-1, 2)
+
+
 def trajectory(ctx: Context, x0, v0, m, M, c, dt: float, nsteps: int, checkpoint: int = 0):
     """Differentiable nsteps of KDK (single-cluster context): returns (x_T,
     v_T) as torch tensors whose backward gives gradients with respect to x0,
     v0, the hole mass M and c (0-d tensors); m[0] is replaced by M and the
-    context's c by c.  The forward runs pn_step, the backward pn_step_vjp."""
+    context's c by c.  The forward runs pn_step_save (pn_step keeping the
+    adjoint's checkpoints), the backward pn_step_vjp_saved."""
     import torch
     return _Trajectory.apply(x0, v0, M, c, m, ctx, float(dt), int(nsteps), int(checkpoint))
 
@@ -330,9 +376,14 @@ def _trajectory_class():
             x, v = x0.detach().clone(), v0.detach().clone()
             a = torch.empty_like(x)
             pn_accel(ctx, x, v, mm, a)
-            pn_step(ctx, x, v, mm, a, dt, nsteps)
+            if ctx.params.integrator == PN_KDK:
+                ckpt = pn_step_save(ctx, x, v, mm, a, dt, nsteps, checkpoint)
+            else:                   # no adjoint: the backward reports it
+                pn_step(ctx, x, v, mm, a, dt, nsteps)
+                ckpt = None
             pn_sync(ctx)
             fctx.save_for_backward(x0.detach(), v0.detach(), mm)
+            fctx.ckpt = ckpt
             fctx.args = (ctx, dt, nsteps, checkpoint, cc)
             return x, v
 
@@ -344,7 +395,11 @@ def _trajectory_class():
             gv = torch.zeros_like(v0) if gv is None else gv.contiguous()
             xb, vb = torch.empty_like(x0), torch.empty_like(v0)
             pn_set_params(ctx, c=cc)
-            scal = pn_step_vjp(ctx, x0, v0, mm, dt, nsteps, gx, gv, xb, vb, checkpoint)
+            if fctx.ckpt is not None:
+                scal = pn_step_vjp_saved(ctx, fctx.ckpt, mm, dt, nsteps, gx, gv, xb, vb,
+                                         checkpoint)
+            else:
+                scal = pn_step_vjp(ctx, x0, v0, mm, dt, nsteps, gx, gv, xb, vb, checkpoint)
             Mb = torch.tensor(scal[0, 0], dtype=x0.dtype, device=x0.device)
             cb = torch.tensor(-2.0 * scal[0, 1] / cc ** 3, dtype=x0.dtype, device=x0.device)
             return xb, vb, Mb, cb, None, None, None, None, None

@@ -86,12 +86,19 @@ def test_null_arguments(lib):
     for name, nargs in (("pn_accel", 5), ("pn_step", 7), ("pn_energy", 5), ("pn_sync", 1),
                         ("pn_step_host", 7), ("pn_set_timing", 2), ("pn_get_launch", 2),
                         ("pn_get_pair_stats", 2),
-                        ("pn_launch_count", 2), ("pn_jerk", 6), ("pn_accel_vjp", 8)):
+                        ("pn_launch_count", 2), ("pn_jerk", 6), ("pn_accel_vjp", 8),
+                        ("pn_step_save", 9), ("pn_step_vjp_saved", 11)):
         fn = getattr(lib, name)
         args = [None] * nargs
-        if name in ("pn_step", "pn_step_host"):
+        if name in ("pn_step", "pn_step_host", "pn_step_save"):
             args[5] = 0.01
             args[6] = 1
+        if name == "pn_step_save":
+            args[7] = 0
+        if name == "pn_step_vjp_saved":
+            args[3] = 0.01
+            args[4] = 1
+            args[5] = 0
         if name == "pn_set_timing":
             args[1] = 1
         assert fn(*args) == 1, name

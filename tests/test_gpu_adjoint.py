@@ -287,7 +287,7 @@ def test_adjoint_workload_gradients_match_central_differences():
     near = np.argsort(np.linalg.norm(x[1:] - x[0], axis=1))[:16] + 1
     stream = torch.cuda.current_stream(DEV)
     nst = 200
-    gm = bench.adjoint_gradient(0, stream, w, state, near, nst, "mixed")[:4]
+    gm = bench.adjoint_gradient(0, stream, w, state, near, nst, "mixed", from_x0=True)[:4]
     g6 = bench.adjoint_gradient(0, stream, w, state, near, nst, "fp64")[:4]
     assert np.linalg.norm(gm[0] - g6[0]) <= 1e-6 * np.linalg.norm(g6[0])
     assert np.linalg.norm(gm[1] - g6[1]) <= 1e-6 * np.linalg.norm(g6[1])
@@ -354,3 +354,60 @@ def test_step_vjp_batched_per_cluster(orc):
         assert np.abs(vb[a:b] - want[1]).max() <= 1e-9 * np.abs(want[1]).max()
         assert abs(scal[k, 0] - want[2]) <= 1e-9 * abs(want[2])
         assert abs(scal[k, 1] - want[3]) <= 1e-9 * abs(want[3])
+
+
+@pytest.mark.parametrize("vel_mode,checkpoint", [("vpred_end", 0), ("vhalf", 3)])
+def test_saved_checkpoints_give_the_same_trajectory_and_gradient(vel_mode, checkpoint):
+    """pn_step_save runs the same trajectory as pn_step, and the backward from
+    its checkpoints (pn_step_vjp_saved) equals pn_step_vjp's from the same
+    start state, bit for bit, in a batched mixed context."""
+    sizes = [700, 300]
+    parts = [make_cluster(n, 0.1 + 0.05 * k, 40 + k) for k, n in enumerate(sizes)]
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    x = np.concatenate([p[0] for p in parts])
+    v = np.concatenate([p[1] for p in parts])
+    m = np.concatenate([p[2] for p in parts])
+    n, nst, dt = int(off[-1]), 11, 1.0 / 1024
+    ctx = pn.pn_init_batched(off, c=[20.0, 35.0], eps=1e-3, precision="mixed",
+                             vel_mode=vel_mode, device=0)
+    X, V, M = dev(x), dev(v), dev(m)
+    A = torch.empty_like(X)
+    pn.pn_accel(ctx, X, V, M, A)
+    X2, V2, A2 = X.clone(), V.clone(), A.clone()
+    ckpt = pn.pn_step_save(ctx, X, V, M, A, dt, nst, checkpoint)
+    pn.pn_step(ctx, X2, V2, M, A2, dt, nst)
+    pn.pn_sync(ctx)
+    assert torch.equal(X, X2) and torch.equal(V, V2) and torch.equal(A, A2)
+    rng = np.random.default_rng(3)
+    xbT, vbT = dev(rng.normal(size=(n, 3))), dev(rng.normal(size=(n, 3)))
+    XB, VB, XB2, VB2 = (torch.empty((n, 3), dtype=torch.float64, device=DEV) for _ in range(4))
+    s1 = pn.pn_step_vjp_saved(ctx, ckpt, M, dt, nst, xbT, vbT, XB, VB, checkpoint)
+    s2 = pn.pn_step_vjp(ctx, dev(x), dev(v), M, dt, nst, xbT, vbT, XB2, VB2, checkpoint)
+    assert torch.equal(XB, XB2) and torch.equal(VB, VB2) and np.array_equal(s1, s2)
+    ctx.close()
+
+
+def test_saved_checkpoints_edge_cases():
+    x, v, m = state(40, 901)
+    X, V, M = dev(x), dev(v), dev(m)
+    XB, VB = torch.empty_like(X), torch.empty_like(X)
+    ctx = pn.pn_init(40, c=10.0, eps=1e-2, precision="fp64", device=0)
+    A = torch.empty_like(X)
+    pn.pn_accel(ctx, X, V, M, A)
+    # no steps: the cotangents pass through, nothing else contributes
+    ckpt = pn.pn_step_save(ctx, X, V, M, A, 1e-3, 0)
+    xbT, vbT = dev(np.ones((40, 3))), dev(2 * np.ones((40, 3)))
+    scal = pn.pn_step_vjp_saved(ctx, ckpt, M, 1e-3, 0, xbT, vbT, XB, VB)
+    assert torch.equal(XB, xbT) and torch.equal(VB, vbT) and np.all(scal == 0.0)
+    lib = pn._load()
+    assert lib.pn_step_save(ctx.handle, X.data_ptr(), V.data_ptr(), M.data_ptr(), A.data_ptr(),
+                            1e-3, 4, 0, None) == pn.PN_EINVAL
+    assert lib.pn_step_vjp_saved(ctx.handle, None, M.data_ptr(), 1e-3, 4, 0, xbT.data_ptr(),
+                                 vbT.data_ptr(), XB.data_ptr(), VB.data_ptr(),
+                                 np.zeros(2).ctypes.data) == pn.PN_EINVAL
+    ctx.close()
+    ctx = pn.pn_init(40, c=10.0, eps=1e-2, precision="fp64", integrator="rk4", device=0)
+    with pytest.raises(pn.PNError) as e:
+        pn.pn_step_save(ctx, X, V, M, A, 1e-3, 3)
+    assert e.value.status == pn.PN_EUNSUPPORTED
+    ctx.close()
