@@ -135,6 +135,8 @@ void free_all(pn_ctx *c)
         cudaStreamDestroy(c->cap_stream);
     if (c->side)
         cudaStreamDestroy(c->side);
+    if (c->adj_stream)
+        cudaStreamDestroy(c->adj_stream);
     if (c->ev_fork)
         cudaEventDestroy(c->ev_fork);
     if (c->ev_join)
@@ -873,13 +875,16 @@ namespace {
 // Workspace of the KDK adjoint: one step's states and cotangents and one
 // segment of K pre-step states.
 struct AdjWork {
-    double *xs, *vs, *as, *xp, *vp, *atot, *xbA, *vpbA, *xb, *vb, *ab, *seg, *dscal;
+    double *xs, *vs, *as, *xp, *vp, *atot, *xbA, *vpbA, *xb, *vb, *ab, *dscal;
     double *w;
+    // one segment's pre-step states (K x 9n doubles); with sums two sets, so
+    // that one segment is recomputed while the previous one is reversed
+    double *seg[2];
     // mixed contexts with the fused kernel: each recomputed step's 16
     // forward pair sums (16 S doubles) and staged source records (9 S
     // float4), for the reverse of that step (nullptr otherwise)
-    double *sums;
-    float4 *srec;
+    double *sums[2];
+    float4 *srec[2];
 };
 
 // The recomputed segments keep their pair sums for the reverse (see
@@ -907,13 +912,17 @@ pn_status adj_alloc(pn_ctx *c, int64_t K, int64_t ncp, bool own_checkpoints, Adj
 {
     const size_t n3 = 3 * (size_t)c->n;
     const size_t per_step = adj_saves_sums(c) ? (size_t)(kAdjSumVals + kAdjSrecDoubles) * c->S : 0;
+    const int nbuf = per_step ? 2 : 1;
     // (+ 16 doubles: the saved regions start 128-byte aligned)
-    const size_t nwork = 11 * n3 + (size_t)((own_checkpoints ? ncp : 0) + K) * 3 * n3 +
-                         (size_t)K * per_step + (per_step ? 16 : 0);
+    const size_t nwork = 11 * n3 + (size_t)(own_checkpoints ? ncp : 0) * 3 * n3 +
+                         (size_t)nbuf * K * (3 * n3 + per_step) + (per_step ? 16 : 0);
     W->w = nullptr;
     W->dscal = nullptr;
-    W->sums = nullptr;
-    W->srec = nullptr;
+    for (int b = 0; b < 2; ++b) {
+        W->seg[b] = nullptr;
+        W->sums[b] = nullptr;
+        W->srec[b] = nullptr;
+    }
     if (std::getenv("PN_FAIL_ALLOC") ||
         cudaMalloc((void **)&W->w, sizeof(double) * nwork) != cudaSuccess) {
         cudaGetLastError();
@@ -944,13 +953,20 @@ pn_status adj_alloc(pn_ctx *c, int64_t K, int64_t ncp, bool own_checkpoints, Adj
         *cp = after;
         after += (size_t)ncp * 3 * n3;
     }
-    W->seg = after;
-    after += (size_t)K * 3 * n3;
+    for (int b = 0; b < nbuf; ++b) {
+        W->seg[b] = after;
+        after += (size_t)K * 3 * n3;
+    }
     if (per_step) {
-        // S is a multiple of 512, so the records follow the sums aligned too
+        // S is a multiple of 512, so every region after the first stays aligned
         const uintptr_t a = (reinterpret_cast<uintptr_t>(after) + 127) & ~(uintptr_t)127;
-        W->sums = reinterpret_cast<double *>(a);
-        W->srec = reinterpret_cast<float4 *>(W->sums + (size_t)K * kAdjSumVals * c->S);
+        double *p = reinterpret_cast<double *>(a);
+        for (int b = 0; b < 2; ++b) {
+            W->sums[b] = p;
+            p += (size_t)K * kAdjSumVals * c->S;
+            W->srec[b] = reinterpret_cast<float4 *>(p);
+            p += (size_t)K * kAdjSrecDoubles * c->S;
+        }
     }
     return PN_OK;
 }
@@ -1018,6 +1034,63 @@ pn_status kdk_forward_checkpoints(pn_ctx *c, double *x, double *v, const double 
     return PN_OK;
 }
 
+// Segment sg (steps [sg K, min((sg + 1) K, nsteps))) forward once more from
+// its checkpoint, on c->stream: the pre-step states into W.seg[b] and, where
+// kept, each step's pair sums and staged records into W.sums[b] / W.srec[b]
+// (the segment's last step is taken too for its sums).
+pn_status rerun_segment(pn_ctx *c, const double *cp, int64_t sg, int64_t K, int64_t nsteps,
+                        const double *m, double dt, const AdjWork &W, int b)
+{
+    const size_t n3 = 3 * (size_t)c->n, b3 = sizeof(double) * n3, S = (size_t)c->S;
+    const int64_t s0 = sg * K, s1 = s0 + K < nsteps ? s0 + K : nsteps;
+    const double *q = cp + (size_t)sg * 3 * n3;
+    double *xs = W.xs, *vs = W.vs, *as = W.as;
+    PN_CUDA(cudaMemcpyAsync(xs, q, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+    PN_CUDA(cudaMemcpyAsync(vs, q + n3, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+    PN_CUDA(cudaMemcpyAsync(as, q + 2 * n3, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+    for (int64_t s = s0; s < s1; ++s) {
+        double *r = W.seg[b] + (size_t)(s - s0) * 3 * n3;
+        PN_CUDA(cudaMemcpyAsync(r, xs, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+        PN_CUDA(cudaMemcpyAsync(r + n3, vs, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+        PN_CUDA(cudaMemcpyAsync(r + 2 * n3, as, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
+        if (s + 1 < s1 || W.sums[b]) {
+            const pn_status st = run_steps(c, xs, vs, m, as, dt, 1);
+            if (st != PN_OK)
+                return st;
+        }
+        if (W.sums[b]) {
+            PN_CUDA(cudaMemcpyAsync(W.sums[b] + (size_t)(s - s0) * kAdjSumVals * S, c->part,
+                                    sizeof(double) * kAdjSumVals * S, cudaMemcpyDeviceToDevice,
+                                    c->stream), "copy sums");
+            PN_CUDA(cudaMemcpyAsync(W.srec[b] + (size_t)(s - s0) * pn::kPackVals * S,
+                                    c->mrec + 5 * S, sizeof(float4) * pn::kPackVals * S,
+                                    cudaMemcpyDeviceToDevice, c->stream), "copy records");
+        }
+    }
+    return PN_OK;
+}
+
+// The reverse of segment sg's steps, last to first, on c->stream, from the
+// states (and kept sums) in buffers b.
+pn_status reverse_segment(pn_ctx *c, int64_t sg, int64_t K, int64_t nsteps, const double *m,
+                          double dt, const AdjWork &W, int b)
+{
+    const size_t n3 = 3 * (size_t)c->n, S = (size_t)c->S;
+    const int64_t s0 = sg * K, s1 = s0 + K < nsteps ? s0 + K : nsteps;
+    for (int64_t s = s1 - 1; s >= s0; --s) {
+        const double *r = W.seg[b] + (size_t)(s - s0) * 3 * n3;
+        const double *fs = W.sums[b] ? W.sums[b] + (size_t)(s - s0) * kAdjSumVals * S : nullptr;
+        const float4 *fr = W.sums[b] ? W.srec[b] + (size_t)(s - s0) * pn::kPackVals * S : nullptr;
+        PN_CUDA(pn::launch_adj_kdk(c, 0, dt, r, r + n3, r + 2 * n3, W.xp, W.vp, W.xb, W.vb, W.ab,
+                                   W.atot, nullptr, nullptr), "adjoint step launch");
+        PN_CUDA(pn::launch_accel_vjp(c, W.xp, W.vp, m, W.atot, W.xbA, W.vpbA, W.dscal, true, fs,
+                                     fr), "accel vjp launch");
+        PN_CUDA(pn::launch_adj_kdk(c, 1, dt, nullptr, nullptr, nullptr, nullptr, nullptr, W.xb,
+                                   W.vb, W.ab, nullptr, W.xbA, W.vpbA), "adjoint step launch");
+    }
+    return PN_OK;
+}
+
 // The reverse of nsteps KDK steps from their checkpoints cp (the states
 // before steps 0, K, 2K, ...): each segment is run forward once more keeping
 // its pre-step states, then walked back; last the entry acceleration
@@ -1030,53 +1103,68 @@ pn_status kdk_backward(pn_ctx *c, const double *cp, int64_t K, const double *x0,
 {
     const size_t n3 = 3 * (size_t)c->n, b3 = sizeof(double) * n3;
     const int64_t ncp = nsteps > 0 ? (nsteps + K - 1) / K : 0;
-    double *xs = W.xs, *vs = W.vs, *as = W.as, *xp = W.xp, *vp = W.vp, *atot = W.atot;
-    double *xbA = W.xbA, *vpbA = W.vpbA, *xb = W.xb, *vb = W.vb, *ab = W.ab, *seg = W.seg;
+    double *xbA = W.xbA, *vpbA = W.vpbA, *xb = W.xb, *vb = W.vb, *ab = W.ab;
     double *dscal = W.dscal;
     pn_status s2 = PN_OK;
     PN_CUDA(cudaMemcpyAsync(xb, xbar_T, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
     PN_CUDA(cudaMemcpyAsync(vb, vbar_T, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
     PN_CUDA(cudaMemsetAsync(ab, 0, b3, c->stream), "memset");
     PN_CUDA(cudaMemsetAsync(dscal, 0, sizeof(double) * 2 * c->nclu, c->stream), "memset");
-    for (int64_t sg = ncp - 1; sg >= 0; --sg) {
-        const int64_t s0 = sg * K, s1 = s0 + K < nsteps ? s0 + K : nsteps;
-        const double *q = cp + (size_t)sg * 3 * n3;
-        PN_CUDA(cudaMemcpyAsync(xs, q, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
-        PN_CUDA(cudaMemcpyAsync(vs, q + n3, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
-        PN_CUDA(cudaMemcpyAsync(as, q + 2 * n3, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
-        for (int64_t s = s0; s < s1; ++s) {
-            double *r = seg + (size_t)(s - s0) * 3 * n3;
-            PN_CUDA(cudaMemcpyAsync(r, xs, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
-            PN_CUDA(cudaMemcpyAsync(r + n3, vs, b3, cudaMemcpyDeviceToDevice, c->stream), "copy");
-            PN_CUDA(cudaMemcpyAsync(r + 2 * n3, as, b3, cudaMemcpyDeviceToDevice, c->stream),
-                    "copy");
-            // the segment's last step too when its evaluation's sums are kept
-            if (s + 1 < s1 || W.sums) {
-                if ((s2 = run_steps(c, xs, vs, m, as, dt, 1)) != PN_OK)
-                    return s2;
-            }
-            if (W.sums) {
-                const size_t S = (size_t)c->S;
-                PN_CUDA(cudaMemcpyAsync(W.sums + (size_t)(s - s0) * kAdjSumVals * S, c->part,
-                                        sizeof(double) * kAdjSumVals * S,
-                                        cudaMemcpyDeviceToDevice, c->stream), "copy sums");
-                PN_CUDA(cudaMemcpyAsync(W.srec + (size_t)(s - s0) * pn::kPackVals * S,
-                                        c->mrec + 5 * S, sizeof(float4) * pn::kPackVals * S,
-                                        cudaMemcpyDeviceToDevice, c->stream), "copy records");
-            }
+    if (!W.sums[0]) {
+        for (int64_t sg = ncp - 1; sg >= 0; --sg) {
+            if ((s2 = rerun_segment(c, cp, sg, K, nsteps, m, dt, W, 0)) != PN_OK)
+                return s2;
+            if ((s2 = reverse_segment(c, sg, K, nsteps, m, dt, W, 0)) != PN_OK)
+                return s2;
         }
-        for (int64_t s = s1 - 1; s >= s0; --s) {
-            const double *r = seg + (size_t)(s - s0) * 3 * n3;
-            const size_t S = (size_t)c->S;
-            const double *fs = W.sums ? W.sums + (size_t)(s - s0) * kAdjSumVals * S : nullptr;
-            const float4 *fr = W.sums ? W.srec + (size_t)(s - s0) * pn::kPackVals * S : nullptr;
-            PN_CUDA(pn::launch_adj_kdk(c, 0, dt, r, r + n3, r + 2 * n3, xp, vp, xb, vb, ab,
-                                       atot, nullptr, nullptr), "adjoint step launch");
-            PN_CUDA(pn::launch_accel_vjp(c, xp, vp, m, atot, xbA, vpbA, dscal, true, fs, fr),
-                    "accel vjp launch");
-            PN_CUDA(pn::launch_adj_kdk(c, 1, dt, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                       xb, vb, ab, nullptr, xbA, vpbA), "adjoint step launch");
-        }
+    } else if (ncp > 0) {
+        // segment sg - 1 is recomputed on the adjoint stream while segment sg
+        // is reversed on the context's stream (buffers sg % 2 alternate;
+        // events order each handoff); the reverse keeps only its own scratch
+        // and the kept sums, so the two share no buffer
+        if (!c->adj_stream)
+            PN_CUDA(cudaStreamCreateWithFlags(&c->adj_stream, cudaStreamNonBlocking),
+                    "adjoint stream");
+        cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+        for (auto &e : ev)
+            PN_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+        cudaEvent_t start = ev[0], rerun_done[2] = {ev[1], ev[2]}, rev_done[2] = {ev[3], ev[4]};
+        cudaStream_t A = c->stream, B = c->adj_stream;
+        auto on_b = [&](int64_t sg) -> pn_status {
+            c->stream = B;
+            const pn_status r = rerun_segment(c, cp, sg, K, nsteps, m, dt, W, (int)(sg % 2));
+            c->stream = A;
+            if (r != PN_OK)
+                return r;
+            PN_CUDA(cudaEventRecord(rerun_done[sg % 2], B), "event");
+            return PN_OK;
+        };
+        auto run = [&]() -> pn_status {
+            PN_CUDA(cudaEventRecord(start, A), "event");       // checkpoints, cotangents
+            PN_CUDA(cudaStreamWaitEvent(B, start, 0), "event wait");
+            pn_status r = on_b(ncp - 1);
+            for (int64_t sg = ncp - 1; sg >= 0 && r == PN_OK; --sg) {
+                PN_CUDA(cudaStreamWaitEvent(A, rerun_done[sg % 2], 0), "event wait");
+                if (sg >= 1) {
+                    if (sg + 1 <= ncp - 1)       // buffers (sg - 1) % 2 were segment sg + 1's
+                        PN_CUDA(cudaStreamWaitEvent(B, rev_done[(sg - 1) % 2], 0), "event wait");
+                    if ((r = on_b(sg - 1)) != PN_OK)
+                        break;
+                }
+                if ((r = reverse_segment(c, sg, K, nsteps, m, dt, W, (int)(sg % 2))) != PN_OK)
+                    break;
+                PN_CUDA(cudaEventRecord(rev_done[sg % 2], A), "event");
+            }
+            return r;
+        };
+        s2 = run();
+        c->stream = A;
+        cudaStreamSynchronize(B);      // (on an error, before the buffers go)
+        for (auto &e : ev)
+            if (e)
+                cudaEventDestroy(e);
+        if (s2 != PN_OK)
+            return s2;
     }
     // the entry acceleration A(x0, v0)
     if (x0) {
@@ -1138,7 +1226,7 @@ pn_status pn_step_vjp(pn_ctx *c, const double *x0, const double *v0, const doubl
             s2 = kdk_forward_checkpoints(c, W.xs, W.vs, m, W.as, dt, nsteps, K, cp);
         if (s2 == PN_OK) {
             FarForm far;
-            if (W.sums)
+            if (W.sums[0])
                 s2 = far.enter(c);
             if (s2 == PN_OK)
                 s2 = kdk_backward(c, cp, K, x0, v0, m, dt, nsteps, xbar_T, vbar_T, xbar0, vbar0,
@@ -1199,7 +1287,7 @@ pn_status pn_step_vjp_saved(pn_ctx *c, const double *ckpt, const double *m, doub
     const double *x0 = nsteps > 0 ? ckpt : nullptr;
     const double *v0 = nsteps > 0 ? ckpt + n3 : nullptr;
     FarForm far;
-    if (W.sums)
+    if (W.sums[0])
         st = far.enter(c);
     if (st == PN_OK)
         st = kdk_backward(c, ckpt, K, x0, v0, m, dt, nsteps, xbar_T, vbar_T, xbar0, vbar0, scal,

@@ -172,6 +172,7 @@ struct pn_ctx {
     // the near-source pass's side stream and its fork / join events
     cudaStream_t side;
     cudaEvent_t ev_fork, ev_join;
+    cudaStream_t adj_stream;   // the adjoint's segment recomputations (created on first use)
 
     // CUDA graph of pn_step_graph: captured once per (arrays, dt, nsteps)
     cudaStream_t cap_stream;
