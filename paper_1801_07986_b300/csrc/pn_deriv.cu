@@ -620,12 +620,13 @@ k_hermite(int stage, int64_t n3, double *__restrict__ x, double *__restrict__ v,
 // A is taken, of the hole mass M and of inv_c2 = 1/c^2.  Reverse mode over
 // the same decomposition, in double precision, without the near-source
 // split (far form throughout):
-//   star assembly (star_eqs): forward-mode Duals, one pass per input (33),
-//     contracted with the output cotangents (per star, O(n));
+//   star assembly (star_eqs): hand-derived reverse for the inputs that
+//     enter nonlinearly (d_i, v_i, M), closed forms for the sums that enter
+//     linearly (per star, one thread, O(n));
 //   pair sums: hand-derived reverse of the pair terms (below), one sweep
 //     over sources per target and one over targets per source (O(n^2));
-//   records and cluster sums: forward-mode Duals over (d_j, v_j, M), 7
-//     passes, contracted with their cotangents (per star, O(n)).
+//   records and cluster sums: their gradient in (d_j, v_j, M) in closed
+//     form, contracted with their cotangents (per star, one thread, O(n)).
 //
 // Pair terms (target i, source j), x = d_i - d_j, s^2 = |x|^2 + eps^2,
 // is = 1/s, mis3 = m_j is^3, xvj = x.v_j, xvi = x.v'_i (v' = 8/3 v),
@@ -740,128 +741,196 @@ __device__ __forceinline__ void star_lin_adj(double G, double M, double mi, doub
     out[24] = -4.0 * G2 * bw;                    // Phi
 }
 
-// Per star slot: the assembly's reverse.  Inputs: the forward sums (part,
-// split-major, double), the cluster sums (Dual layout, values used) and the
-// cotangent abar.  Outputs: the sums' cotangents sbar[16][slot], the direct
-// cotangents of d_i and of the velocity kbar[6][slot], and per block the
-// cotangents of the cluster sums, of M and of inv_c2 (kAdjGlob values).
-// Eight lanes per star slot, four stars per warp: lanes 0..6 run star_eqs on
-// Duals seeded in d_i (3), v_i (3) and M, lane 7 unseeded; lane 7 then adds
-// the closed-form cotangents of the linearly entering sums (star_lin_adj),
-// and the 1/c^2 cotangent ab . (1PN bracket) from its pass (A is linear in
-// 1/c^2).
-constexpr int kAdjStarLanes = 8;
-constexpr int kAdjStarWarps = kGlueThreads / kAdjStarLanes;   // star slots per block
+// Reverse of star_eqs (T = double) for the inputs that enter it
+// nonlinearly, d_i, v_i and M, the sums held fixed: with ab the cotangent
+// of a_i and bb that of the star's term of the hole's acceleration (1/c^2
+// included), the cotangents db, vb and Mb of ab.a_i + bb.bh_i, and the
+// values ab.pn_i (pn: the 1PN bracket) and bh_i that the 1/c^2 cotangent
+// takes.  Hand-derived, star_eqs' statements walked backwards: every
+// intermediate q of the forward (iR, iR3, v2, vd, vQ, Qd, S, cd, cv, cN,
+// cQ, c7, b1, gmr3, Wx, w_i, GM) gets its cotangent qb from the statements
+// that read it, then passes it on to its own inputs.  With al = ic ab and
+// gM = gmr3/M, X = 4 vQ (bb.d) - 3 vd (bb.Q) - 4 Qd (bb.v):
+//   cdb = al.d  cvb = al.v  cNb = al.N  cQb = al.Q  c7b = iR (al.Wx) - al.E
+//   Sb = G GM iR3 cdb   b1b = bb.w_i   gmr3b = -3 vd (bb.v) + X/M
+// (b1's two m_i/R_i terms cancel, so it reads -G(...) - G^2 (4 Phi + ...)).
+struct StarAdj {
+    double db[3], vb[3], Mb, apn, bh[3];
+};
 
-__global__ void __launch_bounds__(kGlueThreads)
+__device__ __forceinline__ void star_vjp(double G, double M, double mi, double eps2, double ic,
+                                         double fi, const double (&d)[3], const double (&vv)[3],
+                                         const StarSums<double> &s, const ClusterSums<double> &g,
+                                         const double (&ab)[3], const double (&bb)[3],
+                                         StarAdj &o)
+{
+    auto dot = [](const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; };
+    const double GM = G * M, G2 = G * G;
+    const double R2 = dot(d, d);
+    const double iR = 1.0 / sqrt(R2), iR2 = iR * iR, iR3 = iR2 * iR;
+    const double v2 = dot(vv, vv), vd = dot(vv, d);
+    double wi[3], Wx[3], al[3], PE[3];
+    for (int k = 0; k < 3; ++k) {
+        wi[k] = mi * iR3 * d[k];
+        Wx[k] = g.Wf[k] - fi * wi[k];
+        al[k] = ic * ab[k];
+        PE[k] = s.P[k] - 3.5 * s.Ee[k];
+    }
+    const double vQ = dot(vv, g.Q), Qd = dot(g.Q, d);
+    const double S = 4.0 * s.U + (g.SA - fi * 1.25 * mi * iR) + 0.5 * dot(d, Wx) -
+                     (g.SB - fi * 0.25 * mi * (R2 + eps2) * iR3);
+    const double A = 4.0 * GM * iR - v2;
+    const double cd = GM * iR3 * A + 5.0 * G * GM * mi * iR3 * iR + G * GM * iR3 * S -
+                      4.0 * G * iR3 * vQ;
+    const double cv = 4.0 * GM * iR3 * vd + 3.0 * G * iR3 * Qd;
+    const double cN = G * A, cQ = 4.0 * G * iR3 * vd, c7 = 3.5 * G * GM;
+    const double gmr3 = G * mi * iR3, gM = gmr3 / M;
+    const double Y = R2 * s.Z - s.Wr;
+    const double b1 = -G * (5.0 * GM * iR - 2.0 * v2 + 1.5 * vd * vd * iR2) -
+                      4.0 * G2 * mi * iR - G2 * (4.0 * (g.Phi - mi * iR) + 1.25 * s.U + 0.25 * Y);
+    // values: ab.pn and bh
+    double apn = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        const double pn = cd * d[k] + cv * vv[k] + G * 1.5 * s.Vp[k] + cN * s.N[k] -
+                          c7 * (s.E[k] - Wx[k] * iR) + cQ * g.Q[k] +
+                          G * 1.5 * (s.Hs * vv[k] - s.Hv[k]) + G * GM * PE[k];
+        apn += ab[k] * pn;
+        o.bh[k] = b1 * wi[k] - 3.0 * gmr3 * vd * vv[k] - 3.5 * G2 * mi * iR * s.N[k] +
+                  gM * (4.0 * vQ * d[k] - 3.0 * vd * g.Q[k] - 4.0 * Qd * vv[k]);
+    }
+    o.apn = apn;
+    // reverse
+    const double abd = dot(ab, d), ad = dot(al, d), av = dot(al, vv), aN = dot(al, s.N);
+    const double aQ = dot(al, g.Q), aWx = dot(al, Wx), aE = dot(al, s.E), aPE = dot(al, PE);
+    const double bw = dot(bb, wi), bv = dot(bb, vv), bd = dot(bb, d), bQ = dot(bb, g.Q);
+    const double bN = dot(bb, s.N);
+    const double X = 4.0 * vQ * bd - 3.0 * vd * bQ - 4.0 * Qd * bv;
+    const double cdb = ad, cvb = av, cNb = aN, cQb = aQ, c7b = aWx * iR - aE;
+    const double Sb = G * GM * iR3 * cdb, b1b = bw, gmr3b = -3.0 * vd * bv + X / M;
+    const double GMb = -abd * iR3 + G * aPE + 3.5 * G * c7b + 4.0 * G * iR * cNb +
+                       4.0 * iR3 * vd * cvb +
+                       cdb * (iR3 * A + 4.0 * GM * iR3 * iR + 5.0 * G * mi * iR3 * iR +
+                              G * iR3 * S) -
+                       5.0 * G * iR * b1b;
+    o.Mb = G * GMb - gM * X / M;
+    double iR3b = -GM * abd + 4.0 * G * vd * cQb + (4.0 * GM * vd + 3.0 * G * Qd) * cvb +
+                  cdb * (GM * A + 5.0 * G * GM * mi * iR + G * GM * S - 4.0 * G * vQ) +
+                  G * mi * gmr3b + fi * 0.25 * mi * (R2 + eps2) * Sb;
+    double iRb = c7 * aWx + 4.0 * G * GM * cNb + cdb * (4.0 * GM * GM * iR3 + 5.0 * G * GM * mi * iR3) -
+                 3.5 * G2 * mi * bN - b1b * (5.0 * G * GM + 3.0 * G * vd * vd * iR) -
+                 fi * 1.25 * mi * Sb;
+    const double v2b = -G * cNb - cdb * GM * iR3 + 2.0 * G * b1b;
+    const double vdb = 4.0 * G * iR3 * cQb + 4.0 * GM * iR3 * cvb - 3.0 * gmr3 * bv -
+                       3.0 * gM * bQ - 3.0 * G * vd * iR2 * b1b;
+    const double Qdb = 3.0 * G * iR3 * cvb - 4.0 * gM * bv;
+    const double vQb = -4.0 * G * iR3 * cdb + 4.0 * gM * bd;
+    double R2b = -0.25 * G2 * s.Z * b1b + fi * 0.25 * mi * iR3 * Sb;
+    double wib[3];
+    for (int k = 0; k < 3; ++k) {
+        const double Wxb = c7 * iR * al[k] + 0.5 * Sb * d[k];
+        wib[k] = b1 * bb[k] - fi * Wxb;
+    }
+    iR3b += mi * dot(wib, d);
+    iRb += 3.0 * iR2 * iR3b;
+    R2b -= 0.5 * iR3 * iRb;
+    for (int k = 0; k < 3; ++k) {
+        o.db[k] = -GM * iR3 * ab[k] + cd * al[k] + 0.5 * Sb * Wx[k] + 4.0 * gM * vQ * bb[k] +
+                  mi * iR3 * wib[k] + g.Q[k] * Qdb + vv[k] * vdb + 2.0 * d[k] * R2b;
+        o.vb[k] = (cv + 1.5 * G * s.Hs) * al[k] - (3.0 * gmr3 * vd + 4.0 * gM * Qd) * bb[k] +
+                  g.Q[k] * vQb + d[k] * vdb + 2.0 * vv[k] * v2b;
+    }
+}
+
+// Per star slot, one thread each: the assembly's reverse.  Inputs: the
+// forward sums (part, split-major, double; the js splits added in order),
+// the cluster sums (Dual layout, values used) and the cotangent abar.
+// Outputs: the sums' cotangents sbar[16][slot], the direct cotangents of d_i
+// and of the velocity kbar[6][slot], and per block of kAdjStarSlots slots the
+// cotangents of the cluster sums, of M and of inv_c2 (kAdjGlob values, added
+// in slot order): star_vjp for d_i, v_i and M, star_lin_adj for the sums
+// that enter linearly, and for 1/c^2 ab_i.pn_i + abar_hole.bh_i (A is linear
+// in 1/c^2; the hole's term carries 1/c^2 outside).
+constexpr int kAdjStarSlots = 32;     // star slots (threads) per block
+
+__global__ void __launch_bounds__(kAdjStarSlots)
 k_adj_star(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_clu,
            const double *__restrict__ x, const double *__restrict__ v,
            const double *__restrict__ m, const double *__restrict__ part, int js,
            const double *__restrict__ globs, const double *__restrict__ abar,
            double *__restrict__ sbar, double *__restrict__ kbar, double *__restrict__ blk)
 {
-    __shared__ double su[kAdjStarWarps][33];     // the star's inputs
-    __shared__ double sub[kAdjStarWarps][34];    // their cotangents (+ the hole's inv_c2 term)
-    const int st = threadIdx.x / kAdjStarLanes, sl = threadIdx.x % kAdjStarLanes;
-    const int64_t t = (int64_t)blockIdx.x * kAdjStarWarps + st;
+    __shared__ double sg[kAdjGlob][kAdjStarSlots];
+    const int64_t t = (int64_t)blockIdx.x * kAdjStarSlots + threadIdx.x;
     const int k_clu = cluster_of_block(blk_clu, t / kGlueThreads);
     const Clu Cl = clu[k_clu];
-    const double *glob = globs + (int64_t)k_clu * 2 * kJVals;
     const int64_t lt = t - Cl.slot0;
     const bool star = lt < Cl.ns;
-    const int64_t i = Cl.body0 + 1 + lt, hb = Cl.body0;
     if (star) {
-        if (sl < 3) {
-            su[st][sl] = x[3 * i + sl] - x[3 * hb + sl];
-            su[st][3 + sl] = v[3 * i + sl];
-            su[st][22 + sl] = glob[2 * sl];            // Q
-            su[st][25 + sl] = glob[2 * (6 + sl)];      // W_far (= W: far form)
-        }
-        for (int k = sl; k < kFusedVals; k += kAdjStarLanes) {
+        const double *glob = globs + (int64_t)k_clu * 2 * kJVals;
+        const int64_t i = Cl.body0 + 1 + lt, hb = Cl.body0;
+        double f[kFusedVals];
+#pragma unroll
+        for (int k = 0; k < kFusedVals; ++k) {
             double sv = 0.0;
             for (int q = 0; q < js; ++q)
                 sv += part[((int64_t)q * kFusedVals + k) * S + t];
-            su[st][6 + k] = sv;
+            f[k] = sv;
         }
-        if (sl == 3) {
-            su[st][28] = glob[18];
-            su[st][29] = glob[20];
-            su[st][30] = glob[22];
-            su[st][31] = m[hb];
-            su[st][32] = Cl.inv_c2;
+        double d[3], vv[3], ab[3], bb[3];
+        StarSums<double> ss;
+        ClusterSums<double> gs;
+        for (int k = 0; k < 3; ++k) {
+            d[k] = x[3 * i + k] - x[3 * hb + k];
+            vv[k] = v[3 * i + k];
+            ab[k] = abar[3 * i + k];
+            bb[k] = Cl.inv_c2 * abar[3 * hb + k];
+            ss.N[k] = f[k];
+            ss.Vp[k] = f[6 + k];
+            ss.Hv[k] = f[10 + k];
+            ss.E[k] = f[13 + k];
+            ss.P[k] = 0.0;
+            ss.Ee[k] = 0.0;
+            gs.Q[k] = glob[2 * k];
+            gs.Wf[k] = glob[2 * (6 + k)];     // W_far = W: far form
         }
+        ss.U = f[3];
+        ss.Z = f[4];
+        ss.Wr = f[5];
+        ss.Hs = f[9];
+        gs.SA = glob[18];
+        gs.SB = glob[20];
+        gs.Phi = glob[22];
+        const double M = m[hb];
+        StarAdj o;
+        star_vjp(Cl.G, M, m[i], Cl.eps2, Cl.inv_c2, 1.0, d, vv, ss, gs, ab, bb, o);
+        double lin[25];
+        star_lin_adj(Cl.G, M, m[i], Cl.inv_c2, d, vv, ab, bb, lin);
+        for (int k = 0; k < kFusedVals; ++k)
+            sbar[(int64_t)k * S + t] = lin[k];
+        for (int k = 0; k < 3; ++k) {
+            kbar[(int64_t)k * S + t] = o.db[k];
+            kbar[(int64_t)(3 + k) * S + t] = o.vb[k];
+        }
+        for (int k = 0; k < 9; ++k)
+            sg[k][threadIdx.x] = lin[16 + k];
+        sg[9][threadIdx.x] = o.Mb;
+        sg[10][threadIdx.x] = o.apn + (abar[3 * hb] * o.bh[0] + abar[3 * hb + 1] * o.bh[1] +
+                                       abar[3 * hb + 2] * o.bh[2]);
+    } else {
+        for (int k = 0; k < kFusedVals; ++k)
+            sbar[(int64_t)k * S + t] = 0.0;
+        for (int k = 0; k < 6; ++k)
+            kbar[(int64_t)k * S + t] = 0.0;
+        for (int k = 0; k < kAdjGlob; ++k)
+            sg[k][threadIdx.x] = 0.0;
     }
     __syncwarp();
-    if (star) {
-        const double ab[3] = {abar[3 * i], abar[3 * i + 1], abar[3 * i + 2]};
-        const double bb[3] = {Cl.inv_c2 * abar[3 * hb], Cl.inv_c2 * abar[3 * hb + 1],
-                              Cl.inv_c2 * abar[3 * hb + 2]};
-        const int seed = sl < 6 ? sl : (sl == 6 ? 31 : -1);
-        Dual w[33];
-        for (int k = 0; k < 33; ++k)
-            w[k] = dual(su[st][k], k == seed ? 1.0 : 0.0);
-        Dual d[3] = {w[0], w[1], w[2]}, vv[3] = {w[3], w[4], w[5]};
-        StarSums<Dual> ss;
-        for (int k = 0; k < 3; ++k) {
-            ss.N[k] = w[6 + k];
-            ss.Vp[k] = w[12 + k];
-            ss.Hv[k] = w[16 + k];
-            ss.E[k] = w[19 + k];
-            ss.P[k] = dual(0.0, 0.0);
-            ss.Ee[k] = dual(0.0, 0.0);
-        }
-        ss.U = w[9];
-        ss.Z = w[10];
-        ss.Wr = w[11];
-        ss.Hs = w[15];
-        ClusterSums<Dual> gs;
-        for (int k = 0; k < 3; ++k) {
-            gs.Q[k] = w[22 + k];
-            gs.Wf[k] = w[25 + k];
-        }
-        gs.SA = w[28];
-        gs.SB = w[29];
-        gs.Phi = w[30];
-        Dual ai[3], bh[3], pn[3];
-        star_eqs<Dual, Dual>(Cl.G, w[31], m[i], Cl.eps2, w[32], 1.0, d, vv, ss, gs, ai, bh, pn);
-        if (seed >= 0) {
-            double acc = 0.0;
-            for (int k = 0; k < 3; ++k)
-                acc += ab[k] * ai[k].d + bb[k] * bh[k].d;
-            sub[st][seed] = acc;
-        } else {
-            const double dv[3] = {su[st][0], su[st][1], su[st][2]};
-            const double vv0[3] = {su[st][3], su[st][4], su[st][5]};
-            double lin[25];
-            star_lin_adj(Cl.G, su[st][31], m[i], Cl.inv_c2, dv, vv0, ab, bb, lin);
-            for (int k = 0; k < kFusedVals; ++k)
-                sub[st][6 + k] = lin[k];
-            for (int k = 0; k < 9; ++k)
-                sub[st][22 + k] = lin[16 + k];
-            // d/d(inv_c2): abar_i . (1PN bracket); bh does not depend on it
-            sub[st][32] = ab[0] * pn[0].v + ab[1] * pn[1].v + ab[2] * pn[2].v;
-            // the hole's inv_c2 term: abar_hole . (star i's term)
-            sub[st][33] = abar[3 * hb] * bh[0].v + abar[3 * hb + 1] * bh[1].v +
-                          abar[3 * hb + 2] * bh[2].v;
-        }
-    }
-    __syncwarp();
-    for (int k = sl; k < kFusedVals; k += kAdjStarLanes)
-        sbar[(int64_t)k * S + t] = star ? sub[st][6 + k] : 0.0;
-    if (sl < 6)
-        kbar[(int64_t)sl * S + t] = star ? sub[st][sl] : 0.0;
-    __syncthreads();
     // per-block sums over the block's star slots, in slot order
     if (threadIdx.x < kAdjGlob) {
-        const int k = threadIdx.x;
         double g = 0.0;
-        for (int w2 = 0; w2 < kAdjStarWarps; ++w2) {
-            const int64_t t2 = (int64_t)blockIdx.x * kAdjStarWarps + w2;
-            if (t2 - Cl.slot0 >= Cl.ns)
-                continue;
-            g += k < 9 ? sub[w2][22 + k] : (k == 9 ? sub[w2][31] : sub[w2][32] + sub[w2][33]);
-        }
-        blk[(int64_t)blockIdx.x * kAdjGlob + k] = g;
+        for (int w2 = 0; w2 < kAdjStarSlots; ++w2)
+            g += sg[threadIdx.x][w2];
+        blk[(int64_t)blockIdx.x * kAdjGlob + threadIdx.x] = g;
     }
 }
 
@@ -871,7 +940,7 @@ k_adj_globals(const Clu *__restrict__ clu, const double *__restrict__ blk,
 {
     __shared__ double sh[kAdjGlob][kGlueThreads];
     const Clu C = clu[blockIdx.x];
-    sum_blocks<kAdjGlob>(blk + (C.slot0 / kAdjStarWarps) * kAdjGlob, C.ns_pad / kAdjStarWarps, sh);
+    sum_blocks<kAdjGlob>(blk + (C.slot0 / kAdjStarSlots) * kAdjGlob, C.ns_pad / kAdjStarSlots, sh);
     if (threadIdx.x < kAdjGlob)
         gbar[(int64_t)blockIdx.x * kAdjGlob + threadIdx.x] = sh[threadIdx.x][0];
 }
@@ -1334,12 +1403,6 @@ k_adj_sources_packed(const float4 *__restrict__ srec, const float4 *__restrict__
         atomicOr(flag, kFlagTimeout);
 }
 
-// Per star slot: the records' and cluster sums' reverse (forward-mode Duals
-// over d_j (3), v_j (3), M), plus every cotangent gathered so far; writes
-// the star's xbar, vbar and, per block, -sum dbar (the hole's xbar) and the
-// M cotangent (4 values).  Eight lanes per star slot (as k_adj_star): the
-// lanes first sum the split partials (each a share of the 20 values, splits
-// in order), then lanes 0..6 take one seed each.
 // Split partials of the jerk's and the reverse sweeps' pair kernels summed in
 // place: part holds js splits of nv values of S slots ([split][value][slot]);
 // thread (k, t) adds the js partials of value k of slot t, in split order,
@@ -1369,7 +1432,26 @@ k_split_sum(int64_t S, int nv, int js, double *__restrict__ part)
     part[e] = acc;
 }
 
-__global__ void __launch_bounds__(kGlueThreads)
+// Per star slot, one thread each: the records' and cluster sums' reverse for
+// star j (d_j, v_j and M), plus every cotangent gathered so far; writes the
+// star's xbar and vbar and, per block of kAdjStarSlots slots, -sum dbar (the
+// hole's xbar) and the M cotangent (4 values, added in slot order).  The
+// record and cluster-sum terms that depend on d_j, v_j and M, contracted
+// with their cotangents (sp: the source sweep's 14, gb: the cluster sums'),
+// with GM = G M, Wb = W cotangent + G abar_hole, D8 = sp_D.d_j,
+// Wd = (sp_w + Wb).d_j:
+//   a = sp_R2 R^2 + sp_C [GM (iR + eps^2 iR3/6) - 4/3 v^2] - GM/3 iR3 D8
+//       + m_j iR3 Wd + m_j (gb_Q.v) + m_j (5/4 gb_SA iR + 1/4 gb_SB (R^2 + eps^2) iR3
+//       + gb_Phi iR)
+// (C_j = c/1.5 - 4/3 v^2 with c = GM (1.5 iR + 1/4 eps^2 iR3), D_j = -e/1.5
+// = -GM/3 iR3 d_j, w_j = m_j iR3 d_j); its gradient in closed form:
+//   da/dM   = G [sp_C (iR + eps^2 iR3/6) - iR3 D8/3]
+//   da/dv   = -8/3 sp_C v + m_j gb_Q
+//   da/dd   = iR3 (m_j (sp_w + Wb) - GM/3 sp_D) + 2 d R2b, where
+//   R2b = sp_R2 + 1/4 gb_SB m_j iR3 - iR3/2 [da/diR + 3 iR^2 da/diR3],
+//   da/diR  = sp_C GM + m_j (5/4 gb_SA + gb_Phi),
+//   da/diR3 = sp_C GM eps^2/6 - GM/3 D8 + m_j Wd + 1/4 gb_SB m_j (R^2 + eps^2).
+__global__ void __launch_bounds__(kAdjStarSlots)
 k_adj_records(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_clu,
               const double *__restrict__ x, const double *__restrict__ v,
               const double *__restrict__ m, const double *__restrict__ abar,
@@ -1377,86 +1459,69 @@ k_adj_records(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ bl
               const double *__restrict__ spart, int jss, const double *__restrict__ gbar,
               double *__restrict__ xbar, double *__restrict__ vbar, double *__restrict__ blk)
 {
-    constexpr int kNT = 6, kNV = kNT + kAdjSrc;       // target and source partials
-    __shared__ double sp_[kAdjStarWarps][kNV];
-    __shared__ double ub_[kAdjStarWarps][8];
-    __shared__ double h4_[kAdjStarWarps][4];
-    const int st = threadIdx.x / kAdjStarLanes, sl = threadIdx.x % kAdjStarLanes;
-    const int64_t t = (int64_t)blockIdx.x * kAdjStarWarps + st;
+    constexpr int kNT = 6;
+    __shared__ double h4_[4][kAdjStarSlots];
+    const int64_t t = (int64_t)blockIdx.x * kAdjStarSlots + threadIdx.x;
     const int k_clu = cluster_of_block(blk_clu, t / kGlueThreads);
     const Clu Cl = clu[k_clu];
     const double *gb = gbar + (int64_t)k_clu * kAdjGlob;
     const int64_t lt = t - Cl.slot0;
     const bool star = lt < Cl.ns;
-    const int64_t j = Cl.body0 + 1 + lt, hb = Cl.body0;
+    for (int k = 0; k < 4; ++k)
+        h4_[k][threadIdx.x] = 0.0;
     if (star) {
-        // split sums: values sl, sl + 8, sl + 16 of (tp[6], sp[14])
-        double acc[3] = {0.0, 0.0, 0.0};
-        for (int q = 0; q < (jst > jss ? jst : jss); ++q)
+        const int64_t j = Cl.body0 + 1 + lt, hb = Cl.body0;
+        // split sums of the target (6) and source (14) partials, splits in order
+        double tp[kNT], sp[kAdjSrc];
 #pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                const int k = sl + 8 * r;
-                if (k < kNT) {
-                    if (q < jst)
-                        acc[r] += tpart[((int64_t)q * kNT + k) * S + t];
-                } else if (k < kNV) {
-                    if (q < jss)
-                        acc[r] += spart[((int64_t)q * kAdjSrc + (k - kNT)) * S + t];
-                }
-            }
+        for (int k = 0; k < kNT; ++k) {
+            double a = 0.0;
+            for (int q = 0; q < jst; ++q)
+                a += tpart[((int64_t)q * kNT + k) * S + t];
+            tp[k] = a;
+        }
 #pragma unroll
-        for (int r = 0; r < 3; ++r)
-            if (sl + 8 * r < kNV)
-                sp_[st][sl + 8 * r] = acc[r];
+        for (int k = 0; k < kAdjSrc; ++k) {
+            double a = 0.0;
+            for (int q = 0; q < jss; ++q)
+                a += spart[((int64_t)q * kAdjSrc + k) * S + t];
+            sp[k] = a;
+        }
+        const double mj = m[j], G = Cl.G, eps2 = Cl.eps2, GM = G * m[hb];
+        double d[3], vv[3];
+        for (int k = 0; k < 3; ++k) {
+            d[k] = x[3 * j + k] - x[3 * hb + k];
+            vv[k] = v[3 * j + k];
+        }
+        const double R2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        const double iR = 1.0 / sqrt(R2), iR3 = iR * iR * iR;
+        double Ws[3], D8 = 0.0, Wd = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            Ws[k] = sp[11 + k] + gb[3 + k] + G * abar[3 * hb + k];
+            D8 += sp[8 + k] * d[k];
+            Wd += Ws[k] * d[k];
+        }
+        const double daiR = sp[7] * GM + mj * (1.25 * gb[6] + gb[8]);
+        const double daiR3 = sp[7] * GM * eps2 / 6.0 - GM / 3.0 * D8 + mj * Wd +
+                             0.25 * gb[7] * mj * (R2 + eps2);
+        const double R2b = sp[6] + 0.25 * gb[7] * mj * iR3 -
+                           0.5 * iR3 * (daiR + 3.0 * iR * iR * daiR3);
+        for (int k = 0; k < 3; ++k) {
+            const double ud = iR3 * (mj * Ws[k] - GM / 3.0 * sp[8 + k]) + 2.0 * d[k] * R2b;
+            const double uv = -8.0 / 3.0 * sp[7] * vv[k] + mj * gb[k];
+            const double dbar = kbar[(int64_t)k * S + t] + tp[k] + sp[k] + ud;
+            xbar[3 * j + k] = dbar;
+            vbar[3 * j + k] = kbar[(int64_t)(3 + k) * S + t] + 8.0 / 3.0 * tp[3 + k] + sp[3 + k] + uv;
+            h4_[k][threadIdx.x] = -dbar;
+        }
+        h4_[3][threadIdx.x] = G * (sp[7] * (iR + eps2 * iR3 / 6.0) - iR3 * D8 / 3.0);
     }
     __syncwarp();
-    if (star && sl < 7) {
-        const double *sp = sp_[st] + kNT;
-        const double mj = m[j], G = Cl.G, eps2 = Cl.eps2;
-        const double Wb[3] = {gb[3] + G * abar[3 * hb], gb[4] + G * abar[3 * hb + 1],
-                              gb[5] + G * abar[3 * hb + 2]};
-        Dual w[7];
-        for (int k = 0; k < 3; ++k) {
-            w[k] = dual(x[3 * j + k] - x[3 * hb + k], sl == k ? 1.0 : 0.0);
-            w[3 + k] = dual(v[3 * j + k], sl == 3 + k ? 1.0 : 0.0);
-        }
-        w[6] = dual(m[hb], sl == 6 ? 1.0 : 0.0);
-        const Dual R2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
-        const Dual iR = 1.0 / tsqrt(R2);
-        const Dual iR3 = iR * iR * iR;
-        const Dual GM = G * w[6];
-        const Dual c = GM * (1.5 * iR + 0.25 * eps2 * iR3);
-        const Dual Cc = c / 1.5 - (4.0 / 3.0) * (w[3] * w[3] + w[4] * w[4] + w[5] * w[5]);
-        const Dual ne = -(GM / 3.0) * iR3;       // -e/1.5 = ne d
-        Dual a = sp[6] * R2 + sp[7] * Cc;
-        for (int k = 0; k < 3; ++k) {
-            a += sp[8 + k] * (ne * w[k]);
-            a += (sp[11 + k] + Wb[k]) * (mj * iR3 * w[k]);
-            a += gb[k] * (mj * w[3 + k]);
-        }
-        a += gb[6] * (1.25 * mj * iR) + gb[7] * (0.25 * mj * (R2 + eps2) * iR3) +
-             gb[8] * (mj * iR);
-        ub_[st][sl] = a.d;
-    }
-    __syncwarp();
-    if (sl < 4)
-        h4_[st][sl] = 0.0;
-    if (star && sl < 3) {
-        const double *tp = sp_[st], *sp = sp_[st] + kNT;
-        const double dbar = kbar[(int64_t)sl * S + t] + tp[sl] + sp[sl] + ub_[st][sl];
-        xbar[3 * j + sl] = dbar;
-        vbar[3 * j + sl] = kbar[(int64_t)(3 + sl) * S + t] + 8.0 / 3.0 * tp[3 + sl] + sp[3 + sl] +
-                           ub_[st][3 + sl];
-        h4_[st][sl] = -dbar;
-    }
-    if (star && sl == 3)
-        h4_[st][3] = ub_[st][6];
-    __syncthreads();
     // per-block sums over the block's star slots, in slot order
     if (threadIdx.x < 4) {
         double g = 0.0;
-        for (int w2 = 0; w2 < kAdjStarWarps; ++w2)
-            g += h4_[w2][threadIdx.x];
+        for (int w2 = 0; w2 < kAdjStarSlots; ++w2)
+            g += h4_[threadIdx.x][w2];
         blk[(int64_t)blockIdx.x * 4 + threadIdx.x] = g;
     }
 }
@@ -1471,7 +1536,7 @@ k_adj_hole(const Clu *__restrict__ clu, const double *__restrict__ blk,
 {
     __shared__ double sh[4][kGlueThreads];
     const Clu C = clu[blockIdx.x];
-    sum_blocks<4>(blk + (C.slot0 / kAdjStarWarps) * 4, C.ns_pad / kAdjStarWarps, sh);
+    sum_blocks<4>(blk + (C.slot0 / kAdjStarSlots) * 4, C.ns_pad / kAdjStarSlots, sh);
     if (threadIdx.x == 0) {
         const double *gb = gbar + (int64_t)blockIdx.x * kAdjGlob;
         for (int k = 0; k < 3; ++k) {
@@ -1640,7 +1705,7 @@ size_t adjoint_buffer_doubles(const pn_ctx *c)
 {
     const int64_t S = c->S, js = jerk_part_splits(c);
     return (size_t)((16 + 6) * S + js * (6 + kAdjSrc) * S + kAdjTVals * 2 * S +
-                    (S / kAdjStarWarps) * (kAdjGlob + 4) + (int64_t)c->nclu * kAdjGlob);
+                    (S / kAdjStarSlots) * (kAdjGlob + 4) + (int64_t)c->nclu * kAdjGlob);
 }
 
 cudaError_t launch_accel_vjp(pn_ctx *c, const double *x, const double *v, const double *m,
@@ -1658,7 +1723,7 @@ cudaError_t launch_accel_vjp(pn_ctx *c, const double *x, const double *v, const 
     // staged targets of the packed source sweep (13 float4 per slot, 16-byte aligned)
     float4 *tst = reinterpret_cast<float4 *>(spart + (int64_t)js * kAdjSrc * S);
     double *kblk = spart + (int64_t)js * kAdjSrc * S + kAdjTVals * 2 * S;
-    double *gbar = kblk + (S / kAdjStarWarps) * kAdjGlob, *hblk = gbar + (int64_t)c->nclu * kAdjGlob;
+    double *gbar = kblk + (S / kAdjStarSlots) * kAdjGlob, *hblk = gbar + (int64_t)c->nclu * kAdjGlob;
     const int *bc = c->nclu > 1 ? c->blk_clu : nullptr;
     dim3 grid((unsigned)(S / kJThreads), (unsigned)js);
     const bool mixed = c->p.precision == PN_MIXED;
@@ -1696,7 +1761,7 @@ cudaError_t launch_accel_vjp(pn_ctx *c, const double *x, const double *v, const 
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
     // reverse
-    k_adj_star<<<(unsigned)(S / kAdjStarWarps), kGlueThreads, 0, c->stream>>>(S, c->d_clu, bc, x, v, m, fwd, jsf,
+    k_adj_star<<<(unsigned)(S / kAdjStarSlots), kAdjStarSlots, 0, c->stream>>>(S, c->d_clu, bc, x, v, m, fwd, jsf,
                                                                jglob, abar, sbar, kbar, kblk);
     k_adj_globals<<<c->nclu, kGlueThreads, 0, c->stream>>>(c->d_clu, kblk, gbar);
     int jsr = js;
@@ -1733,7 +1798,7 @@ cudaError_t launch_accel_vjp(pn_ctx *c, const double *x, const double *v, const 
                       0, c->stream>>>(S, kAdjSrc, jsr, spart);
         c->launches += 2;
     }
-    k_adj_records<<<(unsigned)(S / kAdjStarWarps), kGlueThreads, 0, c->stream>>>(
+    k_adj_records<<<(unsigned)(S / kAdjStarSlots), kAdjStarSlots, 0, c->stream>>>(
         S, c->d_clu, bc, x, v, m, abar, kbar, tpart, 1, spart, 1, gbar, xbar, vbar, hblk);
     k_adj_hole<<<c->nclu, kGlueThreads, 0, c->stream>>>(c->d_clu, hblk, gbar, xbar, vbar, scal,
                                                        accumulate ? 1 : 0);

@@ -234,8 +234,7 @@ template <class T, class TM>
 __device__ __forceinline__ void star_eqs(double G, const TM &M, double mi, double eps2,
                                          const TM &inv_c2, double fi, const T (&d)[3],
                                          const T (&vv)[3], const StarSums<T> &s,
-                                         const ClusterSums<T> &g, T (&ai)[3], T (&bh)[3],
-                                         T *pn_out = nullptr)
+                                         const ClusterSums<T> &g, T (&ai)[3], T (&bh)[3])
 {
     const TM GM = G * M;
     const T R2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
@@ -268,8 +267,6 @@ __device__ __forceinline__ void star_eqs(double G, const TM &M, double mi, doubl
                      c7 * (s.E[k] - Wx[k] * iR) + cQ * g.Q[k] + G * H[k] +
                      G * GM * (s.P[k] - 3.5 * s.Ee[k]);
         ai[k] = (-GM * iR3 * d[k] - G * s.N[k]) + inv_c2 * pn;
-        if (pn_out)               // dai/d(inv_c2): A is linear in 1/c^2
-            pn_out[k] = pn;
     }
     const T b1 = -G * (5.0 * GM * iR - 2.0 * v2 + 1.5 * vd * vd * iR * iR) -
                  4.0 * G * G * mi * iR - G * G * (4.0 * (g.Phi - mi * iR) + 1.25 * s.U + 0.25 * Y);
