@@ -595,6 +595,9 @@ static pn_status init_common(pn_ctx **out, int nclu, const int64_t *off, const p
         c->fused_tile = pn::kPackTile;
         c->fused_stages = pn::kPackStages;
     }
+    // the adjoint's pair sweeps: one merged pass unless PN_ADJ_SEPARATE is set
+    if (const char *as = std::getenv("PN_ADJ_SEPARATE"))
+        c->adj_separate = std::atoi(as) != 0;
     pn::FusedShape fs{};
     // segment buffer: the largest over every fused variant (the tuner may switch)
     int64_t seg_max = 0;

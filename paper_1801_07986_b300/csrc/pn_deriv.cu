@@ -1403,6 +1403,216 @@ k_adj_sources_packed(const float4 *__restrict__ srec, const float4 *__restrict__
         atomicOr(flag, kFlagTimeout);
 }
 
+// Both reverse sweeps in one pass over the pairs (mixed contexts, replacing
+// the two kernels above where the rows fit): two targets per thread as in
+// k_adj_targets_packed, their (d, v') cotangents summed in registers over
+// the block's sources, and the 14 record cotangents of every source (as in
+// k_adj_sources_packed) summed over the block's 256 targets, so that each
+// pair's intermediates are computed once for both.  Inside a warp the
+// sources rotate: a tile is two chunks of 32 sources; at step q of a chunk
+// lane l takes source (l + q) mod 32 together with that source's running
+// sums, adds its two targets' terms and hands the sums to lane l - 1, so
+// after 32 steps lane l holds source l's sums over the warp's 64 targets
+// (each sum visits lanes s, s - 1, ..., a fixed order).  The four warps'
+// sums are then added in warp order (shared rows, two sets alternating by
+// tile so one barrier per tile suffices) into one FP32 row per target
+// block: spf[p][14][slot], p the target block's index within its cluster.
+constexpr int kAdjWarps = kMixThreads / 32;
+
+__global__ void __launch_bounds__(kMixThreads, 3)
+k_adj_pairs_packed(const float4 *__restrict__ srec, int64_t S, const Clu *__restrict__ clu,
+                   const int *__restrict__ blk_clu, const double *__restrict__ sbar,
+                   int *__restrict__ flag, double *__restrict__ tpart, float *__restrict__ spf)
+{
+    __shared__ __align__(128) float4 sh[2][kAdjPackTile][kPackVals];
+    __shared__ float red[2][kAdjWarps][kAdjSrc][kAdjPackTile];
+    __shared__ __align__(8) uint64_t full[2];
+    const int64_t t0 = (int64_t)blockIdx.x * 2 * kMixThreads;
+    const Clu C = clu[cluster_of_block(blk_clu, t0 / kGlueThreads)];
+    const int64_t ntiles = C.ns_pad / kAdjPackTile, js = gridDim.y, sp = blockIdx.y;
+    const int64_t tb = sp * ntiles / js, te = (sp + 1) * ntiles / js;
+    double *out = tpart + sp * 6 * S;
+    float *srow = spf + (t0 - C.slot0) / (2 * kMixThreads) * kAdjSrc * S;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t ta = t0 + threadIdx.x, tq = ta + kMixThreads;
+    if (te <= tb) {
+        for (int k = 0; k < 6; ++k) {
+            out[k * S + ta] = 0.0;
+            out[k * S + tq] = 0.0;
+        }
+        return;
+    }
+    const float4 *ra = srec + ta * kPackVals, *rq = srec + tq * kPackVals;
+    const float4 A0 = ra[0], A1 = ra[1], A2 = ra[2], A3 = ra[3], A4 = ra[4], A5 = ra[5];
+    const float4 B0 = rq[0], B1 = rq[1], B2 = rq[2], B3 = rq[3], B4 = rq[4], B5 = rq[5];
+    const float e3 = 8.0f / 3.0f;
+    const float2 hx = make_float2(-A0.x, -B0.x), hy = make_float2(-A0.z, -B0.z),
+                 hz = make_float2(-A1.x, -B1.x), lx = make_float2(-A2.x, -B2.x),
+                 ly = make_float2(-A2.z, -B2.z), lz = make_float2(-A3.x, -B3.x);
+    const float2 vpx = make_float2(e3 * A4.x, e3 * B4.x), vpy = make_float2(e3 * A4.z, e3 * B4.z),
+                 vpz = make_float2(e3 * A5.x, e3 * B5.x);
+    float2 sb[kFusedVals];
+#pragma unroll
+    for (int k = 0; k < kFusedVals; ++k)
+        sb[k] = make_float2((float)sbar[k * S + ta], (float)sbar[k * S + tq]);
+    sb[3] = make_float2(-sb[3].x, -sb[3].y);
+    const float e2 = (float)C.eps2;
+    const float2 eps2 = make_float2(e2, e2);
+    float2 acc[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+        acc[k] = make_float2(0.0f, 0.0f);
+    if (threadIdx.x == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    constexpr unsigned kBytes = kAdjPackTile * kPackVals * 16;
+    if (threadIdx.x == 0) {
+        bulk_load(sh[0], srec + (C.slot0 + tb * kAdjPackTile) * kPackVals, kBytes, &full[0], 0);
+        if (tb + 1 < te)
+            bulk_load(sh[1], srec + (C.slot0 + (tb + 1) * kAdjPackTile) * kPackVals, kBytes,
+                      &full[1], 0);
+    }
+    bool first = true;
+    for (int64_t tile = tb; tile < te; ++tile) {
+        const int b = (int)((tile - tb) & 1);
+        const bool ok = mbar_wait(&full[b], (unsigned)(((tile - tb) >> 1) & 1));
+        const int64_t j0 = C.slot0 + tile * kAdjPackTile;
+        const bool diag = (j0 < t0 + 2 * kMixThreads) && (t0 < j0 + kAdjPackTile);
+        const float4 (*tl)[kPackVals] = sh[b];
+#pragma unroll 1
+        for (int ch = 0; ch < kAdjPackTile; ch += 32) {
+            float s[kAdjSrc];
+#pragma unroll
+            for (int k = 0; k < kAdjSrc; ++k)
+                s[k] = 0.0f;
+#pragma unroll 1
+            for (int q = 0; q < 32; ++q) {
+                const int u = ch + ((lane + q) & 31);
+                const float4 S0 = tl[u][0], S1 = tl[u][1], S2 = tl[u][2], S3 = tl[u][3],
+                             S4 = tl[u][4], S5 = tl[u][5], S6 = tl[u][6], S7 = tl[u][7],
+                             S8 = tl[u][8];
+                const bool sx = diag && j0 + u == ta, sy = diag && j0 + u == tq;
+                AdjP2 p;
+                adj_pair2(hx, hy, hz, lx, ly, lz, vpx, vpy, vpz, sb, lo2(S0), hi2(S0), lo2(S1),
+                          lo2(S2), hi2(S2), lo2(S3), hi2(S1), hi2(S3), lo2(S4), hi2(S4),
+                          lo2(S5), hi2(S5), lo2(S6), hi2(S6), lo2(S7), hi2(S7), lo2(S8),
+                          hi2(S8), eps2, sx, sy, p);
+                const float2 mVx = mul2(p.mis3, p.Vx), mHb = mul2(p.mis3, p.Hb);
+                // the targets' sums
+                acc[0] = fma2(mVx, lo2(S6), add2(acc[0], p.gx));
+                acc[1] = fma2(mVx, hi2(S6), add2(acc[1], p.gy));
+                acc[2] = fma2(mVx, lo2(S7), add2(acc[2], p.gz));
+                acc[3] = fma2(mHb, p.x, fma2(mVx, lo2(S4), acc[3]));
+                acc[4] = fma2(mHb, p.y, fma2(mVx, hi2(S4), acc[4]));
+                acc[5] = fma2(mHb, p.z, fma2(mVx, lo2(S5), acc[5]));
+                // the source's terms from both targets (d via x negated at the store)
+                const float2 gg = mul2(p.mis3, p.Gq);
+                float2 c[kAdjSrc];
+                c[0] = p.gx;
+                c[1] = p.gy;
+                c[2] = p.gz;
+                c[3] = fma2(gg, sb[10], mul2(p.mis3, fma2(p.cv, p.x, mul2(p.Vx, vpx))));
+                c[4] = fma2(gg, sb[11], mul2(p.mis3, fma2(p.cv, p.y, mul2(p.Vx, vpy))));
+                c[5] = fma2(gg, sb[12], mul2(p.mis3, fma2(p.cv, p.z, mul2(p.Vx, vpz))));
+                c[6] = mul2(p.mis3, sb[5]);
+                c[7] = mVx;
+                c[8] = mul2(mVx, p.dx);
+                c[9] = mul2(mVx, p.dy);
+                c[10] = mul2(mVx, p.dz);
+                c[11] = mul2(p.is, sb[13]);
+                c[12] = mul2(p.is, sb[14]);
+                c[13] = mul2(p.is, sb[15]);
+#pragma unroll
+                for (int k = 0; k < kAdjSrc; ++k)
+                    s[k] = __shfl_sync(0xffffffffu, s[k] + c[k].x + c[k].y, (lane + 1) & 31);
+            }
+#pragma unroll
+            for (int k = 0; k < kAdjSrc; ++k)
+                red[b][wid][k][ch + lane] = s[k];
+        }
+        if (((tile - tb + 1) % kAdjPackFlush) == 0 || tile + 1 == te) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                adj_out(out + k * S + ta, acc[k].x, first);
+                adj_out(out + k * S + tq, acc[k].y, first);
+                acc[k] = make_float2(0.0f, 0.0f);
+            }
+            first = false;
+        }
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0 && tile + 1 < te)
+                mbar_wait(&full[b ^ 1], (unsigned)(((tile - tb + 1) >> 1) & 1));
+            if (threadIdx.x == 0)
+                atomicOr(flag, kFlagTimeout);
+            return;
+        }
+        if (threadIdx.x == 0 && tile + 2 < te)
+            bulk_load(sh[b], srec + (C.slot0 + (tile + 2) * kAdjPackTile) * kPackVals, kBytes,
+                      &full[b], 0);
+        // this tile's source rows: the warps' sums in warp order (set b is
+        // written again two tiles on, after the next barrier)
+        for (int e = threadIdx.x; e < kAdjSrc * kAdjPackTile; e += kMixThreads) {
+            const int k = e / kAdjPackTile, u = e % kAdjPackTile;
+            float r = red[b][0][k][u];
+#pragma unroll
+            for (int w = 1; w < kAdjWarps; ++w)
+                r += red[b][w][k][u];
+            srow[(int64_t)k * S + j0 + u] = k < 3 ? -r : r;
+        }
+    }
+}
+
+// The merged sweep's partials summed, one thread per value and slot, eight
+// loads in flight: e < 14 S, value k = e / S of slot t = e % S, adds its
+// cluster's FP32 source rows in target-block order into spart[e] -- a
+// compensated FP32 sum (Knuth's TwoSum carrying each addition's rounding
+// error), so no FP64 additions, whose pipe runs at 1/64 of FP32's; the
+// remaining 6 S threads add the jst FP64 target splits in split order into
+// split 0 (as k_split_sum).
+__global__ void __launch_bounds__(kGlueThreads)
+k_adj_row_sums(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_clu,
+               const float *__restrict__ spf, double *__restrict__ spart,
+               double *__restrict__ tpart, int jst)
+{
+    const int64_t e = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
+    const int64_t stride = (int64_t)kAdjSrc * S;
+    if (e >= stride) {
+        const int64_t f = e - stride, ts = 6 * S;
+        if (f >= ts)
+            return;
+        double acc = tpart[f];
+        for (int q = 1; q < jst; ++q)
+            acc += tpart[(int64_t)q * ts + f];
+        tpart[f] = acc;
+        return;
+    }
+    const int64_t t = e % S;
+    const Clu C = clu[cluster_of_block(blk_clu, t / kGlueThreads)];
+    const int64_t np = C.ns_pad / (2 * kMixThreads);
+    float hi = 0.0f, lo = 0.0f;
+    auto add = [&](float x) {        // hi + lo += x, the rounding error of hi + x kept in lo
+        const float sum = hi + x, z = sum - hi;
+        lo += (hi - (sum - z)) + (x - z);
+        hi = sum;
+    };
+    int64_t p = 0;
+    for (; p + 8 <= np; p += 8) {
+        float r[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            r[i] = spf[(p + i) * stride + e];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            add(r[i]);
+    }
+    for (; p < np; ++p)
+        add(spf[p * stride + e]);
+    spart[e] = (double)hi + (double)lo;
+}
+
 // Split partials of the jerk's and the reverse sweeps' pair kernels summed in
 // place: part holds js splits of nv values of S slots ([split][value][slot]);
 // thread (k, t) adds the js partials of value k of slot t, in split order,
@@ -1697,15 +1907,31 @@ static int64_t adj_pack_splits(const pn_ctx *c)
     return js > cap ? cap : js;
 }
 
+// Target-block rows of the merged sweep's source sums (FP32, rows x 14 x S):
+// one per target block of the largest cluster, or 0 where the two separate
+// sweeps run instead (PN_ADJ_SEPARATE set when the context was created, or
+// rows above kAdjRowBytes).  Independent of the precision, which
+// pn_set_params may change after the scratch exists.
+constexpr size_t kAdjRowBytes = size_t(4) << 30;
+
+static int64_t adj_rows(const pn_ctx *c)
+{
+    const int64_t rows = c->max_ns_pad / (2 * kMixThreads);
+    if (c->adj_separate || (size_t)rows * kAdjSrc * c->S * sizeof(float) > kAdjRowBytes)
+        return 0;
+    return rows;
+}
+
 // Adjoint scratch (doubles): sbar 16 S, kbar 6 S, target partials js 6 S,
 // source partials js 14 S, staged targets of the packed sweep 26 S (13
 // float4 per slot), block cotangents (S/32) 11, cluster cotangents nclu 11,
-// hole blocks (S/32) 4.
+// hole blocks (S/32) 4, then the merged sweep's FP32 source rows.
 size_t adjoint_buffer_doubles(const pn_ctx *c)
 {
     const int64_t S = c->S, js = jerk_part_splits(c);
     return (size_t)((16 + 6) * S + js * (6 + kAdjSrc) * S + kAdjTVals * 2 * S +
-                    (S / kAdjStarSlots) * (kAdjGlob + 4) + (int64_t)c->nclu * kAdjGlob);
+                    (S / kAdjStarSlots) * (kAdjGlob + 4) + (int64_t)c->nclu * kAdjGlob +
+                    (adj_rows(c) * kAdjSrc * S + 1) / 2);
 }
 
 cudaError_t launch_accel_vjp(pn_ctx *c, const double *x, const double *v, const double *m,
@@ -1764,7 +1990,7 @@ cudaError_t launch_accel_vjp(pn_ctx *c, const double *x, const double *v, const 
     k_adj_star<<<(unsigned)(S / kAdjStarSlots), kAdjStarSlots, 0, c->stream>>>(S, c->d_clu, bc, x, v, m, fwd, jsf,
                                                                jglob, abar, sbar, kbar, kblk);
     k_adj_globals<<<c->nclu, kGlueThreads, 0, c->stream>>>(c->d_clu, kblk, gbar);
-    int jsr = js;
+    int jsr = js, jss = js;
     if (mixed) {
         // packed sweeps: sources from the staged records of the forward pass
         const float4 *srec = srec_saved ? srec_saved : c->mrec + 5 * S;
@@ -1778,14 +2004,29 @@ cudaError_t launch_accel_vjp(pn_ctx *c, const double *x, const double *v, const 
                                  cudaFuncAttributePreferredSharedMemoryCarveout, 100);
             cudaFuncSetAttribute(k_adj_sources_packed,
                                  cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+            cudaFuncSetAttribute(k_adj_pairs_packed,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout, 100);
             carveout = true;
         }
         const dim3 pgrid((unsigned)(S / (2 * kMixThreads)), (unsigned)jsr);
-        k_adj_tstage<<<(unsigned)nglue, kGlueThreads, 0, c->stream>>>(S, frec, sbar, tst);
-        k_adj_targets_packed<<<pgrid, kMixThreads, 0, c->stream>>>(srec, S, c->d_clu, bc, sbar,
-                                                                  c->flag, tpart);
-        k_adj_sources_packed<<<pgrid, kMixThreads, 0, c->stream>>>(srec, tst, S, c->d_clu, bc,
-                                                                  c->flag, spart);
+        if (adj_rows(c) > 0) {
+            // one pass for both sweeps; the source rows summed into split 0
+            float *spf = reinterpret_cast<float *>(hblk + (S / kAdjStarSlots) * 4);
+            k_adj_pairs_packed<<<pgrid, kMixThreads, 0, c->stream>>>(srec, S, c->d_clu, bc, sbar,
+                                                                    c->flag, tpart, spf);
+            k_adj_row_sums<<<(unsigned)(((kAdjSrc + 6) * S + kGlueThreads - 1) / kGlueThreads),
+                             kGlueThreads, 0, c->stream>>>(S, c->d_clu, bc, spf, spart, tpart,
+                                                           jsr);
+            jss = 1;
+            jsr = 1;
+        } else {
+            k_adj_tstage<<<(unsigned)nglue, kGlueThreads, 0, c->stream>>>(S, frec, sbar, tst);
+            k_adj_targets_packed<<<pgrid, kMixThreads, 0, c->stream>>>(srec, S, c->d_clu, bc,
+                                                                      sbar, c->flag, tpart);
+            k_adj_sources_packed<<<pgrid, kMixThreads, 0, c->stream>>>(srec, tst, S, c->d_clu, bc,
+                                                                      c->flag, spart);
+            jss = jsr;
+        }
         c->launches += 1;
     } else {
         k_adj_targets<<<grid, kJThreads, 0, c->stream>>>(rec, S, c->d_clu, bc, sbar, tpart);
@@ -1794,9 +2035,12 @@ cudaError_t launch_accel_vjp(pn_ctx *c, const double *x, const double *v, const 
     if (jsr > 1) {              // the sweeps' split partials, summed into split 0
         k_split_sum<<<(unsigned)((6 * S + kGlueThreads - 1) / kGlueThreads), kGlueThreads, 0,
                       c->stream>>>(S, 6, jsr, tpart);
+        c->launches += 1;
+    }
+    if (jss > 1) {
         k_split_sum<<<(unsigned)((kAdjSrc * S + kGlueThreads - 1) / kGlueThreads), kGlueThreads,
-                      0, c->stream>>>(S, kAdjSrc, jsr, spart);
-        c->launches += 2;
+                      0, c->stream>>>(S, kAdjSrc, jss, spart);
+        c->launches += 1;
     }
     k_adj_records<<<(unsigned)(S / kAdjStarSlots), kAdjStarSlots, 0, c->stream>>>(
         S, c->d_clu, bc, x, v, m, abar, kbar, tpart, 1, spart, 1, gbar, xbar, vbar, hblk);

@@ -173,6 +173,7 @@ struct pn_ctx {
     cudaStream_t side;
     cudaEvent_t ev_fork, ev_join;
     cudaStream_t adj_stream;   // the adjoint's segment recomputations (created on first use)
+    int adj_separate;          // PN_ADJ_SEPARATE: the adjoint's two pair sweeps, not the merged one
 
     // CUDA graph of pn_step_graph: captured once per (arrays, dt, nsteps)
     cudaStream_t cap_stream;

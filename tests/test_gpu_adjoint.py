@@ -90,19 +90,24 @@ def test_accel_vjp_larger_cluster_random_projections(orc):
         assert abs(lhs - rhs) <= 1e-9 * abs(rhs), (lhs, rhs)
 
 
-def test_accel_vjp_mixed_context(orc):
+@pytest.mark.parametrize("sweeps", ["merged", "separate"])
+def test_accel_vjp_mixed_context(orc, sweeps, monkeypatch):
     """Mixed contexts run the reverse pair sweeps in single precision (hi/lo
-    positions): the VJP stays within 1e-5 of the oracle's exact one along
-    random directions, and per body within median 1e-6 / max 1e-4 of the
-    oracle's exact cotangents (20 sampled bodies, the hole and a star near
-    it among them, all six components, each from the oracle's complex-step
-    derivative along that unit direction)."""
+    positions), both in one pass over the pairs (merged) or, with
+    PN_ADJ_SEPARATE, one pass per side: the VJP stays within 1e-5 of the
+    oracle's exact one along random directions, and per body within median
+    1e-6 / max 1e-4 of the oracle's exact cotangents (20 sampled bodies, the
+    hole and a star near it among them, all six components, each from the
+    oracle's complex-step derivative along that unit direction)."""
     x, v, m = make_cluster(700, 0.1, 73)
     x[3] = x[0] + np.array([0.004, 0.001, 0.0])        # a star close to the hole
     c, eps = 15.0, 1e-3
     rng = np.random.default_rng(19)
     abar = rng.normal(size=x.shape)
+    if sweeps == "separate":
+        monkeypatch.setenv("PN_ADJ_SEPARATE", "1")
     ctx = pn.pn_init(700, c=c, eps=eps, precision="mixed", device=0)
+    monkeypatch.delenv("PN_ADJ_SEPARATE", raising=False)
     XB, VB = torch.empty((700, 3), dtype=torch.float64, device=DEV), torch.empty(
         (700, 3), dtype=torch.float64, device=DEV)
     scal = pn.pn_accel_vjp(ctx, dev(x), dev(v), dev(m), dev(abar), XB, VB)
@@ -134,6 +139,34 @@ def test_accel_vjp_mixed_context(orc):
     cw = np.sum(abar * orc.accel_jvp(x, v, m, z, z, dinv_c2=1.0, c=c, eps=eps))
     assert abs(scal[0, 0] - Mw) <= 1e-6 * abs(Mw), (scal[0, 0], Mw)
     assert abs(scal[0, 1] - cw) <= 1e-6 * abs(cw), (scal[0, 1], cw)
+
+
+def test_merged_and_separate_sweeps_agree(monkeypatch):
+    """The merged reverse sweep and the two separate ones add the same FP32
+    pair terms in different orders: on a 3000-body cluster (12 target
+    blocks, several source splits, a star near the hole) their VJPs agree
+    per body to median 1e-6 and max 5e-5 of the cotangent's norm (FP32 sums
+    of thousands of terms, some cancelling), and M, 1/c^2 within 1e-6."""
+    n = 3000
+    x, v, m = make_cluster(n, 0.1, 5)
+    x[7] = x[0] + np.array([0.003, -0.002, 0.001])
+    abar = np.random.default_rng(4).normal(size=x.shape)
+    out = {}
+    for sweeps in ("merged", "separate"):
+        if sweeps == "separate":
+            monkeypatch.setenv("PN_ADJ_SEPARATE", "1")
+        ctx = pn.pn_init(n, c=15.0, eps=1e-3, precision="mixed", device=0)
+        monkeypatch.delenv("PN_ADJ_SEPARATE", raising=False)
+        XB = torch.empty((n, 3), dtype=torch.float64, device=DEV)
+        VB = torch.empty((n, 3), dtype=torch.float64, device=DEV)
+        scal = pn.pn_accel_vjp(ctx, dev(x), dev(v), dev(m), dev(abar), XB, VB)
+        ctx.close()
+        out[sweeps] = (XB.cpu().numpy(), VB.cpu().numpy(), scal)
+    (xa, va, sa), (xs, vs, ss) = out["merged"], out["separate"]
+    for a, b in ((xa, xs), (va[1:], vs[1:])):
+        err = np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
+        assert np.median(err) <= 1e-6 and err.max() <= 5e-5, (np.median(err), err.max())
+    assert np.all(np.abs(sa - ss) <= 1e-6 * np.abs(ss)), (sa, ss)
 
 
 def oracle_step_grad(orc, x, v, m, dt, nst, xbT, vbT, c, eps, vel_mode=0):
