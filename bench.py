@@ -54,6 +54,8 @@ FLOPS_PACKED_FAR = 67  # the same body on far units of the spatial order (x_ij f
                        # parts: 6 adds fewer)
 OPS_PACKED_FAR = 40
 FLOPS_JERK = 213   # hand count of the dual-number pair body of the jerk
+FLOPS_ENERGY = 44  # hand count of the FP64 energy pair body (Eq. 7-8 sums; FMA = 2, the
+                   # rsqrt seed 1, its Newton step 5)
                    # (dual add 2, dual multiply 4, scalar x dual 2, rsqrt + its derivative 6)
 FP32_LANES_PER_SM = 128
 
@@ -77,6 +79,7 @@ def parse():
     ap.add_argument("--steps-16k", type=int, default=1000)
     ap.add_argument("--batched-steps", type=int, default=500)
     ap.add_argument("--no-jerk", action="store_true")
+    ap.add_argument("--no-energy", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--adjoint-steps", type=int, default=1000)
     ap.add_argument("--no-adjoint-fd", action="store_true",
@@ -524,6 +527,12 @@ def run_native(args, w):
         except Exception as e:  # reported, not required
             line["jerk"] = {"error": str(e)[:300]}
 
+    if not args.no_energy and world == 1:
+        try:
+            line["energy"] = run_energy(local, stream)
+        except Exception as e:  # reported, not required
+            line["energy"] = {"error": str(e)[:300]}
+
     if not args.no_adjoint and world == 1:
         try:
             line["adjoint"] = run_adjoint(local, stream, args.adjoint_steps,
@@ -719,6 +728,47 @@ def run_jerk(local, stream, warmup, reps=5):
                          "flops_per_pair_with_A": FLOPS_JERK + FLOPS_PACKED,
                          "note_with_A": "the call's whole work: the A evaluation it returns "
                                         "(packed pair body) and the dual jerk body"}}
+
+
+def run_energy(local, stream, reps=5):
+    """Eq. 7-8 (pn_energy, FP64 pair sums whatever the context's precision)
+    on the 16k Plummer workload: whole calls timed with CUDA events (the
+    prologue, the FP64 pair kernel, the per-star and per-cluster sums and
+    the 8-double copy back), against the measured FP64 FMA rate."""
+    import torch
+    from paper_1801_07986_b300 import pn
+    from paper_1801_07986_b300.inputs import WORKLOADS
+    w = WORKLOADS["plummer16k"]
+    x, v, m = w.state()
+    dev = torch.device(f"cuda:{local}")
+    X, V, M = (torch.tensor(a, device=dev) for a in (x, v, m))
+    ctx = pn.pn_init(w.n, G=w.G, c=w.c, eps=w.eps, precision="mixed", device=local,
+                     stream=stream)
+    first = pn.pn_energy(ctx, X, V, M)
+    pn.pn_sync(ctx)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        pn.pn_energy(ctx, X, V, M)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    ctx.close()
+    pairs = float(w.n - 1) * (w.n - 2)
+    meas = pn.pn_measure_peaks(local, stream)
+    achieved = FLOPS_ENERGY * pairs / (ms * 1e-3) / 1e12
+    return {"workload": "plummer16k", "n_bodies": w.n, "ms_per_call": ms,
+            "value": float(w.n) * (w.n - 1) / (ms * 1e-3), "unit": "interactions/s",
+            "what": "pn_energy (Eq. 7 energy, Eq. 8 momentum), FP64 pair sums, whole call",
+            "E": first["E"],
+            "roofline": {"bound": "alu", "pipe": "fp64", "achieved": achieved,
+                         "peak": meas["fp64_fma_tflops"], "unit": "TFLOP/s",
+                         "frac": achieved / meas["fp64_fma_tflops"],
+                         "peak_basis": "FP64 FMA-chain microbenchmark on this device "
+                                       "(pn_measure_peaks); 1.25 TFLOP/s nominal",
+                         "flops_per_pair": FLOPS_ENERGY,
+                         "note": "whole call timed; the pair kernel's flops only"}}
 
 
 def run_adjoint(local, stream, nsteps, fd=True):

@@ -639,8 +639,9 @@ static pn_status init_common(pn_ctx **out, int nclu, const int64_t *off, const p
     const int64_t part_f64 = (int64_t)c->f64.jsplit * (pn::kP1Vals + pn::kP2Vals) * S;
     if (part_f64 > part)
         part = part_f64;
-    if ((int64_t)pn::kEVals * S > part)
-        part = (int64_t)pn::kEVals * S;
+    const int64_t e_js = pn::energy_splits(S, c->sm_count, c->max_ns_pad);
+    if ((int64_t)pn::kEVals * e_js * S > part)
+        part = (int64_t)pn::kEVals * e_js * S;
     part += (int64_t)pn::kNearVals * S;   // near-pass partials after both passes
     // fused layout: pass sums, near sums, then the largest segment buffer
     const int64_t part_fused = (int64_t)(pn::kP1Vals + pn::kP2Vals + pn::kNearVals) * S +

@@ -45,6 +45,7 @@ constexpr int kGatherThreads = 64; // stream-K gather blocks, likewise
 constexpr int kP1Vals = 6;         // N (3), U, Z, Wr
 constexpr int kP2Vals = 10;        // V' (3), Hs (1), Hv (3), E (3)
 constexpr int kEVals = 8;          // pot, Smv (3), Snn, Spx (3)
+constexpr int kEnergySplitsMax = 32;  // source splits of the energy pair kernel, at most
 constexpr int kFusedVals = kP1Vals + kP2Vals;
 constexpr int kPackSums = kFusedVals - 1;   // packed fused kernel: the pass-1 sums without Wr
 // Near-source pass: sources per tile and values per target.
@@ -229,6 +230,7 @@ cudaError_t launch_epilogue(pn_ctx *c, const double *x, const double *vel, const
                             double *a, double *v, double half_dt, unsigned long long step,
                             double dt_next = 0.0);
 cudaError_t launch_energy(pn_ctx *c, const double *x, const double *v, const double *m);
+int64_t energy_splits(int64_t S, int sm_count, int64_t max_ns_pad);
 cudaError_t launch_watch(pn_ctx *c);   // after launch_energy: compare with the references
 cudaError_t launch_energy_on(cudaStream_t st, int64_t S, const Clu *clu, const double *x,
                              const double *v, const double *m, double4_32a *drec, double *part,

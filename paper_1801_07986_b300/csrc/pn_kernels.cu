@@ -1358,9 +1358,21 @@ k_pass_f64(const double4_32a *__restrict__ rec, int64_t S, const Clu *__restrict
     }
 }
 
+// 1/sqrt(s2) in double for the energy sums: the single-precision seed
+// (rsqrtf, relative error <= 2^-22) refined by one Newton step, whose result
+// is low by at most 1.5 (2^-22)^2 ~ 9e-14 relative -- far below the 1e-10
+// that energy differences need (each pair term enters Eq. 7-8 once).
+__device__ __forceinline__ double rsqrt_f64_energy(double s2)
+{
+    const double y = (double)rsqrtf((float)s2);
+    return y * fma(-0.5 * s2, y * y, 1.5);
+}
+
 // Energy pair sums, double precision, records A = (d, m), B = (v, 0):
 //   pot += m_j/r, Smv += m_j/r v_j, Snn += m_j/r (n.v_i)(n.v_j),
-//   Spx += m_j/r (n.v_i)/r x_ij,   n = x_ij / r.
+//   Spx += m_j/r (n.v_i)/r x_ij,   n = x_ij / r,
+// the last two through the unnormalised projections u_i = x.v_i, u_j = x.v_j:
+// m_j/r (n.v_i)(n.v_j) = (m_j/r^3 u_i) u_j, m_j/r (n.v_i)/r = m_j/r^3 u_i.
 template <bool MASK>
 __device__ __forceinline__ void energy_tile(const double4_32a (*__restrict__ sh)[kF64Tile],
                                             int64_t j0, const double (&di)[3],
@@ -1379,23 +1391,25 @@ __device__ __forceinline__ void energy_tile(const double4_32a (*__restrict__ sh)
             s2 = self ? 1.0 : s2;
             mj = self ? 0.0 : mj;
         }
-        const double is = rsqrt_f64(s2);
+        const double is = rsqrt_f64_energy(s2);
         const double ms = mj * is;
-        const double nvi = fma(dx, vi[0], fma(dy, vi[1], dz * vi[2])) * is;
-        const double nvj = fma(dx, B.x, fma(dy, B.y, dz * B.z)) * is;
+        const double ui = fma(dx, vi[0], fma(dy, vi[1], dz * vi[2]));
+        const double uj = fma(dx, B.x, fma(dy, B.y, dz * B.z));
         acc[0] += ms;
         acc[1] = fma(ms, B.x, acc[1]);
         acc[2] = fma(ms, B.y, acc[2]);
         acc[3] = fma(ms, B.z, acc[3]);
-        acc[4] = fma(ms * nvi, nvj, acc[4]);
-        const double px = ms * nvi * is;
+        const double px = ms * (is * is) * ui;
+        acc[4] = fma(px, uj, acc[4]);
         acc[5] = fma(px, dx, acc[5]);
         acc[6] = fma(px, dy, acc[6]);
         acc[7] = fma(px, dz, acc[7]);
     }
 }
 
-// One block per 128 target slots, sweeping every tile of its own cluster.
+// Grid (blocks of 128 target slots, source splits): split s of a block in
+// cluster k sweeps the cluster's tiles [s T / js, (s+1) T / js) (T tiles)
+// into part[s][value][slot]; the splits fill every SM at small N.
 __global__ void __launch_bounds__(kF64Threads)
 k_energy_pairs(const double4_32a *__restrict__ rec, int64_t S, const Clu *__restrict__ clu,
                const int *__restrict__ blk_clu, double *__restrict__ part)
@@ -1404,7 +1418,8 @@ k_energy_pairs(const double4_32a *__restrict__ rec, int64_t S, const Clu *__rest
     const int64_t t0 = (int64_t)blockIdx.x * kF64Threads;
     const Clu C = clu[cluster_of_block(blk_clu, t0 / kGlueThreads)];
     const double eps2 = C.eps2;
-    const int ntiles = (int)(C.ns_pad / kF64Tile);
+    const int64_t ntiles = C.ns_pad / kF64Tile, js = gridDim.y, sp = blockIdx.y;
+    const int64_t tb = sp * ntiles / js, te = (sp + 1) * ntiles / js;
     const int64_t ti = t0 + threadIdx.x;
     const double4_32a A = rec[ti];
     const double4_32a B = rec[S + ti];
@@ -1414,8 +1429,8 @@ k_energy_pairs(const double4_32a *__restrict__ rec, int64_t S, const Clu *__rest
 #pragma unroll
     for (int k = 0; k < kEVals; ++k)
         acc[k] = 0.0;
-    for (int tile = 0; tile < ntiles; ++tile) {
-        const int64_t j0 = C.slot0 + (int64_t)tile * kF64Tile;
+    for (int64_t tile = tb; tile < te; ++tile) {
+        const int64_t j0 = C.slot0 + tile * kF64Tile;
         __syncthreads();
         for (int q = threadIdx.x; q < kF64Tile; q += kF64Threads) {
             const int64_t jq = PN_IDX(j0 + q, S, 14);
@@ -1431,7 +1446,7 @@ k_energy_pairs(const double4_32a *__restrict__ rec, int64_t S, const Clu *__rest
     }
 #pragma unroll
     for (int k = 0; k < kEVals; ++k)
-        part[(int64_t)k * S + ti] = acc[k];
+        part[(sp * kEVals + k) * S + ti] = acc[k];
 }
 
 // ------------------------------------------------------- near sources --
@@ -1795,7 +1810,7 @@ k_epilogue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_c
 __global__ void __launch_bounds__(kGlueThreads)
 k_energy_epilogue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_clu,
                   const double *__restrict__ x, const double *__restrict__ vel,
-                  const double *__restrict__ m, const double *__restrict__ pe,
+                  const double *__restrict__ m, const double *__restrict__ pe, int js,
                   double *__restrict__ blk)
 {
     __shared__ double sh[kEBlockVals][kGlueThreads];
@@ -1815,9 +1830,12 @@ k_energy_epilogue(int64_t S, const Clu *__restrict__ clu, const int *__restrict_
         const double iR = 1.0 / R;
         const double vi[3] = {vel[3 * i], vel[3 * i + 1], vel[3 * i + 2]};
         const double v1[3] = {vel[3 * hb], vel[3 * hb + 1], vel[3 * hb + 2]};
-        double s[kEVals];
+        double s[kEVals];          // the pair sums, splits added in order
         for (int k = 0; k < kEVals; ++k)
             s[k] = pe[(int64_t)k * S + t];
+        for (int q = 1; q < js; ++q)
+            for (int k = 0; k < kEVals; ++k)
+                s[k] += pe[((int64_t)q * kEVals + k) * S + t];
         const double vi2 = vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2];
         const double v12 = v1[0] * v1[0] + v1[1] * v1[1] + v1[2] * v1[2];
         const double v1vi = v1[0] * vi[0] + v1[1] * vi[1] + v1[2] * vi[2];
@@ -2409,18 +2427,32 @@ cudaError_t launch_epilogue(pn_ctx *c, const double *x, const double *vel, const
     return cudaGetLastError();
 }
 
+// Source splits of the energy pair kernel: about 24 blocks per SM over the
+// 128-slot target blocks (the FP64 pipe is full with a few; the rest keep
+// the last wave short), at most one per tile of the largest cluster and at
+// most kEnergySplitsMax.
+int64_t energy_splits(int64_t S, int sm_count, int64_t max_ns_pad)
+{
+    const int64_t nb = S / kF64Threads, tiles = max_ns_pad / kF64Tile;
+    int64_t js = (24 * (int64_t)sm_count + nb - 1) / nb;
+    js = js > tiles ? tiles : js;
+    js = js > kEnergySplitsMax ? kEnergySplitsMax : js;
+    return js < 1 ? 1 : js;
+}
+
 cudaError_t launch_energy(pn_ctx *c, const double *x, const double *v, const double *m)
 {
     cudaError_t e = launch_prologue(c, x, v, m, true);
     if (e != cudaSuccess)
         return e;
-    k_energy_pairs<<<(unsigned)(c->S / kF64Threads), kF64Threads, 0, c->stream>>>(
-        c->drec, c->S, c->d_clu, blk_table(c), c->part);
+    const int js = (int)energy_splits(c->S, c->sm_count, c->max_ns_pad);
+    k_energy_pairs<<<dim3((unsigned)(c->S / kF64Threads), (unsigned)js), kF64Threads, 0,
+                     c->stream>>>(c->drec, c->S, c->d_clu, blk_table(c), c->part);
     c->launches += 1;
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
     k_energy_epilogue<<<(unsigned)(c->S / kGlueThreads), kGlueThreads, 0, c->stream>>>(
-        c->S, c->d_clu, blk_table(c), x, v, m, c->part, c->blk);
+        c->S, c->d_clu, blk_table(c), x, v, m, c->part, js, c->blk);
     c->launches += 1;
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
@@ -2455,7 +2487,7 @@ cudaError_t launch_energy_on(cudaStream_t st, int64_t S, const Clu *clu, const d
         return e;
     // one kGlueThreads-slot block per row of blk (S / kGlueThreads rows)
     k_energy_epilogue<<<(unsigned)(S / kGlueThreads), kGlueThreads, 0, st>>>(S, clu, nullptr, x, v,
-                                                                            m, part, blk);
+                                                                            m, part, 1, blk);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
     k_energy_final<<<1, kGlueThreads, 0, st>>>(clu, blk, v, m, out);
