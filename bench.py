@@ -317,9 +317,10 @@ def kernel_source_hash(tag: str | None = None):
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel_tag: str):
+def profiled_traffic(kernel_tag: str, inst: str = ""):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
+    the current kernel source and on the instantiation `inst` that runs
+    (else None)."""
     d = os.path.join(ROOT, "profiles")
     if not os.path.isdir(d):
         return None
@@ -328,7 +329,8 @@ def profiled_traffic(kernel_tag: str):
         if not f.endswith(".md"):
             continue
         txt = open(os.path.join(d, f)).read()
-        m1 = re.search(rf"traffic_bytes_per_launch\[{kernel_tag}\]:\s*([0-9.eE+]+)", txt)
+        m1 = re.search(rf"traffic_bytes_per_launch\[{re.escape(kernel_tag + inst)}\]:\s*([0-9.eE+]+)",
+                       txt)
         m2 = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
         if m1 and m2 and m2.group(1) == src:
             return float(m1.group(1))
@@ -391,6 +393,9 @@ def run_native(args, w):
     inter = float(w.n) * (w.n - 1) * steps * world
     value = inter / (ms * 1e-3)
     launch = pn.pn_get_launch(ctx)
+    variant = pn.pn_get_variant(ctx)
+    if variant["targets_per_thread"]:
+        launch.update({k: variant[k] for k in ("unroll", "form", "stages")})
 
     # roofline of the dominant pair kernel (plain FP32 ALU bound)
     peaks = measured_peaks()
@@ -411,14 +416,23 @@ def run_native(args, w):
     flops = fpp * pairs
     achieved = flops / (per_launch_ms * 1e-3) / 1e12
     clocks = clk.summary()
+    inst = ""
     if fused:
         tag = "fused_packed" if launch.get("packed") else "fused_mixed"
+        # the instantiation the traffic was captured on
+        # (k_fused_packed<NP, UNROLL, FORM, TILE, ST>, NP = targets / 2; the scalar
+        # k_fused_mixed<P, UNROLL>)
+        if launch.get("packed"):
+            inst = "<{},{},{},{},{}>".format(variant["targets_per_thread"] // 2, variant["unroll"],
+                                             variant["form"], variant["tile"], variant["stages"])
+        else:
+            inst = "<{},{}>".format(variant["targets_per_thread"], variant["unroll"])
     elif f64_fused:
         tag = "fused_f64"
     else:
         tag = f"pass{k_dom + 1}_{args.precision}"
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": profiled_traffic(tag), "kernel": tag,
+            "frac": achieved / peak, "traffic": profiled_traffic(tag, inst), "kernel": tag + inst,
             "flops_per_pair": fpp,
             "launch_ms": per_launch_ms,
             "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz "

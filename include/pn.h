@@ -342,6 +342,18 @@ pn_status pn_get_pair_stats(pn_ctx *ctx, int64_t out[2]);
 pn_status pn_get_launch(pn_ctx *ctx, int64_t out[8]);
 
 /*
+ * The fused pair kernel's instantiation for this context (mixed precision,
+ * fused pair kernel): out[0] targets per thread, out[1] source-loop unroll,
+ * out[2] form of the hole term (0 dot-product form, 1 law-of-cosines form,
+ * 2 law-of-cosines form on the spatial order), out[3] sources per tile,
+ * out[4] shared-memory tile buffers (stages; 0 for the scalar kernel),
+ * out[5] 1 if it is the packed FP32x2 kernel.  All zero when the context
+ * does not run the fused kernel (FP64 or PN_PAIR_TWO_PASS).  No device work.
+ * Errors: PN_EINVAL (bad context, NULL out).
+ */
+pn_status pn_get_variant(pn_ctx *ctx, int64_t out[6]);
+
+/*
  * Number of CUDA kernels this context has launched since pn_init (host-side
  * count, no synchronisation).  A pn_step_graph replay adds the kernels of the
  * captured graph; capturing it adds nothing.  Takes a NULL count as

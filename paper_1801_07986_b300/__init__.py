@@ -10,7 +10,7 @@ initial conditions.
 from .pn import (PN_FP64, PN_HERMITE, PN_KDK, PN_MIXED, PN_RK4, PN_PAIR_FUSED, PN_PAIR_TWO_PASS, PN_VHALF, PN_VPRED_END,  # noqa: F401
                  Context, PNError, pn_accel, pn_energy_noalloc, pn_init_batched,
                  pn_step_graph, pn_tune,
-                 pn_accel_vjp, pn_destroy, pn_energy, pn_get_launch, pn_get_timing, pn_jerk,
+                 pn_accel_vjp, pn_destroy, pn_energy, pn_get_launch, pn_get_timing, pn_get_variant, pn_jerk,
                  pn_launch_count, pn_step_vjp, trajectory, pn_init, pn_last_error,
                  pn_set_params, pn_set_stream, pn_set_timing, pn_step, pn_step_host, pn_sync,
                  pn_version)

@@ -508,13 +508,16 @@ static pn_status init_common(pn_ctx **out, int nclu, const int64_t *off, const p
     cudaError_t e = pn::occupancy(&occ_mix, &occ_f64);
     // fused-kernel variant; PN_FUSED_PACKED / PN_FUSED_TARGETS / PN_FUSED_UNROLL /
     // PN_FUSED_WORKERS override the default (tuning sweeps)
-    c->fused_packed = true;  // packed FP32x2 kernel, 4 targets per thread, 2-way unroll:
-    c->fused_P = 4;          // measured fastest on B300 at N = 131072
-    c->fused_unroll = 2;
+    c->fused_packed = true;  // packed FP32x2 kernel, 4 targets per thread, no unroll:
+    c->fused_P = 4;          // measured fastest on B300 at N = 131072 (22.11 ms
+    c->fused_unroll = 1;     // against 22.50 with the 2-way unroll)
     // small systems: 2 targets per thread (4 resident blocks per SM, shorter
-    // target blocks), measured 8 % faster per step at N = 8192 and 1 % at 16384
-    if (c->max_ns_pad <= 16384)
+    // target blocks) with the 2-way unroll, measured 8 % faster per step at
+    // N = 8192 and 1 % at 16384 (the unroll: 455 against 461 us at 16384)
+    if (c->max_ns_pad <= 16384) {
         c->fused_P = 2;
+        c->fused_unroll = 2;
+    }
     c->fused_tile = pn::kPackTile;
     c->fused_stages = pn::kPackStages;
     c->workers_max = pn::kPackWorkersMax;
@@ -1579,6 +1582,26 @@ pn_status pn_get_launch(pn_ctx *c, int64_t out[8])
     out[5] = fused ? c->fused_occ : s.occupancy;
     out[6] = c->sm_count;
     out[7] = fused && c->fused_packed ? 1 : 0;
+    return ok();
+}
+
+pn_status pn_get_variant(pn_ctx *c, int64_t out[6])
+{
+    if (check_ctx(c) != PN_OK)
+        return PN_EINVAL;
+    if (!out)
+        return fail(PN_EINVAL, "pn_get_variant: NULL output");
+    for (int k = 0; k < 6; ++k)
+        out[k] = 0;
+    if (pn::use_fused(c)) {
+        const pn::FusedVariant v = pn::fused_variant(c);
+        out[0] = v.P;
+        out[1] = v.unroll;
+        out[2] = v.packed ? (pn::packed_loc(c) ? (c->spatial ? 2 : 1) : 0) : 0;
+        out[3] = pn::fused_tile_size(v);
+        out[4] = v.packed ? v.stages : 0;
+        out[5] = v.packed;
+    }
     return ok();
 }
 

@@ -105,6 +105,7 @@ def _load():
                 "pn_set_timing": [P, I],
                 "pn_get_timing": [P, P, P],
                 "pn_get_launch": [P, P],
+                "pn_get_variant": [P, P],
                 "pn_get_pair_stats": [P, P],
                 "pn_launch_count": [P, P],
                 "pn_energy_noalloc": [I, P, I64, D, D, D, P, P, P, P],
@@ -551,6 +552,16 @@ def pn_get_launch(ctx: Context) -> dict:
     _check(_load().pn_get_launch(ctx.handle, out.ctypes.data_as(ctypes.c_void_p)))
     keys = ("threads", "targets_per_thread", "tile", "blocks_i", "jsplit", "occupancy", "sms",
             "packed")
+    return {k: int(v) for k, v in zip(keys, out)}
+
+
+def pn_get_variant(ctx: Context) -> dict:
+    """The fused pair kernel's instantiation: targets per thread, unroll,
+    form (0 dot product, 1 law of cosines, 2 law of cosines on the spatial
+    order), tile, stages, packed (all 0 off the fused kernel)."""
+    out = np.zeros(6, dtype=np.int64)
+    _check(_load().pn_get_variant(ctx.handle, out.ctypes.data_as(ctypes.c_void_p)))
+    keys = ("targets_per_thread", "unroll", "form", "tile", "stages", "packed")
     return {k: int(v) for k, v in zip(keys, out)}
 
 

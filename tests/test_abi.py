@@ -85,7 +85,7 @@ def test_null_arguments(lib):
     assert lib.pn_init(ctypes.byref(ctypes.c_void_p()), 10, None, 0, None) == 1
     for name, nargs in (("pn_accel", 5), ("pn_step", 7), ("pn_energy", 5), ("pn_sync", 1),
                         ("pn_step_host", 7), ("pn_set_timing", 2), ("pn_get_launch", 2),
-                        ("pn_get_pair_stats", 2),
+                        ("pn_get_pair_stats", 2), ("pn_get_variant", 2),
                         ("pn_launch_count", 2), ("pn_jerk", 6), ("pn_accel_vjp", 8),
                         ("pn_step_save", 9), ("pn_step_vjp_saved", 11)):
         fn = getattr(lib, name)
