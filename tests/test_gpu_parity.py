@@ -116,6 +116,9 @@ def test_fused_variants_match_oracle(orc, monkeypatch, packed, targets, unroll):
     assert shape["packed"] == (packed == "1")
     want_p = (2 if targets == "2" else 4) if packed == "1" else int(targets)
     assert shape["targets_per_thread"] == want_p
+    var = pn.pn_get_variant(ctx)
+    assert (var["targets_per_thread"], var["unroll"], var["packed"]) == \
+        (want_p, int(unroll), int(packed == "1"))
     X, V, M = dev(x), dev(v), dev(m)
     A = torch.empty_like(X)
     pn.pn_accel(ctx, X, V, M, A)
@@ -154,6 +157,28 @@ def test_packed_tile_variants_match_oracle(orc, monkeypatch, spatial, tile, stag
     ctx.close()
     err = rel(got, want)
     assert np.median(err) <= MIX_MED and err.max() <= MIX_MAX, (np.median(err), err.max())
+
+
+def test_default_variants():
+    """The default fused-kernel instantiation: 2 targets per thread with the
+    2-way unroll up to 16384 star slots per cluster, 4 targets without the
+    unroll above; the law-of-cosines form, on the spatial order from 2^32
+    slot pairs; nothing off the fused kernel (FP64, two-pass)."""
+    def variant(n, **kw):
+        ctx = pn.pn_init(n, c=15.0, eps=1e-4, device=0, **kw)
+        try:
+            return pn.pn_get_variant(ctx)
+        finally:
+            ctx.close()
+    small = variant(8192, precision="mixed")
+    assert (small["targets_per_thread"], small["unroll"], small["form"], small["tile"],
+            small["stages"], small["packed"]) == (2, 2, 1, 64, 6, 1)
+    mid = variant(20000, precision="mixed")
+    assert (mid["targets_per_thread"], mid["unroll"], mid["form"]) == (4, 1, 1)
+    big = variant(70000, precision="mixed")           # 70144^2 > 2^32 slot pairs
+    assert (big["targets_per_thread"], big["unroll"], big["form"]) == (4, 1, 2)
+    assert not any(variant(3000, precision="fp64").values())
+    assert not any(variant(3000, precision="mixed", pair_kernel="two_pass").values())
 
 
 def test_fp64_fused_equals_two_pass():
