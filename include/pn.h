@@ -201,10 +201,13 @@ pn_status pn_jerk(pn_ctx *ctx, const double *x, const double *v, const double *m
  * (n x 3 each, device) and, on the host, scal[2 k] = abar . dA/dM_k and
  * scal[2 k + 1] = abar . dA/d(1/c_k^2) for the hole mass M_k and c_k of
  * cluster k (dA/dc = -2/c^3 dA/d(1/c^2)).  Reverse mode over the same
- * decomposition as the kernels, in double precision, without the
- * near-source split.  The paper has no counterpart: it is the gradient of
- * its Eq. 1-6.  Allocates its scratch on the first call; waits.  Errors:
- * PN_EINVAL (NULL pointer, aliasing), PN_ENOMEM, PN_ECUDA.
+ * decomposition as the kernels, without the near-source split: in double
+ * precision in PN_FP64 contexts; in PN_MIXED contexts the forward pair sums
+ * and their reverse run in single precision on hi/lo separations, every
+ * per-star and per-cluster term in double.  The paper has no counterpart:
+ * it is the gradient of its Eq. 1-6.  Allocates its scratch on the first
+ * call; waits.  Errors: PN_EINVAL (NULL pointer, aliasing), PN_ENOMEM,
+ * PN_ECUDA.
  */
 pn_status pn_accel_vjp(pn_ctx *ctx, const double *x, const double *v, const double *m,
                        const double *abar, double *xbar, double *vbar, double *scal);
@@ -216,11 +219,16 @@ pn_status pn_accel_vjp(pn_ctx *ctx, const double *x, const double *v, const doub
  * to x0, v0, device, n x 3) and on the host scal[2 k], scal[2 k + 1], the
  * gradient with respect to the hole mass and 1/c^2 of cluster k.  The
  * forward trajectory runs in the context's precision; each step's
- * acceleration is differentiated in double precision (pn_accel_vjp).
- * Checkpointing: the state is stored every `checkpoint` steps (0: the
- * integer ceiling of sqrt(nsteps)) and each segment is recomputed once on
- * the way back, so memory is (checkpoint + nsteps/checkpoint) x 9n doubles
- * and the forward steps run twice.  Allocates and frees its scratch; waits.
+ * acceleration is differentiated as pn_accel_vjp does.  Checkpointing: the
+ * state is stored every `checkpoint` steps (0: the integer ceiling of
+ * sqrt(nsteps)) and each segment is recomputed once on the way back, so
+ * memory is (checkpoint + nsteps/checkpoint) x 9n doubles and the forward
+ * steps run twice.  In PN_MIXED contexts the recomputation of a segment
+ * keeps each step's forward pair sums and staged records for its reverse
+ * (34 doubles per star slot per step) and runs on a second, internal
+ * stream while the previous segment is reversed, so those buffers and the
+ * segment's states are held twice; events order the two streams.
+ * Allocates and frees its scratch; waits.
  * Errors: PN_EINVAL, PN_EUNSUPPORTED (integrator other than PN_KDK),
  * PN_ENOMEM, PN_ECUDA, PN_ENONFINITE.
  */
