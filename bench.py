@@ -56,6 +56,8 @@ OPS_PACKED_FAR = 40
 FLOPS_JERK = 213   # hand count of the dual-number pair body of the jerk
 FLOPS_ENERGY = 44  # hand count of the FP64 energy pair body (Eq. 7-8 sums; FMA = 2, the
                    # rsqrt seed 1, its Newton step 5)
+OPS_ENERGY_DS = 355  # FP32-pipe operations per pair of the double-single energy body (mixed
+                     # contexts; ncu's FMA-pipe instruction count gives the same)
                    # (dual add 2, dual multiply 4, scalar x dual 2, rsqrt + its derivative 6)
 FP32_LANES_PER_SM = 128
 
@@ -745,10 +747,12 @@ def run_jerk(local, stream, warmup, reps=5):
 
 
 def run_energy(local, stream, reps=5):
-    """Eq. 7-8 (pn_energy, FP64 pair sums whatever the context's precision)
-    on the 16k Plummer workload: whole calls timed with CUDA events (the
-    prologue, the FP64 pair kernel, the per-star and per-cluster sums and
-    the 8-double copy back), against the measured FP64 FMA rate."""
+    """Eq. 7-8 (pn_energy) on the 16k Plummer workload: whole calls timed
+    with CUDA events (the prologue, the pair kernel, the per-star and
+    per-cluster sums and the 8-double copy back).  A mixed context takes the
+    pair sums in double-single arithmetic on the FP32 pipe (roofline: its
+    lane-operation rate); beside it an FP64 context's FP64 pair sums
+    (roofline: the measured FP64 FMA rate)."""
     import torch
     from paper_1801_07986_b300 import pn
     from paper_1801_07986_b300.inputs import WORKLOADS
@@ -756,33 +760,50 @@ def run_energy(local, stream, reps=5):
     x, v, m = w.state()
     dev = torch.device(f"cuda:{local}")
     X, V, M = (torch.tensor(a, device=dev) for a in (x, v, m))
-    ctx = pn.pn_init(w.n, G=w.G, c=w.c, eps=w.eps, precision="mixed", device=local,
-                     stream=stream)
-    first = pn.pn_energy(ctx, X, V, M)
-    pn.pn_sync(ctx)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        pn.pn_energy(ctx, X, V, M)
-    e1.record(stream)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1) / reps
-    ctx.close()
+
+    def timed(precision):
+        ctx = pn.pn_init(w.n, G=w.G, c=w.c, eps=w.eps, precision=precision, device=local,
+                         stream=stream)
+        first = pn.pn_energy(ctx, X, V, M)
+        pn.pn_sync(ctx)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            pn.pn_energy(ctx, X, V, M)
+        e1.record(stream)
+        e1.synchronize()
+        ctx.close()
+        return e0.elapsed_time(e1) / reps, first["E"]
+
+    ms, E = timed("mixed")
+    ms64, E64 = timed("fp64")
     pairs = float(w.n - 1) * (w.n - 2)
     meas = pn.pn_measure_peaks(local, stream)
-    achieved = FLOPS_ENERGY * pairs / (ms * 1e-3) / 1e12
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    lane_peak = meas["sms"] * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12      # Tops/s
+    achieved = OPS_ENERGY_DS * pairs / (ms * 1e-3) / 1e12
+    achieved64 = FLOPS_ENERGY * pairs / (ms64 * 1e-3) / 1e12
     return {"workload": "plummer16k", "n_bodies": w.n, "ms_per_call": ms,
             "value": float(w.n) * (w.n - 1) / (ms * 1e-3), "unit": "interactions/s",
-            "what": "pn_energy (Eq. 7 energy, Eq. 8 momentum), FP64 pair sums, whole call",
-            "E": first["E"],
-            "roofline": {"bound": "alu", "pipe": "fp64", "achieved": achieved,
-                         "peak": meas["fp64_fma_tflops"], "unit": "TFLOP/s",
-                         "frac": achieved / meas["fp64_fma_tflops"],
-                         "peak_basis": "FP64 FMA-chain microbenchmark on this device "
-                                       "(pn_measure_peaks); 1.25 TFLOP/s nominal",
-                         "flops_per_pair": FLOPS_ENERGY,
-                         "note": "whole call timed; the pair kernel's flops only"}}
+            "what": "pn_energy (Eq. 7 energy, Eq. 8 momentum) in a mixed context: "
+                    "double-single pair sums on the FP32 pipe, whole call",
+            "E": E, "E_rel_vs_fp64_context": abs(E - E64) / abs(E64),
+            "roofline": {"bound": "alu", "pipe": "fp32", "achieved": achieved,
+                         "peak": lane_peak, "unit": "Tops/s", "frac": achieved / lane_peak,
+                         "peak_basis": f"{meas['sms']} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                                       f"{sm_max:.0f} MHz (operations, an FMA counted once)",
+                         "ops_per_pair": OPS_ENERGY_DS,
+                         "note": "whole call timed; the pair kernel's operations only"},
+            "fp64_context": {"ms_per_call": ms64,
+                             "value": float(w.n) * (w.n - 1) / (ms64 * 1e-3),
+                             "roofline": {"bound": "alu", "pipe": "fp64", "achieved": achieved64,
+                                          "peak": meas["fp64_fma_tflops"], "unit": "TFLOP/s",
+                                          "frac": achieved64 / meas["fp64_fma_tflops"],
+                                          "peak_basis": "FP64 FMA-chain microbenchmark on this "
+                                                        "device (pn_measure_peaks)",
+                                          "flops_per_pair": FLOPS_ENERGY}}}
 
 
 def run_adjoint(local, stream, nsteps, fd=True):

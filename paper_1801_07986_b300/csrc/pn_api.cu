@@ -642,9 +642,11 @@ static pn_status init_common(pn_ctx **out, int nclu, const int64_t *off, const p
     const int64_t part_f64 = (int64_t)c->f64.jsplit * (pn::kP1Vals + pn::kP2Vals) * S;
     if (part_f64 > part)
         part = part_f64;
+    // energy: the split partials, then (mixed contexts) the double-single
+    // records, 16 floats per slot
     const int64_t e_js = pn::energy_splits(S, c->sm_count, c->max_ns_pad);
-    if ((int64_t)pn::kEVals * e_js * S > part)
-        part = (int64_t)pn::kEVals * e_js * S;
+    if (((int64_t)pn::kEVals * e_js + 8) * S > part)
+        part = ((int64_t)pn::kEVals * e_js + 8) * S;
     part += (int64_t)pn::kNearVals * S;   // near-pass partials after both passes
     // fused layout: pass sums, near sums, then the largest segment buffer
     const int64_t part_fused = (int64_t)(pn::kP1Vals + pn::kP2Vals + pn::kNearVals) * S +

@@ -1449,6 +1449,135 @@ k_energy_pairs(const double4_32a *__restrict__ rec, int64_t S, const Clu *__rest
         part[(sp * kEVals + k) * S + ti] = acc[k];
 }
 
+// ---- energy pair sums in double-single arithmetic (mixed contexts) ----
+//
+// A double-single number is the unevaluated sum hi + lo of two floats
+// (|lo| <= ulp(hi) / 2, about 48 significant bits), computed on the FP32
+// pipe with error-free transformations: Knuth's TwoSum, Dekker's Fast2Sum
+// (|a| >= |b|) and the FMA product error a b - fl(a b).  B300 runs FP64 at
+// 1/64 of the FP32 rate, so the energy's pair sums in this form (about 355
+// FP32 operations per pair) cost a fraction of k_energy_pairs' ~30 FP64
+// instructions; each sum stays within ~1e-13 relative, far below the 1e-10
+// that energy differences need.
+struct DS {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DS ds_fast2sum(float a, float b)
+{
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+
+__device__ __forceinline__ DS ds_add(DS x, DS y)
+{
+    const float s = x.hi + y.hi, bb = s - x.hi;
+    const float e = ((x.hi - (s - bb)) + (y.hi - bb)) + (x.lo + y.lo);
+    return ds_fast2sum(s, e);
+}
+
+__device__ __forceinline__ DS ds_sub(DS x, DS y) { return ds_add(x, DS{-y.hi, -y.lo}); }
+
+__device__ __forceinline__ DS ds_mul(DS x, DS y)
+{
+    const float p = x.hi * y.hi;
+    const float e = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, fmaf(x.hi, y.hi, -p)));
+    return ds_fast2sum(p, e);
+}
+
+__device__ __forceinline__ DS ds_of(double a)
+{
+    const float h = (float)a;
+    return {h, (float)(a - (double)h)};
+}
+
+// Double-single records per slot from the energy prologue's FP64 records
+// (A = (d, m), B = (v, 0)): four float4, (d_x, d_y), (d_z, m), (v_x, v_y),
+// (v_z, 0) as (hi, lo) pairs.
+__global__ void __launch_bounds__(kGlueThreads)
+k_energy_stage_ds(int64_t S, const double4_32a *__restrict__ rec, float4 *__restrict__ drs)
+{
+    const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
+    if (t >= S)
+        return;
+    const double4_32a A = rec[t], B = rec[S + t];
+    const DS dx = ds_of(A.x), dy = ds_of(A.y), dz = ds_of(A.z), m = ds_of(A.w);
+    const DS vx = ds_of(B.x), vy = ds_of(B.y), vz = ds_of(B.z);
+    float4 *o = drs + 4 * t;
+    o[0] = make_float4(dx.hi, dx.lo, dy.hi, dy.lo);
+    o[1] = make_float4(dz.hi, dz.lo, m.hi, m.lo);
+    o[2] = make_float4(vx.hi, vx.lo, vy.hi, vy.lo);
+    o[3] = make_float4(vz.hi, vz.lo, 0.0f, 0.0f);
+}
+
+// The sums of energy_tile (same definitions and output layout, splits as in
+// k_energy_pairs) in double-single arithmetic.  1/r: the single-precision
+// seed y0 refined by one Newton step whose residual 1 - s^2 y0^2 is formed
+// in double-single (relative error about 1.5 (2^-22)^2 ~ 9e-14).
+__global__ void __launch_bounds__(kF64Threads)
+k_energy_pairs_ds(const float4 *__restrict__ drs, int64_t S, const Clu *__restrict__ clu,
+                  const int *__restrict__ blk_clu, double *__restrict__ part)
+{
+    __shared__ float4 sh[kF64Tile][4];
+    const int64_t t0 = (int64_t)blockIdx.x * kF64Threads;
+    const Clu C = clu[cluster_of_block(blk_clu, t0 / kGlueThreads)];
+    const DS eps2 = ds_of(C.eps2);
+    const int64_t ntiles = C.ns_pad / kF64Tile, js = gridDim.y, sp = blockIdx.y;
+    const int64_t tb = sp * ntiles / js, te = (sp + 1) * ntiles / js;
+    const int64_t ti = t0 + threadIdx.x;
+    const float4 T0 = drs[4 * ti], T2 = drs[4 * ti + 2], T3 = drs[4 * ti + 3];
+    const float4 T1 = drs[4 * ti + 1];
+    const DS di[3] = {{T0.x, T0.y}, {T0.z, T0.w}, {T1.x, T1.y}};
+    const DS vi[3] = {{T2.x, T2.y}, {T2.z, T2.w}, {T3.x, T3.y}};
+    DS acc[kEVals];
+#pragma unroll
+    for (int k = 0; k < kEVals; ++k)
+        acc[k] = DS{0.0f, 0.0f};
+    for (int64_t tile = tb; tile < te; ++tile) {
+        const int64_t j0 = C.slot0 + tile * kF64Tile;
+        __syncthreads();
+        for (int q = threadIdx.x; q < 4 * kF64Tile; q += kF64Threads) {
+            const int64_t jq = PN_IDX(j0 + q / 4, S, 14);
+            sh[q / 4][q % 4] = drs[4 * jq + q % 4];
+        }
+        __syncthreads();
+        const bool diag = (j0 < t0 + kF64Threads) && (t0 < j0 + kF64Tile);
+#pragma unroll 1
+        for (int q = 0; q < kF64Tile; ++q) {
+            const float4 R0 = sh[q][0], R1 = sh[q][1], R2 = sh[q][2], R3 = sh[q][3];
+            const DS dx = ds_sub(di[0], DS{R0.x, R0.y}), dy = ds_sub(di[1], DS{R0.z, R0.w}),
+                     dz = ds_sub(di[2], DS{R1.x, R1.y});
+            DS s2 = ds_add(ds_add(ds_mul(dx, dx), ds_mul(dy, dy)), ds_add(ds_mul(dz, dz), eps2));
+            DS mj{R1.z, R1.w};
+            if (diag && j0 + q == ti) {
+                s2 = DS{1.0f, 0.0f};
+                mj = DS{0.0f, 0.0f};
+            }
+            const float y0 = rsqrtf(s2.hi);
+            const float p0 = y0 * y0;
+            const DS u = ds_mul(s2, DS{p0, fmaf(y0, y0, -p0)});
+            const float h = (1.0f - u.hi) - u.lo;            // 1 - s^2 y0^2
+            const DS y = ds_fast2sum(y0, 0.5f * y0 * h);
+            const DS ms = ds_mul(mj, y);
+            const DS vj[3] = {{R2.x, R2.y}, {R2.z, R2.w}, {R3.x, R3.y}};
+            const DS ui = ds_add(ds_add(ds_mul(dx, vi[0]), ds_mul(dy, vi[1])), ds_mul(dz, vi[2]));
+            const DS uj = ds_add(ds_add(ds_mul(dx, vj[0]), ds_mul(dy, vj[1])), ds_mul(dz, vj[2]));
+            acc[0] = ds_add(acc[0], ms);
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                acc[1 + k] = ds_add(acc[1 + k], ds_mul(ms, vj[k]));
+            const DS px = ds_mul(ds_mul(ms, ds_mul(y, y)), ui);   // m/r^3 u_i
+            acc[4] = ds_add(acc[4], ds_mul(px, uj));
+            acc[5] = ds_add(acc[5], ds_mul(px, dx));
+            acc[6] = ds_add(acc[6], ds_mul(px, dy));
+            acc[7] = ds_add(acc[7], ds_mul(px, dz));
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kEVals; ++k)
+        part[(sp * kEVals + k) * S + ti] = (double)acc[k].hi + (double)acc[k].lo;
+}
+
 // ------------------------------------------------------- near sources --
 
 // Eq. 6 lines 2-4 for a near source j (R_j < r_near), pair by pair in a
@@ -2446,9 +2575,19 @@ cudaError_t launch_energy(pn_ctx *c, const double *x, const double *v, const dou
     if (e != cudaSuccess)
         return e;
     const int js = (int)energy_splits(c->S, c->sm_count, c->max_ns_pad);
-    k_energy_pairs<<<dim3((unsigned)(c->S / kF64Threads), (unsigned)js), kF64Threads, 0,
-                     c->stream>>>(c->drec, c->S, c->d_clu, blk_table(c), c->part);
-    c->launches += 1;
+    const dim3 grid((unsigned)(c->S / kF64Threads), (unsigned)js);
+    if (c->p.precision == PN_MIXED) {      // double-single pair sums on the FP32 pipe
+        float4 *drs = reinterpret_cast<float4 *>(c->part + (int64_t)kEVals * js * c->S);
+        k_energy_stage_ds<<<(unsigned)(c->S / kGlueThreads), kGlueThreads, 0, c->stream>>>(
+            c->S, c->drec, drs);
+        k_energy_pairs_ds<<<grid, kF64Threads, 0, c->stream>>>(drs, c->S, c->d_clu,
+                                                              blk_table(c), c->part);
+        c->launches += 2;
+    } else {
+        k_energy_pairs<<<grid, kF64Threads, 0, c->stream>>>(c->drec, c->S, c->d_clu,
+                                                            blk_table(c), c->part);
+        c->launches += 1;
+    }
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
     k_energy_epilogue<<<(unsigned)(c->S / kGlueThreads), kGlueThreads, 0, c->stream>>>(

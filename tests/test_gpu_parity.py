@@ -228,6 +228,39 @@ def test_energy_matches_oracle(orc, precision, tol):
         assert np.abs(got[k] - want[k]).max() <= tol * pscale, k
 
 
+def test_energy_double_single_matches_fp64_on_16k(orc):
+    """Mixed contexts take the energy's pair sums in double-single arithmetic
+    on the FP32 pipe: on the 16k workload (a moving hole, 28 source splits)
+    E_N, E_PN and both momenta agree with the FP64 context's to 1e-12, and
+    with the oracle's on a 3000-body cluster."""
+    w = WORKLOADS["plummer16k"]
+    x, v, m = w.state()
+    v = v.copy()
+    v[0] = [0.01, -0.02, 0.005]
+    got = {}
+    for precision in ("mixed", "fp64"):
+        ctx = pn.pn_init(w.n, G=w.G, c=w.c, eps=w.eps, precision=precision, device=0)
+        got[precision] = pn.pn_energy(ctx, dev(x), dev(v), dev(m))
+        ctx.close()
+    pscale = float(np.sum(m[:, None] * np.abs(v)))
+    for k in ("E_N", "E_PN"):
+        assert abs(got["mixed"][k] - got["fp64"][k]) <= 1e-12 * abs(got["fp64"][k]), k
+    for k in ("P_N", "P_PN"):
+        assert np.abs(got["mixed"][k] - got["fp64"][k]).max() <= 1e-12 * pscale, k
+    x, v, m = make_cluster(3000, 0.1, 77)
+    v = v.copy()
+    v[0] = [-0.01, 0.003, 0.02]
+    want = orc.energy(x, v, m, c=20.0, eps=1e-3)
+    ctx = pn.pn_init(3000, c=20.0, eps=1e-3, precision="mixed", device=0)
+    g = pn.pn_energy(ctx, dev(x), dev(v), dev(m))
+    ctx.close()
+    for k in ("E_N", "E_PN"):
+        assert abs(g[k] - want[k]) <= 1e-12 * abs(want[k]), k
+    pscale = float(np.sum(m[:, None] * np.abs(v)))
+    for k in ("P_N", "P_PN"):
+        assert np.abs(g[k] - want[k]).max() <= 1e-12 * pscale, k
+
+
 @pytest.mark.parametrize("vel_mode,mode_id", [("vpred_end", 0), ("vhalf", 1)])
 def test_steps_fp64_match_oracle(orc, vel_mode, mode_id):
     """20 KDK steps of the 1k workload: same trajectory to round-off, and at

@@ -87,10 +87,11 @@ def test_watchdog_costs_nothing_when_off_and_rejects_bad_arguments():
     pn.pn_step(ctx, X, V, M, A, w.dt, 20)
     pn.pn_sync(ctx)
     watched = pn.pn_launch_count(ctx) - l0
-    # two checks (steps 30 and 40 of the context's count): 4 energy kernels +
-    # the comparison each, and the kick-drift kernel of step 31, whose kick
-    # and drift could not ride on the epilogue of the checked step 30
-    assert watched - plain == 2 * 5 + 1
+    # two checks (steps 30 and 40 of the context's count): 5 energy kernels
+    # (prologue, double-single staging, pair sums, per-star and per-cluster
+    # sums) + the comparison each, and the kick-drift kernel of step 31, whose
+    # kick and drift could not ride on the epilogue of the checked step 30
+    assert watched - plain == 2 * 6 + 1
     pn.pn_set_watchdog(ctx, 0.0)
     l0 = pn.pn_launch_count(ctx)
     pn.pn_step(ctx, X, V, M, A, w.dt, 20)
