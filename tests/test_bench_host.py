@@ -91,3 +91,23 @@ def test_kernel_hash_follows_code_changes(tmp_path, monkeypatch, edit):
         (dst / "pn_internal.h").write_text(
             hdr.replace(m.group(0), f"constexpr int kPackFlushSources = {2 * int(m.group(1))};"))
     assert _hash_at(monkeypatch, root) != h0
+
+
+def test_committed_traffic_is_found_for_its_instantiation_only():
+    """The committed 128k ncu summary names the kernel instantiation it was
+    captured on; bench.py finds its traffic figure for that instantiation
+    (on the current source) and for no other, e.g. the 2-way unrolled one."""
+    d = os.path.join(bench.ROOT, "profiles")
+    keys = []
+    for f in os.listdir(d):
+        if f.endswith(".md"):
+            keys += re.findall(r"traffic_bytes_per_launch\[fused_packed(<[0-9,]+>)\]",
+                               open(os.path.join(d, f)).read())
+    assert keys, "no committed traffic figure for the packed kernel"
+    inst = keys[0]
+    assert bench.profiled_traffic("fused_packed", inst) is not None
+    nums = [int(v) for v in inst.strip("<>").split(",")]
+    other = nums[:]
+    other[1] = 2 if nums[1] == 1 else 1                  # the other unroll
+    assert bench.profiled_traffic("fused_packed", "<" + ",".join(map(str, other)) + ">") is None
+    assert bench.profiled_traffic("fused_packed") is None  # no instantiation named
