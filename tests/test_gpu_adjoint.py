@@ -68,6 +68,32 @@ def test_accel_vjp_matches_oracle(orc, n):
     assert abs(scal[0, 1] - want[3]) <= 1e-10 * abs(want[3])
 
 
+@pytest.mark.parametrize("sweeps", ["merged", "separate"])
+@pytest.mark.parametrize("n", [2, 3, 40, 513])
+def test_accel_vjp_mixed_small_and_ragged(orc, monkeypatch, n, sweeps):
+    """Mixed contexts on the degenerate and ragged sizes (one star; two; a
+    cluster one slot past a padded block): every cotangent against the
+    oracle's exact one, within the single-precision pair sums' 1e-5 of the
+    largest (the mixed adjoint's own tolerance on the adjoint workload)."""
+    x, v, m = state(n, 900 + n)
+    c, eps = 6.0, 1e-2
+    abar = np.random.default_rng(n + 1).normal(size=(n, 3))
+    want = oracle_vjp_accel(orc, x, v, m, abar, c, eps)
+    if sweeps == "separate":
+        monkeypatch.setenv("PN_ADJ_SEPARATE", "1")
+    ctx = pn.pn_init(n, c=c, eps=eps, precision="mixed", device=0)
+    monkeypatch.delenv("PN_ADJ_SEPARATE", raising=False)
+    X, V, M, AB = dev(x), dev(v), dev(m), dev(abar)
+    XB, VB = torch.empty_like(X), torch.empty_like(X)
+    scal = pn.pn_accel_vjp(ctx, X, V, M, AB, XB, VB)
+    ctx.close()
+    xb, vb = XB.cpu().numpy(), VB.cpu().numpy()
+    assert np.abs(xb - want[0]).max() <= 1e-5 * np.abs(want[0]).max()
+    assert np.abs(vb - want[1]).max() <= 1e-5 * max(np.abs(want[1]).max(), 1e-300)
+    assert abs(scal[0, 0] - want[2]) <= 1e-5 * abs(want[2])
+    assert abs(scal[0, 1] - want[3]) <= 1e-5 * abs(want[3])
+
+
 def test_accel_vjp_larger_cluster_random_projections(orc):
     """n spanning several tiles and splits: check <xbar, u> + <vbar, w> + M_bar
     dM + c2_bar dc2 against abar . (directional derivative) for random

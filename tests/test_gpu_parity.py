@@ -211,6 +211,27 @@ def test_newtonian_limit_and_linearity_in_inv_c2(orc):
     assert rel(d1, o1).max() < 1e-8
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("n", [2, 3])
+def test_energy_smallest_systems(orc, precision, n):
+    """The hole and one or two stars (a single tile, padding slots only
+    otherwise) with a moving hole: every result within 1e-12 of the oracle."""
+    rng = np.random.default_rng(n)
+    x = rng.normal(size=(n, 3))
+    v = rng.normal(size=(n, 3)) * 0.3
+    m = np.full(n, 0.05)
+    m[0] = 0.5
+    want = orc.energy(x, v, m, c=8.0, eps=1e-3)
+    ctx = pn.pn_init(n, c=8.0, eps=1e-3, precision=precision, device=0)
+    got = pn.pn_energy(ctx, dev(x), dev(v), dev(m))
+    ctx.close()
+    for k in ("E_N", "E_PN"):
+        assert abs(got[k] - want[k]) <= 1e-12 * abs(want[k]), k
+    pscale = float(np.sum(m[:, None] * np.abs(v)))
+    for k in ("P_N", "P_PN"):
+        assert np.abs(got[k] - want[k]).max() <= 1e-12 * pscale, k
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-12)])
 def test_energy_matches_oracle(orc, precision, tol):
     x, v, m = make_cluster(513, 0.1, 41)
