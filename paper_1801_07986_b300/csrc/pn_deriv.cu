@@ -1066,20 +1066,71 @@ k_adj_sources(const double4_32a *__restrict__ rec, int64_t S, const Clu *__restr
 // B = (lo d, R^2), C = (v, C), D = (-e/1.5, 0), E = (w, 0), made from the
 // FP64 records; the forward pair kernel stages them.
 
-__global__ void __launch_bounds__(kGlueThreads)
-k_adj_frec(int64_t S, const double4_32a *__restrict__ rec, float4 *__restrict__ frec)
+// Mixed contexts: the adjoint's forward records straight in their
+// single-precision form (rows of 5 float4: hi d and m; lo d and R^2; v and C;
+// -e/1.5; w -- k_jerk_prologue's values, without its zero derivatives, hi/lo
+// split), and the per-block cluster-sum values in k_jerk_prologue's layout
+// (derivative entries zero) for k_jerk_globals.
+__global__ void __launch_bounds__(kProThreads)
+k_adj_prologue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ blk_clu,
+               const double *__restrict__ x, const double *__restrict__ v,
+               const double *__restrict__ m, float4 *__restrict__ frec, double *__restrict__ blk)
 {
-    const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
-    if (t >= S)
-        return;
-    const double4_32a A0 = rec[t], A2 = rec[2 * S + t], A4 = rec[4 * S + t], A6 = rec[6 * S + t];
-    const float h0 = (float)A0.x, h1 = (float)A0.y, h2 = (float)A0.z;
-    frec[t] = make_float4(h0, h1, h2, (float)A0.w);
-    frec[S + t] = make_float4((float)(A0.x - (double)h0), (float)(A0.y - (double)h1),
-                              (float)(A0.z - (double)h2), (float)A2.w);
-    frec[2 * S + t] = make_float4((float)A2.x, (float)A2.y, (float)A2.z, (float)A4.w);
-    frec[3 * S + t] = make_float4((float)A4.x, (float)A4.y, (float)A4.z, 0.0f);
-    frec[4 * S + t] = make_float4((float)A6.x, (float)A6.y, (float)A6.z, 0.0f);
+    __shared__ double sh[2 * kJVals][kProThreads];
+    const int64_t t = (int64_t)blockIdx.x * kProThreads + threadIdx.x;
+    const Clu C = clu[cluster_of_block(blk_clu, (int64_t)blockIdx.x * kProThreads / kGlueThreads)];
+    const int64_t lt = t - C.slot0;
+    double g[2 * kJVals];
+#pragma unroll
+    for (int k = 0; k < 2 * kJVals; ++k)
+        g[k] = 0.0;
+    if (lt < C.ns) {
+        const int64_t j = C.body0 + 1 + lt, h = C.body0;
+        const double GM = C.G * m[h], mj = m[j];
+        double d[3], vel[3];
+        for (int k = 0; k < 3; ++k) {
+            d[k] = x[3 * j + k] - x[3 * h + k];
+            vel[k] = v[3 * j + k];
+        }
+        const double R2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        const double iR = 1.0 / sqrt(R2);
+        const double iR3 = iR * iR * iR;
+        const double c = GM * (1.5 * iR + 0.25 * C.eps2 * iR3);
+        const double Cc = c / 1.5 - (4.0 / 3.0) * (vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]);
+        const double ne = -(0.5 * GM / 1.5) * iR3;
+        double e3[3], w[3];
+        for (int k = 0; k < 3; ++k) {
+            e3[k] = ne * d[k];
+            w[k] = mj * iR3 * d[k];
+        }
+        const float h0 = (float)d[0], h1 = (float)d[1], h2 = (float)d[2];
+        frec[t] = make_float4(h0, h1, h2, (float)mj);
+        frec[S + t] = make_float4((float)(d[0] - (double)h0), (float)(d[1] - (double)h1),
+                                  (float)(d[2] - (double)h2), (float)R2);
+        frec[2 * S + t] = make_float4((float)vel[0], (float)vel[1], (float)vel[2], (float)Cc);
+        frec[3 * S + t] = make_float4((float)e3[0], (float)e3[1], (float)e3[2], 0.0f);
+        frec[4 * S + t] = make_float4((float)w[0], (float)w[1], (float)w[2], 0.0f);
+        for (int k = 0; k < 3; ++k) {
+            g[2 * k] = mj * vel[k];
+            g[2 * (3 + k)] = w[k];
+            g[2 * (6 + k)] = w[k];
+        }
+        g[18] = 1.25 * mj * iR;
+        g[20] = 0.25 * mj * (R2 + C.eps2) * iR3;
+        g[22] = mj * iR;
+    } else {
+        const double px = 1.0e4 + (double)(lt - C.ns);
+        const float hp = (float)px;
+        const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        frec[t] = make_float4(hp, 0.0f, 0.0f, 0.0f);
+        frec[S + t] = make_float4((float)(px - (double)hp), 0.0f, 0.0f, 0.0f);
+        frec[2 * S + t] = z;
+        frec[3 * S + t] = z;
+        frec[4 * S + t] = z;
+    }
+    block_sum<2 * kJVals, kProThreads>(g, sh);
+    if (threadIdx.x < 2 * kJVals)
+        blk[(int64_t)blockIdx.x * 2 * kJVals + threadIdx.x] = sh[threadIdx.x][0];
 }
 
 // ---- packed sweeps (two targets or two sources per f32x2 lane pair) ----
@@ -1959,15 +2010,17 @@ cudaError_t launch_accel_vjp(pn_ctx *c, const double *x, const double *v, const 
     cudaError_t e;
     // forward: records and cluster sums (values); the 16 pair sums in double,
     // or (mixed) by the fused pair kernel on the single-precision records
-    k_jerk_prologue<<<(unsigned)(S / kProThreads), kProThreads, 0, c->stream>>>(
-        S, c->d_clu, bc, x, v, m, nullptr, rec, jblk);
+    if (mixed)     // the single-precision records directly
+        k_adj_prologue<<<(unsigned)(S / kProThreads), kProThreads, 0, c->stream>>>(
+            S, c->d_clu, bc, x, v, m, frec, jblk);
+    else
+        k_jerk_prologue<<<(unsigned)(S / kProThreads), kProThreads, 0, c->stream>>>(
+            S, c->d_clu, bc, x, v, m, nullptr, rec, jblk);
     k_jerk_globals<<<c->nclu, kGlueThreads, 0, c->stream>>>(c->d_clu, jblk, jglob);
     c->launches += 2;
     const double *fwd = part;
     int jsf = js;
     if (mixed) {
-        k_adj_frec<<<(unsigned)nglue, kGlueThreads, 0, c->stream>>>(S, rec, frec);
-        c->launches += 1;
         if ((e = cudaGetLastError()) != cudaSuccess)
             return e;
         // the forward pair sums: given by the caller (an evaluation at this
