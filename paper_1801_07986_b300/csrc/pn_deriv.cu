@@ -387,10 +387,13 @@ __device__ __forceinline__ void jerk_out(double *o, float p, bool first)
 // Grid (target blocks of 256 slots, source splits); split s of a block in a
 // cluster with T tiles sweeps tiles [s T / js, (s+1) T / js).  A copy that
 // does not complete within the wait limit sets kFlagTimeout in `flag`.
+// fpart != nullptr (the caller's splits hold at most kJPackFlush tiles, so a
+// split's partial is one FP32 sum): the partials go to fpart as floats, same
+// layout, for k_split_sum_f32.
 __global__ void __launch_bounds__(kMixThreads, 3)
 k_jerk_pairs_packed(const float4 *__restrict__ srec, int64_t S, const Clu *__restrict__ clu,
                     const int *__restrict__ blk_clu, int *__restrict__ flag,
-                    double *__restrict__ part)
+                    double *__restrict__ part, float *__restrict__ fpart)
 {
     __shared__ __align__(128) float4 sh[2][kJPackTile][kJPackVals];
     __shared__ __align__(8) uint64_t full[2];
@@ -400,11 +403,17 @@ k_jerk_pairs_packed(const float4 *__restrict__ srec, int64_t S, const Clu *__res
     const int64_t js = gridDim.y, sp = blockIdx.y;
     const int64_t tb = sp * ntiles / js, te = (sp + 1) * ntiles / js;
     double *out = part + sp * 2 * kFusedVals * S;
+    float *fout = fpart ? fpart + sp * 2 * kFusedVals * S : nullptr;
     const int64_t ta = t0 + threadIdx.x, tq = ta + kMixThreads;
     if (te <= tb) {               // an empty split still owns its outputs
         for (int k = 0; k < 2 * kFusedVals; ++k) {
-            out[k * S + ta] = 0.0;
-            out[k * S + tq] = 0.0;
+            if (fout) {
+                fout[k * S + ta] = 0.0f;
+                fout[k * S + tq] = 0.0f;
+            } else {
+                out[k * S + ta] = 0.0;
+                out[k * S + tq] = 0.0;
+            }
         }
         return;
     }
@@ -468,10 +477,17 @@ k_jerk_pairs_packed(const float4 *__restrict__ srec, int64_t S, const Clu *__res
         if (((tile - tb + 1) % kJPackFlush) == 0 || tile + 1 == te) {
 #pragma unroll
             for (int k = 0; k < kFusedVals; ++k) {
-                jerk_out(out + (2 * k) * S + ta, acc[k].v.x, first);
-                jerk_out(out + (2 * k) * S + tq, acc[k].v.y, first);
-                jerk_out(out + (2 * k + 1) * S + ta, acc[k].d.x, first);
-                jerk_out(out + (2 * k + 1) * S + tq, acc[k].d.y, first);
+                if (fout) {            // the split's only flush
+                    fout[(2 * k) * S + ta] = acc[k].v.x;
+                    fout[(2 * k) * S + tq] = acc[k].v.y;
+                    fout[(2 * k + 1) * S + ta] = acc[k].d.x;
+                    fout[(2 * k + 1) * S + tq] = acc[k].d.y;
+                } else {
+                    jerk_out(out + (2 * k) * S + ta, acc[k].v.x, first);
+                    jerk_out(out + (2 * k) * S + tq, acc[k].v.y, first);
+                    jerk_out(out + (2 * k + 1) * S + ta, acc[k].d.x, first);
+                    jerk_out(out + (2 * k + 1) * S + tq, acc[k].d.y, first);
+                }
                 acc[k] = P2{make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
             }
             first = false;
@@ -1693,6 +1709,39 @@ k_split_sum(int64_t S, int nv, int js, double *__restrict__ part)
     part[e] = acc;
 }
 
+// FP32 split partials (fpart, [split][value][slot], each one FP32 sum)
+// added in split order by a compensated FP32 sum (Knuth's TwoSum carrying
+// every addition's rounding error: no FP64 additions, whose pipe runs at
+// 1/64 of FP32's) into split 0 of the FP64 layout, out[value][slot].
+__global__ void __launch_bounds__(kGlueThreads)
+k_split_sum_f32(int64_t S, int nv, int js, const float *__restrict__ fpart,
+                double *__restrict__ out)
+{
+    const int64_t e = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
+    if (e >= nv * S)
+        return;
+    const int64_t stride = (int64_t)nv * S;
+    float hi = 0.0f, lo = 0.0f;
+    auto add = [&](float x) {
+        const float sum = hi + x, z = sum - hi;
+        lo += (hi - (sum - z)) + (x - z);
+        hi = sum;
+    };
+    int q = 0;
+    for (; q + 8 <= js; q += 8) {
+        float r[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            r[i] = fpart[(int64_t)(q + i) * stride + e];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            add(r[i]);
+    }
+    for (; q < js; ++q)
+        add(fpart[(int64_t)q * stride + e]);
+    out[e] = (double)hi + (double)lo;
+}
+
 // Per star slot, one thread each: the records' and cluster sums' reverse for
 // star j (d_j, v_j and M), plus every cotangent gathered so far; writes the
 // star's xbar and vbar and, per block of kAdjStarSlots slots, -sum dbar (the
@@ -1917,11 +1966,25 @@ cudaError_t launch_jerk(pn_ctx *c, const double *x, const double *v, const doubl
                                  cudaFuncAttributePreferredSharedMemoryCarveout, 100);
             carveout = true;
         }
+        // splits of at most kJPackFlush tiles: FP32 partials (one flush each)
+        // in the upper half of the partial region, summed by k_split_sum_f32
+        const int64_t tps = (c->max_ns_pad / kJPackTile + jp - 1) / jp;
+        float *fpart = (jp > 1 && tps <= kJPackFlush)
+                           ? reinterpret_cast<float *>(part + (int64_t)js * kFusedVals * S)
+                           : nullptr;
         k_jerk_stage<<<(unsigned)nglue, kGlueThreads, 0, c->stream>>>(S, rec, srec);
         k_jerk_pairs_packed<<<dim3((unsigned)(S / kJPackTI), (unsigned)jp), kMixThreads, 0,
-                              c->stream>>>(srec, S, c->d_clu, bc, c->flag, part);
+                              c->stream>>>(srec, S, c->d_clu, bc, c->flag, part, fpart);
         c->launches += 2;
         jsum = jp;
+        if (fpart) {
+            if ((e = cudaGetLastError()) != cudaSuccess)
+                return e;
+            k_split_sum_f32<<<(unsigned)((2 * kFusedVals * S + kGlueThreads - 1) / kGlueThreads),
+                              kGlueThreads, 0, c->stream>>>(S, 2 * kFusedVals, jp, fpart, part);
+            c->launches += 1;
+            jsum = 1;
+        }
     } else {
         k_dual_pairs<Dual><<<grid, kJThreads, 0, c->stream>>>(rec, S, c->d_clu, bc, part);
         c->launches += 1;
