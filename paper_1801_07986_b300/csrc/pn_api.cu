@@ -1134,9 +1134,18 @@ pn_status kdk_backward(pn_ctx *c, const double *cp, int64_t K, const double *x0,
         if (!c->adj_stream)
             PN_CUDA(cudaStreamCreateWithFlags(&c->adj_stream, cudaStreamNonBlocking),
                     "adjoint stream");
-        cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-        for (auto &e : ev)
-            PN_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+        struct Events {        // the handoff events, destroyed on every return
+            cudaEvent_t e[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+            ~Events()
+            {
+                for (cudaEvent_t x : e)
+                    if (x)
+                        cudaEventDestroy(x);
+            }
+        } evs;
+        cudaEvent_t *ev = evs.e;
+        for (int k = 0; k < 5; ++k)
+            PN_CUDA(cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming), "event");
         cudaEvent_t start = ev[0], rerun_done[2] = {ev[1], ev[2]}, rev_done[2] = {ev[3], ev[4]};
         cudaStream_t A = c->stream, B = c->adj_stream;
         auto on_b = [&](int64_t sg) -> pn_status {
@@ -1169,9 +1178,6 @@ pn_status kdk_backward(pn_ctx *c, const double *cp, int64_t K, const double *x0,
         s2 = run();
         c->stream = A;
         cudaStreamSynchronize(B);      // (on an error, before the buffers go)
-        for (auto &e : ev)
-            if (e)
-                cudaEventDestroy(e);
         if (s2 != PN_OK)
             return s2;
     }
