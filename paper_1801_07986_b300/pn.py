@@ -467,8 +467,9 @@ def pn_step_host(ctx: Context, x, v, m, a, dt: float, nsteps: int = 1) -> None:
 
 
 def pn_energy(ctx: Context, x, v, m):
-    """Eq. 7 energy and Eq. 8 momentum (FP64), as a dict like the oracle's
-    (a list of dicts, one per cluster, on a batched context)."""
+    """Eq. 7 energy and Eq. 8 momentum, as a dict like the oracle's (a list
+    of dicts, one per cluster, on a batched context).  Pair sums in FP64
+    (FP64 context) or double-single (mixed context), the rest in FP64."""
     n = ctx.n
     out = np.zeros(8 * ctx.n_clusters)
     _check(_load().pn_energy(ctx.handle, _dev(ctx, x, (n, 3), "x"), _dev(ctx, v, (n, 3), "v"),
