@@ -499,10 +499,14 @@ def run_native(args, w):
             e1.record(stream)
             e1.synchronize()
             tot += e0.elapsed_time(e1)
-        line["e2e"] = {"value": float(w.n) * (w.n - 1) * e2e_steps / (tot * 1e-3),
+        if world > 1:       # whole job: every rank's steps over the slowest rank's time
+            t = torch.tensor([tot, dev_ms], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            tot, dev_ms = float(t[0].item()), float(t[1].item())
+        line["e2e"] = {"value": float(w.n) * (w.n - 1) * e2e_steps * world / (tot * 1e-3),
                        "unit": "interactions/s", "h2d_bytes_per_step": 80 * w.n,
                        "d2h_bytes_per_step": 72 * w.n, "steps": e2e_steps,
-                       "device_value_same_steps": float(w.n) * (w.n - 1) * e2e_steps
+                       "device_value_same_steps": float(w.n) * (w.n - 1) * e2e_steps * world
                        / (dev_ms * 1e-3),
                        "steps_note": "the first steps of the timed run, again from its start state"}
 
