@@ -119,6 +119,48 @@ def test_batched_steps_match_oracle_and_graph_replays_bitwise(orc):
     ctx.close()
 
 
+@pytest.mark.parametrize("spatial", ["0", "1"])
+def test_mixed_graph_replays_equal_eager_steps_bitwise(orc, monkeypatch, spatial):
+    """Mixed precision with the near-source split and its side stream, on the
+    slot order and on the Hilbert order (sorted again every evaluation):
+    two replays of a 3-step graph give the same bits as one 6-step pn_step
+    call (no step depends on how the steps are grouped into calls), and the
+    final state stays within the mixed tolerance of the oracle's 6 KDK
+    steps, cluster by cluster (the median relative error of the change of x
+    and of v over the steps within 1e-6; the 1PN terms make a median 2e-5
+    to 4e-4 of the velocity change in these clusters, so a dropped term
+    fails it)."""
+    monkeypatch.setenv("PN_SPATIAL", spatial)
+    x, v, m, off, cs, es = batch(sizes=[300, 1025, 2048, 513])
+    dt = 1.0 / 2048
+    ctx = pn.pn_init_batched(off, c=cs, eps=es, precision="mixed", device=0)
+    X, V, M = dev(x), dev(v), dev(m)
+    A = torch.empty_like(X)
+    pn.pn_accel(ctx, X, V, M, A)
+    X2, V2, A2 = X.clone(), V.clone(), A.clone()
+    pn.pn_step(ctx, X, V, M, A, dt, 6)
+    pn.pn_step_graph(ctx, X2, V2, M, A2, dt, 3)
+    pn.pn_step_graph(ctx, X2, V2, M, A2, dt, 3)
+    pn.pn_sync(ctx)
+    assert torch.equal(X, X2) and torch.equal(V, V2) and torch.equal(A, A2)
+    if spatial == "1":
+        _, units = pn.pn_get_pair_stats(ctx)
+        assert units > 0            # the spatially ordered kernel ran
+    xg, vg = X.cpu().numpy(), V.cpu().numpy()
+    for k, (a, b) in enumerate(zip(off[:-1], off[1:])):
+        a0 = orc.accel(x[a:b], v[a:b], m[a:b], c=cs[k], eps=es[k])
+        xo, vo, _ = orc.step(x[a:b], v[a:b], m[a:b], a0, dt, 6, c=cs[k], eps=es[k])
+        # six steps of dt carry the force error as dt^2-sized position error
+        # on top of the state: compare the change over the steps
+        dx = np.linalg.norm((xg[a:b] - xo), axis=-1)
+        scale = np.linalg.norm(xo - x[a:b], axis=-1)
+        assert np.median(dx / scale) <= 1e-6, (k, np.median(dx / scale))
+        dv = np.linalg.norm((vg[a:b] - vo), axis=-1)
+        vscale = np.linalg.norm(vo - v[a:b], axis=-1)
+        assert np.median(dv / vscale) <= 1e-6, (k, np.median(dv / vscale))
+    ctx.close()
+
+
 def test_tune_keeps_parity(orc):
     x, v, m, off, cs, es = batch()
     ctx = pn.pn_init_batched(off, c=cs, eps=es, precision="mixed", device=0)
