@@ -340,7 +340,8 @@ __device__ __forceinline__ void jerk_pair(const JTarget &tg, const float4 *__res
     acc[3].d = add2(acc[3].d, mis.d);
     acc[4].v = add2(acc[4].v, mis3.v);
     acc[4].d = add2(acc[4].d, mis3.d);
-    p2_acc(acc[5], mis3, P2{hi2(S3), hi2(S5)});
+    // acc[5] (Wr and its derivative) is not summed: k_jerk_epilogue restores
+    // it from N, U and Z by the identity of the acceleration path
     const float4 S6 = sq[6], S7 = sq[7], S8 = sq[8], S9 = sq[9];
     const P2 vjx = {lo2(S6), lo2(S8)}, vjy = {hi2(S6), hi2(S8)}, vjz = {lo2(S7), lo2(S9)};
     // x . v_j, x . (8/3) v_i
@@ -515,7 +516,7 @@ k_jerk_epilogue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ 
                 const double *__restrict__ m, const double *__restrict__ a,
                 const double *__restrict__ part, int js, const double *__restrict__ globs,
                 double *__restrict__ jerk, int *flag, unsigned long long *flag_step,
-                unsigned long long step, double *__restrict__ blk)
+                unsigned long long step, double *__restrict__ blk, int wr_identity)
 {
     __shared__ double sh[6][kProThreads];
     const int64_t t = (int64_t)blockIdx.x * kProThreads + threadIdx.x;
@@ -555,6 +556,14 @@ k_jerk_epilogue(int64_t S, const Clu *__restrict__ clu, const int *__restrict__ 
         ss.U = s[3];
         ss.Z = s[4];
         ss.Wr = s[5];
+        if (wr_identity) {
+            // the pair kernel left Wr out: R_j^2 = R_i^2 - 2 d_i.x_ij + r_ij^2 - eps^2
+            // gives Wr = sum_j m_j R_j^2 / r_ij^3 = (R_i^2 - eps^2) Z - 2 d_i.N + U,
+            // here on Duals (the value and its derivative along the trajectory)
+            const Dual R2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            ss.Wr = (R2 - Cl.eps2) * ss.Z - 2.0 * (d[0] * ss.N[0] + d[1] * ss.N[1] + d[2] * ss.N[2]) +
+                    ss.U;
+        }
         ss.Hs = s[9];
         ClusterSums<Dual> gs;
         for (int k = 0; k < 3; ++k) {
@@ -1997,7 +2006,8 @@ cudaError_t launch_jerk(pn_ctx *c, const double *x, const double *v, const doubl
         c->launches += 1;
     }
     k_jerk_epilogue<<<(unsigned)npb, kProThreads, 0, c->stream>>>(
-        S, c->d_clu, bc, x, v, m, a, part, 1, glob, jerk, c->flag, c->flag_step, step, bhb);
+        S, c->d_clu, bc, x, v, m, a, part, 1, glob, jerk, c->flag, c->flag_step, step, bhb,
+        c->p.precision == PN_MIXED ? 1 : 0);
     c->launches += 1;
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;

@@ -82,6 +82,15 @@ def test_jerk_strong_field_and_near_hole(orc):
     assert np.median(rel(a_mix, a_want)) <= 2e-7
     err = rel(j_mix, j_want)
     assert np.median(err) <= 2e-5 and err.max() <= 1e-3, (np.median(err), err.max())
+    # the hole's jerk against the size of its 1PN part: the mixed pair kernel
+    # leaves the stars' Wr sums out and the epilogue restores them from N, U
+    # and Z (Wr enters the hole's Eq. 3 terms only); with Wr left out
+    # altogether the hole's error here is 3e-4 of its 1PN part, with the
+    # restoration 2e-9
+    hole_1pn = np.linalg.norm(j_want[0] - jn[0])
+    for jj in (j, j_mix):
+        assert np.linalg.norm(jj[0] - j_want[0]) <= 1e-6 * hole_1pn, (
+            np.linalg.norm(jj[0] - j_want[0]) / hole_1pn)
 
 
 def test_jerk_plummer16k_against_oracle(orc):
