@@ -696,7 +696,8 @@ def run_jerk(local, stream, warmup, reps=5):
     """The jerk (Appendix A) and the Hermite integrator on the 16k Plummer
     workload in a mixed-precision context: pn_jerk (A, then the dual-number
     jerk pass with single-precision pair sums) timed with CUDA events, and a
-    Hermite step (two A + two jerk evaluations)."""
+    Hermite step (two A + two jerk evaluations) from calls of 2 and 10
+    steps."""
     import torch
     from paper_1801_07986_b300 import pn
     from paper_1801_07986_b300.inputs import WORKLOADS
@@ -720,12 +721,19 @@ def run_jerk(local, stream, warmup, reps=5):
     ms_jerk = e0.elapsed_time(e1) / reps
     pn.pn_step(ctx, X, V, M, A, w.dt, 1)
     pn.pn_sync(ctx)
-    e0.record(stream)
-    pn.pn_step(ctx, X, V, M, A, w.dt, 2)
-    e1.record(stream)
-    e1.synchronize()
-    pn.pn_sync(ctx)
-    ms_step = e0.elapsed_time(e1) / 2
+    # a call of k Hermite steps costs k steps (two A + two jerk evaluations
+    # each) plus the call's own jerk at the entry state and A at the end:
+    # calls of 2 and 10 steps separate the two
+    call_ms = {}
+    for k in (2, 10):
+        e0.record(stream)
+        pn.pn_step(ctx, X, V, M, A, w.dt, k)
+        e1.record(stream)
+        e1.synchronize()
+        pn.pn_sync(ctx)
+        call_ms[k] = e0.elapsed_time(e1)
+    ms_step = (call_ms[10] - call_ms[2]) / 8
+    ms_call_fixed = call_ms[2] - 2 * ms_step
     ctx.close()
     pairs = float(w.n - 1) * (w.n - 2)
     peaks = measured_peaks()
@@ -738,6 +746,9 @@ def run_jerk(local, stream, warmup, reps=5):
             "what": "pn_jerk in a mixed context: A + dual-number jerk (FP32 pair sums), "
                     "per evaluation",
             "ms_per_jerk": ms_jerk, "hermite_ms_per_step": ms_step,
+            "hermite_ms_per_call_fixed": ms_call_fixed,
+            "hermite_note": "per step from calls of 2 and 10 steps; the fixed part is each "
+                            "call's jerk at the entry state and its final A",
             "roofline": {"bound": "alu", "achieved": both, "peak": peak, "unit": "TFLOP/s",
                          "frac": both / peak,
                          "peak_basis": f"148 SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
