@@ -235,7 +235,8 @@ k_dual_pairs(const double4_32a *__restrict__ rec, int64_t S, const Clu *__restri
 //   S8 = (ax, ay)    S9 = (az, C')   S10 = (Dx, Dy)     S11 = (Dz, D'x)
 //   S12 = (D'y, D'z) S13 = (wx, wy)  S14 = (wz, w'x)    S15 = (w'y, w'z)
 // (h, l = hi/lo split of d_j, primes: derivatives along the trajectory,
-// a = v', D = -e_j/1.5, C = c_j/1.5 - 4/3 |v_j|^2).  Tiles of kJPackTile
+// a = v', D = -e_j/1.5, C = c_j/1.5 - 4/3 |v_j|^2; R^2 and (R^2)' are
+// staged but not read, the epilogue restoring the Wr sum).  Tiles of kJPackTile
 // sources move by bulk copies into two shared buffers as in the
 // acceleration kernel.
 
