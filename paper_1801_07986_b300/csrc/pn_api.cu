@@ -1665,11 +1665,14 @@ void read_tune_file()
     FILE *f = std::fopen(path, "r");
     if (!f)
         return;
-    TuneKey k;
-    pn::FusedVariant v;
-    while (std::fscanf(f, "%d %d %d %d %d %d %d %d", &k.bucket, &k.precision, &k.many, &v.P,
-                       &v.unroll, &v.packed, &v.tile, &v.stages) == 8)
-        g_tune[k] = v;
+    char line[256];
+    while (std::fgets(line, sizeof line, f)) {
+        TuneKey k;
+        pn::FusedVariant v;
+        if (std::sscanf(line, "%d %d %d %d %d %d %d %d", &k.bucket, &k.precision, &k.many, &v.P,
+                        &v.unroll, &v.packed, &v.tile, &v.stages) == 8)
+            g_tune[k] = v;
+    }
     std::fclose(f);
 }
 

@@ -195,14 +195,19 @@ print(int(t["cached"]), t["targets_per_thread"], t["unroll"], int(t["packed"]), 
 def test_tune_reports_tile_and_keeps_its_choice_in_the_cache_file(tmp_path):
     """pn_tune searches the packed kernel's j-tile and buffers too, reports
     them, and with PN_TUNE_CACHE a later process takes the choice from the
-    file without timing again."""
+    file without timing again (a malformed line before it is skipped)."""
     import os
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    env = dict(os.environ, PYTHONPATH=root, PN_TUNE_CACHE=str(tmp_path / "tune.txt"))
-    runs = [subprocess.run([sys.executable, "-c", TUNE_CHILD], env=env, capture_output=True,
-                           text=True, timeout=600, cwd=root) for _ in range(2)]
+    cache = tmp_path / "tune.txt"
+    env = dict(os.environ, PYTHONPATH=root, PN_TUNE_CACHE=str(cache))
+    runs = []
+    for q in range(2):
+        if q == 1:
+            cache.write_text("not a tuning line\n" + cache.read_text())
+        runs.append(subprocess.run([sys.executable, "-c", TUNE_CHILD], env=env,
+                                   capture_output=True, text=True, timeout=600, cwd=root))
     for r in runs:
         assert r.returncode == 0, r.stderr[-2000:]
     first, second = (r.stdout.split() for r in runs)
@@ -210,8 +215,8 @@ def test_tune_reports_tile_and_keeps_its_choice_in_the_cache_file(tmp_path):
     assert first[1:] == second[1:]
     P, unroll, packed, tile, stages = (int(q) for q in first[1:])
     assert (tile, stages) in ((64, 6), (64, 4), (32, 8)) if packed else stages == 0
-    lines = (tmp_path / "tune.txt").read_text().split("\n")
-    assert len([q for q in lines if q.strip()]) == 1
+    lines = cache.read_text().split("\n")
+    assert len([q for q in lines if q.strip()]) == 2      # the bad line + the one choice
 
 
 def test_nonfinite_in_one_cluster_is_reported():
