@@ -53,8 +53,9 @@ OPS_PACKED = 46    # FP32-pipe operations per pair of that body (FMA, add and mu
 FLOPS_PACKED_FAR = 67  # the same body on far units of the spatial order (x_ij from the high
                        # parts: 6 adds fewer)
 OPS_PACKED_FAR = 40
-FLOPS_JERK = 207   # hand count of the FP32 dual-number pair body of the jerk (mixed contexts;
-                   # the FP64 contexts' body also sums Wr: 213)
+FLOPS_JERK = 199   # hand count of the FP32 dual-number pair body of the jerk (mixed contexts,
+                   # sources beyond r_near, the law-of-cosines hole term; nearer sources 207;
+                   # the FP64 contexts' body, D form and the Wr sum: 213)
 FLOPS_ENERGY = 44  # hand count of the FP64 energy pair body (Eq. 7-8 sums; FMA = 2, the
                    # rsqrt seed 1, its Newton step 5)
 OPS_ENERGY_DS = 355  # FP32-pipe operations per pair of the double-single energy body (mixed

@@ -230,13 +230,16 @@ k_dual_pairs(const double4_32a *__restrict__ rec, int64_t S, const Clu *__restri
 // two targets (t, t + 128 of a 256-target block) against one source, on
 // duals P2 = (two values, two derivatives).  Staged source records, every
 // field duplicated (f, f) and the position terms negated (16 float4 per slot):
-//   S0 = (-hx, -hy)  S1 = (-hz, m)    S2 = (-lx, -ly)    S3 = (-lz, R^2)
-//   S4 = (-d'x, -d'y) S5 = (-d'z, (R^2)')  S6 = (vx, vy)  S7 = (vz, C)
-//   S8 = (ax, ay)    S9 = (az, C')   S10 = (Dx, Dy)     S11 = (Dz, D'x)
+//   S0 = (-hx, -hy)  S1 = (-hz, m)    S2 = (-lx, -ly)    S3 = (-lz, al)
+//   S4 = (-d'x, -d'y) S5 = (-d'z, al')  S6 = (vx, vy)    S7 = (vz, K)
+//   S8 = (ax, ay)    S9 = (az, K')   S10 = (Dx, Dy)     S11 = (Dz, D'x)
 //   S12 = (D'y, D'z) S13 = (wx, wy)  S14 = (wz, w'x)    S15 = (w'y, w'z)
 // (h, l = hi/lo split of d_j, primes: derivatives along the trajectory,
-// a = v', D = -e_j/1.5, C = c_j/1.5 - 4/3 |v_j|^2; R^2 and (R^2)' are
-// staged but not read, the epilogue restoring the Wr sum).  Tiles of kJPackTile
+// a = v', D = -e_j/1.5, C = c_j/1.5 - 4/3 |v_j|^2.  Sources at least r_near
+// from the hole take the hole term of kappa in the law-of-cosines form of
+// the acceleration kernel: al = D.d_j / (2 R_j^2) = -G M / (6 R_j^3),
+// K = C + al (R_j^2 + eps^2); nearer ones keep the D form, with al = 0 and
+// K = C.  The Wr sum is left out, the epilogue restoring it.)  Tiles of kJPackTile
 // sources move by bulk copies into two shared buffers as in the
 // acceleration kernel.
 
@@ -247,11 +250,13 @@ constexpr int kJPackTI = 2 * kMixThreads;   // targets per block
 constexpr int kJPackBytes = kJPackTile * kJPackVals * 16;
 
 __global__ void __launch_bounds__(kGlueThreads)
-k_jerk_stage(int64_t S, const double4_32a *__restrict__ rec, float4 *__restrict__ srec)
+k_jerk_stage(int64_t S, const double4_32a *__restrict__ rec, float4 *__restrict__ srec,
+             const Clu *__restrict__ clu, const int *__restrict__ blk_clu)
 {
     const int64_t t = (int64_t)blockIdx.x * kGlueThreads + threadIdx.x;
     if (t >= S)
         return;
+    const Clu Cl = clu[cluster_of_block(blk_clu, blockIdx.x)];
     const double4_32a J0 = rec[t], J1 = rec[S + t], J2 = rec[2 * S + t], J3 = rec[3 * S + t];
     const double4_32a J4 = rec[4 * S + t], J5 = rec[5 * S + t], J6 = rec[6 * S + t],
                       J7 = rec[7 * S + t];
@@ -264,14 +269,29 @@ k_jerk_stage(int64_t S, const double4_32a *__restrict__ rec, float4 *__restrict_
     float4 *o = srec + t * kJPackVals;
     o[0] = make_float4(-h0, -h0, -h1, -h1);
     o[1] = make_float4(-h2, -h2, (float)J0.w, (float)J0.w);
+    // far sources (R_j >= r_near): the law-of-cosines form of the hole term,
+    // D_j.d_i = al (R_i^2 - r_ij^2) + al (R_j^2 + eps^2) with al = D_j.d_j /
+    // (2 R_j^2), on duals; near sources keep the D form (al = 0 marks them)
+    const double R2 = J2.w, R2p = J3.w;
+    double al = 0.0, alp = 0.0, K = J4.w, Kp = J5.w;
+    if (Cl.r_near > 0.0 && R2 >= Cl.r_near * Cl.r_near) {
+        const double Dd = J4.x * J0.x + J4.y * J0.y + J4.z * J0.z;
+        const double Dpd = J5.x * J0.x + J5.y * J0.y + J5.z * J0.z;
+        const double Ddp = J4.x * J1.x + J4.y * J1.y + J4.z * J1.z;
+        al = Dd / (2.0 * R2);
+        alp = (Dpd + Ddp) / (2.0 * R2) - al * R2p / R2;
+        const double s = R2 + Cl.eps2;
+        K = J4.w + al * s;
+        Kp = J5.w + alp * s + al * R2p;
+    }
     o[2] = make_float4(-l0, -l0, -l1, -l1);
-    o[3] = make_float4(-l2, -l2, (float)J2.w, (float)J2.w);
+    o[3] = make_float4(-l2, -l2, (float)al, (float)al);
     o[4] = dup(-J1.x, -J1.y);
-    o[5] = dup(-J1.z, J3.w);
+    o[5] = dup(-J1.z, alp);
     o[6] = dup(J2.x, J2.y);
-    o[7] = dup(J2.z, J4.w);
+    o[7] = dup(J2.z, K);
     o[8] = dup(J3.x, J3.y);
-    o[9] = dup(J3.z, J5.w);
+    o[9] = dup(J3.z, Kp);
     o[10] = dup(J4.x, J4.y);
     o[11] = dup(J4.z, J5.x);
     o[12] = dup(J5.y, J5.z);
@@ -300,6 +320,7 @@ struct JTarget {
     float2 hx, hy, hz, lx, ly, lz;   // hi/lo split of d_i
     float2 dx, dy, dz;               // d_i'
     float2 vx, vy, vz, ax, ay, az;   // 8/3 v_i, 8/3 a_i
+    float2 rr, rrp;                  // R_i^2 and its derivative
 };
 
 template <bool MASK>
@@ -352,15 +373,25 @@ __device__ __forceinline__ void jerk_pair(const JTarget &tg, const float4 *__res
     P2 xvi = p2_mul(x, P2{tg.vx, tg.ax});
     p2_acc(xvi, y, P2{tg.vy, tg.ay});
     p2_acc(xvi, z, P2{tg.vz, tg.az});
-    // kk = C_j + (8/3) v_i . v_j + D_j . h_i
-    const float4 S10 = sq[10], S11 = sq[11], S12 = sq[12];
-    P2 kk = {hi2(S7), hi2(S9)};
+    // kk = C_j + (8/3) v_i . v_j + D_j . h_i; far sources (al != 0, the same
+    // for every lane) take D_j . d_i = al (R_i^2 - r_ij^2) + (K - C)
+    const float2 al = hi2(S3);
+    P2 kk;
+    if (al.x != 0.0f) {
+        const float2 alp = hi2(S5);
+        const float2 tt = fma2(s2, make_float2(-1.0f, -1.0f), tg.rr);
+        kk = P2{fma2(al, tt, hi2(S7)),
+                fma2(alp, tt, fma2(al, fma2(q, make_float2(-2.0f, -2.0f), tg.rrp), hi2(S9)))};
+    } else {
+        const float4 S10 = sq[10], S11 = sq[11], S12 = sq[12];
+        kk = P2{hi2(S7), hi2(S9)};
+        p2_acc(kk, P2{lo2(S10), hi2(S11)}, P2{tg.hx, tg.dx});
+        p2_acc(kk, P2{hi2(S10), lo2(S12)}, P2{tg.hy, tg.dy});
+        p2_acc(kk, P2{lo2(S11), hi2(S12)}, P2{tg.hz, tg.dz});
+    }
     p2_acc(kk, P2{tg.vx, tg.ax}, vjx);
     p2_acc(kk, P2{tg.vy, tg.ay}, vjy);
     p2_acc(kk, P2{tg.vz, tg.az}, vjz);
-    p2_acc(kk, P2{lo2(S10), hi2(S11)}, P2{tg.hx, tg.dx});
-    p2_acc(kk, P2{hi2(S10), lo2(S12)}, P2{tg.hy, tg.dy});
-    p2_acc(kk, P2{lo2(S11), hi2(S12)}, P2{tg.hz, tg.dz});
     const P2 h = p2_mul(xvj, is2);
     p2_acc(kk, h, xvj);
     const P2 f = p2_mul(mis3, kk);
@@ -454,6 +485,9 @@ k_jerk_pairs_packed(const float4 *__restrict__ srec, int64_t S, const Clu *__res
         tg.ax = make_float2(e3 * A8.x, e3 * B8.x);
         tg.ay = make_float2(e3 * A8.z, e3 * B8.z);
         tg.az = make_float2(e3 * A9.x, e3 * B9.x);
+        tg.rr = fma2(tg.hx, tg.hx, fma2(tg.hy, tg.hy, mul2(tg.hz, tg.hz)));
+        tg.rrp = mul2(make_float2(2.0f, 2.0f),
+                      fma2(tg.hx, tg.dx, fma2(tg.hy, tg.dy, mul2(tg.hz, tg.dz))));
     }
     const float e2 = (float)C.eps2;
     const float2 eps2 = make_float2(e2, e2);
@@ -1982,7 +2016,7 @@ cudaError_t launch_jerk(pn_ctx *c, const double *x, const double *v, const doubl
         float *fpart = (jp > 1 && tps <= kJPackFlush)
                            ? reinterpret_cast<float *>(part + (int64_t)js * kFusedVals * S)
                            : nullptr;
-        k_jerk_stage<<<(unsigned)nglue, kGlueThreads, 0, c->stream>>>(S, rec, srec);
+        k_jerk_stage<<<(unsigned)nglue, kGlueThreads, 0, c->stream>>>(S, rec, srec, c->d_clu, bc);
         k_jerk_pairs_packed<<<dim3((unsigned)(S / kJPackTI), (unsigned)jp), kMixThreads, 0,
                               c->stream>>>(srec, S, c->d_clu, bc, c->flag, part, fpart);
         c->launches += 2;

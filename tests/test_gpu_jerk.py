@@ -63,9 +63,13 @@ def test_jerk_fp64_matches_oracle(orc, n, c):
     assert err.max() <= JERK_TOL, (err.max(), int(err.argmax()))
 
 
-def test_jerk_strong_field_and_near_hole(orc):
+@pytest.mark.parametrize("r_near", [0.05, 0.0])
+def test_jerk_strong_field_and_near_hole(orc, r_near):
     """Stars close to the hole at low c, where the 1PN part of the jerk is
-    large (and the mixed acceleration path splits near sources off)."""
+    large (and the mixed acceleration path splits near sources off).  In the
+    mixed jerk, sources beyond r_near take the hole term in the
+    law-of-cosines form and nearer ones (here star 5, 0.01 from the hole)
+    the D form; r_near = 0 puts every source on the D form."""
     x, v, m = cluster(600, 0.5, 77)
     x[5] = x[0] + np.array([0.01, 0.0, 0.002])
     v[5] = v[0] + np.array([0.0, 7.0, 0.0])
@@ -78,7 +82,7 @@ def test_jerk_strong_field_and_near_hole(orc):
     assert rel(j, j_want).max() <= JERK_TOL
     # mixed context: a in mixed precision, the jerk's pair sums in FP32 (the
     # jerk enters Hermite's predictor and corrector with dt^2, dt^3 weights)
-    a_mix, j_mix = gpu_jerk(x, v, m, precision="mixed", c=c, eps=1e-4)
+    a_mix, j_mix = gpu_jerk(x, v, m, precision="mixed", c=c, eps=1e-4, r_near=r_near)
     assert np.median(rel(a_mix, a_want)) <= 2e-7
     err = rel(j_mix, j_want)
     assert np.median(err) <= 2e-5 and err.max() <= 1e-3, (np.median(err), err.max())
